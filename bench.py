@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of the Jacobi-PCG hot path on one B300 per rank.
+
+Workload (one step = one full solve, inputs resident in HBM): the 3D 7-point
+variable-coefficient diffusion operator on an N^3 interior grid (default
+N = 256: n = 16,777,216 unknowns, nnz = 117,047,296), face coefficients
+exp(N(0,1)) from seed 1, b ~ U[-1,1] from seed 11, Jacobi-preconditioned CG
+from x0 = 0 to relative residual 1e-8 (recursive residual, then the true
+residual is recomputed).  The working set (~2.2 GB) is far larger than L2,
+so no flush is needed between steps.
+
+Ranks (torchrun) are independent replicas: each solves its own copy, no
+collective touches the data path (the solve does not shard on one box).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG time to rel-res 1e-8 & SpMV GB/s vs 8 TB/s; learned vs Jacobi-PCG speedup"
+NOMINAL_HBM_GBS = 8000.0
+FALLBACK_HBM_GBS = 6400.0
+FP64_PEAK_TFLOPS = 1.102  # measured DFMA throughput of this B300 SKU (2 flop / DFMA), see DESIGN
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=256, help="grid side N of the N^3 system")
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--cpu-iters", type=int, default=0,
+                    help="oracle iterations per CPU sample (0: pick ~15 s of work)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(N: int):
+    from paper_2601_13994_b300 import inputs as I
+    rp, c, v = I.diffusion3d_random(N, 1)
+    b = I.rhs_uniform(N ** 3, 11)
+    return rp, c, v, b
+
+
+def bytes_per_iter(n: int, nnz: int) -> int:
+    """Algorithmic bytes of one fused Jacobi-PCG iteration (int32 CSR, FP64):
+    12 nnz + 4 (n+1) for the matrix, 13 n-vectors of 8 bytes."""
+    return 12 * nnz + 4 * (n + 1) + 104 * n
+
+
+def flops_per_iter(n: int, nnz: int) -> int:
+    """FP64 flops of one iteration: 2 per stored entry (SpMV) + 14 per row
+    (p.q, two axpys, D^-1 r, r.z, r.r, p update; FMA = 2)."""
+    return 2 * nnz + 14 * n
+
+
+def spmv_bytes(n: int, nnz: int) -> int:
+    return 12 * nnz + 4 * (n + 1) + 16 * n
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def golden(N: int):
+    p = os.path.join(ROOT, "tests", "golden", "oracle_diffusion3d_%d.json" % N)
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.rows = []
+        self.proc = None
+        self.bus_id = bus_id
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in self.rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(self.rows),
+                "reasons": sorted(reasons)}
+
+
+def cpu_sample(rp, c, v, b, iters_per_sample: int):
+    """Times the oracle (single thread, as it stands) on `iters_per_sample`
+    Jacobi-PCG iterations of the full system; returns seconds per iteration."""
+    import oracle
+    t0 = time.perf_counter()
+    _, info = oracle.pcg(rp, c, v, b, rtol=0.0, atol=0.0, max_iter=iters_per_sample, max_restarts=0)
+    dt = time.perf_counter() - t0
+    return dt / max(1, info["iters"]), info["iters"]
+
+
+def pick_cpu_iters(n: int) -> int:
+    # about 0.3 s per iteration at n = 16.8M on one core: ~15 s of work
+    return int(max(3, min(200, 15.0 / (n * 2.1e-8 + 1e-4))))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    N = args.size
+    rp, c, v, b = workload(N)
+    n, nnz = len(rp) - 1, int(rp[-1])
+    g = golden(N)
+    iters_solve = g["pcg_rtol_1e-8"]["iters"] if g else None
+    k = args.cpu_iters or pick_cpu_iters(n)
+    for _ in range(args.warmup):
+        cpu_sample(rp, c, v, b, max(1, k // 5))
+    per = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s, _ = cpu_sample(rp, c, v, b, k)
+        per.append(s)
+    wall = time.perf_counter() - t0
+    s_iter = statistics.median(per)
+    value = s_iter * iters_solve if iters_solve else None
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "diffusion3d_%d_jacobi_pcg_rtol%.0e" % (N, args.rtol), "n": n, "nnz": nnz},
+        "seconds_per_iteration": s_iter,
+        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": "%d Jacobi-PCG iterations of the oracle on the full %d^3 system per step; "
+                                   "time to solution = median s/iteration x the oracle's own iteration "
+                                   "count at rtol 1e-8 (%s, tests/golden)" % (k, N, iters_solve)},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2601_13994_b300 import sla
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    N = args.size
+    rp, c, v, b = workload(N)
+    n, nnz = len(rp) - 1, int(rp[-1])
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    val = torch.from_numpy(v).to(dev)
+    bt = torch.from_numpy(b).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # ---- warm-up and timed solves (device-resident inputs)
+    for _ in range(args.warmup):
+        x, info = sla.cg(A, val, bt, rtol=args.rtol)
+    torch.cuda.synchronize(dev)
+    status = info.status
+    iters = info.iters
+    props = torch.cuda.get_device_properties(dev)
+    bus = None
+    try:
+        bus = "%08X:%02X:%02X.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except AttributeError:
+        pass
+    sampler = ClockSampler(bus) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.4)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        x, info = sla.cg(A, val, bt, rtol=args.rtol)
+        infos.append(info)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = sampler.stop() if sampler else None
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    iters_all = [i.iters for i in infos]
+    status_all = [i.status for i in infos]
+    true_rel = infos[-1].true_rel_res
+
+    # ---- standalone SpMV (same row-tile code as the solver's K1), events on its stream
+    xs = torch.from_numpy(np.random.default_rng(0).uniform(-1, 1, n)).to(dev)
+    ys = torch.empty_like(xs)
+    for _ in range(3):
+        sla.spmv(A, val, xs, out=ys)
+    reps = 20
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(reps):
+        sla.spmv(A, val, xs, out=ys)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    spmv_ms = s0.elapsed_time(s1) / reps
+
+    # ---- end to end through the public call with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_rp = torch.from_numpy(rp).pin_memory()
+        h_c = torch.from_numpy(c).pin_memory()
+        h_v = torch.from_numpy(v).pin_memory()
+        h_b = torch.from_numpy(b).pin_memory()
+        h_x = torch.empty(n, dtype=torch.float64).pin_memory()
+        d_rp = torch.empty_like(h_rp, device=dev)
+        d_c = torch.empty_like(h_c, device=dev)
+        d_v = torch.empty_like(h_v, device=dev)
+        d_b = torch.empty_like(h_b, device=dev)
+
+        def e2e_step():
+            d_rp.copy_(h_rp, non_blocking=True)
+            d_c.copy_(h_c, non_blocking=True)
+            d_v.copy_(h_v, non_blocking=True)
+            d_b.copy_(h_b, non_blocking=True)
+            Ad = sla.CSRMatrix(d_rp, d_c, check=False)
+            xd, inf = sla.cg(Ad, d_v, d_b, rtol=args.rtol)
+            h_x.copy_(xd, non_blocking=True)
+            return inf
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for _ in range(args.steps):
+            inf = e2e_step()
+        k1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = k0.elapsed_time(k1) / args.steps
+        h2d = rp.nbytes + c.nbytes + v.nbytes + b.nbytes
+        d2h = 8 * n + 24  # x and the info record
+        e2e = {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "iters": inf.iters}
+
+    peak, peak_kind = measured_peaks()
+    it = statistics.median(iters_all)
+    bpi = bytes_per_iter(n, nnz)
+    achieved = bpi * it / (ms_max / 1e3) / 1e9
+    fpi = flops_per_iter(n, nnz)
+    fp64_tf = fpi * it / (ms_max / 1e3) / 1e12
+    spmv_gbs = spmv_bytes(n, nnz) / (spmv_ms / 1e3) / 1e9
+    launches = args.steps * (1 + 2 + 3 * (it + 1))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g = golden(N)
+        k = args.cpu_iters or pick_cpu_iters(n)
+        s_iter, done = cpu_sample(rp, c, v, b, k)
+        oracle_iters = g["pcg_rtol_1e-8"]["iters"] if g else None
+        used = oracle_iters if oracle_iters else it
+        cpu = {"value": s_iter * used, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": "%d Jacobi-PCG iterations of the single-threaded FP64 oracle on the full "
+                         "%d^3 system (%.2f s/iteration), scaled by %s iteration count %d"
+                         % (done, N, s_iter, "the oracle's own (tests/golden)" if oracle_iters else
+                            "the GPU solve's", used)}
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "diffusion3d_%d_jacobi_pcg_rtol%.0e" % (N, args.rtol), "n": n, "nnz": nnz,
+                   "precond": "jacobi", "x0": "zero", "l2": "inputs larger than L2 (%.1f GB working set)"
+                   % ((12 * nnz + 4 * n + 7 * 8 * n) / 1e9), "parallelism": "replicas"},
+        "iters": it, "status": sorted(set(status_all)), "true_rel_res": true_rel,
+        "pcg_gbs": achieved, "pcg_frac_of_8tbs": achieved / NOMINAL_HBM_GBS,
+        "spmv_gbs": spmv_gbs, "spmv_frac_of_8tbs": spmv_gbs / NOMINAL_HBM_GBS,
+        "spmv_ms": spmv_ms,
+        "fp64": {"achieved_tflops": fp64_tf, "peak_tflops": FP64_PEAK_TFLOPS,
+                 "frac": fp64_tf / FP64_PEAK_TFLOPS, "flops_per_iter": fpi},
+        "roofline": {"kernel": "Jacobi-PCG iteration (cg_spmv_pq + cg_update + cg_pupdate)",
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "bytes_per_launch": bpi, "traffic": None},
+        "roofline_spmv": {"kernel": "spmv_tiles_kernel", "bound": "hbm", "achieved": spmv_gbs, "peak": peak,
+                          "unit": "GB/s", "frac": spmv_gbs / peak, "bytes_per_launch": spmv_bytes(n, nnz)},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,150 @@
+/*
+ * sla.h -- C ABI of the B300 (sm_103a) sparse Krylov solve + adjoint library.
+ *
+ * The operations follow arXiv 2601.13994 ("torch-sla"): x = A.solve(b) for a
+ * sparse A given on a sparsity pattern (App. B), solved by the paper's
+ * GPU-native iterative backend -- Jacobi-preconditioned CG for SPD systems
+ * (Sec. 3.1, Sec. 4.1, Algorithm 1 with one process) and BiCGStab for
+ * nonsymmetric ones (Sec. 1, Sec. 3.1) -- and the linear adjoint backward
+ * A^T lambda = dL/dx, dL/db = lambda, dL/dA_ij = -lambda_i x_j (Eq. 2-3).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Matrices are square n x n in CSR form: int32 row pointers (n+1 entries,
+ *    rowptr[0] = 0, non-decreasing, rowptr[n] = nnz), int32 column indices
+ *    in [0, n) (ascending and distinct inside a row), float64 values.
+ *  - Every array pointer is a DEVICE pointer owned by the caller unless the
+ *    argument says "host".  The library never frees caller memory and never
+ *    allocates device memory: scratch space is a caller-provided workspace
+ *    whose size comes from sla_workspace_size().  Workspace pointers must be
+ *    256-byte aligned.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All work is enqueued on it; no call synchronises the host
+ *    except where stated.
+ *  - Return value: a negative code is a synchronous argument or CUDA error
+ *    and nothing was enqueued; 0 means the work was enqueued.  Numerical
+ *    outcomes of a solve (converged, not converged, breakdown, not SPD) are
+ *    written to the DEVICE sla_info record(s) when the enqueued work runs.
+ *  - Not thread-safe for concurrent calls that share a workspace.
+ */
+#ifndef SLA_H_
+#define SLA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Status codes                                                         */
+/* ------------------------------------------------------------------ */
+#define SLA_OK 0                /* converged: ||r|| <= max(rtol*||b||, atol) */
+#define SLA_NOT_CONVERGED 1     /* max_iter reached (or restarts exhausted)   */
+#define SLA_BREAKDOWN 2         /* non-finite scalar, or BiCGStab rho/omega=0 */
+#define SLA_NOT_SPD 3           /* CG: A_ii <= 0 with Jacobi, or p^T A p <= 0  */
+#define SLA_ERR_INVALID (-1)    /* bad argument (sizes, null pointers, flags)  */
+#define SLA_ERR_CUDA (-2)       /* a CUDA runtime call failed                  */
+#define SLA_ERR_WORKSPACE (-3)  /* workspace too small or misaligned           */
+#define SLA_ERR_TIMEOUT (-4)    /* a bounded device-side wait ran out          */
+
+/* Preconditioners (sla_opts.precond). */
+#define SLA_PRECOND_NONE 0
+#define SLA_PRECOND_JACOBI 1    /* z = D^{-1} r, D = diag(A) (Sec. 4.1)       */
+
+/* Workspace kinds for sla_workspace_size(). */
+#define SLA_WS_CG 1
+
+/* Pattern of a square CSR matrix (all pointers device). */
+typedef struct sla_csr {
+  int32_t n;              /* rows = columns, >= 0                            */
+  int32_t nnz;            /* stored entries, >= 0                            */
+  const int32_t* rowptr;  /* [n+1]                                           */
+  const int32_t* col;     /* [nnz]                                           */
+} sla_csr;
+
+/* Solver options (host struct, copied at call time). */
+typedef struct sla_opts {
+  double rtol;            /* relative tolerance on ||r||_2 / ||b||_2, >= 0    */
+  double atol;            /* absolute floor on ||r||_2, >= 0                  */
+  int32_t max_iter;       /* iteration cap, >= 0                              */
+  int32_t max_restarts;   /* true-residual restarts allowed, 0..16            */
+  int32_t precond;        /* SLA_PRECOND_*                                    */
+  int32_t use_x0;         /* 1: x holds the initial guess; 0: start at x = 0 */
+} sla_opts;
+
+/* Per-system solve record (DEVICE memory, written by the enqueued work). */
+typedef struct sla_info {
+  int32_t iters;          /* Krylov iterations performed                      */
+  int32_t status;         /* SLA_OK / SLA_NOT_CONVERGED / ...                 */
+  double rel_res;         /* last recursive ||r|| / ||b||                     */
+  double true_rel_res;    /* ||b - A x|| / ||b|| recomputed at exit           */
+} sla_info;
+
+/* ------------------------------------------------------------------ */
+/* Library information                                                  */
+/* ------------------------------------------------------------------ */
+
+/* Version string of this build (static storage). */
+const char* sla_version(void);
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char* sla_status_string(int32_t code);
+
+/* ------------------------------------------------------------------ */
+/* Workspace size query                                                 */
+/* ------------------------------------------------------------------ */
+
+/* Bytes of device workspace needed by the entry point `kind` for a system
+ * with n rows, nnz entries and `batch` systems (1 for single solves).
+ * Host-only; writes *bytes.  Returns SLA_ERR_INVALID for a bad kind or
+ * negative sizes. */
+int32_t sla_workspace_size(int32_t kind, int32_t n, int32_t nnz,
+                           int32_t batch, size_t* bytes);
+
+/* ------------------------------------------------------------------ */
+/* Pattern validation                                                   */
+/* ------------------------------------------------------------------ */
+
+/* Checks a CSR pattern on the device: rowptr[0] == 0, rowptr non-decreasing,
+ * rowptr[n] == nnz, every column in [0, n), columns strictly ascending in
+ * each row.  Writes 1 (valid) or 0 (invalid) to the DEVICE int32 *ok.
+ * Every access is bounds-checked, so an invalid pattern cannot fault. */
+int32_t sla_csr_check(const sla_csr* A, int32_t* ok, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* SpMV  y = A x   (the product every Krylov step is built on:            */
+/* Algorithm 1 step 3a; torch.sparse in the paper's pytorch backend)     */
+/* ------------------------------------------------------------------ */
+
+/* val [nnz], x [n] -> y [n].  x and y must not overlap.  The kernel is
+ * picked from the mean row length (nnz/n) and, inside each row tile, from
+ * the tile's entry count: short rows are staged through shared memory and
+ * summed one row per thread, long rows one row per warp. */
+int32_t sla_spmv(const sla_csr* A, const double* val, const double* x,
+                 double* y, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Preconditioned conjugate gradient for SPD A                           */
+/* (Algorithm 1 with P = 1; Jacobi preconditioner of Sec. 4.1)           */
+/* ------------------------------------------------------------------ */
+
+/* Solves A x = b.  b [n] (read), x [n] (written; read first if use_x0).
+ * Stops when ||r_k||_2 <= max(rtol ||b||_2, atol) on the recursive
+ * residual, then recomputes b - A x; if that is above twice the target the
+ * recurrence restarts from x (at most max_restarts times).  b = 0 gives
+ * x = 0 after 0 iterations.  *info (DEVICE) receives the outcome.
+ * The whole solve is one CUDA-graph launch whose device-side while-loop
+ * decides convergence; the host is not synchronised.  The first call with a
+ * given workspace address and sizes builds and caches that graph.
+ * Workspace: sla_workspace_size(SLA_WS_CG, n, nnz, 1, &bytes). */
+int32_t sla_cg(const sla_csr* A, const double* val, const double* b,
+               double* x, const sla_opts* opts, sla_info* info, void* ws,
+               size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLA_H_ */

@@ -1,0 +1,94 @@
+"""ctypes binding of ``libsla.so`` (the C ABI declared in include/sla.h).
+
+Argument marshalling only: every entry point is called with raw device
+pointers taken from torch tensors and the current CUDA stream.  There is no
+fallback: if the shared library is missing the import of any solver raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsla.so")
+
+SLA_OK = 0
+SLA_NOT_CONVERGED = 1
+SLA_BREAKDOWN = 2
+SLA_NOT_SPD = 3
+SLA_ERR_INVALID = -1
+SLA_ERR_CUDA = -2
+SLA_ERR_WORKSPACE = -3
+SLA_ERR_TIMEOUT = -4
+
+SLA_PRECOND_NONE = 0
+SLA_PRECOND_JACOBI = 1
+
+SLA_WS_CG = 1
+
+STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NOT_SPD", -1: "ERR_INVALID",
+                -2: "ERR_CUDA", -3: "ERR_WORKSPACE", -4: "ERR_TIMEOUT"}
+
+INFO_BYTES = 24  # sla_info: int32 iters, int32 status, double rel_res, double true_rel_res
+
+
+class SlaCsr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32),
+                ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p)]
+
+
+class SlaOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
+                ("precond", ctypes.c_int32), ("use_x0", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SlaError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__("%s returned %d (%s)" % (fn, code, STATUS_NAMES.get(code, "?")))
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsla.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libsla.so is not built (expected at %s); run "
+                                   "`python -m paper_2601_13994_b300.build`" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            P = ctypes.c_void_p
+            i32 = ctypes.c_int32
+            L.sla_version.argtypes = []
+            L.sla_version.restype = ctypes.c_char_p
+            L.sla_status_string.argtypes = [i32]
+            L.sla_status_string.restype = ctypes.c_char_p
+            L.sla_workspace_size.argtypes = [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+            L.sla_workspace_size.restype = i32
+            L.sla_csr_check.argtypes = [ctypes.POINTER(SlaCsr), P, P]
+            L.sla_csr_check.restype = i32
+            L.sla_spmv.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, P]
+            L.sla_spmv.restype = i32
+            L.sla_cg.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, ctypes.POINTER(SlaOpts), P, P,
+                                 ctypes.c_size_t, P]
+            L.sla_cg.restype = i32
+            _lib = L
+    return _lib
+
+
+def check(fn: str, code: int) -> int:
+    if code < 0:
+        raise SlaError(fn, code)
+    return code
+
+
+def workspace_size(kind: int, n: int, nnz: int, batch: int = 1) -> int:
+    out = ctypes.c_size_t(0)
+    check("sla_workspace_size", lib().sla_workspace_size(kind, n, nnz, batch, ctypes.byref(out)))
+    return int(out.value)

@@ -1,0 +1,538 @@
+// sla_cg.cu -- preconditioned conjugate gradient for SPD A.
+//
+// Algorithm 1 (App. C) with a single process: every all_reduce becomes an
+// in-kernel grid reduction, and the halo exchange disappears.  The Jacobi
+// preconditioner z = D^{-1} r is the one the paper's CG backend uses
+// (Sec. 4.1).  One iteration is three kernels:
+//
+//   K1  q = A p, partial p.q            -> last block: alpha = rho / p.q
+//   K2  x += alpha p, r -= alpha q, z = D^{-1} r, partial r.z, r.r
+//                                       -> last block: convergence, beta
+//   K3  p = z + beta p   (or, once the recursive residual has converged,
+//       the true-residual check b - A x with an optional restart)
+//                                       -> last block: loop condition
+//
+// The loop runs inside one CUDA graph as a conditional WHILE node whose
+// condition K3's last block sets, so a whole solve is one graph launch and
+// no host synchronisation.  Per-call arguments live in a descriptor in the
+// workspace, so the instantiated graph depends only on the workspace address
+// and the sizes and is cached.
+//
+// Algorithmic bytes per iteration (int32 CSR, FP64): 12 nnz + 4 (n+1)
+// + 104 n  (K1: p, q; K2: x rw, r rw, p, q, dinv, z w; K3: z, p rw).
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "sla_internal.cuh"
+#include "sla_workspace.h"
+
+namespace sla {
+
+constexpr int kVecThreads = 256;
+
+struct CgPtrs {
+  KrylovDesc* d;
+  KrylovState* st;
+  double* part;
+  double* r;
+  double* z;
+  double* p;
+  double* q;
+  double* dinv;
+};
+
+// Writes the per-call descriptor and zeroes the ticket counters, so that a
+// workspace whose memory held anything before still starts every solve with
+// every grid reduction armed (the loop condition depends on them).
+__global__ void cg_write_desc_kernel(KrylovDesc* dst, KrylovDesc src, KrylovState* st) {
+  *dst = src;
+  for (int i = 0; i < 8; ++i) st->cnt[i] = 0u;
+}
+
+// Row i of A times v, summed sequentially from global memory.
+__device__ __forceinline__ double row_dot(const int* __restrict__ rowptr,
+                                          const int* __restrict__ col,
+                                          const double* __restrict__ val,
+                                          const double* __restrict__ v, int i) {
+  const int a = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
+  double s = 0.0;
+  for (int k = a; k < e; ++k) s = fma(__ldg(val + k), __ldg(v + __ldg(col + k)), s);
+  return s;
+}
+
+// ---------------------------------------------------------------- init
+// dinv = 1 / diag(A) (or 1 without preconditioner), r = b - A x0,
+// z = dinv r, p = z; sums ||b||^2, ||r||^2, r.z and a bad-diagonal flag.
+__global__ void __launch_bounds__(kVecThreads) cg_init_kernel(CgPtrs P) {
+  __shared__ double red[kVecThreads / kWarp];
+  __shared__ bool s_last;
+  const KrylovDesc d = *P.d;
+  const int n = d.n;
+  double bb = 0.0, rr = 0.0, rz = 0.0, bad = 0.0;
+  const int stride = gridDim.x * kVecThreads;
+  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride) {
+    const int a = d.rowptr[i], e = d.rowptr[i + 1];
+    double diag = 0.0, ax = 0.0;
+    for (int k = a; k < e; ++k) {
+      const int c = d.col[k];
+      const double v = d.val[k];
+      if (c == i) diag += v;
+      if (d.use_x0) ax = fma(v, d.x[c], ax);
+    }
+    const double bi = d.b[i];
+    const double ri = bi - ax;
+    double di = 1.0;
+    if (d.precond == SLA_PRECOND_JACOBI) {
+      if (!(diag > 0.0)) bad = 1.0;
+      di = 1.0 / diag;
+    }
+    const double zi = di * ri;
+    P.dinv[i] = di;
+    P.r[i] = ri;
+    P.z[i] = zi;
+    P.p[i] = zi;
+    bb = fma(bi, bi, bb);
+    rr = fma(ri, ri, rr);
+    rz = fma(ri, zi, rz);
+  }
+  if (!d.use_x0) {
+    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride) d.x[i] = 0.0;
+  }
+  const double sbb = block_sum<kVecThreads>(bb, red);
+  const double srr = block_sum<kVecThreads>(rr, red);
+  const double srz = block_sum<kVecThreads>(rz, red);
+  const double sbad = block_sum<kVecThreads>(bad, red);
+  if (threadIdx.x == 0) {
+    P.part[0 * kMaxBlocks + blockIdx.x] = sbb;
+    P.part[1 * kMaxBlocks + blockIdx.x] = srr;
+    P.part[2 * kMaxBlocks + blockIdx.x] = srz;
+    P.part[3 * kMaxBlocks + blockIdx.x] = sbad;
+  }
+  if (!last_block_arrive(&P.st->cnt[0], &s_last)) return;
+  const int G = gridDim.x;
+  const double tbb = reduce_partials<kVecThreads>(P.part + 0 * kMaxBlocks, G, red);
+  const double trr = reduce_partials<kVecThreads>(P.part + 1 * kMaxBlocks, G, red);
+  const double trz = reduce_partials<kVecThreads>(P.part + 2 * kMaxBlocks, G, red);
+  const double tbad = reduce_partials<kVecThreads>(P.part + 3 * kMaxBlocks, G, red);
+  if (threadIdx.x == 0) {
+    KrylovState& s = *P.st;
+    s.bnorm = sqrt(tbb);
+    s.thresh = fmax(d.rtol * s.bnorm, d.atol);
+    s.rho = trz;
+    s.rr = trr;
+    s.tt = 0.0;
+    s.alpha = s.beta = 0.0;
+    s.iters = 0;
+    s.restarts = 0;
+    s.body = 0;
+    s.zero_rhs = 0;
+    s.bad_diag = 0;
+    s.status = SLA_NOT_CONVERGED;
+    s.phase = kPhaseRun;
+    if (tbad > 0.0) {
+      s.bad_diag = 1;
+      s.status = SLA_NOT_SPD;
+      s.phase = kPhaseDone;
+    } else if (s.bnorm == 0.0) {
+      s.zero_rhs = 1;
+      s.status = SLA_OK;
+      s.phase = kPhaseDone;
+    } else if (!isfinite(trz) || !isfinite(trr)) {
+      s.status = SLA_BREAKDOWN;
+      s.phase = kPhaseDone;
+    } else if (sqrt(trr) <= s.thresh) {
+      s.phase = kPhaseCheck;
+    } else if (d.max_iter <= 0) {
+      s.phase = kPhaseDone;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- K1
+__global__ void __launch_bounds__(kTileThreads) cg_spmv_pq_kernel(CgPtrs P) {
+  __shared__ TileSmem sm;
+  __shared__ bool s_last;
+  if (__ldcg(&P.st->phase) != kPhaseRun) return;
+  const KrylovDesc d = *P.d;
+  const int n = d.n;
+  const double* __restrict__ p = P.p;
+  double* __restrict__ q = P.q;
+  double pq = 0.0;
+  const int ntiles = (n + kTileRows - 1) / kTileRows;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
+    spmv_tile(t, n, d.rowptr, d.col, d.val, p, sm, [&](int row, double s) {
+      q[row] = s;
+      pq = fma(__ldg(p + row), s, pq);
+    });
+  const double spq = block_sum<kTileThreads>(pq, sm.red);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = spq;
+  if (!last_block_arrive(&P.st->cnt[1], &s_last)) return;
+  const double tpq = reduce_partials<kTileThreads>(P.part, gridDim.x, sm.red);
+  if (threadIdx.x == 0) {
+    KrylovState& s = *P.st;
+    s.pq = tpq;
+    if (!isfinite(tpq)) {
+      s.status = SLA_BREAKDOWN;
+      s.phase = kPhaseDone;
+    } else if (!(tpq > 0.0)) {
+      s.status = SLA_NOT_SPD;
+      s.phase = kPhaseDone;
+    } else {
+      s.alpha = s.rho / tpq;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- K2
+__global__ void __launch_bounds__(kVecThreads) cg_update_kernel(CgPtrs P) {
+  __shared__ double red[kVecThreads / kWarp];
+  __shared__ bool s_last;
+  if (__ldcg(&P.st->phase) != kPhaseRun) return;
+  const KrylovDesc d = *P.d;
+  const int n = d.n;
+  const double alpha = __ldcg(&P.st->alpha);
+  double* __restrict__ x = d.x;
+  double* __restrict__ r = P.r;
+  double* __restrict__ z = P.z;
+  const double* __restrict__ p = P.p;
+  const double* __restrict__ q = P.q;
+  const double* __restrict__ dinv = P.dinv;
+  double rz = 0.0, rr = 0.0;
+  const int stride = gridDim.x * kVecThreads;
+  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride) {
+    const double pi = __ldg(p + i), qi = __ldg(q + i), di = __ldg(dinv + i);
+    const double xi = fma(alpha, pi, x[i]);
+    const double ri = fma(-alpha, qi, r[i]);
+    const double zi = di * ri;
+    x[i] = xi;
+    r[i] = ri;
+    z[i] = zi;
+    rz = fma(ri, zi, rz);
+    rr = fma(ri, ri, rr);
+  }
+  const double srz = block_sum<kVecThreads>(rz, red);
+  const double srr = block_sum<kVecThreads>(rr, red);
+  if (threadIdx.x == 0) {
+    P.part[0 * kMaxBlocks + blockIdx.x] = srz;
+    P.part[1 * kMaxBlocks + blockIdx.x] = srr;
+  }
+  if (!last_block_arrive(&P.st->cnt[2], &s_last)) return;
+  const int G = gridDim.x;
+  const double trz = reduce_partials<kVecThreads>(P.part + 0 * kMaxBlocks, G, red);
+  const double trr = reduce_partials<kVecThreads>(P.part + 1 * kMaxBlocks, G, red);
+  if (threadIdx.x == 0) {
+    KrylovState& s = *P.st;
+    s.iters += 1;
+    s.rr = trr;
+    if (!isfinite(trz) || !isfinite(trr)) {
+      s.status = SLA_BREAKDOWN;
+      s.phase = kPhaseDone;
+    } else if (sqrt(trr) <= s.thresh) {
+      s.status = SLA_OK;
+      s.phase = kPhaseCheck;
+    } else if (!(trz > 0.0)) {
+      s.status = SLA_NOT_SPD;
+      s.phase = kPhaseDone;
+    } else {
+      s.beta = trz / s.rho;
+      s.rho = trz;
+      if (s.iters >= d.max_iter) {
+        s.status = SLA_NOT_CONVERGED;
+        s.phase = kPhaseDone;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- K3
+__global__ void __launch_bounds__(kVecThreads)
+cg_pupdate_kernel(CgPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ double red[kVecThreads / kWarp];
+  __shared__ bool s_last;
+  const int phase = __ldcg(&P.st->phase);
+  const KrylovDesc d = *P.d;
+  const int n = d.n;
+  const int stride = gridDim.x * kVecThreads;
+  double tt = 0.0, rz = 0.0;
+  if (phase == kPhaseRun) {
+    const double beta = __ldcg(&P.st->beta);
+    const double* __restrict__ z = P.z;
+    double* __restrict__ p = P.p;
+    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride)
+      p[i] = fma(beta, p[i], __ldg(z + i));
+  } else if (phase == kPhaseCheck) {
+    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride) {
+      const double ti = d.b[i] - row_dot(d.rowptr, d.col, d.val, d.x, i);
+      const double zi = P.dinv[i] * ti;
+      P.r[i] = ti;
+      P.z[i] = zi;
+      P.p[i] = zi;
+      tt = fma(ti, ti, tt);
+      rz = fma(ti, zi, rz);
+    }
+  }
+  if (phase == kPhaseCheck) {
+    const double stt = block_sum<kVecThreads>(tt, red);
+    const double srz = block_sum<kVecThreads>(rz, red);
+    if (threadIdx.x == 0) {
+      P.part[0 * kMaxBlocks + blockIdx.x] = stt;
+      P.part[1 * kMaxBlocks + blockIdx.x] = srz;
+    }
+  }
+  if (!last_block_arrive(&P.st->cnt[3], &s_last)) return;
+  double ttt = 0.0, trz = 0.0;
+  if (phase == kPhaseCheck) {
+    ttt = reduce_partials<kVecThreads>(P.part + 0 * kMaxBlocks, gridDim.x, red);
+    trz = reduce_partials<kVecThreads>(P.part + 1 * kMaxBlocks, gridDim.x, red);
+  }
+  if (threadIdx.x == 0) {
+    KrylovState& s = *P.st;
+    if (phase == kPhaseCheck) {
+      const double tn = sqrt(ttt);
+      s.tt = ttt;
+      if (tn <= 2.0 * s.thresh) {
+        s.status = SLA_OK;
+        s.phase = kPhaseDone;
+      } else if (!isfinite(ttt) || !isfinite(trz)) {
+        s.status = SLA_BREAKDOWN;
+        s.phase = kPhaseDone;
+      } else if (s.restarts >= d.max_restarts || s.iters >= d.max_iter) {
+        s.status = SLA_NOT_CONVERGED;
+        s.phase = kPhaseDone;
+      } else {
+        s.restarts += 1;
+        s.rho = trz;
+        s.rr = ttt;
+        s.status = SLA_NOT_CONVERGED;
+        s.phase = kPhaseRun;
+      }
+    }
+    // hard cap on loop bodies: each one either advances iters or consumes a
+    // restart, so this only fires if the state machine is broken
+    s.body += 1;
+    const int cap = d.max_iter + 2 * d.max_restarts + 8;
+    if (s.phase != kPhaseDone && s.body > cap) {
+      s.status = SLA_NOT_CONVERGED;
+      s.phase = kPhaseDone;
+    }
+    if (use_cond) cudaGraphSetConditional(cond, s.phase != kPhaseDone ? 1u : 0u);
+  }
+}
+
+// ---------------------------------------------------------------- final
+__global__ void __launch_bounds__(kVecThreads) cg_final_kernel(CgPtrs P) {
+  __shared__ double red[kVecThreads / kWarp];
+  __shared__ bool s_last;
+  const KrylovDesc d = *P.d;
+  const int n = d.n;
+  const int zero_rhs = __ldcg(&P.st->zero_rhs);
+  const int bad = __ldcg(&P.st->bad_diag);
+  const int stride = gridDim.x * kVecThreads;
+  double tt = 0.0;
+  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride) {
+    if (zero_rhs || bad) {
+      if (zero_rhs) d.x[i] = 0.0;
+    } else {
+      const double ti = d.b[i] - row_dot(d.rowptr, d.col, d.val, d.x, i);
+      tt = fma(ti, ti, tt);
+    }
+  }
+  const double stt = block_sum<kVecThreads>(tt, red);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = stt;
+  if (!last_block_arrive(&P.st->cnt[4], &s_last)) return;
+  const double ttt = reduce_partials<kVecThreads>(P.part, gridDim.x, red);
+  if (threadIdx.x == 0) {
+    const KrylovState& s = *P.st;
+    sla_info inf;
+    inf.iters = s.iters;
+    inf.status = s.phase == kPhaseDone ? s.status : SLA_NOT_CONVERGED;
+    if (s.zero_rhs) {
+      inf.rel_res = 0.0;
+      inf.true_rel_res = 0.0;
+    } else if (s.bad_diag) {
+      inf.rel_res = NAN;
+      inf.true_rel_res = NAN;
+    } else {
+      inf.rel_res = sqrt(s.rr) / s.bnorm;
+      inf.true_rel_res = sqrt(ttt) / s.bnorm;
+    }
+    *d.info = inf;
+  }
+}
+
+__global__ void write_info_kernel(sla_info* info, sla_info v) { *info = v; }
+
+// ---------------------------------------------------------------- graph
+namespace {
+
+struct CgGraphKey {
+  int dev;
+  const void* ws;
+  int n, nnz, g1, gv;
+  bool operator==(const CgGraphKey& o) const {
+    return dev == o.dev && ws == o.ws && n == o.n && nnz == o.nnz && g1 == o.g1 && gv == o.gv;
+  }
+};
+
+struct CgGraphEntry {
+  CgGraphKey key;
+  cudaGraphExec_t exec;
+};
+
+std::mutex g_mu;
+std::vector<CgGraphEntry> g_cache;
+constexpr size_t kCacheMax = 64;
+
+int occupancy(const void* fn, int threads) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, 0) != cudaSuccess || b <= 0)
+    b = 2;
+  return b;
+}
+
+cudaError_t add_kernel(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                       cudaGraphNode_t* out, const void* fn, int grid, int block, void** args) {
+  cudaKernelNodeParams kp = {};
+  kp.func = const_cast<void*>(fn);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(block);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  return cudaGraphAddKernelNode(out, g, deps, ndeps, &kp);
+}
+
+int build_graph(CgPtrs P, int g1, int gv, cudaGraphExec_t* exec) {
+  cudaGraph_t g = nullptr;
+  SLA_CUDA_TRY(cudaGraphCreate(&g, 0));
+  int rc = SLA_ERR_CUDA;
+  do {
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
+    cudaGraphNode_t n_init, n_while, n1, n2, n3, n_final;
+    void* a_init[] = {&P};
+    if (add_kernel(g, nullptr, 0, &n_init, (const void*)cg_init_kernel, gv, kVecThreads, a_init) != cudaSuccess) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp) != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    int use_cond = 1;
+    void* a1[] = {&P};
+    void* a3[] = {&P, &h, &use_cond};
+    if (add_kernel(body, nullptr, 0, &n1, (const void*)cg_spmv_pq_kernel, g1, kTileThreads, a1) != cudaSuccess) break;
+    if (add_kernel(body, &n1, 1, &n2, (const void*)cg_update_kernel, gv, kVecThreads, a1) != cudaSuccess) break;
+    if (add_kernel(body, &n2, 1, &n3, (const void*)cg_pupdate_kernel, gv, kVecThreads, a3) != cudaSuccess) break;
+    if (add_kernel(g, &n_while, 1, &n_final, (const void*)cg_final_kernel, gv, kVecThreads, a_init) != cudaSuccess) break;
+    if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) break;
+    rc = SLA_OK;
+  } while (0);
+  cudaGraphDestroy(g);
+  return rc;
+}
+
+}  // namespace
+
+int cg_grids(int dev, int n, int* g1, int* gv) {
+  static int occ1 = 0, occv = 0;
+  if (occ1 == 0) occ1 = occupancy((const void*)cg_spmv_pq_kernel, kTileThreads);
+  if (occv == 0) occv = occupancy((const void*)cg_update_kernel, kVecThreads);
+  const long long ntiles = (n + kTileRows - 1) / kTileRows;
+  *g1 = persistent_grid(dev, ntiles, occ1, kMaxBlocks);
+  *gv = persistent_grid(dev, ((long long)n + kVecThreads - 1) / kVecThreads, occv, kMaxBlocks);
+  return SLA_OK;
+}
+
+int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s) {
+  const int n = desc.n;
+  const CgLayout L = cg_layout(n);
+  char* base = (char*)ws;
+  CgPtrs P;
+  P.d = (KrylovDesc*)(base + L.desc);
+  P.st = (KrylovState*)(base + L.state);
+  P.part = (double*)(base + L.part);
+  P.r = (double*)(base + L.r);
+  P.z = (double*)(base + L.z);
+  P.p = (double*)(base + L.p);
+  P.q = (double*)(base + L.q);
+  P.dinv = (double*)(base + L.dinv);
+  const int dev = current_device();
+  int g1, gv;
+  cg_grids(dev, n, &g1, &gv);
+  CgGraphKey key{dev, ws, n, desc.nnz, g1, gv};
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& e : g_cache)
+      if (e.key == key) exec = e.exec;
+    if (exec == nullptr) {
+      const int rc = build_graph(P, g1, gv, &exec);
+      if (rc != SLA_OK) return rc;
+      if (g_cache.size() >= kCacheMax) {
+        SLA_CUDA_TRY(cudaDeviceSynchronize());
+        for (auto& e : g_cache) cudaGraphExecDestroy(e.exec);
+        g_cache.clear();
+      }
+      g_cache.push_back(CgGraphEntry{key, exec});
+    }
+  }
+  cg_write_desc_kernel<<<1, 1, 0, s>>>(P.d, desc, P.st);
+  SLA_CUDA_TRY(cudaGetLastError());
+  SLA_CUDA_TRY(cudaGraphLaunch(exec, s));
+  return SLA_OK;
+}
+
+int validate_solve_args(const sla_csr* A, const double* val, const double* b, const double* x,
+                        const sla_opts* o, const sla_info* info, const void* ws, size_t ws_bytes,
+                        size_t need) {
+  if (A == nullptr || o == nullptr || info == nullptr) return SLA_ERR_INVALID;
+  if (A->n < 0 || A->nnz < 0) return SLA_ERR_INVALID;
+  if (A->n > 0 && (A->rowptr == nullptr || b == nullptr || x == nullptr)) return SLA_ERR_INVALID;
+  if (A->nnz > 0 && (A->col == nullptr || val == nullptr)) return SLA_ERR_INVALID;
+  if (A->n > 0 && (const void*)b == (const void*)x) return SLA_ERR_INVALID;
+  if (!(o->rtol >= 0.0) || !(o->atol >= 0.0) || o->max_iter < 0 || o->max_restarts < 0 ||
+      o->max_restarts > 16 || (o->use_x0 != 0 && o->use_x0 != 1))
+    return SLA_ERR_INVALID;
+  if (ws == nullptr || ((uintptr_t)ws & 255u) != 0 || ws_bytes < need) return SLA_ERR_WORKSPACE;
+  return SLA_OK;
+}
+
+}  // namespace sla
+
+using namespace sla;
+
+extern "C" int32_t sla_cg(const sla_csr* A, const double* val, const double* b, double* x,
+                          const sla_opts* opts, sla_info* info, void* ws, size_t ws_bytes,
+                          void* stream) {
+  if (A == nullptr) return SLA_ERR_INVALID;
+  const size_t need = cg_layout(A->n > 0 ? A->n : 0).total;
+  int rc = validate_solve_args(A, val, b, x, opts, info, ws, ws_bytes, need);
+  if (rc != SLA_OK) return rc;
+  if (opts->precond != SLA_PRECOND_NONE && opts->precond != SLA_PRECOND_JACOBI) return SLA_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (A->n == 0) {
+    sla_info v{0, SLA_OK, 0.0, 0.0};
+    write_info_kernel<<<1, 1, 0, s>>>(info, v);
+    SLA_CUDA_TRY(cudaGetLastError());
+    return SLA_OK;
+  }
+  KrylovDesc d = {};
+  d.n = A->n;
+  d.nnz = A->nnz;
+  d.rowptr = A->rowptr;
+  d.col = A->col;
+  d.val = val;
+  d.b = b;
+  d.x = x;
+  d.info = info;
+  d.rtol = opts->rtol;
+  d.atol = opts->atol;
+  d.max_iter = opts->max_iter;
+  d.max_restarts = opts->max_restarts;
+  d.precond = opts->precond;
+  d.use_x0 = opts->use_x0;
+  return launch_cg(d, ws, s);
+}

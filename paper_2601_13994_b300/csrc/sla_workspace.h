@@ -1,0 +1,85 @@
+// sla_workspace.h -- device workspace layouts (host + device visible).
+//
+// Every solver carves the caller-provided workspace into a call descriptor,
+// a device-side solver state (scalars, phase, ticket counters), per-block
+// partial sums and the Krylov work vectors.  All offsets are multiples of
+// 256 bytes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+
+#include "sla.h"
+
+namespace sla {
+
+constexpr int kMaxBlocks = 2048;   // cap on the grid of every reducing kernel
+constexpr int kPartSlots = 4;      // partial-sum arrays of kMaxBlocks doubles
+
+// Solver phase (CgState::phase).
+enum : int { kPhaseRun = 0, kPhaseCheck = 1, kPhaseDone = 2 };
+
+// Per-call arguments, written to device memory before the cached graph runs,
+// so that one instantiated graph serves every call with the same workspace.
+struct KrylovDesc {
+  int n, nnz;
+  const int* rowptr;
+  const int* col;
+  const double* val;
+  const double* b;
+  double* x;
+  sla_info* info;
+  double rtol, atol;
+  int max_iter, max_restarts, precond, use_x0;
+  // CSR of A^T for the BiCGStab adjoint (unused by CG)
+  const int* rowptr_t;
+  const int* col_t;
+  const int* perm_t;
+};
+
+// Device-side solver scalars.  Counters are reset by the last block of the
+// kernel that uses them.
+struct KrylovState {
+  double rho, pq, rr, bnorm, thresh, alpha, beta, omega;
+  double rho_prev, tt, ts, ss;
+  int iters, status, phase, restarts, body, zero_rhs, bad_diag, pad;
+  unsigned cnt[8];
+};
+
+struct CgLayout {
+  size_t desc, state, part, r, z, p, q, dinv, total;
+};
+
+inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+inline CgLayout cg_layout(int n) {
+  CgLayout L;
+  size_t o = 0;
+  const size_t vec = al256(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  L.desc = o;  o += al256(sizeof(KrylovDesc));
+  L.state = o; o += al256(sizeof(KrylovState));
+  L.part = o;  o += al256(sizeof(double) * kMaxBlocks * kPartSlots);
+  L.r = o;     o += vec;
+  L.z = o;     o += vec;
+  L.p = o;     o += vec;
+  L.q = o;     o += vec;
+  L.dinv = o;  o += vec;
+  L.total = o;
+  return L;
+}
+
+inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
+  (void)nnz;
+  (void)batch;
+  switch (kind) {
+    case SLA_WS_CG:
+      *out = cg_layout(n).total;
+      return true;
+    default:
+      return false;
+  }
+}
+
+}  // namespace sla

@@ -1,0 +1,93 @@
+"""CPU-side checks of the C ABI: the shared library loads, exports every
+symbol include/sla.h declares, and rejects bad arguments synchronously
+(before any CUDA call, so these run without a GPU)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2601_13994_b300 import _lib as L
+from paper_2601_13994_b300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def setup_module(module):
+    B.build()
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(sla_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_symbols()
+    assert "sla_cg" in names and "sla_spmv" in names
+    lib = ctypes.CDLL(L.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_status_strings():
+    lib = L.lib()
+    assert b"sm_103a" in lib.sla_version()
+    for code, name in L.STATUS_NAMES.items():
+        assert lib.sla_status_string(code).decode() == name
+    assert lib.sla_status_string(12345) == b"UNKNOWN"
+
+
+def test_header_constants_match_binding():
+    src = open(os.path.join(ROOT, "include", "sla.h")).read()
+    consts = dict(re.findall(r"#define (SLA_\w+) \(?(-?\d+)\)?", src))
+    for k, v in consts.items():
+        if hasattr(L, k):
+            assert getattr(L, k) == int(v), k
+
+
+def test_workspace_size_query():
+    b1 = L.workspace_size(L.SLA_WS_CG, 1000, 5000)
+    b2 = L.workspace_size(L.SLA_WS_CG, 2000, 5000)
+    assert b1 % 256 == 0 and b2 > b1 >= 5 * 8 * 1000
+    with pytest.raises(L.SlaError):
+        L.workspace_size(999, 10, 10)
+    with pytest.raises(L.SlaError):
+        L.workspace_size(L.SLA_WS_CG, -1, 10)
+
+
+def test_bad_arguments_rejected_without_launch():
+    lib = L.lib()
+    A = L.SlaCsr(10, 20, None, None)
+    o = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0)
+    # null pattern pointers
+    assert lib.sla_spmv(ctypes.byref(A), None, None, None, None) == L.SLA_ERR_INVALID
+    assert lib.sla_cg(ctypes.byref(A), None, None, None, ctypes.byref(o), None, None, 0, None) == L.SLA_ERR_INVALID
+    assert lib.sla_cg(None, None, None, None, None, None, None, 0, None) == L.SLA_ERR_INVALID
+    # negative sizes
+    A2 = L.SlaCsr(-1, 0, None, None)
+    assert lib.sla_spmv(ctypes.byref(A2), None, None, None, None) == L.SLA_ERR_INVALID
+    # bad options / workspace (fake but non-null pointers; rejected before use)
+    fake = ctypes.c_void_p(0x1000)
+    A3 = L.SlaCsr(10, 20, fake, fake)
+    bad = L.SlaOpts(-1.0, 0.0, 100, 2, 1, 0)
+    assert lib.sla_cg(ctypes.byref(A3), fake, fake, ctypes.c_void_p(0x2000), ctypes.byref(bad), fake,
+                      fake, 1 << 20, None) == L.SLA_ERR_INVALID
+    o2 = L.SlaOpts(1e-8, 0.0, 100, 2, 7, 0)
+    assert lib.sla_cg(ctypes.byref(A3), fake, fake, ctypes.c_void_p(0x2000), ctypes.byref(o2), fake,
+                      ctypes.c_void_p(0x100000), 1 << 20, None) == L.SLA_ERR_INVALID
+    o3 = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0)
+    # misaligned and undersized workspace
+    assert lib.sla_cg(ctypes.byref(A3), fake, fake, ctypes.c_void_p(0x2000), ctypes.byref(o3), fake,
+                      ctypes.c_void_p(0x100010), 1 << 20, None) == L.SLA_ERR_WORKSPACE
+    assert lib.sla_cg(ctypes.byref(A3), fake, fake, ctypes.c_void_p(0x2000), ctypes.byref(o3), fake,
+                      ctypes.c_void_p(0x100000), 16, None) == L.SLA_ERR_WORKSPACE
+    # x aliasing b
+    assert lib.sla_cg(ctypes.byref(A3), fake, fake, fake, ctypes.byref(o3), fake,
+                      ctypes.c_void_p(0x100000), 1 << 20, None) == L.SLA_ERR_INVALID
