@@ -49,6 +49,10 @@ def parse():
                     help="oracle iterations per CPU sample (0: pick ~15 s of work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="launch the solver kernels from a host loop instead of one graph (profiling)")
+    ap.add_argument("--max-iter", type=int, default=None,
+                    help="iteration cap (bounded profiling runs; the timed numbers are then not a solve)")
     return ap.parse_args()
 
 
@@ -226,11 +230,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     # ---- warm-up and timed solves (device-resident inputs)
+    solve_kw = {"rtol": args.rtol, "graph": not args.host_loop, "max_iter": args.max_iter}
     for _ in range(args.warmup):
-        x, info = sla.cg(A, val, bt, rtol=args.rtol)
+        x, info = sla.cg(A, val, bt, **solve_kw)
     torch.cuda.synchronize(dev)
-    status = info.status
-    iters = info.iters
     props = torch.cuda.get_device_properties(dev)
     bus = None
     try:
@@ -248,7 +251,7 @@ def run_ours(args):
     e0.record(stream)
     infos = []
     for _ in range(args.steps):
-        x, info = sla.cg(A, val, bt, rtol=args.rtol)
+        x, info = sla.cg(A, val, bt, **solve_kw)
         infos.append(info)
     e1.record(stream)
     torch.cuda.synchronize(dev)
@@ -297,7 +300,7 @@ def run_ours(args):
             d_v.copy_(h_v, non_blocking=True)
             d_b.copy_(h_b, non_blocking=True)
             Ad = sla.CSRMatrix(d_rp, d_c, check=False)
-            xd, inf = sla.cg(Ad, d_v, d_b, rtol=args.rtol)
+            xd, inf = sla.cg(Ad, d_v, d_b, **solve_kw)
             h_x.copy_(xd, non_blocking=True)
             return inf
 

@@ -53,6 +53,12 @@ extern "C" {
 #define SLA_PRECOND_NONE 0
 #define SLA_PRECOND_JACOBI 1    /* z = D^{-1} r, D = diag(A) (Sec. 4.1)       */
 
+/* Flags (sla_opts.flags). */
+#define SLA_FLAG_HOST_LOOP 1    /* run the Krylov loop as plain stream launches
+                                   driven by the host (checks the device state
+                                   every 16 iterations, synchronising the
+                                   stream) instead of one graph launch       */
+
 /* Workspace kinds for sla_workspace_size(). */
 #define SLA_WS_CG 1
 
@@ -72,6 +78,7 @@ typedef struct sla_opts {
   int32_t max_restarts;   /* true-residual restarts allowed, 0..16            */
   int32_t precond;        /* SLA_PRECOND_*                                    */
   int32_t use_x0;         /* 1: x holds the initial guess; 0: start at x = 0 */
+  int32_t flags;          /* SLA_FLAG_* bits, 0 by default                    */
 } sla_opts;
 
 /* Per-system solve record (DEVICE memory, written by the enqueued work). */
@@ -137,7 +144,9 @@ int32_t sla_spmv(const sla_csr* A, const double* val, const double* x,
  * x = 0 after 0 iterations.  *info (DEVICE) receives the outcome.
  * The whole solve is one CUDA-graph launch whose device-side while-loop
  * decides convergence; the host is not synchronised.  The first call with a
- * given workspace address and sizes builds and caches that graph.
+ * given workspace address and sizes builds and caches that graph.  With
+ * SLA_FLAG_HOST_LOOP the same kernels are launched one by one on `stream`
+ * and the call returns after the loop has ended (it synchronises `stream`).
  * Workspace: sla_workspace_size(SLA_WS_CG, n, nnz, 1, &bytes). */
 int32_t sla_cg(const sla_csr* A, const double* val, const double* b,
                double* x, const sla_opts* opts, sla_info* info, void* ws,

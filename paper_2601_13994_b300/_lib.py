@@ -25,6 +25,8 @@ SLA_ERR_TIMEOUT = -4
 SLA_PRECOND_NONE = 0
 SLA_PRECOND_JACOBI = 1
 
+SLA_FLAG_HOST_LOOP = 1
+
 SLA_WS_CG = 1
 
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NOT_SPD", -1: "ERR_INVALID",
@@ -41,7 +43,8 @@ class SlaCsr(ctypes.Structure):
 class SlaOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
-                ("precond", ctypes.c_int32), ("use_x0", ctypes.c_int32)]
+                ("precond", ctypes.c_int32), ("use_x0", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

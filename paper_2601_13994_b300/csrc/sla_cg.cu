@@ -446,7 +446,33 @@ int cg_grids(int dev, int n, int* g1, int* gv) {
   return SLA_OK;
 }
 
-int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s) {
+// Host-driven loop: the same kernels as the graph, launched one by one.  The
+// device state is polled every kPollEvery loop bodies; kernels of a finished
+// solve return immediately, so overshooting the poll is harmless.
+constexpr int kPollEvery = 16;
+
+int run_host_loop(const CgPtrs& P, const KrylovDesc& desc, int g1, int gv, cudaStream_t s) {
+  cg_write_desc_kernel<<<1, 1, 0, s>>>(P.d, desc, P.st);
+  cg_init_kernel<<<gv, kVecThreads, 0, s>>>(P);
+  const long long cap = (long long)desc.max_iter + 2LL * desc.max_restarts + 8;
+  for (long long body = 0; body < cap; ++body) {
+    cg_spmv_pq_kernel<<<g1, kTileThreads, 0, s>>>(P);
+    cg_update_kernel<<<gv, kVecThreads, 0, s>>>(P);
+    cg_pupdate_kernel<<<gv, kVecThreads, 0, s>>>(P, cudaGraphConditionalHandle(0), 0);
+    if ((body + 1) % kPollEvery == 0) {
+      int phase = 0;
+      SLA_CUDA_TRY(cudaMemcpyAsync(&phase, &P.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SLA_CUDA_TRY(cudaStreamSynchronize(s));
+      if (phase == kPhaseDone) break;
+    }
+  }
+  cg_final_kernel<<<gv, kVecThreads, 0, s>>>(P);
+  SLA_CUDA_TRY(cudaGetLastError());
+  SLA_CUDA_TRY(cudaStreamSynchronize(s));
+  return SLA_OK;
+}
+
+int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags) {
   const int n = desc.n;
   const CgLayout L = cg_layout(n);
   char* base = (char*)ws;
@@ -462,6 +488,7 @@ int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s) {
   const int dev = current_device();
   int g1, gv;
   cg_grids(dev, n, &g1, &gv);
+  if (flags & SLA_FLAG_HOST_LOOP) return run_host_loop(P, desc, g1, gv, s);
   CgGraphKey key{dev, ws, n, desc.nnz, g1, gv};
   cudaGraphExec_t exec = nullptr;
   {
@@ -494,7 +521,7 @@ int validate_solve_args(const sla_csr* A, const double* val, const double* b, co
   if (A->nnz > 0 && (A->col == nullptr || val == nullptr)) return SLA_ERR_INVALID;
   if (A->n > 0 && (const void*)b == (const void*)x) return SLA_ERR_INVALID;
   if (!(o->rtol >= 0.0) || !(o->atol >= 0.0) || o->max_iter < 0 || o->max_restarts < 0 ||
-      o->max_restarts > 16 || (o->use_x0 != 0 && o->use_x0 != 1))
+      o->max_restarts > 16 || (o->use_x0 != 0 && o->use_x0 != 1) || (o->flags & ~1) != 0)
     return SLA_ERR_INVALID;
   if (ws == nullptr || ((uintptr_t)ws & 255u) != 0 || ws_bytes < need) return SLA_ERR_WORKSPACE;
   return SLA_OK;
@@ -534,5 +561,5 @@ extern "C" int32_t sla_cg(const sla_csr* A, const double* val, const double* b, 
   d.max_restarts = opts->max_restarts;
   d.precond = opts->precond;
   d.use_x0 = opts->use_x0;
-  return launch_cg(d, ws, s);
+  return launch_cg(d, ws, s, opts->flags);
 }

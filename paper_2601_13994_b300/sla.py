@@ -168,19 +168,21 @@ def spmv(A: CSRMatrix, val: torch.Tensor, x: torch.Tensor, out: torch.Tensor | N
 _PRECOND = {"none": L.SLA_PRECOND_NONE, "jacobi": L.SLA_PRECOND_JACOBI}
 
 
-def _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, n):
+def _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, n, graph=True):
     mi = default_max_iter(n) if max_iter is None else int(max_iter)
     if precond not in _PRECOND:
         raise ValueError("precond must be one of %s" % sorted(_PRECOND))
-    return L.SlaOpts(float(rtol), float(atol), mi, int(max_restarts), _PRECOND[precond], int(use_x0))
+    return L.SlaOpts(float(rtol), float(atol), mi, int(max_restarts), _PRECOND[precond], int(use_x0),
+                     0 if graph else L.SLA_FLAG_HOST_LOOP)
 
 
 def cg(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10, atol: float = 0.0,
        max_iter: int | None = None, precond: str = "jacobi", x0: torch.Tensor | None = None,
-       max_restarts: int = 2, out: torch.Tensor | None = None):
+       max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True):
     """Preconditioned CG for SPD A (Algorithm 1, one process).  Returns
-    (x, SolveInfo).  Runs as one graph launch; nothing synchronises until the
-    info is read."""
+    (x, SolveInfo).  With ``graph=True`` the solve is one graph launch and
+    nothing synchronises until the info is read; ``graph=False`` launches the
+    same kernels from a host loop (synchronising the stream)."""
     _need(val, torch.float64, A.device, "val", A.nnz)
     _need(b, torch.float64, A.device, "b", A.n)
     if out is None:
@@ -195,7 +197,7 @@ def cg(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10,
             x.copy_(x0)
         use_x0 = 1
     info = torch.empty((1, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
-    o = _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, A.n)
+    o = _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, A.n, graph)
     ws = workspace(L.SLA_WS_CG, A.n, A.nnz, 1, A.device)
     L.check("sla_cg", L.lib().sla_cg(ctypes.byref(A.c), _ptr(val), _ptr(b), _ptr(x), ctypes.byref(o),
                                     info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(A.device)))

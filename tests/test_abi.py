@@ -65,7 +65,7 @@ def test_workspace_size_query():
 def test_bad_arguments_rejected_without_launch():
     lib = L.lib()
     A = L.SlaCsr(10, 20, None, None)
-    o = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0)
+    o = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0, 0)
     # null pattern pointers
     assert lib.sla_spmv(ctypes.byref(A), None, None, None, None) == L.SLA_ERR_INVALID
     assert lib.sla_cg(ctypes.byref(A), None, None, None, ctypes.byref(o), None, None, 0, None) == L.SLA_ERR_INVALID
@@ -76,13 +76,13 @@ def test_bad_arguments_rejected_without_launch():
     # bad options / workspace (fake but non-null pointers; rejected before use)
     fake = ctypes.c_void_p(0x1000)
     A3 = L.SlaCsr(10, 20, fake, fake)
-    bad = L.SlaOpts(-1.0, 0.0, 100, 2, 1, 0)
+    bad = L.SlaOpts(-1.0, 0.0, 100, 2, 1, 0, 0)
     assert lib.sla_cg(ctypes.byref(A3), fake, fake, ctypes.c_void_p(0x2000), ctypes.byref(bad), fake,
                       fake, 1 << 20, None) == L.SLA_ERR_INVALID
-    o2 = L.SlaOpts(1e-8, 0.0, 100, 2, 7, 0)
+    o2 = L.SlaOpts(1e-8, 0.0, 100, 2, 7, 0, 0)
     assert lib.sla_cg(ctypes.byref(A3), fake, fake, ctypes.c_void_p(0x2000), ctypes.byref(o2), fake,
                       ctypes.c_void_p(0x100000), 1 << 20, None) == L.SLA_ERR_INVALID
-    o3 = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0)
+    o3 = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0, 0)
     # misaligned and undersized workspace
     assert lib.sla_cg(ctypes.byref(A3), fake, fake, ctypes.c_void_p(0x2000), ctypes.byref(o3), fake,
                       ctypes.c_void_p(0x100010), 1 << 20, None) == L.SLA_ERR_WORKSPACE

@@ -141,3 +141,19 @@ def test_full_size_diffusion3d_256_true_residual():
     true_rel = np.linalg.norm(r) / np.linalg.norm(b)
     assert true_rel <= 2e-8
     assert abs(true_rel - info["true_rel_res"]) <= 1e-3 * true_rel
+
+
+def test_host_loop_mode_reproduces_graph_mode():
+    """Same kernels, same grids: the host-driven loop must give the same bits."""
+    rp, c, v = I.diffusion3d_random(20, 9)
+    n = 8000
+    A = csr(rp, c)
+    vt = to_dev(v)
+    b = to_dev(I.rhs_uniform(n, 3))
+    xg, ig = sla.cg(A, vt, b, rtol=1e-10)
+    xh, ih = sla.cg(A, vt, b, rtol=1e-10, graph=False)
+    torch.cuda.synchronize()
+    assert torch.equal(xg, xh) and ig.iters == ih.iters and ig.status == ih.status == 0
+    # bounded run (iteration cap) in host-loop mode
+    _, ic = sla.cg(A, vt, b, rtol=1e-14, max_iter=20, graph=False)
+    assert ic.iters == 20 and ic.status_name == "NOT_CONVERGED"
