@@ -152,6 +152,40 @@ int32_t sla_cg(const sla_csr* A, const double* val, const double* b,
                double* x, const sla_opts* opts, sla_info* info, void* ws,
                size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------ */
+/* Allocation-free CG (no counterpart in the paper)                      */
+/* ------------------------------------------------------------------ */
+
+/* Largest n accepted by sla_cg_noalloc. */
+#define SLA_NOALLOC_MAX_N 393216
+
+/* Same solve as sla_cg (same kernels, same results), for callers that cannot
+ * allocate device memory at the time they solve: code that runs inside a
+ * framework's allocator or memory hook (a cudaMalloc there would re-enter the
+ * allocator), serving or real-time hosts that reserve all device memory at
+ * start-up and forbid later allocations, and plug-ins handed a stream but no
+ * allocator.  The caller passes inputs and outputs only; no workspace.
+ *
+ * Scratch space: a fixed array of about 16 MB (room for n <= SLA_NOALLOC_MAX_N)
+ * built into the library.  Every device that loads the library holds it until
+ * the process exits.  n > SLA_NOALLOC_MAX_N returns SLA_ERR_WORKSPACE and
+ * enqueues nothing.  The call never calls cudaMalloc, cudaFree or any
+ * allocating routine.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls on a device share the one array, which keeps the last
+ * call's contents (everything a solve needs zeroed is cleared at its start):
+ * calls that overlap on the GPU -- different streams, threads or processes
+ * sharing the context -- race and must be serialised by the caller.
+ *
+ * The loop is driven from the host (as with SLA_FLAG_HOST_LOOP): the call
+ * returns after the solve has finished on `stream`.  Other arguments,
+ * options and the *info record behave as for sla_cg. */
+int32_t sla_cg_noalloc(const sla_csr* A, const double* val, const double* b,
+                       double* x, const sla_opts* opts, sla_info* info,
+                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

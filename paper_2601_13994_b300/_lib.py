@@ -29,6 +29,8 @@ SLA_FLAG_HOST_LOOP = 1
 
 SLA_WS_CG = 1
 
+SLA_NOALLOC_MAX_N = 393216
+
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NOT_SPD", -1: "ERR_INVALID",
                 -2: "ERR_CUDA", -3: "ERR_WORKSPACE", -4: "ERR_TIMEOUT"}
 
@@ -81,6 +83,8 @@ def lib() -> ctypes.CDLL:
             L.sla_cg.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, ctypes.POINTER(SlaOpts), P, P,
                                  ctypes.c_size_t, P]
             L.sla_cg.restype = i32
+            L.sla_cg_noalloc.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, ctypes.POINTER(SlaOpts), P, P]
+            L.sla_cg_noalloc.restype = i32
             _lib = L
     return _lib
 

@@ -563,3 +563,76 @@ extern "C" int32_t sla_cg(const sla_csr* A, const double* val, const double* b, 
   d.use_x0 = opts->use_x0;
   return launch_cg(d, ws, s, opts->flags);
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free CG.  The paper has no counterpart: this exists for callers
+// that cannot allocate device memory when they solve -- code running inside a
+// framework's allocator or memory hook (a cudaMalloc there would re-enter the
+// allocator), serving or real-time hosts that reserve all device memory once
+// at start-up and forbid allocations afterwards, and plug-ins that receive a
+// stream but no allocator.  Such callers still pass inputs and outputs; the
+// scratch space (descriptor, state, partial sums, five n-vectors) lives in
+// the fixed-size array below, which every device that loads this library
+// holds until the process exits.
+// ---------------------------------------------------------------------------
+static constexpr size_t kNoallocScratchBytes = sla::cg_layout(SLA_NOALLOC_MAX_N).total;
+static __device__ __align__(256) unsigned char sla_noalloc_scratch[kNoallocScratchBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device.  In host code the array's name is only a host-side stand-in,
+// never a device address, so it is resolved with cudaGetSymbolAddress.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SLA_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (g_noalloc_addr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, sla_noalloc_scratch) != cudaSuccess || p == nullptr)
+      return SLA_ERR_CUDA;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return SLA_OK;
+}
+}  // namespace
+
+extern "C" int32_t sla_cg_noalloc(const sla_csr* A, const double* val, const double* b, double* x,
+                                  const sla_opts* opts, sla_info* info, void* stream) {
+  if (A == nullptr || opts == nullptr) return SLA_ERR_INVALID;
+  if (A->n > SLA_NOALLOC_MAX_N) return SLA_ERR_WORKSPACE;
+  void* ws = nullptr;
+  int rc = noalloc_scratch(&ws);
+  if (rc != SLA_OK) return rc;
+  const size_t need = cg_layout(A->n > 0 ? A->n : 0).total;
+  rc = validate_solve_args(A, val, b, x, opts, info, ws, kNoallocScratchBytes, need);
+  if (rc != SLA_OK) return rc;
+  if (opts->precond != SLA_PRECOND_NONE && opts->precond != SLA_PRECOND_JACOBI) return SLA_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (A->n == 0) {
+    sla_info v{0, SLA_OK, 0.0, 0.0};
+    write_info_kernel<<<1, 1, 0, s>>>(info, v);
+    SLA_CUDA_TRY(cudaGetLastError());
+    return SLA_OK;
+  }
+  KrylovDesc d = {};
+  d.n = A->n;
+  d.nnz = A->nnz;
+  d.rowptr = A->rowptr;
+  d.col = A->col;
+  d.val = val;
+  d.b = b;
+  d.x = x;
+  d.info = info;
+  d.rtol = opts->rtol;
+  d.atol = opts->atol;
+  d.max_iter = opts->max_iter;
+  d.max_restarts = opts->max_restarts;
+  d.precond = opts->precond;
+  d.use_x0 = opts->use_x0;
+  // plain launches from a host loop: no graph objects are created
+  return launch_cg(d, ws, s, opts->flags | SLA_FLAG_HOST_LOOP);
+}

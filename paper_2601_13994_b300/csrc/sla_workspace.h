@@ -52,10 +52,10 @@ struct CgLayout {
   size_t desc, state, part, r, z, p, q, dinv, total;
 };
 
-inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+constexpr size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
-inline CgLayout cg_layout(int n) {
-  CgLayout L;
+constexpr CgLayout cg_layout(int n) {
+  CgLayout L{};
   size_t o = 0;
   const size_t vec = al256(sizeof(double) * (size_t)(n > 0 ? n : 1));
   L.desc = o;  o += al256(sizeof(KrylovDesc));
