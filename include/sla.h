@@ -61,6 +61,7 @@ extern "C" {
 
 /* Workspace kinds for sla_workspace_size(). */
 #define SLA_WS_CG 1
+#define SLA_WS_BICGSTAB 2
 
 /* Pattern of a square CSR matrix (all pointers device). */
 typedef struct sla_csr {
@@ -151,6 +152,24 @@ int32_t sla_spmv(const sla_csr* A, const double* val, const double* x,
 int32_t sla_cg(const sla_csr* A, const double* val, const double* b,
                double* x, const sla_opts* opts, sla_info* info, void* ws,
                size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* BiCGStab for nonsymmetric A (van der Vorst 1992; the paper's GPU      */
+/* iterative backend offers it for nonsymmetric systems, Sec. 1 and 3.1) */
+/* ------------------------------------------------------------------ */
+
+/* Solves A x = b with right-preconditioned BiCGStab (shadow residual
+ * r^ = r0; with SLA_PRECOND_JACOBI, M = diag(A)).  Arguments, stopping rule,
+ * true-residual restart, graph/host-loop execution and the info record are
+ * as for sla_cg.  Outcomes: OK (also at the half step, when ||s|| meets the
+ * target), NOT_CONVERGED, BREAKDOWN (|rho| < 1e-300, r^.v = 0, t.t = 0,
+ * omega = 0 or a non-finite scalar), and status SLA_ERR_INVALID in *info when
+ * Jacobi meets a zero diagonal.  Iterations count full BiCGStab steps (two
+ * SpMVs each).  Workspace: sla_workspace_size(SLA_WS_BICGSTAB, n, nnz, 1,
+ * &bytes). */
+int32_t sla_bicgstab(const sla_csr* A, const double* val, const double* b,
+                     double* x, const sla_opts* opts, sla_info* info,
+                     void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Allocation-free CG (no counterpart in the paper)                      */

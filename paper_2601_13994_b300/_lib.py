@@ -28,6 +28,7 @@ SLA_PRECOND_JACOBI = 1
 SLA_FLAG_HOST_LOOP = 1
 
 SLA_WS_CG = 1
+SLA_WS_BICGSTAB = 2
 
 SLA_NOALLOC_MAX_N = 393216
 
@@ -83,6 +84,9 @@ def lib() -> ctypes.CDLL:
             L.sla_cg.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, ctypes.POINTER(SlaOpts), P, P,
                                  ctypes.c_size_t, P]
             L.sla_cg.restype = i32
+            L.sla_bicgstab.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, ctypes.POINTER(SlaOpts), P, P,
+                                       ctypes.c_size_t, P]
+            L.sla_bicgstab.restype = i32
             L.sla_cg_noalloc.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, ctypes.POINTER(SlaOpts), P, P]
             L.sla_cg_noalloc.restype = i32
             _lib = L

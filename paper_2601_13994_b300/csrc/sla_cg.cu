@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "sla_internal.cuh"
+#include "sla_tma.cuh"
 #include "sla_workspace.h"
 
 namespace sla {
@@ -48,28 +49,28 @@ struct CgPtrs {
 __global__ void cg_write_desc_kernel(KrylovDesc* dst, KrylovDesc src, KrylovState* st) {
   *dst = src;
   for (int i = 0; i < 8; ++i) st->cnt[i] = 0u;
+  st->err = 0;
 }
 
-// Row i of A times v, summed sequentially from global memory.
-__device__ __forceinline__ double row_dot(const int* __restrict__ rowptr,
-                                          const int* __restrict__ col,
-                                          const double* __restrict__ val,
-                                          const double* __restrict__ v, int i) {
-  const int a = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
-  double s = 0.0;
-  for (int k = a; k < e; ++k) s = fma(__ldg(val + k), __ldg(v + __ldg(col + k)), s);
-  return s;
-}
+// Shared scratch of the vector kernels: up to 4 reduced values per block.
+constexpr int kRedSlots = 4;
+struct VecSmem {
+  double red[kRedSlots * kVecThreads + kRedSlots];
+  bool last;
+};
+
+// Unroll factor of the streaming loops: U independent elements per thread
+// per pass keep 5 U loads in flight.
+constexpr int kUnroll = 4;
 
 // ---------------------------------------------------------------- init
 // dinv = 1 / diag(A) (or 1 without preconditioner), r = b - A x0,
 // z = dinv r, p = z; sums ||b||^2, ||r||^2, r.z and a bad-diagonal flag.
 __global__ void __launch_bounds__(kVecThreads) cg_init_kernel(CgPtrs P) {
-  __shared__ double red[kVecThreads / kWarp];
-  __shared__ bool s_last;
+  __shared__ VecSmem sm;
   const KrylovDesc d = *P.d;
   const int n = d.n;
-  double bb = 0.0, rr = 0.0, rz = 0.0, bad = 0.0;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // bb, rr, rz, bad
   const int stride = gridDim.x * kVecThreads;
   for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride) {
     const int a = d.rowptr[i], e = d.rowptr[i + 1];
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(kVecThreads) cg_init_kernel(CgPtrs P) {
     const double ri = bi - ax;
     double di = 1.0;
     if (d.precond == SLA_PRECOND_JACOBI) {
-      if (!(diag > 0.0)) bad = 1.0;
+      if (!(diag > 0.0)) acc[3] = 1.0;
       di = 1.0 / diag;
     }
     const double zi = di * ri;
@@ -92,30 +93,21 @@ __global__ void __launch_bounds__(kVecThreads) cg_init_kernel(CgPtrs P) {
     P.r[i] = ri;
     P.z[i] = zi;
     P.p[i] = zi;
-    bb = fma(bi, bi, bb);
-    rr = fma(ri, ri, rr);
-    rz = fma(ri, zi, rz);
+    acc[0] = fma(bi, bi, acc[0]);
+    acc[1] = fma(ri, ri, acc[1]);
+    acc[2] = fma(ri, zi, acc[2]);
   }
   if (!d.use_x0) {
     for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride) d.x[i] = 0.0;
   }
-  const double sbb = block_sum<kVecThreads>(bb, red);
-  const double srr = block_sum<kVecThreads>(rr, red);
-  const double srz = block_sum<kVecThreads>(rz, red);
-  const double sbad = block_sum<kVecThreads>(bad, red);
+  block_sums<kVecThreads, 4>(acc, sm.red);
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 4; ++j) P.part[j * kMaxBlocks + blockIdx.x] = acc[j];
+  if (!last_block_arrive(&P.st->cnt[0], &sm.last)) return;
+  double t[4];
+  reduce_partials<kVecThreads, 4>(P.part, kMaxBlocks, gridDim.x, t, sm.red);
   if (threadIdx.x == 0) {
-    P.part[0 * kMaxBlocks + blockIdx.x] = sbb;
-    P.part[1 * kMaxBlocks + blockIdx.x] = srr;
-    P.part[2 * kMaxBlocks + blockIdx.x] = srz;
-    P.part[3 * kMaxBlocks + blockIdx.x] = sbad;
-  }
-  if (!last_block_arrive(&P.st->cnt[0], &s_last)) return;
-  const int G = gridDim.x;
-  const double tbb = reduce_partials<kVecThreads>(P.part + 0 * kMaxBlocks, G, red);
-  const double trr = reduce_partials<kVecThreads>(P.part + 1 * kMaxBlocks, G, red);
-  const double trz = reduce_partials<kVecThreads>(P.part + 2 * kMaxBlocks, G, red);
-  const double tbad = reduce_partials<kVecThreads>(P.part + 3 * kMaxBlocks, G, red);
-  if (threadIdx.x == 0) {
+    const double tbb = t[0], trr = t[1], trz = t[2], tbad = t[3];
     KrylovState& s = *P.st;
     s.bnorm = sqrt(tbb);
     s.thresh = fmax(d.rtol * s.bnorm, d.atol);
@@ -150,7 +142,7 @@ __global__ void __launch_bounds__(kVecThreads) cg_init_kernel(CgPtrs P) {
 }
 
 // ---------------------------------------------------------------- K1
-__global__ void __launch_bounds__(kTileThreads) cg_spmv_pq_kernel(CgPtrs P) {
+__global__ void __launch_bounds__(kTileThreads, 3) cg_spmv_pq_kernel(CgPtrs P) {
   __shared__ TileSmem sm;
   __shared__ bool s_last;
   if (__ldcg(&P.st->phase) != kPhaseRun) return;
@@ -165,11 +157,13 @@ __global__ void __launch_bounds__(kTileThreads) cg_spmv_pq_kernel(CgPtrs P) {
       q[row] = s;
       pq = fma(__ldg(p + row), s, pq);
     });
-  const double spq = block_sum<kTileThreads>(pq, sm.red);
-  if (threadIdx.x == 0) P.part[blockIdx.x] = spq;
+  double v[1] = {pq};
+  block_sums<kTileThreads, 1>(v, sm.val);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
   if (!last_block_arrive(&P.st->cnt[1], &s_last)) return;
-  const double tpq = reduce_partials<kTileThreads>(P.part, gridDim.x, sm.red);
+  reduce_partials<kTileThreads, 1>(P.part, kMaxBlocks, gridDim.x, v, sm.val);
   if (threadIdx.x == 0) {
+    const double tpq = v[0];
     KrylovState& s = *P.st;
     s.pq = tpq;
     if (!isfinite(tpq)) {
@@ -184,10 +178,47 @@ __global__ void __launch_bounds__(kTileThreads) cg_spmv_pq_kernel(CgPtrs P) {
   }
 }
 
+// K1 on the TMA-pipelined tiles (see sla_tma.cuh).
+__global__ void __launch_bounds__(tma::kThreads) cg_spmv_pq_tma_kernel(CgPtrs P) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
+  if (__ldcg(&P.st->phase) != kPhaseRun) return;
+  const KrylovDesc d = *P.d;
+  const double* __restrict__ p = P.p;
+  double* __restrict__ q = P.q;
+  double pq = 0.0;
+  tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, p, p, sm, &P.st->err,
+                     [&](int row, double s, double prow) {
+                       q[row] = s;
+                       pq = fma(prow, s, pq);
+                     });
+  double v[1] = {pq};
+  block_sums<tma::kThreads, 1>(v, sm.red);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
+  if (!last_block_arrive(&P.st->cnt[1], &sm.last)) return;
+  reduce_partials<tma::kThreads, 1>(P.part, kMaxBlocks, gridDim.x, v, sm.red);
+  if (threadIdx.x == 0) {
+    const double tpq = v[0];
+    KrylovState& s = *P.st;
+    s.pq = tpq;
+    if (__ldcg(&s.err) != 0) {
+      s.status = SLA_ERR_TIMEOUT;
+      s.phase = kPhaseDone;
+    } else if (!isfinite(tpq)) {
+      s.status = SLA_BREAKDOWN;
+      s.phase = kPhaseDone;
+    } else if (!(tpq > 0.0)) {
+      s.status = SLA_NOT_SPD;
+      s.phase = kPhaseDone;
+    } else {
+      s.alpha = s.rho / tpq;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- K2
 __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(CgPtrs P) {
-  __shared__ double red[kVecThreads / kWarp];
-  __shared__ bool s_last;
+  __shared__ VecSmem sm;
   if (__ldcg(&P.st->phase) != kPhaseRun) return;
   const KrylovDesc d = *P.d;
   const int n = d.n;
@@ -198,30 +229,51 @@ __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(CgPtrs P) {
   const double* __restrict__ p = P.p;
   const double* __restrict__ q = P.q;
   const double* __restrict__ dinv = P.dinv;
-  double rz = 0.0, rr = 0.0;
+  double rz0 = 0.0, rz1 = 0.0, rr0 = 0.0, rr1 = 0.0;
   const int stride = gridDim.x * kVecThreads;
-  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride) {
-    const double pi = __ldg(p + i), qi = __ldg(q + i), di = __ldg(dinv + i);
-    const double xi = fma(alpha, pi, x[i]);
-    const double ri = fma(-alpha, qi, r[i]);
-    const double zi = di * ri;
-    x[i] = xi;
-    r[i] = ri;
-    z[i] = zi;
-    rz = fma(ri, zi, rz);
-    rr = fma(ri, ri, rr);
+  for (int i0 = blockIdx.x * kVecThreads + threadIdx.x; i0 < n; i0 += kUnroll * stride) {
+    double pi[kUnroll], qi[kUnroll], di[kUnroll], xi[kUnroll], ri[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = i0 + u * stride;
+      if (i < n) {
+        pi[u] = __ldg(p + i);
+        qi[u] = __ldg(q + i);
+        di[u] = __ldg(dinv + i);
+        xi[u] = x[i];
+        ri[u] = r[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = i0 + u * stride;
+      if (i < n) {
+        const double xn = fma(alpha, pi[u], xi[u]);
+        const double rn = fma(-alpha, qi[u], ri[u]);
+        const double zn = di[u] * rn;
+        x[i] = xn;
+        r[i] = rn;
+        z[i] = zn;
+        if (u & 1) {
+          rz1 = fma(rn, zn, rz1);
+          rr1 = fma(rn, rn, rr1);
+        } else {
+          rz0 = fma(rn, zn, rz0);
+          rr0 = fma(rn, rn, rr0);
+        }
+      }
+    }
   }
-  const double srz = block_sum<kVecThreads>(rz, red);
-  const double srr = block_sum<kVecThreads>(rr, red);
+  double v[2] = {rz0 + rz1, rr0 + rr1};
+  block_sums<kVecThreads, 2>(v, sm.red);
   if (threadIdx.x == 0) {
-    P.part[0 * kMaxBlocks + blockIdx.x] = srz;
-    P.part[1 * kMaxBlocks + blockIdx.x] = srr;
+    P.part[0 * kMaxBlocks + blockIdx.x] = v[0];
+    P.part[1 * kMaxBlocks + blockIdx.x] = v[1];
   }
-  if (!last_block_arrive(&P.st->cnt[2], &s_last)) return;
-  const int G = gridDim.x;
-  const double trz = reduce_partials<kVecThreads>(P.part + 0 * kMaxBlocks, G, red);
-  const double trr = reduce_partials<kVecThreads>(P.part + 1 * kMaxBlocks, G, red);
+  if (!last_block_arrive(&P.st->cnt[2], &sm.last)) return;
+  reduce_partials<kVecThreads, 2>(P.part, kMaxBlocks, gridDim.x, v, sm.red);
   if (threadIdx.x == 0) {
+    const double trz = v[0], trr = v[1];
     KrylovState& s = *P.st;
     s.iters += 1;
     s.rr = trr;
@@ -248,19 +300,32 @@ __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(CgPtrs P) {
 // ---------------------------------------------------------------- K3
 __global__ void __launch_bounds__(kVecThreads)
 cg_pupdate_kernel(CgPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
-  __shared__ double red[kVecThreads / kWarp];
-  __shared__ bool s_last;
+  __shared__ VecSmem sm;
   const int phase = __ldcg(&P.st->phase);
   const KrylovDesc d = *P.d;
   const int n = d.n;
   const int stride = gridDim.x * kVecThreads;
-  double tt = 0.0, rz = 0.0;
+  double v[2] = {0.0, 0.0};  // tt, rz of the check pass
   if (phase == kPhaseRun) {
     const double beta = __ldcg(&P.st->beta);
     const double* __restrict__ z = P.z;
     double* __restrict__ p = P.p;
-    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride)
-      p[i] = fma(beta, p[i], __ldg(z + i));
+    for (int i0 = blockIdx.x * kVecThreads + threadIdx.x; i0 < n; i0 += kUnroll * stride) {
+      double zi[kUnroll], pi[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * stride;
+        if (i < n) {
+          zi[u] = __ldg(z + i);
+          pi[u] = p[i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * stride;
+        if (i < n) p[i] = fma(beta, pi[u], zi[u]);
+      }
+    }
   } else if (phase == kPhaseCheck) {
     for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride) {
       const double ti = d.b[i] - row_dot(d.rowptr, d.col, d.val, d.x, i);
@@ -268,27 +333,21 @@ cg_pupdate_kernel(CgPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
       P.r[i] = ti;
       P.z[i] = zi;
       P.p[i] = zi;
-      tt = fma(ti, ti, tt);
-      rz = fma(ti, zi, rz);
+      v[0] = fma(ti, ti, v[0]);
+      v[1] = fma(ti, zi, v[1]);
     }
-  }
-  if (phase == kPhaseCheck) {
-    const double stt = block_sum<kVecThreads>(tt, red);
-    const double srz = block_sum<kVecThreads>(rz, red);
+    block_sums<kVecThreads, 2>(v, sm.red);
     if (threadIdx.x == 0) {
-      P.part[0 * kMaxBlocks + blockIdx.x] = stt;
-      P.part[1 * kMaxBlocks + blockIdx.x] = srz;
+      P.part[0 * kMaxBlocks + blockIdx.x] = v[0];
+      P.part[1 * kMaxBlocks + blockIdx.x] = v[1];
     }
   }
-  if (!last_block_arrive(&P.st->cnt[3], &s_last)) return;
-  double ttt = 0.0, trz = 0.0;
-  if (phase == kPhaseCheck) {
-    ttt = reduce_partials<kVecThreads>(P.part + 0 * kMaxBlocks, gridDim.x, red);
-    trz = reduce_partials<kVecThreads>(P.part + 1 * kMaxBlocks, gridDim.x, red);
-  }
+  if (!last_block_arrive(&P.st->cnt[3], &sm.last)) return;
+  if (phase == kPhaseCheck) reduce_partials<kVecThreads, 2>(P.part, kMaxBlocks, gridDim.x, v, sm.red);
   if (threadIdx.x == 0) {
     KrylovState& s = *P.st;
     if (phase == kPhaseCheck) {
+      const double ttt = v[0], trz = v[1];
       const double tn = sqrt(ttt);
       s.tt = ttt;
       if (tn <= 2.0 * s.thresh) {
@@ -322,27 +381,27 @@ cg_pupdate_kernel(CgPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
 
 // ---------------------------------------------------------------- final
 __global__ void __launch_bounds__(kVecThreads) cg_final_kernel(CgPtrs P) {
-  __shared__ double red[kVecThreads / kWarp];
-  __shared__ bool s_last;
+  __shared__ VecSmem sm;
   const KrylovDesc d = *P.d;
   const int n = d.n;
   const int zero_rhs = __ldcg(&P.st->zero_rhs);
   const int bad = __ldcg(&P.st->bad_diag);
   const int stride = gridDim.x * kVecThreads;
-  double tt = 0.0;
+  double v[1] = {0.0};
   for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride) {
     if (zero_rhs || bad) {
       if (zero_rhs) d.x[i] = 0.0;
     } else {
       const double ti = d.b[i] - row_dot(d.rowptr, d.col, d.val, d.x, i);
-      tt = fma(ti, ti, tt);
+      v[0] = fma(ti, ti, v[0]);
     }
   }
-  const double stt = block_sum<kVecThreads>(tt, red);
-  if (threadIdx.x == 0) P.part[blockIdx.x] = stt;
-  if (!last_block_arrive(&P.st->cnt[4], &s_last)) return;
-  const double ttt = reduce_partials<kVecThreads>(P.part, gridDim.x, red);
+  block_sums<kVecThreads, 1>(v, sm.red);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
+  if (!last_block_arrive(&P.st->cnt[4], &sm.last)) return;
+  reduce_partials<kVecThreads, 1>(P.part, kMaxBlocks, gridDim.x, v, sm.red);
   if (threadIdx.x == 0) {
+    const double ttt = v[0];
     const KrylovState& s = *P.st;
     sla_info inf;
     inf.iters = s.iters;
@@ -363,15 +422,43 @@ __global__ void __launch_bounds__(kVecThreads) cg_final_kernel(CgPtrs P) {
 
 __global__ void write_info_kernel(sla_info* info, sla_info v) { *info = v; }
 
+int occupancy(const void* fn, int threads, size_t smem) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem) != cudaSuccess || b <= 0)
+    b = 1;
+  return b;
+}
+
+cudaError_t add_kernel(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                       cudaGraphNode_t* out, const void* fn, int grid, int block, void** args,
+                       unsigned smem) {
+  cudaKernelNodeParams kp = {};
+  kp.func = const_cast<void*>(fn);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(block);
+  kp.sharedMemBytes = smem;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  return cudaGraphAddKernelNode(out, g, deps, ndeps, &kp);
+}
+
+
+int write_info(sla_info* info, sla_info v, cudaStream_t s) {
+  write_info_kernel<<<1, 1, 0, s>>>(info, v);
+  SLA_CUDA_TRY(cudaGetLastError());
+  return SLA_OK;
+}
+
 // ---------------------------------------------------------------- graph
 namespace {
 
 struct CgGraphKey {
   int dev;
   const void* ws;
-  int n, nnz, g1, gv;
+  int n, nnz, g1, gv, tma;
   bool operator==(const CgGraphKey& o) const {
-    return dev == o.dev && ws == o.ws && n == o.n && nnz == o.nnz && g1 == o.g1 && gv == o.gv;
+    return dev == o.dev && ws == o.ws && n == o.n && nnz == o.nnz && g1 == o.g1 && gv == o.gv &&
+           tma == o.tma;
   }
 };
 
@@ -384,26 +471,19 @@ std::mutex g_mu;
 std::vector<CgGraphEntry> g_cache;
 constexpr size_t kCacheMax = 64;
 
-int occupancy(const void* fn, int threads) {
-  int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, 0) != cudaSuccess || b <= 0)
-    b = 2;
-  return b;
+// The K1 variant in use: kernel, block size and dynamic shared memory.
+struct K1Launch {
+  const void* fn;
+  int threads;
+  unsigned smem;
+};
+
+K1Launch k1_launch(bool tma) {
+  if (tma) return K1Launch{(const void*)cg_spmv_pq_tma_kernel, tma::kThreads, (unsigned)tma::kSmemBytes};
+  return K1Launch{(const void*)cg_spmv_pq_kernel, kTileThreads, 0u};
 }
 
-cudaError_t add_kernel(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
-                       cudaGraphNode_t* out, const void* fn, int grid, int block, void** args) {
-  cudaKernelNodeParams kp = {};
-  kp.func = const_cast<void*>(fn);
-  kp.gridDim = dim3(grid);
-  kp.blockDim = dim3(block);
-  kp.sharedMemBytes = 0;
-  kp.kernelParams = args;
-  kp.extra = nullptr;
-  return cudaGraphAddKernelNode(out, g, deps, ndeps, &kp);
-}
-
-int build_graph(CgPtrs P, int g1, int gv, cudaGraphExec_t* exec) {
+int build_graph(CgPtrs P, K1Launch k1, int g1, int gv, cudaGraphExec_t* exec) {
   cudaGraph_t g = nullptr;
   SLA_CUDA_TRY(cudaGraphCreate(&g, 0));
   int rc = SLA_ERR_CUDA;
@@ -423,7 +503,7 @@ int build_graph(CgPtrs P, int g1, int gv, cudaGraphExec_t* exec) {
     int use_cond = 1;
     void* a1[] = {&P};
     void* a3[] = {&P, &h, &use_cond};
-    if (add_kernel(body, nullptr, 0, &n1, (const void*)cg_spmv_pq_kernel, g1, kTileThreads, a1) != cudaSuccess) break;
+    if (add_kernel(body, nullptr, 0, &n1, k1.fn, g1, k1.threads, a1, k1.smem) != cudaSuccess) break;
     if (add_kernel(body, &n1, 1, &n2, (const void*)cg_update_kernel, gv, kVecThreads, a1) != cudaSuccess) break;
     if (add_kernel(body, &n2, 1, &n3, (const void*)cg_pupdate_kernel, gv, kVecThreads, a3) != cudaSuccess) break;
     if (add_kernel(g, &n_while, 1, &n_final, (const void*)cg_final_kernel, gv, kVecThreads, a_init) != cudaSuccess) break;
@@ -436,12 +516,17 @@ int build_graph(CgPtrs P, int g1, int gv, cudaGraphExec_t* exec) {
 
 }  // namespace
 
-int cg_grids(int dev, int n, int* g1, int* gv) {
-  static int occ1 = 0, occv = 0;
+int cg_grids(int dev, int n, bool tma, int* g1, int* gv) {
+  static int occ1 = 0, occ1t = 0, occv = 0;
   if (occ1 == 0) occ1 = occupancy((const void*)cg_spmv_pq_kernel, kTileThreads);
+  if (occ1t == 0) {
+    cudaFuncSetAttribute(cg_spmv_pq_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tma::kSmemBytes);
+    occ1t = occupancy((const void*)cg_spmv_pq_tma_kernel, tma::kThreads, tma::kSmemBytes);
+  }
   if (occv == 0) occv = occupancy((const void*)cg_update_kernel, kVecThreads);
   const long long ntiles = (n + kTileRows - 1) / kTileRows;
-  *g1 = persistent_grid(dev, ntiles, occ1, kMaxBlocks);
+  *g1 = persistent_grid(dev, ntiles, tma ? occ1t : occ1, kMaxBlocks);
   *gv = persistent_grid(dev, ((long long)n + kVecThreads - 1) / kVecThreads, occv, kMaxBlocks);
   return SLA_OK;
 }
@@ -451,12 +536,14 @@ int cg_grids(int dev, int n, int* g1, int* gv) {
 // solve return immediately, so overshooting the poll is harmless.
 constexpr int kPollEvery = 16;
 
-int run_host_loop(const CgPtrs& P, const KrylovDesc& desc, int g1, int gv, cudaStream_t s) {
+int run_host_loop(const CgPtrs& P, const KrylovDesc& desc, K1Launch k1, int g1, int gv,
+                  cudaStream_t s) {
   cg_write_desc_kernel<<<1, 1, 0, s>>>(P.d, desc, P.st);
   cg_init_kernel<<<gv, kVecThreads, 0, s>>>(P);
   const long long cap = (long long)desc.max_iter + 2LL * desc.max_restarts + 8;
   for (long long body = 0; body < cap; ++body) {
-    cg_spmv_pq_kernel<<<g1, kTileThreads, 0, s>>>(P);
+    void* a1[] = {const_cast<CgPtrs*>(&P)};
+    SLA_CUDA_TRY(cudaLaunchKernel(k1.fn, dim3(g1), dim3(k1.threads), a1, k1.smem, s));
     cg_update_kernel<<<gv, kVecThreads, 0, s>>>(P);
     cg_pupdate_kernel<<<gv, kVecThreads, 0, s>>>(P, cudaGraphConditionalHandle(0), 0);
     if ((body + 1) % kPollEvery == 0) {
@@ -486,17 +573,19 @@ int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags) {
   P.q = (double*)(base + L.q);
   P.dinv = (double*)(base + L.dinv);
   const int dev = current_device();
+  const bool tma = use_tma_spmv();
+  const K1Launch k1 = k1_launch(tma);
   int g1, gv;
-  cg_grids(dev, n, &g1, &gv);
-  if (flags & SLA_FLAG_HOST_LOOP) return run_host_loop(P, desc, g1, gv, s);
-  CgGraphKey key{dev, ws, n, desc.nnz, g1, gv};
+  cg_grids(dev, n, tma, &g1, &gv);
+  if (flags & SLA_FLAG_HOST_LOOP) return run_host_loop(P, desc, k1, g1, gv, s);
+  CgGraphKey key{dev, ws, n, desc.nnz, g1, gv, tma ? 1 : 0};
   cudaGraphExec_t exec = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto& e : g_cache)
       if (e.key == key) exec = e.exec;
     if (exec == nullptr) {
-      const int rc = build_graph(P, g1, gv, &exec);
+      const int rc = build_graph(P, k1, g1, gv, &exec);
       if (rc != SLA_OK) return rc;
       if (g_cache.size() >= kCacheMax) {
         SLA_CUDA_TRY(cudaDeviceSynchronize());

@@ -1,5 +1,7 @@
 // sla_common.cu -- library information, device-property cache, workspace
 // size query and CSR pattern validation.
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 #include "sla_internal.cuh"
@@ -16,6 +18,15 @@ int current_device() {
   int d = 0;
   cudaGetDevice(&d);
   return d;
+}
+
+bool use_tma_spmv() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("SLA_SPMV_KERNEL");
+    v = (e != nullptr && strcmp(e, "tile") == 0) ? 0 : 1;
+  }
+  return v == 1;
 }
 
 int num_sms(int device) {

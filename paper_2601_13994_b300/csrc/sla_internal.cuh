@@ -39,18 +39,41 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum over the block; result valid in every thread.  `sh` needs NT/32 doubles.
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  static_assert(NT % kWarp == 0 && NT <= 1024, "block size");
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  v = warp_sum(v);
+// Sums NV values over the block; on return v[j] holds block total j in every
+// thread.  Each thread parks its values in shared memory and warp j adds
+// value j: lane l takes entries l, l+32, l+64, ... in that order
+// (bank-conflict free), then a 5-level butterfly.  That is NT/32 + 4 FP64
+// adds per lane of one warp per value, instead of a butterfly in every warp
+// -- FP64 adds are the scarce unit on this part.  Needs NV <= NT/32; the
+// scratch array must hold NV*NT + NV doubles (checked at compile time).
+template <int NT, int NV, int M>
+__device__ __forceinline__ void block_sums(double (&v)[NV], double (&sh)[M]) {
+  static_assert(NT % kWarp == 0 && NT <= 1024 && NV <= NT / kWarp, "block size");
+  static_assert(M >= NV * NT + NV, "reduction scratch too small");
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   __syncthreads();
-  if (lane == 0) sh[wid] = v;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) sh[j * NT + tid] = v[j];
   __syncthreads();
-  double t = (lane < NT / kWarp) ? sh[lane] : 0.0;
-  t = warp_sum(t);
-  return t;
+  if (w < NV) {
+    const double* col = sh + w * NT + lane;
+    double s = col[0];
+#pragma unroll
+    for (int k = 1; k < NT / kWarp; ++k) s += col[kWarp * k];
+    s = warp_sum(s);
+    if (lane == 0) sh[NV * NT + w] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = sh[NV * NT + j];
+}
+
+// Single-value form of block_sums.
+template <int NT, int M>
+__device__ __forceinline__ double block_sum(double v, double (&sh)[M]) {
+  double a[1] = {v};
+  block_sums<NT, 1>(a, sh);
+  return a[0];
 }
 
 // Each block publishes `nv` partial sums (thread 0's values) to
@@ -74,12 +97,69 @@ __device__ __forceinline__ bool last_block_arrive(unsigned* counter, bool* s_las
   return last;
 }
 
-// Fixed-order sum of part[0..m) by one block (strided per thread, then tree).
-template <int NT>
-__device__ __forceinline__ double reduce_partials(const double* part, int m, double* sh) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < m; i += NT) s += __ldcg(part + i);
-  return block_sum<NT>(s, sh);
+// Fixed-order sums of NV partial arrays part[j*stride + 0..m) by one block
+// (strided per thread, then block_sums).
+template <int NT, int NV, int M>
+__device__ __forceinline__ void reduce_partials(const double* part, int stride, int m,
+                                                double (&out)[NV], double (&sh)[M]) {
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < m; i += NT) s += __ldcg(part + j * stride + i);
+    out[j] = s;
+  }
+  block_sums<NT, NV>(out, sh);
+}
+
+// ------------------------------------------------------------------------
+// One row's sum  sum_k val[k] x[col[k]]  over k in [a, e), with the gathers
+// batched: the column indices of up to 8 entries are read first, then all 8
+// x loads are issued back to back, then the FMAs run in entry order (the same
+// sequential sum as one entry at a time, so the bits do not change).  A row
+// therefore waits for one gather latency per 8 entries instead of one per
+// entry.  col_at(k) / val_at(k) read entry k (shared or global memory).
+// ------------------------------------------------------------------------
+constexpr int kGatherBatch = 8;
+
+template <class ColAt, class ValAt>
+__device__ __forceinline__ double row_sum_batched(int a, int e, ColAt&& col_at, ValAt&& val_at,
+                                                  const double* __restrict__ x) {
+  double acc = 0.0;
+  int k0 = a;
+  for (; k0 + kGatherBatch <= e; k0 += kGatherBatch) {
+    int c[kGatherBatch];
+    double v[kGatherBatch], xv[kGatherBatch];
+#pragma unroll
+    for (int j = 0; j < kGatherBatch; ++j) {
+      c[j] = col_at(k0 + j);
+      v[j] = val_at(k0 + j);
+    }
+#pragma unroll
+    for (int j = 0; j < kGatherBatch; ++j) xv[j] = __ldg(x + c[j]);
+#pragma unroll
+    for (int j = 0; j < kGatherBatch; ++j) acc = fma(v[j], xv[j], acc);
+  }
+  const int rem = e - k0;
+  if (rem > 0) {
+    int c[kGatherBatch];
+    double v[kGatherBatch], xv[kGatherBatch];
+#pragma unroll
+    for (int j = 0; j < kGatherBatch; ++j)
+      if (j < rem) {
+        c[j] = col_at(k0 + j);
+        v[j] = val_at(k0 + j);
+      }
+#pragma unroll
+    for (int j = 0; j < kGatherBatch; ++j)
+      if (j < rem) xv[j] = __ldg(x + c[j]);
+    // explicit exit: the FP64 pipe must not see the padding lanes
+#pragma unroll
+    for (int j = 0; j < kGatherBatch; ++j) {
+      if (j >= rem) break;
+      acc = fma(v[j], xv[j], acc);
+    }
+  }
+  return acc;
 }
 
 // ------------------------------------------------------------------------
@@ -101,9 +181,7 @@ constexpr int kTileThreads = kTileRows;
 struct TileSmem {
   int rp[kTileRows + 1];
   int col[kTileCap];
-  double val[kTileCap];
-  double red[kTileThreads / kWarp];
-  int cnt;
+  double val[kTileCap];   // doubles as reduction scratch between tiles
 };
 
 // Calls epi(row, y_row) once for every row of the tile, from exactly one
@@ -131,7 +209,7 @@ __device__ __forceinline__ void spmv_tile(int tile, int n, const int* __restrict
       double s = 0.0;
       for (int k = base + tid; k < e; k += kTileThreads)
         s = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
-      s = block_sum<kTileThreads>(s, sm.red);
+      s = block_sum<kTileThreads>(s, sm.val);
       if (tid == 0) epi(r0 + a, s);
       __syncthreads();
       a += 1;
@@ -162,14 +240,39 @@ __device__ __forceinline__ void spmv_tile(int tile, int n, const int* __restrict
     const int row = a + tid;
     if (row < b) {
       const int s0 = sm.rp[row] - base, s1 = sm.rp[row + 1] - base;
-      double s = 0.0;
-      for (int k = s0; k < s1; ++k) s = fma(sm.val[k], __ldg(x + sm.col[k]), s);
+      const double s = row_sum_batched(
+          s0, s1, [&](int k) { return sm.col[k]; }, [&](int k) { return sm.val[k]; }, x);
       epi(r0 + row, s);
     }
     __syncthreads();
     a = b;
   }
 }
+
+// Row i of A times v, summed sequentially from global memory.
+__device__ __forceinline__ double row_dot(const int* __restrict__ rowptr,
+                                          const int* __restrict__ col,
+                                          const double* __restrict__ val,
+                                          const double* __restrict__ v, int i) {
+  const int a = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
+  double s = 0.0;
+  for (int k = a; k < e; ++k) s = fma(__ldg(val + k), __ldg(v + __ldg(col + k)), s);
+  return s;
+}
+
+// Host helpers shared by the solvers (defined in sla_cg.cu).
+int occupancy(const void* fn, int threads, size_t smem = 0);
+cudaError_t add_kernel(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                       cudaGraphNode_t* out, const void* fn, int grid, int block, void** args,
+                       unsigned smem = 0);
+int write_info(sla_info* info, sla_info v, cudaStream_t s);
+int validate_solve_args(const sla_csr* A, const double* val, const double* b, const double* x,
+                        const sla_opts* o, const sla_info* info, const void* ws, size_t ws_bytes,
+                        size_t need);
+
+// SpMV kernel family chosen once per process: the TMA-pipelined tiles
+// (default) or the register-staged tiles (environment SLA_SPMV_KERNEL=tile).
+bool use_tma_spmv();
 
 // Grid size for a kernel that loops over `units` work items, `per_sm`
 // resident blocks per SM, capped at `cap`.

@@ -1,0 +1,220 @@
+// sla_tma.cuh -- TMA-pipelined CSR row tiles (sm_100+ bulk copies).
+//
+// A persistent block owns tiles blockIdx.x, blockIdx.x + G, ...  One producer
+// warp streams each 256-row tile's row pointers, column indices and values
+// from HBM into a ring of kStages shared-memory stages with cp.async.bulk
+// (the 1-D TMA path), completing on an mbarrier with a byte count.  Eight
+// consumer warps then sum one row per thread from shared memory (one FP64
+// FMA per entry, no shuffles) and release the stage on a second mbarrier.
+// The producer runs up to kStages tiles ahead, so ~90 KB per block are in
+// flight without registers or extra threads.
+//
+// Bulk copies need 16-byte aligned addresses and sizes: the copied entry
+// range is widened down/up to multiples of 4 (int32) / 2 (float64) entries
+// but never past the end of the arrays; entries outside the copied window
+// (the array tail) and tiles that do not fit a stage (too many entries, the
+// last partial tile, or misaligned base pointers) are read from global
+// memory directly, one warp per row.
+//
+// Every mbarrier wait is bounded by a clock64 budget (about 2 s at the
+// highest clock); a wait that runs out sets *err and the warp leaves its
+// loop, so the kernel always terminates.
+#pragma once
+
+#include "sla_internal.cuh"
+
+namespace sla {
+namespace tma {
+
+constexpr int kRows = 256;                  // rows per tile == consumer threads
+constexpr int kCap = 2048;                  // entries per stage
+constexpr int kStages = 4;
+constexpr int kConsumerWarps = kRows / kWarp;
+constexpr int kThreads = kRows + kWarp;     // + one producer warp
+constexpr long long kWaitBudgetCycles = 4000000000LL;
+
+struct Stage {
+  int rp[kRows];             // rowptr[r0 .. r0 + 256)
+  int col[kCap + 8];         // entries [ka_c, kb_c)
+  double val[kCap + 4];      // entries [ka_v, kb_v)
+  int hdr[8];                // mode, k1, ka_c, kb_c, ka_v, kb_v, r0, nr
+};
+
+struct Smem {
+  Stage st[kStages];
+  unsigned long long full[kStages];
+  unsigned long long empty[kStages];
+  double red[2 * kThreads + 2];  // block_sums of up to two values
+  bool last;
+};
+
+constexpr size_t kSmemBytes = sizeof(Smem);
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false (and *err set) if
+// the budget ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitBudgetCycles) {
+      atomicOr(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Row `row` of the matrix from global memory by one warp (lane-strided
+// entries, fixed butterfly); result valid in every lane.
+__device__ __forceinline__ double warp_row(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                           const double* __restrict__ val,
+                                           const double* __restrict__ x, int row, int lane) {
+  const int a = __ldg(rowptr + row), e = __ldg(rowptr + row + 1);
+  double s = 0.0;
+  for (int k = a + lane; k < e; k += kWarp) s = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
+  return warp_sum(s);
+}
+
+// Runs the pipelined tile loop over all rows; calls epi(row, y_row, aux_row)
+// once per row from exactly one consumer thread, where aux_row = aux[row]
+// (prefetched before the row's gathers; 0 when aux is null).  Must be called by all kThreads
+// threads of the block, with `sm` in dynamic shared memory.  The producer
+// warp returns from this function as soon as it has issued its last tile;
+// nothing after the call may rely on its values.
+template <class Epi>
+__device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restrict__ rowptr,
+                                              const int* __restrict__ col,
+                                              const double* __restrict__ val,
+                                              const double* __restrict__ x,
+                                              const double* __restrict__ aux, Smem& sm, int* err,
+                                              Epi&& epi) {
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int ntiles = (n + kRows - 1) / kRows;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(rowptr) | reinterpret_cast<uintptr_t>(col) |
+                         reinterpret_cast<uintptr_t>(val)) & 15u) == 0;
+  if (warp == kConsumerWarps) {
+    // ---------------- producer warp (lane 0 issues)
+    if (lane == 0) {
+      const int nnz_c = nnz & ~3, nnz_v = nnz & ~1;
+      int k = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+        const int s = k % kStages;
+        const unsigned round = (unsigned)(k / kStages);
+        if (!mbar_wait(&sm.empty[s], (round & 1u) ^ 1u, err)) break;
+        Stage& S = sm.st[s];
+        const int r0 = t * kRows;
+        const int nr = min(kRows, n - r0);
+        const int k0 = __ldg(rowptr + r0);
+        const int k1 = __ldg(rowptr + r0 + nr);
+        int mode = 1;
+        int ka_c = 0, kb_c = 0, ka_v = 0, kb_v = 0;
+        if (aligned && nr == kRows && k1 - k0 <= kCap) {
+          mode = 0;
+          ka_c = k0 & ~3;
+          kb_c = min((k1 + 3) & ~3, nnz_c);
+          if (kb_c < ka_c) kb_c = ka_c;
+          ka_v = k0 & ~1;
+          kb_v = min((k1 + 1) & ~1, nnz_v);
+          if (kb_v < ka_v) kb_v = ka_v;
+        }
+        S.hdr[0] = mode;
+        S.hdr[1] = k1;
+        S.hdr[2] = ka_c;
+        S.hdr[3] = kb_c;
+        S.hdr[4] = ka_v;
+        S.hdr[5] = kb_v;
+        S.hdr[6] = r0;
+        S.hdr[7] = nr;
+        if (mode == 0) {
+          const unsigned bc = (unsigned)(kb_c - ka_c) * 4u, bv = (unsigned)(kb_v - ka_v) * 8u;
+          mbar_arrive_expect_tx(&sm.full[s], (unsigned)(kRows * 4) + bc + bv);
+          bulk_g2s(S.rp, rowptr + r0, kRows * 4, &sm.full[s]);
+          if (bc) bulk_g2s(S.col, col + ka_c, bc, &sm.full[s]);
+          if (bv) bulk_g2s(S.val, val + ka_v, bv, &sm.full[s]);
+        } else {
+          mbar_arrive(&sm.full[s]);
+        }
+      }
+    }
+    __syncwarp();
+    return;
+  }
+  // ---------------- consumer warps
+  int k = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    const int s = k % kStages;
+    const unsigned round = (unsigned)(k / kStages);
+    if (!mbar_wait(&sm.full[s], round & 1u, err)) break;
+    const Stage& S = sm.st[s];
+    const int mode = S.hdr[0];
+    const int r0 = S.hdr[6], nr = S.hdr[7];
+    if (mode == 0) {
+      const int k1 = S.hdr[1], ka_c = S.hdr[2], kb_c = S.hdr[3], ka_v = S.hdr[4], kb_v = S.hdr[5];
+      const double av = aux ? __ldg(aux + r0 + tid) : 0.0;
+      const int a = S.rp[tid];
+      const int e = (tid + 1 < kRows) ? S.rp[tid + 1] : k1;
+      const double acc = row_sum_batched(
+          a, e, [&](int kk) { return kk < kb_c ? S.col[kk - ka_c] : __ldg(col + kk); },
+          [&](int kk) { return kk < kb_v ? S.val[kk - ka_v] : __ldg(val + kk); }, x);
+      epi(r0 + tid, acc, av);
+    } else {
+      for (int rr = warp; rr < nr; rr += kConsumerWarps) {
+        const double acc = warp_row(rowptr, col, val, x, r0 + rr, lane);
+        if (lane == 0) epi(r0 + rr, acc, aux ? __ldg(aux + r0 + rr) : 0.0);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sm.empty[s]);
+  }
+}
+
+}  // namespace tma
+}  // namespace sla

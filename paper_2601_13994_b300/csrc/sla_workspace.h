@@ -44,7 +44,7 @@ struct KrylovDesc {
 struct KrylovState {
   double rho, pq, rr, bnorm, thresh, alpha, beta, omega;
   double rho_prev, tt, ts, ss;
-  int iters, status, phase, restarts, body, zero_rhs, bad_diag, pad;
+  int iters, status, phase, restarts, body, zero_rhs, bad_diag, err;
   unsigned cnt[8];
 };
 
@@ -70,12 +70,32 @@ constexpr CgLayout cg_layout(int n) {
   return L;
 }
 
+// BiCGStab: descriptor, state, partials, then r, r^, p, p^, v, s, s^, t, dinv.
+struct BiLayout {
+  size_t desc, state, part, vec, vec_stride, total;
+};
+
+constexpr BiLayout bicg_layout(int n) {
+  BiLayout L{};
+  size_t o = 0;
+  L.vec_stride = al256(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  L.desc = o;  o += al256(sizeof(KrylovDesc));
+  L.state = o; o += al256(sizeof(KrylovState));
+  L.part = o;  o += al256(sizeof(double) * kMaxBlocks * kPartSlots);
+  L.vec = o;   o += 9 * L.vec_stride;
+  L.total = o;
+  return L;
+}
+
 inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
   (void)nnz;
   (void)batch;
   switch (kind) {
     case SLA_WS_CG:
       *out = cg_layout(n).total;
+      return true;
+    case SLA_WS_BICGSTAB:
+      *out = bicg_layout(n).total;
       return true;
     default:
       return false;

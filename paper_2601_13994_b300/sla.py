@@ -16,7 +16,7 @@ import torch
 
 from . import _lib as L
 
-__all__ = ["CSRMatrix", "SolveInfo", "spmv", "cg", "default_max_iter"]
+__all__ = ["CSRMatrix", "SolveInfo", "spmv", "cg", "bicgstab", "default_max_iter"]
 
 
 def _stream_ptr(device: torch.device) -> int:
@@ -176,13 +176,8 @@ def _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, n, graph=True):
                      0 if graph else L.SLA_FLAG_HOST_LOOP)
 
 
-def cg(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10, atol: float = 0.0,
-       max_iter: int | None = None, precond: str = "jacobi", x0: torch.Tensor | None = None,
-       max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True):
-    """Preconditioned CG for SPD A (Algorithm 1, one process).  Returns
-    (x, SolveInfo).  With ``graph=True`` the solve is one graph launch and
-    nothing synchronises until the info is read; ``graph=False`` launches the
-    same kernels from a host loop (synchronising the stream)."""
+def _krylov(fn_name: str, ws_kind: int, A: CSRMatrix, val, b, rtol, atol, max_iter, precond, x0,
+            max_restarts, out, graph):
     _need(val, torch.float64, A.device, "val", A.nnz)
     _need(b, torch.float64, A.device, "b", A.n)
     if out is None:
@@ -198,7 +193,27 @@ def cg(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10,
         use_x0 = 1
     info = torch.empty((1, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
     o = _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, A.n, graph)
-    ws = workspace(L.SLA_WS_CG, A.n, A.nnz, 1, A.device)
-    L.check("sla_cg", L.lib().sla_cg(ctypes.byref(A.c), _ptr(val), _ptr(b), _ptr(x), ctypes.byref(o),
-                                    info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(A.device)))
+    ws = workspace(ws_kind, A.n, A.nnz, 1, A.device)
+    fn = getattr(L.lib(), fn_name)
+    L.check(fn_name, fn(ctypes.byref(A.c), _ptr(val), _ptr(b), _ptr(x), ctypes.byref(o), info.data_ptr(),
+                        ws.data_ptr(), ws.numel(), _stream_ptr(A.device)))
     return x, SolveInfo(info)
+
+
+def bicgstab(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10, atol: float = 0.0,
+             max_iter: int | None = None, precond: str = "jacobi", x0: torch.Tensor | None = None,
+             max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True):
+    """Right-preconditioned BiCGStab for nonsymmetric A.  Returns (x, SolveInfo)."""
+    return _krylov("sla_bicgstab", L.SLA_WS_BICGSTAB, A, val, b, rtol, atol, max_iter, precond, x0,
+                   max_restarts, out, graph)
+
+
+def cg(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10, atol: float = 0.0,
+       max_iter: int | None = None, precond: str = "jacobi", x0: torch.Tensor | None = None,
+       max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True):
+    """Preconditioned CG for SPD A (Algorithm 1, one process).  Returns
+    (x, SolveInfo).  With ``graph=True`` the solve is one graph launch and
+    nothing synchronises until the info is read; ``graph=False`` launches the
+    same kernels from a host loop (synchronising the stream)."""
+    return _krylov("sla_cg", L.SLA_WS_CG, A, val, b, rtol, atol, max_iter, precond, x0, max_restarts, out,
+                   graph)
