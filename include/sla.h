@@ -62,6 +62,13 @@ extern "C" {
 /* Workspace kinds for sla_workspace_size(). */
 #define SLA_WS_CG 1
 #define SLA_WS_BICGSTAB 2
+#define SLA_WS_ADJOINT 3        /* sla_adjoint_backward                        */
+#define SLA_WS_TRANSPOSE 4      /* sla_csr_transpose                           */
+#define SLA_WS_COO 5            /* sla_coo_to_csr (pass the COO entry count as nnz) */
+
+/* Adjoint solve methods (sla_adjoint_backward). */
+#define SLA_ADJ_CG 0            /* A symmetric: A^T = A, CG on A               */
+#define SLA_ADJ_BICGSTAB 1      /* general A: BiCGStab on the CSR of A^T       */
 
 /* Pattern of a square CSR matrix (all pointers device). */
 typedef struct sla_csr {
@@ -70,6 +77,15 @@ typedef struct sla_csr {
   const int32_t* rowptr;  /* [n+1]                                           */
   const int32_t* col;     /* [nnz]                                           */
 } sla_csr;
+
+/* CSR of A^T, as produced by sla_csr_transpose (all pointers device):
+ * row j of A^T lists the entries of column j of A in increasing row order;
+ * perm_t[m] is the index into A's values of the m-th entry of A^T. */
+typedef struct sla_csr_t {
+  const int32_t* rowptr_t;  /* [n+1]                                         */
+  const int32_t* col_t;     /* [nnz]                                         */
+  const int32_t* perm_t;    /* [nnz]                                         */
+} sla_csr_t;
 
 /* Solver options (host struct, copied at call time). */
 typedef struct sla_opts {
@@ -170,6 +186,76 @@ int32_t sla_cg(const sla_csr* A, const double* val, const double* b,
 int32_t sla_bicgstab(const sla_csr* A, const double* val, const double* b,
                      double* x, const sla_opts* opts, sla_info* info,
                      void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Pattern utilities                                                     */
+/* ------------------------------------------------------------------ */
+
+/* CSR of A^T (needed by the adjoint A^T lambda = dL/dx of Eq. 3 when A is
+ * not symmetric).  Outputs: rowptrT [n+1], colT [nnz], permT [nnz] (device,
+ * caller-owned), with valT = val[permT].  Stable: within a row of A^T the
+ * entries keep increasing row of A, so the result is unique and matches a
+ * sequential counting sort bit for bit.  Workspace: SLA_WS_TRANSPOSE.
+ * Asynchronous on `stream`. */
+int32_t sla_csr_transpose(const sla_csr* A, int32_t* rowptrT, int32_t* colT,
+                          int32_t* permT, void* ws, size_t ws_bytes,
+                          void* stream);
+
+/* COO -> CSR ingest for SparseTensor(val, row, col, shape) (App. B).
+ * row, col: int64 [m] in [0, n), any order, duplicates allowed; val [m].
+ * Outputs (device, caller-owned, capacity m): rowptr [n+1], col_out,
+ * val_out (duplicates summed in increasing COO index), perm [m] with
+ * perm[e] = CSR slot of COO entry e.  Optional (may be NULL): order [m],
+ * the COO entries in (row, col, index) order, and segptr [m+1], where
+ * CSR slot s gathers order[segptr[s] .. segptr[s+1]) -- with
+ * sla_segment_sum they rebuild CSR values from new COO values on the same
+ * pattern.  *nnz_out (device int32) receives the CSR entry count, or -1 if
+ * some row/col is out of range (then the other outputs are unspecified).
+ * Workspace: SLA_WS_COO with nnz = m.  Asynchronous on `stream`. */
+int32_t sla_coo_to_csr(int32_t n, int64_t m, const int64_t* row,
+                       const int64_t* col, const double* val, int32_t* rowptr,
+                       int32_t* col_out, double* val_out, int32_t* perm,
+                       int32_t* order, int32_t* segptr, int32_t* nnz_out,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* out[s] = sum of val[idx[q]] for q in [segptr[s], segptr[s+1]), added in
+ * increasing q, for s < nseg (duplicates of a COO input summed in COO
+ * order, with idx/segptr from sla_coo_to_csr).  Device arrays. */
+int32_t sla_segment_sum(int32_t nseg, const int32_t* segptr,
+                        const int32_t* idx, const double* val, double* out,
+                        void* stream);
+
+/* out[k] = val[perm[k]] for k < nnz: the values of A^T in CSR-of-A^T order,
+ * or gradients mapped back to the caller's COO order (perm of
+ * sla_coo_to_csr).  Device arrays; asynchronous. */
+int32_t sla_gather_values(int64_t nnz, const int32_t* perm, const double* val,
+                          double* out, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Linear adjoint backward (Eq. 2-3)                                     */
+/* ------------------------------------------------------------------ */
+
+/* Matrix gradient of Eq. 3 on the pattern:
+ *   grad_val[k] = -lambda[i] * x[col[k]]   for every entry k of row i.
+ * lambda [n], x [n] -> grad_val [nnz]; one pass over the entries. */
+int32_t sla_grad_values(const sla_csr* A, const double* lambda,
+                        const double* x, double* grad_val, void* stream);
+
+/* Backward pass of x = A^{-1} b (Eq. 2 with J = A, Eq. 3): solves
+ * A^T lambda = grad_x, then writes grad_b = lambda [n] and
+ * grad_val[k] = -lambda[i] x[col[k]] [nnz].  x is the forward solution.
+ * method SLA_ADJ_CG: A symmetric (A^T = A), CG on A; AT may be NULL.
+ * method SLA_ADJ_BICGSTAB: BiCGStab on A^T given by AT (sla_csr_transpose
+ * of A); its values are gathered into the workspace.
+ * opts: tolerance of the adjoint solve relative to ||grad_x|| (use_x0 is
+ * ignored: lambda starts at 0); *info receives the adjoint solve's record.
+ * Workspace: SLA_WS_ADJOINT.  Asynchronous (graph launch + one kernel). */
+int32_t sla_adjoint_backward(const sla_csr* A, const sla_csr_t* AT,
+                             const double* val, const double* x,
+                             const double* grad_x, double* grad_b,
+                             double* grad_val, int32_t method,
+                             const sla_opts* opts, sla_info* info, void* ws,
+                             size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Allocation-free CG (no counterpart in the paper)                      */

@@ -29,6 +29,12 @@ SLA_FLAG_HOST_LOOP = 1
 
 SLA_WS_CG = 1
 SLA_WS_BICGSTAB = 2
+SLA_WS_ADJOINT = 3
+SLA_WS_TRANSPOSE = 4
+SLA_WS_COO = 5
+
+SLA_ADJ_CG = 0
+SLA_ADJ_BICGSTAB = 1
 
 SLA_NOALLOC_MAX_N = 393216
 
@@ -41,6 +47,10 @@ INFO_BYTES = 24  # sla_info: int32 iters, int32 status, double rel_res, double t
 class SlaCsr(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32),
                 ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p)]
+
+
+class SlaCsrT(ctypes.Structure):
+    _fields_ = [("rowptr_t", ctypes.c_void_p), ("col_t", ctypes.c_void_p), ("perm_t", ctypes.c_void_p)]
 
 
 class SlaOpts(ctypes.Structure):
@@ -87,6 +97,20 @@ def lib() -> ctypes.CDLL:
             L.sla_bicgstab.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, ctypes.POINTER(SlaOpts), P, P,
                                        ctypes.c_size_t, P]
             L.sla_bicgstab.restype = i32
+            i64 = ctypes.c_int64
+            L.sla_csr_transpose.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, P, ctypes.c_size_t, P]
+            L.sla_csr_transpose.restype = i32
+            L.sla_coo_to_csr.argtypes = [i32, i64, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_size_t, P]
+            L.sla_coo_to_csr.restype = i32
+            L.sla_segment_sum.argtypes = [i32, P, P, P, P, P]
+            L.sla_segment_sum.restype = i32
+            L.sla_gather_values.argtypes = [i64, P, P, P, P]
+            L.sla_gather_values.restype = i32
+            L.sla_grad_values.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, P]
+            L.sla_grad_values.restype = i32
+            L.sla_adjoint_backward.argtypes = [ctypes.POINTER(SlaCsr), ctypes.POINTER(SlaCsrT), P, P, P, P,
+                                               P, i32, ctypes.POINTER(SlaOpts), P, P, ctypes.c_size_t, P]
+            L.sla_adjoint_backward.restype = i32
             L.sla_cg_noalloc.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, ctypes.POINTER(SlaOpts), P, P]
             L.sla_cg_noalloc.restype = i32
             _lib = L

@@ -87,6 +87,17 @@ constexpr BiLayout bicg_layout(int n) {
   return L;
 }
 
+// Pattern utilities (sla_pattern.cu).
+size_t transpose_ws_bytes(int n, int nnz);
+size_t coo_ws_bytes(int n, long long m);
+
+// Adjoint: the larger of the CG scratch and BiCGStab scratch + valT.
+inline size_t adjoint_ws_bytes(int n, int nnz) {
+  const size_t a = cg_layout(n).total;
+  const size_t b = al256(bicg_layout(n).total) + al256(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  return a > b ? a : b;
+}
+
 inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
   (void)nnz;
   (void)batch;
@@ -96,6 +107,15 @@ inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
       return true;
     case SLA_WS_BICGSTAB:
       *out = bicg_layout(n).total;
+      return true;
+    case SLA_WS_ADJOINT:
+      *out = adjoint_ws_bytes(n, nnz);
+      return true;
+    case SLA_WS_TRANSPOSE:
+      *out = transpose_ws_bytes(n, nnz);
+      return true;
+    case SLA_WS_COO:
+      *out = coo_ws_bytes(n, nnz);
       return true;
     default:
       return false;

@@ -16,7 +16,8 @@ import torch
 
 from . import _lib as L
 
-__all__ = ["CSRMatrix", "SolveInfo", "spmv", "cg", "bicgstab", "default_max_iter"]
+__all__ = ["CSRMatrix", "SparseTensor", "SolveInfo", "spmv", "cg", "bicgstab", "solve", "adjoint_backward",
+           "grad_values", "csr_transpose", "coo_to_csr", "segment_sum", "gather_values", "default_max_iter"]
 
 
 def _stream_ptr(device: torch.device) -> int:
@@ -217,3 +218,212 @@ def cg(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10,
     same kernels from a host loop (synchronising the stream)."""
     return _krylov("sla_cg", L.SLA_WS_CG, A, val, b, rtol, atol, max_iter, precond, x0, max_restarts, out,
                    graph)
+
+
+# ---------------------------------------------------------------------------
+# Pattern utilities
+# ---------------------------------------------------------------------------
+
+def _scratch(kind: int, n: int, nnz: int, device: torch.device) -> torch.Tensor:
+    nbytes = L.workspace_size(kind, n, nnz, 1)
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def csr_transpose(A: CSRMatrix):
+    """CSR of A^T: (rowptrT, colT, permT) with valT = val[permT] (stable)."""
+    dev = A.device
+    rpT = torch.empty(A.n + 1, dtype=torch.int32, device=dev)
+    cT = torch.empty(max(A.nnz, 1), dtype=torch.int32, device=dev)
+    pT = torch.empty(max(A.nnz, 1), dtype=torch.int32, device=dev)
+    ws = _scratch(L.SLA_WS_TRANSPOSE, A.n, A.nnz, dev)
+    L.check("sla_csr_transpose", L.lib().sla_csr_transpose(ctypes.byref(A.c), rpT.data_ptr(), cT.data_ptr(),
+                                                          pT.data_ptr(), ws.data_ptr(), ws.numel(),
+                                                          _stream_ptr(dev)))
+    return rpT, cT[:A.nnz], pT[:A.nnz]
+
+
+def transpose_of(A: CSRMatrix):
+    """Cached CSR of A^T for a pattern (computed on first use)."""
+    t = getattr(A, "_transpose", None)
+    if t is None:
+        t = csr_transpose(A)
+        A._transpose = t
+        A._transpose_c = L.SlaCsrT(t[0].data_ptr(), t[1].data_ptr() if A.nnz else None,
+                                   t[2].data_ptr() if A.nnz else None)
+    return t
+
+
+def gather_values(perm: torch.Tensor, val: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """out[k] = val[perm[k]]."""
+    m = perm.numel()
+    out = torch.empty(m, dtype=torch.float64, device=val.device) if out is None else out
+    L.check("sla_gather_values", L.lib().sla_gather_values(m, perm.data_ptr(), val.data_ptr(),
+                                                          out.data_ptr(), _stream_ptr(val.device)))
+    return out
+
+
+def coo_to_csr(n: int, row: torch.Tensor, col: torch.Tensor, val: torch.Tensor | None = None):
+    """COO (int64 row/col, any order, duplicates) -> CSR pattern on the device.
+
+    Returns (CSRMatrix, val_csr or None, perm, order, segptr): perm[e] is the
+    CSR slot of COO entry e; (order, segptr) rebuild CSR values from new COO
+    values with ``segment_sum``."""
+    dev = row.device
+    m = row.numel()
+    row = row.to(torch.int64).contiguous()
+    col = col.to(torch.int64).contiguous()
+    v = torch.zeros(m, dtype=torch.float64, device=dev) if val is None else val.detach().contiguous()
+    rowptr = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    col_out = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    val_out = torch.empty(max(m, 1), dtype=torch.float64, device=dev)
+    perm = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    order = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    segptr = torch.empty(m + 1, dtype=torch.int32, device=dev)
+    nnz_out = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = _scratch(L.SLA_WS_COO, n, m, dev)
+    L.check("sla_coo_to_csr", L.lib().sla_coo_to_csr(
+        n, m, row.data_ptr(), col.data_ptr(), v.data_ptr(), rowptr.data_ptr(), col_out.data_ptr(),
+        val_out.data_ptr(), perm.data_ptr(), order.data_ptr(), segptr.data_ptr(), nnz_out.data_ptr(),
+        ws.data_ptr(), ws.numel(), _stream_ptr(dev)))
+    nnz = int(nnz_out.item())
+    if nnz < 0:
+        raise ValueError("COO row/col index out of range [0, %d)" % n)
+    A = CSRMatrix(rowptr, col_out[:nnz].clone(), check=False)
+    return (A, None if val is None else val_out[:nnz].clone(), perm[:m], order[:m], segptr[:nnz + 1])
+
+
+def segment_sum(segptr: torch.Tensor, idx: torch.Tensor, val: torch.Tensor) -> torch.Tensor:
+    nseg = segptr.numel() - 1
+    out = torch.empty(nseg, dtype=torch.float64, device=val.device)
+    L.check("sla_segment_sum", L.lib().sla_segment_sum(nseg, segptr.data_ptr(), idx.data_ptr(),
+                                                      val.data_ptr(), out.data_ptr(),
+                                                      _stream_ptr(val.device)))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Adjoint (Eq. 2-3) and the autograd bridge (Sec. 3.1, "Bridging backends")
+# ---------------------------------------------------------------------------
+
+def grad_values(A: CSRMatrix, lam: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+    """grad_val[k] = -lam[row(k)] * x[col(k)] (Eq. 3)."""
+    g = torch.empty(A.nnz, dtype=torch.float64, device=A.device)
+    L.check("sla_grad_values", L.lib().sla_grad_values(ctypes.byref(A.c), lam.data_ptr(), x.data_ptr(),
+                                                      g.data_ptr(), _stream_ptr(A.device)))
+    return g
+
+
+_ADJ = {"cg": L.SLA_ADJ_CG, "bicgstab": L.SLA_ADJ_BICGSTAB}
+
+
+def adjoint_backward(A: CSRMatrix, val: torch.Tensor, x: torch.Tensor, grad_x: torch.Tensor, *,
+                     method: str = "cg", rtol: float = 1e-10, atol: float = 0.0,
+                     max_iter: int | None = None, precond: str = "jacobi", max_restarts: int = 2,
+                     graph: bool = True):
+    """Solve A^T lambda = grad_x; returns (grad_b = lambda, grad_val, SolveInfo)."""
+    _need(val, torch.float64, A.device, "val", A.nnz)
+    _need(x, torch.float64, A.device, "x", A.n)
+    _need(grad_x, torch.float64, A.device, "grad_x", A.n)
+    gb = torch.empty(A.n, dtype=torch.float64, device=A.device)
+    gv = torch.empty(A.nnz, dtype=torch.float64, device=A.device)
+    info = torch.empty((1, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
+    o = _opts(rtol, atol, max_iter, max_restarts, precond, 0, A.n, graph)
+    atp = None
+    if method == "bicgstab":
+        transpose_of(A)
+        atp = ctypes.byref(A._transpose_c)
+    ws = workspace(L.SLA_WS_ADJOINT, A.n, A.nnz, 1, A.device)
+    L.check("sla_adjoint_backward", L.lib().sla_adjoint_backward(
+        ctypes.byref(A.c), atp, val.data_ptr(), x.data_ptr(), grad_x.data_ptr(), gb.data_ptr(),
+        gv.data_ptr(), _ADJ[method], ctypes.byref(o), info.data_ptr(), ws.data_ptr(), ws.numel(),
+        _stream_ptr(A.device)))
+    return gb, gv, SolveInfo(info)
+
+
+class SolveError(RuntimeError):
+    pass
+
+
+def _check_info(info: SolveInfo, what: str, strict: bool):
+    if info.status != L.SLA_OK:
+        msg = "%s: %s after %d iterations (rel_res %.3e)" % (what, info.status_name, info.iters, info.rel_res)
+        if strict:
+            raise SolveError(msg)
+        import warnings
+        warnings.warn(msg)
+
+
+class SparseSolve(torch.autograd.Function):
+    """x = A^{-1} b with the adjoint backward: forward runs the Krylov solve
+    without recording anything, backward is one adjoint solve plus one
+    O(nnz) pass, so the autograd graph holds one node whatever the iteration
+    count (Sec. 3.1-3.2, Tab. 2)."""
+
+    @staticmethod
+    def forward(ctx, val, b, A, method, kw, strict):
+        fn = cg if method == "cg" else bicgstab
+        x, info = fn(A, val.detach(), b.detach(), **kw)
+        if strict is not None:
+            _check_info(info, "forward " + method, strict)
+        ctx.save_for_backward(val, x)
+        ctx.A, ctx.method, ctx.kw, ctx.strict = A, method, kw, strict
+        ctx.info = info
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        val, x = ctx.saved_tensors
+        kw = {k: v for k, v in ctx.kw.items() if k not in ("x0", "out")}
+        gb, gv, info = adjoint_backward(ctx.A, val.detach(), x, gx.contiguous().to(torch.float64),
+                                        method=ctx.method, **kw)
+        if ctx.strict is not None:
+            _check_info(info, "adjoint " + ctx.method, ctx.strict)
+        return gv, gb, None, None, None, None
+
+
+def solve(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, method: str = "cg", strict: bool | None = True,
+          **kw) -> torch.Tensor:
+    """Differentiable x = A^{-1} b w.r.t. val (CSR order) and b.  method:
+    "cg" (SPD A; the adjoint reuses A since A^T = A) or "bicgstab" (the
+    adjoint runs on the cached CSR of A^T).  strict=True raises on a failed
+    solve, False warns, None skips the check (no host synchronisation)."""
+    if method not in _ADJ:
+        raise ValueError("method must be 'cg' or 'bicgstab'")
+    return SparseSolve.apply(val, b, A, method, kw, strict)
+
+
+class _CooValues(torch.autograd.Function):
+    """COO values -> CSR values on a fixed pattern (duplicates summed in COO
+    order); backward gathers the CSR gradient back to every COO entry."""
+
+    @staticmethod
+    def forward(ctx, val, segptr, order, perm):
+        ctx.perm = perm
+        return segment_sum(segptr, order, val.detach().contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        return gather_values(ctx.perm, g.contiguous()), None, None, None
+
+
+class SparseTensor:
+    """The paper's SparseTensor(val, row, col, shape) (App. B) on one CUDA
+    device: COO input (any order, duplicates summed), a CSR pattern built
+    once, and differentiable ``solve`` / ``matvec``."""
+
+    def __init__(self, val: torch.Tensor, row: torch.Tensor, col: torch.Tensor, shape):
+        n, n2 = int(shape[-2]), int(shape[-1])
+        if n != n2:
+            raise ValueError("square matrices only")
+        self.val = val
+        self.shape = (n, n)
+        self.A, _, self.perm, self.order, self.segptr = coo_to_csr(n, row, col)
+
+    def csr_values(self) -> torch.Tensor:
+        return _CooValues.apply(self.val, self.segptr, self.order, self.perm)
+
+    def solve(self, b: torch.Tensor, method: str = "cg", **kw) -> torch.Tensor:
+        return solve(self.A, self.csr_values(), b, method=method, **kw)
+
+    def matvec(self, x: torch.Tensor) -> torch.Tensor:
+        return spmv(self.A, self.csr_values().detach(), x.contiguous())
