@@ -65,6 +65,8 @@ extern "C" {
 #define SLA_WS_ADJOINT 3        /* sla_adjoint_backward                        */
 #define SLA_WS_TRANSPOSE 4      /* sla_csr_transpose                           */
 #define SLA_WS_COO 5            /* sla_coo_to_csr (pass the COO entry count as nnz) */
+#define SLA_WS_BATCHED 6        /* batched CG: n = rows per system (shared
+                                   pattern) or total rows with batch = 1 (list) */
 
 /* Adjoint solve methods (sla_adjoint_backward). */
 #define SLA_ADJ_CG 0            /* A symmetric: A^T = A, CG on A               */
@@ -256,6 +258,56 @@ int32_t sla_adjoint_backward(const sla_csr* A, const sla_csr_t* AT,
                              double* grad_val, int32_t method,
                              const sla_opts* opts, sla_info* info, void* ws,
                              size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Batched Jacobi-PCG in one persistent launch (SparseTensor batch with a  */
+/* shared pattern, SparseTensorList with distinct patterns; Sec. 3.1)     */
+/* ------------------------------------------------------------------ */
+
+/* Each system is solved by one CTA running the complete PCG recurrence of
+ * sla_cg (same stopping rule, restart and statuses; info[s] per system);
+ * persistent CTAs take systems from a counter, so one launch serves any
+ * batch and a converged system frees its CTA for the next.  The Krylov
+ * vectors stay in shared memory when 5 n doubles fit, else in the
+ * workspace.  config: 0 = automatic; low 4 bits 1/2/3 = 256/512/1024
+ * threads per CTA, bit 4 set = vectors in global memory (the autotuner in
+ * the Python layer times these).  The call only enqueues kernels (no host
+ * synchronisation), so it can be captured in a CUDA graph.
+ * Shared pattern: val [batch, nnz], b and x [batch, n] row-major.
+ * Workspace: SLA_WS_BATCHED with (n, batch). */
+int32_t sla_cg_batched_shared(const sla_csr* A, int32_t batch,
+                              const double* val, const double* b, double* x,
+                              const sla_opts* opts, sla_info* info,
+                              int32_t config, void* ws, size_t ws_bytes,
+                              void* stream);
+
+/* Distinct patterns, concatenated: n_off, nnz_off [batch+1] (device) give
+ * system s rows [n_off[s], n_off[s+1]) of b and x and entries
+ * [nnz_off[s], nnz_off[s+1]) of col and val; rowptr holds the per-system
+ * row pointers (each starting at 0, n_s + 1 entries) back to back, so system
+ * s's start at rowptr + n_off[s] + s; columns are local.  n_max = largest
+ * n_s, total_rows = n_off[batch].  order (device, optional): the order in
+ * which CTAs take systems (largest first balances the load).
+ * Workspace: SLA_WS_BATCHED with (total_rows, 1). */
+int32_t sla_cg_batched_list(int32_t batch, int32_t n_max, int32_t total_rows,
+                            const int32_t* n_off, const int32_t* nnz_off,
+                            const int32_t* rowptr, const int32_t* col,
+                            const double* val, const double* b, double* x,
+                            const int32_t* order, const sla_opts* opts,
+                            sla_info* info, int32_t config, void* ws,
+                            size_t ws_bytes, void* stream);
+
+/* Batched Eq. 3 gradient: grad_val[s, k] = -lambda[s, i] x[s, col k] for the
+ * entries k of row i of system s.  shared_pattern = 1: (n, nnz, rowptr,
+ * col) is the pattern, lambda/x [batch, n], grad_val [batch, nnz];
+ * shared_pattern = 0: the concatenated layout of sla_cg_batched_list with
+ * n = n_max. */
+int32_t sla_grad_values_batched(int32_t batch, int32_t shared_pattern,
+                                int32_t n, int32_t nnz, const int32_t* rowptr,
+                                const int32_t* col, const int32_t* n_off,
+                                const int32_t* nnz_off, const double* lambda,
+                                const double* x, double* grad_val,
+                                void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Allocation-free CG (no counterpart in the paper)                      */

@@ -32,6 +32,7 @@ SLA_WS_BICGSTAB = 2
 SLA_WS_ADJOINT = 3
 SLA_WS_TRANSPOSE = 4
 SLA_WS_COO = 5
+SLA_WS_BATCHED = 6
 
 SLA_ADJ_CG = 0
 SLA_ADJ_BICGSTAB = 1
@@ -111,6 +112,14 @@ def lib() -> ctypes.CDLL:
             L.sla_adjoint_backward.argtypes = [ctypes.POINTER(SlaCsr), ctypes.POINTER(SlaCsrT), P, P, P, P,
                                                P, i32, ctypes.POINTER(SlaOpts), P, P, ctypes.c_size_t, P]
             L.sla_adjoint_backward.restype = i32
+            L.sla_cg_batched_shared.argtypes = [ctypes.POINTER(SlaCsr), i32, P, P, P, ctypes.POINTER(SlaOpts), P,
+                                                i32, P, ctypes.c_size_t, P]
+            L.sla_cg_batched_shared.restype = i32
+            L.sla_cg_batched_list.argtypes = [i32, i32, i32, P, P, P, P, P, P, P, P, ctypes.POINTER(SlaOpts), P,
+                                              i32, P, ctypes.c_size_t, P]
+            L.sla_cg_batched_list.restype = i32
+            L.sla_grad_values_batched.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, P]
+            L.sla_grad_values_batched.restype = i32
             L.sla_cg_noalloc.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, ctypes.POINTER(SlaOpts), P, P]
             L.sla_cg_noalloc.restype = i32
             _lib = L

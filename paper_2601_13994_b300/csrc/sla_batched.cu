@@ -1,0 +1,403 @@
+// sla_batched.cu -- many Jacobi-PCG solves in one persistent launch.
+//
+// The paper's SparseTensor holds a batch on one shared pattern and
+// SparseTensorList a batch of distinct patterns (Sec. 3.1); both dispatch
+// solves per element.  Here a whole batch is one kernel launch: persistent
+// CTAs take systems from an atomic counter (largest first when an order is
+// given) and each CTA runs the complete PCG recurrence of its system --
+// Algorithm 1 with P = 1 and the Jacobi preconditioner, the same stopping
+// rule, true-residual restart and statuses as the single-system solver --
+// with block-level reductions only.  A system's convergence ends only its
+// own CTA's loop, which is the per-system convergence mask.  No block ever
+// waits for another, so the launch always terminates.
+//
+// On this part a batched small system is FP64-bound, not memory-bound: with
+// the Krylov vectors in shared memory (when 5 n doubles fit; otherwise in a
+// per-CTA global slot) an iteration reads only the values and the pattern.
+#include <cmath>
+
+#include "sla_internal.cuh"
+#include "sla_workspace.h"
+
+namespace sla {
+namespace {
+
+struct BatchDesc {
+  int batch, shared_pattern;
+  int n, nnz;                 // shared pattern sizes
+  const int* rowptr;          // shared: [n+1]; list: per-system rowptrs concatenated
+  const int* col;             // shared: [nnz]; list: local columns concatenated
+  const int* n_off;           // list: [batch+1] row offsets (device)
+  const int* nnz_off;         // list: [batch+1] entry offsets (device)
+  const double* val;          // shared: [batch, nnz]; list: concatenated
+  const double* b;
+  double* x;
+  sla_info* info;             // [batch]
+  const int* order;           // optional processing order
+  unsigned* next;             // scheduling counter (zeroed before launch)
+  double* gvec;               // per-system vector storage: 5 n doubles at 5 * (row offset)
+  int n_max, smem_rows;       // rows whose vectors fit the dynamic shared memory
+  double rtol, atol;
+  int max_iter, max_restarts, precond, use_x0;
+};
+
+template <int NT>
+struct BSmem {
+  double red[2 * NT + 2];
+  int sys;
+};
+
+// Sum of row i of (rp, cl, v) times w, entries in order.  w may live in
+// shared memory or be written earlier in this same launch (x, p), so it is
+// read with plain generic loads, never through the read-only path; the
+// pattern and values are read-only.  With the vectors on chip the gathers
+// are short-latency, so no batching (which would cost registers here).
+__device__ __forceinline__ double brow(const int* __restrict__ rp, const int* __restrict__ cl,
+                                       const double* __restrict__ v, const double* w, int i) {
+  const int a = __ldg(rp + i), e = __ldg(rp + i + 1);
+  double acc = 0.0;
+  for (int k = a; k < e; ++k) acc = fma(__ldg(v + k), w[__ldg(cl + k)], acc);
+  return acc;
+}
+
+template <int NT>
+__device__ void solve_system(const BatchDesc& d, int n, const int* __restrict__ rp,
+                             const int* __restrict__ cl, const double* __restrict__ v,
+                             const double* __restrict__ b, double* __restrict__ x, double* vec,
+                             BSmem<NT>& sm, sla_info* info) {
+  double* r = vec;
+  double* z = vec + n;
+  double* p = vec + 2 * (size_t)n;
+  double* q = vec + 3 * (size_t)n;
+  double* dinv = vec + 4 * (size_t)n;
+  const int t = threadIdx.x;
+  // ---- init: dinv, r = b - A x0, bnorm, bad diagonal
+  double acc[2] = {0.0, 0.0};  // bb, bad
+  for (int i = t; i < n; i += NT) {
+    double diag = 0.0;
+    for (int k = __ldg(rp + i); k < __ldg(rp + i + 1); ++k)
+      if (__ldg(cl + k) == i) diag += __ldg(v + k);
+    double di = 1.0;
+    if (d.precond == SLA_PRECOND_JACOBI) {
+      if (!(diag > 0.0)) acc[1] = 1.0;
+      di = 1.0 / diag;
+    }
+    dinv[i] = di;
+    if (!d.use_x0) x[i] = 0.0;
+    acc[0] = fma(b[i], b[i], acc[0]);
+  }
+  block_sums<NT, 2>(acc, sm.red);
+  const double bnorm = sqrt(acc[0]);
+  const double thresh = fmax(d.rtol * bnorm, d.atol);
+  sla_info inf{0, SLA_NOT_CONVERGED, 0.0, 0.0};
+  if (acc[1] > 0.0) {
+    if (t == 0) *info = sla_info{0, SLA_NOT_SPD, NAN, NAN};
+    return;
+  }
+  if (bnorm == 0.0) {
+    for (int i = t; i < n; i += NT) x[i] = 0.0;
+    if (t == 0) *info = sla_info{0, SLA_OK, 0.0, 0.0};
+    return;
+  }
+  int it = 0, status = SLA_NOT_CONVERGED;
+  double rnorm = 0.0;
+  for (int restart = 0; restart <= d.max_restarts; ++restart) {
+    // r = b - A x ; z = dinv r ; p = z ; rho = r.z
+    double s2[2] = {0.0, 0.0};  // rz, rr
+    for (int i = t; i < n; i += NT) {
+      const double ri = b[i] - brow(rp, cl, v, x, i);
+      const double zi = dinv[i] * ri;
+      r[i] = ri;
+      z[i] = zi;
+      p[i] = zi;
+      s2[0] = fma(ri, zi, s2[0]);
+      s2[1] = fma(ri, ri, s2[1]);
+    }
+    block_sums<NT, 2>(s2, sm.red);  // also orders the p writes before the SpMV
+    double rho = s2[0];
+    rnorm = sqrt(s2[1]);
+    status = SLA_NOT_CONVERGED;
+    if (!isfinite(rho) || !isfinite(rnorm)) {
+      status = SLA_BREAKDOWN;
+      break;
+    }
+    while (!(rnorm <= thresh) && it < d.max_iter) {
+      double pq[1] = {0.0};
+      for (int i = t; i < n; i += NT) {
+        const double qi = brow(rp, cl, v, p, i);
+        q[i] = qi;
+        pq[0] = fma(p[i], qi, pq[0]);
+      }
+      block_sums<NT, 1>(pq, sm.red);
+      if (!isfinite(pq[0])) { status = SLA_BREAKDOWN; break; }
+      if (!(pq[0] > 0.0)) { status = SLA_NOT_SPD; break; }
+      const double alpha = rho / pq[0];
+      double u[2] = {0.0, 0.0};  // rz, rr
+      for (int i = t; i < n; i += NT) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        const double zi = dinv[i] * ri;
+        r[i] = ri;
+        z[i] = zi;
+        u[0] = fma(ri, zi, u[0]);
+        u[1] = fma(ri, ri, u[1]);
+      }
+      block_sums<NT, 2>(u, sm.red);
+      const double rho_new = u[0];
+      rnorm = sqrt(u[1]);
+      ++it;
+      if (!isfinite(rho_new) || !isfinite(rnorm)) { status = SLA_BREAKDOWN; break; }
+      if (rnorm <= thresh) { status = SLA_OK; break; }
+      if (!(rho_new > 0.0)) { status = SLA_NOT_SPD; break; }
+      const double beta = rho_new / rho;
+      for (int i = t; i < n; i += NT) p[i] = fma(beta, p[i], z[i]);
+      __syncthreads();
+      rho = rho_new;
+    }
+    if (rnorm <= thresh) status = SLA_OK;
+    if (status != SLA_OK) break;
+    // true residual
+    double tt[1] = {0.0};
+    for (int i = t; i < n; i += NT) {
+      const double ti = b[i] - brow(rp, cl, v, x, i);
+      tt[0] = fma(ti, ti, tt[0]);
+    }
+    block_sums<NT, 1>(tt, sm.red);
+    if (sqrt(tt[0]) <= 2.0 * thresh) break;
+    if (restart == d.max_restarts) {
+      status = SLA_NOT_CONVERGED;
+      break;
+    }
+  }
+  double tt[1] = {0.0};
+  for (int i = t; i < n; i += NT) {
+    const double ti = b[i] - brow(rp, cl, v, x, i);
+    tt[0] = fma(ti, ti, tt[0]);
+  }
+  block_sums<NT, 1>(tt, sm.red);
+  inf.iters = it;
+  inf.status = status;
+  inf.rel_res = rnorm / bnorm;
+  inf.true_rel_res = sqrt(tt[0]) / bnorm;
+  if (t == 0) *info = inf;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) batched_pcg_kernel(BatchDesc d) {
+  extern __shared__ __align__(16) double dyn[];
+  __shared__ BSmem<NT> sm;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) sm.sys = (int)atomicAdd(d.next, 1u);
+    __syncthreads();
+    const int k = sm.sys;
+    if (k >= d.batch) break;
+    const int s = d.order ? d.order[k] : k;
+    int n;
+    size_t row0;
+    const int *rp, *cl;
+    const double *v, *b;
+    double* x;
+    if (d.shared_pattern) {
+      n = d.n;
+      row0 = (size_t)s * n;
+      rp = d.rowptr;
+      cl = d.col;
+      v = d.val + (size_t)s * d.nnz;
+      b = d.b + (size_t)s * n;
+      x = d.x + (size_t)s * n;
+    } else {
+      const int n0 = d.n_off[s];
+      n = d.n_off[s + 1] - n0;
+      row0 = (size_t)n0;
+      const int e0 = d.nnz_off[s];
+      rp = d.rowptr + n0 + s;
+      cl = d.col + e0;
+      v = d.val + e0;
+      b = d.b + n0;
+      x = d.x + n0;
+    }
+    double* vec = n <= d.smem_rows ? dyn : d.gvec + 5 * row0;
+    solve_system<NT>(d, n, rp, cl, v, b, x, vec, sm, d.info + s);
+  }
+}
+
+template <int NT>
+int launch_batched(const BatchDesc& d0, bool use_smem, cudaStream_t s) {
+  BatchDesc d = d0;
+  static int smem_limit = 0;
+  if (smem_limit == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, current_device());
+    smem_limit = v > 0 ? v : 48 * 1024;
+  }
+  const int static_bytes = (int)sizeof(BSmem<NT>) + 1024;
+  int rows = use_smem ? (smem_limit - static_bytes) / (5 * (int)sizeof(double)) : 0;
+  if (rows > d.n_max) rows = d.n_max;
+  if (rows < 0) rows = 0;
+  d.smem_rows = rows;
+  const size_t dyn = (size_t)rows * 5 * sizeof(double);
+  SLA_CUDA_TRY(cudaFuncSetAttribute(batched_pcg_kernel<NT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_pcg_kernel<NT>, NT, dyn) !=
+          cudaSuccess || per_sm <= 0)
+    per_sm = 1;
+  const int grid = persistent_grid(current_device(), d.batch, per_sm, kMaxBlocks);
+  SLA_CUDA_TRY(cudaMemsetAsync(d.next, 0, sizeof(unsigned), s));
+  batched_pcg_kernel<NT><<<grid, NT, dyn, s>>>(d);
+  SLA_CUDA_TRY(cudaGetLastError());
+  return SLA_OK;
+}
+
+// config: low 4 bits = block size code (1: 256, 2: 512, 3: 1024; 0: auto),
+// bit 4 = keep the vectors in global memory even when they fit on chip.
+int dispatch(const BatchDesc& d, int config, cudaStream_t s) {
+  int code = config & 15;
+  const bool use_smem = ((config >> 4) & 1) == 0;
+  if (code == 0) code = d.n_max >= 2048 ? 2 : 1;
+  switch (code) {
+    case 1: return launch_batched<256>(d, use_smem, s);
+    case 2: return launch_batched<512>(d, use_smem, s);
+    case 3: return launch_batched<1024>(d, use_smem, s);
+    default: return SLA_ERR_INVALID;
+  }
+}
+
+int check_opts(const sla_opts* o) {
+  if (o == nullptr || !(o->rtol >= 0.0) || !(o->atol >= 0.0) || o->max_iter < 0 ||
+      o->max_restarts < 0 || o->max_restarts > 16 || (o->use_x0 != 0 && o->use_x0 != 1) ||
+      (o->precond != SLA_PRECOND_NONE && o->precond != SLA_PRECOND_JACOBI))
+    return SLA_ERR_INVALID;
+  return SLA_OK;
+}
+
+void fill_opts(BatchDesc& d, const sla_opts* o) {
+  d.rtol = o->rtol;
+  d.atol = o->atol;
+  d.max_iter = o->max_iter;
+  d.max_restarts = o->max_restarts;
+  d.precond = o->precond;
+  d.use_x0 = o->use_x0;
+}
+
+// batched gradient: grad_val[s, k] = -lambda[s, row k] x[s, col k]
+__global__ void batched_grad_kernel(int batch, int shared_pattern, int n, int nnz,
+                                    const int* __restrict__ rowptr, const int* __restrict__ col,
+                                    const int* __restrict__ n_off, const int* __restrict__ nnz_off,
+                                    const double* __restrict__ lambda, const double* __restrict__ x,
+                                    double* __restrict__ g) {
+  for (int s = blockIdx.y; s < batch; s += gridDim.y) {
+    int ns, e0, n0;
+    const int* rp;
+    if (shared_pattern) {
+      ns = n;
+      rp = rowptr;
+      e0 = s * nnz;
+      n0 = s * n;
+    } else {
+      n0 = n_off[s];
+      ns = n_off[s + 1] - n0;
+      rp = rowptr + n0 + s;
+      e0 = nnz_off[s];
+    }
+    const int* cl = shared_pattern ? col : col + e0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
+      const double li = -lambda[n0 + i];
+      for (int k = rp[i]; k < rp[i + 1]; ++k) g[(size_t)e0 + k] = li * x[n0 + cl[k]];
+    }
+  }
+}
+
+}  // namespace
+
+size_t batched_ws_bytes(long long total_rows) {
+  // scheduling counter + 5 doubles per row of the batch (used by the systems
+  // whose vectors do not fit in shared memory)
+  return 256 + al256((size_t)5 * sizeof(double) * (size_t)(total_rows > 0 ? total_rows : 1));
+}
+
+}  // namespace sla
+
+using namespace sla;
+
+extern "C" int32_t sla_cg_batched_shared(const sla_csr* A, int32_t batch, const double* val,
+                                         const double* b, double* x, const sla_opts* opts,
+                                         sla_info* info, int32_t config, void* ws, size_t ws_bytes,
+                                         void* stream) {
+  if (A == nullptr || batch < 0 || A->n < 0 || A->nnz < 0) return SLA_ERR_INVALID;
+  if (check_opts(opts) != SLA_OK) return SLA_ERR_INVALID;
+  if (batch == 0 || A->n == 0) return batch == 0 ? SLA_OK : SLA_ERR_INVALID;
+  if (A->rowptr == nullptr || b == nullptr || x == nullptr || info == nullptr) return SLA_ERR_INVALID;
+  if (A->nnz > 0 && (A->col == nullptr || val == nullptr)) return SLA_ERR_INVALID;
+  if (ws == nullptr || ((uintptr_t)ws & 255u) ||
+      ws_bytes < batched_ws_bytes((long long)batch * A->n))
+    return SLA_ERR_WORKSPACE;
+  BatchDesc d = {};
+  d.batch = batch;
+  d.shared_pattern = 1;
+  d.n = A->n;
+  d.nnz = A->nnz;
+  d.rowptr = A->rowptr;
+  d.col = A->col;
+  d.val = val;
+  d.b = b;
+  d.x = x;
+  d.info = info;
+  d.next = (unsigned*)ws;
+  d.gvec = (double*)((char*)ws + 256);
+  d.n_max = A->n;
+  fill_opts(d, opts);
+  return dispatch(d, config, (cudaStream_t)stream);
+}
+
+extern "C" int32_t sla_cg_batched_list(int32_t batch, int32_t n_max, int32_t total_rows,
+                                       const int32_t* n_off,
+                                       const int32_t* nnz_off, const int32_t* rowptr,
+                                       const int32_t* col, const double* val, const double* b,
+                                       double* x, const int32_t* order, const sla_opts* opts,
+                                       sla_info* info, int32_t config, void* ws, size_t ws_bytes,
+                                       void* stream) {
+  if (batch < 0 || n_max < 0 || total_rows < 0 || check_opts(opts) != SLA_OK) return SLA_ERR_INVALID;
+  if (batch == 0) return SLA_OK;
+  if (n_off == nullptr || nnz_off == nullptr || rowptr == nullptr || col == nullptr ||
+      val == nullptr || b == nullptr || x == nullptr || info == nullptr)
+    return SLA_ERR_INVALID;
+  if (ws == nullptr || ((uintptr_t)ws & 255u) || ws_bytes < batched_ws_bytes(total_rows))
+    return SLA_ERR_WORKSPACE;
+  BatchDesc d = {};
+  d.batch = batch;
+  d.shared_pattern = 0;
+  d.rowptr = rowptr;
+  d.col = col;
+  d.n_off = n_off;
+  d.nnz_off = nnz_off;
+  d.val = val;
+  d.b = b;
+  d.x = x;
+  d.info = info;
+  d.order = order;
+  d.next = (unsigned*)ws;
+  d.gvec = (double*)((char*)ws + 256);
+  d.n_max = n_max;
+  fill_opts(d, opts);
+  return dispatch(d, config, (cudaStream_t)stream);
+}
+
+extern "C" int32_t sla_grad_values_batched(int32_t batch, int32_t shared_pattern, int32_t n,
+                                           int32_t nnz, const int32_t* rowptr, const int32_t* col,
+                                           const int32_t* n_off, const int32_t* nnz_off,
+                                           const double* lambda, const double* x,
+                                           double* grad_val, void* stream) {
+  if (batch < 0 || n < 0 || nnz < 0) return SLA_ERR_INVALID;
+  if (batch == 0) return SLA_OK;
+  if (rowptr == nullptr || col == nullptr || lambda == nullptr || x == nullptr || grad_val == nullptr)
+    return SLA_ERR_INVALID;
+  if (!shared_pattern && (n_off == nullptr || nnz_off == nullptr || n <= 0)) return SLA_ERR_INVALID;
+  const int gx = (n + 255) / 256;
+  dim3 grid((unsigned)(gx > 64 ? 64 : (gx > 0 ? gx : 1)), (unsigned)(batch < 65535 ? batch : 65535));
+  batched_grad_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(batch, shared_pattern, n, nnz, rowptr, col,
+                                                              n_off, nnz_off, lambda, x, grad_val);
+  SLA_CUDA_TRY(cudaGetLastError());
+  return SLA_OK;
+}

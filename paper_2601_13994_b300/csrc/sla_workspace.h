@@ -87,6 +87,9 @@ constexpr BiLayout bicg_layout(int n) {
   return L;
 }
 
+// Batched solves (sla_batched.cu); argument = total rows of the batch.
+size_t batched_ws_bytes(long long total_rows);
+
 // Pattern utilities (sla_pattern.cu).
 size_t transpose_ws_bytes(int n, int nnz);
 size_t coo_ws_bytes(int n, long long m);
@@ -116,6 +119,9 @@ inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
       return true;
     case SLA_WS_COO:
       *out = coo_ws_bytes(n, nnz);
+      return true;
+    case SLA_WS_BATCHED:
+      *out = batched_ws_bytes((long long)n * (batch > 0 ? batch : 1));
       return true;
     default:
       return false;

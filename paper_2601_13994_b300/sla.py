@@ -427,3 +427,190 @@ class SparseTensor:
 
     def matvec(self, x: torch.Tensor) -> torch.Tensor:
         return spmv(self.A, self.csr_values().detach(), x.contiguous())
+
+
+# ---------------------------------------------------------------------------
+# Batched solves in one persistent launch (shared pattern / distinct patterns)
+# ---------------------------------------------------------------------------
+
+BATCH_CONFIGS = (1, 2, 3, 1 | 16, 2 | 16, 3 | 16)  # 256/512/1024 threads, vectors on chip / in global
+
+
+class CSRList:
+    """Distinct square patterns concatenated on one device (SparseTensorList
+    of Sec. 3.1): per-system row pointers back to back, local columns,
+    offsets n_off / nnz_off, and a largest-first processing order."""
+
+    def __init__(self, patterns, device="cuda"):
+        dev = torch.device(device)
+        ns = [len(rp) - 1 for rp, _ in patterns]
+        nnzs = [int(rp[-1]) for rp, _ in patterns]
+        self.batch = len(patterns)
+        self.n_off_h = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+        self.nnz_off_h = np.concatenate([[0], np.cumsum(nnzs)]).astype(np.int64)
+        if self.n_off_h[-1] >= 2 ** 31 or self.nnz_off_h[-1] >= 2 ** 31:
+            raise ValueError("batch too large for int32 offsets")
+        self.n_max = max(ns) if ns else 0
+        self.total_rows = int(self.n_off_h[-1])
+        self.total_nnz = int(self.nnz_off_h[-1])
+        rp_cat = np.concatenate([np.asarray(rp, np.int32) for rp, _ in patterns]) if patterns else np.zeros(0, np.int32)
+        c_cat = np.concatenate([np.asarray(c, np.int32) for _, c in patterns]) if patterns else np.zeros(0, np.int32)
+        self.rowptr = torch.from_numpy(rp_cat).to(dev)
+        self.col = torch.from_numpy(c_cat).to(dev)
+        self.n_off = torch.from_numpy(self.n_off_h.astype(np.int32)).to(dev)
+        self.nnz_off = torch.from_numpy(self.nnz_off_h.astype(np.int32)).to(dev)
+        self.order = torch.from_numpy(np.argsort(-np.asarray(nnzs), kind="stable").astype(np.int32)).to(dev)
+        self.device = self.rowptr.device
+
+
+_tune_cache: dict = {}
+
+
+def _batched_opts(rtol, atol, max_iter, max_restarts, precond, use_x0, n):
+    return _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, n, True)
+
+
+def cg_batched(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10, atol: float = 0.0,
+               max_iter: int | None = None, precond: str = "jacobi", x0: torch.Tensor | None = None,
+               max_restarts: int = 2, config: int | str = "auto", out: torch.Tensor | None = None):
+    """B systems on one pattern: val [B, nnz], b [B, n] -> x [B, n], SolveInfo
+    (B records).  One persistent launch; config "tune" runs the autotuner."""
+    B = b.shape[0]
+    _need(val, torch.float64, A.device, "val", B * A.nnz)
+    _need(b, torch.float64, A.device, "b", B * A.n)
+    x = torch.empty((B, A.n), dtype=torch.float64, device=A.device) if out is None else out
+    use_x0 = 0
+    if x0 is not None:
+        x.copy_(x0)
+        use_x0 = 1
+    info = torch.empty((B, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
+    o = _batched_opts(rtol, atol, max_iter, max_restarts, precond, use_x0, A.n)
+    ws = workspace(L.SLA_WS_BATCHED, A.n, A.nnz, B, A.device)
+
+    def run(cfg):
+        L.check("sla_cg_batched_shared", L.lib().sla_cg_batched_shared(
+            ctypes.byref(A.c), B, val.data_ptr(), b.data_ptr(), x.data_ptr(), ctypes.byref(o), info.data_ptr(),
+            cfg, ws.data_ptr(), ws.numel(), _stream_ptr(A.device)))
+
+    cfg = _resolve_config(config, ("shared", A.n, A.nnz, B), run, x, x0)
+    run(cfg)
+    return x, SolveInfo(info)
+
+
+def cg_batched_list(P: CSRList, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10, atol: float = 0.0,
+                    max_iter: int | None = None, precond: str = "jacobi", x0: torch.Tensor | None = None,
+                    max_restarts: int = 2, config: int | str = "auto", out: torch.Tensor | None = None):
+    """Distinct patterns (concatenated values / right-hand sides) in one
+    persistent launch; returns (x concatenated, SolveInfo with B records)."""
+    _need(val, torch.float64, P.device, "val", P.total_nnz)
+    _need(b, torch.float64, P.device, "b", P.total_rows)
+    x = torch.empty(P.total_rows, dtype=torch.float64, device=P.device) if out is None else out
+    use_x0 = 0
+    if x0 is not None:
+        x.copy_(x0)
+        use_x0 = 1
+    info = torch.empty((P.batch, L.INFO_BYTES), dtype=torch.uint8, device=P.device)
+    o = _batched_opts(rtol, atol, max_iter, max_restarts, precond, use_x0, P.n_max)
+    ws = workspace(L.SLA_WS_BATCHED, P.total_rows, P.total_nnz, 1, P.device)
+
+    def run(cfg):
+        L.check("sla_cg_batched_list", L.lib().sla_cg_batched_list(
+            P.batch, P.n_max, P.total_rows, P.n_off.data_ptr(), P.nnz_off.data_ptr(), P.rowptr.data_ptr(),
+            P.col.data_ptr(), val.data_ptr(), b.data_ptr(), x.data_ptr(), P.order.data_ptr(), ctypes.byref(o),
+            info.data_ptr(), cfg, ws.data_ptr(), ws.numel(), _stream_ptr(P.device)))
+
+    cfg = _resolve_config(config, ("list", P.n_max, P.total_rows, P.total_nnz, P.batch), run, x, x0)
+    run(cfg)
+    return x, SolveInfo(info)
+
+
+def _resolve_config(config, key, run, x, x0):
+    """'auto': cached tuned choice if any, else the library's heuristic (0);
+    'tune': time every kernel variant on this batch (two runs each, CUDA
+    events) and cache the fastest under the batch's shape key."""
+    if isinstance(config, int):
+        return config
+    if config == "auto":
+        return _tune_cache.get(key, 0)
+    if config != "tune":
+        raise ValueError("config must be an int, 'auto' or 'tune'")
+    best, best_t = 0, float("inf")
+    for cfg in BATCH_CONFIGS:
+        times = []
+        for _ in range(2):
+            if x0 is not None:
+                x.copy_(x0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run(cfg)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        if min(times) < best_t:
+            best, best_t = cfg, min(times)
+    _tune_cache[key] = best
+    return best
+
+
+def tuned_configs() -> dict:
+    return dict(_tune_cache)
+
+
+def grad_values_batched_shared(A: CSRMatrix, lam: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+    B = lam.shape[0]
+    g = torch.empty((B, A.nnz), dtype=torch.float64, device=A.device)
+    L.check("sla_grad_values_batched", L.lib().sla_grad_values_batched(
+        B, 1, A.n, A.nnz, A.rowptr.data_ptr(), A.col.data_ptr(), None, None, lam.data_ptr(), x.data_ptr(),
+        g.data_ptr(), _stream_ptr(A.device)))
+    return g
+
+
+def grad_values_batched_list(P: CSRList, lam: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+    g = torch.empty(P.total_nnz, dtype=torch.float64, device=P.device)
+    L.check("sla_grad_values_batched", L.lib().sla_grad_values_batched(
+        P.batch, 0, P.n_max, 0, P.rowptr.data_ptr(), P.col.data_ptr(), P.n_off.data_ptr(), P.nnz_off.data_ptr(),
+        lam.data_ptr(), x.data_ptr(), g.data_ptr(), _stream_ptr(P.device)))
+    return g
+
+
+class BatchedSolve(torch.autograd.Function):
+    """x[s] = A_s^{-1} b[s] for a batch on one shared SPD pattern, with the
+    adjoint backward: one batched CG for all lambda_s, one gradient pass."""
+
+    @staticmethod
+    def forward(ctx, val, b, A, kw, strict):
+        x, info = cg_batched(A, val.detach().contiguous(), b.detach().contiguous(), **kw)
+        if strict is not None:
+            _check_batch(info, "batched forward", strict)
+        ctx.save_for_backward(val, x)
+        ctx.A, ctx.kw, ctx.strict = A, kw, strict
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        val, x = ctx.saved_tensors
+        kw = {k: v for k, v in ctx.kw.items() if k not in ("x0", "out")}
+        lam, info = cg_batched(ctx.A, val.detach().contiguous(), gx.contiguous().to(torch.float64), **kw)
+        if ctx.strict is not None:
+            _check_batch(info, "batched adjoint", ctx.strict)
+        return grad_values_batched_shared(ctx.A, lam, x), lam, None, None, None
+
+
+def _check_batch(info: SolveInfo, what: str, strict: bool):
+    st = np.atleast_1d(info.status)
+    bad = np.nonzero(st != L.SLA_OK)[0]
+    if bad.size:
+        msg = "%s: %d of %d systems did not converge (first: system %d, %s)" % (
+            what, bad.size, st.size, bad[0], L.STATUS_NAMES.get(int(st[bad[0]]), "?"))
+        if strict:
+            raise SolveError(msg)
+        import warnings
+        warnings.warn(msg)
+
+
+def solve_batched(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, strict: bool | None = True,
+                  **kw) -> torch.Tensor:
+    """Differentiable batched SPD solve on a shared pattern: val [B, nnz],
+    b [B, n] -> x [B, n]."""
+    return BatchedSolve.apply(val, b, A, kw, strict)

@@ -1,0 +1,169 @@
+"""Batched Jacobi-PCG (one persistent launch) against the oracle solved one
+system at a time; per-system statuses; kernel variants; autotuner; CUDA
+graph capture; batched adjoint gradients."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2601_13994_b300 import inputs as I
+from paper_2601_13994_b300 import sla
+from tests.gpu_util import csr, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _per_system_check(rp, c, vals, bs, x, info, rtol, iters_tol=2, idx=None):
+    its = np.atleast_1d(info.iters)
+    st = np.atleast_1d(info.status)
+    idx = range(len(bs)) if idx is None else idx
+    for s in idx:
+        xo, io = oracle.pcg(rp[s], c[s], vals[s], bs[s], rtol=rtol)
+        assert st[s] == io["status"] == 0, s
+        assert rel(x[s], xo) <= 1e-8, s
+        assert abs(int(its[s]) - io["iters"]) <= iters_tol, (s, its[s], io["iters"])
+
+
+def test_shared_pattern_matches_oracle_per_system():
+    B, N = 48, 32
+    rp, c, vals = I.batched_shared_2d(N, B, seed0=1000, sigma=0.5)
+    b = I.rhs_uniform(N * N, 5, batch=B)
+    A = csr(rp, c)
+    x, info = sla.cg_batched(A, to_dev(vals), to_dev(b), rtol=1e-10)
+    torch.cuda.synchronize()
+    xh = x.cpu().numpy()
+    _per_system_check([rp] * B, [c] * B, vals, b, xh, info, 1e-10)
+    # systems converge after different iteration counts: each CTA stopped on its own
+    assert len(set(np.atleast_1d(info.iters).tolist())) > 1
+
+
+def test_mixed_statuses_do_not_leak_between_systems():
+    B, N = 6, 20
+    rp, c, vals = I.batched_shared_2d(N, B, seed0=7, sigma=0.5)
+    b = I.rhs_uniform(N * N, 1, batch=B)
+    b[1] = 0.0                                       # zero right-hand side
+    diag = np.nonzero(c == np.repeat(np.arange(N * N), np.diff(rp)))[0]
+    vals[3, diag[10]] = -1.0                         # non-positive diagonal
+    x, info = sla.cg_batched(csr(rp, c), to_dev(vals), to_dev(b), rtol=1e-10, max_iter=400)
+    torch.cuda.synchronize()
+    st = np.atleast_1d(info.status)
+    its = np.atleast_1d(info.iters)
+    assert st[1] == 0 and its[1] == 0 and not x[1].any()
+    assert sla.L.STATUS_NAMES[int(st[3])] == "NOT_SPD"
+    for s in (0, 2, 4, 5):
+        xo, io = oracle.pcg(rp, c, vals[s], b[s], rtol=1e-10)
+        assert st[s] == 0 and rel(x[s].cpu().numpy(), xo) <= 1e-8
+
+
+def test_all_kernel_variants_agree():
+    B, N = 16, 24
+    rp, c, vals = I.batched_shared_2d(N, B, seed0=3, sigma=0.5)
+    b = to_dev(I.rhs_uniform(N * N, 2, batch=B))
+    A = csr(rp, c)
+    v = to_dev(vals)
+    res = {}
+    for cfg in sla.BATCH_CONFIGS:
+        x, info = sla.cg_batched(A, v, b, rtol=1e-10, config=cfg)
+        torch.cuda.synchronize()
+        res[cfg] = (x.clone(), np.atleast_1d(info.iters).copy())
+    for code in (1, 2, 3):
+        # same block size: on-chip or global vectors give the same bits
+        assert torch.equal(res[code][0], res[code | 16][0])
+        assert np.array_equal(res[code][1], res[code | 16][1])
+        assert rel(res[code][0].cpu().numpy(), res[1][0].cpu().numpy()) <= 1e-9
+    tuned = sla.cg_batched(A, v, b, rtol=1e-10, config="tune")[0]
+    assert any(k[0] == "shared" for k in sla.tuned_configs())
+    assert rel(tuned.cpu().numpy(), res[1][0].cpu().numpy()) <= 1e-9
+
+
+def test_distinct_patterns_match_oracle():
+    mats = I.fem_list(30, seed0=2000, n_lo=100, n_hi=3000)
+    mats.append(I.diffusion2d_random(80, 9))         # 6400 rows: vectors off chip
+    P = sla.CSRList([(rp, c) for rp, c, _ in mats])
+    vals = np.concatenate([v for _, _, v in mats])
+    bs = [I.rhs_uniform(len(rp) - 1, 50 + s) for s, (rp, _, _) in enumerate(mats)]
+    x, info = sla.cg_batched_list(P, to_dev(vals), to_dev(np.concatenate(bs)), rtol=1e-10)
+    torch.cuda.synchronize()
+    xh = x.cpu().numpy()
+    xs = [xh[P.n_off_h[s]:P.n_off_h[s + 1]] for s in range(len(mats))]
+    _per_system_check([m[0] for m in mats], [m[1] for m in mats], [m[2] for m in mats], bs, xs, info, 1e-10)
+
+
+def test_graph_capture_and_replay():
+    B, N = 8, 16
+    rp, c, vals = I.batched_shared_2d(N, B, seed0=11, sigma=0.5)
+    A = csr(rp, c)
+    v = to_dev(vals)
+    b_static = to_dev(I.rhs_uniform(N * N, 1, batch=B))
+    x_static = torch.empty_like(b_static)
+    sla.cg_batched(A, v, b_static, rtol=1e-10, out=x_static)  # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            sla.cg_batched(A, v, b_static, rtol=1e-10, out=x_static)
+    torch.cuda.current_stream().wait_stream(s)
+    b_new = to_dev(I.rhs_uniform(N * N, 2, batch=B))
+    b_static.copy_(b_new)
+    g.replay()
+    torch.cuda.synchronize()
+    x_ref, _ = sla.cg_batched(A, v, b_new, rtol=1e-10)
+    torch.cuda.synchronize()
+    assert torch.equal(x_static, x_ref)
+
+
+def test_batched_adjoint_matches_single_solves():
+    B, N = 5, 16
+    rp, c, vals = I.batched_shared_2d(N, B, seed0=21, sigma=0.5)
+    A = csr(rp, c)
+    v = to_dev(vals).requires_grad_(True)
+    b = to_dev(I.rhs_uniform(N * N, 3, batch=B)).requires_grad_(True)
+    x = sla.solve_batched(A, v, b, rtol=1e-12)
+    (x * x).sum().backward()
+    for s in range(B):
+        xo, _ = oracle.pcg(rp, c, vals[s], b[s].detach().cpu().numpy(), rtol=1e-13)
+        gb, gv, _ = oracle.adjoint_backward(rp, c, vals[s], xo, 2 * xo, rtol=1e-13)
+        assert rel(b.grad[s].cpu().numpy(), gb) <= 1e-6
+        assert rel(v.grad[s].cpu().numpy(), gv) <= 1e-6
+
+
+@pytest.mark.slow
+def test_full_size_shared_1024_systems_64():
+    """The shared-pattern batch at full size: 1024 systems on the 64 x 64
+    five-point pattern, faces exp(N(0, 0.5^2)) from seeds 1000 + s, rtol 1e-8:
+    sampled systems against the oracle, every system's residual by the
+    oracle's SpMV."""
+    B, N = 1024, 64
+    rp, c, vals = I.batched_shared_2d(N, B, seed0=1000, sigma=0.5)
+    b = I.rhs_uniform(N * N, 7, batch=B)
+    x, info = sla.cg_batched(csr(rp, c), to_dev(vals), to_dev(b), rtol=1e-8)
+    torch.cuda.synchronize()
+    xh = x.cpu().numpy()
+    assert (np.atleast_1d(info.status) == 0).all()
+    for s in range(B):
+        r = b[s] - oracle.spmv(rp, c, vals[s], xh[s])
+        assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(b[s])
+    _per_system_check([rp] * B, [c] * B, vals, b, xh, info, 1e-8, idx=[0, 1, 511, 1023])
+
+
+@pytest.mark.slow
+def test_full_size_fem_list_512():
+    """512 jittered, holed P1 FEM Laplacians with n log-uniform in [1e3, 5e4]
+    (+1e-3 I), rtol 1e-8, in one launch."""
+    mats = I.fem_list(512, seed0=2000)
+    P = sla.CSRList([(rp, c) for rp, c, _ in mats])
+    vals = np.concatenate([v for _, _, v in mats])
+    bs = [I.rhs_uniform(len(rp) - 1, 3000 + s) for s, (rp, _, _) in enumerate(mats)]
+    x, info = sla.cg_batched_list(P, to_dev(vals), to_dev(np.concatenate(bs)), rtol=1e-8)
+    torch.cuda.synchronize()
+    xh = x.cpu().numpy()
+    assert (np.atleast_1d(info.status) == 0).all()
+    xs = [xh[P.n_off_h[s]:P.n_off_h[s + 1]] for s in range(len(mats))]
+    for s, (rp, c, v) in enumerate(mats):
+        r = bs[s] - oracle.spmv(rp, c, v, xs[s])
+        assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(bs[s])
+    big = int(np.argmax([len(m[0]) for m in mats]))
+    _per_system_check([m[0] for m in mats], [m[1] for m in mats], [m[2] for m in mats], bs, xs, info, 1e-8,
+                      iters_tol=5, idx=[0, 1, big])
