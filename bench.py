@@ -34,7 +34,11 @@ sys.path.insert(0, ROOT)
 METRIC = "PCG time to rel-res 1e-8 & SpMV GB/s vs 8 TB/s; learned vs Jacobi-PCG speedup"
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6400.0
-FP64_PEAK_TFLOPS = 1.102  # measured DFMA throughput of this B300 SKU (2 flop / DFMA), see DESIGN
+# DRAM bytes (read + write) of one PCG iteration at 256^3, summed over the
+# three kernels of one ncu --set full capture (profiles/pcg_iteration_diffusion3d_256.md);
+# valid only for these kernels and this size.
+TRAFFIC_PER_ITER_256 = 3.122e9
+FP64_PEAK_TFLOPS = 1.203  # 2 DFMA/clk/SM (ncu peak_sustained) x 148 SMs x 2 flop x 2.032 GHz
 
 
 def parse():
@@ -53,6 +57,8 @@ def parse():
                     help="launch the solver kernels from a host loop instead of one graph (profiling)")
     ap.add_argument("--max-iter", type=int, default=None,
                     help="iteration cap (bounded profiling runs; the timed numbers are then not a solve)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other rows' measurements (BiCGStab, adjoint, batched)")
     return ap.parse_args()
 
 
@@ -164,6 +170,94 @@ def cpu_sample(rp, c, v, b, iters_per_sample: int):
 def pick_cpu_iters(n: int) -> int:
     # about 0.3 s per iteration at n = 16.8M on one core: ~15 s of work
     return int(max(3, min(200, 15.0 / (n * 2.1e-8 + 1e-4))))
+
+
+def _time(fn, reps=3, warm=1):
+    """Median milliseconds of fn() over `reps` runs, CUDA events on the current stream."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts), out
+
+
+def extra_rows(dev, args, peak):
+    """Measurements of the other rows of the path on their own workloads
+    (each after one warm-up run, median of 3, CUDA events)."""
+    import torch
+
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import sla
+    out = {}
+    # BiCGStab: 3D convection-diffusion 128^3, cell Peclet 10, rtol 1e-8
+    rp, c, v = I.convdiff3d(128, 10.0)
+    n, nnz = len(rp) - 1, int(rp[-1])
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    vt = torch.from_numpy(v).to(dev)
+    bt = torch.from_numpy(I.rhs_uniform(n, 5)).to(dev)
+    ms, (x, info) = _time(lambda: sla.bicgstab(A, vt, bt, rtol=1e-8))
+    bpi = 2 * (12 * nnz + 4 * (n + 1)) + 200 * n
+    gbs = bpi * info.iters / (ms / 1e3) / 1e9
+    out["bicgstab_convdiff3d_128_pe10"] = {"s": ms / 1e3, "iters": info.iters, "status": info.status,
+                                           "gbs": gbs, "frac_of_measured_hbm": gbs / peak,
+                                           "bytes_per_iter": bpi}
+    del A, vt, bt, x
+    # adjoint backward at the bench size: A^T lambda = 2x (L = sum x^2) + gradient pass
+    rp, c, v, b = workload(args.size)
+    n, nnz = len(rp) - 1, int(rp[-1])
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    vt = torch.from_numpy(v).to(dev)
+    bt = torch.from_numpy(b).to(dev)
+    x, _ = sla.cg(A, vt, bt, rtol=args.rtol)
+    g = 2 * x
+    ms, (gb, gv, info) = _time(lambda: sla.adjoint_backward(A, vt, x, g, rtol=args.rtol))
+    out["adjoint_backward_diffusion3d_%d" % args.size] = {"s": ms / 1e3, "iters": info.iters,
+                                                          "status": info.status}
+    del A, vt, bt, x, g, gb, gv
+    # batched, shared pattern: 1024 systems on the 64^2 five-point pattern
+    B, N = 1024, 64
+    rp, c, vals = I.batched_shared_2d(N, B, seed0=1000, sigma=0.5)
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    vt = torch.from_numpy(vals).to(dev)
+    bt = torch.from_numpy(I.rhs_uniform(N * N, 7, batch=B)).to(dev)
+    sla.cg_batched(A, vt, bt, rtol=1e-8, config="tune")
+    ms, (x, info) = _time(lambda: sla.cg_batched(A, vt, bt, rtol=1e-8))
+    its = np.atleast_1d(info.iters)
+    fl = float((2 * int(rp[-1]) + 14 * N * N) * its.sum())
+    out["batched_shared_1024x64x64"] = {"s": ms / 1e3, "iters_mean": float(its.mean()),
+                                        "iters_max": int(its.max()),
+                                        "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
+                                        "fp64_tflops": fl / (ms / 1e3) / 1e12,
+                                        "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                                        "config": {str(k): v for k, v in sla.tuned_configs().items()}}
+    del A, vt, bt, x
+    # batched, distinct patterns: 512 P1 FEM systems, n log-uniform in [1e3, 5e4]
+    mats = I.fem_list(512, seed0=2000)
+    P = sla.CSRList([(m[0], m[1]) for m in mats], device=dev)
+    vt = torch.from_numpy(np.concatenate([m[2] for m in mats])).to(dev)
+    bt = torch.from_numpy(np.concatenate([I.rhs_uniform(len(m[0]) - 1, 3000 + s)
+                                          for s, m in enumerate(mats)])).to(dev)
+    sla.cg_batched_list(P, vt, bt, rtol=1e-8, config="tune")
+    ms, (x, info) = _time(lambda: sla.cg_batched_list(P, vt, bt, rtol=1e-8))
+    its = np.atleast_1d(info.iters)
+    fl = 0.0
+    for s, m in enumerate(mats):
+        fl += (2 * int(m[0][-1]) + 14 * (len(m[0]) - 1)) * int(its[s])
+    out["batched_list_512_fem"] = {"s": ms / 1e3, "total_rows": P.total_rows, "iters_mean": float(its.mean()),
+                                   "iters_max": int(its.max()),
+                                   "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
+                                   "fp64_tflops": fl / (ms / 1e3) / 1e12,
+                                   "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+    return out
 
 
 def run_reference(args):
@@ -340,6 +434,9 @@ def run_ours(args):
                          "%d^3 system (%.2f s/iteration), scaled by %s iteration count %d"
                          % (done, N, s_iter, "the oracle's own (tests/golden)" if oracle_iters else
                             "the GPU solve's", used)}
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra = extra_rows(dev, args, peak)
     if rank != 0:
         return 0
     line = {
@@ -358,13 +455,16 @@ def run_ours(args):
         "roofline": {"kernel": "Jacobi-PCG iteration (cg_spmv_pq + cg_update + cg_pupdate)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
-                     "bytes_per_launch": bpi, "traffic": None},
+                     "bytes_per_launch": bpi,
+                     "traffic": TRAFFIC_PER_ITER_256 if N == 256 else None,
+                     "traffic_unit": "bytes per iteration (3 kernels)"},
         "roofline_spmv": {"kernel": "spmv_tiles_kernel", "bound": "hbm", "achieved": spmv_gbs, "peak": peak,
                           "unit": "GB/s", "frac": spmv_gbs / peak, "bytes_per_launch": spmv_bytes(n, nnz)},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": int(launches),
+        "extra": extra,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
