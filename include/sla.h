@@ -52,6 +52,10 @@ extern "C" {
 /* Preconditioners (sla_opts.precond). */
 #define SLA_PRECOND_NONE 0
 #define SLA_PRECOND_JACOBI 1    /* z = D^{-1} r, D = diag(A) (Sec. 4.1)       */
+#define SLA_PRECOND_GGT 2       /* z = G (G^T r): a factored approximate inverse
+                                   M^{-1} = G G^T (G lower triangular), e.g.
+                                   the learned preconditioner the paper names
+                                   as future work (Sec. 5); sla_cg_ggt only   */
 
 /* Flags (sla_opts.flags). */
 #define SLA_FLAG_HOST_LOOP 1    /* run the Krylov loop as plain stream launches
@@ -65,6 +69,7 @@ extern "C" {
 #define SLA_WS_ADJOINT 3        /* sla_adjoint_backward                        */
 #define SLA_WS_TRANSPOSE 4      /* sla_csr_transpose                           */
 #define SLA_WS_COO 5            /* sla_coo_to_csr (pass the COO entry count as nnz) */
+#define SLA_WS_CG_GGT 7         /* sla_cg_ggt: pass the entry count of G as nnz */
 #define SLA_WS_BATCHED 6        /* batched CG: n = rows per system (shared
                                    pattern) or total rows with batch = 1 (list) */
 
@@ -170,6 +175,23 @@ int32_t sla_spmv(const sla_csr* A, const double* val, const double* x,
 int32_t sla_cg(const sla_csr* A, const double* val, const double* b,
                double* x, const sla_opts* opts, sla_info* info, void* ws,
                size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* CG with a factored preconditioner M^{-1} = G G^T                      */
+/* ------------------------------------------------------------------ */
+
+/* Solves A x = b (A SPD) by PCG with z = G (G^T r): two SpMVs per
+ * iteration, so M stays SPD whenever G is nonsingular.  G: lower-triangular
+ * CSR (device: g_rowptr [n+1], g_col, g_val [nnz_g]); GT: its transpose
+ * pattern from sla_csr_transpose of G (perm into g_val; the values of G^T
+ * are gathered once per call).  Same stopping rule, true-residual restart,
+ * statuses (NOT_SPD on p^T A p <= 0 or r^T z <= 0), graph / host-loop
+ * execution and info record as sla_cg (opts->precond is ignored).
+ * Workspace: SLA_WS_CG_GGT with nnz = nnz_g. */
+int32_t sla_cg_ggt(const sla_csr* A, const double* val, const sla_csr* G,
+                   const double* g_val, const sla_csr_t* GT, const double* b,
+                   double* x, const sla_opts* opts, sla_info* info, void* ws,
+                   size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* BiCGStab for nonsymmetric A (van der Vorst 1992; the paper's GPU      */

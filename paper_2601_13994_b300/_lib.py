@@ -24,6 +24,7 @@ SLA_ERR_TIMEOUT = -4
 
 SLA_PRECOND_NONE = 0
 SLA_PRECOND_JACOBI = 1
+SLA_PRECOND_GGT = 2
 
 SLA_FLAG_HOST_LOOP = 1
 
@@ -33,6 +34,7 @@ SLA_WS_ADJOINT = 3
 SLA_WS_TRANSPOSE = 4
 SLA_WS_COO = 5
 SLA_WS_BATCHED = 6
+SLA_WS_CG_GGT = 7
 
 SLA_ADJ_CG = 0
 SLA_ADJ_BICGSTAB = 1
@@ -120,6 +122,9 @@ def lib() -> ctypes.CDLL:
             L.sla_cg_batched_list.restype = i32
             L.sla_grad_values_batched.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, P]
             L.sla_grad_values_batched.restype = i32
+            L.sla_cg_ggt.argtypes = [ctypes.POINTER(SlaCsr), P, ctypes.POINTER(SlaCsr), P, ctypes.POINTER(SlaCsrT),
+                                     P, P, ctypes.POINTER(SlaOpts), P, P, ctypes.c_size_t, P]
+            L.sla_cg_ggt.restype = i32
             L.sla_cg_noalloc.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, ctypes.POINTER(SlaOpts), P, P]
             L.sla_cg_noalloc.restype = i32
             _lib = L

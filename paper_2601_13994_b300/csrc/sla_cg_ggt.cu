@@ -1,0 +1,512 @@
+// sla_cg_ggt.cu -- PCG with a factored approximate inverse M^{-1} = G G^T.
+//
+// Algorithm 1 (P = 1) with z = G (G^T r).  G is lower triangular (for the
+// learned preconditioner it lives on the pattern of tril(A)); applying it
+// as two SpMVs keeps M SPD for any nonsingular G.  One iteration is five
+// kernels in the graph's WHILE body:
+//
+//   K1  q = A p, partial p.q                    -> alpha
+//   K2  x += alpha p, r -= alpha q, partial r.r -> iteration count
+//   GT  t = G^T r          (CSR of G^T, values gathered once per solve)
+//   GZ  z = G t, partial r.z                    -> convergence, beta
+//   K3  p = z + beta p   (or the true-residual check / restart)
+//
+// Phase PRECOND (start and after a restart) runs only GT and GZ, which then
+// also sets p = z and rho = r.z.  Algorithmic bytes per iteration:
+// 12 nnz + 4(n+1) + 2 (12 nnz_g + 4(n+1)) + 128 n.
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "sla_internal.cuh"
+#include "sla_tma.cuh"
+#include "sla_workspace.h"
+
+namespace sla {
+namespace {
+
+constexpr int kVT = 256;
+constexpr int kU = 4;
+constexpr int kPhasePrecond = 4;
+
+struct GPtrs {
+  KrylovDesc* d;
+  KrylovState* st;
+  double* part;
+  double *r, *z, *p, *q, *t, *gtv;
+};
+
+struct VSmem {
+  double red[4 * kVT + 4];
+  bool last;
+};
+
+__global__ void ggt_write_desc_kernel(KrylovDesc* dst, KrylovDesc src, KrylovState* st) {
+  *dst = src;
+  for (int i = 0; i < 8; ++i) st->cnt[i] = 0u;
+  st->err = 0;
+  st->fresh_p = 0;
+}
+
+// r = b - A x0 (x = 0 unless use_x0), partial ||b||^2, ||r||^2; gathers the
+// values of G^T.
+__global__ void __launch_bounds__(kVT) ggt_init_kernel(GPtrs P) {
+  __shared__ VSmem sm;
+  const KrylovDesc d = *P.d;
+  const int n = d.n;
+  const int stride = gridDim.x * kVT;
+  for (long long k = blockIdx.x * (long long)kVT + threadIdx.x; k < d.nnz_g; k += stride)
+    P.gtv[k] = __ldg(d.g_val + __ldg(d.perm_t + k));
+  double acc[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * kVT + threadIdx.x; i < n; i += stride) {
+    const double ax = d.use_x0 ? row_dot(d.rowptr, d.col, d.val, d.x, i) : 0.0;
+    const double bi = d.b[i];
+    const double ri = bi - ax;
+    P.r[i] = ri;
+    acc[0] = fma(bi, bi, acc[0]);
+    acc[1] = fma(ri, ri, acc[1]);
+  }
+  if (!d.use_x0)
+    for (int i = blockIdx.x * kVT + threadIdx.x; i < n; i += stride) d.x[i] = 0.0;
+  block_sums<kVT, 2>(acc, sm.red);
+  if (threadIdx.x == 0) {
+    P.part[blockIdx.x] = acc[0];
+    P.part[kMaxBlocks + blockIdx.x] = acc[1];
+  }
+  if (!last_block_arrive(&P.st->cnt[0], &sm.last)) return;
+  reduce_partials<kVT, 2>(P.part, kMaxBlocks, gridDim.x, acc, sm.red);
+  if (threadIdx.x == 0) {
+    KrylovState& s = *P.st;
+    s.bnorm = sqrt(acc[0]);
+    s.thresh = fmax(d.rtol * s.bnorm, d.atol);
+    s.rr = acc[1];
+    s.rho = s.alpha = s.beta = 0.0;
+    s.iters = s.restarts = s.body = 0;
+    s.zero_rhs = s.bad_diag = 0;
+    s.fresh_p = 0;
+    s.status = SLA_NOT_CONVERGED;
+    if (s.bnorm == 0.0) {
+      s.zero_rhs = 1;
+      s.status = SLA_OK;
+      s.phase = kPhaseDone;
+    } else {
+      s.phase = kPhasePrecond;
+    }
+  }
+}
+
+// K1: q = A p, p.q -> alpha (RUN only)
+__global__ void __launch_bounds__(tma::kThreads, 2) ggt_spmv_pq_kernel(GPtrs P) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
+  if (__ldcg(&P.st->phase) != kPhaseRun) return;
+  const KrylovDesc d = *P.d;
+  double* __restrict__ q = P.q;
+  double pq = 0.0;
+  tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, P.p, P.p, sm, &P.st->err,
+                     [&](int row, double y, double prow) {
+                       q[row] = y;
+                       pq = fma(prow, y, pq);
+                     });
+  double v[1] = {pq};
+  block_sums<tma::kThreads, 1>(v, sm.red);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
+  if (!last_block_arrive(&P.st->cnt[1], &sm.last)) return;
+  reduce_partials<tma::kThreads, 1>(P.part, kMaxBlocks, gridDim.x, v, sm.red);
+  if (threadIdx.x == 0) {
+    KrylovState& s = *P.st;
+    if (__ldcg(&s.err) != 0) {
+      s.status = SLA_ERR_TIMEOUT;
+      s.phase = kPhaseDone;
+    } else if (!isfinite(v[0])) {
+      s.status = SLA_BREAKDOWN;
+      s.phase = kPhaseDone;
+    } else if (!(v[0] > 0.0)) {
+      s.status = SLA_NOT_SPD;
+      s.phase = kPhaseDone;
+    } else {
+      s.alpha = s.rho / v[0];
+    }
+  }
+}
+
+// K2: x += alpha p, r -= alpha q, ||r||^2 (RUN only)
+__global__ void __launch_bounds__(kVT) ggt_update_kernel(GPtrs P) {
+  __shared__ VSmem sm;
+  if (__ldcg(&P.st->phase) != kPhaseRun) return;
+  const KrylovDesc d = *P.d;
+  const int n = d.n;
+  const double alpha = __ldcg(&P.st->alpha);
+  const int stride = gridDim.x * kVT;
+  double rr0 = 0.0, rr1 = 0.0;
+  for (int i0 = blockIdx.x * kVT + threadIdx.x; i0 < n; i0 += kU * stride) {
+    double pi[kU], qi[kU], xi[kU], ri[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = i0 + u * stride;
+      if (i < n) {
+        pi[u] = __ldg(P.p + i);
+        qi[u] = __ldg(P.q + i);
+        xi[u] = d.x[i];
+        ri[u] = P.r[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = i0 + u * stride;
+      if (i < n) {
+        d.x[i] = fma(alpha, pi[u], xi[u]);
+        const double rn = fma(-alpha, qi[u], ri[u]);
+        P.r[i] = rn;
+        if (u & 1) rr1 = fma(rn, rn, rr1);
+        else rr0 = fma(rn, rn, rr0);
+      }
+    }
+  }
+  double v[1] = {rr0 + rr1};
+  block_sums<kVT, 1>(v, sm.red);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
+  if (!last_block_arrive(&P.st->cnt[2], &sm.last)) return;
+  reduce_partials<kVT, 1>(P.part, kMaxBlocks, gridDim.x, v, sm.red);
+  if (threadIdx.x == 0) {
+    P.st->rr = v[0];
+    P.st->iters += 1;
+  }
+}
+
+// GT: t = G^T r (RUN and PRECOND)
+__global__ void __launch_bounds__(tma::kThreads, 2) ggt_gt_kernel(GPtrs P) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
+  const int ph = __ldcg(&P.st->phase);
+  if (ph != kPhaseRun && ph != kPhasePrecond) return;
+  const KrylovDesc d = *P.d;
+  double* __restrict__ t = P.t;
+  tma::spmv_pipeline(d.n, d.nnz_g, d.rowptr_t, d.col_t, P.gtv, P.r, nullptr, sm, &P.st->err,
+                     [&](int row, double y, double) { t[row] = y; });
+}
+
+// GZ: z = G t, r.z; decisions (RUN: convergence and beta; PRECOND: p = z, rho)
+__global__ void __launch_bounds__(tma::kThreads, 2) ggt_gz_kernel(GPtrs P) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
+  const int ph = __ldcg(&P.st->phase);
+  if (ph != kPhaseRun && ph != kPhasePrecond) return;
+  const KrylovDesc d = *P.d;
+  double* __restrict__ z = P.z;
+  double* __restrict__ p = P.p;
+  const bool pre = ph == kPhasePrecond;
+  double rz = 0.0;
+  tma::spmv_pipeline(d.n, d.nnz_g, d.g_rowptr, d.g_col, d.g_val, P.t, P.r, sm, &P.st->err,
+                     [&](int row, double y, double rrow) {
+                       z[row] = y;
+                       if (pre) p[row] = y;
+                       rz = fma(rrow, y, rz);
+                     });
+  double v[1] = {rz};
+  block_sums<tma::kThreads, 1>(v, sm.red);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
+  if (!last_block_arrive(&P.st->cnt[3], &sm.last)) return;
+  reduce_partials<tma::kThreads, 1>(P.part, kMaxBlocks, gridDim.x, v, sm.red);
+  if (threadIdx.x == 0) {
+    KrylovState& s = *P.st;
+    const double trz = v[0], rnorm = sqrt(s.rr);
+    if (__ldcg(&s.err) != 0) {
+      s.status = SLA_ERR_TIMEOUT;
+      s.phase = kPhaseDone;
+    } else if (pre) {
+      s.rho = trz;
+      s.fresh_p = 1;
+      s.status = SLA_NOT_CONVERGED;
+      if (!isfinite(trz) || !isfinite(rnorm)) {
+        s.status = SLA_BREAKDOWN;
+        s.phase = kPhaseDone;
+      } else if (rnorm <= s.thresh) {
+        s.phase = kPhaseCheck;
+      } else if (s.iters >= d.max_iter) {
+        s.phase = kPhaseDone;
+      } else {
+        s.phase = kPhaseRun;
+      }
+    } else {
+      if (!isfinite(trz) || !isfinite(rnorm)) {
+        s.status = SLA_BREAKDOWN;
+        s.phase = kPhaseDone;
+      } else if (rnorm <= s.thresh) {
+        s.status = SLA_OK;
+        s.phase = kPhaseCheck;
+      } else if (!(trz > 0.0)) {
+        s.status = SLA_NOT_SPD;
+        s.phase = kPhaseDone;
+      } else {
+        s.beta = trz / s.rho;
+        s.rho = trz;
+        if (s.iters >= d.max_iter) {
+          s.status = SLA_NOT_CONVERGED;
+          s.phase = kPhaseDone;
+        }
+      }
+    }
+  }
+}
+
+// K3: p = z + beta p (unless p was just reset), or the true-residual check
+__global__ void __launch_bounds__(kVT)
+ggt_k3_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ VSmem sm;
+  const int ph = __ldcg(&P.st->phase);
+  const int fresh = __ldcg(&P.st->fresh_p);
+  const KrylovDesc d = *P.d;
+  const int n = d.n;
+  const int stride = gridDim.x * kVT;
+  double v[1] = {0.0};
+  if (ph == kPhaseRun && !fresh) {
+    const double beta = __ldcg(&P.st->beta);
+    for (int i0 = blockIdx.x * kVT + threadIdx.x; i0 < n; i0 += kU * stride) {
+      double zi[kU], pi[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int i = i0 + u * stride;
+        if (i < n) {
+          zi[u] = __ldg(P.z + i);
+          pi[u] = P.p[i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int i = i0 + u * stride;
+        if (i < n) P.p[i] = fma(beta, pi[u], zi[u]);
+      }
+    }
+  } else if (ph == kPhaseCheck) {
+    for (int i = blockIdx.x * kVT + threadIdx.x; i < n; i += stride) {
+      const double ti = d.b[i] - row_dot(d.rowptr, d.col, d.val, d.x, i);
+      P.r[i] = ti;
+      v[0] = fma(ti, ti, v[0]);
+    }
+    block_sums<kVT, 1>(v, sm.red);
+    if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
+  }
+  if (!last_block_arrive(&P.st->cnt[4], &sm.last)) return;
+  if (ph == kPhaseCheck) reduce_partials<kVT, 1>(P.part, kMaxBlocks, gridDim.x, v, sm.red);
+  if (threadIdx.x == 0) {
+    KrylovState& s = *P.st;
+    s.fresh_p = 0;
+    if (ph == kPhaseCheck) {
+      const double tt = v[0];
+      s.tt = tt;
+      if (sqrt(tt) <= 2.0 * s.thresh) {
+        s.status = SLA_OK;
+        s.phase = kPhaseDone;
+      } else if (!isfinite(tt)) {
+        s.status = SLA_BREAKDOWN;
+        s.phase = kPhaseDone;
+      } else if (s.restarts >= d.max_restarts || s.iters >= d.max_iter) {
+        s.status = SLA_NOT_CONVERGED;
+        s.phase = kPhaseDone;
+      } else {
+        s.restarts += 1;
+        s.rr = tt;
+        s.status = SLA_NOT_CONVERGED;
+        s.phase = kPhasePrecond;
+      }
+    }
+    s.body += 1;
+    const int cap = d.max_iter + 3 * d.max_restarts + 8;
+    if (s.phase != kPhaseDone && s.body > cap) {
+      s.status = SLA_NOT_CONVERGED;
+      s.phase = kPhaseDone;
+    }
+    if (use_cond) cudaGraphSetConditional(cond, s.phase != kPhaseDone ? 1u : 0u);
+  }
+}
+
+__global__ void __launch_bounds__(kVT) ggt_final_kernel(GPtrs P) {
+  __shared__ VSmem sm;
+  const KrylovDesc d = *P.d;
+  const int n = d.n;
+  const int zero_rhs = __ldcg(&P.st->zero_rhs);
+  const int stride = gridDim.x * kVT;
+  double v[1] = {0.0};
+  for (int i = blockIdx.x * kVT + threadIdx.x; i < n; i += stride) {
+    if (zero_rhs) {
+      d.x[i] = 0.0;
+    } else {
+      const double ti = d.b[i] - row_dot(d.rowptr, d.col, d.val, d.x, i);
+      v[0] = fma(ti, ti, v[0]);
+    }
+  }
+  block_sums<kVT, 1>(v, sm.red);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
+  if (!last_block_arrive(&P.st->cnt[5], &sm.last)) return;
+  reduce_partials<kVT, 1>(P.part, kMaxBlocks, gridDim.x, v, sm.red);
+  if (threadIdx.x == 0) {
+    const KrylovState& s = *P.st;
+    sla_info inf;
+    inf.iters = s.iters;
+    inf.status = s.phase == kPhaseDone ? s.status : SLA_NOT_CONVERGED;
+    if (s.zero_rhs) {
+      inf.rel_res = inf.true_rel_res = 0.0;
+    } else {
+      inf.rel_res = sqrt(s.rr) / s.bnorm;
+      inf.true_rel_res = sqrt(v[0]) / s.bnorm;
+    }
+    *d.info = inf;
+  }
+}
+
+struct Key {
+  int dev;
+  const void* ws;
+  int n, nnz, nnz_g, gs, gv;
+  bool operator==(const Key& o) const {
+    return dev == o.dev && ws == o.ws && n == o.n && nnz == o.nnz && nnz_g == o.nnz_g && gs == o.gs &&
+           gv == o.gv;
+  }
+};
+
+std::mutex g_mu;
+std::vector<std::pair<Key, cudaGraphExec_t>> g_cache;
+
+void grids(int dev, int n, int* gs, int* gv) {
+  static int occ_s = 0, occ_v = 0;
+  if (occ_s == 0) {
+    const int sm = (int)tma::kSmemBytes;
+    cudaFuncSetAttribute(ggt_spmv_pq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(ggt_gt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(ggt_gz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    occ_s = occupancy((const void*)ggt_gz_kernel, tma::kThreads, tma::kSmemBytes);
+  }
+  if (occ_v == 0) occ_v = occupancy((const void*)ggt_update_kernel, kVT);
+  *gs = persistent_grid(dev, (n + tma::kRows - 1) / tma::kRows, occ_s, kMaxBlocks);
+  *gv = persistent_grid(dev, ((long long)n + kVT - 1) / kVT, occ_v, kMaxBlocks);
+}
+
+int build_graph(GPtrs P, int gs, int gv, cudaGraphExec_t* exec) {
+  cudaGraph_t g = nullptr;
+  SLA_CUDA_TRY(cudaGraphCreate(&g, 0));
+  int rc = SLA_ERR_CUDA;
+  do {
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
+    cudaGraphNode_t n_init, n_while, n1, n2, n3, n4, n5, n_final;
+    void* a[] = {&P};
+    int use_cond = 1;
+    void* a5[] = {&P, &h, &use_cond};
+    const unsigned sm = (unsigned)tma::kSmemBytes;
+    if (add_kernel(g, nullptr, 0, &n_init, (const void*)ggt_init_kernel, gv, kVT, a) != cudaSuccess) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp) != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (add_kernel(body, nullptr, 0, &n1, (const void*)ggt_spmv_pq_kernel, gs, tma::kThreads, a, sm) != cudaSuccess) break;
+    if (add_kernel(body, &n1, 1, &n2, (const void*)ggt_update_kernel, gv, kVT, a) != cudaSuccess) break;
+    if (add_kernel(body, &n2, 1, &n3, (const void*)ggt_gt_kernel, gs, tma::kThreads, a, sm) != cudaSuccess) break;
+    if (add_kernel(body, &n3, 1, &n4, (const void*)ggt_gz_kernel, gs, tma::kThreads, a, sm) != cudaSuccess) break;
+    if (add_kernel(body, &n4, 1, &n5, (const void*)ggt_k3_kernel, gv, kVT, a5) != cudaSuccess) break;
+    if (add_kernel(g, &n_while, 1, &n_final, (const void*)ggt_final_kernel, gv, kVT, a) != cudaSuccess) break;
+    if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) break;
+    rc = SLA_OK;
+  } while (0);
+  cudaGraphDestroy(g);
+  return rc;
+}
+
+int run_host_loop(GPtrs P, const KrylovDesc& desc, int gs, int gv, cudaStream_t s) {
+  const size_t sm = tma::kSmemBytes;
+  ggt_write_desc_kernel<<<1, 1, 0, s>>>(P.d, desc, P.st);
+  ggt_init_kernel<<<gv, kVT, 0, s>>>(P);
+  const long long cap = (long long)desc.max_iter + 3LL * desc.max_restarts + 8;
+  for (long long body = 0; body < cap; ++body) {
+    ggt_spmv_pq_kernel<<<gs, tma::kThreads, sm, s>>>(P);
+    ggt_update_kernel<<<gv, kVT, 0, s>>>(P);
+    ggt_gt_kernel<<<gs, tma::kThreads, sm, s>>>(P);
+    ggt_gz_kernel<<<gs, tma::kThreads, sm, s>>>(P);
+    ggt_k3_kernel<<<gv, kVT, 0, s>>>(P, cudaGraphConditionalHandle(0), 0);
+    if ((body + 1) % 16 == 0) {
+      int phase = 0;
+      SLA_CUDA_TRY(cudaMemcpyAsync(&phase, &P.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SLA_CUDA_TRY(cudaStreamSynchronize(s));
+      if (phase == kPhaseDone) break;
+    }
+  }
+  ggt_final_kernel<<<gv, kVT, 0, s>>>(P);
+  SLA_CUDA_TRY(cudaGetLastError());
+  SLA_CUDA_TRY(cudaStreamSynchronize(s));
+  return SLA_OK;
+}
+
+}  // namespace
+
+KrylovDesc make_desc(const sla_csr* A, const double* val, const double* b, double* x,
+                     const sla_opts* o, sla_info* info);
+
+}  // namespace sla
+
+using namespace sla;
+
+extern "C" int32_t sla_cg_ggt(const sla_csr* A, const double* val, const sla_csr* G,
+                              const double* g_val, const sla_csr_t* GT, const double* b, double* x,
+                              const sla_opts* opts, sla_info* info, void* ws, size_t ws_bytes,
+                              void* stream) {
+  if (A == nullptr || G == nullptr || GT == nullptr) return SLA_ERR_INVALID;
+  const int n = A->n;
+  if (G->n != n || G->nnz < 0) return SLA_ERR_INVALID;
+  if (n > 0 && (G->rowptr == nullptr || GT->rowptr_t == nullptr)) return SLA_ERR_INVALID;
+  if (G->nnz > 0 && (G->col == nullptr || g_val == nullptr || GT->col_t == nullptr ||
+                     GT->perm_t == nullptr))
+    return SLA_ERR_INVALID;
+  const GgtLayout L = ggt_layout(n > 0 ? n : 0, G->nnz);
+  int rc = validate_solve_args(A, val, b, x, opts, info, ws, ws_bytes, L.total);
+  if (rc != SLA_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) return write_info(info, sla_info{0, SLA_OK, 0.0, 0.0}, s);
+  KrylovDesc d = make_desc(A, val, b, x, opts, info);
+  d.precond = SLA_PRECOND_GGT;
+  d.g_rowptr = G->rowptr;
+  d.g_col = G->col;
+  d.g_val = g_val;
+  d.nnz_g = G->nnz;
+  d.rowptr_t = GT->rowptr_t;
+  d.col_t = GT->col_t;
+  d.perm_t = GT->perm_t;
+  char* base = (char*)ws;
+  GPtrs P;
+  P.d = (KrylovDesc*)(base + L.desc);
+  P.st = (KrylovState*)(base + L.state);
+  P.part = (double*)(base + L.part);
+  P.r = (double*)(base + L.r);
+  P.z = (double*)(base + L.z);
+  P.p = (double*)(base + L.p);
+  P.q = (double*)(base + L.q);
+  P.t = (double*)(base + L.t);
+  P.gtv = (double*)(base + L.gtv);
+  const int dev = current_device();
+  int gs, gv;
+  grids(dev, n, &gs, &gv);
+  if (opts->flags & SLA_FLAG_HOST_LOOP) return run_host_loop(P, d, gs, gv, s);
+  Key key{dev, ws, n, A->nnz, G->nnz, gs, gv};
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& e : g_cache)
+      if (e.first == key) exec = e.second;
+    if (exec == nullptr) {
+      rc = build_graph(P, gs, gv, &exec);
+      if (rc != SLA_OK) return rc;
+      if (g_cache.size() >= 64) {
+        SLA_CUDA_TRY(cudaDeviceSynchronize());
+        for (auto& e : g_cache) cudaGraphExecDestroy(e.second);
+        g_cache.clear();
+      }
+      g_cache.push_back({key, exec});
+    }
+  }
+  ggt_write_desc_kernel<<<1, 1, 0, s>>>(P.d, d, P.st);
+  SLA_CUDA_TRY(cudaGetLastError());
+  SLA_CUDA_TRY(cudaGraphLaunch(exec, s));
+  return SLA_OK;
+}

@@ -33,10 +33,16 @@ struct KrylovDesc {
   sla_info* info;
   double rtol, atol;
   int max_iter, max_restarts, precond, use_x0;
-  // CSR of A^T for the BiCGStab adjoint (unused by CG)
+  // CSR of A^T for the BiCGStab adjoint (unused by CG); for G G^T PCG the
+  // CSR of G^T (perm_t into g_val)
   const int* rowptr_t;
   const int* col_t;
   const int* perm_t;
+  // lower-triangular factor G of M^{-1} = G G^T (precond SLA_PRECOND_GGT)
+  const int* g_rowptr;
+  const int* g_col;
+  const double* g_val;
+  int nnz_g, pad_g;
 };
 
 // Device-side solver scalars.  Counters are reset by the last block of the
@@ -45,6 +51,7 @@ struct KrylovState {
   double rho, pq, rr, bnorm, thresh, alpha, beta, omega;
   double rho_prev, tt, ts, ss;
   int iters, status, phase, restarts, body, zero_rhs, bad_diag, err;
+  int fresh_p, pad2;
   unsigned cnt[8];
 };
 
@@ -90,6 +97,29 @@ constexpr BiLayout bicg_layout(int n) {
 // Batched solves (sla_batched.cu); argument = total rows of the batch.
 size_t batched_ws_bytes(long long total_rows);
 
+// G G^T-preconditioned CG: descriptor, state, partials, r, z, p, q, t, then
+// the values of G^T (nnz_g doubles).
+struct GgtLayout {
+  size_t desc, state, part, r, z, p, q, t, gtv, total;
+};
+
+constexpr GgtLayout ggt_layout(int n, int nnz_g) {
+  GgtLayout L{};
+  size_t o = 0;
+  const size_t vec = al256(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  L.desc = o;  o += al256(sizeof(KrylovDesc));
+  L.state = o; o += al256(sizeof(KrylovState));
+  L.part = o;  o += al256(sizeof(double) * kMaxBlocks * kPartSlots);
+  L.r = o;     o += vec;
+  L.z = o;     o += vec;
+  L.p = o;     o += vec;
+  L.q = o;     o += vec;
+  L.t = o;     o += vec;
+  L.gtv = o;   o += al256(sizeof(double) * (size_t)(nnz_g > 0 ? nnz_g : 1));
+  L.total = o;
+  return L;
+}
+
 // Pattern utilities (sla_pattern.cu).
 size_t transpose_ws_bytes(int n, int nnz);
 size_t coo_ws_bytes(int n, long long m);
@@ -119,6 +149,9 @@ inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
       return true;
     case SLA_WS_COO:
       *out = coo_ws_bytes(n, nnz);
+      return true;
+    case SLA_WS_CG_GGT:
+      *out = ggt_layout(n, nnz).total;  // nnz = entries of G
       return true;
     case SLA_WS_BATCHED:
       *out = batched_ws_bytes((long long)n * (batch > 0 ? batch : 1));

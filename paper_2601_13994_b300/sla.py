@@ -614,3 +614,34 @@ def solve_batched(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, strict: b
     """Differentiable batched SPD solve on a shared pattern: val [B, nnz],
     b [B, n] -> x [B, n]."""
     return BatchedSolve.apply(val, b, A, kw, strict)
+
+
+# ---------------------------------------------------------------------------
+# CG with a factored preconditioner M^{-1} = G G^T
+# ---------------------------------------------------------------------------
+
+def cg_ggt(A: CSRMatrix, val: torch.Tensor, G: CSRMatrix, g_val: torch.Tensor, b: torch.Tensor, *,
+           rtol: float = 1e-10, atol: float = 0.0, max_iter: int | None = None, x0: torch.Tensor | None = None,
+           max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True):
+    """PCG with z = G (G^T r), G lower triangular (CSR pattern G, values
+    g_val).  The CSR of G^T is computed once per pattern and cached."""
+    _need(val, torch.float64, A.device, "val", A.nnz)
+    _need(g_val, torch.float64, A.device, "g_val", G.nnz)
+    _need(b, torch.float64, A.device, "b", A.n)
+    if G.n != A.n:
+        raise ValueError("G must be n x n")
+    transpose_of(G)
+    x = torch.empty(A.n, dtype=torch.float64, device=A.device) if out is None else out
+    use_x0 = 0
+    if x0 is not None:
+        if x0.data_ptr() != x.data_ptr():
+            x.copy_(x0)
+        use_x0 = 1
+    info = torch.empty((1, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
+    o = _opts(rtol, atol, max_iter, max_restarts, "jacobi", use_x0, A.n, graph)
+    ws = workspace(L.SLA_WS_CG_GGT, A.n, G.nnz, 1, A.device)
+    L.check("sla_cg_ggt", L.lib().sla_cg_ggt(
+        ctypes.byref(A.c), val.data_ptr(), ctypes.byref(G.c), g_val.data_ptr(), ctypes.byref(G._transpose_c),
+        b.data_ptr(), x.data_ptr(), ctypes.byref(o), info.data_ptr(), ws.data_ptr(), ws.numel(),
+        _stream_ptr(A.device)))
+    return x, SolveInfo(info)
