@@ -194,6 +194,103 @@ int32_t sla_cg_ggt(const sla_csr* A, const double* val, const sla_csr* G,
                    size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ */
+/* Learned factor G (message-passing network; the paper names learned    */
+/* preconditioners as future work, Sec. 5, without a design)             */
+/* ------------------------------------------------------------------ */
+/* Network: width 32, BF16 weights (W arguments: __nv_bfloat16 bit patterns,
+ * row-major [M x K]), FP32 accumulation and activations, FP32 master weights
+ * for training.  All arrays are device memory; node arrays are row-major
+ * [n x width].  Every reduction is deterministic. */
+
+/* d = diag(A) (FP64 [n]); e[k] = A_ij / sqrt(d_i d_j) (FP32 [nnz]); node
+ * features F [n x 3] = (sum_{j!=i} |e_ij|, sum_{j!=i} e_ij, deg_i / 8). */
+int32_t sla_mp_features(const sla_csr* A, const double* val, double* d,
+                        float* e, float* F, void* stream);
+
+/* CSR of tril(A) (diagonal included): g_rowptr [n+1], g_col / g_src
+ * [capacity nnz]; g_src[k] = index in A of entry k; *nnz_g (device int32)
+ * receives the count.  Workspace: sla_tril_pattern_ws(n) bytes. */
+int32_t sla_tril_pattern(const sla_csr* A, int32_t* g_rowptr, int32_t* g_col,
+                         int32_t* g_src, int32_t* nnz_g, void* ws,
+                         size_t ws_bytes, void* stream);
+size_t sla_tril_pattern_ws(int32_t n);
+
+/* Y = [X1 | X2] W^T + bias (K1 + K2 <= 64 inputs, M <= 96 outputs); Ypre
+ * (optional) receives that; Y = relu(.) if relu, plus R (optional residual
+ * [n x M]). */
+int32_t sla_mp_dense_fwd(int32_t n, int32_t K1, const float* X1, int32_t K2,
+                         const float* X2, int32_t M, const void* W_bf16,
+                         const float* bias, const float* R, int32_t relu,
+                         float* Ypre, float* Y, void* stream);
+
+/* dX = base + dY W[:, col0 : col0 + K] (W has wstride columns; base
+ * optional [n x K]). */
+int32_t sla_mp_dense_bwdx(int32_t n, int32_t M, const float* dY, int32_t K,
+                          const void* W_bf16, int32_t col0, int32_t wstride,
+                          const float* base, float* dX, void* stream);
+
+/* dW [M x (K1+K2)] = dY^T [X1 | X2], db [M] = column sums of dY (optional):
+ * per-block partials reduced in a fixed order.  Workspace:
+ * sla_mp_dense_bwdw_ws(M, K1 + K2) bytes. */
+int32_t sla_mp_dense_bwdw(int32_t n, int32_t M, const float* dY, int32_t K1,
+                          const float* X1, int32_t K2, const float* X2,
+                          float* dW, float* db, void* ws, size_t ws_bytes,
+                          void* stream);
+size_t sla_mp_dense_bwdw_ws(int32_t M, int32_t K);
+
+/* out = dY * (pre > 0), elementwise over count entries. */
+int32_t sla_mp_relu_mask(int64_t count, const float* dY, const float* pre,
+                         float* out, void* stream);
+
+/* Agg_i (+)= sum_{j != i} e_ij X_j over the pattern of A (X, Agg [n x 32]);
+ * for symmetric A this operator is its own transpose, which the backward
+ * pass uses. */
+int32_t sla_mp_aggregate(const sla_csr* A, const float* e, const float* X,
+                         float* Agg, int32_t accumulate, void* stream);
+
+/* Head on the tril pattern, PQR = [P | Q | R] rows [n x 96]:
+ *   off-diagonal (i,j): theta = v . relu(P_i + Q_j + ue e_ij), g = theta / sqrt(d_i)
+ *   diagonal:           theta = vd . relu(R_i),                g = exp(theta) / sqrt(d_i)
+ * theta [nnz_g] FP32, g_val [nnz_g] FP64. */
+int32_t sla_mp_head_fwd(int32_t n, const int32_t* g_rowptr, const int32_t* g_col,
+                        const int32_t* g_src, const float* e, const double* d,
+                        const float* PQR, const float* ue, const float* v,
+                        const float* vd, float* theta, double* g_val,
+                        void* stream);
+
+/* Backward of the head for dG = dloss/dg_val: dtheta [nnz_g], dPQR [n x 96],
+ * grads [96] = (dv, due, dvd).  gt_* is the CSR of the transposed tril
+ * pattern (sla_csr_transpose: gt_row = its column array, i.e. the row of
+ * each entry in G).  Workspace: sla_mp_head_bwd_ws(n) bytes. */
+int32_t sla_mp_head_bwd(int32_t n, const int32_t* g_rowptr, const int32_t* g_col,
+                        const int32_t* g_src, const int32_t* gt_rowptr,
+                        const int32_t* gt_row, const int32_t* gt_perm,
+                        const float* e, const double* d, const float* PQR,
+                        const float* ue, const float* v, const float* vd,
+                        const double* g_val, const double* dG, float* dtheta,
+                        float* dPQR, float* grads, void* ws, size_t ws_bytes,
+                        void* stream);
+size_t sla_mp_head_bwd_ws(int32_t n);
+
+/* Training loss of the factor on one system (FP64):
+ *   loss[0] = (x* - G G^T u)^T A (x* - G G^T u) / (x*^T u),  loss[1] = -2 / (x*^T u)
+ * with x* = A^{-1} u, and dG = dloss/dg_val on the pattern of G
+ * (g_i s_j + u_i h_j with s = G^T u, g = -2 A e / (x*^T u), h = G^T g).
+ * Workspace: sla_ggt_loss_ws(n) bytes. */
+int32_t sla_ggt_loss_grad(const sla_csr* A, const double* val, const sla_csr* G,
+                          const double* g_val, const sla_csr_t* GT,
+                          const double* u, const double* xstar, double* loss,
+                          double* dG, void* ws, size_t ws_bytes, void* stream);
+size_t sla_ggt_loss_ws(int32_t n);
+
+/* Adam on FP32 master weights (step t >= 1; clip > 0 clips each gradient
+ * entry), writing the BF16 copy the kernels read. */
+int32_t sla_adam_step(int32_t np, float* p, const float* g, float* m, float* v,
+                      float lr, float b1, float b2, float eps, int32_t t,
+                      float clip, void* p_bf16, void* stream);
+int32_t sla_to_bf16(int32_t np, const float* p, void* p_bf16, void* stream);
+
+/* ------------------------------------------------------------------ */
 /* BiCGStab for nonsymmetric A (van der Vorst 1992; the paper's GPU      */
 /* iterative backend offers it for nonsymmetric systems, Sec. 1 and 3.1) */
 /* ------------------------------------------------------------------ */

@@ -270,6 +270,11 @@ int validate_solve_args(const sla_csr* A, const double* val, const double* b, co
                         const sla_opts* o, const sla_info* info, const void* ws, size_t ws_bytes,
                         size_t need);
 
+// Device-wide exclusive scan of int32 (sla_pattern.cu): tmp needs
+// scan_tmp_ints(n) ints; *total (device, may be null) receives the sum.
+long long scan_tmp_ints(long long n);
+int device_exclusive_scan(const int* in, long long n, int* out, int* tmp, int* total, cudaStream_t s);
+
 // SpMV kernel family chosen once per process: the TMA-pipelined tiles
 // (default) or the register-staged tiles (environment SLA_SPMV_KERNEL=tile).
 bool use_tma_spmv();

@@ -376,6 +376,12 @@ PatternLayout pattern_layout(long long m, int n) {
 }  // namespace
 
 size_t transpose_ws_bytes(int n, int nnz) { return pattern_layout(nnz, n).total; }
+
+long long scan_tmp_ints(long long n) { return scan_tiles(n) + 1; }
+
+int device_exclusive_scan(const int* in, long long n, int* out, int* tmp, int* total, cudaStream_t s) {
+  return exclusive_scan(in, n, out, tmp, total, s);
+}
 size_t coo_ws_bytes(int n, long long m) { return pattern_layout(m, n).total; }
 
 }  // namespace sla

@@ -1,0 +1,104 @@
+"""Learned factored preconditioner: kernels against the FP64 oracle
+(oracle/mpnn.py), and what training gains over Jacobi-PCG."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mpnn as OM
+from paper_2601_13994_b300 import inputs as I
+from paper_2601_13994_b300 import learned as LP
+from paper_2601_13994_b300 import sla
+from tests.gpu_util import csr, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_params(model):
+    """The exact values the kernels read: BF16 weight matrices, FP32 vectors."""
+    pb = model.params_numpy(bf16=True)
+    pf = model.params_numpy(bf16=False)
+    return {k: (pb[k] if pb[k].ndim == 2 else pf[k]) for k in pf}
+
+
+def test_zero_head_gives_the_jacobi_factor_exactly():
+    rp, c, v = I.diffusion2d_random(24, 3)
+    model = LP.LearnedPreconditioner(seed=0)
+    G, gv = model.factor(csr(rp, c), to_dev(v))
+    grp, gcol, og = OM.forward(oracle_params(model), rp, c, v)
+    g, o = gv.cpu().numpy(), og.numpy()
+    assert np.array_equal(G.rowptr.cpu().numpy(), grp) and np.array_equal(G.col.cpu().numpy(), gcol)
+    # G = D^{-1/2} (off-diagonal zero) to rounding: within 2 ulps of the oracle
+    relerr = np.abs(g - o) / np.where(o != 0, np.abs(o), 1.0)
+    assert relerr.max() <= 4.5e-16, relerr.max()
+    rows = np.repeat(np.arange(len(grp) - 1), np.diff(grp))
+    assert not g[rows != gcol].any()
+
+
+@pytest.mark.parametrize("mat", ["var2d", "var3d", "fem"])
+def test_forward_and_gradients_match_oracle(mat):
+    if mat == "var2d":
+        rp, c, v = I.diffusion2d_random(20, 4, 1.5)
+    elif mat == "var3d":
+        rp, c, v = I.diffusion3d_random(7, 5)
+    else:
+        rp, c, v = I.fem_p1_laplacian(16, 7)
+    n = len(rp) - 1
+    model = LP.LearnedPreconditioner(seed=1)
+    # a non-zero head so that every parameter matters
+    model.view("v").copy_(torch.linspace(-0.3, 0.3, 32, device="cuda"))
+    model.view("vd").copy_(torch.linspace(0.2, -0.2, 32, device="cuda"))
+    model._sync_bf16()
+    A = csr(rp, c)
+    vt = to_dev(v)
+    gr = model.graph(A, vt)
+    gv = model.forward(gr).cpu().numpy()
+    P = oracle_params(model)
+    _, _, og = OM.forward(P, rp, c, v)
+    assert rel(gv, og.numpy()) <= 1e-5
+    b = np.random.default_rng(0).standard_normal(n)
+    xs, _ = oracle.pcg(rp, c, v, b, rtol=1e-13)
+    Lg = float(model.loss_grad(gr, to_dev(b), to_dev(xs)))
+    model.backward(gr)
+    Lo, grads, _ = OM.loss_and_grads(P, rp, c, v, b, xs)
+    assert abs(Lg - Lo) <= 1e-4 * abs(Lo)
+    for k, go in grads.items():
+        gk = model.view(k, "g").double().cpu().numpy()
+        assert rel(gk, go) <= 2e-3, (k, rel(gk, go))
+
+
+def test_loss_gradient_wrt_g_matches_oracle():
+    import torch as T
+    rp, c, v = I.diffusion2d_random(12, 6)
+    n = len(rp) - 1
+    model = LP.LearnedPreconditioner(seed=2)
+    model.view("v").fill_(0.1)
+    model._sync_bf16()
+    gr = model.graph(csr(rp, c), to_dev(v))
+    gv = model.forward(gr).cpu().numpy()
+    b = np.random.default_rng(1).standard_normal(n)
+    xs, _ = oracle.pcg(rp, c, v, b, rtol=1e-13)
+    model.loss_grad(gr, to_dev(b), to_dev(xs))
+    dG = gr.dG[:gr.nnz_g].cpu().numpy()
+    g = T.tensor(gv, requires_grad=True)
+    L = OM.loss(gr.G.rowptr.cpu().numpy(), gr.G.col.cpu().numpy(), g, rp, c, v, b, xs)
+    L.backward()
+    assert rel(dG, g.grad.numpy()) <= 1e-12
+
+
+def test_training_beats_jacobi_on_unseen_system():
+    torch.manual_seed(0)
+    model = LP.LearnedPreconditioner(seed=3)
+    hist = LP.train(model, systems=16, steps=300, lr=3e-3, n_lo=32, n_hi=64, log_every=50)
+    assert hist[-1] < hist[0]
+    rp, c, v = I.diffusion2d_random(96, 990001, 1.5)   # unseen size and seed
+    A = csr(rp, c)
+    vt = to_dev(v)
+    b = to_dev(I.rhs_uniform(len(rp) - 1, 5))
+    x, info, fb = model.solve(A, vt, b, rtol=1e-8)
+    xj, ij = sla.cg(A, vt, b, rtol=1e-8)
+    torch.cuda.synchronize()
+    assert info.status == 0 and not fb
+    assert info.true_rel_res <= 2e-8
+    assert info.iters < ij.iters
+    assert rel(x.cpu().numpy(), xj.cpu().numpy()) <= 1e-6

@@ -417,3 +417,64 @@ def test_adjoint_agrees_with_naive_autograd_through_cg():
     # explains the paper's 6.8e-4 the same way); it bounds the naive path, so
     # only its order of magnitude is checked here
     assert np.linalg.norm(gv - vt.grad.numpy()) / np.linalg.norm(gv) <= 10 * paper["grad_A_rel_err"]
+
+
+# ---------------------------------------------------------------- learned factor (MPNN) oracle
+
+def test_mpnn_zero_head_is_jacobi_factor():
+    from oracle import mpnn
+    rp, c, v = I.diffusion2d_random(9, 1)
+    P = mpnn.init_params(0, zero_head=True)
+    grp, gcol, gv = mpnn.forward(P, rp, c, v)
+    n = len(rp) - 1
+    d = np.diag(dense(rp, c, v))
+    G = dense(grp, gcol, gv.numpy(), n)
+    assert np.allclose(G, np.diag(1 / np.sqrt(d)), rtol=0, atol=1e-15)
+    # and the factor has exactly the pattern of tril(A)
+    A = dense(rp, c, v)
+    assert np.array_equal(dense(grp, gcol, np.ones(len(gcol)), n) != 0, np.tril(A) != 0)
+
+
+def test_mpnn_loss_zero_for_exact_factor_and_gradcheck():
+    import torch
+    from oracle import mpnn
+    rp, c, v = I.diffusion2d_random(4, 2)
+    n = len(rp) - 1
+    A = dense(rp, c, v)
+    b = np.random.default_rng(0).standard_normal(n)
+    xs = np.linalg.solve(A, b)
+    # full lower factor with G G^T = A^{-1}: loss 0
+    Gd = np.linalg.cholesky(np.linalg.inv(A))
+    rpf = np.array([0] + list(np.cumsum(np.arange(1, n + 1))), np.int32)
+    cf = np.concatenate([np.arange(i + 1) for i in range(n)]).astype(np.int32)
+    gvf = torch.tensor(np.concatenate([Gd[i, :i + 1] for i in range(n)]))
+    assert float(mpnn.loss(rpf, cf, gvf, rp, c, v, b, xs)) < 1e-24
+    # autograd of the oracle's forward + loss against central differences
+    P = mpnn.init_params(3, zero_head=False)
+
+    def f(*flat):
+        d = dict(zip(P.keys(), flat))
+        grp, gcol, gv = mpnn.forward(d, rp, c, v)
+        return mpnn.loss(grp, gcol, gv, rp, c, v, b, xs)
+
+    ts = tuple(torch.tensor(P[k] * 0.5, requires_grad=True) for k in P)
+    assert torch.autograd.gradcheck(f, ts, eps=1e-6, atol=1e-6, rtol=1e-5, fast_mode=True)
+
+
+def test_mpnn_permutation_equivariance():
+    from oracle import mpnn
+    rp, c, v = I.diffusion2d_random(5, 3)
+    n = len(rp) - 1
+    A = dense(rp, c, v)
+    P = mpnn.init_params(4, zero_head=False)
+    grp, gcol, gv = mpnn.forward(P, rp, c, v)
+    G = dense(grp, gcol, gv.numpy(), n)
+    # reverse the order of the unknowns: tril <-> triu, so compare the symmetric part of the
+    # message-passing embedding through the diagonal of G, which is order independent
+    perm = np.random.default_rng(1).permutation(n)
+    Ap = A[np.ix_(perm, perm)]
+    S = sp.csr_matrix(Ap)
+    S.sort_indices()
+    grp2, gcol2, gv2 = mpnn.forward(P, S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data)
+    G2 = dense(grp2, gcol2, gv2.numpy(), n)
+    assert np.allclose(np.diag(G2), np.diag(G)[perm], rtol=1e-12, atol=0)
