@@ -257,6 +257,41 @@ def extra_rows(dev, args, peak):
                                    "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
                                    "fp64_tflops": fl / (ms / 1e3) / 1e12,
                                    "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+    out["learned_vs_jacobi"] = learned_vs_jacobi(dev)
+    return out
+
+
+def learned_vs_jacobi(dev, systems=48, steps=800, lr=3e-3, n_lo=64, n_hi=128, evals=None):
+    """Config 5: train the learned G G^T preconditioner (seeded, on systems the
+    library's CG solves), then time PCG to rtol 1e-8 with it and with Jacobi on
+    unseen systems; the FP64 true residual is checked by the solver."""
+    import torch
+
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import learned as LP
+    from paper_2601_13994_b300 import sla
+    model = LP.LearnedPreconditioner(device=dev, seed=0)
+    t0 = time.perf_counter()
+    hist = LP.train(model, systems=systems, steps=steps, lr=lr, n_lo=n_lo, n_hi=n_hi, log_every=max(1, steps // 8))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    out = {"train": {"systems": systems, "steps": steps, "grid": [n_lo, n_hi], "seconds": t_train,
+                     "loss_first": hist[0], "loss_last": hist[-1]}}
+    evals = evals or [("2d_1024_sigma1", lambda: I.diffusion2d_random(1024, 900001, 1.0)),
+                      ("3d_128_sigma1", lambda: I.diffusion3d_random(128, 900002, 1.0))]
+    for name, gen in evals:
+        rp, c, v = gen()
+        A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+        vt = torch.from_numpy(v).to(dev)
+        bt = torch.from_numpy(I.rhs_uniform(len(rp) - 1, 77)).to(dev)
+        ms_j, (xj, ij) = _time(lambda: sla.cg(A, vt, bt, rtol=1e-8))
+        ms_f, fac = _time(lambda: model.factor(A, vt))
+        ms_g, (xg, ig) = _time(lambda: sla.cg_ggt(A, vt, fac[0], fac[1], bt, rtol=1e-8))
+        out[name] = {"jacobi_s": ms_j / 1e3, "jacobi_iters": ij.iters, "learned_s": ms_g / 1e3,
+                     "learned_iters": ig.iters, "learned_status": ig.status,
+                     "learned_true_rel_res": ig.true_rel_res, "factor_s": ms_f / 1e3,
+                     "iters_ratio": ij.iters / max(1, ig.iters), "speedup_solve": ms_j / ms_g,
+                     "speedup_with_factor": ms_j / (ms_g + ms_f)}
     return out
 
 

@@ -2,18 +2,25 @@
 //
 // Algorithm 1 (P = 1) with z = G (G^T r).  G is lower triangular (for the
 // learned preconditioner it lives on the pattern of tril(A)); applying it
-// as two SpMVs keeps M SPD for any nonsingular G.  One iteration is five
+// as two SpMVs keeps M SPD for any nonsingular G.  One iteration is four
 // kernels in the graph's WHILE body:
 //
 //   K1  q = A p, partial p.q                    -> alpha
+//       (phase CHECK: r = b - A x, the true residual, and the restart rule)
 //   K2  x += alpha p, r -= alpha q, partial r.r -> iteration count
-//   GT  t = G^T r          (CSR of G^T, values gathered once per solve)
-//   GZ  z = G t, partial r.z                    -> convergence, beta
-//   K3  p = z + beta p   (or the true-residual check / restart)
+//   GT  t = G^T r, partial t.t                  -> convergence, beta
+//   GZ  p = G t + beta p   (p = G t right after a (re)start)
 //
-// Phase PRECOND (start and after a restart) runs only GT and GZ, which then
-// also sets p = z and rho = r.z.  Algorithmic bytes per iteration:
-// 12 nnz + 4(n+1) + 2 (12 nnz_g + 4(n+1)) + 128 n.
+// r.z = r^T G G^T r = ||G^T r||^2, so the preconditioned inner product comes
+// from GT's epilogue, and since beta is known before GZ starts, z = G t is
+// folded into the p update and never stored.  The loop condition is set
+// once per body: by GT's last block, or by K1's when it ends the solve.  The factor's values are
+// held in FP32 (converted once per solve; the network produces FP32 values
+// anyway) and widened exactly inside the SpMVs: the preconditioner is the
+// fixed SPD operator G32 G32^T, while the recurrence and the residual check
+// stay FP64.  Phase PRECOND (start and after a restart) runs only GT and GZ.
+// Algorithmic bytes per iteration: 12 nnz + 4(n+1) + 2 (8 nnz_g + 4(n+1))
+// + 96 n.
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -33,8 +40,17 @@ struct GPtrs {
   KrylovDesc* d;
   KrylovState* st;
   double* part;
-  double *r, *z, *p, *q, *t, *gtv;
+  double *r, *z, *p, *q, *t;
+  float *gv, *gtv;
 };
+
+// FP32 copy of a factor value, subnormals flushed (the widening in the
+// SpMVs maps them to zero, so both operators see the same value).
+__device__ __forceinline__ float f32_of(double v) {
+  float f = __double2float_rn(v);
+  if (fabsf(f) < 1.17549435e-38f) f = 0.0f;
+  return f;
+}
 
 struct VSmem {
   double red[4 * kVT + 4];
@@ -55,8 +71,10 @@ __global__ void __launch_bounds__(kVT) ggt_init_kernel(GPtrs P) {
   const KrylovDesc d = *P.d;
   const int n = d.n;
   const int stride = gridDim.x * kVT;
-  for (long long k = blockIdx.x * (long long)kVT + threadIdx.x; k < d.nnz_g; k += stride)
-    P.gtv[k] = __ldg(d.g_val + __ldg(d.perm_t + k));
+  for (long long k = blockIdx.x * (long long)kVT + threadIdx.x; k < d.nnz_g; k += stride) {
+    P.gv[k] = f32_of(__ldg(d.g_val + k));
+    P.gtv[k] = f32_of(__ldg(d.g_val + __ldg(d.perm_t + k)));
+  }
   double acc[2] = {0.0, 0.0};
   for (int i = blockIdx.x * kVT + threadIdx.x; i < n; i += stride) {
     const double ax = d.use_x0 ? row_dot(d.rowptr, d.col, d.val, d.x, i) : 0.0;
@@ -95,20 +113,46 @@ __global__ void __launch_bounds__(kVT) ggt_init_kernel(GPtrs P) {
   }
 }
 
-// K1: q = A p, p.q -> alpha (RUN only)
-__global__ void __launch_bounds__(tma::kThreads, 2) ggt_spmv_pq_kernel(GPtrs P) {
+// Ends the loop: marks the solve done and clears the WHILE condition.
+__device__ __forceinline__ void finish(KrylovState& s, int status, cudaGraphConditionalHandle cond,
+                                       int use_cond) {
+  s.status = status;
+  s.phase = kPhaseDone;
+  if (use_cond) cudaGraphSetConditional(cond, 0u);
+}
+
+// K1: RUN: q = A p, p.q -> alpha.  CHECK: r = b - A x (true residual) ->
+// done, or a restart through phase PRECOND.  DONE at entry: clear the loop
+// condition (nothing else runs in this body).
+__global__ void __launch_bounds__(tma::kThreads, tma::kMinBlocks)
+ggt_spmv_pq_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ __align__(128) unsigned char dsm[];
   tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
-  if (__ldcg(&P.st->phase) != kPhaseRun) return;
+  const int ph = __ldcg(&P.st->phase);
+  if (ph == kPhaseDone) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && use_cond) cudaGraphSetConditional(cond, 0u);
+    return;
+  }
+  if (ph != kPhaseRun && ph != kPhaseCheck) return;
   const KrylovDesc d = *P.d;
-  double* __restrict__ q = P.q;
-  double pq = 0.0;
-  tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, P.p, P.p, sm, &P.st->err,
-                     [&](int row, double y, double prow) {
-                       q[row] = y;
-                       pq = fma(prow, y, pq);
-                     });
-  double v[1] = {pq};
+  double acc = 0.0;
+  if (ph == kPhaseRun) {
+    double* __restrict__ q = P.q;
+    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, P.p, P.p, sm, &P.st->err,
+                       [&](int row, double y, double prow) {
+                         q[row] = y;
+                         acc = fma(prow, y, acc);
+                       });
+  } else {
+    double* __restrict__ r = P.r;
+    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, d.x, d.b, sm, &P.st->err,
+                       [&](int row, double y, double brow) {
+                         const double ti = brow - y;
+                         r[row] = ti;
+                         acc = fma(ti, ti, acc);
+                       });
+  }
+  double v[1] = {acc};
   block_sums<tma::kThreads, 1>(v, sm.red);
   if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
   if (!last_block_arrive(&P.st->cnt[1], &sm.last)) return;
@@ -116,16 +160,24 @@ __global__ void __launch_bounds__(tma::kThreads, 2) ggt_spmv_pq_kernel(GPtrs P) 
   if (threadIdx.x == 0) {
     KrylovState& s = *P.st;
     if (__ldcg(&s.err) != 0) {
-      s.status = SLA_ERR_TIMEOUT;
-      s.phase = kPhaseDone;
-    } else if (!isfinite(v[0])) {
-      s.status = SLA_BREAKDOWN;
-      s.phase = kPhaseDone;
-    } else if (!(v[0] > 0.0)) {
-      s.status = SLA_NOT_SPD;
-      s.phase = kPhaseDone;
+      finish(s, SLA_ERR_TIMEOUT, cond, use_cond);
+    } else if (ph == kPhaseRun) {
+      if (!isfinite(v[0])) finish(s, SLA_BREAKDOWN, cond, use_cond);
+      else if (!(v[0] > 0.0)) finish(s, SLA_NOT_SPD, cond, use_cond);
+      else s.alpha = s.rho / v[0];
     } else {
-      s.alpha = s.rho / v[0];
+      const double tt = v[0];
+      s.tt = tt;
+      if (sqrt(tt) <= 2.0 * s.thresh) finish(s, SLA_OK, cond, use_cond);
+      else if (!isfinite(tt)) finish(s, SLA_BREAKDOWN, cond, use_cond);
+      else if (s.restarts >= d.max_restarts || s.iters >= d.max_iter)
+        finish(s, SLA_NOT_CONVERGED, cond, use_cond);
+      else {
+        s.restarts += 1;
+        s.rr = tt;
+        s.status = SLA_NOT_CONVERGED;
+        s.phase = kPhasePrecond;
+      }
     }
   }
 }
@@ -174,36 +226,23 @@ __global__ void __launch_bounds__(kVT) ggt_update_kernel(GPtrs P) {
   }
 }
 
-// GT: t = G^T r (RUN and PRECOND)
-__global__ void __launch_bounds__(tma::kThreads, 2) ggt_gt_kernel(GPtrs P) {
+// GT: t = G^T r and ||t||^2 = r.z; decisions (RUN: convergence and beta;
+// PRECOND: rho and a fresh p)
+__global__ void __launch_bounds__(tma::kThreads, tma::kMinBlocks)
+ggt_gt_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ __align__(128) unsigned char dsm[];
-  tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
+  tma::SmemT<float>& sm = *reinterpret_cast<tma::SmemT<float>*>(dsm);
   const int ph = __ldcg(&P.st->phase);
   if (ph != kPhaseRun && ph != kPhasePrecond) return;
   const KrylovDesc d = *P.d;
   double* __restrict__ t = P.t;
-  tma::spmv_pipeline(d.n, d.nnz_g, d.rowptr_t, d.col_t, P.gtv, P.r, nullptr, sm, &P.st->err,
-                     [&](int row, double y, double) { t[row] = y; });
-}
-
-// GZ: z = G t, r.z; decisions (RUN: convergence and beta; PRECOND: p = z, rho)
-__global__ void __launch_bounds__(tma::kThreads, 2) ggt_gz_kernel(GPtrs P) {
-  extern __shared__ __align__(128) unsigned char dsm[];
-  tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
-  const int ph = __ldcg(&P.st->phase);
-  if (ph != kPhaseRun && ph != kPhasePrecond) return;
-  const KrylovDesc d = *P.d;
-  double* __restrict__ z = P.z;
-  double* __restrict__ p = P.p;
-  const bool pre = ph == kPhasePrecond;
-  double rz = 0.0;
-  tma::spmv_pipeline(d.n, d.nnz_g, d.g_rowptr, d.g_col, d.g_val, P.t, P.r, sm, &P.st->err,
-                     [&](int row, double y, double rrow) {
-                       z[row] = y;
-                       if (pre) p[row] = y;
-                       rz = fma(rrow, y, rz);
+  double tt = 0.0;
+  tma::spmv_pipeline(d.n, d.nnz_g, d.rowptr_t, d.col_t, (const float*)P.gtv, P.r, nullptr, sm, &P.st->err,
+                     [&](int row, double y, double) {
+                       t[row] = y;
+                       tt = fma(y, y, tt);
                      });
-  double v[1] = {rz};
+  double v[1] = {tt};
   block_sums<tma::kThreads, 1>(v, sm.red);
   if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
   if (!last_block_arrive(&P.st->cnt[3], &sm.last)) return;
@@ -214,7 +253,7 @@ __global__ void __launch_bounds__(tma::kThreads, 2) ggt_gz_kernel(GPtrs P) {
     if (__ldcg(&s.err) != 0) {
       s.status = SLA_ERR_TIMEOUT;
       s.phase = kPhaseDone;
-    } else if (pre) {
+    } else if (ph == kPhasePrecond) {
       s.rho = trz;
       s.fresh_p = 1;
       s.status = SLA_NOT_CONVERGED;
@@ -241,84 +280,36 @@ __global__ void __launch_bounds__(tma::kThreads, 2) ggt_gz_kernel(GPtrs P) {
       } else {
         s.beta = trz / s.rho;
         s.rho = trz;
+        s.fresh_p = 0;
         if (s.iters >= d.max_iter) {
           s.status = SLA_NOT_CONVERGED;
           s.phase = kPhaseDone;
         }
       }
     }
-  }
-}
-
-// K3: p = z + beta p (unless p was just reset), or the true-residual check
-__global__ void __launch_bounds__(kVT)
-ggt_k3_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
-  __shared__ VSmem sm;
-  const int ph = __ldcg(&P.st->phase);
-  const int fresh = __ldcg(&P.st->fresh_p);
-  const KrylovDesc d = *P.d;
-  const int n = d.n;
-  const int stride = gridDim.x * kVT;
-  double v[1] = {0.0};
-  if (ph == kPhaseRun && !fresh) {
-    const double beta = __ldcg(&P.st->beta);
-    for (int i0 = blockIdx.x * kVT + threadIdx.x; i0 < n; i0 += kU * stride) {
-      double zi[kU], pi[kU];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int i = i0 + u * stride;
-        if (i < n) {
-          zi[u] = __ldg(P.z + i);
-          pi[u] = P.p[i];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int i = i0 + u * stride;
-        if (i < n) P.p[i] = fma(beta, pi[u], zi[u]);
-      }
-    }
-  } else if (ph == kPhaseCheck) {
-    for (int i = blockIdx.x * kVT + threadIdx.x; i < n; i += stride) {
-      const double ti = d.b[i] - row_dot(d.rowptr, d.col, d.val, d.x, i);
-      P.r[i] = ti;
-      v[0] = fma(ti, ti, v[0]);
-    }
-    block_sums<kVT, 1>(v, sm.red);
-    if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
-  }
-  if (!last_block_arrive(&P.st->cnt[4], &sm.last)) return;
-  if (ph == kPhaseCheck) reduce_partials<kVT, 1>(P.part, kMaxBlocks, gridDim.x, v, sm.red);
-  if (threadIdx.x == 0) {
-    KrylovState& s = *P.st;
-    s.fresh_p = 0;
-    if (ph == kPhaseCheck) {
-      const double tt = v[0];
-      s.tt = tt;
-      if (sqrt(tt) <= 2.0 * s.thresh) {
-        s.status = SLA_OK;
-        s.phase = kPhaseDone;
-      } else if (!isfinite(tt)) {
-        s.status = SLA_BREAKDOWN;
-        s.phase = kPhaseDone;
-      } else if (s.restarts >= d.max_restarts || s.iters >= d.max_iter) {
-        s.status = SLA_NOT_CONVERGED;
-        s.phase = kPhaseDone;
-      } else {
-        s.restarts += 1;
-        s.rr = tt;
-        s.status = SLA_NOT_CONVERGED;
-        s.phase = kPhasePrecond;
-      }
-    }
+    // hard cap on loop bodies (each advances the iteration count or a
+    // restart); only fires if the state machine is broken
     s.body += 1;
-    const int cap = d.max_iter + 3 * d.max_restarts + 8;
-    if (s.phase != kPhaseDone && s.body > cap) {
+    if (s.phase != kPhaseDone && s.body > d.max_iter + 3 * d.max_restarts + 8) {
       s.status = SLA_NOT_CONVERGED;
       s.phase = kPhaseDone;
     }
     if (use_cond) cudaGraphSetConditional(cond, s.phase != kPhaseDone ? 1u : 0u);
   }
+}
+
+// GZ: p = G t + beta p (p = G t right after a (re)start); RUN only, after GT
+__global__ void __launch_bounds__(tma::kThreads, tma::kMinBlocks) ggt_gz_kernel(GPtrs P) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  tma::SmemT<float>& sm = *reinterpret_cast<tma::SmemT<float>*>(dsm);
+  if (__ldcg(&P.st->phase) != kPhaseRun) return;
+  // after a (re)start p holds stale memory (possibly NaN): do not read it
+  const bool fresh = __ldcg(&P.st->fresh_p) != 0;
+  const double beta = fresh ? 0.0 : __ldcg(&P.st->beta);
+  const KrylovDesc d = *P.d;
+  double* __restrict__ p = P.p;
+  tma::spmv_pipeline(d.n, d.nnz_g, d.g_rowptr, d.g_col, (const float*)P.gv, P.t, fresh ? nullptr : p, sm,
+                     &P.st->err, [&](int row, double y, double prow) { p[row] = fma(beta, prow, y); });
 }
 
 __global__ void __launch_bounds__(kVT) ggt_final_kernel(GPtrs P) {
@@ -371,11 +362,11 @@ std::vector<std::pair<Key, cudaGraphExec_t>> g_cache;
 void grids(int dev, int n, int* gs, int* gv) {
   static int occ_s = 0, occ_v = 0;
   if (occ_s == 0) {
-    const int sm = (int)tma::kSmemBytes;
-    cudaFuncSetAttribute(ggt_spmv_pq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(ggt_gt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(ggt_gz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    occ_s = occupancy((const void*)ggt_gz_kernel, tma::kThreads, tma::kSmemBytes);
+    cudaFuncSetAttribute(ggt_spmv_pq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tma::kSmemBytes);
+    cudaFuncSetAttribute(ggt_gt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::kSmemBytesF32);
+    cudaFuncSetAttribute(ggt_gz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::kSmemBytesF32);
+    occ_s = occupancy((const void*)ggt_spmv_pq_kernel, tma::kThreads, tma::kSmemBytes);
   }
   if (occ_v == 0) occ_v = occupancy((const void*)ggt_update_kernel, kVT);
   *gs = persistent_grid(dev, (n + tma::kRows - 1) / tma::kRows, occ_s, kMaxBlocks);
@@ -389,11 +380,11 @@ int build_graph(GPtrs P, int gs, int gv, cudaGraphExec_t* exec) {
   do {
     cudaGraphConditionalHandle h;
     if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
-    cudaGraphNode_t n_init, n_while, n1, n2, n3, n4, n5, n_final;
+    cudaGraphNode_t n_init, n_while, n1, n2, n3, n4, n_final;
     void* a[] = {&P};
     int use_cond = 1;
-    void* a5[] = {&P, &h, &use_cond};
-    const unsigned sm = (unsigned)tma::kSmemBytes;
+    void* ac[] = {&P, &h, &use_cond};
+    const unsigned sm = (unsigned)tma::kSmemBytes, sm32 = (unsigned)tma::kSmemBytesF32;
     if (add_kernel(g, nullptr, 0, &n_init, (const void*)ggt_init_kernel, gv, kVT, a) != cudaSuccess) break;
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
@@ -402,11 +393,10 @@ int build_graph(GPtrs P, int gs, int gv, cudaGraphExec_t* exec) {
     cp.conditional.size = 1;
     if (cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp) != cudaSuccess) break;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if (add_kernel(body, nullptr, 0, &n1, (const void*)ggt_spmv_pq_kernel, gs, tma::kThreads, a, sm) != cudaSuccess) break;
+    if (add_kernel(body, nullptr, 0, &n1, (const void*)ggt_spmv_pq_kernel, gs, tma::kThreads, ac, sm) != cudaSuccess) break;
     if (add_kernel(body, &n1, 1, &n2, (const void*)ggt_update_kernel, gv, kVT, a) != cudaSuccess) break;
-    if (add_kernel(body, &n2, 1, &n3, (const void*)ggt_gt_kernel, gs, tma::kThreads, a, sm) != cudaSuccess) break;
-    if (add_kernel(body, &n3, 1, &n4, (const void*)ggt_gz_kernel, gs, tma::kThreads, a, sm) != cudaSuccess) break;
-    if (add_kernel(body, &n4, 1, &n5, (const void*)ggt_k3_kernel, gv, kVT, a5) != cudaSuccess) break;
+    if (add_kernel(body, &n2, 1, &n3, (const void*)ggt_gt_kernel, gs, tma::kThreads, ac, sm32) != cudaSuccess) break;
+    if (add_kernel(body, &n3, 1, &n4, (const void*)ggt_gz_kernel, gs, tma::kThreads, a, sm32) != cudaSuccess) break;
     if (add_kernel(g, &n_while, 1, &n_final, (const void*)ggt_final_kernel, gv, kVT, a) != cudaSuccess) break;
     if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) break;
     rc = SLA_OK;
@@ -416,16 +406,15 @@ int build_graph(GPtrs P, int gs, int gv, cudaGraphExec_t* exec) {
 }
 
 int run_host_loop(GPtrs P, const KrylovDesc& desc, int gs, int gv, cudaStream_t s) {
-  const size_t sm = tma::kSmemBytes;
+  const size_t sm = tma::kSmemBytes, sm32 = tma::kSmemBytesF32;
   ggt_write_desc_kernel<<<1, 1, 0, s>>>(P.d, desc, P.st);
   ggt_init_kernel<<<gv, kVT, 0, s>>>(P);
   const long long cap = (long long)desc.max_iter + 3LL * desc.max_restarts + 8;
   for (long long body = 0; body < cap; ++body) {
-    ggt_spmv_pq_kernel<<<gs, tma::kThreads, sm, s>>>(P);
+    ggt_spmv_pq_kernel<<<gs, tma::kThreads, sm, s>>>(P, cudaGraphConditionalHandle(0), 0);
     ggt_update_kernel<<<gv, kVT, 0, s>>>(P);
-    ggt_gt_kernel<<<gs, tma::kThreads, sm, s>>>(P);
-    ggt_gz_kernel<<<gs, tma::kThreads, sm, s>>>(P);
-    ggt_k3_kernel<<<gv, kVT, 0, s>>>(P, cudaGraphConditionalHandle(0), 0);
+    ggt_gt_kernel<<<gs, tma::kThreads, sm32, s>>>(P, cudaGraphConditionalHandle(0), 0);
+    ggt_gz_kernel<<<gs, tma::kThreads, sm32, s>>>(P);
     if ((body + 1) % 16 == 0) {
       int phase = 0;
       SLA_CUDA_TRY(cudaMemcpyAsync(&phase, &P.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -483,7 +472,8 @@ extern "C" int32_t sla_cg_ggt(const sla_csr* A, const double* val, const sla_csr
   P.p = (double*)(base + L.p);
   P.q = (double*)(base + L.q);
   P.t = (double*)(base + L.t);
-  P.gtv = (double*)(base + L.gtv);
+  P.gv = (float*)(base + L.gv);
+  P.gtv = (float*)(base + L.gtv);
   const int dev = current_device();
   int gs, gv;
   grids(dev, n, &gs, &gv);

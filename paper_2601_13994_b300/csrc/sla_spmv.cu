@@ -25,7 +25,7 @@ spmv_tiles_kernel(int n, const int* __restrict__ rowptr, const int* __restrict__
 // Wait-budget flag of the TMA kernel (set only if a bounded wait ran out).
 __device__ int g_spmv_err = 0;
 
-__global__ void __launch_bounds__(tma::kThreads, 2)
+__global__ void __launch_bounds__(tma::kThreads, tma::kMinBlocks)
 spmv_tma_kernel(int n, int nnz, const int* __restrict__ rowptr, const int* __restrict__ col,
                 const double* __restrict__ val, const double* __restrict__ x,
                 double* __restrict__ y) {

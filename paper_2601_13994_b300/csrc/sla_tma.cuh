@@ -7,18 +7,25 @@
 // consumer warps then sum one row per thread from shared memory (one FP64
 // FMA per entry, no shuffles) and release the stage on a second mbarrier.
 // The producer runs up to kStages tiles ahead, so ~90 KB per block are in
-// flight without registers or extra threads.
+// flight without registers or extra threads; its 32 lanes load the row
+// bounds of 32 tiles at once, so a tile costs it no global round trip.
+//
+// (A warp-specialised variant -- separate gather warps storing x[col[k]]
+// into shared memory for the FMA warps -- was measured 1.3x slower at
+// 16.7 M rows: each stage then waits for two latencies in sequence, and the
+// extra 16 KB per stage leaves one block per SM.)
 //
 // Bulk copies need 16-byte aligned addresses and sizes: the copied entry
-// range is widened down/up to multiples of 4 (int32) / 2 (float64) entries
-// but never past the end of the arrays; entries outside the copied window
-// (the array tail) and tiles that do not fit a stage (too many entries, the
-// last partial tile, or misaligned base pointers) are read from global
-// memory directly, one warp per row.
+// range is widened down/up to multiples of 4 (int32) / 16 bytes (values) but
+// never past the end of the arrays; entries outside the copied window (the
+// array tail) and tiles that do not fit a stage (too many entries, the last
+// partial tile, or misaligned base pointers) are read from global memory
+// directly, one warp per row.
 //
 // Every mbarrier wait is bounded by a clock64 budget (about 2 s at the
 // highest clock); a wait that runs out sets *err and the warp leaves its
-// loop, so the kernel always terminates.
+// loop, and the producer waits (bounded) for its copies still in flight
+// before it leaves, so the kernel always terminates with no copy pending.
 #pragma once
 
 #include "sla_internal.cuh"
@@ -31,24 +38,49 @@ constexpr int kCap = 2048;                  // entries per stage
 constexpr int kStages = 4;
 constexpr int kConsumerWarps = kRows / kWarp;
 constexpr int kThreads = kRows + kWarp;     // + one producer warp
+constexpr int kMinBlocks = 2;
 constexpr long long kWaitBudgetCycles = 4000000000LL;
 
-struct Stage {
+// Matrix values are FP64, or FP32 for factors whose values carry no more
+// (the learned G); FP32 values are widened to FP64 exactly with integer bit
+// operations (to_f64), since a hardware conversion would occupy the FP64
+// pipe, the scarce unit on this part.
+template <class V>
+struct StageT {
   int rp[kRows];             // rowptr[r0 .. r0 + 256)
   int col[kCap + 8];         // entries [ka_c, kb_c)
-  double val[kCap + 4];      // entries [ka_v, kb_v)
+  V val[kCap + 8];           // entries [ka_v, kb_v)
   int hdr[8];                // mode, k1, ka_c, kb_c, ka_v, kb_v, r0, nr
 };
 
-struct Smem {
-  Stage st[kStages];
+template <class V>
+struct SmemT {
+  StageT<V> st[kStages];
   unsigned long long full[kStages];
   unsigned long long empty[kStages];
   double red[2 * kThreads + 2];  // block_sums of up to two values
   bool last;
 };
 
+using Stage = StageT<double>;
+using Smem = SmemT<double>;
 constexpr size_t kSmemBytes = sizeof(Smem);
+constexpr size_t kSmemBytesF32 = sizeof(SmemT<float>);
+static_assert(kMinBlocks * kSmemBytes <= 232448, "TMA pipeline stages exceed the shared memory of an SM");
+
+__device__ __forceinline__ double to_f64(double v) { return v; }
+
+// Exact float -> double for normal numbers, signed zero for zero/subnormal
+// inputs (callers store no subnormal values), inf/nan kept.
+__device__ __forceinline__ double to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if (ex == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long e64 = ex == 0xffu ? 2047ull : (unsigned long long)(ex + 896u);
+  const unsigned long long man = (unsigned long long)(u & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(sign | (e64 << 52) | man));
+}
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -105,28 +137,30 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 
 // Row `row` of the matrix from global memory by one warp (lane-strided
 // entries, fixed butterfly); result valid in every lane.
+template <class V>
 __device__ __forceinline__ double warp_row(const int* __restrict__ rowptr, const int* __restrict__ col,
-                                           const double* __restrict__ val,
+                                           const V* __restrict__ val,
                                            const double* __restrict__ x, int row, int lane) {
   const int a = __ldg(rowptr + row), e = __ldg(rowptr + row + 1);
   double s = 0.0;
-  for (int k = a + lane; k < e; k += kWarp) s = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
+  for (int k = a + lane; k < e; k += kWarp) s = fma(to_f64(__ldg(val + k)), __ldg(x + __ldg(col + k)), s);
   return warp_sum(s);
 }
 
 // Runs the pipelined tile loop over all rows; calls epi(row, y_row, aux_row)
 // once per row from exactly one consumer thread, where aux_row = aux[row]
-// (prefetched before the row's gathers; 0 when aux is null).  Must be called by all kThreads
-// threads of the block, with `sm` in dynamic shared memory.  The producer
-// warp returns from this function as soon as it has issued its last tile;
-// nothing after the call may rely on its values.
-template <class Epi>
+// (prefetched before the row's gathers; 0 when aux is null).  Must be called
+// by all kThreads threads of the block, with `sm` in dynamic shared memory.
+// The producer warp returns from this function as soon as its copies have
+// landed; nothing after the call may rely on its values.
+template <class V, class Epi>
 __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restrict__ rowptr,
                                               const int* __restrict__ col,
-                                              const double* __restrict__ val,
+                                              const V* __restrict__ val,
                                               const double* __restrict__ x,
-                                              const double* __restrict__ aux, Smem& sm, int* err,
+                                              const double* __restrict__ aux, SmemT<V>& sm, int* err,
                                               Epi&& epi) {
+  constexpr int kVE = 16 / (int)sizeof(V);  // values per 16 bytes
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -141,48 +175,78 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
   const bool aligned = ((reinterpret_cast<uintptr_t>(rowptr) | reinterpret_cast<uintptr_t>(col) |
                          reinterpret_cast<uintptr_t>(val)) & 15u) == 0;
   if (warp == kConsumerWarps) {
-    // ---------------- producer warp (lane 0 issues)
-    if (lane == 0) {
-      const int nnz_c = nnz & ~3, nnz_v = nnz & ~1;
-      int k = 0;
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-        const int s = k % kStages;
-        const unsigned round = (unsigned)(k / kStages);
-        if (!mbar_wait(&sm.empty[s], (round & 1u) ^ 1u, err)) break;
-        Stage& S = sm.st[s];
-        const int r0 = t * kRows;
-        const int nr = min(kRows, n - r0);
-        const int k0 = __ldg(rowptr + r0);
-        const int k1 = __ldg(rowptr + r0 + nr);
-        int mode = 1;
-        int ka_c = 0, kb_c = 0, ka_v = 0, kb_v = 0;
-        if (aligned && nr == kRows && k1 - k0 <= kCap) {
-          mode = 0;
-          ka_c = k0 & ~3;
-          kb_c = min((k1 + 3) & ~3, nnz_c);
-          if (kb_c < ka_c) kb_c = ka_c;
-          ka_v = k0 & ~1;
-          kb_v = min((k1 + 1) & ~1, nnz_v);
-          if (kb_v < ka_v) kb_v = ka_v;
-        }
-        S.hdr[0] = mode;
-        S.hdr[1] = k1;
-        S.hdr[2] = ka_c;
-        S.hdr[3] = kb_c;
-        S.hdr[4] = ka_v;
-        S.hdr[5] = kb_v;
-        S.hdr[6] = r0;
-        S.hdr[7] = nr;
-        if (mode == 0) {
-          const unsigned bc = (unsigned)(kb_c - ka_c) * 4u, bv = (unsigned)(kb_v - ka_v) * 8u;
-          mbar_arrive_expect_tx(&sm.full[s], (unsigned)(kRows * 4) + bc + bv);
-          bulk_g2s(S.rp, rowptr + r0, kRows * 4, &sm.full[s]);
-          if (bc) bulk_g2s(S.col, col + ka_c, bc, &sm.full[s]);
-          if (bv) bulk_g2s(S.val, val + ka_v, bv, &sm.full[s]);
-        } else {
-          mbar_arrive(&sm.full[s]);
-        }
+    // ---------------- producer warp
+    // The row-pointer bounds of the next 32 tiles are loaded by the 32 lanes
+    // at once; lane 0 then waits for free stages and issues the bulk copies.
+    const int nnz_c = nnz & ~3, nnz_v = nnz & ~(kVE - 1);
+    int k = 0;
+    bool ok = true;
+    for (int tb = blockIdx.x; tb < ntiles && ok; tb += 32 * gridDim.x) {
+      const int tl = tb + lane * gridDim.x;
+      int k0l = 0, k1l = 0;
+      if (tl < ntiles) {
+        const int r0 = tl * kRows;
+        k0l = __ldg(rowptr + r0);
+        k1l = __ldg(rowptr + r0 + min(kRows, n - r0));
       }
+      for (int j = 0; j < 32; ++j) {
+        const int t = tb + j * gridDim.x;
+        if (t >= ntiles) break;
+        const int k0 = __shfl_sync(0xffffffffu, k0l, j);
+        const int k1 = __shfl_sync(0xffffffffu, k1l, j);
+        int good = 1;
+        if (lane == 0) {
+          const int s = k % kStages;
+          const unsigned round = (unsigned)(k / kStages);
+          if (!mbar_wait(&sm.empty[s], (round & 1u) ^ 1u, err)) {
+            good = 0;
+          } else {
+            StageT<V>& S = sm.st[s];
+            const int r0 = t * kRows;
+            const int nr = min(kRows, n - r0);
+            int mode = 1;
+            int ka_c = 0, kb_c = 0, ka_v = 0, kb_v = 0;
+            if (aligned && nr == kRows && k1 - k0 <= kCap) {
+              mode = 0;
+              ka_c = k0 & ~3;
+              kb_c = min((k1 + 3) & ~3, nnz_c);
+              if (kb_c < ka_c) kb_c = ka_c;
+              ka_v = k0 & ~(kVE - 1);
+              kb_v = min((k1 + kVE - 1) & ~(kVE - 1), nnz_v);
+              if (kb_v < ka_v) kb_v = ka_v;
+            }
+            S.hdr[0] = mode;
+            S.hdr[1] = k1;
+            S.hdr[2] = ka_c;
+            S.hdr[3] = kb_c;
+            S.hdr[4] = ka_v;
+            S.hdr[5] = kb_v;
+            S.hdr[6] = r0;
+            S.hdr[7] = nr;
+            if (mode == 0) {
+              const unsigned bc = (unsigned)(kb_c - ka_c) * 4u;
+              const unsigned bv = (unsigned)(kb_v - ka_v) * (unsigned)sizeof(V);
+              mbar_arrive_expect_tx(&sm.full[s], (unsigned)(kRows * 4) + bc + bv);
+              bulk_g2s(S.rp, rowptr + r0, kRows * 4, &sm.full[s]);
+              if (bc) bulk_g2s(S.col, col + ka_c, bc, &sm.full[s]);
+              if (bv) bulk_g2s(S.val, val + ka_v, bv, &sm.full[s]);
+            } else {
+              mbar_arrive(&sm.full[s]);
+            }
+          }
+        }
+        if (!__shfl_sync(0xffffffffu, good, 0)) {
+          ok = false;
+          break;
+        }
+        ++k;
+      }
+    }
+    // Drain: the last (up to kStages) stages filled may still have copies in
+    // flight if the consumers gave up; wait for them before leaving.
+    if (lane == 0) {
+      for (int kk = max(0, k - kStages); kk < k; ++kk)
+        if (!mbar_wait(&sm.full[kk % kStages], (unsigned)(kk / kStages) & 1u, err)) break;
     }
     __syncwarp();
     return;
@@ -193,7 +257,7 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
     const int s = k % kStages;
     const unsigned round = (unsigned)(k / kStages);
     if (!mbar_wait(&sm.full[s], round & 1u, err)) break;
-    const Stage& S = sm.st[s];
+    const StageT<V>& S = sm.st[s];
     const int mode = S.hdr[0];
     const int r0 = S.hdr[6], nr = S.hdr[7];
     if (mode == 0) {
@@ -203,7 +267,7 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
       const int e = (tid + 1 < kRows) ? S.rp[tid + 1] : k1;
       const double acc = row_sum_batched(
           a, e, [&](int kk) { return kk < kb_c ? S.col[kk - ka_c] : __ldg(col + kk); },
-          [&](int kk) { return kk < kb_v ? S.val[kk - ka_v] : __ldg(val + kk); }, x);
+          [&](int kk) { return to_f64(kk < kb_v ? S.val[kk - ka_v] : __ldg(val + kk)); }, x);
       epi(r0 + tid, acc, av);
     } else {
       for (int rr = warp; rr < nr; rr += kConsumerWarps) {

@@ -98,9 +98,9 @@ constexpr BiLayout bicg_layout(int n) {
 size_t batched_ws_bytes(long long total_rows);
 
 // G G^T-preconditioned CG: descriptor, state, partials, r, z, p, q, t, then
-// the values of G^T (nnz_g doubles).
+// the FP32 values of G and of G^T (nnz_g floats each).
 struct GgtLayout {
-  size_t desc, state, part, r, z, p, q, t, gtv, total;
+  size_t desc, state, part, r, z, p, q, t, gv, gtv, total;
 };
 
 constexpr GgtLayout ggt_layout(int n, int nnz_g) {
@@ -115,7 +115,8 @@ constexpr GgtLayout ggt_layout(int n, int nnz_g) {
   L.p = o;     o += vec;
   L.q = o;     o += vec;
   L.t = o;     o += vec;
-  L.gtv = o;   o += al256(sizeof(double) * (size_t)(nnz_g > 0 ? nnz_g : 1));
+  L.gv = o;    o += al256(sizeof(float) * (size_t)(nnz_g > 0 ? nnz_g : 1));
+  L.gtv = o;   o += al256(sizeof(float) * (size_t)(nnz_g > 0 ? nnz_g : 1));
   L.total = o;
   return L;
 }

