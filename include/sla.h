@@ -70,6 +70,8 @@ extern "C" {
 #define SLA_WS_TRANSPOSE 4      /* sla_csr_transpose                           */
 #define SLA_WS_COO 5            /* sla_coo_to_csr (pass the COO entry count as nnz) */
 #define SLA_WS_CG_GGT 7         /* sla_cg_ggt: pass the entry count of G as nnz */
+#define SLA_WS_CG_MULTI 8       /* sla_cg_multi / sla_adjoint_backward_multi:
+                                   batch = number of right-hand sides k       */
 #define SLA_WS_BATCHED 6        /* batched CG: n = rows per system (shared
                                    pattern) or total rows with batch = 1 (list) */
 
@@ -307,6 +309,48 @@ int32_t sla_to_bf16(int32_t np, const float* p, void* p_bf16, void* stream);
 int32_t sla_bicgstab(const sla_csr* A, const double* val, const double* b,
                      double* x, const sla_opts* opts, sla_info* info,
                      void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Several right-hand sides sharing one matrix                          */
+/* ------------------------------------------------------------------ */
+
+/* Largest number of right-hand sides of sla_cg_multi. */
+#define SLA_MULTI_MAX_RHS 32
+
+/* A X = B for one SPD A and k right-hand sides (1 <= k <= SLA_MULTI_MAX_RHS):
+ * k independent CG / Jacobi-PCG solves (Algorithm 1; Jacobi per Sec. 4.1),
+ * each with its own step sizes, stopping test ||r_j|| <= max(rtol ||b_j||,
+ * atol), true-residual check and restarts exactly as sla_cg, run by the same
+ * kernels so that every iteration reads A once for all k columns.  This is
+ * the forward solve of the paper's inverse problem (Sec. 4.6) with a batch
+ * of right-hand sides.
+ *
+ * b, x: [k, n] row-major (right-hand side / solution j at b + j n, x + j n),
+ * device, caller-owned, not overlapping; x is the initial guess when
+ * opts->use_x0 = 1 and the solution on exit.  info: device array of k
+ * records.  opts->precond: SLA_PRECOND_NONE or SLA_PRECOND_JACOBI (others:
+ * SLA_ERR_INVALID).  Workspace: sla_workspace_size(SLA_WS_CG_MULTI, n, nnz,
+ * k, &bytes) (six n x W FP64 vectors, W = k rounded up to a power of two).
+ * Asynchronous on `stream` (one cached CUDA-graph launch, or a host loop
+ * with SLA_FLAG_HOST_LOOP). */
+int32_t sla_cg_multi(const sla_csr* A, const double* val, int32_t k,
+                     const double* b, double* x, const sla_opts* opts,
+                     sla_info* info, void* ws, size_t ws_bytes, void* stream);
+
+/* Adjoint backward of sla_cg_multi for symmetric A (Eq. 2-3 per column):
+ * A lambda_j = grad_x_j, grad_b_j = lambda_j, and, since the k systems share
+ * A's values, grad_val[e] = -sum_j lambda_j[row e] x_j[col e] (summed over
+ * the columns in a fixed order).  x, grad_x, grad_b: [k, n] as in
+ * sla_cg_multi; grad_b receives lambda and must not overlap x or grad_x.
+ * grad_val: [nnz] in CSR entry order (overwritten).  info: device [k],
+ * records of the adjoint solves (tolerance relative to ||grad_x_j||).
+ * Workspace: SLA_WS_CG_MULTI with batch = k.  Asynchronous on `stream`. */
+int32_t sla_adjoint_backward_multi(const sla_csr* A, const double* val,
+                                   int32_t k, const double* x,
+                                   const double* grad_x, double* grad_b,
+                                   double* grad_val, const sla_opts* opts,
+                                   sla_info* info, void* ws, size_t ws_bytes,
+                                   void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Pattern utilities                                                     */

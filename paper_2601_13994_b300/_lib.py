@@ -35,6 +35,8 @@ SLA_WS_TRANSPOSE = 4
 SLA_WS_COO = 5
 SLA_WS_BATCHED = 6
 SLA_WS_CG_GGT = 7
+SLA_WS_CG_MULTI = 8
+SLA_MULTI_MAX_RHS = 32
 
 SLA_ADJ_CG = 0
 SLA_ADJ_BICGSTAB = 1
@@ -125,6 +127,12 @@ def lib() -> ctypes.CDLL:
             L.sla_cg_ggt.argtypes = [ctypes.POINTER(SlaCsr), P, ctypes.POINTER(SlaCsr), P, ctypes.POINTER(SlaCsrT),
                                      P, P, ctypes.POINTER(SlaOpts), P, P, ctypes.c_size_t, P]
             L.sla_cg_ggt.restype = i32
+            L.sla_cg_multi.argtypes = [ctypes.POINTER(SlaCsr), P, i32, P, P, ctypes.POINTER(SlaOpts), P, P,
+                                       ctypes.c_size_t, P]
+            L.sla_cg_multi.restype = i32
+            L.sla_adjoint_backward_multi.argtypes = [ctypes.POINTER(SlaCsr), P, i32, P, P, P, P,
+                                                     ctypes.POINTER(SlaOpts), P, P, ctypes.c_size_t, P]
+            L.sla_adjoint_backward_multi.restype = i32
             L.sla_cg_noalloc.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, ctypes.POINTER(SlaOpts), P, P]
             L.sla_cg_noalloc.restype = i32
             _lib = L

@@ -121,6 +121,9 @@ constexpr GgtLayout ggt_layout(int n, int nnz_g) {
   return L;
 }
 
+// Several right-hand sides sharing one matrix (sla_multi.cu).
+size_t multi_ws_bytes(int n, int k);
+
 // Pattern utilities (sla_pattern.cu).
 size_t transpose_ws_bytes(int n, int nnz);
 size_t coo_ws_bytes(int n, long long m);
@@ -153,6 +156,9 @@ inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
       return true;
     case SLA_WS_CG_GGT:
       *out = ggt_layout(n, nnz).total;  // nnz = entries of G
+      return true;
+    case SLA_WS_CG_MULTI:
+      *out = multi_ws_bytes(n, batch);
       return true;
     case SLA_WS_BATCHED:
       *out = batched_ws_bytes((long long)n * (batch > 0 ? batch : 1));

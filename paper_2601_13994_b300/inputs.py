@@ -25,6 +25,7 @@ __all__ = [
     "poisson2d", "diffusion2d", "diffusion2d_random", "diffusion3d",
     "diffusion3d_random", "convdiff3d", "rhs_uniform", "powerlaw_matrix",
     "batched_shared_2d", "fem_p1_laplacian", "fem_list", "nnz_2d", "nnz_3d",
+    "gaussian_random_field",
 ]
 
 
@@ -300,3 +301,24 @@ def fem_list(count: int, seed0: int, n_lo: float = 1e3, n_hi: float = 5e4):
         m = max(4, int(round(math.sqrt(target / 0.9))) + 2)
         out.append(fem_p1_laplacian(m, seed0 + k))
     return out
+
+
+def gaussian_random_field(N: int, seed: int, sigma_cells: float = 8.0, std: float = 0.5) -> np.ndarray:
+    """Smooth random field on N x N cells: white noise N(0, 1) from
+    ``default_rng(seed)`` convolved with a Gaussian of standard deviation
+    ``sigma_cells`` cells (product with the Gaussian's transform under the
+    FFT, on the field extended by mirror reflection by ceil(4 sigma) cells per
+    side so that the borders do not wrap around), cropped back to N x N, then
+    shifted to zero mean and scaled to standard deviation ``std``.  The
+    log-coefficient of the inverse problem (Sec. 4.6, scaled to 512 x 512)."""
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal((N, N))
+    pad = int(math.ceil(4.0 * sigma_cells))
+    wp = np.pad(w, pad, mode="symmetric")
+    f0 = np.fft.fftfreq(wp.shape[0])
+    f1 = np.fft.fftfreq(wp.shape[1])
+    g = np.exp(-2.0 * (math.pi * sigma_cells) ** 2 * (f0[:, None] ** 2 + f1[None, :] ** 2))
+    sm = np.real(np.fft.ifft2(np.fft.fft2(wp) * g))[pad:pad + N, pad:pad + N]
+    sm = sm - sm.mean()
+    sd = sm.std()
+    return std * sm / sd if sd > 0 else sm

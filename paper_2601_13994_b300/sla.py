@@ -17,7 +17,8 @@ import torch
 from . import _lib as L
 
 __all__ = ["CSRMatrix", "SparseTensor", "SolveInfo", "spmv", "cg", "bicgstab", "solve", "adjoint_backward",
-           "grad_values", "csr_transpose", "coo_to_csr", "segment_sum", "gather_values", "default_max_iter"]
+           "grad_values", "csr_transpose", "coo_to_csr", "segment_sum", "gather_values", "default_max_iter",
+           "cg_multi", "adjoint_backward_multi", "solve_multi"]
 
 
 def _stream_ptr(device: torch.device) -> int:
@@ -614,6 +615,97 @@ def solve_batched(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, strict: b
     """Differentiable batched SPD solve on a shared pattern: val [B, nnz],
     b [B, n] -> x [B, n]."""
     return BatchedSolve.apply(val, b, A, kw, strict)
+
+
+# ---------------------------------------------------------------------------
+# Several right-hand sides sharing one matrix
+# ---------------------------------------------------------------------------
+
+def _rhs_block(t: torch.Tensor, A: CSRMatrix, name: str) -> int:
+    _need(t, torch.float64, A.device, name)
+    if t.dim() != 2 or t.shape[1] != A.n:
+        raise ValueError("%s must be [k, n] with n = %d" % (name, A.n))
+    k = t.shape[0]
+    if not 1 <= k <= L.SLA_MULTI_MAX_RHS:
+        raise ValueError("k = %d right-hand sides; 1 <= k <= %d" % (k, L.SLA_MULTI_MAX_RHS))
+    return k
+
+
+def cg_multi(A: CSRMatrix, val: torch.Tensor, B: torch.Tensor, *, rtol: float = 1e-10, atol: float = 0.0,
+             max_iter: int | None = None, precond: str = "jacobi", x0: torch.Tensor | None = None,
+             max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True):
+    """A X = B for k <= 32 right-hand sides (rows of B [k, n]) sharing one SPD
+    matrix: k independent PCG solves advanced together, A read once per
+    iteration for all of them.  Returns (X [k, n], SolveInfo over k)."""
+    _need(val, torch.float64, A.device, "val", A.nnz)
+    k = _rhs_block(B, A, "B")
+    X = torch.empty((k, A.n), dtype=torch.float64, device=A.device) if out is None else out
+    _need(X, torch.float64, A.device, "out", k * A.n)
+    use_x0 = 0
+    if x0 is not None:
+        _need(x0, torch.float64, A.device, "x0", k * A.n)
+        if x0.data_ptr() != X.data_ptr():
+            X.copy_(x0.view(k, A.n))
+        use_x0 = 1
+    info = torch.empty((k, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
+    o = _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, A.n, graph)
+    ws = workspace(L.SLA_WS_CG_MULTI, A.n, A.nnz, k, A.device)
+    L.check("sla_cg_multi", L.lib().sla_cg_multi(ctypes.byref(A.c), _ptr(val), k, _ptr(B), _ptr(X),
+                                                ctypes.byref(o), info.data_ptr(), ws.data_ptr(), ws.numel(),
+                                                _stream_ptr(A.device)))
+    return X, SolveInfo(info)
+
+
+def adjoint_backward_multi(A: CSRMatrix, val: torch.Tensor, X: torch.Tensor, grad_X: torch.Tensor, *,
+                           rtol: float = 1e-10, atol: float = 0.0, max_iter: int | None = None,
+                           precond: str = "jacobi", max_restarts: int = 2, graph: bool = True):
+    """Adjoint of cg_multi (symmetric A): A Lambda_j = grad_X_j; returns
+    (grad_B = Lambda [k, n], grad_val [nnz] summed over the columns, SolveInfo)."""
+    _need(val, torch.float64, A.device, "val", A.nnz)
+    k = _rhs_block(X, A, "X")
+    if _rhs_block(grad_X, A, "grad_X") != k:
+        raise ValueError("grad_X must have the shape of X")
+    gb = torch.empty((k, A.n), dtype=torch.float64, device=A.device)
+    gv = torch.empty(A.nnz, dtype=torch.float64, device=A.device)
+    info = torch.empty((k, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
+    o = _opts(rtol, atol, max_iter, max_restarts, precond, 0, A.n, graph)
+    ws = workspace(L.SLA_WS_CG_MULTI, A.n, A.nnz, k, A.device)
+    L.check("sla_adjoint_backward_multi", L.lib().sla_adjoint_backward_multi(
+        ctypes.byref(A.c), _ptr(val), k, _ptr(X), _ptr(grad_X), _ptr(gb), _ptr(gv), ctypes.byref(o),
+        info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(A.device)))
+    return gb, gv, SolveInfo(info)
+
+
+class MultiSolve(torch.autograd.Function):
+    """X = A^{-1} B for the rows of B [k, n], one SPD A: one multi-RHS PCG
+    forward, one multi-RHS adjoint solve and one O(k nnz) gradient pass
+    backward (Eq. 2-3 per column, the value gradients summed)."""
+
+    @staticmethod
+    def forward(ctx, val, B, A, kw, strict):
+        X, info = cg_multi(A, val.detach(), B.detach().contiguous(), **kw)
+        if strict is not None:
+            _check_batch(info, "multi-RHS forward", strict)
+        ctx.save_for_backward(val, X)
+        ctx.A, ctx.kw, ctx.strict = A, kw, strict
+        ctx.info = info
+        return X
+
+    @staticmethod
+    def backward(ctx, gX):
+        val, X = ctx.saved_tensors
+        kw = {k: v for k, v in ctx.kw.items() if k not in ("x0", "out")}
+        gb, gv, info = adjoint_backward_multi(ctx.A, val.detach(), X, gX.contiguous().to(torch.float64), **kw)
+        if ctx.strict is not None:
+            _check_batch(info, "multi-RHS adjoint", ctx.strict)
+        return gv, gb, None, None, None
+
+
+def solve_multi(A: CSRMatrix, val: torch.Tensor, B: torch.Tensor, *, strict: bool | None = True,
+                **kw) -> torch.Tensor:
+    """Differentiable X = A^{-1} B for B [k, n] (k <= 32 right-hand sides of
+    one SPD matrix), w.r.t. val (CSR order) and B."""
+    return MultiSolve.apply(val, B, A, kw, strict)
 
 
 # ---------------------------------------------------------------------------

@@ -91,3 +91,40 @@ def test_bad_arguments_rejected_without_launch():
     # x aliasing b
     assert lib.sla_cg(ctypes.byref(A3), fake, fake, fake, ctypes.byref(o3), fake,
                       ctypes.c_void_p(0x100000), 1 << 20, None) == L.SLA_ERR_INVALID
+
+
+def test_multi_rhs_arguments_rejected_without_launch():
+    lib = L.lib()
+    fake = ctypes.c_void_p(0x1000)
+    A = L.SlaCsr(10, 20, fake, fake)
+    o = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0, 0)
+    big = ctypes.c_size_t(1 << 40)
+    ws = ctypes.c_void_p(0x100000)
+    # k out of range
+    for k in (0, -1, L.SLA_MULTI_MAX_RHS + 1):
+        assert lib.sla_cg_multi(ctypes.byref(A), fake, k, fake, ctypes.c_void_p(0x2000), ctypes.byref(o), fake,
+                                ws, big, None) == L.SLA_ERR_INVALID
+    # the factored preconditioner is not offered for several right-hand sides
+    og = L.SlaOpts(1e-8, 0.0, 100, 2, 2, 0, 0)
+    assert lib.sla_cg_multi(ctypes.byref(A), fake, 4, fake, ctypes.c_void_p(0x2000), ctypes.byref(og), fake,
+                            ws, big, None) == L.SLA_ERR_INVALID
+    # b aliasing x
+    assert lib.sla_cg_multi(ctypes.byref(A), fake, 4, fake, fake, ctypes.byref(o), fake, ws, big,
+                            None) == L.SLA_ERR_INVALID
+    # workspace too small / misaligned
+    need = L.workspace_size(L.SLA_WS_CG_MULTI, 10, 20, 4)
+    assert lib.sla_cg_multi(ctypes.byref(A), fake, 4, fake, ctypes.c_void_p(0x2000), ctypes.byref(o), fake,
+                            ws, need - 1, None) == L.SLA_ERR_WORKSPACE
+    assert lib.sla_cg_multi(ctypes.byref(A), fake, 4, fake, ctypes.c_void_p(0x2000), ctypes.byref(o), fake,
+                            ctypes.c_void_p(0x100010), big, None) == L.SLA_ERR_WORKSPACE
+    # adjoint: grad_b aliasing x
+    assert lib.sla_adjoint_backward_multi(ctypes.byref(A), fake, 4, fake, ctypes.c_void_p(0x3000), fake,
+                                          ctypes.c_void_p(0x4000), ctypes.byref(o), fake, ws, big,
+                                          None) == L.SLA_ERR_INVALID
+
+
+def test_multi_rhs_workspace_grows_with_width():
+    b1 = L.workspace_size(L.SLA_WS_CG_MULTI, 1000, 5000, 1)
+    b16 = L.workspace_size(L.SLA_WS_CG_MULTI, 1000, 5000, 16)
+    b13 = L.workspace_size(L.SLA_WS_CG_MULTI, 1000, 5000, 13)
+    assert b16 == b13 > b1 and b16 >= 6 * 8 * 1000 * 16

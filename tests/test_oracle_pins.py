@@ -478,3 +478,92 @@ def test_mpnn_permutation_equivariance():
     grp2, gcol2, gv2 = mpnn.forward(P, S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data)
     G2 = dense(grp2, gcol2, gv2.numpy(), n)
     assert np.allclose(np.diag(G2), np.diag(G)[perm], rtol=1e-12, atol=0)
+
+
+# ---------------------------------------------------------------- inverse problem (Sec. 4.6)
+
+def test_inverse_assembly_theta_zero_is_poisson_and_spd():
+    """kappa = 1 puts coefficient 1 on every face, boundary faces included:
+    the unscaled 2D Poisson matrix exactly; any theta gives a symmetric
+    positive definite A (Cholesky succeeds, values equal their transpose)."""
+    import oracle.inverse as OI
+    for N in (1, 2, 7):
+        rp, c, v = OI.assemble(np.zeros((N, N)))
+        r2, c2, v2 = I.poisson2d(N)
+        assert np.array_equal(rp, r2) and np.array_equal(c, c2) and np.array_equal(v, v2)
+    th = I.gaussian_random_field(9, 5, sigma_cells=2.0)
+    rp, c, v = OI.assemble(th)
+    rpt, ct, pt = oracle.transpose(rp, c)
+    assert np.array_equal(rp, rpt) and np.array_equal(c, ct) and np.array_equal(v, v[pt])
+    np.linalg.cholesky(dense(rp, c, v))
+
+
+def test_inverse_single_cell_closed_form():
+    """One cell: four boundary faces, A = [4 kappa], x = b / (4 e^theta),
+    L = (x - x_t)^2, dL/dtheta = -2 (x - x_t) x."""
+    import oracle.inverse as OI
+    th = np.array([[0.3]])
+    b = np.array([[0.7], [-0.2]])
+    xt = np.array([[0.1], [0.05]])
+    L, g, _ = OI.loss_and_grad(th, b, xt)
+    x = b[:, 0] / (4.0 * math.exp(0.3))
+    assert abs(L - np.mean((x - xt[:, 0]) ** 2)) <= 1e-15
+    gref = np.mean(-2.0 * (x - xt[:, 0]) * x)
+    assert abs(g[0, 0] - gref) <= 1e-14 * abs(gref)
+
+
+def test_inverse_oracle_gradient_central_differences():
+    """dL/dtheta of the oracle (adjoint per right-hand side + chain rule)
+    against central differences (eps = 1e-5, Sec. 4.3) of the loss from
+    dense LU solves: random directions and single cells."""
+    import oracle.inverse as OI
+    N, k = 8, 3
+    th = I.gaussian_random_field(N, 3, sigma_cells=2.0)
+    B = I.rhs_uniform(N * N, 5, batch=k)
+    Xt = OI.solve_dense(I.gaussian_random_field(N, 4, sigma_cells=2.0), B)
+    L, g, gB = OI.loss_and_grad(th, B, Xt)
+    assert abs(L - OI.loss_dense(th, B, Xt)) <= 1e-12 * L
+    rng = np.random.default_rng(0)
+    eps = 1e-5
+    dirs = [rng.standard_normal(th.shape) for _ in range(3)]
+    for (q, p) in ((0, 0), (3, 5), (7, 7), (0, 6)):
+        e = np.zeros(th.shape)
+        e[q, p] = 1.0
+        dirs.append(e)
+    for d in dirs:
+        fd = (OI.loss_dense(th + eps * d, B, Xt) - OI.loss_dense(th - eps * d, B, Xt)) / (2 * eps)
+        an = float((g * d).sum())
+        assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(g).max())
+
+
+def test_gaussian_random_field_recipe():
+    """Zero mean, the requested standard deviation, deterministic per seed,
+    and smooth: neighbouring cells of a sigma = 8 field are highly correlated
+    while white noise is not."""
+    f = I.gaussian_random_field(64, 11)
+    assert abs(f.mean()) <= 1e-12 and abs(f.std() - 0.5) <= 1e-12
+    assert np.array_equal(f, I.gaussian_random_field(64, 11))
+    corr = np.corrcoef(f[:, 1:].ravel(), f[:, :-1].ravel())[0, 1]
+    assert corr > 0.95
+    w = I.gaussian_random_field(64, 11, sigma_cells=1e-3)
+    assert abs(np.corrcoef(w[:, 1:].ravel(), w[:, :-1].ravel())[0, 1]) < 0.1
+
+
+def test_inverse_torch_assembly_matches_oracle_on_cpu():
+    """The product's differentiable assembly (torch, here on CPU tensors)
+    against the oracle's loops: values to rounding, and its autograd chain
+    rule against the oracle's face-by-face one."""
+    import torch
+
+    import oracle.inverse as OI
+    from paper_2601_13994_b300.inverse import _selection, assemble_values
+    N = 6
+    th = I.gaussian_random_field(N, 8, sigma_cells=1.5)
+    rp, c, v = OI.assemble(th)
+    t = torch.tensor(th, requires_grad=True)
+    vt = assemble_values(t, _selection(N, "cpu"))
+    assert np.max(np.abs(vt.detach().numpy() - v)) <= 4e-16 * np.max(np.abs(v))
+    gv = np.random.default_rng(1).standard_normal(len(v))
+    vt.backward(torch.tensor(gv))
+    ref = OI.chain_theta(th, rp, c, gv)
+    assert np.max(np.abs(t.grad.numpy() - ref)) <= 1e-14 * np.max(np.abs(ref))
