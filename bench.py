@@ -258,7 +258,47 @@ def extra_rows(dev, args, peak):
                                    "fp64_tflops": fl / (ms / 1e3) / 1e12,
                                    "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
     out["learned_vs_jacobi"] = learned_vs_jacobi(dev)
+    out["inverse_512_16rhs"] = inverse_rows(dev, peak)
     return out
+
+
+def inverse_rows(dev, peak, N=512, k=16):
+    """Config 4: 2D inverse coefficient problem on 512^2 cells with 16
+    right-hand sides.  Times (a) the 16-column PCG to rtol 1e-8 at the true
+    field against 16 single-column solves of the same systems and (b) one
+    loss + gradient step (multi-RHS forward, multi-RHS adjoint, autograd
+    through the assembly) at theta = 0."""
+    import torch
+
+    from paper_2601_13994_b300 import sla
+    from paper_2601_13994_b300.inverse import InverseProblem
+    P = InverseProblem(N, k, device=dev)
+    vals = P.values(P.theta_true)
+    ms_m, (X, info) = _time(lambda: sla.cg_multi(P.A, vals, P.B, rtol=1e-8))
+    its = np.atleast_1d(info.iters)
+
+    def singles():
+        return [sla.cg(P.A, vals, P.B[j].contiguous(), rtol=1e-8) for j in range(k)]
+
+    ms_s, outs = _time(singles)
+    n, nnz = P.n, P.A.nnz
+    bpi = 12 * nnz + 4 * (n + 1) + 104 * n * k
+    gbs = bpi * int(its.max()) / (ms_m / 1e3) / 1e9
+    th0 = torch.zeros((N, N), dtype=torch.float64, device=dev)
+
+    def step():
+        t = th0.clone().requires_grad_(True)
+        L = P.loss(t)
+        L.backward()
+        return L.detach()
+
+    ms_step, L = _time(step)
+    return {"n": n, "k": k, "multi_s": ms_m / 1e3, "iters_max": int(its.max()), "iters_mean": float(its.mean()),
+            "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
+            "us_per_iter": ms_m * 1e3 / int(its.max()), "gbs_model": gbs, "frac_of_measured_hbm": gbs / peak,
+            "bytes_per_iter": bpi, "singles_s": ms_s / 1e3,
+            "singles_iters": [int(o[1].iters) for o in outs], "speedup_vs_singles": ms_s / ms_m,
+            "step_s": ms_step / 1e3, "loss_theta0": float(L)}
 
 
 def learned_vs_jacobi(dev, systems=48, steps=800, lr=3e-3, n_lo=64, n_hi=128, evals=None):

@@ -227,17 +227,19 @@ __global__ void __launch_bounds__(kVT) ggt_update_kernel(GPtrs P) {
 }
 
 // GT: t = G^T r and ||t||^2 = r.z; decisions (RUN: convergence and beta;
-// PRECOND: rho and a fresh p)
+// PRECOND: rho and a fresh p).  RPT rows of G^T per consumer thread.
+template <int RPT>
 __global__ void __launch_bounds__(tma::kThreads, tma::kMinBlocks)
 ggt_gt_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ __align__(128) unsigned char dsm[];
-  tma::SmemT<float>& sm = *reinterpret_cast<tma::SmemT<float>*>(dsm);
+  tma::SmemT<float, RPT>& sm = *reinterpret_cast<tma::SmemT<float, RPT>*>(dsm);
   const int ph = __ldcg(&P.st->phase);
   if (ph != kPhaseRun && ph != kPhasePrecond) return;
   const KrylovDesc d = *P.d;
   double* __restrict__ t = P.t;
   double tt = 0.0;
-  tma::spmv_pipeline(d.n, d.nnz_g, d.rowptr_t, d.col_t, (const float*)P.gtv, P.r, nullptr, sm, &P.st->err,
+  tma::spmv_pipeline<RPT>(d.n, d.nnz_g, d.rowptr_t, d.col_t, (const float*)P.gtv, P.r, (const double*)nullptr, sm,
+                          &P.st->err,
                      [&](int row, double y, double) {
                        t[row] = y;
                        tt = fma(y, y, tt);
@@ -299,16 +301,17 @@ ggt_gt_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
 }
 
 // GZ: p = G t + beta p (p = G t right after a (re)start); RUN only, after GT
+template <int RPT>
 __global__ void __launch_bounds__(tma::kThreads, tma::kMinBlocks) ggt_gz_kernel(GPtrs P) {
   extern __shared__ __align__(128) unsigned char dsm[];
-  tma::SmemT<float>& sm = *reinterpret_cast<tma::SmemT<float>*>(dsm);
+  tma::SmemT<float, RPT>& sm = *reinterpret_cast<tma::SmemT<float, RPT>*>(dsm);
   if (__ldcg(&P.st->phase) != kPhaseRun) return;
   // after a (re)start p holds stale memory (possibly NaN): do not read it
   const bool fresh = __ldcg(&P.st->fresh_p) != 0;
   const double beta = fresh ? 0.0 : __ldcg(&P.st->beta);
   const KrylovDesc d = *P.d;
   double* __restrict__ p = P.p;
-  tma::spmv_pipeline(d.n, d.nnz_g, d.g_rowptr, d.g_col, (const float*)P.gv, P.t, fresh ? nullptr : p, sm,
+  tma::spmv_pipeline<RPT>(d.n, d.nnz_g, d.g_rowptr, d.g_col, (const float*)P.gv, P.t, fresh ? nullptr : p, sm,
                      &P.st->err, [&](int row, double y, double prow) { p[row] = fma(beta, prow, y); });
 }
 
@@ -349,31 +352,55 @@ __global__ void __launch_bounds__(kVT) ggt_final_kernel(GPtrs P) {
 struct Key {
   int dev;
   const void* ws;
-  int n, nnz, nnz_g, gs, gv;
+  int n, nnz, nnz_g, gs, gg, gv, rpt;
   bool operator==(const Key& o) const {
     return dev == o.dev && ws == o.ws && n == o.n && nnz == o.nnz && nnz_g == o.nnz_g && gs == o.gs &&
-           gv == o.gv;
+           gg == o.gg && gv == o.gv && rpt == o.rpt;
   }
 };
+
+// The factor SpMVs take two rows per consumer thread (512-row tiles) when G
+// averages at most 4 entries per row, so that a tile still fits a stage:
+// twice the rows in flight per SM for the short rows of tril(A).
+int factor_rpt(int n, int nnz_g) { return (long long)nnz_g <= 4LL * n ? 2 : 1; }
+
+struct FactorKernels {
+  const void* gt;
+  const void* gz;
+  unsigned smem;
+};
+
+FactorKernels factor_kernels(int rpt) {
+  if (rpt == 2)
+    return FactorKernels{(const void*)ggt_gt_kernel<2>, (const void*)ggt_gz_kernel<2>,
+                         (unsigned)tma::kSmemBytesF32x2};
+  return FactorKernels{(const void*)ggt_gt_kernel<1>, (const void*)ggt_gz_kernel<1>, (unsigned)tma::kSmemBytesF32};
+}
 
 std::mutex g_mu;
 std::vector<std::pair<Key, cudaGraphExec_t>> g_cache;
 
-void grids(int dev, int n, int* gs, int* gv) {
-  static int occ_s = 0, occ_v = 0;
+void grids(int dev, int n, int rpt, int* gs, int* gg, int* gv) {
+  static int occ_s = 0, occ_v = 0, occ_g[3] = {0, 0, 0};
   if (occ_s == 0) {
     cudaFuncSetAttribute(ggt_spmv_pq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tma::kSmemBytes);
-    cudaFuncSetAttribute(ggt_gt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::kSmemBytesF32);
-    cudaFuncSetAttribute(ggt_gz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::kSmemBytesF32);
+    for (int r = 1; r <= 2; ++r) {
+      const FactorKernels f = factor_kernels(r);
+      cudaFuncSetAttribute(f.gt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem);
+      cudaFuncSetAttribute(f.gz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem);
+      occ_g[r] = occupancy(f.gt, tma::kThreads, f.smem);
+    }
     occ_s = occupancy((const void*)ggt_spmv_pq_kernel, tma::kThreads, tma::kSmemBytes);
   }
   if (occ_v == 0) occ_v = occupancy((const void*)ggt_update_kernel, kVT);
+  const int tr = tma::kRows * rpt;
   *gs = persistent_grid(dev, (n + tma::kRows - 1) / tma::kRows, occ_s, kMaxBlocks);
+  *gg = persistent_grid(dev, (n + tr - 1) / tr, occ_g[rpt], kMaxBlocks);
   *gv = persistent_grid(dev, ((long long)n + kVT - 1) / kVT, occ_v, kMaxBlocks);
 }
 
-int build_graph(GPtrs P, int gs, int gv, cudaGraphExec_t* exec) {
+int build_graph(GPtrs P, int gs, int gg, int gv, FactorKernels f, cudaGraphExec_t* exec) {
   cudaGraph_t g = nullptr;
   SLA_CUDA_TRY(cudaGraphCreate(&g, 0));
   int rc = SLA_ERR_CUDA;
@@ -384,7 +411,7 @@ int build_graph(GPtrs P, int gs, int gv, cudaGraphExec_t* exec) {
     void* a[] = {&P};
     int use_cond = 1;
     void* ac[] = {&P, &h, &use_cond};
-    const unsigned sm = (unsigned)tma::kSmemBytes, sm32 = (unsigned)tma::kSmemBytesF32;
+    const unsigned sm = (unsigned)tma::kSmemBytes;
     if (add_kernel(g, nullptr, 0, &n_init, (const void*)ggt_init_kernel, gv, kVT, a) != cudaSuccess) break;
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
@@ -395,8 +422,8 @@ int build_graph(GPtrs P, int gs, int gv, cudaGraphExec_t* exec) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     if (add_kernel(body, nullptr, 0, &n1, (const void*)ggt_spmv_pq_kernel, gs, tma::kThreads, ac, sm) != cudaSuccess) break;
     if (add_kernel(body, &n1, 1, &n2, (const void*)ggt_update_kernel, gv, kVT, a) != cudaSuccess) break;
-    if (add_kernel(body, &n2, 1, &n3, (const void*)ggt_gt_kernel, gs, tma::kThreads, ac, sm32) != cudaSuccess) break;
-    if (add_kernel(body, &n3, 1, &n4, (const void*)ggt_gz_kernel, gs, tma::kThreads, a, sm32) != cudaSuccess) break;
+    if (add_kernel(body, &n2, 1, &n3, f.gt, gg, tma::kThreads, ac, f.smem) != cudaSuccess) break;
+    if (add_kernel(body, &n3, 1, &n4, f.gz, gg, tma::kThreads, a, f.smem) != cudaSuccess) break;
     if (add_kernel(g, &n_while, 1, &n_final, (const void*)ggt_final_kernel, gv, kVT, a) != cudaSuccess) break;
     if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) break;
     rc = SLA_OK;
@@ -405,16 +432,22 @@ int build_graph(GPtrs P, int gs, int gv, cudaGraphExec_t* exec) {
   return rc;
 }
 
-int run_host_loop(GPtrs P, const KrylovDesc& desc, int gs, int gv, cudaStream_t s) {
-  const size_t sm = tma::kSmemBytes, sm32 = tma::kSmemBytesF32;
+int run_host_loop(GPtrs P, const KrylovDesc& desc, int gs, int gg, int gv, FactorKernels f, cudaStream_t s) {
+  const size_t sm = tma::kSmemBytes;
   ggt_write_desc_kernel<<<1, 1, 0, s>>>(P.d, desc, P.st);
   ggt_init_kernel<<<gv, kVT, 0, s>>>(P);
   const long long cap = (long long)desc.max_iter + 3LL * desc.max_restarts + 8;
   for (long long body = 0; body < cap; ++body) {
     ggt_spmv_pq_kernel<<<gs, tma::kThreads, sm, s>>>(P, cudaGraphConditionalHandle(0), 0);
     ggt_update_kernel<<<gv, kVT, 0, s>>>(P);
-    ggt_gt_kernel<<<gs, tma::kThreads, sm32, s>>>(P, cudaGraphConditionalHandle(0), 0);
-    ggt_gz_kernel<<<gs, tma::kThreads, sm32, s>>>(P);
+    {
+      cudaGraphConditionalHandle h0 = 0;
+      int uc = 0;
+      void* ac[] = {&P, &h0, &uc};
+      void* a[] = {&P};
+      SLA_CUDA_TRY(cudaLaunchKernel(f.gt, dim3(gg), dim3(tma::kThreads), ac, f.smem, s));
+      SLA_CUDA_TRY(cudaLaunchKernel(f.gz, dim3(gg), dim3(tma::kThreads), a, f.smem, s));
+    }
     if ((body + 1) % 16 == 0) {
       int phase = 0;
       SLA_CUDA_TRY(cudaMemcpyAsync(&phase, &P.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -475,17 +508,19 @@ extern "C" int32_t sla_cg_ggt(const sla_csr* A, const double* val, const sla_csr
   P.gv = (float*)(base + L.gv);
   P.gtv = (float*)(base + L.gtv);
   const int dev = current_device();
-  int gs, gv;
-  grids(dev, n, &gs, &gv);
-  if (opts->flags & SLA_FLAG_HOST_LOOP) return run_host_loop(P, d, gs, gv, s);
-  Key key{dev, ws, n, A->nnz, G->nnz, gs, gv};
+  const int rpt = factor_rpt(n, G->nnz);
+  const FactorKernels fk = factor_kernels(rpt);
+  int gs, gg, gv;
+  grids(dev, n, rpt, &gs, &gg, &gv);
+  if (opts->flags & SLA_FLAG_HOST_LOOP) return run_host_loop(P, d, gs, gg, gv, fk, s);
+  Key key{dev, ws, n, A->nnz, G->nnz, gs, gg, gv, rpt};
   cudaGraphExec_t exec = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto& e : g_cache)
       if (e.first == key) exec = e.second;
     if (exec == nullptr) {
-      rc = build_graph(P, gs, gv, &exec);
+      rc = build_graph(P, gs, gg, gv, fk, &exec);
       if (rc != SLA_OK) return rc;
       if (g_cache.size() >= 64) {
         SLA_CUDA_TRY(cudaDeviceSynchronize());

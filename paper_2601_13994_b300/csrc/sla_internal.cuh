@@ -117,18 +117,20 @@ __device__ __forceinline__ void reduce_partials(const double* part, int stride, 
 // x loads are issued back to back, then the FMAs run in entry order (the same
 // sequential sum as one entry at a time, so the bits do not change).  A row
 // therefore waits for one gather latency per 8 entries instead of one per
-// entry.  col_at(k) / val_at(k) read entry k (shared or global memory).
+// entry.  col_at(k) / val_at(k) read entry k (shared or global memory);
+// T is the type of x, of val_at's result and of the sum (FP64, or FP32 for
+// a preconditioner applied in single precision).
 // ------------------------------------------------------------------------
 constexpr int kGatherBatch = 8;
 
-template <class ColAt, class ValAt>
-__device__ __forceinline__ double row_sum_batched(int a, int e, ColAt&& col_at, ValAt&& val_at,
-                                                  const double* __restrict__ x) {
-  double acc = 0.0;
+template <class T, class ColAt, class ValAt>
+__device__ __forceinline__ T row_sum_batched(int a, int e, ColAt&& col_at, ValAt&& val_at,
+                                             const T* __restrict__ x) {
+  T acc = T(0);
   int k0 = a;
   for (; k0 + kGatherBatch <= e; k0 += kGatherBatch) {
     int c[kGatherBatch];
-    double v[kGatherBatch], xv[kGatherBatch];
+    T v[kGatherBatch], xv[kGatherBatch];
 #pragma unroll
     for (int j = 0; j < kGatherBatch; ++j) {
       c[j] = col_at(k0 + j);
@@ -142,7 +144,7 @@ __device__ __forceinline__ double row_sum_batched(int a, int e, ColAt&& col_at, 
   const int rem = e - k0;
   if (rem > 0) {
     int c[kGatherBatch];
-    double v[kGatherBatch], xv[kGatherBatch];
+    T v[kGatherBatch], xv[kGatherBatch];
 #pragma unroll
     for (int j = 0; j < kGatherBatch; ++j)
       if (j < rem) {

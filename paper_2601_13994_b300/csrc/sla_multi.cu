@@ -110,24 +110,46 @@ __device__ __forceinline__ void col_block_sums(double (&v)[NV], int w, double* p
   }
 }
 
-// Last block: column sums over the grid's partials, in block order, one warp
-// per (value, column); result in out[m * kMaxK + j] (shared memory).
+// Last block: column sums over the grid's partials; result in
+// out[m * kMaxK + j] (shared memory).  Each (value, column) pair gets G
+// threads (G a power of two, G * NV * w <= kMT); thread g adds blocks g,
+// g + G, ... with eight independent loads in flight, then the G partial sums
+// are added in thread order -- a fixed order for a given grid.
 template <int NV>
-__device__ __forceinline__ void col_grid_sums(const double* part, int w, int nblocks, double* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int mj = warp; mj < NV * w; mj += kMW) {
+__device__ __forceinline__ void col_grid_sums(const double* part, int w, int nblocks, double* out,
+                                              double* scratch /* kMT doubles */) {
+  const int nvw = NV * w;
+  int G = 1;
+  while (G * 2 * nvw <= kMT) G *= 2;
+  const int tid = threadIdx.x;
+  const int mj = tid / G, g = tid % G;
+  double s = 0.0;
+  if (mj < nvw) {
     const int m = mj / w, j = mj % w;
     const double* src = part + (m * kMaxK + j) * kMaxBlocks;
-    double s = 0.0;
-    for (int b = lane; b < nblocks; b += kWarp) s += __ldcg(src + b);
-    s = warp_sum(s);
-    if (lane == 0) out[m * kMaxK + j] = s;
+    int b = g;
+    for (; b + 7 * G < nblocks; b += 8 * G) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcg(src + b + u * G);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; b < nblocks; b += G) s += __ldcg(src + b);
+  }
+  scratch[tid] = s;
+  __syncthreads();
+  if (tid < nvw) {
+    double t = scratch[tid * G];
+    for (int q = 1; q < G; ++q) t += scratch[tid * G + q];
+    out[(tid / w) * kMaxK + (tid % w)] = t;
   }
   __syncthreads();
 }
 
 struct MSmem {
   double sh[kMParts * kMW * kMaxK];
+  double scratch[kMT];
   double tot[kMParts * kMaxK];
   int phase[kMaxK];
   double alpha[kMaxK];
@@ -255,7 +277,7 @@ __global__ void __launch_bounds__(kMT) multi_init_kernel(MultiPtrs P) {
   if (bad) atomicOr(&P.st->bad_diag, 1);
   col_block_sums<3>(acc, w, P.part, sm.sh);
   if (!last_block_arrive(&P.st->cnt[0], &sm.last)) return;
-  col_grid_sums<3>(P.part, w, gridDim.x, sm.tot);
+  col_grid_sums<3>(P.part, w, gridDim.x, sm.tot, sm.scratch);
   if (threadIdx.x < w) {
     const int c = threadIdx.x;
     const double tbb = sm.tot[0 * kMaxK + c], trr = sm.tot[1 * kMaxK + c], trz = sm.tot[2 * kMaxK + c];
@@ -290,6 +312,15 @@ __global__ void __launch_bounds__(kMT) multi_init_kernel(MultiPtrs P) {
 }
 
 // ---------------------------------------------------------------- K1
+// Each thread sums kRU rows of its column at once; the first kEB entries of
+// every row have their column indices, values and gathers all issued before
+// the first FMA (rows longer than kEB finish one entry at a time).  The FMA
+// loop exits at the row's end, so no padding FMA reaches the FP64 pipe.
+// (Measured at 512^2 x 16: one row per thread at four blocks per SM beats
+// two rows per thread, whose 98 registers allow only two blocks.)
+constexpr int kRU = 1;
+constexpr int kEB = 8;
+
 __global__ void __launch_bounds__(kMT) multi_spmm_kernel(MultiPtrs P) {
   __shared__ MSmem sm;
   const MultiDesc d = *P.d;
@@ -300,20 +331,67 @@ __global__ void __launch_bounds__(kMT) multi_spmm_kernel(MultiPtrs P) {
   const bool run = sm.phase[j] == kPhaseRun;
   const int i0 = (int)(((size_t)blockIdx.x * kMT + threadIdx.x) / w);
   const int rs = gridDim.x * kMT / w;
+  const int* __restrict__ rowptr = d.rowptr;
+  const int* __restrict__ col = d.col;
+  const double* __restrict__ val = d.val;
   const double* __restrict__ p = P.p;
   double* __restrict__ q = P.q;
   double pq[1] = {0.0};
   if (run) {
-    for (int i = i0; i < n; i += rs) {
-      const double s = row_dot_col(d.rowptr, d.col, d.val, p, w, i, j);
-      const size_t el = (size_t)i * w + j;
-      q[el] = s;
-      pq[0] = fma(__ldg(p + el), s, pq[0]);
+    for (int ib = i0; ib < n; ib += kRU * rs) {
+      int a[kRU], len[kRU];
+      double pi[kRU];
+#pragma unroll
+      for (int u = 0; u < kRU; ++u) {
+        const int i = ib + u * rs;
+        a[u] = 0;
+        len[u] = 0;
+        pi[u] = 0.0;
+        if (i < n) {
+          a[u] = __ldg(rowptr + i);
+          len[u] = __ldg(rowptr + i + 1) - a[u];
+          pi[u] = __ldg(p + (size_t)i * w + j);
+        }
+      }
+      int cc[kRU][kEB];
+      double vv[kRU][kEB], xx[kRU][kEB];
+#pragma unroll
+      for (int u = 0; u < kRU; ++u)
+#pragma unroll
+        for (int t = 0; t < kEB; ++t) {
+          const bool ok = t < len[u];
+          cc[u][t] = ok ? __ldg(col + a[u] + t) : 0;
+          vv[u][t] = ok ? __ldg(val + a[u] + t) : 0.0;
+        }
+#pragma unroll
+      for (int u = 0; u < kRU; ++u)
+#pragma unroll
+        for (int t = 0; t < kEB; ++t) xx[u][t] = t < len[u] ? __ldg(p + (size_t)cc[u][t] * w + j) : 0.0;
+      double acc[kRU];
+#pragma unroll
+      for (int u = 0; u < kRU; ++u) {
+        acc[u] = 0.0;
+#pragma unroll
+        for (int t = 0; t < kEB; ++t) {
+          if (t >= len[u]) break;
+          acc[u] = fma(vv[u][t], xx[u][t], acc[u]);
+        }
+        for (int kk = a[u] + kEB; kk < a[u] + len[u]; ++kk)
+          acc[u] = fma(__ldg(val + kk), __ldg(p + (size_t)__ldg(col + kk) * w + j), acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kRU; ++u) {
+        const int i = ib + u * rs;
+        if (i < n) {
+          q[(size_t)i * w + j] = acc[u];
+          pq[0] = fma(pi[u], acc[u], pq[0]);
+        }
+      }
     }
   }
   col_block_sums<1>(pq, w, P.part, sm.sh);
   if (!last_block_arrive(&P.st->cnt[1], &sm.last)) return;
-  col_grid_sums<1>(P.part, w, gridDim.x, sm.tot);
+  col_grid_sums<1>(P.part, w, gridDim.x, sm.tot, sm.scratch);
   if (threadIdx.x < w && sm.phase[threadIdx.x] == kPhaseRun) {
     MCol& s = P.st->c[threadIdx.x];
     const double tpq = sm.tot[threadIdx.x];
@@ -379,7 +457,7 @@ __global__ void __launch_bounds__(kMT) multi_update_kernel(MultiPtrs P) {
   }
   col_block_sums<2>(v, w, P.part, sm.sh);
   if (!last_block_arrive(&P.st->cnt[2], &sm.last)) return;
-  col_grid_sums<2>(P.part, w, gridDim.x, sm.tot);
+  col_grid_sums<2>(P.part, w, gridDim.x, sm.tot, sm.scratch);
   if (threadIdx.x < w && __ldcg(&P.st->c[threadIdx.x].phase) == kPhaseRun) {
     MCol& s = P.st->c[threadIdx.x];
     const double trz = sm.tot[0 * kMaxK + threadIdx.x], trr = sm.tot[1 * kMaxK + threadIdx.x];
@@ -419,9 +497,23 @@ multi_pupdate_kernel(MultiPtrs P, cudaGraphConditionalHandle cond, int use_cond)
   double v[2] = {0.0, 0.0};  // tt, rz of the check pass
   if (ph == kPhaseRun) {
     const double beta = __ldcg(&P.st->c[j].beta);
-    for (int i = i0; i < n; i += rs) {
-      const size_t el = (size_t)i * w + j;
-      P.p[el] = fma(beta, P.p[el], __ldg(P.z + el));
+    constexpr int U = 4;
+    for (int ib = i0; ib < n; ib += U * rs) {
+      double zi[U], pi[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = ib + u * rs;
+        if (i < n) {
+          const size_t el = (size_t)i * w + j;
+          zi[u] = __ldg(P.z + el);
+          pi[u] = P.p[el];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = ib + u * rs;
+        if (i < n) P.p[(size_t)i * w + j] = fma(beta, pi[u], zi[u]);
+      }
     }
   } else if (ph == kPhaseCheck) {
     for (int i = i0; i < n; i += rs) {
@@ -437,7 +529,7 @@ multi_pupdate_kernel(MultiPtrs P, cudaGraphConditionalHandle cond, int use_cond)
   }
   col_block_sums<2>(v, w, P.part, sm.sh);
   if (!last_block_arrive(&P.st->cnt[3], &sm.last)) return;
-  col_grid_sums<2>(P.part, w, gridDim.x, sm.tot);
+  col_grid_sums<2>(P.part, w, gridDim.x, sm.tot, sm.scratch);
   if (threadIdx.x < w && sm.phase[threadIdx.x] == kPhaseCheck) {
     MCol& s = P.st->c[threadIdx.x];
     const double ttt = sm.tot[0 * kMaxK + threadIdx.x], trz = sm.tot[1 * kMaxK + threadIdx.x];
@@ -505,7 +597,7 @@ __global__ void __launch_bounds__(kMT) multi_final_kernel(MultiPtrs P) {
   }
   col_block_sums<1>(v, w, P.part, sm.sh);
   if (!last_block_arrive(&P.st->cnt[4], &sm.last)) return;
-  col_grid_sums<1>(P.part, w, gridDim.x, sm.tot);
+  col_grid_sums<1>(P.part, w, gridDim.x, sm.tot, sm.scratch);
   if (threadIdx.x < d.k) {
     const MCol& s = P.st->c[threadIdx.x];
     sla_info inf;
@@ -601,19 +693,37 @@ MultiPtrs carve(void* ws, int n, int w) {
   return P;
 }
 
-int multi_grid(int dev, int n, int w) {
-  static int occ = 0;
-  if (occ == 0) occ = occupancy((const void*)multi_update_kernel, kMT);
+// Grids of the loop kernels: persistent, at most kBlocksPerSm blocks per SM
+// (any grid works: 256 threads per block keep every thread on one column).
+// Few blocks keep the last block's pass over the per-block partials short;
+// the unrolled loops keep enough loads in flight.
+constexpr int kBlocksPerSm = 4;
+struct MultiGrids {
+  int g1, g2, g3, gv;
+};
+
+MultiGrids multi_grids(int dev, int n, int w) {
+  static int o1 = 0, o2 = 0, o3 = 0, ov = 0;
+  if (o1 == 0) {
+    o1 = occupancy((const void*)multi_spmm_kernel, kMT);
+    o2 = occupancy((const void*)multi_update_kernel, kMT);
+    o3 = occupancy((const void*)multi_pupdate_kernel, kMT);
+    ov = occupancy((const void*)multi_init_kernel, kMT);
+  }
   const long long blocks = ((long long)n * w + kMT - 1) / kMT;
-  return persistent_grid(dev, blocks, occ, kMaxBlocks);
+  return MultiGrids{persistent_grid(dev, blocks, min(o1, kBlocksPerSm), kMaxBlocks),
+                    persistent_grid(dev, blocks, min(o2, kBlocksPerSm), kMaxBlocks),
+                    persistent_grid(dev, blocks, min(o3, kBlocksPerSm), kMaxBlocks),
+                    persistent_grid(dev, blocks, min(ov, kBlocksPerSm), kMaxBlocks)};
 }
 
 struct MultiKey {
   int dev;
   const void* ws;
-  int n, nnz, w, g;
+  int n, nnz, w, g1, g2, g3, gv;
   bool operator==(const MultiKey& o) const {
-    return dev == o.dev && ws == o.ws && n == o.n && nnz == o.nnz && w == o.w && g == o.g;
+    return dev == o.dev && ws == o.ws && n == o.n && nnz == o.nnz && w == o.w && g1 == o.g1 && g2 == o.g2 &&
+           g3 == o.g3 && gv == o.gv;
   }
 };
 struct MultiEntry {
@@ -624,7 +734,7 @@ std::mutex g_mmu;
 std::vector<MultiEntry> g_mcache;
 constexpr size_t kMCacheMax = 64;
 
-int build_multi_graph(MultiPtrs P, int g, cudaGraphExec_t* exec) {
+int build_multi_graph(MultiPtrs P, MultiGrids g, cudaGraphExec_t* exec) {
   cudaGraph_t gr = nullptr;
   SLA_CUDA_TRY(cudaGraphCreate(&gr, 0));
   int rc = SLA_ERR_CUDA;
@@ -633,7 +743,7 @@ int build_multi_graph(MultiPtrs P, int g, cudaGraphExec_t* exec) {
     if (cudaGraphConditionalHandleCreate(&h, gr, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
     cudaGraphNode_t n_init, n_while, n1, n2, n3, n_final;
     void* a[] = {&P};
-    if (add_kernel(gr, nullptr, 0, &n_init, (const void*)multi_init_kernel, g, kMT, a) != cudaSuccess) break;
+    if (add_kernel(gr, nullptr, 0, &n_init, (const void*)multi_init_kernel, g.gv, kMT, a) != cudaSuccess) break;
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
@@ -643,10 +753,10 @@ int build_multi_graph(MultiPtrs P, int g, cudaGraphExec_t* exec) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     int use_cond = 1;
     void* a3[] = {&P, &h, &use_cond};
-    if (add_kernel(body, nullptr, 0, &n1, (const void*)multi_spmm_kernel, g, kMT, a) != cudaSuccess) break;
-    if (add_kernel(body, &n1, 1, &n2, (const void*)multi_update_kernel, g, kMT, a) != cudaSuccess) break;
-    if (add_kernel(body, &n2, 1, &n3, (const void*)multi_pupdate_kernel, g, kMT, a3) != cudaSuccess) break;
-    if (add_kernel(gr, &n_while, 1, &n_final, (const void*)multi_final_kernel, g, kMT, a) != cudaSuccess) break;
+    if (add_kernel(body, nullptr, 0, &n1, (const void*)multi_spmm_kernel, g.g1, kMT, a) != cudaSuccess) break;
+    if (add_kernel(body, &n1, 1, &n2, (const void*)multi_update_kernel, g.g2, kMT, a) != cudaSuccess) break;
+    if (add_kernel(body, &n2, 1, &n3, (const void*)multi_pupdate_kernel, g.g3, kMT, a3) != cudaSuccess) break;
+    if (add_kernel(gr, &n_while, 1, &n_final, (const void*)multi_final_kernel, g.gv, kMT, a) != cudaSuccess) break;
     if (cudaGraphInstantiate(exec, gr, 0) != cudaSuccess) break;
     rc = SLA_OK;
   } while (0);
@@ -661,19 +771,19 @@ constexpr int kMPollEvery = 16;
 int launch_multi(const MultiDesc& d, void* ws, cudaStream_t s, int flags) {
   const MultiPtrs P = carve(ws, d.n, d.w);
   const int dev = current_device();
-  const int g = multi_grid(dev, d.n, d.w);
+  const MultiGrids g = multi_grids(dev, d.n, d.w);
   const int gt = persistent_grid(dev, (d.n + 31) / 32, 8, kMaxBlocks);
   multi_write_desc_kernel<<<1, 1, 0, s>>>(P.d, d, P.st);
   multi_interleave_kernel<<<gt, kMT, 0, s>>>(d.n, d.k, d.w, d.b, P.bi, 0);
   multi_interleave_kernel<<<gt, kMT, 0, s>>>(d.n, d.k, d.w, d.x, P.xi, d.use_x0 ? 0 : 1);
   SLA_CUDA_TRY(cudaGetLastError());
   if (flags & SLA_FLAG_HOST_LOOP) {
-    multi_init_kernel<<<g, kMT, 0, s>>>(P);
+    multi_init_kernel<<<g.gv, kMT, 0, s>>>(P);
     const long long cap = (long long)d.max_iter + 2LL * d.max_restarts + 8;
     for (long long body = 0; body < cap; ++body) {
-      multi_spmm_kernel<<<g, kMT, 0, s>>>(P);
-      multi_update_kernel<<<g, kMT, 0, s>>>(P);
-      multi_pupdate_kernel<<<g, kMT, 0, s>>>(P, cudaGraphConditionalHandle(0), 0);
+      multi_spmm_kernel<<<g.g1, kMT, 0, s>>>(P);
+      multi_update_kernel<<<g.g2, kMT, 0, s>>>(P);
+      multi_pupdate_kernel<<<g.g3, kMT, 0, s>>>(P, cudaGraphConditionalHandle(0), 0);
       if ((body + 1) % kMPollEvery == 0) {
         MultiState hs;
         SLA_CUDA_TRY(cudaMemcpyAsync(&hs, P.st, sizeof(MultiState), cudaMemcpyDeviceToHost, s));
@@ -683,9 +793,9 @@ int launch_multi(const MultiDesc& d, void* ws, cudaStream_t s, int flags) {
         if (!live) break;
       }
     }
-    multi_final_kernel<<<g, kMT, 0, s>>>(P);
+    multi_final_kernel<<<g.gv, kMT, 0, s>>>(P);
   } else {
-    MultiKey key{dev, ws, d.n, d.nnz, d.w, g};
+    MultiKey key{dev, ws, d.n, d.nnz, d.w, g.g1, g.g2, g.g3, g.gv};
     cudaGraphExec_t exec = nullptr;
     {
       std::lock_guard<std::mutex> lk(g_mmu);

@@ -31,7 +31,7 @@ spmv_tma_kernel(int n, int nnz, const int* __restrict__ rowptr, const int* __res
                 double* __restrict__ y) {
   extern __shared__ __align__(128) unsigned char dsm[];
   tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
-  tma::spmv_pipeline(n, nnz, rowptr, col, val, x, nullptr, sm, &g_spmv_err,
+  tma::spmv_pipeline(n, nnz, rowptr, col, val, x, (const double*)nullptr, sm, &g_spmv_err,
                      [&](int row, double s, double) { y[row] = s; });
 }
 

@@ -45,17 +45,17 @@ constexpr long long kWaitBudgetCycles = 4000000000LL;
 // (the learned G); FP32 values are widened to FP64 exactly with integer bit
 // operations (to_f64), since a hardware conversion would occupy the FP64
 // pipe, the scarce unit on this part.
-template <class V>
+template <class V, int RPT = 1>
 struct StageT {
-  int rp[kRows];             // rowptr[r0 .. r0 + 256)
+  int rp[kRows * RPT];       // rowptr[r0 .. r0 + 256 RPT)
   int col[kCap + 8];         // entries [ka_c, kb_c)
   V val[kCap + 8];           // entries [ka_v, kb_v)
   int hdr[8];                // mode, k1, ka_c, kb_c, ka_v, kb_v, r0, nr
 };
 
-template <class V>
+template <class V, int RPT = 1>
 struct SmemT {
-  StageT<V> st[kStages];
+  StageT<V, RPT> st[kStages];
   unsigned long long full[kStages];
   unsigned long long empty[kStages];
   double red[2 * kThreads + 2];  // block_sums of up to two values
@@ -66,6 +66,7 @@ using Stage = StageT<double>;
 using Smem = SmemT<double>;
 constexpr size_t kSmemBytes = sizeof(Smem);
 constexpr size_t kSmemBytesF32 = sizeof(SmemT<float>);
+constexpr size_t kSmemBytesF32x2 = sizeof(SmemT<float, 2>);
 static_assert(kMinBlocks * kSmemBytes <= 232448, "TMA pipeline stages exceed the shared memory of an SM");
 
 __device__ __forceinline__ double to_f64(double v) { return v; }
@@ -135,32 +136,95 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
+// A stored value in the arithmetic type X of the sum: FP64 values as they
+// are, FP32 values widened exactly for an FP64 sum or kept for an FP32 sum.
+template <class X>
+__device__ __forceinline__ X as_x(double v) { return v; }
+template <class X>
+__device__ __forceinline__ X as_x(float v);
+template <>
+__device__ __forceinline__ double as_x<double>(float v) { return to_f64(v); }
+template <>
+__device__ __forceinline__ float as_x<float>(float v) { return v; }
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_any(double v) { return warp_sum(v); }
+__device__ __forceinline__ float warp_sum_any(float v) { return warp_sum_f(v); }
+
 // Row `row` of the matrix from global memory by one warp (lane-strided
 // entries, fixed butterfly); result valid in every lane.
-template <class V>
-__device__ __forceinline__ double warp_row(const int* __restrict__ rowptr, const int* __restrict__ col,
-                                           const V* __restrict__ val,
-                                           const double* __restrict__ x, int row, int lane) {
+template <class V, class X>
+__device__ __forceinline__ X warp_row(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                      const V* __restrict__ val, const X* __restrict__ x, int row, int lane) {
   const int a = __ldg(rowptr + row), e = __ldg(rowptr + row + 1);
-  double s = 0.0;
-  for (int k = a + lane; k < e; k += kWarp) s = fma(to_f64(__ldg(val + k)), __ldg(x + __ldg(col + k)), s);
-  return warp_sum(s);
+  X s = X(0);
+  for (int k = a + lane; k < e; k += kWarp) s = fma(as_x<X>(__ldg(val + k)), __ldg(x + __ldg(col + k)), s);
+  return warp_sum_any(s);
 }
 
-// Runs the pipelined tile loop over all rows; calls epi(row, y_row, aux_row)
+// Sums of two adjacent rows whose entries are [a, m) and [m, e): the column
+// indices and values of up to 8 entries of the pair are read first, their x
+// gathers issued back to back, then each row's FMAs run in entry order with
+// explicit exits (no padding FMA reaches the FP64 pipe); pairs with more
+// than 8 entries continue one entry at a time.
+template <class X, class ColAt, class ValAt>
+__device__ __forceinline__ void two_row_sum(int a, int m, int e, ColAt&& col_at, ValAt&& val_at,
+                                            const X* __restrict__ x, X& acc0, X& acc1) {
+  constexpr int B = kGatherBatch;
+  acc0 = X(0);
+  acc1 = X(0);
+  const int cnt = e - a;
+  int c[B];
+  X v[B], xv[B];
+#pragma unroll
+  for (int j = 0; j < B; ++j)
+    if (j < cnt) {
+      c[j] = col_at(a + j);
+      v[j] = val_at(a + j);
+    }
+#pragma unroll
+  for (int j = 0; j < B; ++j)
+    if (j < cnt) xv[j] = __ldg(x + c[j]);
+  const int n0 = m - a;  // entries of the first row
+#pragma unroll
+  for (int jj = 0; jj < B; ++jj) {
+    if (jj >= n0 || jj >= cnt) break;
+    acc0 = fma(v[jj], xv[jj], acc0);
+  }
+  for (int k = a + B; k < m; ++k) acc0 = fma(val_at(k), __ldg(x + col_at(k)), acc0);
+#pragma unroll
+  for (int jj = 0; jj < B; ++jj) {
+    if (jj < n0) continue;
+    if (jj >= cnt) break;
+    acc1 = fma(v[jj], xv[jj], acc1);
+  }
+  for (int k = max(m, a + B); k < e; ++k) acc1 = fma(val_at(k), __ldg(x + col_at(k)), acc1);
+}
+
+// Runs the pipelined tile loop over all rows (tiles of 256 RPT rows, RPT
+// adjacent rows per consumer thread); calls epi(row, y_row, aux_row)
 // once per row from exactly one consumer thread, where aux_row = aux[row]
-// (prefetched before the row's gathers; 0 when aux is null).  Must be called
+// (prefetched before the row's gathers; 0 when aux is null; any element
+// type).  The sum y_row
+// is formed in the type X of x: FP64, or FP32 (values V = float) for a
+// preconditioner applied in single precision.  Must be called
 // by all kThreads threads of the block, with `sm` in dynamic shared memory.
 // The producer warp returns from this function as soon as its copies have
 // landed; nothing after the call may rely on its values.
-template <class V, class Epi>
+template <int RPT = 1, class V, class X, class Aux, class Epi>
 __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restrict__ rowptr,
                                               const int* __restrict__ col,
                                               const V* __restrict__ val,
-                                              const double* __restrict__ x,
-                                              const double* __restrict__ aux, SmemT<V>& sm, int* err,
+                                              const X* __restrict__ x,
+                                              const Aux* __restrict__ aux, SmemT<V, RPT>& sm, int* err,
                                               Epi&& epi) {
+  static_assert(RPT == 1 || RPT == 2, "one or two rows per consumer thread");
   constexpr int kVE = 16 / (int)sizeof(V);  // values per 16 bytes
+  constexpr int kTR = kRows * RPT;          // rows per tile
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -171,7 +235,7 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int ntiles = (n + kRows - 1) / kRows;
+  const int ntiles = (n + kTR - 1) / kTR;
   const bool aligned = ((reinterpret_cast<uintptr_t>(rowptr) | reinterpret_cast<uintptr_t>(col) |
                          reinterpret_cast<uintptr_t>(val)) & 15u) == 0;
   if (warp == kConsumerWarps) {
@@ -185,9 +249,9 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
       const int tl = tb + lane * gridDim.x;
       int k0l = 0, k1l = 0;
       if (tl < ntiles) {
-        const int r0 = tl * kRows;
+        const int r0 = tl * kTR;
         k0l = __ldg(rowptr + r0);
-        k1l = __ldg(rowptr + r0 + min(kRows, n - r0));
+        k1l = __ldg(rowptr + r0 + min(kTR, n - r0));
       }
       for (int j = 0; j < 32; ++j) {
         const int t = tb + j * gridDim.x;
@@ -201,12 +265,12 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
           if (!mbar_wait(&sm.empty[s], (round & 1u) ^ 1u, err)) {
             good = 0;
           } else {
-            StageT<V>& S = sm.st[s];
-            const int r0 = t * kRows;
-            const int nr = min(kRows, n - r0);
+            StageT<V, RPT>& S = sm.st[s];
+            const int r0 = t * kTR;
+            const int nr = min(kTR, n - r0);
             int mode = 1;
             int ka_c = 0, kb_c = 0, ka_v = 0, kb_v = 0;
-            if (aligned && nr == kRows && k1 - k0 <= kCap) {
+            if (aligned && nr == kTR && k1 - k0 <= kCap) {
               mode = 0;
               ka_c = k0 & ~3;
               kb_c = min((k1 + 3) & ~3, nnz_c);
@@ -226,8 +290,8 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
             if (mode == 0) {
               const unsigned bc = (unsigned)(kb_c - ka_c) * 4u;
               const unsigned bv = (unsigned)(kb_v - ka_v) * (unsigned)sizeof(V);
-              mbar_arrive_expect_tx(&sm.full[s], (unsigned)(kRows * 4) + bc + bv);
-              bulk_g2s(S.rp, rowptr + r0, kRows * 4, &sm.full[s]);
+              mbar_arrive_expect_tx(&sm.full[s], (unsigned)(kTR * 4) + bc + bv);
+              bulk_g2s(S.rp, rowptr + r0, kTR * 4, &sm.full[s]);
               if (bc) bulk_g2s(S.col, col + ka_c, bc, &sm.full[s]);
               if (bv) bulk_g2s(S.val, val + ka_v, bv, &sm.full[s]);
             } else {
@@ -257,22 +321,34 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
     const int s = k % kStages;
     const unsigned round = (unsigned)(k / kStages);
     if (!mbar_wait(&sm.full[s], round & 1u, err)) break;
-    const StageT<V>& S = sm.st[s];
+    const StageT<V, RPT>& S = sm.st[s];
     const int mode = S.hdr[0];
     const int r0 = S.hdr[6], nr = S.hdr[7];
     if (mode == 0) {
       const int k1 = S.hdr[1], ka_c = S.hdr[2], kb_c = S.hdr[3], ka_v = S.hdr[4], kb_v = S.hdr[5];
-      const double av = aux ? __ldg(aux + r0 + tid) : 0.0;
-      const int a = S.rp[tid];
-      const int e = (tid + 1 < kRows) ? S.rp[tid + 1] : k1;
-      const double acc = row_sum_batched(
-          a, e, [&](int kk) { return kk < kb_c ? S.col[kk - ka_c] : __ldg(col + kk); },
-          [&](int kk) { return to_f64(kk < kb_v ? S.val[kk - ka_v] : __ldg(val + kk)); }, x);
-      epi(r0 + tid, acc, av);
+      auto col_at = [&](int kk) { return kk < kb_c ? S.col[kk - ka_c] : __ldg(col + kk); };
+      auto val_at = [&](int kk) { return as_x<X>(kk < kb_v ? S.val[kk - ka_v] : __ldg(val + kk)); };
+      if constexpr (RPT == 1) {
+        const Aux av = aux ? __ldg(aux + r0 + tid) : Aux(0);
+        const int a = S.rp[tid];
+        const int e = (tid + 1 < kRows) ? S.rp[tid + 1] : k1;
+        const X acc = row_sum_batched(a, e, col_at, val_at, x);
+        epi(r0 + tid, acc, av);
+      } else {
+        const int i0 = 2 * tid;
+        const Aux av0 = aux ? __ldg(aux + r0 + i0) : Aux(0);
+        const Aux av1 = aux ? __ldg(aux + r0 + i0 + 1) : Aux(0);
+        const int a = S.rp[i0], m = S.rp[i0 + 1];
+        const int e = (i0 + 2 < kTR) ? S.rp[i0 + 2] : k1;
+        X acc0, acc1;
+        two_row_sum(a, m, e, col_at, val_at, x, acc0, acc1);
+        epi(r0 + i0, acc0, av0);
+        epi(r0 + i0 + 1, acc1, av1);
+      }
     } else {
       for (int rr = warp; rr < nr; rr += kConsumerWarps) {
-        const double acc = warp_row(rowptr, col, val, x, r0 + rr, lane);
-        if (lane == 0) epi(r0 + rr, acc, aux ? __ldg(aux + r0 + rr) : 0.0);
+        const X acc = warp_row(rowptr, col, val, x, r0 + rr, lane);
+        if (lane == 0) epi(r0 + rr, acc, aux ? __ldg(aux + r0 + rr) : Aux(0));
       }
     }
     __syncwarp();
