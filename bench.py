@@ -59,7 +59,58 @@ def parse():
                     help="iteration cap (bounded profiling runs; the timed numbers are then not a solve)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other rows' measurements (BiCGStab, adjoint, batched)")
+    ap.add_argument("--profile-row", choices=sorted(PROFILE_ROWS), default=None,
+                    help="run one bounded solve of another row's workload from a host loop "
+                         "(for ncu captures; default 20 iterations) and exit")
     return ap.parse_args()
+
+
+def _profile_ggt(dev, max_iter, precond):
+    """2D 1024^2 sigma = 1 (the learned preconditioner's unseen 2D system):
+    G-PCG with an untrained but non-trivial head (the kernels' cost does not
+    depend on the weights), or Jacobi-PCG."""
+    import torch
+
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import learned as LP
+    from paper_2601_13994_b300 import sla
+    rp, c, v = I.diffusion2d_random(1024, 900001, 1.0)
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    vt = torch.from_numpy(v).to(dev)
+    bt = torch.from_numpy(I.rhs_uniform(len(rp) - 1, 77)).to(dev)
+    if precond == "jacobi":
+        x, info = sla.cg(A, vt, bt, rtol=1e-8, max_iter=max_iter, graph=False)
+    else:
+        m = LP.LearnedPreconditioner(device=dev, seed=0)
+        m.view("v").fill_(0.05)
+        m._sync_bf16()
+        G, gv = m.factor(A, vt)
+        x, info = sla.cg_ggt(A, vt, G, gv, bt, rtol=1e-8, max_iter=max_iter, graph=False)
+    return {"iters": info.iters, "status": info.status}
+
+
+def _profile_multi(dev, max_iter):
+    """512^2 inverse-problem matrix at theta_true, 16 right-hand sides."""
+    import torch
+
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import sla
+    from paper_2601_13994_b300.inverse import _selection, assemble_values
+    N, k = 512, 16
+    rp, c, _ = I.poisson2d(N)
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    th = torch.from_numpy(I.gaussian_random_field(N, 4000)).to(dev)
+    vals = assemble_values(th, _selection(N, dev)).contiguous()
+    B = torch.from_numpy(I.rhs_uniform(N * N, 4001, batch=k)).to(dev)
+    X, info = sla.cg_multi(A, vals, B, rtol=1e-8, max_iter=max_iter, graph=False)
+    return {"iters": [int(i) for i in info.iters]}
+
+
+PROFILE_ROWS = {
+    "ggt_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "ggt"),
+    "jacobi_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "jacobi"),
+    "multi_512x16": _profile_multi,
+}
 
 
 def workload(N: int):
@@ -549,6 +600,13 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.profile_row is not None:
+        import torch
+        dev = torch.device("cuda", 0)
+        out = PROFILE_ROWS[args.profile_row](dev, args.max_iter or 20)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_row": args.profile_row, **out}))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -63,21 +63,25 @@ __global__ void feat_kernel(int n, const int* __restrict__ rp, const int* __rest
                             const double* __restrict__ v, const double* __restrict__ d,
                             float* __restrict__ e, float* __restrict__ F) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double sa = 0.0, ss = 0.0;
     int deg = 0;
-    const double di = d[i];
+    // e_ij = (A_ij / sqrt(d_i)) / sqrt(d_j): the FP64 part is per row (one
+    // thread per row, so each FP64 instruction serves 32 rows), the neighbour
+    // factor is FP32 -- e is stored in FP32, so its accuracy is unchanged in
+    // kind (a few FP32 ulps)
+    const double rsi = 1.0 / sqrt(d[i]);
+    float fa = 0.0f, fs = 0.0f;
     for (int k = rp[i]; k < rp[i + 1]; ++k) {
       const int j = c[k];
-      const double ek = v[k] / sqrt(di * d[j]);
-      e[k] = (float)ek;
+      const float ek = (float)(v[k] * rsi) * rsqrtf((float)d[j]);
+      e[k] = ek;
       if (j != i) {
-        sa += fabs(ek);
-        ss += ek;
+        fa += fabsf(ek);
+        fs += ek;
         ++deg;
       }
     }
-    F[3 * (size_t)i + 0] = (float)sa;
-    F[3 * (size_t)i + 1] = (float)ss;
+    F[3 * (size_t)i + 0] = fa;
+    F[3 * (size_t)i + 1] = fs;
     F[3 * (size_t)i + 2] = (float)deg / 8.0f;
   }
 }
@@ -110,6 +114,7 @@ __global__ void tril_fill_kernel(int n, const int* __restrict__ rp, const int* _
 // ------------------------------------------------------------ dense
 // Y[i, m] = b[m] + sum_k [X1 | X2][i, k] W[m, k]; Ypre = that (optional);
 // Y = (relu ? max(0, .) : .) + R[i, m] (optional).
+template <int NM>
 __global__ void __launch_bounds__(kDT) dense_fwd_kernel(int n, int K1, const float* __restrict__ X1,
                                                         int K2, const float* __restrict__ X2, int M,
                                                         const __nv_bfloat16* __restrict__ W,
@@ -117,34 +122,106 @@ __global__ void __launch_bounds__(kDT) dense_fwd_kernel(int n, int K1, const flo
                                                         const float* __restrict__ R, int relu,
                                                         float* __restrict__ Ypre,
                                                         float* __restrict__ Y) {
-  __shared__ float WsT[kMaxK * kMaxM];  // [k][m]
-  __shared__ float Xs[kTN * kMaxK];
+  // Register-blocked: thread (rg = warp, m0 = lane) owns rows rg + 8 rr
+  // (rr < 8) of a 64-row tile and columns m0 + 32 mm (mm < NM).  Inputs and
+  // weights sit in shared memory with rows padded to Kp + 4 floats (Kp = K
+  // rounded up to 4, zero-filled), so every step over 4 k is one 16-byte
+  // load of W per column (conflict-free across the warp) and one broadcast
+  // 16-byte load of X per row: 32 NM FMAs per (8 + NM) shared loads.  Each
+  // output is still the sequential sum over k = 0 .. K-1 started from the
+  // bias, as before.
+  constexpr int kRowsT = 64, kRR = kRowsT / 8;
+  __shared__ __align__(16) float Ws[kMaxM * (kMaxK + 4)];
+  __shared__ __align__(16) float Xs[kRowsT * (kMaxK + 4)];
   const int K = K1 + K2;
-  for (int idx = threadIdx.x; idx < M * K; idx += kDT) {
-    const int m = idx / K, k = idx % K;
-    WsT[k * M + m] = __bfloat162float(W[idx]);
+  const int Kp = (K + 3) & ~3;
+  const int S = Kp + 4;
+  for (int idx = threadIdx.x; idx < M * Kp; idx += kDT) {
+    const int m = idx / Kp, k = idx % Kp;
+    Ws[m * S + k] = k < K ? __bfloat162float(W[m * K + k]) : 0.0f;
   }
-  const int ntiles = (n + kTN - 1) / kTN;
+  const int m0 = threadIdx.x & 31, rg = threadIdx.x >> 5;
+  const int ntiles = (n + kRowsT - 1) / kRowsT;
+  // vector loads need 16-byte aligned rows of both inputs
+  const bool vec = (K1 % 4 == 0) && (K2 % 4 == 0) &&
+                   ((reinterpret_cast<uintptr_t>(X1) | reinterpret_cast<uintptr_t>(X2)) & 15u) == 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     __syncthreads();
-    for (int idx = threadIdx.x; idx < kTN * K; idx += kDT) {
-      const int r = idx / K, k = idx % K;
-      const int i = t * kTN + r;
-      float xv = 0.0f;
-      if (i < n) xv = k < K1 ? X1[(size_t)i * K1 + k] : X2[(size_t)i * K2 + (k - K1)];
-      Xs[idx] = xv;
+    if (vec) {
+      // 16-byte chunks, all loads of the thread issued before its stores
+      constexpr int kMaxC = kRowsT * kMaxK / 4 / kDT;  // chunks per thread
+      const int cpr = Kp / 4, nch = kRowsT * cpr;
+      float4 buf[kMaxC];
+#pragma unroll
+      for (int u = 0; u < kMaxC; ++u) {
+        const int idx = threadIdx.x + u * kDT;
+        buf[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (idx < nch) {
+          const int r = idx / cpr, k = 4 * (idx % cpr);
+          const int i = t * kRowsT + r;
+          if (i < n)
+            buf[u] = k < K1 ? *reinterpret_cast<const float4*>(X1 + (size_t)i * K1 + k)
+                            : *reinterpret_cast<const float4*>(X2 + (size_t)i * K2 + (k - K1));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kMaxC; ++u) {
+        const int idx = threadIdx.x + u * kDT;
+        if (idx < nch) *reinterpret_cast<float4*>(&Xs[(idx / cpr) * S + 4 * (idx % cpr)]) = buf[u];
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < kRowsT * Kp; idx += kDT) {
+        const int r = idx / Kp, k = idx % Kp;
+        const int i = t * kRowsT + r;
+        float xv = 0.0f;
+        if (i < n && k < K) xv = k < K1 ? X1[(size_t)i * K1 + k] : X2[(size_t)i * K2 + (k - K1)];
+        Xs[r * S + k] = xv;
+      }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < kTN * M; idx += kDT) {
-      const int r = idx / M, m = idx % M;
-      const int i = t * kTN + r;
-      if (i >= n) continue;
-      float acc = bias ? bias[m] : 0.0f;
-      for (int k = 0; k < K; ++k) acc = fmaf(Xs[r * K + k], WsT[k * M + m], acc);
-      if (Ypre) Ypre[(size_t)i * M + m] = acc;
-      float y = relu ? fmaxf(acc, 0.0f) : acc;
-      if (R) y += R[(size_t)i * M + m];
-      Y[(size_t)i * M + m] = y;
+    float acc[NM][kRR];
+#pragma unroll
+    for (int mm = 0; mm < NM; ++mm) {
+      const int m = m0 + 32 * mm;
+      const float b0 = (bias && m < M) ? bias[m] : 0.0f;
+#pragma unroll
+      for (int rr = 0; rr < kRR; ++rr) acc[mm][rr] = b0;
+    }
+    for (int k = 0; k < Kp; k += 4) {
+      float4 w[NM];
+#pragma unroll
+      for (int mm = 0; mm < NM; ++mm) {
+        const int m = min(m0 + 32 * mm, M - 1);
+        w[mm] = *reinterpret_cast<const float4*>(&Ws[m * S + k]);
+      }
+#pragma unroll
+      for (int rr = 0; rr < kRR; ++rr) {
+        const float4 xv = *reinterpret_cast<const float4*>(&Xs[(rg + 8 * rr) * S + k]);
+#pragma unroll
+        for (int mm = 0; mm < NM; ++mm) {
+          float a0 = acc[mm][rr];
+          a0 = fmaf(xv.x, w[mm].x, a0);
+          a0 = fmaf(xv.y, w[mm].y, a0);
+          a0 = fmaf(xv.z, w[mm].z, a0);
+          a0 = fmaf(xv.w, w[mm].w, a0);
+          acc[mm][rr] = a0;
+        }
+      }
+    }
+#pragma unroll
+    for (int mm = 0; mm < NM; ++mm) {
+      const int m = m0 + 32 * mm;
+      if (m >= M) continue;
+#pragma unroll
+      for (int rr = 0; rr < kRR; ++rr) {
+        const int i = t * kRowsT + rg + 8 * rr;
+        if (i >= n) continue;
+        const float a0 = acc[mm][rr];
+        if (Ypre) Ypre[(size_t)i * M + m] = a0;
+        float y = relu ? fmaxf(a0, 0.0f) : a0;
+        if (R) y += R[(size_t)i * M + m];
+        Y[(size_t)i * M + m] = y;
+      }
     }
   }
 }
@@ -262,11 +339,32 @@ __global__ void relu_mask_kernel(long long cnt, const float* __restrict__ dY, co
 __global__ void aggregate_kernel(int n, const int* __restrict__ rp, const int* __restrict__ c,
                                  const float* __restrict__ e, const float* __restrict__ X,
                                  float* __restrict__ Agg, int acc) {
+  // warp per row, lane = feature.  The row's first 8 column indices and
+  // edge values are loaded by 8 lanes at once and broadcast, and the 8
+  // neighbour rows are gathered back to back before the FMAs, which then run
+  // in entry order (the same sum as one entry at a time).
+  constexpr int B = 8;
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
     float s = acc ? Agg[(size_t)i * kW + lane] : 0.0f;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+    const int k0 = rp[i], k1 = rp[i + 1];
+    const int cnt = k1 - k0;
+    const int cl = lane < min(cnt, B) ? c[k0 + lane] : i;
+    const float el = lane < min(cnt, B) ? e[k0 + lane] : 0.0f;
+    float xs[B];
+#pragma unroll
+    for (int m = 0; m < B; ++m) {
+      const int j = __shfl_sync(0xffffffffu, cl, m);
+      xs[m] = j != i ? X[(size_t)j * kW + lane] : 0.0f;
+    }
+#pragma unroll
+    for (int m = 0; m < B; ++m) {
+      const int j = __shfl_sync(0xffffffffu, cl, m);
+      const float em = __shfl_sync(0xffffffffu, el, m);
+      if (m < cnt && j != i) s = fmaf(em, xs[m], s);
+    }
+    for (int k = k0 + B; k < k1; ++k) {
       const int j = c[k];
       if (j != i) s = fmaf(e[k], X[(size_t)j * kW + lane], s);
     }
@@ -282,41 +380,86 @@ __global__ void head_fwd_kernel(int n, const int* __restrict__ grp, const int* _
                                 const float* __restrict__ ue, const float* __restrict__ vv,
                                 const float* __restrict__ vd, float* __restrict__ theta,
                                 double* __restrict__ g_val) {
+  // warp per row, lane = hidden unit; the first 8 entries of the row have
+  // their columns, edge values and Q rows loaded back to back before the
+  // warp sums (theta only; G values in head_gval_kernel)
+  constexpr int B = 8;
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
+  (void)d;
+  (void)g_val;
   for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
     const float Pm = PQR[(size_t)i * 96 + lane];
     const float Rm = fmaxf(PQR[(size_t)i * 96 + 64 + lane], 0.0f);
     const float uem = ue[lane], vm = vv[lane], vdm = vd[lane];
-    const double sdi = sqrt(d[i]);
-    for (int kg = grp[i]; kg < grp[i + 1]; ++kg) {
+    const int k0 = grp[i], k1 = grp[i + 1];
+    const int cnt = k1 - k0;
+    const int jl = lane < min(cnt, B) ? gcol[k0 + lane] : i;
+    const float el = lane < min(cnt, B) ? e[gsrc[k0 + lane]] : 0.0f;
+    float q[B];
+#pragma unroll
+    for (int m = 0; m < B; ++m) {
+      const int j = __shfl_sync(0xffffffffu, jl, m);
+      q[m] = (m < cnt && j != i) ? PQR[(size_t)j * 96 + 32 + lane] : 0.0f;
+    }
+#pragma unroll
+    for (int m = 0; m < B; ++m) {
+      if (m >= cnt) break;
+      const int j = __shfl_sync(0xffffffffu, jl, m);
+      const float em = __shfl_sync(0xffffffffu, el, m);
+      const float th = j == i ? warp_sum_f(vdm * Rm) : warp_sum_f(vm * fmaxf(Pm + q[m] + uem * em, 0.0f));
+      if (lane == 0) theta[k0 + m] = th;
+    }
+    for (int kg = k0 + B; kg < k1; ++kg) {
       const int j = gcol[kg];
       float th;
-      double gv;
       if (j == i) {
         th = warp_sum_f(vdm * Rm);
-        gv = exp((double)th) / sdi;
       } else {
         const float pre = Pm + PQR[(size_t)j * 96 + 32 + lane] + uem * e[gsrc[kg]];
         th = warp_sum_f(vm * fmaxf(pre, 0.0f));
-        gv = (double)th / sdi;
       }
-      if (lane == 0) {
-        theta[kg] = th;
-        g_val[kg] = gv;
-      }
+      if (lane == 0) theta[kg] = th;
     }
   }
 }
 
-// Backward by rows: dtheta per entry, dP and dR rows, per-block partial
-// sums of dv, due, dvd (partial[block][0:32] dv, [32:64] due, [64:96] dvd).
+// G values from theta, one thread per row: G_ii = exp(theta_ii) / sqrt(d_i),
+// G_ij = theta_ij / sqrt(d_i).  The FP64 work is here, vectorised over rows
+// (on this part an FP64 warp instruction costs its full pipe time however
+// few lanes are active, so per-lane FP64 inside the warp-per-row head would
+// cost 32 times as much).  exp runs in FP32 (theta is FP32).
+__global__ void head_gval_kernel(int n, const int* __restrict__ grp, const int* __restrict__ gcol,
+                                 const double* __restrict__ d, const float* __restrict__ theta,
+                                 double* __restrict__ g_val) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double rsd = 1.0 / sqrt(d[i]);
+    for (int kg = grp[i]; kg < grp[i + 1]; ++kg) {
+      const float th = theta[kg];
+      g_val[kg] = (double)(gcol[kg] == i ? expf(th) : th) * rsd;
+    }
+  }
+}
+
+// dtheta per entry, one thread per row: dG * G_ii on the diagonal (the
+// derivative of exp(theta)/sqrt(d)), dG / sqrt(d_i) off it.
+__global__ void head_dtheta_kernel(int n, const int* __restrict__ grp, const int* __restrict__ gcol,
+                                   const double* __restrict__ d, const double* __restrict__ g_val,
+                                   const double* __restrict__ dG, float* __restrict__ dtheta) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double rsd = 1.0 / sqrt(d[i]);
+    for (int kg = grp[i]; kg < grp[i + 1]; ++kg)
+      dtheta[kg] = (float)(dG[kg] * (gcol[kg] == i ? g_val[kg] : rsd));
+  }
+}
+
+// Backward by rows: dP and dR rows from dtheta, per-block partial sums of
+// dv, due, dvd (partial[block][0:32] dv, [32:64] due, [64:96] dvd).
 __global__ void __launch_bounds__(256) head_bwd_rows_kernel(
     int n, const int* __restrict__ grp, const int* __restrict__ gcol, const int* __restrict__ gsrc,
     const float* __restrict__ e, const double* __restrict__ d, const float* __restrict__ PQR,
     const float* __restrict__ ue, const float* __restrict__ vv, const float* __restrict__ vd,
-    const double* __restrict__ g_val, const double* __restrict__ dG, float* __restrict__ dtheta,
-    float* __restrict__ dPQR, float* __restrict__ partial) {
+    const float* __restrict__ dtheta, float* __restrict__ dPQR, float* __restrict__ partial) {
   __shared__ float red[8][96];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float a_v = 0.0f, a_ue = 0.0f, a_vd = 0.0f;
@@ -324,17 +467,14 @@ __global__ void __launch_bounds__(256) head_bwd_rows_kernel(
     const float Pm = PQR[(size_t)i * 96 + lane];
     const float Rpre = PQR[(size_t)i * 96 + 64 + lane];
     const float uem = ue[lane], vm = vv[lane], vdm = vd[lane];
-    const double sdi = sqrt(d[i]);
     float dP = 0.0f, dR = 0.0f;
     for (int kg = grp[i]; kg < grp[i + 1]; ++kg) {
       const int j = gcol[kg];
-      float dth;
+      const float dth = dtheta[kg];  // from head_dtheta_kernel
       if (j == i) {
-        dth = (float)(dG[kg] * g_val[kg]);  // d(exp(theta)/sqrt(d))/dtheta = g
         a_vd = fmaf(fmaxf(Rpre, 0.0f), dth, a_vd);
         dR = Rpre > 0.0f ? vdm * dth : 0.0f;
       } else {
-        dth = (float)(dG[kg] / sdi);
         const float ek = e[gsrc[kg]];
         const float pre = Pm + PQR[(size_t)j * 96 + 32 + lane] + uem * ek;
         const float dpre = pre > 0.0f ? vm * dth : 0.0f;
@@ -342,7 +482,6 @@ __global__ void __launch_bounds__(256) head_bwd_rows_kernel(
         a_ue = fmaf(dpre, ek, a_ue);
         a_v = fmaf(fmaxf(pre, 0.0f), dth, a_v);
       }
-      if (lane == 0) dtheta[kg] = dth;
     }
     dPQR[(size_t)i * 96 + lane] = dP;
     dPQR[(size_t)i * 96 + 64 + lane] = dR;
@@ -510,8 +649,13 @@ extern "C" int32_t sla_mp_dense_fwd(int32_t n, int32_t K1, const float* X1, int3
   if (n < 0 || K1 < 0 || K2 < 0 || K1 + K2 < 1 || K1 + K2 > kMaxK || M < 1 || M > kMaxM) return SLA_ERR_INVALID;
   if (n == 0) return SLA_OK;
   if (!W_bf16 || !Y || (K1 && !X1) || (K2 && !X2)) return SLA_ERR_INVALID;
-  dense_fwd_kernel<<<grid_rows(n, kTN, 4096), kDT, 0, (cudaStream_t)stream>>>(
-      n, K1, X1, K2, X2, M, (const __nv_bfloat16*)W_bf16, bias, R, relu, Ypre, Y);
+  const int nm = (M + 31) / 32;
+  const int blocks = grid_rows(n, 64, 148 * 4);
+  cudaStream_t s = (cudaStream_t)stream;
+  const __nv_bfloat16* Wb = (const __nv_bfloat16*)W_bf16;
+  if (nm == 1) dense_fwd_kernel<1><<<blocks, kDT, 0, s>>>(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y);
+  else if (nm == 2) dense_fwd_kernel<2><<<blocks, kDT, 0, s>>>(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y);
+  else dense_fwd_kernel<3><<<blocks, kDT, 0, s>>>(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y);
   MP_LAUNCH_CHECK();
   return SLA_OK;
 }
@@ -577,6 +721,7 @@ extern "C" int32_t sla_mp_head_fwd(int32_t n, const int32_t* g_rowptr, const int
   if (n == 0) return SLA_OK;
   head_fwd_kernel<<<grid_rows(n, 8), 256, 0, (cudaStream_t)stream>>>(n, g_rowptr, g_col, g_src, e, d, PQR,
                                                                     ue, v, vd, theta, g_val);
+  head_gval_kernel<<<grid_rows(n, 256), 256, 0, (cudaStream_t)stream>>>(n, g_rowptr, g_col, d, theta, g_val);
   MP_LAUNCH_CHECK();
   return SLA_OK;
 }
@@ -598,8 +743,9 @@ extern "C" int32_t sla_mp_head_bwd(int32_t n, const int32_t* g_rowptr, const int
   cudaStream_t s = (cudaStream_t)stream;
   const int blocks = grid_rows(n, 8, 2048);
   float* partial = (float*)ws;
-  head_bwd_rows_kernel<<<blocks, 256, 0, s>>>(n, g_rowptr, g_col, g_src, e, d, PQR, ue, v, vd, g_val, dG, dtheta,
-                                              dPQR, partial);
+  head_dtheta_kernel<<<grid_rows(n, 256), 256, 0, s>>>(n, g_rowptr, g_col, d, g_val, dG, dtheta);
+  head_bwd_rows_kernel<<<blocks, 256, 0, s>>>(n, g_rowptr, g_col, g_src, e, d, PQR, ue, v, vd, dtheta, dPQR,
+                                              partial);
   head_bwd_cols_kernel<<<grid_rows(n, 8), 256, 0, s>>>(n, gt_rowptr, gt_row, gt_perm, g_src, e, PQR, ue, v,
                                                        dtheta, dPQR);
   reduce_blocks_kernel<<<1, 96, 0, s>>>(blocks, 96, partial, grads);
