@@ -117,15 +117,27 @@ __device__ __forceinline__ void reduce_partials(const double* part, int stride, 
 // x loads are issued back to back, then the FMAs run in entry order (the same
 // sequential sum as one entry at a time, so the bits do not change).  A row
 // therefore waits for one gather latency per 8 entries instead of one per
-// entry.  col_at(k) / val_at(k) read entry k (shared or global memory);
-// T is the type of x, of val_at's result and of the sum (FP64, or FP32 for
-// a preconditioner applied in single precision).
+// entry.  col_at(k) / val_at(k) read entry k (shared or global memory); x is
+// an array or a functor of the column (gather_at); its element type is the
+// type of val_at's result and of the sum.
 // ------------------------------------------------------------------------
 constexpr int kGatherBatch = 8;
 
-template <class T, class ColAt, class ValAt>
-__device__ __forceinline__ T row_sum_batched(int a, int e, ColAt&& col_at, ValAt&& val_at,
-                                             const T* __restrict__ x) {
+// x[c] for a gathered operand given as an array (read through the read-only
+// path) or as a functor of the column (an operand formed on the fly).
+template <class T>
+__device__ __forceinline__ T gather_at(const T* __restrict__ x, int c) {
+  return __ldg(x + c);
+}
+template <class F>
+__device__ __forceinline__ auto gather_at(F& f, int c) -> decltype(f(c)) {
+  return f(c);
+}
+
+template <class ColAt, class ValAt, class XAt>
+__device__ __forceinline__ auto row_sum_batched(int a, int e, ColAt&& col_at, ValAt&& val_at, XAt&& x)
+    -> decltype(gather_at(x, 0)) {
+  using T = decltype(gather_at(x, 0));
   T acc = T(0);
   int k0 = a;
   for (; k0 + kGatherBatch <= e; k0 += kGatherBatch) {
@@ -137,7 +149,7 @@ __device__ __forceinline__ T row_sum_batched(int a, int e, ColAt&& col_at, ValAt
       v[j] = val_at(k0 + j);
     }
 #pragma unroll
-    for (int j = 0; j < kGatherBatch; ++j) xv[j] = __ldg(x + c[j]);
+    for (int j = 0; j < kGatherBatch; ++j) xv[j] = gather_at(x, c[j]);
 #pragma unroll
     for (int j = 0; j < kGatherBatch; ++j) acc = fma(v[j], xv[j], acc);
   }
@@ -153,7 +165,7 @@ __device__ __forceinline__ T row_sum_batched(int a, int e, ColAt&& col_at, ValAt
       }
 #pragma unroll
     for (int j = 0; j < kGatherBatch; ++j)
-      if (j < rem) xv[j] = __ldg(x + c[j]);
+      if (j < rem) xv[j] = gather_at(x, c[j]);
     // explicit exit: the FP64 pipe must not see the padding lanes
 #pragma unroll
     for (int j = 0; j < kGatherBatch; ++j) {

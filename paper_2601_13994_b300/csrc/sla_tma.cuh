@@ -157,13 +157,26 @@ __device__ __forceinline__ float warp_sum_any(float v) { return warp_sum_f(v); }
 
 // Row `row` of the matrix from global memory by one warp (lane-strided
 // entries, fixed butterfly); result valid in every lane.
-template <class V, class X>
-__device__ __forceinline__ X warp_row(const int* __restrict__ rowptr, const int* __restrict__ col,
-                                      const V* __restrict__ val, const X* __restrict__ x, int row, int lane) {
+template <class V, class XAt>
+__device__ __forceinline__ auto warp_row(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                         const V* __restrict__ val, XAt&& x, int row, int lane)
+    -> decltype(gather_at(x, 0)) {
+  using X = decltype(gather_at(x, 0));
   const int a = __ldg(rowptr + row), e = __ldg(rowptr + row + 1);
   X s = X(0);
-  for (int k = a + lane; k < e; k += kWarp) s = fma(as_x<X>(__ldg(val + k)), __ldg(x + __ldg(col + k)), s);
+  for (int k = a + lane; k < e; k += kWarp) s = fma(as_x<X>(__ldg(val + k)), gather_at(x, __ldg(col + k)), s);
   return warp_sum_any(s);
+}
+
+// The epilogue operand of a row: aux[row] for an array (0 when null), or
+// aux(row) for a functor.
+template <class A>
+__device__ __forceinline__ A aux_at(const A* __restrict__ aux, int row) {
+  return aux ? __ldg(aux + row) : A(0);
+}
+template <class F>
+__device__ __forceinline__ auto aux_at(F& f, int row) -> decltype(f(row)) {
+  return f(row);
 }
 
 // Sums of two adjacent rows whose entries are [a, m) and [m, e): the column
@@ -171,9 +184,9 @@ __device__ __forceinline__ X warp_row(const int* __restrict__ rowptr, const int*
 // gathers issued back to back, then each row's FMAs run in entry order with
 // explicit exits (no padding FMA reaches the FP64 pipe); pairs with more
 // than 8 entries continue one entry at a time.
-template <class X, class ColAt, class ValAt>
-__device__ __forceinline__ void two_row_sum(int a, int m, int e, ColAt&& col_at, ValAt&& val_at,
-                                            const X* __restrict__ x, X& acc0, X& acc1) {
+template <class X, class ColAt, class ValAt, class XAt>
+__device__ __forceinline__ void two_row_sum(int a, int m, int e, ColAt&& col_at, ValAt&& val_at, XAt&& x,
+                                            X& acc0, X& acc1) {
   constexpr int B = kGatherBatch;
   acc0 = X(0);
   acc1 = X(0);
@@ -188,25 +201,27 @@ __device__ __forceinline__ void two_row_sum(int a, int m, int e, ColAt&& col_at,
     }
 #pragma unroll
   for (int j = 0; j < B; ++j)
-    if (j < cnt) xv[j] = __ldg(x + c[j]);
+    if (j < cnt) xv[j] = gather_at(x, c[j]);
   const int n0 = m - a;  // entries of the first row
 #pragma unroll
   for (int jj = 0; jj < B; ++jj) {
     if (jj >= n0 || jj >= cnt) break;
     acc0 = fma(v[jj], xv[jj], acc0);
   }
-  for (int k = a + B; k < m; ++k) acc0 = fma(val_at(k), __ldg(x + col_at(k)), acc0);
+  for (int k = a + B; k < m; ++k) acc0 = fma(val_at(k), gather_at(x, col_at(k)), acc0);
 #pragma unroll
   for (int jj = 0; jj < B; ++jj) {
     if (jj < n0) continue;
     if (jj >= cnt) break;
     acc1 = fma(v[jj], xv[jj], acc1);
   }
-  for (int k = max(m, a + B); k < e; ++k) acc1 = fma(val_at(k), __ldg(x + col_at(k)), acc1);
+  for (int k = max(m, a + B); k < e; ++k) acc1 = fma(val_at(k), gather_at(x, col_at(k)), acc1);
 }
 
 // Runs the pipelined tile loop over all rows (tiles of 256 RPT rows, RPT
-// adjacent rows per consumer thread); calls epi(row, y_row, aux_row)
+// adjacent rows per consumer thread); x is an array or a functor of the
+// column (gather_at), aux an array or a functor of the row (aux_at); calls
+// epi(row, y_row, aux_row)
 // once per row from exactly one consumer thread, where aux_row = aux[row]
 // (prefetched before the row's gathers; 0 when aux is null; any element
 // type).  The sum y_row
@@ -215,13 +230,12 @@ __device__ __forceinline__ void two_row_sum(int a, int m, int e, ColAt&& col_at,
 // by all kThreads threads of the block, with `sm` in dynamic shared memory.
 // The producer warp returns from this function as soon as its copies have
 // landed; nothing after the call may rely on its values.
-template <int RPT = 1, class V, class X, class Aux, class Epi>
+template <int RPT = 1, class V, class XAt, class AuxAt, class Epi>
 __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restrict__ rowptr,
                                               const int* __restrict__ col,
-                                              const V* __restrict__ val,
-                                              const X* __restrict__ x,
-                                              const Aux* __restrict__ aux, SmemT<V, RPT>& sm, int* err,
-                                              Epi&& epi) {
+                                              const V* __restrict__ val, XAt x, AuxAt aux,
+                                              SmemT<V, RPT>& sm, int* err, Epi&& epi) {
+  using X = decltype(gather_at(x, 0));
   static_assert(RPT == 1 || RPT == 2, "one or two rows per consumer thread");
   constexpr int kVE = 16 / (int)sizeof(V);  // values per 16 bytes
   constexpr int kTR = kRows * RPT;          // rows per tile
@@ -329,15 +343,15 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
       auto col_at = [&](int kk) { return kk < kb_c ? S.col[kk - ka_c] : __ldg(col + kk); };
       auto val_at = [&](int kk) { return as_x<X>(kk < kb_v ? S.val[kk - ka_v] : __ldg(val + kk)); };
       if constexpr (RPT == 1) {
-        const Aux av = aux ? __ldg(aux + r0 + tid) : Aux(0);
+        const auto av = aux_at(aux, r0 + tid);
         const int a = S.rp[tid];
         const int e = (tid + 1 < kRows) ? S.rp[tid + 1] : k1;
         const X acc = row_sum_batched(a, e, col_at, val_at, x);
         epi(r0 + tid, acc, av);
       } else {
         const int i0 = 2 * tid;
-        const Aux av0 = aux ? __ldg(aux + r0 + i0) : Aux(0);
-        const Aux av1 = aux ? __ldg(aux + r0 + i0 + 1) : Aux(0);
+        const auto av0 = aux_at(aux, r0 + i0);
+        const auto av1 = aux_at(aux, r0 + i0 + 1);
         const int a = S.rp[i0], m = S.rp[i0 + 1];
         const int e = (i0 + 2 < kTR) ? S.rp[i0 + 2] : k1;
         X acc0, acc1;
@@ -348,7 +362,7 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
     } else {
       for (int rr = warp; rr < nr; rr += kConsumerWarps) {
         const X acc = warp_row(rowptr, col, val, x, r0 + rr, lane);
-        if (lane == 0) epi(r0 + rr, acc, aux ? __ldg(aux + r0 + rr) : Aux(0));
+        if (lane == 0) epi(r0 + rr, acc, aux_at(aux, r0 + rr));
       }
     }
     __syncwarp();
