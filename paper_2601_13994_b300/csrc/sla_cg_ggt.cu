@@ -228,8 +228,9 @@ __global__ void __launch_bounds__(kVT) ggt_update_kernel(GPtrs P) {
 
 // GT: t = G^T r and ||t||^2 = r.z; decisions (RUN: convergence and beta;
 // PRECOND: rho and a fresh p).  RPT rows of G^T per consumer thread.
+// Two rows per thread need more registers: three blocks per SM for RPT = 2.
 template <int RPT>
-__global__ void __launch_bounds__(tma::kThreads, tma::kMinBlocks)
+__global__ void __launch_bounds__(tma::kThreads, RPT == 2 ? 3 : tma::kMinBlocks)
 ggt_gt_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ __align__(128) unsigned char dsm[];
   tma::SmemT<float, RPT>& sm = *reinterpret_cast<tma::SmemT<float, RPT>*>(dsm);
@@ -302,7 +303,7 @@ ggt_gt_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
 
 // GZ: p = G t + beta p (p = G t right after a (re)start); RUN only, after GT
 template <int RPT>
-__global__ void __launch_bounds__(tma::kThreads, tma::kMinBlocks) ggt_gz_kernel(GPtrs P) {
+__global__ void __launch_bounds__(tma::kThreads, RPT == 2 ? 3 : tma::kMinBlocks) ggt_gz_kernel(GPtrs P) {
   extern __shared__ __align__(128) unsigned char dsm[];
   tma::SmemT<float, RPT>& sm = *reinterpret_cast<tma::SmemT<float, RPT>*>(dsm);
   if (__ldcg(&P.st->phase) != kPhaseRun) return;

@@ -113,15 +113,15 @@ __device__ __forceinline__ void reduce_partials(const double* part, int stride, 
 
 // ------------------------------------------------------------------------
 // One row's sum  sum_k val[k] x[col[k]]  over k in [a, e), with the gathers
-// batched: the column indices of up to 8 entries are read first, then all 8
-// x loads are issued back to back, then the FMAs run in entry order (the same
-// sequential sum as one entry at a time, so the bits do not change).  A row
-// therefore waits for one gather latency per 8 entries instead of one per
-// entry.  col_at(k) / val_at(k) read entry k (shared or global memory); x is
+// batched: the column indices of up to kGatherBatch entries are read first,
+// then their x loads are issued back to back, then the FMAs run in entry
+// order (the same sequential sum as one entry at a time, so the bits do not
+// change).  A row therefore waits for one gather latency per batch instead
+// of one per entry.  col_at(k) / val_at(k) read entry k (shared or global memory); x is
 // an array or a functor of the column (gather_at); its element type is the
 // type of val_at's result and of the sum.
 // ------------------------------------------------------------------------
-constexpr int kGatherBatch = 8;
+constexpr int kGatherBatch = 4;  // 4 (vs 8) keeps the TMA consumers at four blocks per SM
 
 // x[c] for a gathered operand given as an array (read through the read-only
 // path) or as a functor of the column (an operand formed on the fly).

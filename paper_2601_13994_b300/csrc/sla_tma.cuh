@@ -6,9 +6,9 @@
 // (the 1-D TMA path), completing on an mbarrier with a byte count.  Eight
 // consumer warps then sum one row per thread from shared memory (one FP64
 // FMA per entry, no shuffles) and release the stage on a second mbarrier.
-// The producer runs up to kStages tiles ahead, so ~90 KB per block are in
-// flight without registers or extra threads; its 32 lanes load the row
-// bounds of 32 tiles at once, so a tile costs it no global round trip.
+// The producer runs up to kStages tiles ahead without registers or extra
+// threads; its 32 lanes load the row bounds of 32 tiles at once, so a tile
+// costs it no global round trip.
 //
 // (A warp-specialised variant -- separate gather warps storing x[col[k]]
 // into shared memory for the FMA warps -- was measured 1.3x slower at
@@ -35,10 +35,15 @@ namespace tma {
 
 constexpr int kRows = 256;                  // rows per tile == consumer threads
 constexpr int kCap = 2048;                  // entries per stage
-constexpr int kStages = 4;
+// Two stages and four blocks per SM: measured (3D 7-point, 16.7 M rows) 299
+// against 362 us per SpMV for four stages and two blocks per SM -- the
+// extra resident consumer warps hide the gather latency better than deeper
+// prefetch does; the copy ring still holds ~200 KB per SM.
+constexpr int kStages = 2;
 constexpr int kConsumerWarps = kRows / kWarp;
 constexpr int kThreads = kRows + kWarp;     // + one producer warp
-constexpr int kMinBlocks = 2;
+constexpr int kMinBlocks = 4;
+constexpr int kPairBatch = 8;               // entries per gather batch of a row pair
 constexpr long long kWaitBudgetCycles = 4000000000LL;
 
 // Matrix values are FP64, or FP32 for factors whose values carry no more
@@ -180,14 +185,14 @@ __device__ __forceinline__ auto aux_at(F& f, int row) -> decltype(f(row)) {
 }
 
 // Sums of two adjacent rows whose entries are [a, m) and [m, e): the column
-// indices and values of up to 8 entries of the pair are read first, their x
+// indices and values of up to kPairBatch entries of the pair are read first, their x
 // gathers issued back to back, then each row's FMAs run in entry order with
 // explicit exits (no padding FMA reaches the FP64 pipe); pairs with more
-// than 8 entries continue one entry at a time.
+// entries continue one entry at a time.
 template <class X, class ColAt, class ValAt, class XAt>
 __device__ __forceinline__ void two_row_sum(int a, int m, int e, ColAt&& col_at, ValAt&& val_at, XAt&& x,
                                             X& acc0, X& acc1) {
-  constexpr int B = kGatherBatch;
+  constexpr int B = kPairBatch;
   acc0 = X(0);
   acc1 = X(0);
   const int cnt = e - a;
