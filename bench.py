@@ -584,7 +584,7 @@ def run_ours(args):
                      "bytes_per_launch": bpi,
                      "traffic": TRAFFIC_PER_ITER_256 if N == 256 else None,
                      "traffic_unit": "bytes per iteration (3 kernels)"},
-        "roofline_spmv": {"kernel": "spmv_tiles_kernel", "bound": "hbm", "achieved": spmv_gbs, "peak": peak,
+        "roofline_spmv": {"kernel": "spmv_tma_kernel", "bound": "hbm", "achieved": spmv_gbs, "peak": peak,
                           "unit": "GB/s", "frac": spmv_gbs / peak, "bytes_per_launch": spmv_bytes(n, nnz)},
         "cpu_baseline": cpu,
         "e2e": e2e,

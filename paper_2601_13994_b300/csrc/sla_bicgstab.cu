@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kVT) bicg_p_kernel(BiPtrs P) {
 // -------------------------------------------------------------- KB / KD
 // which == 0: v = A p^, partial r^.v ;  which == 1: t = A s^, partials t.t, t.s
 template <int which>
-__global__ void __launch_bounds__(tma::kThreads, tma::kMinBlocks) bicg_spmv_kernel(BiPtrs P) {
+__global__ void __launch_bounds__(tma::kThreads, 3) bicg_spmv_kernel(BiPtrs P) {  // see cg_spmv_pq_tma_kernel
   extern __shared__ __align__(128) unsigned char dsm[];
   tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
   if (__ldcg(&P.st->phase) != kPhaseRun) return;

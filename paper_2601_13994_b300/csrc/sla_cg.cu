@@ -179,7 +179,9 @@ __global__ void __launch_bounds__(kTileThreads) cg_spmv_pq_kernel(CgPtrs P) {
 }
 
 // K1 on the TMA-pipelined tiles (see sla_tma.cuh).
-__global__ void __launch_bounds__(tma::kThreads, tma::kMinBlocks) cg_spmv_pq_tma_kernel(CgPtrs P) {
+// Three blocks per SM: the p.q epilogue and the state update need more than
+// the 56 registers of four blocks (spills measured 1 % slower in PCG).
+__global__ void __launch_bounds__(tma::kThreads, 3) cg_spmv_pq_tma_kernel(CgPtrs P) {
   extern __shared__ __align__(128) unsigned char dsm[];
   tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
   if (__ldcg(&P.st->phase) != kPhaseRun) return;
