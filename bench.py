@@ -37,7 +37,7 @@ FALLBACK_HBM_GBS = 6400.0
 # DRAM bytes (read + write) of one PCG iteration at 256^3, summed over the
 # three kernels of one ncu --set full capture (profiles/pcg_iteration_diffusion3d_256.md);
 # valid only for these kernels and this size.
-TRAFFIC_PER_ITER_256 = 3.122e9
+TRAFFIC_PER_ITER_256 = 3.130e9  # ncu dram__bytes_read+write of K1+K2+K3, one iteration (profiles/)
 FP64_PEAK_TFLOPS = 1.203  # 2 DFMA/clk/SM (ncu peak_sustained) x 148 SMs x 2 flop x 2.032 GHz
 
 
