@@ -160,39 +160,32 @@ __global__ void __launch_bounds__(kVT) bicg_p_kernel(BiPtrs P) {
 
 // -------------------------------------------------------------- KB / KD
 // which == 0: v = A p^, partial r^.v ;  which == 1: t = A s^, partials t.t, t.s
-template <int which>
-__global__ void __launch_bounds__(tma::kThreads, 3) bicg_spmv_kernel(BiPtrs P) {  // see cg_spmv_pq_tma_kernel
-  extern __shared__ __align__(128) unsigned char dsm[];
-  tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
-  if (__ldcg(&P.st->phase) != kPhaseRun) return;
-  const KrylovDesc d = *P.d;
+// run(x, aux, epi) performs y = A x through one of the SpMV schemes.
+template <int which, int NT, int M, class Run>
+__device__ __forceinline__ void bicg_spmv_body(const BiPtrs& P, double (&red)[M], bool* s_last, Run&& run) {
   double a0 = 0.0, a1 = 0.0;
   if (which == 0) {
     double* __restrict__ v = P.v;
-    const double* __restrict__ rh = P.rh;
-    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, P.ph, rh, sm, &P.st->err,
-                       [&](int row, double y, double rhr) {
-                         v[row] = y;
-                         a0 = fma(rhr, y, a0);
-                       });
+    run(P.ph, P.rh, [&](int row, double y, double rhr) {
+      v[row] = y;
+      a0 = fma(rhr, y, a0);
+    });
   } else {
     double* __restrict__ t = P.t;
-    const double* __restrict__ s = P.s;
-    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, P.sh, s, sm, &P.st->err,
-                       [&](int row, double y, double sr) {
-                         t[row] = y;
-                         a0 = fma(y, y, a0);
-                         a1 = fma(y, sr, a1);
-                       });
+    run(P.sh, P.s, [&](int row, double y, double sr) {
+      t[row] = y;
+      a0 = fma(y, y, a0);
+      a1 = fma(y, sr, a1);
+    });
   }
   double acc[2] = {a0, a1};
-  block_sums<tma::kThreads, 2>(acc, sm.red);
+  block_sums<NT, 2>(acc, red);
   if (threadIdx.x == 0) {
     P.part[blockIdx.x] = acc[0];
     P.part[kMaxBlocks + blockIdx.x] = acc[1];
   }
-  if (!last_block_arrive(&P.st->cnt[which == 0 ? 1 : 3], &sm.last)) return;
-  reduce_partials<tma::kThreads, 2>(P.part, kMaxBlocks, gridDim.x, acc, sm.red);
+  if (!last_block_arrive(&P.st->cnt[which == 0 ? 1 : 3], s_last)) return;
+  reduce_partials<NT, 2>(P.part, kMaxBlocks, gridDim.x, acc, red);
   if (threadIdx.x == 0) {
     KrylovState& s = *P.st;
     if (__ldcg(&s.err) != 0) {
@@ -218,6 +211,28 @@ __global__ void __launch_bounds__(tma::kThreads, 3) bicg_spmv_kernel(BiPtrs P) {
       }
     }
   }
+}
+
+template <int which>
+__global__ void __launch_bounds__(tma::kThreads, 3) bicg_spmv_tma_kernel(BiPtrs P) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
+  if (__ldcg(&P.st->phase) != kPhaseRun) return;
+  const KrylovDesc d = *P.d;
+  bicg_spmv_body<which, tma::kThreads>(P, sm.red, &sm.last, [&](const double* x, const double* aux, auto&& epi) {
+    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, x, aux, sm, &P.st->err, epi);
+  });
+}
+
+template <int which>
+__global__ void __launch_bounds__(kRowThreads) bicg_spmv_rows_kernel(BiPtrs P) {
+  __shared__ double red[2 * kRowThreads + 2];
+  __shared__ bool s_last;
+  if (__ldcg(&P.st->phase) != kPhaseRun) return;
+  const KrylovDesc d = *P.d;
+  bicg_spmv_body<which, kRowThreads>(P, red, &s_last, [&](const double* x, const double* aux, auto&& epi) {
+    csr_rows(d.n, d.rowptr, d.col, d.val, x, aux, epi);
+  });
 }
 
 // -------------------------------------------------------------- KC
@@ -444,30 +459,52 @@ __global__ void __launch_bounds__(kVT) bicg_final_kernel(BiPtrs P) {
 struct BiGraphKey {
   int dev;
   const void* ws;
-  int n, nnz, gs, gv;
+  int n, nnz, gs, gv, kind;
   bool operator==(const BiGraphKey& o) const {
-    return dev == o.dev && ws == o.ws && n == o.n && nnz == o.nnz && gs == o.gs && gv == o.gv;
+    return dev == o.dev && ws == o.ws && n == o.n && nnz == o.nnz && gs == o.gs && gv == o.gv && kind == o.kind;
   }
 };
 
 std::mutex g_mu;
 std::vector<std::pair<BiGraphKey, cudaGraphExec_t>> g_cache;
 
-void grids(int dev, int n, int* gs, int* gv) {
-  static int occ_s = 0, occ_v = 0;
+// The two SpMV kernels of the body: row-per-thread for n <= kRowsKernelMaxN,
+// else the TMA pipeline.
+struct SpmvKernels {
+  const void* kb;
+  const void* kd;
+  int threads;
+  unsigned smem;
+  int kind;
+};
+
+SpmvKernels spmv_kernels(int n) {
+  if (spmv_kind(n) == kSpmvRows)
+    return SpmvKernels{(const void*)bicg_spmv_rows_kernel<0>, (const void*)bicg_spmv_rows_kernel<1>, kRowThreads, 0u,
+                       kSpmvRows};
+  return SpmvKernels{(const void*)bicg_spmv_tma_kernel<0>, (const void*)bicg_spmv_tma_kernel<1>, tma::kThreads,
+                     (unsigned)tma::kSmemBytes, kSpmvTma};
+}
+
+void grids(int dev, int n, const SpmvKernels& k, int* gs, int* gv) {
+  static int occ_s = 0, occ_r = 0, occ_v = 0;
   if (occ_s == 0) {
-    cudaFuncSetAttribute(bicg_spmv_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(bicg_spmv_tma_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tma::kSmemBytes);
-    cudaFuncSetAttribute(bicg_spmv_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(bicg_spmv_tma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tma::kSmemBytes);
-    occ_s = occupancy((const void*)bicg_spmv_kernel<0>, tma::kThreads, tma::kSmemBytes);
+    occ_s = occupancy((const void*)bicg_spmv_tma_kernel<0>, tma::kThreads, tma::kSmemBytes);
+    occ_r = occupancy((const void*)bicg_spmv_rows_kernel<1>, kRowThreads);
   }
   if (occ_v == 0) occ_v = occupancy((const void*)bicg_x_kernel, kVT);
-  *gs = persistent_grid(dev, (n + tma::kRows - 1) / tma::kRows, occ_s, kMaxBlocks);
+  if (k.kind == kSpmvRows)
+    *gs = persistent_grid(dev, ((long long)n + kRowThreads - 1) / kRowThreads, occ_r < 8 ? occ_r : 8, kMaxBlocks);
+  else
+    *gs = persistent_grid(dev, (n + tma::kRows - 1) / tma::kRows, occ_s, kMaxBlocks);
   *gv = persistent_grid(dev, ((long long)n + kVT - 1) / kVT, occ_v, kMaxBlocks);
 }
 
-int build_graph(BiPtrs P, int gs, int gv, cudaGraphExec_t* exec) {
+int build_graph(BiPtrs P, const SpmvKernels& k, int gs, int gv, cudaGraphExec_t* exec) {
   cudaGraph_t g = nullptr;
   SLA_CUDA_TRY(cudaGraphCreate(&g, 0));
   int rc = SLA_ERR_CUDA;
@@ -478,7 +515,6 @@ int build_graph(BiPtrs P, int gs, int gv, cudaGraphExec_t* exec) {
     void* a[] = {&P};
     int use_cond = 1;
     void* ae[] = {&P, &h, &use_cond};
-    const unsigned sm = (unsigned)tma::kSmemBytes;
     if (add_kernel(g, nullptr, 0, &n_init, (const void*)bicg_init_kernel, gv, kVT, a) != cudaSuccess) break;
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
@@ -488,9 +524,9 @@ int build_graph(BiPtrs P, int gs, int gv, cudaGraphExec_t* exec) {
     if (cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp) != cudaSuccess) break;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     if (add_kernel(body, nullptr, 0, &na, (const void*)bicg_p_kernel, gv, kVT, a) != cudaSuccess) break;
-    if (add_kernel(body, &na, 1, &nb, (const void*)bicg_spmv_kernel<0>, gs, tma::kThreads, a, sm) != cudaSuccess) break;
+    if (add_kernel(body, &na, 1, &nb, k.kb, gs, k.threads, a, k.smem) != cudaSuccess) break;
     if (add_kernel(body, &nb, 1, &nc, (const void*)bicg_s_kernel, gv, kVT, a) != cudaSuccess) break;
-    if (add_kernel(body, &nc, 1, &nd, (const void*)bicg_spmv_kernel<1>, gs, tma::kThreads, a, sm) != cudaSuccess) break;
+    if (add_kernel(body, &nc, 1, &nd, k.kd, gs, k.threads, a, k.smem) != cudaSuccess) break;
     if (add_kernel(body, &nd, 1, &ne, (const void*)bicg_x_kernel, gv, kVT, ae) != cudaSuccess) break;
     if (add_kernel(g, &n_while, 1, &n_final, (const void*)bicg_final_kernel, gv, kVT, a) != cudaSuccess) break;
     if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) break;
@@ -500,15 +536,16 @@ int build_graph(BiPtrs P, int gs, int gv, cudaGraphExec_t* exec) {
   return rc;
 }
 
-int run_host_loop(BiPtrs P, const KrylovDesc& desc, int gs, int gv, cudaStream_t s) {
+int run_host_loop(BiPtrs P, const KrylovDesc& desc, const SpmvKernels& k, int gs, int gv, cudaStream_t s) {
+  void* a[] = {&P};
   bicg_write_desc_kernel<<<1, 1, 0, s>>>(P.d, desc, P.st);
   bicg_init_kernel<<<gv, kVT, 0, s>>>(P);
   const long long cap = 2LL * desc.max_iter + 3LL * desc.max_restarts + 8;
   for (long long body = 0; body < cap; ++body) {
     bicg_p_kernel<<<gv, kVT, 0, s>>>(P);
-    bicg_spmv_kernel<0><<<gs, tma::kThreads, tma::kSmemBytes, s>>>(P);
+    SLA_CUDA_TRY(cudaLaunchKernel(k.kb, dim3(gs), dim3(k.threads), a, k.smem, s));
     bicg_s_kernel<<<gv, kVT, 0, s>>>(P);
-    bicg_spmv_kernel<1><<<gs, tma::kThreads, tma::kSmemBytes, s>>>(P);
+    SLA_CUDA_TRY(cudaLaunchKernel(k.kd, dim3(gs), dim3(k.threads), a, k.smem, s));
     bicg_x_kernel<<<gv, kVT, 0, s>>>(P, cudaGraphConditionalHandle(0), 0);
     if ((body + 1) % 16 == 0) {
       int phase = 0;
@@ -538,16 +575,17 @@ int launch_bicgstab(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags)
   P.s = vecs[5]; P.sh = vecs[6]; P.t = vecs[7]; P.dinv = vecs[8];
   const int dev = current_device();
   int gs, gv;
-  grids(dev, desc.n, &gs, &gv);
-  if (flags & SLA_FLAG_HOST_LOOP) return run_host_loop(P, desc, gs, gv, s);
-  BiGraphKey key{dev, ws, desc.n, desc.nnz, gs, gv};
+  const SpmvKernels sk = spmv_kernels(desc.n);
+  grids(dev, desc.n, sk, &gs, &gv);
+  if (flags & SLA_FLAG_HOST_LOOP) return run_host_loop(P, desc, sk, gs, gv, s);
+  BiGraphKey key{dev, ws, desc.n, desc.nnz, gs, gv, sk.kind};
   cudaGraphExec_t exec = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto& e : g_cache)
       if (e.first == key) exec = e.second;
     if (exec == nullptr) {
-      const int rc = build_graph(P, gs, gv, &exec);
+      const int rc = build_graph(P, sk, gs, gv, &exec);
       if (rc != SLA_OK) return rc;
       if (g_cache.size() >= 64) {
         SLA_CUDA_TRY(cudaDeviceSynchronize());

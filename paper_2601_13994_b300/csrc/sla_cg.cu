@@ -142,80 +142,77 @@ __global__ void __launch_bounds__(kVecThreads) cg_init_kernel(CgPtrs P) {
 }
 
 // ---------------------------------------------------------------- K1
+// Last block of K1: alpha = rho / p.q, or the solve's end on a breakdown.
+__device__ __forceinline__ void k1_finish(const CgPtrs& P, double tpq) {
+  KrylovState& s = *P.st;
+  s.pq = tpq;
+  if (__ldcg(&s.err) != 0) {
+    s.status = SLA_ERR_TIMEOUT;
+    s.phase = kPhaseDone;
+  } else if (!isfinite(tpq)) {
+    s.status = SLA_BREAKDOWN;
+    s.phase = kPhaseDone;
+  } else if (!(tpq > 0.0)) {
+    s.status = SLA_NOT_SPD;
+    s.phase = kPhaseDone;
+  } else {
+    s.alpha = s.rho / tpq;
+  }
+}
+
+// K1 body for a block of NT threads: run(epi) performs q = A p through one
+// of the SpMV schemes, calling epi(row, (A p)_row, p_row).
+template <int NT, int M, class Run>
+__device__ __forceinline__ void k1_body(const CgPtrs& P, double (&red)[M], bool* s_last, Run&& run) {
+  double* __restrict__ q = P.q;
+  double pq = 0.0;
+  run([&](int row, double s, double prow) {
+    q[row] = s;
+    pq = fma(prow, s, pq);
+  });
+  double v[1] = {pq};
+  block_sums<NT, 1>(v, red);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
+  if (!last_block_arrive(&P.st->cnt[1], s_last)) return;
+  reduce_partials<NT, 1>(P.part, kMaxBlocks, gridDim.x, v, red);
+  if (threadIdx.x == 0) k1_finish(P, v[0]);
+}
+
+// K1 on register-staged tiles.
 __global__ void __launch_bounds__(kTileThreads) cg_spmv_pq_kernel(CgPtrs P) {
   __shared__ TileSmem sm;
   __shared__ bool s_last;
   if (__ldcg(&P.st->phase) != kPhaseRun) return;
   const KrylovDesc d = *P.d;
-  const int n = d.n;
   const double* __restrict__ p = P.p;
-  double* __restrict__ q = P.q;
-  double pq = 0.0;
-  const int ntiles = (n + kTileRows - 1) / kTileRows;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
-    spmv_tile(t, n, d.rowptr, d.col, d.val, p, sm, [&](int row, double s) {
-      q[row] = s;
-      pq = fma(__ldg(p + row), s, pq);
-    });
-  double v[1] = {pq};
-  block_sums<kTileThreads, 1>(v, sm.val);
-  if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
-  if (!last_block_arrive(&P.st->cnt[1], &s_last)) return;
-  reduce_partials<kTileThreads, 1>(P.part, kMaxBlocks, gridDim.x, v, sm.val);
-  if (threadIdx.x == 0) {
-    const double tpq = v[0];
-    KrylovState& s = *P.st;
-    s.pq = tpq;
-    if (!isfinite(tpq)) {
-      s.status = SLA_BREAKDOWN;
-      s.phase = kPhaseDone;
-    } else if (!(tpq > 0.0)) {
-      s.status = SLA_NOT_SPD;
-      s.phase = kPhaseDone;
-    } else {
-      s.alpha = s.rho / tpq;
-    }
-  }
+  k1_body<kTileThreads>(P, sm.val, &s_last, [&](auto&& epi) {
+    const int ntiles = (d.n + kTileRows - 1) / kTileRows;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
+      spmv_tile(t, d.n, d.rowptr, d.col, d.val, p, sm,
+                [&](int row, double s) { epi(row, s, __ldg(p + row)); });
+  });
 }
 
-// K1 on the TMA-pipelined tiles (see sla_tma.cuh).
-// Three blocks per SM: the p.q epilogue and the state update need more than
-// the 56 registers of four blocks (spills measured 1 % slower in PCG).
+// K1 on the TMA-pipelined tiles (see sla_tma.cuh).  Three blocks per SM: the
+// p.q epilogue and the state update need more than the 56 registers of four
+// blocks (spills measured 1 % slower in PCG).
 __global__ void __launch_bounds__(tma::kThreads, 3) cg_spmv_pq_tma_kernel(CgPtrs P) {
   extern __shared__ __align__(128) unsigned char dsm[];
   tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
   if (__ldcg(&P.st->phase) != kPhaseRun) return;
   const KrylovDesc d = *P.d;
-  const double* __restrict__ p = P.p;
-  double* __restrict__ q = P.q;
-  double pq = 0.0;
-  tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, p, p, sm, &P.st->err,
-                     [&](int row, double s, double prow) {
-                       q[row] = s;
-                       pq = fma(prow, s, pq);
-                     });
-  double v[1] = {pq};
-  block_sums<tma::kThreads, 1>(v, sm.red);
-  if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
-  if (!last_block_arrive(&P.st->cnt[1], &sm.last)) return;
-  reduce_partials<tma::kThreads, 1>(P.part, kMaxBlocks, gridDim.x, v, sm.red);
-  if (threadIdx.x == 0) {
-    const double tpq = v[0];
-    KrylovState& s = *P.st;
-    s.pq = tpq;
-    if (__ldcg(&s.err) != 0) {
-      s.status = SLA_ERR_TIMEOUT;
-      s.phase = kPhaseDone;
-    } else if (!isfinite(tpq)) {
-      s.status = SLA_BREAKDOWN;
-      s.phase = kPhaseDone;
-    } else if (!(tpq > 0.0)) {
-      s.status = SLA_NOT_SPD;
-      s.phase = kPhaseDone;
-    } else {
-      s.alpha = s.rho / tpq;
-    }
-  }
+  k1_body<tma::kThreads>(P, sm.red, &sm.last, [&](auto&& epi) {
+    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, P.p, P.p, sm, &P.st->err, epi);
+  });
+}
+
+// K1 with one thread per row (csr_rows): the scheme for n <= kRowsKernelMaxN.
+__global__ void __launch_bounds__(kRowThreads) cg_spmv_pq_rows_kernel(CgPtrs P) {
+  __shared__ double red[kRowThreads + 2];
+  __shared__ bool s_last;
+  if (__ldcg(&P.st->phase) != kPhaseRun) return;
+  const KrylovDesc d = *P.d;
+  k1_body<kRowThreads>(P, red, &s_last, [&](auto&& epi) { csr_rows(d.n, d.rowptr, d.col, d.val, P.p, P.p, epi); });
 }
 
 // ---------------------------------------------------------------- K2
@@ -480,8 +477,9 @@ struct K1Launch {
   unsigned smem;
 };
 
-K1Launch k1_launch(bool tma) {
-  if (tma) return K1Launch{(const void*)cg_spmv_pq_tma_kernel, tma::kThreads, (unsigned)tma::kSmemBytes};
+K1Launch k1_launch(int kind) {
+  if (kind == kSpmvTma) return K1Launch{(const void*)cg_spmv_pq_tma_kernel, tma::kThreads, (unsigned)tma::kSmemBytes};
+  if (kind == kSpmvRows) return K1Launch{(const void*)cg_spmv_pq_rows_kernel, kRowThreads, 0u};
   return K1Launch{(const void*)cg_spmv_pq_kernel, kTileThreads, 0u};
 }
 
@@ -518,17 +516,20 @@ int build_graph(CgPtrs P, K1Launch k1, int g1, int gv, cudaGraphExec_t* exec) {
 
 }  // namespace
 
-int cg_grids(int dev, int n, bool tma, int* g1, int* gv) {
-  static int occ1 = 0, occ1t = 0, occv = 0;
+int cg_grids(int dev, int n, int kind, int* g1, int* gv) {
+  static int occ1 = 0, occ1t = 0, occ1r = 0, occv = 0;
   if (occ1 == 0) occ1 = occupancy((const void*)cg_spmv_pq_kernel, kTileThreads);
   if (occ1t == 0) {
     cudaFuncSetAttribute(cg_spmv_pq_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tma::kSmemBytes);
     occ1t = occupancy((const void*)cg_spmv_pq_tma_kernel, tma::kThreads, tma::kSmemBytes);
   }
+  if (occ1r == 0) occ1r = occupancy((const void*)cg_spmv_pq_rows_kernel, kRowThreads);
   if (occv == 0) occv = occupancy((const void*)cg_update_kernel, kVecThreads);
-  const long long ntiles = (n + kTileRows - 1) / kTileRows;
-  *g1 = persistent_grid(dev, ntiles, tma ? occ1t : occ1, kMaxBlocks);
+  if (kind == kSpmvRows)
+    *g1 = persistent_grid(dev, ((long long)n + kRowThreads - 1) / kRowThreads, occ1r < 8 ? occ1r : 8, kMaxBlocks);
+  else
+    *g1 = persistent_grid(dev, (n + kTileRows - 1) / kTileRows, kind == kSpmvTma ? occ1t : occ1, kMaxBlocks);
   *gv = persistent_grid(dev, ((long long)n + kVecThreads - 1) / kVecThreads, occv, kMaxBlocks);
   return SLA_OK;
 }
@@ -575,12 +576,12 @@ int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags) {
   P.q = (double*)(base + L.q);
   P.dinv = (double*)(base + L.dinv);
   const int dev = current_device();
-  const bool tma = use_tma_spmv();
-  const K1Launch k1 = k1_launch(tma);
+  const int kind = spmv_kind(n);
+  const K1Launch k1 = k1_launch(kind);
   int g1, gv;
-  cg_grids(dev, n, tma, &g1, &gv);
+  cg_grids(dev, n, kind, &g1, &gv);
   if (flags & SLA_FLAG_HOST_LOOP) return run_host_loop(P, desc, k1, g1, gv, s);
-  CgGraphKey key{dev, ws, n, desc.nnz, g1, gv, tma ? 1 : 0};
+  CgGraphKey key{dev, ws, n, desc.nnz, g1, gv, kind};
   cudaGraphExec_t exec = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);

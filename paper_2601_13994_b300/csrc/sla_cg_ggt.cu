@@ -123,40 +123,32 @@ __device__ __forceinline__ void finish(KrylovState& s, int status, cudaGraphCond
 
 // K1: RUN: q = A p, p.q -> alpha.  CHECK: r = b - A x (true residual) ->
 // done, or a restart through phase PRECOND.  DONE at entry: clear the loop
-// condition (nothing else runs in this body).
-__global__ void __launch_bounds__(tma::kThreads, tma::kMinBlocks)
-ggt_spmv_pq_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
-  extern __shared__ __align__(128) unsigned char dsm[];
-  tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
-  const int ph = __ldcg(&P.st->phase);
-  if (ph == kPhaseDone) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 && use_cond) cudaGraphSetConditional(cond, 0u);
-    return;
-  }
-  if (ph != kPhaseRun && ph != kPhaseCheck) return;
+// condition (nothing else runs in this body).  run(x, aux, epi) performs the
+// SpMV y = A x through one of the schemes.
+template <int NT, int M, class Run>
+__device__ __forceinline__ void ggt_k1_body(GPtrs P, int ph, cudaGraphConditionalHandle cond, int use_cond,
+                                            double (&red)[M], bool* s_last, Run&& run) {
   const KrylovDesc d = *P.d;
   double acc = 0.0;
   if (ph == kPhaseRun) {
     double* __restrict__ q = P.q;
-    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, P.p, P.p, sm, &P.st->err,
-                       [&](int row, double y, double prow) {
-                         q[row] = y;
-                         acc = fma(prow, y, acc);
-                       });
+    run(P.p, P.p, [&](int row, double y, double prow) {
+      q[row] = y;
+      acc = fma(prow, y, acc);
+    });
   } else {
     double* __restrict__ r = P.r;
-    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, d.x, d.b, sm, &P.st->err,
-                       [&](int row, double y, double brow) {
-                         const double ti = brow - y;
-                         r[row] = ti;
-                         acc = fma(ti, ti, acc);
-                       });
+    run(d.x, d.b, [&](int row, double y, double brow) {
+      const double ti = brow - y;
+      r[row] = ti;
+      acc = fma(ti, ti, acc);
+    });
   }
   double v[1] = {acc};
-  block_sums<tma::kThreads, 1>(v, sm.red);
+  block_sums<NT, 1>(v, red);
   if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
-  if (!last_block_arrive(&P.st->cnt[1], &sm.last)) return;
-  reduce_partials<tma::kThreads, 1>(P.part, kMaxBlocks, gridDim.x, v, sm.red);
+  if (!last_block_arrive(&P.st->cnt[1], s_last)) return;
+  reduce_partials<NT, 1>(P.part, kMaxBlocks, gridDim.x, v, red);
   if (threadIdx.x == 0) {
     KrylovState& s = *P.st;
     if (__ldcg(&s.err) != 0) {
@@ -180,6 +172,37 @@ ggt_spmv_pq_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
       }
     }
   }
+}
+
+// Phase gate of K1: DONE clears the loop condition; only RUN and CHECK work.
+__device__ __forceinline__ int ggt_k1_phase(const GPtrs& P, cudaGraphConditionalHandle cond, int use_cond) {
+  const int ph = __ldcg(&P.st->phase);
+  if (ph == kPhaseDone && blockIdx.x == 0 && threadIdx.x == 0 && use_cond) cudaGraphSetConditional(cond, 0u);
+  return ph;
+}
+
+__global__ void __launch_bounds__(tma::kThreads, 3)
+ggt_spmv_pq_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
+  const int ph = ggt_k1_phase(P, cond, use_cond);
+  if (ph != kPhaseRun && ph != kPhaseCheck) return;
+  const KrylovDesc d = *P.d;
+  ggt_k1_body<tma::kThreads>(P, ph, cond, use_cond, sm.red, &sm.last, [&](const double* x, const double* aux, auto&& epi) {
+    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, x, aux, sm, &P.st->err, epi);
+  });
+}
+
+__global__ void __launch_bounds__(kRowThreads)
+ggt_spmv_pq_rows_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ double red[kRowThreads + 2];
+  __shared__ bool s_last;
+  const int ph = ggt_k1_phase(P, cond, use_cond);
+  if (ph != kPhaseRun && ph != kPhaseCheck) return;
+  const KrylovDesc d = *P.d;
+  ggt_k1_body<kRowThreads>(P, ph, cond, use_cond, red, &s_last, [&](const double* x, const double* aux, auto&& epi) {
+    csr_rows(d.n, d.rowptr, d.col, d.val, x, aux, epi);
+  });
 }
 
 // K2: x += alpha p, r -= alpha q, ||r||^2 (RUN only)
@@ -227,29 +250,22 @@ __global__ void __launch_bounds__(kVT) ggt_update_kernel(GPtrs P) {
 }
 
 // GT: t = G^T r and ||t||^2 = r.z; decisions (RUN: convergence and beta;
-// PRECOND: rho and a fresh p).  RPT rows of G^T per consumer thread.
-// Two rows per thread need more registers: three blocks per SM for RPT = 2.
-template <int RPT>
-__global__ void __launch_bounds__(tma::kThreads, RPT == 2 ? 3 : tma::kMinBlocks)
-ggt_gt_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
-  extern __shared__ __align__(128) unsigned char dsm[];
-  tma::SmemT<float, RPT>& sm = *reinterpret_cast<tma::SmemT<float, RPT>*>(dsm);
-  const int ph = __ldcg(&P.st->phase);
-  if (ph != kPhaseRun && ph != kPhasePrecond) return;
+// PRECOND: rho and a fresh p).  run(epi) performs t = G^T r.
+template <int NT, int M, class Run>
+__device__ __forceinline__ void ggt_gt_body(GPtrs P, int ph, cudaGraphConditionalHandle cond, int use_cond,
+                                            double (&red)[M], bool* s_last, Run&& run) {
   const KrylovDesc d = *P.d;
   double* __restrict__ t = P.t;
   double tt = 0.0;
-  tma::spmv_pipeline<RPT>(d.n, d.nnz_g, d.rowptr_t, d.col_t, (const float*)P.gtv, P.r, (const double*)nullptr, sm,
-                          &P.st->err,
-                     [&](int row, double y, double) {
-                       t[row] = y;
-                       tt = fma(y, y, tt);
-                     });
+  run([&](int row, double y, double) {
+    t[row] = y;
+    tt = fma(y, y, tt);
+  });
   double v[1] = {tt};
-  block_sums<tma::kThreads, 1>(v, sm.red);
+  block_sums<NT, 1>(v, red);
   if (threadIdx.x == 0) P.part[blockIdx.x] = v[0];
-  if (!last_block_arrive(&P.st->cnt[3], &sm.last)) return;
-  reduce_partials<tma::kThreads, 1>(P.part, kMaxBlocks, gridDim.x, v, sm.red);
+  if (!last_block_arrive(&P.st->cnt[3], s_last)) return;
+  reduce_partials<NT, 1>(P.part, kMaxBlocks, gridDim.x, v, red);
   if (threadIdx.x == 0) {
     KrylovState& s = *P.st;
     const double trz = v[0], rnorm = sqrt(s.rr);
@@ -301,6 +317,33 @@ ggt_gt_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
   }
 }
 
+// Two rows per thread need more registers: three blocks per SM for RPT = 2.
+template <int RPT>
+__global__ void __launch_bounds__(tma::kThreads, RPT == 2 ? 3 : tma::kMinBlocks)
+ggt_gt_kernel(GPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  tma::SmemT<float, RPT>& sm = *reinterpret_cast<tma::SmemT<float, RPT>*>(dsm);
+  const int ph = __ldcg(&P.st->phase);
+  if (ph != kPhaseRun && ph != kPhasePrecond) return;
+  const KrylovDesc d = *P.d;
+  ggt_gt_body<tma::kThreads>(P, ph, cond, use_cond, sm.red, &sm.last, [&](auto&& epi) {
+    tma::spmv_pipeline<RPT>(d.n, d.nnz_g, d.rowptr_t, d.col_t, (const float*)P.gtv, P.r, (const double*)nullptr,
+                            sm, &P.st->err, epi);
+  });
+}
+
+__global__ void __launch_bounds__(kRowThreads) ggt_gt_rows_kernel(GPtrs P, cudaGraphConditionalHandle cond,
+                                                                  int use_cond) {
+  __shared__ double red[kRowThreads + 2];
+  __shared__ bool s_last;
+  const int ph = __ldcg(&P.st->phase);
+  if (ph != kPhaseRun && ph != kPhasePrecond) return;
+  const KrylovDesc d = *P.d;
+  ggt_gt_body<kRowThreads>(P, ph, cond, use_cond, red, &s_last, [&](auto&& epi) {
+    csr_rows(d.n, d.rowptr_t, d.col_t, (const float*)P.gtv, P.r, (const double*)nullptr, epi);
+  });
+}
+
 // GZ: p = G t + beta p (p = G t right after a (re)start); RUN only, after GT
 template <int RPT>
 __global__ void __launch_bounds__(tma::kThreads, RPT == 2 ? 3 : tma::kMinBlocks) ggt_gz_kernel(GPtrs P) {
@@ -314,6 +357,16 @@ __global__ void __launch_bounds__(tma::kThreads, RPT == 2 ? 3 : tma::kMinBlocks)
   double* __restrict__ p = P.p;
   tma::spmv_pipeline<RPT>(d.n, d.nnz_g, d.g_rowptr, d.g_col, (const float*)P.gv, P.t, fresh ? nullptr : p, sm,
                      &P.st->err, [&](int row, double y, double prow) { p[row] = fma(beta, prow, y); });
+}
+
+__global__ void __launch_bounds__(kRowThreads) ggt_gz_rows_kernel(GPtrs P) {
+  if (__ldcg(&P.st->phase) != kPhaseRun) return;
+  const bool fresh = __ldcg(&P.st->fresh_p) != 0;
+  const double beta = fresh ? 0.0 : __ldcg(&P.st->beta);
+  const KrylovDesc d = *P.d;
+  double* __restrict__ p = P.p;
+  csr_rows(d.n, d.g_rowptr, d.g_col, (const float*)P.gv, P.t, fresh ? nullptr : p,
+           [&](int row, double y, double prow) { p[row] = fma(beta, prow, y); });
 }
 
 __global__ void __launch_bounds__(kVT) ggt_final_kernel(GPtrs P) {
@@ -350,58 +403,86 @@ __global__ void __launch_bounds__(kVT) ggt_final_kernel(GPtrs P) {
   }
 }
 
-struct Key {
-  int dev;
-  const void* ws;
-  int n, nnz, nnz_g, gs, gg, gv, rpt;
-  bool operator==(const Key& o) const {
-    return dev == o.dev && ws == o.ws && n == o.n && nnz == o.nnz && nnz_g == o.nnz_g && gs == o.gs &&
-           gg == o.gg && gv == o.gv && rpt == o.rpt;
-  }
-};
-
-// The factor SpMVs take two rows per consumer thread (512-row tiles) when G
-// averages at most 4 entries per row, so that a tile still fits a stage:
-// twice the rows in flight per SM for the short rows of tril(A).
-int factor_rpt(int n, int nnz_g) { return (long long)nnz_g <= 4LL * n ? 2 : 1; }
-
-struct FactorKernels {
-  const void* gt;
-  const void* gz;
+// One loop kernel of the body: function, grid, block, dynamic shared memory.
+struct LoopKernel {
+  const void* fn;
+  int grid, threads;
   unsigned smem;
 };
 
-FactorKernels factor_kernels(int rpt) {
-  if (rpt == 2)
-    return FactorKernels{(const void*)ggt_gt_kernel<2>, (const void*)ggt_gz_kernel<2>,
-                         (unsigned)tma::kSmemBytesF32x2};
-  return FactorKernels{(const void*)ggt_gt_kernel<1>, (const void*)ggt_gz_kernel<1>, (unsigned)tma::kSmemBytesF32};
+// The body's SpMV kernels: K1 (A), GT (G^T), GZ (G).  Row-per-thread kernels
+// for n <= kRowsKernelMaxN, else the TMA pipeline, whose factor SpMVs take two
+// rows per consumer thread (512-row tiles) when G averages at most 4 entries
+// per row, so that a tile still fits a stage.
+struct BodyKernels {
+  LoopKernel k1, gt, gz;
+  int gv, kind, rpt;
+};
+
+int factor_rpt(int n, int nnz_g) { return (long long)nnz_g <= 4LL * n ? 2 : 1; }
+
+BodyKernels body_kernels(int dev, int n, int nnz_g) {
+  static std::once_flag once;
+  static int occ_s = 0, occ_v = 0, occ_g[3] = {0, 0, 0}, occ_r[3] = {0, 0, 0};
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(ggt_spmv_pq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::kSmemBytes);
+    cudaFuncSetAttribute(ggt_gt_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::kSmemBytesF32);
+    cudaFuncSetAttribute(ggt_gz_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::kSmemBytesF32);
+    cudaFuncSetAttribute(ggt_gt_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::kSmemBytesF32x2);
+    cudaFuncSetAttribute(ggt_gz_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::kSmemBytesF32x2);
+    occ_s = occupancy((const void*)ggt_spmv_pq_kernel, tma::kThreads, tma::kSmemBytes);
+    occ_g[1] = occupancy((const void*)ggt_gt_kernel<1>, tma::kThreads, tma::kSmemBytesF32);
+    occ_g[2] = occupancy((const void*)ggt_gt_kernel<2>, tma::kThreads, tma::kSmemBytesF32x2);
+    occ_r[0] = occupancy((const void*)ggt_spmv_pq_rows_kernel, kRowThreads);
+    occ_r[1] = occupancy((const void*)ggt_gt_rows_kernel, kRowThreads);
+    occ_r[2] = occupancy((const void*)ggt_gz_rows_kernel, kRowThreads);
+    occ_v = occupancy((const void*)ggt_update_kernel, kVT);
+  });
+  BodyKernels k;
+  k.kind = spmv_kind(n) == kSpmvRows ? kSpmvRows : kSpmvTma;
+  k.rpt = factor_rpt(n, nnz_g);
+  k.gv = persistent_grid(dev, ((long long)n + kVT - 1) / kVT, occ_v, kMaxBlocks);
+  if (k.kind == kSpmvRows) {
+    const long long blocks = ((long long)n + kRowThreads - 1) / kRowThreads;
+    auto g = [&](int occ) { return persistent_grid(dev, blocks, occ < 8 ? occ : 8, kMaxBlocks); };
+    k.k1 = LoopKernel{(const void*)ggt_spmv_pq_rows_kernel, g(occ_r[0]), kRowThreads, 0u};
+    k.gt = LoopKernel{(const void*)ggt_gt_rows_kernel, g(occ_r[1]), kRowThreads, 0u};
+    k.gz = LoopKernel{(const void*)ggt_gz_rows_kernel, g(occ_r[2]), kRowThreads, 0u};
+  } else {
+    const int tr = tma::kRows * k.rpt;
+    const int gs = persistent_grid(dev, (n + tma::kRows - 1) / tma::kRows, occ_s, kMaxBlocks);
+    const int gg = persistent_grid(dev, (n + tr - 1) / tr, occ_g[k.rpt], kMaxBlocks);
+    k.k1 = LoopKernel{(const void*)ggt_spmv_pq_kernel, gs, tma::kThreads, (unsigned)tma::kSmemBytes};
+    if (k.rpt == 2) {
+      k.gt = LoopKernel{(const void*)ggt_gt_kernel<2>, gg, tma::kThreads, (unsigned)tma::kSmemBytesF32x2};
+      k.gz = LoopKernel{(const void*)ggt_gz_kernel<2>, gg, tma::kThreads, (unsigned)tma::kSmemBytesF32x2};
+    } else {
+      k.gt = LoopKernel{(const void*)ggt_gt_kernel<1>, gg, tma::kThreads, (unsigned)tma::kSmemBytesF32};
+      k.gz = LoopKernel{(const void*)ggt_gz_kernel<1>, gg, tma::kThreads, (unsigned)tma::kSmemBytesF32};
+    }
+  }
+  return k;
 }
+
+struct Key {
+  int dev;
+  const void* ws;
+  int n, nnz, nnz_g, g1, gg, gv, kind, rpt;
+  bool operator==(const Key& o) const {
+    return dev == o.dev && ws == o.ws && n == o.n && nnz == o.nnz && nnz_g == o.nnz_g && g1 == o.g1 &&
+           gg == o.gg && gv == o.gv && kind == o.kind && rpt == o.rpt;
+  }
+};
 
 std::mutex g_mu;
 std::vector<std::pair<Key, cudaGraphExec_t>> g_cache;
 
-void grids(int dev, int n, int rpt, int* gs, int* gg, int* gv) {
-  static int occ_s = 0, occ_v = 0, occ_g[3] = {0, 0, 0};
-  if (occ_s == 0) {
-    cudaFuncSetAttribute(ggt_spmv_pq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tma::kSmemBytes);
-    for (int r = 1; r <= 2; ++r) {
-      const FactorKernels f = factor_kernels(r);
-      cudaFuncSetAttribute(f.gt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem);
-      cudaFuncSetAttribute(f.gz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem);
-      occ_g[r] = occupancy(f.gt, tma::kThreads, f.smem);
-    }
-    occ_s = occupancy((const void*)ggt_spmv_pq_kernel, tma::kThreads, tma::kSmemBytes);
-  }
-  if (occ_v == 0) occ_v = occupancy((const void*)ggt_update_kernel, kVT);
-  const int tr = tma::kRows * rpt;
-  *gs = persistent_grid(dev, (n + tma::kRows - 1) / tma::kRows, occ_s, kMaxBlocks);
-  *gg = persistent_grid(dev, (n + tr - 1) / tr, occ_g[rpt], kMaxBlocks);
-  *gv = persistent_grid(dev, ((long long)n + kVT - 1) / kVT, occ_v, kMaxBlocks);
+cudaError_t add_loop_kernel(cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphNode_t* out, const LoopKernel& k,
+                            void** args) {
+  return add_kernel(g, dep, dep ? 1 : 0, out, k.fn, k.grid, k.threads, args, k.smem);
 }
 
-int build_graph(GPtrs P, int gs, int gg, int gv, FactorKernels f, cudaGraphExec_t* exec) {
+int build_graph(GPtrs P, const BodyKernels& k, cudaGraphExec_t* exec) {
   cudaGraph_t g = nullptr;
   SLA_CUDA_TRY(cudaGraphCreate(&g, 0));
   int rc = SLA_ERR_CUDA;
@@ -412,8 +493,7 @@ int build_graph(GPtrs P, int gs, int gg, int gv, FactorKernels f, cudaGraphExec_
     void* a[] = {&P};
     int use_cond = 1;
     void* ac[] = {&P, &h, &use_cond};
-    const unsigned sm = (unsigned)tma::kSmemBytes;
-    if (add_kernel(g, nullptr, 0, &n_init, (const void*)ggt_init_kernel, gv, kVT, a) != cudaSuccess) break;
+    if (add_kernel(g, nullptr, 0, &n_init, (const void*)ggt_init_kernel, k.gv, kVT, a) != cudaSuccess) break;
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
@@ -421,11 +501,11 @@ int build_graph(GPtrs P, int gs, int gg, int gv, FactorKernels f, cudaGraphExec_
     cp.conditional.size = 1;
     if (cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp) != cudaSuccess) break;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if (add_kernel(body, nullptr, 0, &n1, (const void*)ggt_spmv_pq_kernel, gs, tma::kThreads, ac, sm) != cudaSuccess) break;
-    if (add_kernel(body, &n1, 1, &n2, (const void*)ggt_update_kernel, gv, kVT, a) != cudaSuccess) break;
-    if (add_kernel(body, &n2, 1, &n3, f.gt, gg, tma::kThreads, ac, f.smem) != cudaSuccess) break;
-    if (add_kernel(body, &n3, 1, &n4, f.gz, gg, tma::kThreads, a, f.smem) != cudaSuccess) break;
-    if (add_kernel(g, &n_while, 1, &n_final, (const void*)ggt_final_kernel, gv, kVT, a) != cudaSuccess) break;
+    if (add_loop_kernel(body, nullptr, &n1, k.k1, ac) != cudaSuccess) break;
+    if (add_kernel(body, &n1, 1, &n2, (const void*)ggt_update_kernel, k.gv, kVT, a) != cudaSuccess) break;
+    if (add_loop_kernel(body, &n2, &n3, k.gt, ac) != cudaSuccess) break;
+    if (add_loop_kernel(body, &n3, &n4, k.gz, a) != cudaSuccess) break;
+    if (add_kernel(g, &n_while, 1, &n_final, (const void*)ggt_final_kernel, k.gv, kVT, a) != cudaSuccess) break;
     if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) break;
     rc = SLA_OK;
   } while (0);
@@ -433,22 +513,22 @@ int build_graph(GPtrs P, int gs, int gg, int gv, FactorKernels f, cudaGraphExec_
   return rc;
 }
 
-int run_host_loop(GPtrs P, const KrylovDesc& desc, int gs, int gg, int gv, FactorKernels f, cudaStream_t s) {
-  const size_t sm = tma::kSmemBytes;
+int run_host_loop(GPtrs P, const KrylovDesc& desc, const BodyKernels& k, cudaStream_t s) {
   ggt_write_desc_kernel<<<1, 1, 0, s>>>(P.d, desc, P.st);
-  ggt_init_kernel<<<gv, kVT, 0, s>>>(P);
+  ggt_init_kernel<<<k.gv, kVT, 0, s>>>(P);
+  cudaGraphConditionalHandle h0 = 0;
+  int uc = 0;
+  void* ac[] = {&P, &h0, &uc};
+  void* a[] = {&P};
+  auto launch = [&](const LoopKernel& lk, void** args) {
+    return cudaLaunchKernel(lk.fn, dim3(lk.grid), dim3(lk.threads), args, lk.smem, s);
+  };
   const long long cap = (long long)desc.max_iter + 3LL * desc.max_restarts + 8;
   for (long long body = 0; body < cap; ++body) {
-    ggt_spmv_pq_kernel<<<gs, tma::kThreads, sm, s>>>(P, cudaGraphConditionalHandle(0), 0);
-    ggt_update_kernel<<<gv, kVT, 0, s>>>(P);
-    {
-      cudaGraphConditionalHandle h0 = 0;
-      int uc = 0;
-      void* ac[] = {&P, &h0, &uc};
-      void* a[] = {&P};
-      SLA_CUDA_TRY(cudaLaunchKernel(f.gt, dim3(gg), dim3(tma::kThreads), ac, f.smem, s));
-      SLA_CUDA_TRY(cudaLaunchKernel(f.gz, dim3(gg), dim3(tma::kThreads), a, f.smem, s));
-    }
+    SLA_CUDA_TRY(launch(k.k1, ac));
+    ggt_update_kernel<<<k.gv, kVT, 0, s>>>(P);
+    SLA_CUDA_TRY(launch(k.gt, ac));
+    SLA_CUDA_TRY(launch(k.gz, a));
     if ((body + 1) % 16 == 0) {
       int phase = 0;
       SLA_CUDA_TRY(cudaMemcpyAsync(&phase, &P.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -456,7 +536,7 @@ int run_host_loop(GPtrs P, const KrylovDesc& desc, int gs, int gg, int gv, Facto
       if (phase == kPhaseDone) break;
     }
   }
-  ggt_final_kernel<<<gv, kVT, 0, s>>>(P);
+  ggt_final_kernel<<<k.gv, kVT, 0, s>>>(P);
   SLA_CUDA_TRY(cudaGetLastError());
   SLA_CUDA_TRY(cudaStreamSynchronize(s));
   return SLA_OK;
@@ -509,19 +589,16 @@ extern "C" int32_t sla_cg_ggt(const sla_csr* A, const double* val, const sla_csr
   P.gv = (float*)(base + L.gv);
   P.gtv = (float*)(base + L.gtv);
   const int dev = current_device();
-  const int rpt = factor_rpt(n, G->nnz);
-  const FactorKernels fk = factor_kernels(rpt);
-  int gs, gg, gv;
-  grids(dev, n, rpt, &gs, &gg, &gv);
-  if (opts->flags & SLA_FLAG_HOST_LOOP) return run_host_loop(P, d, gs, gg, gv, fk, s);
-  Key key{dev, ws, n, A->nnz, G->nnz, gs, gg, gv, rpt};
+  const BodyKernels bk = body_kernels(dev, n, G->nnz);
+  if (opts->flags & SLA_FLAG_HOST_LOOP) return run_host_loop(P, d, bk, s);
+  Key key{dev, ws, n, A->nnz, G->nnz, bk.k1.grid, bk.gt.grid, bk.gv, bk.kind, bk.rpt};
   cudaGraphExec_t exec = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto& e : g_cache)
       if (e.first == key) exec = e.second;
     if (exec == nullptr) {
-      rc = build_graph(P, gs, gg, gv, fk, &exec);
+      rc = build_graph(P, bk, &exec);
       if (rc != SLA_OK) return rc;
       if (g_cache.size() >= 64) {
         SLA_CUDA_TRY(cudaDeviceSynchronize());

@@ -20,13 +20,19 @@ int current_device() {
   return d;
 }
 
-bool use_tma_spmv() {
-  static int v = -1;
-  if (v < 0) {
+int spmv_kind(long long n) {
+  static int forced = -2;
+  if (forced == -2) {
     const char* e = getenv("SLA_SPMV_KERNEL");
-    v = (e != nullptr && strcmp(e, "tile") == 0) ? 0 : 1;
+    forced = -1;
+    if (e != nullptr) {
+      if (strcmp(e, "tile") == 0) forced = kSpmvTile;
+      else if (strcmp(e, "tma") == 0) forced = kSpmvTma;
+      else if (strcmp(e, "rows") == 0) forced = kSpmvRows;
+    }
   }
-  return v == 1;
+  if (forced >= 0) return forced;
+  return n <= kRowsKernelMaxN ? kSpmvRows : kSpmvTma;
 }
 
 int num_sms(int device) {

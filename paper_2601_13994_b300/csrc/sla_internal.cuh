@@ -123,6 +123,56 @@ __device__ __forceinline__ void reduce_partials(const double* part, int stride, 
 // ------------------------------------------------------------------------
 constexpr int kGatherBatch = 4;  // 4 (vs 8) keeps the TMA consumers at four blocks per SM
 
+// ------------------------------------------------------------------------
+// Element types of the SpMVs.  Matrix values are FP64, or FP32 for factors
+// whose values carry no more (the learned G); FP32 values are widened to
+// FP64 exactly with integer bit operations (to_f64), since a hardware
+// conversion would occupy the FP64 pipe, the scarce unit on this part.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ double to_f64(double v) { return v; }
+
+// Exact float -> double for normal numbers, signed zero for zero/subnormal
+// inputs (callers store no subnormal values), inf/nan kept.
+__device__ __forceinline__ double to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if (ex == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long e64 = ex == 0xffu ? 2047ull : (unsigned long long)(ex + 896u);
+  const unsigned long long man = (unsigned long long)(u & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(sign | (e64 << 52) | man));
+}
+
+// A stored value in the arithmetic type X of the sum: FP64 values as they
+// are, FP32 values widened exactly for an FP64 sum or kept for an FP32 sum.
+template <class X>
+__device__ __forceinline__ X as_x(double v) { return v; }
+template <class X>
+__device__ __forceinline__ X as_x(float v);
+template <>
+__device__ __forceinline__ double as_x<double>(float v) { return to_f64(v); }
+template <>
+__device__ __forceinline__ float as_x<float>(float v) { return v; }
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_any(double v) { return warp_sum(v); }
+__device__ __forceinline__ float warp_sum_any(float v) { return warp_sum_f(v); }
+
+// The epilogue operand of a row: aux[row] for an array (0 when null), or
+// aux(row) for a functor.
+template <class A>
+__device__ __forceinline__ A aux_at(const A* __restrict__ aux, int row) {
+  return aux ? __ldg(aux + row) : A(0);
+}
+template <class F>
+__device__ __forceinline__ auto aux_at(F& f, int row) -> decltype(f(row)) {
+  return f(row);
+}
+
 // x[c] for a gathered operand given as an array (read through the read-only
 // path) or as a functor of the column (an operand formed on the fly).
 template <class T>
@@ -175,6 +225,34 @@ __device__ __forceinline__ auto row_sum_batched(int a, int e, ColAt&& col_at, Va
   }
   return acc;
 }
+
+// ------------------------------------------------------------------------
+// Rows of a CSR matrix, one thread per row (grid-stride), each row's gathers
+// batched (row_sum_batched); calls epi(row, y_row, aux_row).  No staging and
+// no pipeline: with 256-thread blocks at up to 8 per SM, the many rows in
+// flight hide the gather latency, which makes this the faster SpMV below a
+// few million rows (a tile pipeline pays one gather latency per tile per
+// block, and at 1-2 M rows a block owns only a handful of tiles), and as
+// fast at 16.7 M rows (3D 7-point: 298 vs 299 us).
+// ------------------------------------------------------------------------
+template <class V, class XAt, class AuxAt, class Epi>
+__device__ __forceinline__ void csr_rows(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                         const V* __restrict__ val, XAt x, AuxAt aux, Epi&& epi) {
+  using X = decltype(gather_at(x, 0));
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const auto av = aux_at(aux, i);
+    const int a = __ldg(rowptr + i), e = __ldg(rowptr + i + 1);
+    const X s = row_sum_batched(
+        a, e, [&](int k) { return __ldg(col + k); }, [&](int k) { return as_x<X>(__ldg(val + k)); }, x);
+    epi(i, s, av);
+  }
+}
+
+// Threads per block of the row-per-thread SpMV kernels, and the size at or
+// below which the solvers use them instead of the TMA tile pipeline.
+constexpr int kRowThreads = 256;
+constexpr long long kRowsKernelMaxN = 4LL << 20;
 
 // ------------------------------------------------------------------------
 // CSR row tile, staged through shared memory.
@@ -291,7 +369,10 @@ int device_exclusive_scan(const int* in, long long n, int* out, int* tmp, int* t
 
 // SpMV kernel family chosen once per process: the TMA-pipelined tiles
 // (default) or the register-staged tiles (environment SLA_SPMV_KERNEL=tile).
-bool use_tma_spmv();
+// SpMV scheme of a solve with n rows: kSpmvRows (one thread per row) for
+// n <= kRowsKernelMaxN, else kSpmvTma; SLA_SPMV_KERNEL=tile|tma|rows forces one.
+enum : int { kSpmvTile = 0, kSpmvTma = 1, kSpmvRows = 2 };
+int spmv_kind(long long n);
 
 // Grid size for a kernel that loops over `units` work items, `per_sm`
 // resident blocks per SM, capped at `cap`.

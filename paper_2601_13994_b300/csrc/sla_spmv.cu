@@ -35,6 +35,13 @@ spmv_tma_kernel(int n, int nnz, const int* __restrict__ rowptr, const int* __res
                      [&](int row, double s, double) { y[row] = s; });
 }
 
+// One thread per row (csr_rows): the scheme for n <= kRowsKernelMaxN.
+__global__ void __launch_bounds__(kRowThreads)
+spmv_rows_kernel(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                 const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+  csr_rows(n, rowptr, col, val, x, (const double*)nullptr, [&](int row, double s, double) { y[row] = s; });
+}
+
 int spmv_tma_blocks_per_sm() {
   static int v = 0;
   if (v == 0) {
@@ -66,7 +73,13 @@ int launch_spmv(int n, int nnz, const int* rowptr, const int* col, const double*
   if (n == 0) return SLA_OK;
   const int dev = current_device();
   const int ntiles = (n + kTileRows - 1) / kTileRows;
-  if (use_tma_spmv()) {
+  const int kind = spmv_kind(n);
+  if (kind == kSpmvRows) {
+    static int occ = 0;
+    if (occ == 0) occ = occupancy((const void*)spmv_rows_kernel, kRowThreads);
+    const int grid = persistent_grid(dev, ((long long)n + kRowThreads - 1) / kRowThreads, occ < 8 ? occ : 8, 1 << 20);
+    spmv_rows_kernel<<<grid, kRowThreads, 0, s>>>(n, rowptr, col, val, x, y);
+  } else if (kind == kSpmvTma) {
     const int grid = persistent_grid(dev, ntiles, spmv_tma_blocks_per_sm(), 1 << 20);
     spmv_tma_kernel<<<grid, tma::kThreads, tma::kSmemBytes, s>>>(n, nnz, rowptr, col, val, x, y);
   } else {

@@ -74,20 +74,6 @@ constexpr size_t kSmemBytesF32 = sizeof(SmemT<float>);
 constexpr size_t kSmemBytesF32x2 = sizeof(SmemT<float, 2>);
 static_assert(kMinBlocks * kSmemBytes <= 232448, "TMA pipeline stages exceed the shared memory of an SM");
 
-__device__ __forceinline__ double to_f64(double v) { return v; }
-
-// Exact float -> double for normal numbers, signed zero for zero/subnormal
-// inputs (callers store no subnormal values), inf/nan kept.
-__device__ __forceinline__ double to_f64(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned ex = (u >> 23) & 0xffu;
-  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-  if (ex == 0) return __longlong_as_double((long long)sign);
-  const unsigned long long e64 = ex == 0xffu ? 2047ull : (unsigned long long)(ex + 896u);
-  const unsigned long long man = (unsigned long long)(u & 0x7fffffu) << 29;
-  return __longlong_as_double((long long)(sign | (e64 << 52) | man));
-}
-
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
@@ -141,25 +127,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
-// A stored value in the arithmetic type X of the sum: FP64 values as they
-// are, FP32 values widened exactly for an FP64 sum or kept for an FP32 sum.
-template <class X>
-__device__ __forceinline__ X as_x(double v) { return v; }
-template <class X>
-__device__ __forceinline__ X as_x(float v);
-template <>
-__device__ __forceinline__ double as_x<double>(float v) { return to_f64(v); }
-template <>
-__device__ __forceinline__ float as_x<float>(float v) { return v; }
-
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_sum_any(double v) { return warp_sum(v); }
-__device__ __forceinline__ float warp_sum_any(float v) { return warp_sum_f(v); }
-
 // Row `row` of the matrix from global memory by one warp (lane-strided
 // entries, fixed butterfly); result valid in every lane.
 template <class V, class XAt>
@@ -171,17 +138,6 @@ __device__ __forceinline__ auto warp_row(const int* __restrict__ rowptr, const i
   X s = X(0);
   for (int k = a + lane; k < e; k += kWarp) s = fma(as_x<X>(__ldg(val + k)), gather_at(x, __ldg(col + k)), s);
   return warp_sum_any(s);
-}
-
-// The epilogue operand of a row: aux[row] for an array (0 when null), or
-// aux(row) for a functor.
-template <class A>
-__device__ __forceinline__ A aux_at(const A* __restrict__ aux, int row) {
-  return aux ? __ldg(aux + row) : A(0);
-}
-template <class F>
-__device__ __forceinline__ auto aux_at(F& f, int row) -> decltype(f(row)) {
-  return f(row);
 }
 
 // Sums of two adjacent rows whose entries are [a, m) and [m, e): the column
