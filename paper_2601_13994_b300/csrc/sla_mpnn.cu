@@ -131,11 +131,13 @@ __global__ void __launch_bounds__(kDT) dense_fwd_kernel(int n, int K1, const flo
   // output is still the sequential sum over k = 0 .. K-1 started from the
   // bias, as before.
   constexpr int kRowsT = 64, kRR = kRowsT / 8;
-  __shared__ __align__(16) float Ws[kMaxM * (kMaxK + 4)];
-  __shared__ __align__(16) float Xs[kRowsT * (kMaxK + 4)];
+  // dynamic shared memory sized for this layer: W [M][S] then X [64][S]
+  extern __shared__ __align__(16) float dsm_f[];
   const int K = K1 + K2;
   const int Kp = (K + 3) & ~3;
   const int S = Kp + 4;
+  float* Ws = dsm_f;
+  float* Xs = dsm_f + M * S;
   for (int idx = threadIdx.x; idx < M * Kp; idx += kDT) {
     const int m = idx / Kp, k = idx % Kp;
     Ws[m * S + k] = k < K ? __bfloat162float(W[m * K + k]) : 0.0f;
@@ -650,12 +652,18 @@ extern "C" int32_t sla_mp_dense_fwd(int32_t n, int32_t K1, const float* X1, int3
   if (n == 0) return SLA_OK;
   if (!W_bf16 || !Y || (K1 && !X1) || (K2 && !X2)) return SLA_ERR_INVALID;
   const int nm = (M + 31) / 32;
-  const int blocks = grid_rows(n, 64, 148 * 4);
+  const int S = ((K1 + K2 + 3) & ~3) + 4;
+  const size_t smem = sizeof(float) * (size_t)(M + 64) * S;
+  const void* fn = nm == 1 ? (const void*)dense_fwd_kernel<1> : nm == 2 ? (const void*)dense_fwd_kernel<2>
+                                                                          : (const void*)dense_fwd_kernel<3>;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kDT, smem) != cudaSuccess || occ < 1) occ = 1;
+  const int blocks = grid_rows(n, 64, 148 * (occ < 8 ? occ : 8));
   cudaStream_t s = (cudaStream_t)stream;
   const __nv_bfloat16* Wb = (const __nv_bfloat16*)W_bf16;
-  if (nm == 1) dense_fwd_kernel<1><<<blocks, kDT, 0, s>>>(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y);
-  else if (nm == 2) dense_fwd_kernel<2><<<blocks, kDT, 0, s>>>(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y);
-  else dense_fwd_kernel<3><<<blocks, kDT, 0, s>>>(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y);
+  if (nm == 1) dense_fwd_kernel<1><<<blocks, kDT, smem, s>>>(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y);
+  else if (nm == 2) dense_fwd_kernel<2><<<blocks, kDT, smem, s>>>(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y);
+  else dense_fwd_kernel<3><<<blocks, kDT, smem, s>>>(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y);
   MP_LAUNCH_CHECK();
   return SLA_OK;
 }
