@@ -106,7 +106,22 @@ def _profile_multi(dev, max_iter):
     return {"iters": [int(i) for i in info.iters]}
 
 
+def _profile_bicgstab(dev, max_iter):
+    """3D convection-diffusion 128^3, cell Peclet 10 (the BiCGStab row)."""
+    import torch
+
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import sla
+    rp, c, v = I.convdiff3d(128, 10.0)
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    vt = torch.from_numpy(v).to(dev)
+    bt = torch.from_numpy(I.rhs_uniform(len(rp) - 1, 5)).to(dev)
+    x, info = sla.bicgstab(A, vt, bt, rtol=1e-8, max_iter=max_iter, graph=False)
+    return {"iters": info.iters, "status": info.status}
+
+
 PROFILE_ROWS = {
+    "bicgstab_convdiff3d_128": _profile_bicgstab,
     "ggt_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "ggt"),
     "jacobi_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "jacobi"),
     "multi_512x16": _profile_multi,
