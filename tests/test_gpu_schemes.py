@@ -27,6 +27,14 @@ x = I.rhs_uniform(3000, 6)
 A = sla.CSRMatrix.from_numpy(rp, c)
 y = sla.spmv(A, torch.from_numpy(v).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
 out["spmv"] = rel(y, oracle.spmv(rp, c, v, x))
+# misaligned arrays (views offset by one element): the TMA pipeline's bulk
+# copies need 16-byte alignment, so every tile takes the warp-per-row path
+cpad = torch.zeros(len(c) + 1, dtype=torch.int32, device="cuda"); cpad[1:] = torch.from_numpy(c).cuda()
+vpad = torch.zeros(len(v) + 1, dtype=torch.float64, device="cuda"); vpad[1:] = torch.from_numpy(v).cuda()
+rpad = torch.zeros(len(rp) + 1, dtype=torch.int32, device="cuda"); rpad[1:] = torch.from_numpy(rp).cuda()
+Am = sla.CSRMatrix(rpad[1:], cpad[1:])
+ym = sla.spmv(Am, vpad[1:], torch.from_numpy(x).cuda()).cpu().numpy()
+out["spmv_misaligned"] = rel(ym, oracle.spmv(rp, c, v, x))
 rp, c, v = I.diffusion3d_random(20, 3)
 b = I.rhs_uniform(len(rp) - 1, 4)
 A = sla.CSRMatrix.from_numpy(rp, c)
@@ -64,7 +72,7 @@ def test_every_spmv_scheme_matches_oracle(scheme):
     res = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode == 0, res.stderr[-3000:]
     out = json.loads(res.stdout.strip().splitlines()[-1])
-    assert out["spmv"] <= 1e-14
+    assert out["spmv"] <= 1e-14 and out["spmv_misaligned"] <= 1e-14
     for k in ("cg", "bicgstab", "ggt"):
         assert out[k][1] == 0, (k, out[k])
         assert out[k][0] <= 1e-8, (k, out[k])
