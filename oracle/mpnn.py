@@ -143,4 +143,4 @@ def loss_and_grads(params: dict, rp, c, v, b, xstar):
     grp, gcol, gv = forward(P, rp, c, v)
     L = loss(grp, gcol, gv, rp, c, v, b, xstar)
     L.backward()
-    return float(L), {k: t.grad.numpy().copy() for k, t in P.items()}, gv.detach().numpy()
+    return float(L.detach()), {k: t.grad.numpy().copy() for k, t in P.items()}, gv.detach().numpy()

@@ -102,3 +102,27 @@ def test_training_beats_jacobi_on_unseen_system():
     assert info.true_rel_res <= 2e-8
     assert info.iters < ij.iters
     assert rel(x.cpu().numpy(), xj.cpu().numpy()) <= 1e-6
+
+
+@pytest.mark.slow
+def test_trained_factor_on_unseen_1024_system():
+    """Config 5 evaluation size: after the bench's short training recipe the
+    learned G G^T PCG reaches rtol 1e-8 on the unseen 2D 1024^2 system with
+    the FP64 true residual inside 2 rtol, in fewer iterations than
+    Jacobi-PCG, and the solution agrees with Jacobi-PCG's."""
+    model = LP.LearnedPreconditioner(seed=0)
+    LP.train(model, systems=48, steps=800, lr=3e-3, n_lo=64, n_hi=128, log_every=400)
+    rp, c, v = I.diffusion2d_random(1024, 900001, 1.0)
+    A = csr(rp, c)
+    vt = to_dev(v)
+    bt = to_dev(I.rhs_uniform(len(rp) - 1, 77))
+    xj, ij = sla.cg(A, vt, bt, rtol=1e-8)
+    G, gv = model.factor(A, vt)
+    xg, ig = sla.cg_ggt(A, vt, G, gv, bt, rtol=1e-8)
+    torch.cuda.synchronize()
+    assert ig.status == 0 and ij.status == 0
+    assert ig.true_rel_res <= 2e-8
+    assert ig.iters * 1.5 < ij.iters
+    r = bt - sla.spmv(A, vt, xg)
+    assert float(r.norm() / bt.norm()) <= 2e-8
+    assert rel(xg.cpu().numpy(), xj.cpu().numpy()) <= 1e-5
