@@ -68,7 +68,8 @@ def parse():
 def _profile_ggt(dev, max_iter, precond):
     """2D 1024^2 sigma = 1 (the learned preconditioner's unseen 2D system):
     G-PCG with an untrained but non-trivial head (the kernels' cost does not
-    depend on the weights), or Jacobi-PCG."""
+    depend on the weights), or Jacobi-PCG (per-phase kernels from a host
+    loop, or the single cooperative launch)."""
     import torch
 
     from paper_2601_13994_b300 import inputs as I
@@ -80,6 +81,9 @@ def _profile_ggt(dev, max_iter, precond):
     bt = torch.from_numpy(I.rhs_uniform(len(rp) - 1, 77)).to(dev)
     if precond == "jacobi":
         x, info = sla.cg(A, vt, bt, rtol=1e-8, max_iter=max_iter, graph=False)
+    elif precond == "coop":
+        # Jacobi-PCG as one cooperative launch (init, iterations, final residual)
+        x, info = sla.cg(A, vt, bt, rtol=1e-8, max_iter=max_iter, max_restarts=0)
     else:
         m = LP.LearnedPreconditioner(device=dev, seed=0)
         m.view("v").fill_(0.05)
@@ -124,6 +128,7 @@ PROFILE_ROWS = {
     "bicgstab_convdiff3d_128": _profile_bicgstab,
     "ggt_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "ggt"),
     "jacobi_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "jacobi"),
+    "coop_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "coop"),
     "multi_512x16": _profile_multi,
 }
 

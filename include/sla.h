@@ -62,6 +62,11 @@ extern "C" {
                                    driven by the host (checks the device state
                                    every 16 iterations, synchronising the
                                    stream) instead of one graph launch       */
+#define SLA_FLAG_NO_COOP 2      /* sla_cg, sla_cg_ggt, sla_cg_noalloc and the
+                                   CG adjoint: use the per-phase kernels
+                                   (graph or host loop) even at sizes where
+                                   the solve would run as one cooperative
+                                   launch                                    */
 
 /* Workspace kinds for sla_workspace_size(). */
 #define SLA_WS_CG 1
@@ -168,11 +173,16 @@ int32_t sla_spmv(const sla_csr* A, const double* val, const double* x,
  * residual, then recomputes b - A x; if that is above twice the target the
  * recurrence restarts from x (at most max_restarts times).  b = 0 gives
  * x = 0 after 0 iterations.  *info (DEVICE) receives the outcome.
- * The whole solve is one CUDA-graph launch whose device-side while-loop
- * decides convergence; the host is not synchronised.  The first call with a
- * given workspace address and sizes builds and caches that graph.  With
- * SLA_FLAG_HOST_LOOP the same kernels are launched one by one on `stream`
- * and the call returns after the loop has ended (it synchronises `stream`).
+ * Systems of up to 2.5 Mi rows run as ONE cooperative kernel launch (every
+ * block resident, grid barriers between the phases of an iteration, the
+ * convergence test taken identically in every block); larger systems, or
+ * calls with SLA_FLAG_NO_COOP, run one CUDA-graph launch whose device-side
+ * while-loop decides convergence.  Either way the host is not synchronised.
+ * The first graph call with a given workspace address and sizes builds and
+ * caches that graph.  With SLA_FLAG_HOST_LOOP the per-phase kernels are
+ * launched one by one on `stream` and the call returns after the loop has
+ * ended (it synchronises `stream`).  A grid barrier that waits more than
+ * about 2 s ends the solve with SLA_ERR_TIMEOUT in *info.
  * Workspace: sla_workspace_size(SLA_WS_CG, n, nnz, 1, &bytes). */
 int32_t sla_cg(const sla_csr* A, const double* val, const double* b,
                double* x, const sla_opts* opts, sla_info* info, void* ws,
@@ -187,8 +197,10 @@ int32_t sla_cg(const sla_csr* A, const double* val, const double* b,
  * CSR (device: g_rowptr [n+1], g_col, g_val [nnz_g]); GT: its transpose
  * pattern from sla_csr_transpose of G (perm into g_val; the values of G^T
  * are gathered once per call).  Same stopping rule, true-residual restart,
- * statuses (NOT_SPD on p^T A p <= 0 or r^T z <= 0), graph / host-loop
- * execution and info record as sla_cg (opts->precond is ignored).
+ * statuses (NOT_SPD on p^T A p <= 0 or r^T z <= 0), execution forms
+ * (one cooperative launch up to 1.5 Mi rows unless SLA_FLAG_NO_COOP, else
+ * the graph, or the host loop with SLA_FLAG_HOST_LOOP) and info record as
+ * sla_cg (opts->precond is ignored).
  * Workspace: SLA_WS_CG_GGT with nnz = nnz_g. */
 int32_t sla_cg_ggt(const sla_csr* A, const double* val, const sla_csr* G,
                    const double* g_val, const sla_csr_t* GT, const double* b,
@@ -499,9 +511,12 @@ int32_t sla_grad_values_batched(int32_t batch, int32_t shared_pattern,
  * calls that overlap on the GPU -- different streams, threads or processes
  * sharing the context -- race and must be serialised by the caller.
  *
- * The loop is driven from the host (as with SLA_FLAG_HOST_LOOP): the call
- * returns after the solve has finished on `stream`.  Other arguments,
- * options and the *info record behave as for sla_cg. */
+ * Systems that sla_cg solves in one cooperative launch are solved the same
+ * way here (the call returns without synchronising); the others -- and every
+ * call with SLA_FLAG_HOST_LOOP or SLA_FLAG_NO_COOP -- are driven from the
+ * host as with SLA_FLAG_HOST_LOOP (no graph objects are created) and the call
+ * returns after the solve has finished on `stream`.  Other arguments, options
+ * and the *info record behave as for sla_cg. */
 int32_t sla_cg_noalloc(const sla_csr* A, const double* val, const double* b,
                        double* x, const sla_opts* opts, sla_info* info,
                        void* stream);

@@ -27,6 +27,7 @@ SLA_PRECOND_JACOBI = 1
 SLA_PRECOND_GGT = 2
 
 SLA_FLAG_HOST_LOOP = 1
+SLA_FLAG_NO_COOP = 2
 
 SLA_WS_CG = 1
 SLA_WS_BICGSTAB = 2

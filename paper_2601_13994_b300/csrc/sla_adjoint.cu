@@ -12,7 +12,7 @@
 
 namespace sla {
 
-int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags);
+int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags, bool allow_graph = true);
 int launch_bicgstab(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags);
 KrylovDesc make_desc(const sla_csr* A, const double* val, const double* b, double* x,
                      const sla_opts* o, sla_info* info);

@@ -562,8 +562,20 @@ int run_host_loop(const CgPtrs& P, const KrylovDesc& desc, K1Launch k1, int g1, 
   return SLA_OK;
 }
 
-int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags) {
+bool use_cg_coop(long long n, bool ggt);
+int launch_cg_coop(const KrylovDesc& desc, void* ws, cudaStream_t s, bool* launched);
+
+// allow_graph = false: where the cooperative launch is not taken, drive the
+// loop from the host (no graph objects), as the allocation-free entry needs.
+int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags, bool allow_graph = true) {
   const int n = desc.n;
+  if (!(flags & (SLA_FLAG_HOST_LOOP | SLA_FLAG_NO_COOP)) && use_cg_coop(n, false)) {
+    // one cooperative launch per solve (sla_cg_coop.cu) where the device runs it
+    bool launched = false;
+    const int rc = launch_cg_coop(desc, ws, s, &launched);
+    if (rc != SLA_OK || launched) return rc;
+  }
+  if (!allow_graph) flags |= SLA_FLAG_HOST_LOOP;
   const CgLayout L = cg_layout(n);
   char* base = (char*)ws;
   CgPtrs P;
@@ -613,7 +625,8 @@ int validate_solve_args(const sla_csr* A, const double* val, const double* b, co
   if (A->nnz > 0 && (A->col == nullptr || val == nullptr)) return SLA_ERR_INVALID;
   if (A->n > 0 && (const void*)b == (const void*)x) return SLA_ERR_INVALID;
   if (!(o->rtol >= 0.0) || !(o->atol >= 0.0) || o->max_iter < 0 || o->max_restarts < 0 ||
-      o->max_restarts > 16 || (o->use_x0 != 0 && o->use_x0 != 1) || (o->flags & ~1) != 0)
+      o->max_restarts > 16 || (o->use_x0 != 0 && o->use_x0 != 1) ||
+      (o->flags & ~(SLA_FLAG_HOST_LOOP | SLA_FLAG_NO_COOP)) != 0)
     return SLA_ERR_INVALID;
   if (ws == nullptr || ((uintptr_t)ws & 255u) != 0 || ws_bytes < need) return SLA_ERR_WORKSPACE;
   return SLA_OK;
@@ -725,6 +738,7 @@ extern "C" int32_t sla_cg_noalloc(const sla_csr* A, const double* val, const dou
   d.max_restarts = opts->max_restarts;
   d.precond = opts->precond;
   d.use_x0 = opts->use_x0;
-  // plain launches from a host loop: no graph objects are created
-  return launch_cg(d, ws, s, opts->flags | SLA_FLAG_HOST_LOOP);
+  // one cooperative launch, else plain launches from a host loop: no graph
+  // objects are created either way
+  return launch_cg(d, ws, s, opts->flags, /*allow_graph=*/false);
 }

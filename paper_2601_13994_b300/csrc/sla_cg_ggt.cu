@@ -57,6 +57,18 @@ struct VSmem {
   bool last;
 };
 
+// FP32 values of G and of G^T (gathered through perm_t), for the
+// cooperative solve, which takes them ready-made.
+__global__ void __launch_bounds__(kVT) ggt_values_kernel(const double* __restrict__ g_val,
+                                                         const int* __restrict__ perm_t, int nnz_g,
+                                                         float* __restrict__ gv, float* __restrict__ gtv) {
+  const int stride = gridDim.x * kVT;
+  for (int k = blockIdx.x * kVT + threadIdx.x; k < nnz_g; k += stride) {
+    gv[k] = f32_of(__ldg(g_val + k));
+    gtv[k] = f32_of(__ldg(g_val + __ldg(perm_t + k)));
+  }
+}
+
 __global__ void ggt_write_desc_kernel(KrylovDesc* dst, KrylovDesc src, KrylovState* st) {
   *dst = src;
   for (int i = 0; i < 8; ++i) st->cnt[i] = 0u;
@@ -546,6 +558,9 @@ int run_host_loop(GPtrs P, const KrylovDesc& desc, const BodyKernels& k, cudaStr
 
 KrylovDesc make_desc(const sla_csr* A, const double* val, const double* b, double* x,
                      const sla_opts* o, sla_info* info);
+bool use_cg_coop(long long n, bool ggt);
+int launch_ggt_coop(const KrylovDesc& desc, KrylovState* st, double* part, double* r, double* p, double* q,
+                    double* t, const float* gv, const float* gtv, cudaStream_t s, bool* launched);
 
 }  // namespace sla
 
@@ -589,6 +604,17 @@ extern "C" int32_t sla_cg_ggt(const sla_csr* A, const double* val, const sla_csr
   P.gv = (float*)(base + L.gv);
   P.gtv = (float*)(base + L.gtv);
   const int dev = current_device();
+  if (!(opts->flags & (SLA_FLAG_HOST_LOOP | SLA_FLAG_NO_COOP)) && use_cg_coop(n, true)) {
+    // one cooperative launch per solve (sla_cg_coop.cu) where the device runs it
+    if (G->nnz > 0) {
+      const int grid = persistent_grid(dev, ((long long)G->nnz + kVT - 1) / kVT, 8, kMaxBlocks);
+      ggt_values_kernel<<<grid, kVT, 0, s>>>(g_val, GT->perm_t, G->nnz, P.gv, P.gtv);
+      SLA_CUDA_TRY(cudaGetLastError());
+    }
+    bool launched = false;
+    rc = launch_ggt_coop(d, P.st, P.part, P.r, P.p, P.q, P.t, P.gv, P.gtv, s, &launched);
+    if (rc != SLA_OK || launched) return rc;
+  }
   const BodyKernels bk = body_kernels(dev, n, G->nnz);
   if (opts->flags & SLA_FLAG_HOST_LOOP) return run_host_loop(P, d, bk, s);
   Key key{dev, ws, n, A->nnz, G->nnz, bk.k1.grid, bk.gt.grid, bk.gv, bk.kind, bk.rpt};

@@ -170,16 +170,16 @@ def spmv(A: CSRMatrix, val: torch.Tensor, x: torch.Tensor, out: torch.Tensor | N
 _PRECOND = {"none": L.SLA_PRECOND_NONE, "jacobi": L.SLA_PRECOND_JACOBI}
 
 
-def _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, n, graph=True):
+def _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, n, graph=True, cooperative=True):
     mi = default_max_iter(n) if max_iter is None else int(max_iter)
     if precond not in _PRECOND:
         raise ValueError("precond must be one of %s" % sorted(_PRECOND))
-    return L.SlaOpts(float(rtol), float(atol), mi, int(max_restarts), _PRECOND[precond], int(use_x0),
-                     0 if graph else L.SLA_FLAG_HOST_LOOP)
+    flags = (0 if graph else L.SLA_FLAG_HOST_LOOP) | (0 if cooperative else L.SLA_FLAG_NO_COOP)
+    return L.SlaOpts(float(rtol), float(atol), mi, int(max_restarts), _PRECOND[precond], int(use_x0), flags)
 
 
 def _krylov(fn_name: str, ws_kind: int, A: CSRMatrix, val, b, rtol, atol, max_iter, precond, x0,
-            max_restarts, out, graph):
+            max_restarts, out, graph, cooperative=True):
     _need(val, torch.float64, A.device, "val", A.nnz)
     _need(b, torch.float64, A.device, "b", A.n)
     if out is None:
@@ -194,7 +194,7 @@ def _krylov(fn_name: str, ws_kind: int, A: CSRMatrix, val, b, rtol, atol, max_it
             x.copy_(x0)
         use_x0 = 1
     info = torch.empty((1, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
-    o = _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, A.n, graph)
+    o = _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, A.n, graph, cooperative)
     ws = workspace(ws_kind, A.n, A.nnz, 1, A.device)
     fn = getattr(L.lib(), fn_name)
     L.check(fn_name, fn(ctypes.byref(A.c), _ptr(val), _ptr(b), _ptr(x), ctypes.byref(o), info.data_ptr(),
@@ -212,13 +212,16 @@ def bicgstab(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 
 
 def cg(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10, atol: float = 0.0,
        max_iter: int | None = None, precond: str = "jacobi", x0: torch.Tensor | None = None,
-       max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True):
+       max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True,
+       cooperative: bool = True):
     """Preconditioned CG for SPD A (Algorithm 1, one process).  Returns
-    (x, SolveInfo).  With ``graph=True`` the solve is one graph launch and
-    nothing synchronises until the info is read; ``graph=False`` launches the
-    same kernels from a host loop (synchronising the stream)."""
+    (x, SolveInfo).  Up to 2.5 Mi rows the solve is one cooperative kernel
+    launch (``cooperative=False`` opts out); otherwise, with ``graph=True``,
+    it is one graph launch.  Nothing synchronises until the info is read;
+    ``graph=False`` launches the per-phase kernels from a host loop
+    (synchronising the stream)."""
     return _krylov("sla_cg", L.SLA_WS_CG, A, val, b, rtol, atol, max_iter, precond, x0, max_restarts, out,
-                   graph)
+                   graph, cooperative)
 
 
 # ---------------------------------------------------------------------------
@@ -320,7 +323,7 @@ _ADJ = {"cg": L.SLA_ADJ_CG, "bicgstab": L.SLA_ADJ_BICGSTAB}
 def adjoint_backward(A: CSRMatrix, val: torch.Tensor, x: torch.Tensor, grad_x: torch.Tensor, *,
                      method: str = "cg", rtol: float = 1e-10, atol: float = 0.0,
                      max_iter: int | None = None, precond: str = "jacobi", max_restarts: int = 2,
-                     graph: bool = True):
+                     graph: bool = True, cooperative: bool = True):
     """Solve A^T lambda = grad_x; returns (grad_b = lambda, grad_val, SolveInfo)."""
     _need(val, torch.float64, A.device, "val", A.nnz)
     _need(x, torch.float64, A.device, "x", A.n)
@@ -328,7 +331,7 @@ def adjoint_backward(A: CSRMatrix, val: torch.Tensor, x: torch.Tensor, grad_x: t
     gb = torch.empty(A.n, dtype=torch.float64, device=A.device)
     gv = torch.empty(A.nnz, dtype=torch.float64, device=A.device)
     info = torch.empty((1, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
-    o = _opts(rtol, atol, max_iter, max_restarts, precond, 0, A.n, graph)
+    o = _opts(rtol, atol, max_iter, max_restarts, precond, 0, A.n, graph, cooperative)
     atp = None
     if method == "bicgstab":
         transpose_of(A)
@@ -714,9 +717,12 @@ def solve_multi(A: CSRMatrix, val: torch.Tensor, B: torch.Tensor, *, strict: boo
 
 def cg_ggt(A: CSRMatrix, val: torch.Tensor, G: CSRMatrix, g_val: torch.Tensor, b: torch.Tensor, *,
            rtol: float = 1e-10, atol: float = 0.0, max_iter: int | None = None, x0: torch.Tensor | None = None,
-           max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True):
+           max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True,
+           cooperative: bool = True):
     """PCG with z = G (G^T r), G lower triangular (CSR pattern G, values
-    g_val).  The CSR of G^T is computed once per pattern and cached."""
+    g_val).  The CSR of G^T is computed once per pattern and cached.  Up to
+    1.5 Mi rows the solve is one cooperative kernel launch (``cooperative=False``
+    opts out); otherwise one graph launch (``graph=False``: a host loop)."""
     _need(val, torch.float64, A.device, "val", A.nnz)
     _need(g_val, torch.float64, A.device, "g_val", G.nnz)
     _need(b, torch.float64, A.device, "b", A.n)
@@ -730,7 +736,7 @@ def cg_ggt(A: CSRMatrix, val: torch.Tensor, G: CSRMatrix, g_val: torch.Tensor, b
             x.copy_(x0)
         use_x0 = 1
     info = torch.empty((1, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
-    o = _opts(rtol, atol, max_iter, max_restarts, "jacobi", use_x0, A.n, graph)
+    o = _opts(rtol, atol, max_iter, max_restarts, "jacobi", use_x0, A.n, graph, cooperative)
     ws = workspace(L.SLA_WS_CG_GGT, A.n, G.nnz, 1, A.device)
     L.check("sla_cg_ggt", L.lib().sla_cg_ggt(
         ctypes.byref(A.c), val.data_ptr(), ctypes.byref(G.c), g_val.data_ptr(), ctypes.byref(G._transpose_c),

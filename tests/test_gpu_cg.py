@@ -144,13 +144,15 @@ def test_full_size_diffusion3d_256_true_residual():
 
 
 def test_host_loop_mode_reproduces_graph_mode():
-    """Same kernels, same grids: the host-driven loop must give the same bits."""
+    """Same kernels, same grids: the host-driven loop must give the same bits
+    as the graph (the per-phase kernels; cooperative=False, since this size
+    would otherwise run as one cooperative launch)."""
     rp, c, v = I.diffusion3d_random(20, 9)
     n = 8000
     A = csr(rp, c)
     vt = to_dev(v)
     b = to_dev(I.rhs_uniform(n, 3))
-    xg, ig = sla.cg(A, vt, b, rtol=1e-10)
+    xg, ig = sla.cg(A, vt, b, rtol=1e-10, cooperative=False)
     xh, ih = sla.cg(A, vt, b, rtol=1e-10, graph=False)
     torch.cuda.synchronize()
     assert torch.equal(xg, xh) and ig.iters == ih.iters and ig.status == ih.status == 0

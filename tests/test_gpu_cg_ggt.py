@@ -75,9 +75,18 @@ def test_ggt_edge_cases_and_host_loop():
     x, info = sla.cg_ggt(A, to_dev(v), Gm, gv, to_dev(np.zeros(n)))
     assert info.status == 0 and info.iters == 0 and not x.cpu().numpy().any()
     b = to_dev(I.rhs_uniform(n, 4))
-    xg, ig = sla.cg_ggt(A, to_dev(v), Gm, gv, b, rtol=1e-11)
+    # graph and host loop run the same per-phase kernels: same bits
+    xg, ig = sla.cg_ggt(A, to_dev(v), Gm, gv, b, rtol=1e-11, cooperative=False)
     xh, ih = sla.cg_ggt(A, to_dev(v), Gm, gv, b, rtol=1e-11, graph=False)
     torch.cuda.synchronize()
     assert torch.equal(xg, xh) and ig.iters == ih.iters
-    _, ic = sla.cg_ggt(A, to_dev(v), Gm, gv, b, rtol=1e-15, max_iter=3)
-    assert ic.status_name == "NOT_CONVERGED" and ic.iters == 3
+    # the cooperative launch: same method, other summation grid
+    xc, ic = sla.cg_ggt(A, to_dev(v), Gm, gv, b, rtol=1e-11)
+    xc2, ic2 = sla.cg_ggt(A, to_dev(v), Gm, gv, b, rtol=1e-11)
+    torch.cuda.synchronize()
+    assert torch.equal(xc, xc2) and ic.iters == ic2.iters
+    assert ic.status == 0 and abs(ic.iters - ig.iters) <= 2
+    assert float((xc - xg).norm() / xg.norm()) <= 1e-8
+    for coop in (True, False):
+        _, ic = sla.cg_ggt(A, to_dev(v), Gm, gv, b, rtol=1e-15, max_iter=3, cooperative=coop)
+        assert ic.status_name == "NOT_CONVERGED" and ic.iters == 3

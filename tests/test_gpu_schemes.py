@@ -1,7 +1,9 @@
 """Every SpMV scheme against the oracle: the solvers pick the row-per-thread
 kernels at n <= 4 Mi rows and the TMA tile pipeline above; SLA_SPMV_KERNEL
 forces one scheme for a whole process, so each scheme runs here in a child
-process on small systems (SpMV, CG, BiCGStab, G G^T PCG)."""
+process on small systems (SpMV, CG, BiCGStab, G G^T PCG; the CG solves with
+cooperative=False, since at these sizes they would otherwise run as one
+cooperative launch that does not use the SpMV kernels)."""
 import json
 import os
 import subprocess
@@ -38,7 +40,7 @@ out["spmv_misaligned"] = rel(ym, oracle.spmv(rp, c, v, x))
 rp, c, v = I.diffusion3d_random(20, 3)
 b = I.rhs_uniform(len(rp) - 1, 4)
 A = sla.CSRMatrix.from_numpy(rp, c)
-xg, info = sla.cg(A, torch.from_numpy(v).cuda(), torch.from_numpy(b).cuda(), rtol=1e-10)
+xg, info = sla.cg(A, torch.from_numpy(v).cuda(), torch.from_numpy(b).cuda(), rtol=1e-10, cooperative=False)
 xo, io = oracle.pcg(rp, c, v, b, rtol=1e-13)
 out["cg"] = [rel(xg.cpu().numpy(), xo), int(info.status)]
 rp, c, v = I.convdiff3d(16, 10.0)
@@ -58,7 +60,7 @@ gval = np.where(gcol == rows[keep], 1.0 / np.sqrt(d[rows[keep]]), -0.05 / np.sqr
 b = I.rhs_uniform(n, 6)
 G = sla.CSRMatrix.from_numpy(grp, gcol)
 xg, info = sla.cg_ggt(A := sla.CSRMatrix.from_numpy(rp, c), torch.from_numpy(v).cuda(), G,
-                      torch.from_numpy(gval).cuda(), torch.from_numpy(b).cuda(), rtol=1e-10)
+                      torch.from_numpy(gval).cuda(), torch.from_numpy(b).cuda(), rtol=1e-10, cooperative=False)
 xo, io = oracle.pcg(rp, c, v, b, rtol=1e-13)
 out["ggt"] = [rel(xg.cpu().numpy(), xo), int(info.status)]
 print(json.dumps(out))

@@ -30,10 +30,10 @@ def _info_host(raw):
     return int(h[:4].view(np.int32)[0]), int(h[4:8].view(np.int32)[0]), float(h[8:16].view(np.float64)[0])
 
 
-def _solve_noalloc(A, val, b, rtol):
+def _solve_noalloc(A, val, b, rtol, flags=0):
     x = torch.empty_like(b)
     info = torch.empty(L.INFO_BYTES, dtype=torch.uint8, device=b.device)
-    o = L.SlaOpts(rtol, 0.0, sla.default_max_iter(A.n), 2, L.SLA_PRECOND_JACOBI, 0, 0)
+    o = L.SlaOpts(rtol, 0.0, sla.default_max_iter(A.n), 2, L.SLA_PRECOND_JACOBI, 0, flags)
     rc = L.lib().sla_cg_noalloc(ctypes.byref(A.c), val.data_ptr(), b.data_ptr(), x.data_ptr(),
                                 ctypes.byref(o), info.data_ptr(),
                                 torch.cuda.current_stream().cuda_stream)
@@ -67,6 +67,12 @@ def test_noalloc_matches_workspace_entry_point_two_calls():
         assert st_ref == st_na == L.SLA_OK
         assert it_na == it_ref
         err = float(torch.linalg.norm(x_na - x_ref) / torch.linalg.norm(x_ref))
+        assert err <= REL_TOL, err
+        # the host-driven per-phase kernels (what sizes beyond the cooperative
+        # launch take) on the same array
+        x_h, (it_h, st_h, _) = _solve_noalloc(A, val, b, 1e-10, flags=L.SLA_FLAG_NO_COOP)
+        assert st_h == L.SLA_OK and abs(it_h - it_ref) <= 2
+        err = float(torch.linalg.norm(x_h - x_ref) / torch.linalg.norm(x_ref))
         assert err <= REL_TOL, err
 
 
