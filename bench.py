@@ -68,8 +68,8 @@ def parse():
 def _profile_ggt(dev, max_iter, precond):
     """2D 1024^2 sigma = 1 (the learned preconditioner's unseen 2D system):
     G-PCG with an untrained but non-trivial head (the kernels' cost does not
-    depend on the weights), or Jacobi-PCG (per-phase kernels from a host
-    loop, or the single cooperative launch)."""
+    depend on the weights), or Jacobi-PCG; per-phase kernels from a host
+    loop, or (coop, ggt_coop) the single cooperative launch."""
     import torch
 
     from paper_2601_13994_b300 import inputs as I
@@ -89,7 +89,10 @@ def _profile_ggt(dev, max_iter, precond):
         m.view("v").fill_(0.05)
         m._sync_bf16()
         G, gv = m.factor(A, vt)
-        x, info = sla.cg_ggt(A, vt, G, gv, bt, rtol=1e-8, max_iter=max_iter, graph=False)
+        if precond == "ggt_coop":
+            x, info = sla.cg_ggt(A, vt, G, gv, bt, rtol=1e-8, max_iter=max_iter, max_restarts=0)
+        else:
+            x, info = sla.cg_ggt(A, vt, G, gv, bt, rtol=1e-8, max_iter=max_iter, graph=False)
     return {"iters": info.iters, "status": info.status}
 
 
@@ -129,6 +132,7 @@ PROFILE_ROWS = {
     "ggt_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "ggt"),
     "jacobi_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "jacobi"),
     "coop_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "coop"),
+    "ggt_coop_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "ggt_coop"),
     "multi_512x16": _profile_multi,
 }
 
