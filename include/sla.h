@@ -445,7 +445,8 @@ int32_t sla_adjoint_backward(const sla_csr* A, const sla_csr_t* AT,
  * batch and a converged system frees its CTA for the next.  The Krylov
  * vectors stay in shared memory when 5 n doubles fit, else in the
  * workspace.  config: 0 = automatic; low 4 bits 1/2/3 = 256/512/1024
- * threads per CTA, bit 4 set = vectors in global memory (the autotuner in
+ * threads per CTA, bit 4 set = vectors in global memory, bit 32 (lists) = no
+ * block teams for the large systems (the autotuner in
  * the Python layer times these).  The call only enqueues kernels (no host
  * synchronisation), so it can be captured in a CUDA graph.
  * Shared pattern: val [batch, nnz], b and x [batch, n] row-major.
@@ -463,6 +464,12 @@ int32_t sla_cg_batched_shared(const sla_csr* A, int32_t batch,
  * s's start at rowptr + n_off[s] + s; columns are local.  n_max = largest
  * n_s, total_rows = n_off[batch].  order (device, optional): the order in
  * which CTAs take systems (largest first balances the load).
+ * Systems with at least 32768 entries are solved first, each by a team of 3
+ * CTAs of one cooperative launch (the same recurrence with team-wide
+ * reductions and barriers bounded like sla_cg's), so that the largest
+ * systems do not run at one SM's rate while the rest of the GPU idles; the
+ * single-CTA launch then takes the others.  config bit 32 turns the teams
+ * off.  Still no host synchronisation.
  * Workspace: SLA_WS_BATCHED with (total_rows, 1). */
 int32_t sla_cg_batched_list(int32_t batch, int32_t n_max, int32_t total_rows,
                             const int32_t* n_off, const int32_t* nnz_off,

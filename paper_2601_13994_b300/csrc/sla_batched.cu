@@ -39,6 +39,8 @@ struct BatchDesc {
   int n_max, smem_rows;       // rows whose vectors fit the dynamic shared memory
   double rtol, atol;
   int max_iter, max_restarts, precond, use_x0;
+  int skip_nnz;               // list: systems with at least this many entries are
+                              // solved by block teams (0: none)
 };
 
 template <int NT>
@@ -211,6 +213,7 @@ __global__ void __launch_bounds__(NT) batched_pcg_kernel(BatchDesc d) {
       n = d.n_off[s + 1] - n0;
       row0 = (size_t)n0;
       const int e0 = d.nnz_off[s];
+      if (d.skip_nnz > 0 && d.nnz_off[s + 1] - e0 >= d.skip_nnz) continue;  // a team's system
       rp = d.rowptr + n0 + s;
       cl = d.col + e0;
       v = d.val + e0;
@@ -251,7 +254,15 @@ int launch_batched(const BatchDesc& d0, bool use_smem, cudaStream_t s) {
 }
 
 // config: low 4 bits = block size code (1: 256, 2: 512, 3: 1024; 0: auto),
-// bit 4 = keep the vectors in global memory even when they fit on chip.
+// bit 4 = keep the vectors in global memory even when they fit on chip,
+// bit 5 = no block teams for the large systems of a list.
+constexpr int kConfigNoTeams = 32;
+// Systems of a list with at least kTeamMinNnz entries are solved by teams of
+// blocks; the team launch is made when some system can have that many
+// (n_max >= kTeamMinRows).
+constexpr int kTeamMinNnz = 32768;
+constexpr int kTeamMinRows = 2048;
+
 int dispatch(const BatchDesc& d, int config, cudaStream_t s) {
   int code = config & 15;
   const bool use_smem = ((config >> 4) & 1) == 0;
@@ -311,11 +322,20 @@ __global__ void batched_grad_kernel(int batch, int shared_pattern, int n, int nn
 
 }  // namespace
 
+size_t team_scratch_bytes();
+int launch_batched_teams(int batch, int min_nnz, const int* rowptr, const int* col, const int* n_off,
+                         const int* nnz_off, const int* order, const double* val, const double* b, double* x,
+                         sla_info* info, double* gvec, void* scratch, double rtol, double atol, int max_iter,
+                         int max_restarts, int precond, int use_x0, cudaStream_t s, bool* launched);
+
+// Workspace: scheduling counter | block-team scratch | 5 doubles per row of
+// the batch (used by the systems whose vectors do not fit in shared memory,
+// and by the systems the teams solve).
 size_t batched_ws_bytes(long long total_rows) {
-  // scheduling counter + 5 doubles per row of the batch (used by the systems
-  // whose vectors do not fit in shared memory)
-  return 256 + al256((size_t)5 * sizeof(double) * (size_t)(total_rows > 0 ? total_rows : 1));
+  return 256 + team_scratch_bytes() + al256((size_t)5 * sizeof(double) * (size_t)(total_rows > 0 ? total_rows : 1));
 }
+
+double* batched_gvec(void* ws) { return (double*)((char*)ws + 256 + team_scratch_bytes()); }
 
 }  // namespace sla
 
@@ -345,7 +365,7 @@ extern "C" int32_t sla_cg_batched_shared(const sla_csr* A, int32_t batch, const 
   d.x = x;
   d.info = info;
   d.next = (unsigned*)ws;
-  d.gvec = (double*)((char*)ws + 256);
+  d.gvec = batched_gvec(ws);
   d.n_max = A->n;
   fill_opts(d, opts);
   return dispatch(d, config, (cudaStream_t)stream);
@@ -378,10 +398,20 @@ extern "C" int32_t sla_cg_batched_list(int32_t batch, int32_t n_max, int32_t tot
   d.info = info;
   d.order = order;
   d.next = (unsigned*)ws;
-  d.gvec = (double*)((char*)ws + 256);
+  d.gvec = batched_gvec(ws);
   d.n_max = n_max;
   fill_opts(d, opts);
-  return dispatch(d, config, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!(config & kConfigNoTeams) && n_max >= kTeamMinRows) {
+    // the large systems first, by teams of blocks (sla_cg_coop.cu)
+    bool launched = false;
+    const int rc = launch_batched_teams(batch, kTeamMinNnz, rowptr, col, n_off, nnz_off, order, val, b, x, info,
+                                        d.gvec, (char*)ws + 256, opts->rtol, opts->atol, opts->max_iter,
+                                        opts->max_restarts, opts->precond, opts->use_x0, s, &launched);
+    if (rc != SLA_OK) return rc;
+    if (launched) d.skip_nnz = kTeamMinNnz;
+  }
+  return dispatch(d, config, s);
 }
 
 extern "C" int32_t sla_grad_values_batched(int32_t batch, int32_t shared_pattern, int32_t n,

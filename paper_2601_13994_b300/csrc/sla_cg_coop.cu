@@ -74,20 +74,33 @@ __device__ __forceinline__ void coop_rows(int n, int g0, int T, const int* __res
   for (int i = g0; i < n; i += T) f(i, __ldg(rowptr + i), __ldg(rowptr + i + 1));
 }
 
-// Grid totals of NV values: block sums -> partials -> barrier -> every block
+// The blocks that solve one system together: the whole grid, or a team of
+// `size` consecutive blocks of a cooperative launch with its own barrier
+// counter and partial-sum buffers (2 x 4 x size doubles).
+struct Team {
+  GridSync gs;
+  int size, rank;
+  double* part;
+  int* err;
+};
+
+__device__ __forceinline__ bool team_sync(Team& tm, CoopSmem& sm) {
+  return grid_sync(tm.gs, (unsigned)tm.size, tm.err, &sm.flag);
+}
+
+// Team totals of NV values: block sums -> partials -> barrier -> every block
 // adds all partials in the same order.  False if the barrier ran out.
 template <int NV>
-__device__ __forceinline__ bool coop_sums(double (&v)[NV], double* part, int& buf, GridSync& gs,
-                                          int* err, CoopSmem& sm) {
+__device__ __forceinline__ bool coop_sums(double (&v)[NV], Team& tm, int& buf, CoopSmem& sm) {
   block_sums<kCoopThreads, NV>(v, sm.red);
-  const int G = gridDim.x;
-  double* pb = part + (size_t)buf * 4 * G;
+  const int G = tm.size;
+  double* pb = tm.part + (size_t)buf * 4 * G;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int j = 0; j < NV; ++j) pb[j * G + blockIdx.x] = v[j];
+    for (int j = 0; j < NV; ++j) pb[j * G + tm.rank] = v[j];
   }
   buf ^= 1;
-  if (!grid_sync(gs, err, &sm.flag)) return false;
+  if (!team_sync(tm, sm)) return false;
   reduce_partials<kCoopThreads, NV>(pb, G, G, v, sm.red);
   return true;
 }
@@ -197,16 +210,17 @@ __device__ __forceinline__ void coop_after_check(CoopState& s, double ttt, doubl
   }
 }
 
-__global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) cg_coop_kernel(CoopArgs A) {
-  __shared__ CoopSmem sm;
-  __shared__ CoopState s;
-  const KrylovDesc& d = A.d;
+// One Jacobi-PCG solve by a team; d (shared memory) describes the system,
+// r, z, p, q, dinv are its n-vectors.  Rank 0 writes *d.info.  Returns
+// false if a barrier ran out (the caller must then leave the kernel).
+// check_err: also report a timeout flagged by any block of the launch.
+__device__ __forceinline__ bool jacobi_team_solve(const KrylovDesc& d, double* r, double* z, double* p, double* q,
+                                                  double* dinv, Team& tm, bool check_err, CoopSmem& sm,
+                                                  CoopState& s) {
   const int n = d.n;
-  const int T = gridDim.x * kCoopThreads;
-  const int g0 = blockIdx.x * kCoopThreads + threadIdx.x;
+  const int T = tm.size * kCoopThreads;
+  const int g0 = tm.rank * kCoopThreads + threadIdx.x;
   const bool t0 = threadIdx.x == 0;
-  int* err = &A.st->err;
-  GridSync gs{&A.st->cnt[5], 0u};
   int buf = 0;
   bool ok = true;
   auto col_at = [&](int k) { return __ldg(d.col + k); };
@@ -232,17 +246,17 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) cg_coop_kernel(C
         di = 1.0 / diag;
       }
       const double zi = di * ri;
-      A.dinv[i] = di;
-      A.r[i] = ri;
-      A.z[i] = zi;
-      A.p[i] = zi;
+      dinv[i] = di;
+      r[i] = ri;
+      z[i] = zi;
+      p[i] = zi;
       acc[0] = fma(bi, bi, acc[0]);
       acc[1] = fma(ri, ri, acc[1]);
       acc[2] = fma(ri, zi, acc[2]);
     }
     if (!d.use_x0)
       for (int i = g0; i < n; i += T) d.x[i] = 0.0;
-    ok = coop_sums(acc, A.part, buf, gs, err, sm);
+    ok = coop_sums(acc, tm, buf, sm);
     if (ok && t0) coop_after_init(s, acc, d);
     __syncthreads();
   }
@@ -254,11 +268,11 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) cg_coop_kernel(C
       {
         double v[1] = {0.0};
         coop_rows(n, g0, T, d.rowptr, [&](int i, int a, int e) {
-          const double y = row_sum_batched(a, e, col_at, val_at, Coherent{A.p});
-          A.q[i] = y;
-          v[0] = fma(A.p[i], y, v[0]);
+          const double y = row_sum_batched(a, e, col_at, val_at, Coherent{p});
+          q[i] = y;
+          v[0] = fma(p[i], y, v[0]);
         });
-        if (!(ok = coop_sums(v, A.part, buf, gs, err, sm))) break;
+        if (!(ok = coop_sums(v, tm, buf, sm))) break;
         if (t0) coop_after_pq(s, v[0]);
         __syncthreads();
         if (s.phase == kPhaseDone) break;
@@ -273,11 +287,11 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) cg_coop_kernel(C
           for (int u = 0; u < kCoopUnroll; ++u) {
             const int i = i0 + u * T;
             if (i < n) {
-              pi[u] = A.p[i];
-              qi[u] = A.q[i];
-              di[u] = A.dinv[i];
+              pi[u] = p[i];
+              qi[u] = q[i];
+              di[u] = dinv[i];
               xi[u] = d.x[i];
-              ri[u] = A.r[i];
+              ri[u] = r[i];
             }
           }
 #pragma unroll
@@ -288,14 +302,14 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) cg_coop_kernel(C
               const double rn = fma(-alpha, qi[u], ri[u]);
               const double zn = di[u] * rn;
               d.x[i] = xn;
-              A.r[i] = rn;
-              A.z[i] = zn;
+              r[i] = rn;
+              z[i] = zn;
               v[0] = fma(rn, zn, v[0]);
               v[1] = fma(rn, rn, v[1]);
             }
           }
         }
-        if (!(ok = coop_sums(v, A.part, buf, gs, err, sm))) break;
+        if (!(ok = coop_sums(v, tm, buf, sm))) break;
         if (t0) {
           coop_after_update(s, v[0], v[1], d);
           coop_end_body(s, d);
@@ -311,31 +325,31 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) cg_coop_kernel(C
           for (int u = 0; u < kCoopUnroll; ++u) {
             const int i = i0 + u * T;
             if (i < n) {
-              zi[u] = A.z[i];
-              pi[u] = A.p[i];
+              zi[u] = z[i];
+              pi[u] = p[i];
             }
           }
 #pragma unroll
           for (int u = 0; u < kCoopUnroll; ++u) {
             const int i = i0 + u * T;
-            if (i < n) A.p[i] = fma(beta, pi[u], zi[u]);
+            if (i < n) p[i] = fma(beta, pi[u], zi[u]);
           }
         }
-        if (!(ok = grid_sync(gs, err, &sm.flag))) break;
+        if (!(ok = team_sync(tm, sm))) break;
       }
     } else {
       // true residual t = b - A x; restart from it (r = t, z = D^{-1} t, p = z)
       double v[2] = {0.0, 0.0};  // t.t, t.z
       coop_rows(n, g0, T, d.rowptr, [&](int i, int a, int e) {
         const double ti = __ldg(d.b + i) - row_sum_batched(a, e, col_at, val_at, Coherent{d.x});
-        const double zi = A.dinv[i] * ti;
-        A.r[i] = ti;
-        A.z[i] = zi;
-        A.p[i] = zi;
+        const double zi = dinv[i] * ti;
+        r[i] = ti;
+        z[i] = zi;
+        p[i] = zi;
         v[0] = fma(ti, ti, v[0]);
         v[1] = fma(ti, zi, v[1]);
       });
-      if (!(ok = coop_sums(v, A.part, buf, gs, err, sm))) break;
+      if (!(ok = coop_sums(v, tm, buf, sm))) break;
       if (t0) {
         coop_after_check(s, v[0], v[1], d);
         coop_end_body(s, d);
@@ -355,14 +369,14 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) cg_coop_kernel(C
         const double ti = __ldg(d.b + i) - row_sum_batched(a, e, col_at, val_at, Coherent{d.x});
         v[0] = fma(ti, ti, v[0]);
       }
-      ok = coop_sums(v, A.part, buf, gs, err, sm);
+      ok = coop_sums(v, tm, buf, sm);
       if (t0) s.ttt = v[0];
     }
   }
-  if (blockIdx.x == 0 && t0) {
+  if (tm.rank == 0 && t0) {
     sla_info inf;
     inf.iters = s.iters;
-    if (!ok || __ldcg(err) != 0) {
+    if (!ok || (check_err && __ldcg(tm.err) != 0)) {
       inf.status = SLA_ERR_TIMEOUT;
       inf.rel_res = NAN;
       inf.true_rel_res = NAN;
@@ -381,6 +395,17 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) cg_coop_kernel(C
     }
     *d.info = inf;
   }
+  return ok;
+}
+
+__global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) cg_coop_kernel(CoopArgs A) {
+  __shared__ CoopSmem sm;
+  __shared__ CoopState s;
+  __shared__ KrylovDesc sd;
+  if (threadIdx.x == 0) sd = A.d;
+  __syncthreads();
+  Team tm{GridSync{&A.st->cnt[5], 0u}, (int)gridDim.x, (int)blockIdx.x, A.part, &A.st->err};
+  jacobi_team_solve(sd, A.r, A.z, A.p, A.q, A.dinv, tm, true, sm, s);
 }
 
 // ------------------------------------------------------------------ G G^T
@@ -482,8 +507,7 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) ggt_coop_kernel(
   const int T = gridDim.x * kCoopThreads;
   const int g0 = blockIdx.x * kCoopThreads + threadIdx.x;
   const bool t0 = threadIdx.x == 0;
-  int* err = &A.st->err;
-  GridSync gs{&A.st->cnt[5], 0u};
+  Team tm{GridSync{&A.st->cnt[5], 0u}, (int)gridDim.x, (int)blockIdx.x, A.part, &A.st->err};
   int buf = 0;
   bool ok = true;
   auto a_col = [&](int k) { return __ldg(d.col + k); };
@@ -510,7 +534,7 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) ggt_coop_kernel(
     }
     if (!d.use_x0)
       for (int i = g0; i < n; i += T) d.x[i] = 0.0;
-    ok = coop_sums(acc, A.part, buf, gs, err, sm);
+    ok = coop_sums(acc, tm, buf, sm);
     if (ok && t0) {
       s.bnorm = sqrt(acc[0]);
       s.thresh = fmax(d.rtol * s.bnorm, d.atol);
@@ -547,7 +571,7 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) ggt_coop_kernel(
           v[0] = fma(ti, ti, v[0]);
         }
       });
-      if (!(ok = coop_sums(v, A.part, buf, gs, err, sm))) break;
+      if (!(ok = coop_sums(v, tm, buf, sm))) break;
       if (t0) ggt_after_k1(s, ph, v[0], d);
       __syncthreads();
       if (s.phase == kPhaseDone) break;
@@ -578,7 +602,7 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) ggt_coop_kernel(
           }
         }
         // G^T gathers r
-        if (!(ok = grid_sync(gs, err, &sm.flag))) break;
+        if (!(ok = team_sync(tm, sm))) break;
       }
     }
     // RUN or PRECOND (possibly entered by a restart in this body)
@@ -591,7 +615,7 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) ggt_coop_kernel(
         A.t[i] = y;
         v[0] = fma(y, y, v[0]);
       });
-      if (!(ok = coop_sums(v, A.part, buf, gs, err, sm))) break;
+      if (!(ok = coop_sums(v, tm, buf, sm))) break;
       if (t0) {
         if (ph2 == kPhaseRun) {
           s.rr = v[1];
@@ -610,7 +634,7 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) ggt_coop_kernel(
         A.p[i] = fresh ? y : fma(beta, A.p[i], y);
       });
       // the next SpMV gathers p
-      if (!(ok = grid_sync(gs, err, &sm.flag))) break;
+      if (!(ok = team_sync(tm, sm))) break;
     }
   }
 
@@ -625,14 +649,14 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) ggt_coop_kernel(
         const double ti = __ldg(d.b + i) - row_sum_batched(a, e, a_col, a_val, Coherent{d.x});
         v[0] = fma(ti, ti, v[0]);
       }
-      ok = coop_sums(v, A.part, buf, gs, err, sm);
+      ok = coop_sums(v, tm, buf, sm);
       if (t0) s.ttt = v[0];
     }
   }
   if (blockIdx.x == 0 && t0) {
     sla_info inf;
     inf.iters = s.iters;
-    if (!ok || __ldcg(err) != 0) {
+    if (!ok || __ldcg(tm.err) != 0) {
       inf.status = SLA_ERR_TIMEOUT;
       inf.rel_res = NAN;
       inf.true_rel_res = NAN;
@@ -646,6 +670,93 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) ggt_coop_kernel(
       }
     }
     *d.info = inf;
+  }
+}
+
+// ------------------------------------------------------------------ batched teams
+//
+// The large systems of a distinct-pattern batch (sla_cg_batched_list): a
+// single-CTA solve of such a system runs at one SM's FP64 rate and sets the
+// whole batch's time (the tail).  Here teams of kTeamBlocks consecutive
+// blocks of one cooperative launch each take a system from a queue and
+// solve it with the Jacobi-PCG above (team barriers on a counter of the
+// team's own); systems with fewer than min_nnz entries are skipped and left
+// to the single-CTA kernel, which skips the others.  Every team reads the
+// whole queue, so the split does not depend on the processing order.
+
+// Team size and (in sla_batched.cu) the entry threshold, swept on the 512
+// FEM systems (B300, ms for the whole batch): teams of 3 from 32768 entries
+// 156.5; of 4 from 8192-65536 entries 160-167; of 2 188-203; of 6 175; of 8
+// 186-215; without teams 219.  Large teams pay their barriers with few rows
+// per thread; without teams the largest system runs at one SM's rate.
+constexpr int kTeamBlocks = 3;
+
+struct TeamBatchArgs {
+  int batch, min_nnz;
+  const int* rowptr;
+  const int* col;
+  const int* n_off;
+  const int* nnz_off;
+  const int* order;   // optional
+  const double* val;
+  const double* b;
+  double* x;
+  sla_info* info;
+  double* gvec;       // 5 doubles per row of the batch, at 5 * n_off[s]
+  unsigned* counters; // [teams] barrier counters, zero at launch
+  int* slots;         // [teams] queue position handed to each team
+  unsigned* next;     // queue counter, zero at launch
+  double* parts;      // [teams][2 * 4 * kTeamBlocks]
+  int* err;
+  double rtol, atol;
+  int max_iter, max_restarts, precond, use_x0;
+};
+
+__global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) batched_team_kernel(TeamBatchArgs B) {
+  __shared__ CoopSmem sm;
+  __shared__ CoopState s;
+  __shared__ KrylovDesc sd;
+  __shared__ long long s_row0;
+  const int q = blockIdx.x / kTeamBlocks, rank = blockIdx.x % kTeamBlocks;
+  Team tm{GridSync{B.counters + q, 0u}, kTeamBlocks, rank, B.parts + (size_t)q * 8 * kTeamBlocks, B.err};
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) B.slots[q] = (int)atomicAdd(B.next, 1u);
+    if (!team_sync(tm, sm)) return;
+    if (threadIdx.x == 0) {
+      const int k = __ldcg(B.slots + q);
+      s_row0 = -2;  // queue exhausted
+      if (k < B.batch) {
+        const int sys = B.order ? B.order[k] : k;
+        const int e0 = B.nnz_off[sys], n0 = B.n_off[sys];
+        s_row0 = -1;  // a small system: the single-CTA kernel's
+        if (B.nnz_off[sys + 1] - e0 >= B.min_nnz) {
+          KrylovDesc t = {};
+          t.n = B.n_off[sys + 1] - n0;
+          t.nnz = B.nnz_off[sys + 1] - e0;
+          t.rowptr = B.rowptr + n0 + sys;
+          t.col = B.col + e0;
+          t.val = B.val + e0;
+          t.b = B.b + n0;
+          t.x = B.x + n0;
+          t.info = B.info + sys;
+          t.rtol = B.rtol;
+          t.atol = B.atol;
+          t.max_iter = B.max_iter;
+          t.max_restarts = B.max_restarts;
+          t.precond = B.precond;
+          t.use_x0 = B.use_x0;
+          sd = t;
+          s_row0 = n0;
+        }
+      }
+    }
+    __syncthreads();
+    const long long row0 = s_row0;
+    if (row0 == -2) return;
+    if (row0 < 0) continue;
+    const size_t n = (size_t)sd.n;
+    double* vec = B.gvec + 5 * (size_t)row0;
+    if (!jacobi_team_solve(sd, vec, vec + n, vec + 2 * n, vec + 3 * n, vec + 4 * n, tm, false, sm, s)) return;
   }
 }
 
@@ -684,7 +795,7 @@ namespace {
 std::mutex g_coop_mu;
 // resident blocks per SM of each kernel per device (0: not yet queried,
 // -1: the device has no cooperative launch)
-int g_occ_cg[64] = {}, g_occ_ggt[64] = {};
+int g_occ_cg[64] = {}, g_occ_ggt[64] = {}, g_occ_team[64] = {};
 
 int coop_occupancy(int dev, int* cache, const void* fn) {
   std::lock_guard<std::mutex> lk(g_coop_mu);
@@ -755,6 +866,78 @@ int launch_ggt_coop(const KrylovDesc& desc, KrylovState* st, double* part, doubl
   void* args[] = {&A};
   SLA_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)ggt_coop_kernel, dim3(coop_grid(dev, desc.n, occ)),
                                            dim3(kCoopThreads), args, 0, s));
+  *launched = true;
+  return SLA_OK;
+}
+
+// Marks every system the teams own as timed out before they start, so that
+// a system a team never reached (a team that left after a barrier ran out)
+// does not keep a stale record; each solve overwrites its own.
+__global__ void team_info_prefill_kernel(int batch, int min_nnz, const int* __restrict__ nnz_off,
+                                         sla_info* info) {
+  for (int sys = blockIdx.x * blockDim.x + threadIdx.x; sys < batch; sys += gridDim.x * blockDim.x)
+    if (nnz_off[sys + 1] - nnz_off[sys] >= min_nnz) info[sys] = sla_info{0, SLA_ERR_TIMEOUT, NAN, NAN};
+}
+
+// Team scratch inside the batched workspace: counters, slots, queue counter,
+// partials for up to kMaxTeams teams.
+constexpr int kMaxTeams = kCoopMaxGrid / kTeamBlocks;
+size_t team_scratch_bytes() {
+  return al256(sizeof(unsigned) * kMaxTeams) + al256(sizeof(int) * kMaxTeams) + 256 +
+         al256(sizeof(double) * kMaxTeams * 8 * kTeamBlocks) + 256;
+}
+
+// Solves the systems of a concatenated batch with at least min_nnz entries
+// by teams of blocks (one cooperative launch); *launched is false (nothing
+// enqueued) when the device cannot run it.
+int launch_batched_teams(int batch, int min_nnz, const int* rowptr, const int* col, const int* n_off,
+                         const int* nnz_off, const int* order, const double* val, const double* b, double* x,
+                         sla_info* info, double* gvec, void* scratch, double rtol, double atol, int max_iter,
+                         int max_restarts, int precond, int use_x0, cudaStream_t s, bool* launched) {
+  *launched = false;
+  const int dev = current_device();
+  if (dev < 0 || dev >= 64) return SLA_OK;
+  const int occ = coop_occupancy(dev, g_occ_team, (const void*)batched_team_kernel);
+  if (occ <= 0) return SLA_OK;
+  int grid = num_sms(dev) * occ;
+  if (grid > kCoopMaxGrid) grid = kCoopMaxGrid;
+  grid -= grid % kTeamBlocks;
+  if (grid < kTeamBlocks) return SLA_OK;
+  char* base = (char*)scratch;
+  TeamBatchArgs B;
+  B.batch = batch;
+  B.min_nnz = min_nnz;
+  B.rowptr = rowptr;
+  B.col = col;
+  B.n_off = n_off;
+  B.nnz_off = nnz_off;
+  B.order = order;
+  B.val = val;
+  B.b = b;
+  B.x = x;
+  B.info = info;
+  B.gvec = gvec;
+  B.counters = (unsigned*)base;
+  base += al256(sizeof(unsigned) * kMaxTeams);
+  B.slots = (int*)base;
+  base += al256(sizeof(int) * kMaxTeams);
+  B.next = (unsigned*)base;
+  B.err = (int*)(base + 128);
+  base += 256;
+  B.parts = (double*)base;
+  B.rtol = rtol;
+  B.atol = atol;
+  B.max_iter = max_iter;
+  B.max_restarts = max_restarts;
+  B.precond = precond;
+  B.use_x0 = use_x0;
+  // counters, queue and error flag start at zero
+  SLA_CUDA_TRY(cudaMemsetAsync(scratch, 0, (char*)B.parts - (char*)scratch, s));
+  team_info_prefill_kernel<<<(batch + 255) / 256, 256, 0, s>>>(batch, min_nnz, nnz_off, info);
+  SLA_CUDA_TRY(cudaGetLastError());
+  void* args[] = {&B};
+  SLA_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)batched_team_kernel, dim3(grid), dim3(kCoopThreads),
+                                           args, 0, s));
   *launched = true;
   return SLA_OK;
 }

@@ -102,7 +102,7 @@ __device__ __forceinline__ bool last_block_arrive(unsigned* counter, bool* s_las
 // counter that only grows: thread 0 of each block adds 1 with release
 // semantics (making the block's writes, ordered before it by the block
 // barrier, visible), and barrier k of the launch is complete once the
-// counter reaches (k + 1) * gridDim.x (compared modulo 2^32), which thread 0
+// counter reaches (k + 1) * members (compared modulo 2^32), which thread 0
 // polls with acquire loads.  `epoch` counts the barriers this block has
 // passed (the same in every block); the counter is zero at launch.  Measured
 // 0.8 us (8 blocks) to 1.6 us (296 blocks) per barrier, against 1.2-2.1 us
@@ -129,10 +129,12 @@ __device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_sync(GridSync& g, int* err, int* s_flag) {
+// `members`: the number of blocks that take part (the whole grid, or a team
+// of blocks of a cooperative launch with a counter of its own).
+__device__ __forceinline__ bool grid_sync(GridSync& g, unsigned members, int* err, int* s_flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned goal = (g.epoch + 1u) * gridDim.x;
+    const unsigned goal = (g.epoch + 1u) * members;
     int ok = 1;
     red_add_release_gpu(g.count, 1u);
     if ((int)(ld_acquire_gpu(g.count) - goal) < 0) {

@@ -437,7 +437,10 @@ class SparseTensor:
 # Batched solves in one persistent launch (shared pattern / distinct patterns)
 # ---------------------------------------------------------------------------
 
-BATCH_CONFIGS = (1, 2, 3, 1 | 16, 2 | 16, 3 | 16)  # 256/512/1024 threads, vectors on chip / in global
+# 256/512/1024 threads, vectors on chip / in global; for lists also without
+# block teams for the large systems (bit 32)
+BATCH_CONFIGS = (1, 2, 3, 1 | 16, 2 | 16, 3 | 16)
+LIST_CONFIGS = BATCH_CONFIGS + (1 | 32, 2 | 32, 3 | 32)
 
 
 class CSRList:
@@ -520,15 +523,17 @@ def cg_batched_list(P: CSRList, val: torch.Tensor, b: torch.Tensor, *, rtol: flo
     def run(cfg):
         L.check("sla_cg_batched_list", L.lib().sla_cg_batched_list(
             P.batch, P.n_max, P.total_rows, P.n_off.data_ptr(), P.nnz_off.data_ptr(), P.rowptr.data_ptr(),
-            P.col.data_ptr(), val.data_ptr(), b.data_ptr(), x.data_ptr(), P.order.data_ptr(), ctypes.byref(o),
+            P.col.data_ptr(), val.data_ptr(), b.data_ptr(), x.data_ptr(),
+            None if P.order is None else P.order.data_ptr(), ctypes.byref(o),
             info.data_ptr(), cfg, ws.data_ptr(), ws.numel(), _stream_ptr(P.device)))
 
-    cfg = _resolve_config(config, ("list", P.n_max, P.total_rows, P.total_nnz, P.batch), run, x, x0)
+    cfg = _resolve_config(config, ("list", P.n_max, P.total_rows, P.total_nnz, P.batch), run, x, x0,
+                          LIST_CONFIGS)
     run(cfg)
     return x, SolveInfo(info)
 
 
-def _resolve_config(config, key, run, x, x0):
+def _resolve_config(config, key, run, x, x0, candidates=BATCH_CONFIGS):
     """'auto': cached tuned choice if any, else the library's heuristic (0);
     'tune': time every kernel variant on this batch (two runs each, CUDA
     events) and cache the fastest under the batch's shape key."""
@@ -539,7 +544,7 @@ def _resolve_config(config, key, run, x, x0):
     if config != "tune":
         raise ValueError("config must be an int, 'auto' or 'tune'")
     best, best_t = 0, float("inf")
-    for cfg in BATCH_CONFIGS:
+    for cfg in candidates:
         times = []
         for _ in range(2):
             if x0 is not None:

@@ -89,6 +89,40 @@ def test_distinct_patterns_match_oracle():
     _per_system_check([m[0] for m in mats], [m[1] for m in mats], [m[2] for m in mats], bs, xs, info, 1e-10)
 
 
+def test_distinct_patterns_with_block_teams():
+    """Systems with at least 32768 entries are solved by teams of blocks of a
+    cooperative launch, the rest by one CTA each; both against the oracle,
+    with the team path off (config bit 32) and without a processing order
+    (teams and CTAs then meet big and small systems interleaved)."""
+    mats = I.fem_list(12, seed0=2100, n_lo=200, n_hi=3000)
+    mats.insert(3, I.diffusion2d_random(120, 31))     # 14400 rows, 71520 entries
+    mats.append(I.diffusion3d_random(25, 32))         # 15625 rows, 105625 entries
+    mats.insert(7, I.diffusion2d_random(130, 33))     # 16900 rows (zero right-hand side below)
+    P = sla.CSRList([(rp, c) for rp, c, _ in mats])
+    nnzs = [int(rp[-1]) for rp, _, _ in mats]
+    assert sum(z >= 32768 for z in nnzs) == 3
+    vals = np.concatenate([v for _, _, v in mats])
+    bs = [I.rhs_uniform(len(rp) - 1, 70 + s) for s, (rp, _, _) in enumerate(mats)]
+    bs[7][:] = 0.0
+    bt = to_dev(np.concatenate(bs))
+    outs = {}
+    for name, cfg, order in (("teams", 0, P.order), ("no_teams", 2 | 32, P.order), ("unordered", 0, None)):
+        P.order = order
+        x, info = sla.cg_batched_list(P, to_dev(vals), bt, rtol=1e-10, config=cfg)
+        torch.cuda.synchronize()
+        xh = x.cpu().numpy()
+        xs = [xh[P.n_off_h[s]:P.n_off_h[s + 1]] for s in range(len(mats))]
+        st = np.atleast_1d(info.status)
+        its = np.atleast_1d(info.iters)
+        assert st[7] == 0 and its[7] == 0 and not xs[7].any()
+        idx = [s for s in range(len(mats)) if s != 7]
+        _per_system_check([m[0] for m in mats], [m[1] for m in mats], [m[2] for m in mats], bs, xs, info, 1e-10,
+                          iters_tol=3, idx=idx)
+        outs[name] = xh
+    # each system is solved the same way whatever the order: same bits
+    assert np.array_equal(outs["teams"], outs["unordered"])
+
+
 def test_graph_capture_and_replay():
     B, N = 8, 16
     rp, c, vals = I.batched_shared_2d(N, B, seed0=11, sigma=0.5)
