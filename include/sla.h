@@ -130,6 +130,22 @@ const char* sla_version(void);
 /* Human-readable name of a status code (static storage, never NULL). */
 const char* sla_status_string(int32_t code);
 
+/* Self-test of the bounded grid barrier that the cooperative solvers use
+ * between phases (no numerical work): one cooperative launch of `blocks`
+ * blocks passes `rounds` barriers, each wait bounded by budget_cycles SM
+ * clock cycles (the solvers use about 2 s).  Block `absent` (0 <= absent <
+ * blocks) never arrives, so every other block's wait runs out and leaves
+ * the kernel -- the failure the solvers report as SLA_ERR_TIMEOUT, made
+ * here on purpose without any fault; absent < 0: every block arrives.
+ * word: DEVICE int32[4], zeroed by the call; afterwards word[0] = blocks
+ * whose wait ran out, word[1] = blocks that passed all rounds, word[2] =
+ * the barrier counter, word[3] = the error flag (1 after a timeout).
+ * Returns SLA_ERR_INVALID (nothing enqueued) for a null word, blocks < 1 or
+ * more than can be co-resident, rounds < 0, budget_cycles < 1 or absent >=
+ * blocks.  Asynchronous. */
+int32_t sla_selftest_grid_barrier(int32_t blocks, int32_t absent, int64_t budget_cycles,
+                                  int32_t rounds, int32_t* word, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Workspace size query                                                 */
 /* ------------------------------------------------------------------ */

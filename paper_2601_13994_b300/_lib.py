@@ -136,6 +136,8 @@ def lib() -> ctypes.CDLL:
             L.sla_adjoint_backward_multi.restype = i32
             L.sla_cg_noalloc.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, ctypes.POINTER(SlaOpts), P, P]
             L.sla_cg_noalloc.restype = i32
+            L.sla_selftest_grid_barrier.argtypes = [i32, i32, ctypes.c_int64, i32, P, P]
+            L.sla_selftest_grid_barrier.restype = i32
             _lib = L
     return _lib
 

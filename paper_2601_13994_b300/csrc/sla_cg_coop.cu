@@ -942,4 +942,49 @@ int launch_batched_teams(int batch, int min_nnz, const int* rowptr, const int* c
   return SLA_OK;
 }
 
+// ------------------------------------------------------------------ self-test
+
+// `rounds` grid barriers with a given wait budget; block `absent` (if any)
+// never arrives, so the others' waits run out.  word[0]: blocks whose wait
+// ran out, word[1]: blocks that passed every barrier, word[2]: the barrier
+// counter, word[3]: the error flag.
+__global__ void grid_barrier_selftest_kernel(int* word, int absent, long long budget, int rounds) {
+  __shared__ int flag;
+  if ((int)blockIdx.x == absent) return;
+  GridSync gs{(unsigned*)(word + 2), 0u};
+  for (int k = 0; k < rounds; ++k) {
+    if (!grid_sync(gs, gridDim.x, word + 3, &flag, budget)) {
+      if (threadIdx.x == 0) atomicAdd(word, 1);
+      return;
+    }
+  }
+  if (threadIdx.x == 0) atomicAdd(word + 1, 1);
+}
+
+int occupancy_selftest() {
+  static int occ = 0;
+  if (occ == 0) occ = occupancy((const void*)grid_barrier_selftest_kernel, kCoopThreads);
+  return occ;
+}
+
 }  // namespace sla
+
+using namespace sla;
+
+extern "C" int32_t sla_selftest_grid_barrier(int32_t blocks, int32_t absent, int64_t budget_cycles,
+                                             int32_t rounds, int32_t* word, void* stream) {
+  if (word == nullptr || blocks < 1 || rounds < 0 || budget_cycles < 1 || absent >= blocks) return SLA_ERR_INVALID;
+  const int dev = current_device();
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop || blocks > num_sms(dev) * occupancy_selftest()) return SLA_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  SLA_CUDA_TRY(cudaMemsetAsync(word, 0, 4 * sizeof(int32_t), s));
+  int a = absent < 0 ? -1 : absent;
+  long long budget = budget_cycles;
+  int r = rounds;
+  void* args[] = {&word, &a, &budget, &r};
+  SLA_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)grid_barrier_selftest_kernel, dim3(blocks),
+                                           dim3(kCoopThreads), args, 0, s));
+  return SLA_OK;
+}

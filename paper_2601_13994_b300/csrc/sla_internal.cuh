@@ -131,7 +131,8 @@ __device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
 
 // `members`: the number of blocks that take part (the whole grid, or a team
 // of blocks of a cooperative launch with a counter of its own).
-__device__ __forceinline__ bool grid_sync(GridSync& g, unsigned members, int* err, int* s_flag) {
+__device__ __forceinline__ bool grid_sync(GridSync& g, unsigned members, int* err, int* s_flag,
+                                          long long budget = kGridWaitBudgetCycles) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned goal = (g.epoch + 1u) * members;
@@ -140,7 +141,7 @@ __device__ __forceinline__ bool grid_sync(GridSync& g, unsigned members, int* er
     if ((int)(ld_acquire_gpu(g.count) - goal) < 0) {
       const long long t0 = clock64();
       while ((int)(ld_acquire_gpu(g.count) - goal) < 0) {
-        if (clock64() - t0 > kGridWaitBudgetCycles) {
+        if (clock64() - t0 > budget) {
           atomicOr(err, 1);
           ok = 0;
           break;

@@ -128,3 +128,13 @@ def test_multi_rhs_workspace_grows_with_width():
     b16 = L.workspace_size(L.SLA_WS_CG_MULTI, 1000, 5000, 16)
     b13 = L.workspace_size(L.SLA_WS_CG_MULTI, 1000, 5000, 13)
     assert b16 == b13 > b1 and b16 >= 6 * 8 * 1000 * 16
+
+
+def test_grid_barrier_selftest_rejects_bad_arguments_without_launch():
+    lib = L.lib()
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.sla_selftest_grid_barrier(4, -1, 1000, 1, None, None) == L.SLA_ERR_INVALID
+    assert lib.sla_selftest_grid_barrier(0, -1, 1000, 1, fake, None) == L.SLA_ERR_INVALID
+    assert lib.sla_selftest_grid_barrier(4, 4, 1000, 1, fake, None) == L.SLA_ERR_INVALID
+    assert lib.sla_selftest_grid_barrier(4, -1, 0, 1, fake, None) == L.SLA_ERR_INVALID
+    assert lib.sla_selftest_grid_barrier(4, -1, 1000, -1, fake, None) == L.SLA_ERR_INVALID
