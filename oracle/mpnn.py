@@ -21,6 +21,15 @@ autograd for the gradients, the design the CUDA kernels implement:
   G G^T is the Jacobi preconditioner exactly.
 * Training loss for one system and right-hand side b with x* = A^{-1} b:
       loss = (x* - G G^T b)^T A (x* - G G^T b) / (x*^T A x*).
+* Column normalisation of the factor the network proposes (applied when the
+  factor is formed for a solve): column j of G is divided by
+  sqrt((G^T A G)_jj) = sqrt(sum_{i,k} G_ij A_ik G_kj), so that diag(G^T A G)
+  = I.  Over all positive column scalings this minimises Kaporin's condition
+  number (tr(G^T A G)/n)^n / det(G^T A G) of the preconditioned operator
+  (arithmetic-geometric mean inequality; det is scaled by the product of the
+  squared scales, tr is minimised relative to it at equal diagonals), the
+  normalisation that the factored sparse approximate inverse (FSAI) built
+  column by column also satisfies.
 """
 from __future__ import annotations
 
@@ -113,6 +122,33 @@ def forward(params: dict, rp, c, v):
     gt = torch.where(diag, torch.exp(theta_d), theta_off)
     g_val = gt / torch.sqrt(d[gi])
     return grp, gcol, g_val
+
+
+def column_normalize(grp, gcol, g_val, rp, c, v):
+    """Columns of G (CSR grp, gcol, g_val) divided by sqrt((G^T A G)_jj),
+    written out with plain loops: for every column j, the entries G_ij of
+    that column and the stored A_ik between their rows.  A column whose
+    quadratic form is not positive and finite is left as it is."""
+    n = len(grp) - 1
+    g = np.asarray(g_val, dtype=np.float64)
+    A = {}
+    for i in range(n):
+        for k in range(rp[i], rp[i + 1]):
+            A[(i, int(c[k]))] = A.get((i, int(c[k])), 0.0) + float(v[k])
+    cols = {}
+    for i in range(n):
+        for e in range(grp[i], grp[i + 1]):
+            cols.setdefault(int(gcol[e]), []).append((i, e))
+    out = g.copy()
+    for j, ent in cols.items():
+        q = 0.0
+        for (i, ei) in ent:
+            for (k, ek) in ent:
+                q += g[ei] * A.get((i, k), 0.0) * g[ek]
+        if q > 0.0 and np.isfinite(q):
+            for (_, e) in ent:
+                out[e] = g[e] / np.sqrt(q)
+    return out
 
 
 def ggt_apply(grp, gcol, g_val, u):

@@ -480,6 +480,68 @@ def test_mpnn_permutation_equivariance():
     assert np.allclose(np.diag(G2), np.diag(G)[perm], rtol=1e-12, atol=0)
 
 
+def _fsai_factor(rp, c, v):
+    """Factored sparse approximate inverse on the pattern of tril(A), built
+    column by column from its published definition: column i solves
+    A[P, P] y = e_1 on P = {j >= i : A_ji != 0} and is divided by sqrt(y_1)."""
+    n = len(rp) - 1
+    A = dense(rp, c, v)
+    G = np.zeros((n, n))
+    for i in range(n):
+        P = [j for j in range(i, n) if A[j, i] != 0.0]
+        y = np.linalg.solve(A[np.ix_(P, P)], np.eye(len(P))[0])
+        G[P, i] = y / np.sqrt(y[0])
+    return G
+
+
+def _csr_of(G):
+    S = sp.csr_matrix(G)
+    S.sort_indices()
+    return S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.copy()
+
+
+def _kaporin(M):
+    n = M.shape[0]
+    sign, logdet = np.linalg.slogdet(M)
+    assert sign > 0
+    return n * np.log(np.trace(M) / n) - logdet
+
+
+@pytest.mark.parametrize("mat", ["var2d", "var3d", "fem"])
+def test_column_normalize_invariants(mat):
+    """The normalised factor has diag(G^T A G) = I (checked with dense
+    products); positive column scalings of G do not change it; FSAI factors
+    (already normalised by construction) and the Jacobi factor D^{-1/2} are
+    fixed points; and Kaporin's condition number does not increase."""
+    from oracle import mpnn
+    rp, c, v = {"var2d": lambda: I.diffusion2d_random(7, 4, 1.5), "var3d": lambda: I.diffusion3d_random(4, 5),
+                "fem": lambda: I.fem_p1_laplacian(6, 6)}[mat]()
+    n = len(rp) - 1
+    A = dense(rp, c, v)
+    rng = np.random.default_rng(7)
+    # a random factor on the pattern of tril(A), positive diagonal
+    L = np.tril(A != 0) * rng.uniform(-0.4, 0.4, (n, n))
+    L[np.diag_indices(n)] = rng.uniform(0.2, 2.0, n)
+    grp, gcol, gv = _csr_of(L)
+    g1 = mpnn.column_normalize(grp, gcol, gv, rp, c, v)
+    G1 = dense(grp, gcol, g1, n)
+    assert np.allclose(np.diag(G1.T @ A @ G1), 1.0, rtol=1e-13, atol=0)
+    # invariant under positive column scalings
+    s = rng.uniform(0.1, 10.0, n)
+    g2 = mpnn.column_normalize(grp, gcol, gv * s[gcol], rp, c, v)
+    assert np.allclose(g2, g1, rtol=1e-13, atol=0)
+    # Kaporin's number of G^T A G does not increase
+    assert _kaporin(G1.T @ A @ G1) <= _kaporin(L.T @ A @ L) + 1e-12
+    # FSAI and Jacobi are fixed points
+    F = _fsai_factor(rp, c, v)
+    frp, fcol, fv = _csr_of(F)
+    assert np.allclose(mpnn.column_normalize(frp, fcol, fv, rp, c, v), fv, rtol=1e-13, atol=0)
+    d = np.diag(A)
+    jv = 1.0 / np.sqrt(d)
+    jrp = np.arange(n + 1, dtype=np.int32)
+    assert np.allclose(mpnn.column_normalize(jrp, np.arange(n, dtype=np.int32), jv, rp, c, v), jv, rtol=1e-15, atol=0)
+
+
 # ---------------------------------------------------------------- inverse problem (Sec. 4.6)
 
 def test_inverse_assembly_theta_zero_is_poisson_and_spd():
