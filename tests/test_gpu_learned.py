@@ -24,7 +24,7 @@ def oracle_params(model):
 def test_zero_head_gives_the_jacobi_factor_exactly():
     rp, c, v = I.diffusion2d_random(24, 3)
     model = LP.LearnedPreconditioner(seed=0)
-    G, gv = model.factor(csr(rp, c), to_dev(v))
+    G, gv = model.factor(csr(rp, c), to_dev(v), normalize=False)
     grp, gcol, og = OM.forward(oracle_params(model), rp, c, v)
     g, o = gv.cpu().numpy(), og.numpy()
     assert np.array_equal(G.rowptr.cpu().numpy(), grp) and np.array_equal(G.col.cpu().numpy(), gcol)
@@ -33,6 +33,40 @@ def test_zero_head_gives_the_jacobi_factor_exactly():
     assert relerr.max() <= 4.5e-16, relerr.max()
     rows = np.repeat(np.arange(len(grp) - 1), np.diff(grp))
     assert not g[rows != gcol].any()
+
+
+@pytest.mark.parametrize("mat", ["var2d", "var3d", "fem"])
+def test_column_normalisation_matches_oracle(mat):
+    """sla_ggt_normalize on the network's factor (untrained, non-zero head)
+    against the oracle's loop form, and the normalised factor's property
+    diag(G^T A G) = I by an independent SpMV; Jacobi stays Jacobi."""
+    rp, c, v = {"var2d": lambda: I.diffusion2d_random(30, 4, 1.5), "var3d": lambda: I.diffusion3d_random(9, 5),
+                "fem": lambda: I.fem_p1_laplacian(20, 6)}[mat]()
+    n = len(rp) - 1
+    model = LP.LearnedPreconditioner(seed=2)
+    model.view("v").fill_(0.05)
+    model._sync_bf16()
+    A = csr(rp, c)
+    G, raw = model.factor(A, to_dev(v), normalize=False)
+    G2, gv = model.factor(A, to_dev(v))
+    grp, gcol = G.rowptr.cpu().numpy(), G.col.cpu().numpy()
+    ref = OM.column_normalize(grp, gcol, raw.cpu().numpy(), rp, c, v)
+    assert rel(gv.cpu().numpy(), ref) <= 1e-14
+    # (G^T A G)_jj = ||A^{1/2} G e_j||^2 = (G e_j)^T A (G e_j) for a few columns
+    import scipy.sparse as sp
+    Gs = sp.csr_matrix((gv.cpu().numpy(), gcol, grp), shape=(n, n))
+    As = sp.csr_matrix((v, c, rp), shape=(n, n))
+    for j in (0, n // 3, n - 1):
+        gj = Gs[:, j].toarray().ravel()
+        assert abs(gj @ (As @ gj) - 1.0) <= 1e-13
+    # the zero head (Jacobi) is a fixed point to rounding
+    mz = LP.LearnedPreconditioner(seed=0)
+    Gz, gz = mz.factor(A, to_dev(v))
+    gz = gz.cpu().numpy()
+    zrows = np.repeat(np.arange(n), np.diff(Gz.rowptr.cpu().numpy()))
+    zdiag = zrows == Gz.col.cpu().numpy()
+    d = v[c == np.repeat(np.arange(n), np.diff(rp))]
+    assert rel(gz[zdiag], 1.0 / np.sqrt(d)) <= 1e-15 and not gz[~zdiag].any()
 
 
 @pytest.mark.parametrize("mat", ["var2d", "var3d", "fem"])
