@@ -127,8 +127,27 @@ def _profile_bicgstab(dev, max_iter):
     return {"iters": info.iters, "status": info.status}
 
 
+def _profile_fem_list(dev, max_iter):
+    """512 P1 FEM systems, n log-uniform in [1e3, 5e4] (the distinct-pattern
+    batch): block teams for the systems with at least 32768 entries, then the
+    single-CTA kernel; max_iter bounds every system."""
+    import numpy as np
+    import torch
+
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import sla
+    mats = I.fem_list(512, seed0=2000)
+    P = sla.CSRList([(m[0], m[1]) for m in mats], device=dev)
+    vt = torch.from_numpy(np.concatenate([m[2] for m in mats])).to(dev)
+    bt = torch.from_numpy(np.concatenate([I.rhs_uniform(len(m[0]) - 1, 3000 + s)
+                                          for s, m in enumerate(mats)])).to(dev)
+    x, info = sla.cg_batched_list(P, vt, bt, rtol=1e-8, max_iter=max_iter)
+    return {"iters_max": int(np.atleast_1d(info.iters).max())}
+
+
 PROFILE_ROWS = {
     "bicgstab_convdiff3d_128": _profile_bicgstab,
+    "fem_list_512": _profile_fem_list,
     "ggt_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "ggt"),
     "jacobi_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "jacobi"),
     "coop_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "coop"),
