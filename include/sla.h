@@ -62,11 +62,11 @@ extern "C" {
                                    driven by the host (checks the device state
                                    every 16 iterations, synchronising the
                                    stream) instead of one graph launch       */
-#define SLA_FLAG_NO_COOP 2      /* sla_cg, sla_cg_ggt, sla_cg_noalloc and the
-                                   CG adjoint: use the per-phase kernels
-                                   (graph or host loop) even at sizes where
-                                   the solve would run as one cooperative
-                                   launch                                    */
+#define SLA_FLAG_NO_COOP 2      /* sla_cg, sla_cg_ggt, sla_bicgstab,
+                                   sla_cg_noalloc and sla_adjoint_backward:
+                                   use the per-phase kernels (graph or host
+                                   loop) even at sizes where the solve would
+                                   run as one cooperative launch             */
 
 /* Workspace kinds for sla_workspace_size(). */
 #define SLA_WS_CG 1
@@ -342,8 +342,9 @@ int32_t sla_to_bf16(int32_t np, const float* p, void* p_bf16, void* stream);
 
 /* Solves A x = b with right-preconditioned BiCGStab (shadow residual
  * r^ = r0; with SLA_PRECOND_JACOBI, M = diag(A)).  Arguments, stopping rule,
- * true-residual restart, graph/host-loop execution and the info record are
- * as for sla_cg.  Outcomes: OK (also at the half step, when ||s|| meets the
+ * true-residual restart, execution forms (one cooperative launch up to 896
+ * Ki rows unless SLA_FLAG_NO_COOP, else the graph or the host loop) and the
+ * info record are as for sla_cg.  Outcomes: OK (also at the half step, when ||s|| meets the
  * target), NOT_CONVERGED, BREAKDOWN (|rho| < 1e-300, r^.v = 0, t.t = 0,
  * omega = 0 or a non-finite scalar), and status SLA_ERR_INVALID in *info when
  * Jacobi meets a zero diagonal.  Iterations count full BiCGStab steps (two

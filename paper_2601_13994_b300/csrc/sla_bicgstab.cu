@@ -562,7 +562,16 @@ int run_host_loop(BiPtrs P, const KrylovDesc& desc, const SpmvKernels& k, int gs
 
 }  // namespace
 
+bool use_bicg_coop(long long n);
+int launch_bicgstab_coop(const KrylovDesc& desc, void* ws, cudaStream_t s, bool* launched);
+
 int launch_bicgstab(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags) {
+  if (!(flags & (SLA_FLAG_HOST_LOOP | SLA_FLAG_NO_COOP)) && use_bicg_coop(desc.n)) {
+    // one cooperative launch per solve (sla_bicgstab_coop.cu) where the device runs it
+    bool launched = false;
+    const int rc = launch_bicgstab_coop(desc, ws, s, &launched);
+    if (rc != SLA_OK || launched) return rc;
+  }
   const BiLayout L = bicg_layout(desc.n);
   char* base = (char*)ws;
   BiPtrs P;

@@ -33,16 +33,9 @@
 #include <cstring>
 #include <mutex>
 
-#include "sla_internal.cuh"
-#include "sla_workspace.h"
+#include "sla_coop.cuh"
 
 namespace sla {
-
-constexpr int kCoopThreads = 512;
-constexpr int kCoopMinBlocks = 2;
-// two buffers of four partial arrays of gridDim.x doubles in the partials area
-constexpr int kCoopMaxGrid = kMaxBlocks * kPartSlots / 8;
-constexpr int kCoopUnroll = 2;
 
 struct CoopArgs {
   KrylovDesc d;
@@ -54,56 +47,6 @@ struct CoopArgs {
   double* q;
   double* dinv;
 };
-
-struct CoopSmem {
-  double red[4 * kCoopThreads + 4];
-  int flag;
-};
-
-// Gathered operand written earlier in this launch: plain (coherent) loads.
-struct Coherent {
-  const double* a;
-  __device__ __forceinline__ double operator()(int i) const { return a[i]; }
-};
-
-// Calls f(i, a, e) for this thread's rows i = g0, g0 + T, ... < n, with
-// [a, e) the row's entries.  (Loading the next row's bounds one row ahead
-// was measured: no change.)
-template <class F>
-__device__ __forceinline__ void coop_rows(int n, int g0, int T, const int* __restrict__ rowptr, F&& f) {
-  for (int i = g0; i < n; i += T) f(i, __ldg(rowptr + i), __ldg(rowptr + i + 1));
-}
-
-// The blocks that solve one system together: the whole grid, or a team of
-// `size` consecutive blocks of a cooperative launch with its own barrier
-// counter and partial-sum buffers (2 x 4 x size doubles).
-struct Team {
-  GridSync gs;
-  int size, rank;
-  double* part;
-  int* err;
-};
-
-__device__ __forceinline__ bool team_sync(Team& tm, CoopSmem& sm) {
-  return grid_sync(tm.gs, (unsigned)tm.size, tm.err, &sm.flag);
-}
-
-// Team totals of NV values: block sums -> partials -> barrier -> every block
-// adds all partials in the same order.  False if the barrier ran out.
-template <int NV>
-__device__ __forceinline__ bool coop_sums(double (&v)[NV], Team& tm, int& buf, CoopSmem& sm) {
-  block_sums<kCoopThreads, NV>(v, sm.red);
-  const int G = tm.size;
-  double* pb = tm.part + (size_t)buf * 4 * G;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) pb[j * G + tm.rank] = v[j];
-  }
-  buf ^= 1;
-  if (!team_sync(tm, sm)) return false;
-  reduce_partials<kCoopThreads, NV>(pb, G, G, v, sm.red);
-  return true;
-}
 
 // Block-uniform solver scalars, kept in shared memory (written by thread 0
 // after each grid reduction, read by all threads after a block barrier):
@@ -776,7 +719,7 @@ __global__ void coop_arm_kernel(KrylovState* st) {
 constexpr long long kCoopMaxNJacobi = 5LL << 19;  // 2.5 Mi rows
 constexpr long long kCoopMaxNGgt = 3LL << 19;     // 1.5 Mi rows
 
-bool use_cg_coop(long long n, bool ggt) {
+bool use_coop(long long n, long long limit) {
   static int forced = -2;
   if (forced == -2) {
     const char* e = getenv("SLA_CG_COOP");
@@ -788,16 +731,19 @@ bool use_cg_coop(long long n, bool ggt) {
   }
   if (forced == 0) return false;
   if (forced == 1) return true;
-  return n <= (ggt ? kCoopMaxNGgt : kCoopMaxNJacobi);
+  return n <= limit;
 }
+
+bool use_cg_coop(long long n, bool ggt) { return use_coop(n, ggt ? kCoopMaxNGgt : kCoopMaxNJacobi); }
 
 namespace {
 std::mutex g_coop_mu;
 // resident blocks per SM of each kernel per device (0: not yet queried,
 // -1: the device has no cooperative launch)
 int g_occ_cg[64] = {}, g_occ_ggt[64] = {}, g_occ_team[64] = {};
+}  // namespace
 
-int coop_occupancy(int dev, int* cache, const void* fn) {
+int coop_occupancy_of(int dev, int* cache, const void* fn) {
   std::lock_guard<std::mutex> lk(g_coop_mu);
   if (cache[dev] == 0) {
     int coop = 0;
@@ -808,11 +754,6 @@ int coop_occupancy(int dev, int* cache, const void* fn) {
   return cache[dev];
 }
 
-int coop_grid(int dev, int n, int occ) {
-  return persistent_grid(dev, ((long long)n + kCoopThreads - 1) / kCoopThreads, occ, kCoopMaxGrid);
-}
-}  // namespace
-
 // Launches the cooperative Jacobi-PCG solve; *launched is false (and nothing
 // was enqueued) when the device cannot run it, so that the caller takes the
 // graph path instead.
@@ -820,7 +761,7 @@ int launch_cg_coop(const KrylovDesc& desc, void* ws, cudaStream_t s, bool* launc
   *launched = false;
   const int dev = current_device();
   if (dev < 0 || dev >= 64) return SLA_OK;
-  const int occ = coop_occupancy(dev, g_occ_cg, (const void*)cg_coop_kernel);
+  const int occ = coop_occupancy_of(dev, g_occ_cg, (const void*)cg_coop_kernel);
   if (occ <= 0) return SLA_OK;
   const CgLayout L = cg_layout(desc.n);
   char* base = (char*)ws;
@@ -849,7 +790,7 @@ int launch_ggt_coop(const KrylovDesc& desc, KrylovState* st, double* part, doubl
   *launched = false;
   const int dev = current_device();
   if (dev < 0 || dev >= 64) return SLA_OK;
-  const int occ = coop_occupancy(dev, g_occ_ggt, (const void*)ggt_coop_kernel);
+  const int occ = coop_occupancy_of(dev, g_occ_ggt, (const void*)ggt_coop_kernel);
   if (occ <= 0) return SLA_OK;
   GgtCoopArgs A;
   A.d = desc;
@@ -897,7 +838,7 @@ int launch_batched_teams(int batch, int min_nnz, const int* rowptr, const int* c
   *launched = false;
   const int dev = current_device();
   if (dev < 0 || dev >= 64) return SLA_OK;
-  const int occ = coop_occupancy(dev, g_occ_team, (const void*)batched_team_kernel);
+  const int occ = coop_occupancy_of(dev, g_occ_team, (const void*)batched_team_kernel);
   if (occ <= 0) return SLA_OK;
   int grid = num_sms(dev) * occ;
   if (grid > kCoopMaxGrid) grid = kCoopMaxGrid;

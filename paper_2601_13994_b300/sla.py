@@ -204,10 +204,12 @@ def _krylov(fn_name: str, ws_kind: int, A: CSRMatrix, val, b, rtol, atol, max_it
 
 def bicgstab(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10, atol: float = 0.0,
              max_iter: int | None = None, precond: str = "jacobi", x0: torch.Tensor | None = None,
-             max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True):
-    """Right-preconditioned BiCGStab for nonsymmetric A.  Returns (x, SolveInfo)."""
+             max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True,
+             cooperative: bool = True):
+    """Right-preconditioned BiCGStab for nonsymmetric A.  Returns (x, SolveInfo).
+    Up to 896 Ki rows one cooperative launch (``cooperative=False`` opts out)."""
     return _krylov("sla_bicgstab", L.SLA_WS_BICGSTAB, A, val, b, rtol, atol, max_iter, precond, x0,
-                   max_restarts, out, graph)
+                   max_restarts, out, graph, cooperative)
 
 
 def cg(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10, atol: float = 0.0,

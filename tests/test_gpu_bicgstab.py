@@ -91,10 +91,70 @@ def test_half_step_exit_and_host_loop():
     b = to_dev(I.rhs_uniform(12 ** 3, 7))
     A = csr(rp, c)
     vt = to_dev(v)
-    xg, ig = sla.bicgstab(A, vt, b, rtol=1e-10)
+    # graph and host loop run the same per-phase kernels: same bits
+    xg, ig = sla.bicgstab(A, vt, b, rtol=1e-10, cooperative=False)
     xh, ih = sla.bicgstab(A, vt, b, rtol=1e-10, graph=False)
     torch.cuda.synchronize()
     assert torch.equal(xg, xh) and ig.iters == ih.iters
+
+
+@pytest.mark.parametrize("gen", [
+    lambda: I.convdiff3d(12, 5.0),
+    lambda: I.convdiff3d(37, 10.0),
+    lambda: I.convdiff3d(64, 1.0),
+])
+def test_cooperative_matches_oracle_and_graph(gen):
+    """BiCGStab as one cooperative launch (the default up to 896 Ki rows)
+    against the oracle and the graph of per-phase kernels: several blocks and
+    ragged tails; deterministic on its own."""
+    rp, c, v = gen()
+    n = len(rp) - 1
+    b = I.rhs_uniform(n, 17)
+    A = csr(rp, c)
+    vt, bt = to_dev(v), to_dev(b)
+    xc, ic = sla.bicgstab(A, vt, bt, rtol=1e-10)
+    xc2, ic2 = sla.bicgstab(A, vt, bt, rtol=1e-10)
+    xg, ig = sla.bicgstab(A, vt, bt, rtol=1e-10, cooperative=False)
+    torch.cuda.synchronize()
+    xo, io = oracle.bicgstab(rp, c, v, b, rtol=1e-13)
+    _, io10 = oracle.bicgstab(rp, c, v, b, rtol=1e-10)
+    assert ic.status == ig.status == 0
+    assert torch.equal(xc, xc2) and ic.iters == ic2.iters
+    assert rel(xc.cpu().numpy(), xo) <= 1e-8 and rel(xg.cpu().numpy(), xo) <= 1e-8
+    assert abs(ic.iters - io10["iters"]) <= max(2, io10["iters"] // 20)
+    assert ic.true_rel_res <= 2e-10
+
+
+def test_cooperative_edge_cases():
+    rp, c, v = I.convdiff3d(10, 8.0)
+    n = len(rp) - 1
+    A = csr(rp, c)
+    vt = to_dev(v)
+    b = I.rhs_uniform(n, 3)
+    for coop in (True, False):
+        # zero right-hand side with a warm start: x = 0, 0 iterations
+        x, inf = sla.bicgstab(A, vt, to_dev(np.zeros(n)), x0=to_dev(np.ones(n)), cooperative=coop)
+        assert inf.status == 0 and inf.iters == 0 and not x.cpu().numpy().any()
+        # iteration cap
+        _, inf = sla.bicgstab(A, vt, to_dev(b), rtol=1e-15, max_iter=3, max_restarts=0, cooperative=coop)
+        assert inf.status_name == "NOT_CONVERGED" and inf.iters == 3
+        # zero diagonal with Jacobi: SLA_ERR_INVALID in the record
+        v2 = v.copy()
+        v2[[k for k in range(rp[4], rp[5]) if c[k] == 4][0]] = 0.0
+        _, inf = sla.bicgstab(A, to_dev(v2), to_dev(b), cooperative=coop)
+        assert inf.status == -1
+        # warm start at the solution
+        xo, _ = oracle.bicgstab(rp, c, v, b, rtol=1e-14)
+        _, inf = sla.bicgstab(A, vt, to_dev(b), x0=to_dev(xo), rtol=1e-9, cooperative=coop)
+        assert inf.status == 0 and inf.iters <= 1
+    # exactly diagonal: half-step exit in iteration 1, cooperative form
+    m = 3000
+    rpd, cd = np.arange(m + 1, dtype=np.int32), np.arange(m, dtype=np.int32)
+    vd = np.linspace(1.0, 3.0, m)
+    bd = I.rhs_uniform(m, 4)
+    x, inf = sla.bicgstab(csr(rpd, cd), to_dev(vd), to_dev(bd), rtol=1e-12)
+    assert inf.status == 0 and inf.iters == 1
+    assert np.allclose(x.cpu().numpy(), bd / vd, rtol=1e-14, atol=0)
 
 
 @pytest.mark.slow

@@ -1,7 +1,7 @@
 """Every SpMV scheme against the oracle: the solvers pick the row-per-thread
 kernels at n <= 4 Mi rows and the TMA tile pipeline above; SLA_SPMV_KERNEL
 forces one scheme for a whole process, so each scheme runs here in a child
-process on small systems (SpMV, CG, BiCGStab, G G^T PCG; the CG solves with
+process on small systems (SpMV, CG, BiCGStab, G G^T PCG; the solves with
 cooperative=False, since at these sizes they would otherwise run as one
 cooperative launch that does not use the SpMV kernels)."""
 import json
@@ -46,7 +46,7 @@ out["cg"] = [rel(xg.cpu().numpy(), xo), int(info.status)]
 rp, c, v = I.convdiff3d(16, 10.0)
 b = I.rhs_uniform(len(rp) - 1, 5)
 A = sla.CSRMatrix.from_numpy(rp, c)
-xg, info = sla.bicgstab(A, torch.from_numpy(v).cuda(), torch.from_numpy(b).cuda(), rtol=1e-10)
+xg, info = sla.bicgstab(A, torch.from_numpy(v).cuda(), torch.from_numpy(b).cuda(), rtol=1e-10, cooperative=False)
 xo, io = oracle.bicgstab(rp, c, v, b, rtol=1e-13)
 out["bicgstab"] = [rel(xg.cpu().numpy(), xo), int(info.status)]
 rp, c, v = I.diffusion2d_random(40, 5)
