@@ -496,12 +496,14 @@ int32_t sla_cg_batched_shared(const sla_csr* A, int32_t batch,
  * s's start at rowptr + n_off[s] + s; columns are local.  n_max = largest
  * n_s, total_rows = n_off[batch].  order (device, optional): the order in
  * which CTAs take systems (largest first balances the load).
- * Systems with at least 32768 entries are solved first, each by a team of 3
- * CTAs of one cooperative launch (the same recurrence with team-wide
- * reductions and barriers bounded like sla_cg's), so that the largest
- * systems do not run at one SM's rate while the rest of the GPU idles; the
- * single-CTA launch then takes the others.  config bit 32 turns the teams
- * off.  Still no host synchronisation.
+ * With the teams on (the default) the batch is one cooperative launch:
+ * systems with at least 32768 entries are solved first, each by a team of 3
+ * CTAs (the same recurrence with team-wide reductions and barriers bounded
+ * like sla_cg's), so that the largest systems do not run at one SM's rate
+ * while the rest of the GPU idles; a team that reaches the small systems
+ * splits into single CTAs, which take them one each (vectors in the
+ * workspace).  config bit 32 turns the teams off (the persistent single-CTA
+ * kernel above takes every system).  Still no host synchronisation.
  * Workspace: SLA_WS_BATCHED with (total_rows, 1). */
 int32_t sla_cg_batched_list(int32_t batch, int32_t n_max, int32_t total_rows,
                             const int32_t* n_off, const int32_t* nnz_off,

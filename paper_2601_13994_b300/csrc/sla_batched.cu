@@ -409,7 +409,7 @@ extern "C" int32_t sla_cg_batched_list(int32_t batch, int32_t n_max, int32_t tot
                                         d.gvec, (char*)ws + 256, opts->rtol, opts->atol, opts->max_iter,
                                         opts->max_restarts, opts->precond, opts->use_x0, s, &launched);
     if (rc != SLA_OK) return rc;
-    if (launched) d.skip_nnz = kTeamMinNnz;
+    if (launched) return SLA_OK;  // the team launch also solved the small systems
   }
   return dispatch(d, config, s);
 }

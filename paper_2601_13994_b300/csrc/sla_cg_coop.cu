@@ -623,14 +623,16 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) ggt_coop_kernel(
 // whole batch's time (the tail).  Here teams of kTeamBlocks consecutive
 // blocks of one cooperative launch each take a system from a queue and
 // solve it with the Jacobi-PCG above (team barriers on a counter of the
-// team's own); systems with fewer than min_nnz entries are skipped and left
-// to the single-CTA kernel, which skips the others.  Every team reads the
-// whole queue, so the split does not depend on the processing order.
+// team's own); when a team meets a system with fewer than min_nnz entries
+// it splits into single blocks that take the rest of the queue one system
+// each, so the small systems fill the time the last large ones take.
 
 // Team size and (in sla_batched.cu) the entry threshold, swept on the 512
-// FEM systems (B300, ms for the whole batch): teams of 3 from 32768 entries
-// 156.5; of 4 from 8192-65536 entries 160-167; of 2 188-203; of 6 175; of 8
-// 186-215; without teams 219.  Large teams pay their barriers with few rows
+// FEM systems (B300, ms for the whole batch, single-CTA systems in a second
+// launch): teams of 3 from 32768 entries 156.5; of 4 from 8192-65536 entries
+// 160-167; of 2 188-203; of 6 175; of 8 186-215; without teams 219.  With the
+// small systems in the same launch: 3 / 32768 150.3, 3 / 16384 151.1,
+// 3 / 65536 152.2, 4 / 65536 163.3, 3 / 131072 168.0, 2 / 65536 183.3.  Large teams pay their barriers with few rows
 // per thread; without teams the largest system runs at one SM's rate.
 constexpr int kTeamBlocks = 3;
 
@@ -655,51 +657,81 @@ struct TeamBatchArgs {
   int max_iter, max_restarts, precond, use_x0;
 };
 
+// Fills sd (shared) for system `sys` of the batch; returns its first row.
+__device__ __forceinline__ long long team_system_desc(const TeamBatchArgs& B, int sys, KrylovDesc& sd) {
+  const int e0 = B.nnz_off[sys], n0 = B.n_off[sys];
+  KrylovDesc t = {};
+  t.n = B.n_off[sys + 1] - n0;
+  t.nnz = B.nnz_off[sys + 1] - e0;
+  t.rowptr = B.rowptr + n0 + sys;
+  t.col = B.col + e0;
+  t.val = B.val + e0;
+  t.b = B.b + n0;
+  t.x = B.x + n0;
+  t.info = B.info + sys;
+  t.rtol = B.rtol;
+  t.atol = B.atol;
+  t.max_iter = B.max_iter;
+  t.max_restarts = B.max_restarts;
+  t.precond = B.precond;
+  t.use_x0 = B.use_x0;
+  sd = t;
+  return n0;
+}
+
+// Teams take systems from the queue while they are large; the first small
+// system a team meets turns it into single blocks, which take the rest of
+// the queue one system per block (the queue is largest first, so from then
+// on every system is small), so no block waits while others finish.
 __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) batched_team_kernel(TeamBatchArgs B) {
   __shared__ CoopSmem sm;
   __shared__ CoopState s;
   __shared__ KrylovDesc sd;
   __shared__ long long s_row0;
+  __shared__ int s_k;
   const int q = blockIdx.x / kTeamBlocks, rank = blockIdx.x % kTeamBlocks;
   Team tm{GridSync{B.counters + q, 0u}, kTeamBlocks, rank, B.parts + (size_t)q * 8 * kTeamBlocks, B.err};
+  int first = -1;  // queue position a block takes first in single mode
   for (;;) {
     if (rank == 0 && threadIdx.x == 0) B.slots[q] = (int)atomicAdd(B.next, 1u);
     if (!team_sync(tm, sm)) return;
     if (threadIdx.x == 0) {
       const int k = __ldcg(B.slots + q);
+      s_k = k;
       s_row0 = -2;  // queue exhausted
       if (k < B.batch) {
         const int sys = B.order ? B.order[k] : k;
-        const int e0 = B.nnz_off[sys], n0 = B.n_off[sys];
-        s_row0 = -1;  // a small system: the single-CTA kernel's
-        if (B.nnz_off[sys + 1] - e0 >= B.min_nnz) {
-          KrylovDesc t = {};
-          t.n = B.n_off[sys + 1] - n0;
-          t.nnz = B.nnz_off[sys + 1] - e0;
-          t.rowptr = B.rowptr + n0 + sys;
-          t.col = B.col + e0;
-          t.val = B.val + e0;
-          t.b = B.b + n0;
-          t.x = B.x + n0;
-          t.info = B.info + sys;
-          t.rtol = B.rtol;
-          t.atol = B.atol;
-          t.max_iter = B.max_iter;
-          t.max_restarts = B.max_restarts;
-          t.precond = B.precond;
-          t.use_x0 = B.use_x0;
-          sd = t;
-          s_row0 = n0;
-        }
+        s_row0 = -1;  // a small system: single mode from here
+        if (B.nnz_off[sys + 1] - B.nnz_off[sys] >= B.min_nnz) s_row0 = team_system_desc(B, sys, sd);
       }
     }
     __syncthreads();
     const long long row0 = s_row0;
     if (row0 == -2) return;
-    if (row0 < 0) continue;
+    if (row0 == -1) {
+      if (rank == 0) first = s_k;
+      break;
+    }
     const size_t n = (size_t)sd.n;
     double* vec = B.gvec + 5 * (size_t)row0;
     if (!jacobi_team_solve(sd, vec, vec + n, vec + 2 * n, vec + 3 * n, vec + 4 * n, tm, false, sm, s)) return;
+  }
+  // single mode: every block solves whole systems on its own
+  Team solo{GridSync{nullptr, 0u}, 1, 0, nullptr, B.err};
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int k = first >= 0 ? first : (int)atomicAdd(B.next, 1u);
+      s_row0 = -2;
+      if (k < B.batch) s_row0 = team_system_desc(B, B.order ? B.order[k] : k, sd);
+    }
+    first = -1;
+    __syncthreads();
+    const long long row0 = s_row0;
+    if (row0 < 0) return;
+    const size_t n = (size_t)sd.n;
+    double* vec = B.gvec + 5 * (size_t)row0;
+    if (!jacobi_team_solve(sd, vec, vec + n, vec + 2 * n, vec + 3 * n, vec + 4 * n, solo, false, sm, s)) return;
+    __syncthreads();  // sd and s_row0 are rewritten for the next system
   }
 }
 
@@ -811,13 +843,12 @@ int launch_ggt_coop(const KrylovDesc& desc, KrylovState* st, double* part, doubl
   return SLA_OK;
 }
 
-// Marks every system the teams own as timed out before they start, so that
-// a system a team never reached (a team that left after a barrier ran out)
-// does not keep a stale record; each solve overwrites its own.
-__global__ void team_info_prefill_kernel(int batch, int min_nnz, const int* __restrict__ nnz_off,
-                                         sla_info* info) {
+// Marks every system as timed out before the launch, so that a system no
+// block reached (blocks that left after a barrier ran out) does not keep a
+// stale record; each solve overwrites its own.
+__global__ void team_info_prefill_kernel(int batch, sla_info* info) {
   for (int sys = blockIdx.x * blockDim.x + threadIdx.x; sys < batch; sys += gridDim.x * blockDim.x)
-    if (nnz_off[sys + 1] - nnz_off[sys] >= min_nnz) info[sys] = sla_info{0, SLA_ERR_TIMEOUT, NAN, NAN};
+    info[sys] = sla_info{0, SLA_ERR_TIMEOUT, NAN, NAN};
 }
 
 // Team scratch inside the batched workspace: counters, slots, queue counter,
@@ -874,7 +905,7 @@ int launch_batched_teams(int batch, int min_nnz, const int* rowptr, const int* c
   B.use_x0 = use_x0;
   // counters, queue and error flag start at zero
   SLA_CUDA_TRY(cudaMemsetAsync(scratch, 0, (char*)B.parts - (char*)scratch, s));
-  team_info_prefill_kernel<<<(batch + 255) / 256, 256, 0, s>>>(batch, min_nnz, nnz_off, info);
+  team_info_prefill_kernel<<<(batch + 255) / 256, 256, 0, s>>>(batch, info);
   SLA_CUDA_TRY(cudaGetLastError());
   void* args[] = {&B};
   SLA_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)batched_team_kernel, dim3(grid), dim3(kCoopThreads),

@@ -46,7 +46,12 @@ struct Team {
   int* err;
 };
 
+// A team of one block needs only the block barrier.
 __device__ __forceinline__ bool team_sync(Team& tm, CoopSmem& sm) {
+  if (tm.size == 1) {
+    __syncthreads();
+    return true;
+  }
   return grid_sync(tm.gs, (unsigned)tm.size, tm.err, &sm.flag);
 }
 
@@ -55,6 +60,7 @@ __device__ __forceinline__ bool team_sync(Team& tm, CoopSmem& sm) {
 template <int NV>
 __device__ __forceinline__ bool coop_sums(double (&v)[NV], Team& tm, int& buf, CoopSmem& sm) {
   block_sums<kCoopThreads, NV>(v, sm.red);
+  if (tm.size == 1) return true;  // the block total is the team total
   const int G = tm.size;
   double* pb = tm.part + (size_t)buf * 4 * G;
   if (threadIdx.x == 0) {
