@@ -127,6 +127,27 @@ def _profile_bicgstab(dev, max_iter):
     return {"iters": info.iters, "status": info.status}
 
 
+def _profile_factor(dev, max_iter):
+    """Learned-factor inference on the unseen 3D 128^3 system (features,
+    three message-passing layers, head, column normalisation), twice; the
+    network's weights do not change the kernels' cost."""
+    import torch
+
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import learned as LP
+    from paper_2601_13994_b300 import sla
+    rp, c, v = I.diffusion3d_random(128, 900002, 1.0)
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    vt = torch.from_numpy(v).to(dev)
+    m = LP.LearnedPreconditioner(device=dev, seed=0)
+    m.view("v").fill_(0.05)
+    m._sync_bf16()
+    for _ in range(2):
+        G, gv = m.factor(A, vt)
+    torch.cuda.synchronize()
+    return {"nnz_g": int(G.nnz)}
+
+
 def _profile_fem_list(dev, max_iter):
     """512 P1 FEM systems, n log-uniform in [1e3, 5e4] (the distinct-pattern
     batch): block teams for the systems with at least 32768 entries, then the
@@ -148,6 +169,7 @@ def _profile_fem_list(dev, max_iter):
 PROFILE_ROWS = {
     "bicgstab_convdiff3d_128": _profile_bicgstab,
     "fem_list_512": _profile_fem_list,
+    "factor_3d_128": _profile_factor,
     "ggt_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "ggt"),
     "jacobi_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "jacobi"),
     "coop_2d_1024": lambda dev, mi: _profile_ggt(dev, mi, "coop"),

@@ -103,13 +103,12 @@ class _Graph:
         lib = _bind()
         dev = A.device
         n = A.n
-        self.A, self.val, self.n, self.dev = A, val, n, dev
+        self.A, self.n, self.dev = A, n, dev
         st = sla._stream_ptr(dev)
         self.d = torch.empty(n, dtype=torch.float64, device=dev)
         self.e = torch.empty(max(A.nnz, 1), dtype=torch.float32, device=dev)
         self.F = torch.empty((n, NFEAT), dtype=torch.float32, device=dev)
-        _chk("sla_mp_features", lib.sla_mp_features(ctypes.byref(A.c), val.data_ptr(), self.d.data_ptr(),
-                                                   self.e.data_ptr(), self.F.data_ptr(), st))
+        self.set_values(val)
         grp = torch.empty(n + 1, dtype=torch.int32, device=dev)
         gcol = torch.empty(max(A.nnz, 1), dtype=torch.int32, device=dev)
         gsrc = torch.empty(max(A.nnz, 1), dtype=torch.int32, device=dev)
@@ -139,6 +138,14 @@ class _Graph:
         self.dAgg = f(n, WIDTH)
         self.dG = torch.empty(max(m, 1), dtype=torch.float64, device=dev)
         self.loss = torch.empty(2, dtype=torch.float64, device=dev)
+
+    def set_values(self, val: torch.Tensor):
+        """The value-dependent inputs (scaled entries and node features) for
+        new values on the same pattern."""
+        self.val = val
+        _chk("sla_mp_features", _bind().sla_mp_features(ctypes.byref(self.A.c), val.data_ptr(), self.d.data_ptr(),
+                                                       self.e.data_ptr(), self.F.data_ptr(),
+                                                       sla._stream_ptr(self.dev)))
 
 
 class LearnedPreconditioner:
@@ -171,6 +178,7 @@ class LearnedPreconditioner:
         self.m = torch.zeros_like(self.p)
         self.v = torch.zeros_like(self.p)
         self.t = 0
+        self._graphs = {}
         self._sync_bf16()
         self._ws = {}
 
@@ -207,24 +215,41 @@ class LearnedPreconditioner:
         return t
 
     # -------------------------------------------------------------- forward
-    def graph(self, A: sla.CSRMatrix, val: torch.Tensor) -> _Graph:
-        return _Graph(A, val)
+    _GRAPH_CACHE = 4
 
-    def forward(self, gr: _Graph) -> torch.Tensor:
-        """G values (FP64, on gr.G's pattern)."""
+    def graph(self, A: sla.CSRMatrix, val: torch.Tensor) -> _Graph:
+        """Per-system buffers.  The pattern work (tril(A), the CSR of G^T) is
+        kept for the last few matrices (by CSRMatrix object), so a factor for
+        new values on a known pattern recomputes only the features."""
+        key = id(A)
+        hit = self._graphs.pop(key, None)
+        if hit is not None and hit.A is A:
+            hit.set_values(val)
+            gr = hit
+        else:
+            gr = _Graph(A, val)
+        self._graphs[key] = gr
+        while len(self._graphs) > self._GRAPH_CACHE:
+            self._graphs.pop(next(iter(self._graphs)))
+        return gr
+
+    def forward(self, gr: _Graph, inference: bool = False) -> torch.Tensor:
+        """G values (FP64, on gr.G's pattern).  inference=True skips storing
+        the pre-activations that only the backward pass reads."""
         lib = _bind()
         st = sla._stream_ptr(self.dev)
         n = gr.n
         pb = lambda k: self.view(k, "pb").data_ptr()
         pf = lambda k: self.view(k, "p").data_ptr()
+        pre = (lambda t: None) if inference else (lambda t: t.data_ptr())
         _chk("dense0", lib.sla_mp_dense_fwd(n, NFEAT, gr.F.data_ptr(), 0, None, WIDTH, pb("W0"), pf("b0"), None, 1,
-                                            gr.H0pre.data_ptr(), gr.H[0].data_ptr(), st))
+                                            pre(gr.H0pre), gr.H[0].data_ptr(), st))
         for l in range(LAYERS):
             _chk("agg", lib.sla_mp_aggregate(ctypes.byref(gr.A.c), gr.e.data_ptr(), gr.H[l].data_ptr(),
                                              gr.Agg[l].data_ptr(), 0, st))
             _chk("dense", lib.sla_mp_dense_fwd(n, WIDTH, gr.H[l].data_ptr(), WIDTH, gr.Agg[l].data_ptr(), WIDTH,
                                                pb("W_%d" % l), pf("c_%d" % l), gr.H[l].data_ptr(), 1,
-                                               gr.Z[l].data_ptr(), gr.H[l + 1].data_ptr(), st))
+                                               pre(gr.Z[l]), gr.H[l + 1].data_ptr(), st))
         _chk("head_dense", lib.sla_mp_dense_fwd(n, WIDTH, gr.H[LAYERS].data_ptr(), 0, None, 3 * WIDTH, pb("Uh"),
                                                 pf("bh"), None, 0, None, gr.PQR.data_ptr(), st))
         _chk("head", lib.sla_mp_head_fwd(n, gr.G.rowptr.data_ptr(), gr.G.col.data_ptr(), gr.gsrc.data_ptr(),
@@ -308,7 +333,7 @@ class LearnedPreconditioner:
         G, with its columns normalised to diag(G^T A G) = I unless
         ``normalize`` is False."""
         gr = self.graph(A, val)
-        gv = self.forward(gr).clone()
+        gv = self.forward(gr, inference=True).clone()
         if normalize:
             self.normalize(gr, gv)
         return gr.G, gv
