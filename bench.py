@@ -488,6 +488,18 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The job's time for a per-rank time: the slowest rank's (an all-reduce
+    MAX over the process group; the value itself with one rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -543,10 +555,7 @@ def run_ours(args):
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     clocks = sampler.stop() if sampler else None
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     iters_all = [i.iters for i in infos]
     status_all = [i.status for i in infos]
     true_rel = infos[-1].true_rel_res
@@ -598,7 +607,8 @@ def run_ours(args):
             inf = e2e_step()
         k1.record(stream)
         torch.cuda.synchronize(dev)
-        e2e_ms = k0.elapsed_time(k1) / args.steps
+        barrier()
+        e2e_ms = max_over_ranks(k0.elapsed_time(k1) / args.steps, world, dev)
         h2d = rp.nbytes + c.nbytes + v.nbytes + b.nbytes
         d2h = 8 * n + 24  # x and the info record
         e2e = {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
