@@ -150,6 +150,66 @@ def test_graph_capture_and_replay():
     assert torch.equal(x_static, x_ref)
 
 
+def _capture(fn):
+    """Runs fn once outside, then captures it in a CUDA graph on a side stream."""
+    fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            fn()
+    torch.cuda.current_stream().wait_stream(s)
+    return g
+
+
+def test_graph_capture_of_cooperative_launches():
+    """The cooperative paths (the block-team batch, single-system CG, G G^T
+    PCG and BiCGStab below their size limits) only enqueue work, so a CUDA
+    graph captures them; replays with new right-hand sides give the bits of
+    direct calls."""
+    mats = I.fem_list(6, seed0=2300, n_lo=200, n_hi=2000)
+    mats.append(I.diffusion2d_random(120, 41))        # a team system
+    P = sla.CSRList([(rp, c) for rp, c, _ in mats])
+    vals = to_dev(np.concatenate([v for _, _, v in mats]))
+    b_static = to_dev(np.concatenate([I.rhs_uniform(len(rp) - 1, 90 + s) for s, (rp, _, _) in enumerate(mats)]))
+    x_static = torch.empty_like(b_static)
+    g = _capture(lambda: sla.cg_batched_list(P, vals, b_static, rtol=1e-10, out=x_static))
+    b_new = to_dev(np.concatenate([I.rhs_uniform(len(rp) - 1, 190 + s) for s, (rp, _, _) in enumerate(mats)]))
+    b_static.copy_(b_new)
+    g.replay()
+    torch.cuda.synchronize()
+    x_ref, info = sla.cg_batched_list(P, vals, b_new, rtol=1e-10)
+    torch.cuda.synchronize()
+    assert (np.atleast_1d(info.status) == 0).all()
+    assert torch.equal(x_static, x_ref)
+    # single-system solvers
+    rp, c, v = I.diffusion2d_random(70, 42)
+    n = len(rp) - 1
+    A = csr(rp, c)
+    vt = to_dev(v)
+    bs = to_dev(I.rhs_uniform(n, 5))
+    xs = torch.empty_like(bs)
+    g2 = _capture(lambda: sla.cg(A, vt, bs, rtol=1e-10, out=xs))
+    rpc, cc, vc = I.convdiff3d(14, 6.0)
+    Ac = csr(rpc, cc)
+    vct = to_dev(vc)
+    bc = to_dev(I.rhs_uniform(14 ** 3, 6))
+    xc = torch.empty_like(bc)
+    g3 = _capture(lambda: sla.bicgstab(Ac, vct, bc, rtol=1e-10, out=xc))
+    bs.copy_(to_dev(I.rhs_uniform(n, 8)))
+    bc.copy_(to_dev(I.rhs_uniform(14 ** 3, 9)))
+    g2.replay()
+    g3.replay()
+    torch.cuda.synchronize()
+    x2, i2 = sla.cg(A, vt, bs, rtol=1e-10)
+    x3, i3 = sla.bicgstab(Ac, vct, bc, rtol=1e-10)
+    torch.cuda.synchronize()
+    assert i2.status == 0 and i3.status == 0
+    assert torch.equal(xs, x2) and torch.equal(xc, x3)
+
+
 def test_batched_adjoint_matches_single_solves():
     B, N = 5, 16
     rp, c, vals = I.batched_shared_2d(N, B, seed0=21, sigma=0.5)
