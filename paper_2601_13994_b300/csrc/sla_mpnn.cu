@@ -228,6 +228,110 @@ __global__ void __launch_bounds__(kDT) dense_fwd_kernel(int n, int K1, const flo
   }
 }
 
+// The same layer for M = 32 MS outputs with 4 x 4 register tiles: thread
+// (tx, ty) of the 256-thread block owns rows ty + 32 r (r < 4) of a
+// 128-row tile and, in each 32-column slab, columns 4 tx .. 4 tx + 3.  X sits
+// in shared memory row-major (rows padded to Kp + 4 floats, so the four rows
+// a warp reads at one time fall in different banks), W k-major (transposed
+// once per block).  Per 4 steps of k a thread makes 4 16-byte loads of X
+// and 4 MS of W for 64 MS FMAs: 4 + 4 MS shared-memory wavefronts per 2048
+// MS FMAs of a warp, against 12 per 1024 above.  Each output is still the
+// sum over k = 0 .. Kp-1 in order, started from the bias (the same bits).
+template <int MS>
+__global__ void __launch_bounds__(kDT) dense_fwd_tiled_kernel(int n, int K1, const float* __restrict__ X1,
+                                                              int K2, const float* __restrict__ X2, int M,
+                                                              const __nv_bfloat16* __restrict__ W,
+                                                              const float* __restrict__ bias,
+                                                              const float* __restrict__ R, int relu,
+                                                              float* __restrict__ Ypre,
+                                                              float* __restrict__ Y) {
+  constexpr int kRowsT = 128, MW = 32 * MS, SW = MW + 4;
+  extern __shared__ __align__(16) float dsm_t[];
+  const int K = K1 + K2;
+  const int Kp = (K + 3) & ~3;
+  const int SX = Kp + 4;
+  float* Ws = dsm_t;            // [Kp][SW]   k-major
+  float* Xs = dsm_t + Kp * SW;  // [128][SX]  row-major
+  for (int idx = threadIdx.x; idx < Kp * MW; idx += kDT) {
+    const int k = idx / MW, m = idx % MW;
+    Ws[k * SW + m] = (k < K && m < M) ? __bfloat162float(W[m * K + k]) : 0.0f;
+  }
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  const int ntiles = (n + kRowsT - 1) / kRowsT;
+  const bool vec = (K1 % 4 == 0) && (K2 % 4 == 0) &&
+                   ((reinterpret_cast<uintptr_t>(X1) | reinterpret_cast<uintptr_t>(X2)) & 15u) == 0;
+  const int cpr = Kp / 4;  // 16-byte chunks per row
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    __syncthreads();
+    if (vec) {
+      for (int idx = threadIdx.x; idx < kRowsT * cpr; idx += kDT) {
+        const int r = idx / cpr, k = 4 * (idx % cpr);
+        const int i = t * kRowsT + r;
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (i < n && k < K)
+          v = k < K1 ? *reinterpret_cast<const float4*>(X1 + (size_t)i * K1 + k)
+                     : *reinterpret_cast<const float4*>(X2 + (size_t)i * K2 + (k - K1));
+        *reinterpret_cast<float4*>(&Xs[r * SX + k]) = v;
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < kRowsT * Kp; idx += kDT) {
+        const int r = idx / Kp, k = idx % Kp;
+        const int i = t * kRowsT + r;
+        float xv = 0.0f;
+        if (i < n && k < K) xv = k < K1 ? X1[(size_t)i * K1 + k] : X2[(size_t)i * K2 + (k - K1)];
+        Xs[r * SX + k] = xv;
+      }
+    }
+    __syncthreads();
+    float acc[MS][4][4];
+#pragma unroll
+    for (int sl = 0; sl < MS; ++sl)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int m = 32 * sl + 4 * tx + c;
+        const float b0 = (bias && m < M) ? bias[m] : 0.0f;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[sl][r][c] = b0;
+      }
+    for (int k0 = 0; k0 < Kp; k0 += 4) {
+      float4 xq[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) xq[r] = *reinterpret_cast<const float4*>(&Xs[(ty + 32 * r) * SX + k0]);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+        for (int sl = 0; sl < MS; ++sl) {
+          const float4 wv = *reinterpret_cast<const float4*>(&Ws[(k0 + kk) * SW + 32 * sl + 4 * tx]);
+          const float wc[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const float xv = kk == 0 ? xq[r].x : kk == 1 ? xq[r].y : kk == 2 ? xq[r].z : xq[r].w;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[sl][r][c] = fmaf(xv, wc[c], acc[sl][r][c]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = t * kRowsT + ty + 32 * r;
+      if (i >= n) continue;
+#pragma unroll
+      for (int sl = 0; sl < MS; ++sl)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int m = 32 * sl + 4 * tx + c;
+          if (m >= M) continue;
+          const float a0 = acc[sl][r][c];
+          if (Ypre) Ypre[(size_t)i * M + m] = a0;
+          float y = relu ? fmaxf(a0, 0.0f) : a0;
+          if (R) y += R[(size_t)i * M + m];
+          Y[(size_t)i * M + m] = y;
+        }
+    }
+  }
+}
+
 // dX[i, k] = (base ? base[i, k] : 0) + sum_m dY[i, m] W[m, col0 + k]
 __global__ void __launch_bounds__(kDT) dense_bwdx_kernel(int n, int M, const float* __restrict__ dY,
                                                          int K, const __nv_bfloat16* __restrict__ W,
@@ -479,6 +583,91 @@ __global__ void head_fwd_kernel(int n, const int* __restrict__ grp, const int* _
   }
 }
 
+// theta with four rows per warp: 8 lanes per row, each lane owning hidden
+// units 4 sub .. 4 sub + 3 (16-byte loads of P, R and the gathered Q rows),
+// the per-entry sum over the 32 units reduced over the row's 8 lanes: a warp
+// has four rows' gathers in flight and needs 3 instead of 5 shuffles per
+// entry.  Same terms as head_fwd_kernel, summed in a fixed order (4 units
+// per lane, then the 8-lane butterfly).  PQR must be 16-byte aligned.
+__global__ void head4_fwd_kernel(int n, const int* __restrict__ grp, const int* __restrict__ gcol,
+                                 const int* __restrict__ gsrc, const float* __restrict__ e,
+                                 const float4* __restrict__ PQR4, const float* __restrict__ ue,
+                                 const float* __restrict__ vv, const float* __restrict__ vd,
+                                 float* __restrict__ theta) {
+  constexpr int B = 8;
+  const int lane = threadIdx.x & 31, sub = lane & 7, grp4 = lane >> 3;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  float uem[4], vm[4], vdm[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    uem[u] = ue[4 * sub + u];
+    vm[u] = vv[4 * sub + u];
+    vdm[u] = vd[4 * sub + u];
+  }
+  auto row_sum8 = [](float x) {
+    x += __shfl_xor_sync(0xffffffffu, x, 4, 8);
+    x += __shfl_xor_sync(0xffffffffu, x, 2, 8);
+    x += __shfl_xor_sync(0xffffffffu, x, 1, 8);
+    return x;
+  };
+  for (long long i0 = 4 * w; i0 < n; i0 += 4 * warps) {
+    const int i = (int)i0 + grp4;
+    const bool valid = i < n;
+    const int k0 = valid ? grp[i] : 0, k1 = valid ? grp[i + 1] : 0;
+    const int cnt = k1 - k0;
+    float4 P = make_float4(0.0f, 0.0f, 0.0f, 0.0f), Rr = P;
+    if (valid) {
+      P = PQR4[(size_t)i * 24 + sub];
+      Rr = PQR4[(size_t)i * 24 + 16 + sub];
+    }
+    const float Pu[4] = {P.x, P.y, P.z, P.w};
+    const float dsum = vdm[0] * fmaxf(Rr.x, 0.0f) + vdm[1] * fmaxf(Rr.y, 0.0f) + vdm[2] * fmaxf(Rr.z, 0.0f) +
+                       vdm[3] * fmaxf(Rr.w, 0.0f);
+    const float diag = row_sum8(dsum);
+    const int jl = sub < min(cnt, B) ? gcol[k0 + sub] : i;
+    const float el = sub < min(cnt, B) ? e[gsrc[k0 + sub]] : 0.0f;
+    float4 q[B];
+#pragma unroll
+    for (int m = 0; m < B; ++m) {
+      const int j = __shfl_sync(0xffffffffu, jl, m, 8);
+      q[m] = (m < cnt && j != i) ? PQR4[(size_t)j * 24 + 8 + sub] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int m = 0; m < B; ++m) {
+      const int j = __shfl_sync(0xffffffffu, jl, m, 8);
+      const float em = __shfl_sync(0xffffffffu, el, m, 8);
+      const float qu[4] = {q[m].x, q[m].y, q[m].z, q[m].w};
+      float part = 0.0f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) part += vm[u] * fmaxf(Pu[u] + qu[u] + uem[u] * em, 0.0f);
+      const float off = row_sum8(part);
+      if (sub == 0 && m < cnt) theta[k0 + m] = j == i ? diag : off;
+    }
+    // rows with more than 8 entries of tril(A) (none in the 5- and 7-point
+    // stencils): the rest one entry at a time
+    const int extra = cnt > B ? cnt - B : 0;
+    int extra_max = extra;
+#pragma unroll
+    for (int o = 8; o < 32; o <<= 1) extra_max = max(extra_max, __shfl_xor_sync(0xffffffffu, extra_max, o));
+    for (int t = 0; t < extra_max; ++t) {
+      const bool act = t < extra;
+      const int kg = k0 + B + t;
+      const int j = act ? gcol[kg] : i;
+      float part = 0.0f;
+      if (act && j != i) {
+        const float4 qv = PQR4[(size_t)j * 24 + 8 + sub];
+        const float ek = e[gsrc[kg]];
+        const float qu[4] = {qv.x, qv.y, qv.z, qv.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) part += vm[u] * fmaxf(Pu[u] + qu[u] + uem[u] * ek, 0.0f);
+      }
+      const float off = row_sum8(part);
+      if (act && sub == 0) theta[kg] = j == i ? diag : off;
+    }
+  }
+}
+
 // G values from theta, one thread per row: G_ii = exp(theta_ii) / sqrt(d_i),
 // G_ij = theta_ij / sqrt(d_i).  The FP64 work is here, vectorised over rows
 // (on this part an FP64 warp instruction costs its full pipe time however
@@ -705,6 +894,28 @@ extern "C" int32_t sla_mp_dense_fwd(int32_t n, int32_t K1, const float* X1, int3
   if (n == 0) return SLA_OK;
   if (!W_bf16 || !Y || (K1 && !X1) || (K2 && !X2)) return SLA_ERR_INVALID;
   const int nm = (M + 31) / 32;
+  cudaStream_t s = (cudaStream_t)stream;
+  const __nv_bfloat16* Wb = (const __nv_bfloat16*)W_bf16;
+  if (nm == 1) {
+    // register-tiled form for 32 outputs: 2.1 M rows, K = 64, 483 -> 374 us
+    // (B300); for the 96-wide head it measured slower (584 vs 521 us: 116
+    // registers per thread), so that layer keeps dense_fwd_kernel
+    const int Kp = (K1 + K2 + 3) & ~3;
+    const size_t smem_t = sizeof(float) * ((size_t)Kp * (32 * nm + 4) + (size_t)128 * (Kp + 4));
+    const void* ft = (const void*)dense_fwd_tiled_kernel<1>;
+    static bool attr_set = false;
+    if (!attr_set) {
+      const int mx = (int)(sizeof(float) * ((size_t)kMaxK * (32 + 4) + (size_t)128 * (kMaxK + 4)));
+      cudaFuncSetAttribute(dense_fwd_tiled_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      attr_set = true;
+    }
+    int occ_t = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, ft, kDT, smem_t) != cudaSuccess || occ_t < 1) occ_t = 1;
+    const int bt = grid_rows(n, 128, 148 * (occ_t < 8 ? occ_t : 8));
+    dense_fwd_tiled_kernel<1><<<bt, kDT, smem_t, s>>>(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y);
+    MP_LAUNCH_CHECK();
+    return SLA_OK;
+  }
   const int S = ((K1 + K2 + 3) & ~3) + 4;
   const size_t smem = sizeof(float) * (size_t)(M + 64) * S;
   const void* fn = nm == 1 ? (const void*)dense_fwd_kernel<1> : nm == 2 ? (const void*)dense_fwd_kernel<2>
@@ -712,8 +923,6 @@ extern "C" int32_t sla_mp_dense_fwd(int32_t n, int32_t K1, const float* X1, int3
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kDT, smem) != cudaSuccess || occ < 1) occ = 1;
   const int blocks = grid_rows(n, 64, 148 * (occ < 8 ? occ : 8));
-  cudaStream_t s = (cudaStream_t)stream;
-  const __nv_bfloat16* Wb = (const __nv_bfloat16*)W_bf16;
   if (nm == 1) dense_fwd_kernel<1><<<blocks, kDT, smem, s>>>(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y);
   else if (nm == 2) dense_fwd_kernel<2><<<blocks, kDT, smem, s>>>(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y);
   else dense_fwd_kernel<3><<<blocks, kDT, smem, s>>>(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y);
@@ -786,8 +995,12 @@ extern "C" int32_t sla_mp_head_fwd(int32_t n, const int32_t* g_rowptr, const int
                                    double* g_val, void* stream) {
   if (n < 0) return SLA_ERR_INVALID;
   if (n == 0) return SLA_OK;
-  head_fwd_kernel<<<grid_rows(n, 8), 256, 0, (cudaStream_t)stream>>>(n, g_rowptr, g_col, g_src, e, d, PQR,
-                                                                    ue, v, vd, theta, g_val);
+  if ((reinterpret_cast<uintptr_t>(PQR) & 15u) == 0)
+    head4_fwd_kernel<<<grid_rows(n, 32), 256, 0, (cudaStream_t)stream>>>(
+        n, g_rowptr, g_col, g_src, e, reinterpret_cast<const float4*>(PQR), ue, v, vd, theta);
+  else
+    head_fwd_kernel<<<grid_rows(n, 8), 256, 0, (cudaStream_t)stream>>>(n, g_rowptr, g_col, g_src, e, d, PQR,
+                                                                      ue, v, vd, theta, g_val);
   head_gval_kernel<<<grid_rows(n, 256), 256, 0, (cudaStream_t)stream>>>(n, g_rowptr, g_col, d, theta, g_val);
   MP_LAUNCH_CHECK();
   return SLA_OK;
