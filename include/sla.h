@@ -75,6 +75,7 @@ extern "C" {
 #define SLA_WS_TRANSPOSE 4      /* sla_csr_transpose                           */
 #define SLA_WS_COO 5            /* sla_coo_to_csr (pass the COO entry count as nnz) */
 #define SLA_WS_CG_GGT 7         /* sla_cg_ggt: pass the entry count of G as nnz */
+#define SLA_WS_SPMV_MERGE 9     /* sla_spmv_merge                              */
 #define SLA_WS_CG_MULTI 8       /* sla_cg_multi / sla_adjoint_backward_multi:
                                    batch = number of right-hand sides k       */
 #define SLA_WS_BATCHED 6        /* batched CG: n = rows per system (shared
@@ -172,10 +173,36 @@ int32_t sla_csr_check(const sla_csr* A, int32_t* ok, void* stream);
 /* Algorithm 1 step 3a; torch.sparse in the paper's pytorch backend)     */
 /* ------------------------------------------------------------------ */
 
-/* val [nnz], x [n] -> y [n].  x and y must not overlap.  The kernel is
- * picked from the mean row length (nnz/n) and, inside each row tile, from
- * the tile's entry count: short rows are staged through shared memory and
- * summed one row per thread, long rows one row per warp. */
+/* val [nnz], x [n] -> y [n].  x and y must not overlap.  Up to 4 Mi rows one
+ * thread sums one row (gathers batched); above, persistent CTAs stream row
+ * tiles into shared memory with bulk copies and sum one row per thread, rows
+ * of an over-full tile one per warp.  For very uneven row lengths use
+ * sla_spmv_merge (sla_spmv_scheme says which). */
+/* Load-balanced SpMV along the merge path of the n row ends and the nnz
+ * nonzeros: every thread takes 8 consecutive items whatever rows they
+ * belong to, so a row of any length costs what its entries cost; rows that
+ * cross threads are completed by a fix-up kernel from per-thread partial
+ * sums added in a fixed order (deterministic; such rows are rounded in that
+ * order rather than as one sequential sum).  Arguments as sla_spmv, plus a
+ * workspace of sla_workspace_size(SLA_WS_SPMV_MERGE, n, nnz, 1) bytes
+ * (256-byte aligned; SLA_ERR_WORKSPACE otherwise).  Asynchronous. */
+int32_t sla_spmv_merge(const sla_csr* A, const double* val, const double* x,
+                       double* y, void* ws, size_t ws_bytes, void* stream);
+
+/* Row-length statistics of a pattern: out (DEVICE int32[2]) receives the
+ * longest row and the number of rows longer than 1024 entries.
+ * Asynchronous. */
+int32_t sla_csr_row_stats(const sla_csr* A, int32_t* out, void* stream);
+
+/* SpMV scheme for a pattern from its statistics: SLA_SPMV_ROWS (sla_spmv)
+ * or SLA_SPMV_MERGE (sla_spmv_merge), the latter when the longest row is
+ * long enough that the one thread (n <= 4 Mi rows) or warp (above) that
+ * sla_spmv gives it would take longer than the merge path over the whole
+ * matrix: max_row > max(256, (n + nnz) / 1024), resp. / 32. */
+#define SLA_SPMV_ROWS 0
+#define SLA_SPMV_MERGE 1
+int32_t sla_spmv_scheme(int32_t n, int64_t nnz, int32_t max_row);
+
 int32_t sla_spmv(const sla_csr* A, const double* val, const double* x,
                  double* y, void* stream);
 

@@ -37,6 +37,9 @@ SLA_WS_COO = 5
 SLA_WS_BATCHED = 6
 SLA_WS_CG_GGT = 7
 SLA_WS_CG_MULTI = 8
+SLA_WS_SPMV_MERGE = 9
+SLA_SPMV_ROWS = 0
+SLA_SPMV_MERGE = 1
 SLA_MULTI_MAX_RHS = 32
 
 SLA_ADJ_CG = 0
@@ -97,6 +100,12 @@ def lib() -> ctypes.CDLL:
             L.sla_csr_check.restype = i32
             L.sla_spmv.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, P]
             L.sla_spmv.restype = i32
+            L.sla_spmv_merge.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, P, ctypes.c_size_t, P]
+            L.sla_spmv_merge.restype = i32
+            L.sla_csr_row_stats.argtypes = [ctypes.POINTER(SlaCsr), P, P]
+            L.sla_csr_row_stats.restype = i32
+            L.sla_spmv_scheme.argtypes = [i32, ctypes.c_int64, i32]
+            L.sla_spmv_scheme.restype = i32
             L.sla_cg.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, ctypes.POINTER(SlaOpts), P, P,
                                  ctypes.c_size_t, P]
             L.sla_cg.restype = i32

@@ -124,6 +124,9 @@ constexpr GgtLayout ggt_layout(int n, int nnz_g) {
 // Several right-hand sides sharing one matrix (sla_multi.cu).
 size_t multi_ws_bytes(int n, int k);
 
+// Merge-path SpMV carries (sla_spmv_merge.cu).
+size_t spmv_merge_ws_bytes(int n, long long nnz);
+
 // Pattern utilities (sla_pattern.cu).
 size_t transpose_ws_bytes(int n, int nnz);
 size_t coo_ws_bytes(int n, long long m);
@@ -156,6 +159,9 @@ inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
       return true;
     case SLA_WS_CG_GGT:
       *out = ggt_layout(n, nnz).total;  // nnz = entries of G
+      return true;
+    case SLA_WS_SPMV_MERGE:
+      *out = spmv_merge_ws_bytes(n, nnz);
       return true;
     case SLA_WS_CG_MULTI:
       *out = multi_ws_bytes(n, batch);

@@ -64,6 +64,7 @@ class CSRMatrix:
         if self.n < 0:
             raise ValueError("rowptr needs n+1 >= 1 entries")
         self._c = L.SlaCsr(self.n, self.nnz, rowptr.data_ptr(), col.data_ptr() if self.nnz else None)
+        self._stats = None
         if check:
             self.validate()
 
@@ -75,12 +76,33 @@ class CSRMatrix:
         return cls(rp, c, check=check)
 
     def validate(self) -> None:
-        ok = torch.empty(1, dtype=torch.int32, device=self.device)
-        L.check("sla_csr_check", L.lib().sla_csr_check(ctypes.byref(self._c), ok.data_ptr(),
-                                                      _stream_ptr(self.device)))
-        if int(ok.item()) != 1:
+        """Checks the pattern and takes its row-length statistics (one host
+        synchronisation for both)."""
+        buf = torch.empty(3, dtype=torch.int32, device=self.device)
+        st = _stream_ptr(self.device)
+        L.check("sla_csr_check", L.lib().sla_csr_check(ctypes.byref(self._c), buf.data_ptr(), st))
+        L.check("sla_csr_row_stats", L.lib().sla_csr_row_stats(ctypes.byref(self._c), buf[1:].data_ptr(), st))
+        h = buf.cpu()
+        if int(h[0]) != 1:
             raise ValueError("invalid CSR pattern (rowptr not monotone, rowptr[n] != nnz, column "
                              "out of range, or columns not strictly ascending in a row)")
+        self._stats = (int(h[1]), int(h[2]))
+
+    def row_stats(self) -> tuple:
+        """(longest row, rows longer than 1024 entries), computed on the
+        device once per pattern."""
+        if self._stats is None:
+            buf = torch.empty(2, dtype=torch.int32, device=self.device)
+            L.check("sla_csr_row_stats", L.lib().sla_csr_row_stats(ctypes.byref(self._c), buf.data_ptr(),
+                                                                  _stream_ptr(self.device)))
+            h = buf.cpu()
+            self._stats = (int(h[0]), int(h[1]))
+        return self._stats
+
+    @property
+    def spmv_scheme(self) -> int:
+        """L.SLA_SPMV_ROWS or L.SLA_SPMV_MERGE, from the row-length statistics."""
+        return int(L.lib().sla_spmv_scheme(self.n, self.nnz, self.row_stats()[0]))
 
     @property
     def c(self) -> L.SlaCsr:
@@ -156,14 +178,31 @@ def clear_workspaces() -> None:
         _ws_cache.clear()
 
 
-def spmv(A: CSRMatrix, val: torch.Tensor, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
-    """y = A x (FP64)."""
+_SCHEMES = {"rows": L.SLA_SPMV_ROWS, "merge": L.SLA_SPMV_MERGE}
+
+
+def spmv(A: CSRMatrix, val: torch.Tensor, x: torch.Tensor, out: torch.Tensor | None = None,
+         scheme: str = "auto") -> torch.Tensor:
+    """y = A x (FP64).  scheme "auto" picks the row kernels (sla_spmv) or
+    the merge-path kernel (sla_spmv_merge) from the pattern's row-length
+    statistics (sla_spmv_scheme); "rows" / "merge" force one."""
     _need(val, torch.float64, A.device, "val", A.nnz)
     _need(x, torch.float64, A.device, "x", A.n)
     y = torch.empty(A.n, dtype=torch.float64, device=A.device) if out is None else out
     _need(y, torch.float64, A.device, "out", A.n)
-    L.check("sla_spmv", L.lib().sla_spmv(ctypes.byref(A.c), _ptr(val), _ptr(x), _ptr(y),
-                                        _stream_ptr(A.device)))
+    if scheme == "auto":
+        kind = A.spmv_scheme
+    elif scheme in _SCHEMES:
+        kind = _SCHEMES[scheme]
+    else:
+        raise ValueError("scheme must be 'auto', 'rows' or 'merge'")
+    if kind == L.SLA_SPMV_MERGE:
+        ws = workspace(L.SLA_WS_SPMV_MERGE, A.n, A.nnz, 1, A.device)
+        L.check("sla_spmv_merge", L.lib().sla_spmv_merge(ctypes.byref(A.c), _ptr(val), _ptr(x), _ptr(y),
+                                                        ws.data_ptr(), ws.numel(), _stream_ptr(A.device)))
+    else:
+        L.check("sla_spmv", L.lib().sla_spmv(ctypes.byref(A.c), _ptr(val), _ptr(x), _ptr(y),
+                                            _stream_ptr(A.device)))
     return y
 
 

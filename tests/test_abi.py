@@ -138,3 +138,23 @@ def test_grid_barrier_selftest_rejects_bad_arguments_without_launch():
     assert lib.sla_selftest_grid_barrier(4, 4, 1000, 1, fake, None) == L.SLA_ERR_INVALID
     assert lib.sla_selftest_grid_barrier(4, -1, 0, 1, fake, None) == L.SLA_ERR_INVALID
     assert lib.sla_selftest_grid_barrier(4, -1, 1000, -1, fake, None) == L.SLA_ERR_INVALID
+
+
+def test_spmv_scheme_rule_and_merge_argument_checks():
+    lib = L.lib()
+    # stencil-like: short rows -> row kernels; one dominant long row -> merge path
+    assert lib.sla_spmv_scheme(1 << 20, 7 << 20, 7) == L.SLA_SPMV_ROWS
+    assert lib.sla_spmv_scheme(100000, 300000, 100000) == L.SLA_SPMV_MERGE
+    assert lib.sla_spmv_scheme(100000, 300000, 256) == L.SLA_SPMV_ROWS        # not above 256
+    assert lib.sla_spmv_scheme(200000, 1431355, 4824) == L.SLA_SPMV_MERGE     # (n + nnz) / 1024 = 1592
+    assert lib.sla_spmv_scheme(1 << 20, 5 << 20, 5000) == L.SLA_SPMV_ROWS     # 6 Mi items: limit 6144
+    # above 4 Mi rows a long row goes to a warp: the limit is (n + nnz) / 32
+    assert lib.sla_spmv_scheme(1 << 23, 7 << 23, 100000) == L.SLA_SPMV_ROWS
+    assert lib.sla_spmv_scheme(1 << 23, 7 << 23, 3000000) == L.SLA_SPMV_MERGE
+    fake = ctypes.c_void_p(0x1000)
+    A = L.SlaCsr(10, 20, fake, fake)
+    assert lib.sla_spmv_merge(None, fake, fake, ctypes.c_void_p(0x2000), fake, 1 << 20, None) == L.SLA_ERR_INVALID
+    assert lib.sla_spmv_merge(ctypes.byref(A), fake, fake, fake, fake, 1 << 20, None) == L.SLA_ERR_INVALID  # x == y
+    assert lib.sla_spmv_merge(ctypes.byref(A), fake, fake, ctypes.c_void_p(0x2000), None, 0,
+                              None) == L.SLA_ERR_WORKSPACE
+    assert L.workspace_size(L.SLA_WS_SPMV_MERGE, 10, 20) >= 4 * 256
