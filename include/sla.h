@@ -198,7 +198,7 @@ int32_t sla_csr_row_stats(const sla_csr* A, int32_t* out, void* stream);
  * or SLA_SPMV_MERGE (sla_spmv_merge), the latter when the longest row is
  * long enough that the one thread (n <= 4 Mi rows) or warp (above) that
  * sla_spmv gives it would take longer than the merge path over the whole
- * matrix: max_row > max(256, (n + nnz) / 1024), resp. / 32. */
+ * matrix: max_row > max(256, (n + nnz) / 8192), resp. / 256. */
 #define SLA_SPMV_ROWS 0
 #define SLA_SPMV_MERGE 1
 int32_t sla_spmv_scheme(int32_t n, int64_t nnz, int32_t max_row);

@@ -146,11 +146,12 @@ def test_spmv_scheme_rule_and_merge_argument_checks():
     assert lib.sla_spmv_scheme(1 << 20, 7 << 20, 7) == L.SLA_SPMV_ROWS
     assert lib.sla_spmv_scheme(100000, 300000, 100000) == L.SLA_SPMV_MERGE
     assert lib.sla_spmv_scheme(100000, 300000, 256) == L.SLA_SPMV_ROWS        # not above 256
-    assert lib.sla_spmv_scheme(200000, 1431355, 4824) == L.SLA_SPMV_MERGE     # (n + nnz) / 1024 = 1592
-    assert lib.sla_spmv_scheme(1 << 20, 5 << 20, 5000) == L.SLA_SPMV_ROWS     # 6 Mi items: limit 6144
-    # above 4 Mi rows a long row goes to a warp: the limit is (n + nnz) / 32
-    assert lib.sla_spmv_scheme(1 << 23, 7 << 23, 100000) == L.SLA_SPMV_ROWS
-    assert lib.sla_spmv_scheme(1 << 23, 7 << 23, 3000000) == L.SLA_SPMV_MERGE
+    assert lib.sla_spmv_scheme(200000, 1431355, 4824) == L.SLA_SPMV_MERGE
+    assert lib.sla_spmv_scheme(1 << 20, 5 << 20, 700) == L.SLA_SPMV_ROWS      # 6 Mi items: limit 768
+    assert lib.sla_spmv_scheme(1 << 20, 5 << 20, 800) == L.SLA_SPMV_MERGE
+    # above 4 Mi rows a long row goes to a warp: the limit is (n + nnz) / 256
+    assert lib.sla_spmv_scheme(1 << 23, 7 << 23, 200000) == L.SLA_SPMV_ROWS
+    assert lib.sla_spmv_scheme(1 << 23, 7 << 23, 300000) == L.SLA_SPMV_MERGE
     fake = ctypes.c_void_p(0x1000)
     A = L.SlaCsr(10, 20, fake, fake)
     assert lib.sla_spmv_merge(None, fake, fake, ctypes.c_void_p(0x2000), fake, 1 << 20, None) == L.SLA_ERR_INVALID
