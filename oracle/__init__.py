@@ -14,6 +14,8 @@ Function map (paper passage each one follows):
   spmv              SpMV y = A x (the product inside Algorithm 1, step 3a)
   diag              Jacobi diagonal (Sec. 4.1, Tab. 3 caption)
   pcg               Algorithm 1 with P = 1, Jacobi / none / G G^T preconditioner
+  pcg_pipelined     pipelined PCG (Ghysels-Vanroose), the merged-reduction CG
+                    variant App. C names as the roadmap for reduction latency
   cg_fixed          exactly k unpreconditioned CG steps (Sec. 4.2, Tab. 7 setting)
   bicgstab          right-preconditioned BiCGStab (cited in Sec. 1 and 3.1)
   transpose         CSR of A^T for A^T lambda = dL/dx (Eq. 3)
@@ -65,6 +67,8 @@ def _load():
             lib.or_diag.restype = None
             lib.or_pcg.argtypes = [i32, P, P, P, P, P, d, d, i32, i32, i32, i32, P, P, P, P, P]
             lib.or_pcg.restype = ctypes.c_int
+            lib.or_pcg_pipelined.argtypes = [i32, P, P, P, P, P, d, d, i32, i32, i32, i32, P, P]
+            lib.or_pcg_pipelined.restype = ctypes.c_int
             lib.or_cg_fixed.argtypes = [i32, P, P, P, P, P, i32]
             lib.or_cg_fixed.restype = None
             lib.or_bicgstab.argtypes = [i32, P, P, P, P, P, d, d, i32, i32, i32, i32, P, P]
@@ -137,6 +141,23 @@ def pcg(rowptr, col, val, b, rtol=1e-10, atol=0.0, max_iter=None, precond="jacob
                    0 if x0 is None else 1, _PRECOND[precond],
                    None if gr is None else _p(gr), None if gc is None else _p(gc),
                    None if gv is None else _p(gv), _p(info), _p(res))
+    return x, _info(info, res)
+
+
+def pcg_pipelined(rowptr, col, val, b, rtol=1e-10, atol=0.0, max_iter=None, precond="jacobi",
+                  x0=None, max_restarts=2):
+    """Pipelined PCG (one merged reduction per iteration; App. C roadmap).
+    Same exits and restarts as pcg.  Returns (x, info)."""
+    if precond not in ("none", "jacobi"):
+        raise ValueError("pcg_pipelined: precond must be 'none' or 'jacobi'")
+    rowptr, col, val, b = _i32(rowptr), _i32(col), _f64(val), _f64(b)
+    n = rowptr.shape[0] - 1
+    x = np.zeros(n) if x0 is None else _f64(x0).copy()
+    info = np.zeros(2, np.int32)
+    res = np.zeros(2)
+    mi = default_max_iter(n) if max_iter is None else int(max_iter)
+    _load().or_pcg_pipelined(n, _p(rowptr), _p(col), _p(val), _p(b), _p(x), rtol, atol, mi,
+                             max_restarts, 0 if x0 is None else 1, _PRECOND[precond], _p(info), _p(res))
     return x, _info(info, res)
 
 

@@ -236,6 +236,152 @@ int or_pcg(int32_t n, const int32_t* rowptr, const int32_t* col,
   return st;
 }
 
+/* ---------------------------------------------------------------------- */
+/* Pipelined PCG (Ghysels & Vanroose, "Hiding global synchronization      */
+/* latency in the preconditioned Conjugate Gradient algorithm", Parallel  */
+/* Computing 2014): one of the CG variants that merge the inner-product   */
+/* reductions, named in App. C as the roadmap item for reduction latency. */
+/* In exact arithmetic its iterates are those of pcg_core; it carries     */
+/* w = A u, s = A p and z = A M^{-1} s as recurrences so that the three   */
+/* inner products of an iteration form one reduction and the iteration's  */
+/* SpMV (of m = M^{-1} w) does not depend on that reduction's result.     */
+/* Per iteration i:                                                        */
+/*   gamma = (r,u), delta = (w,u), ||r||        -- one reduction           */
+/*   m = M^{-1} w ; nv = A m                                               */
+/*   beta = gamma/gamma_prev, alpha = gamma/(delta - beta*gamma/alpha_prev)*/
+/*   (beta = 0, alpha = gamma/delta on the first iteration of a start)     */
+/*   z = nv + beta z ; s = w + beta s ; p = u + beta p                     */
+/*   x += alpha p ; r -= alpha s ; w -= alpha z ; u = M^{-1} r             */
+/* Reading for a pointwise (Jacobi or identity) M: u is recomputed as      */
+/* M^{-1} r rather than carried by the recurrence u -= alpha q, q = m +    */
+/* beta q of the general method; both equal M^{-1} r in exact arithmetic,  */
+/* and q is then not needed.  Exits and restarts as in pcg_core: the       */
+/* recursive-residual test, then the true residual with at most            */
+/* max_restarts restarts from the current x; NOT_SPD when gamma <= 0 or    */
+/* the denominator (= p^T A p) <= 0, BREAKDOWN on a non-finite scalar.     */
+/* precond: 0 none, 1 Jacobi.                                              */
+/* ---------------------------------------------------------------------- */
+int or_pcg_pipelined(int32_t n, const int32_t* rowptr, const int32_t* col,
+                     const double* val, const double* b, double* x,
+                     double rtol, double atol, int32_t max_iter,
+                     int32_t max_restarts, int32_t use_x0, int32_t precond,
+                     int32_t* out_info, double* out_res) {
+  size_t bytes = sizeof(double) * (size_t)(n > 0 ? n : 1);
+  double* dinv = (double*)malloc(bytes);
+  double* r = (double*)malloc(bytes);
+  double* u = (double*)malloc(bytes);
+  double* w = (double*)malloc(bytes);
+  double* m = (double*)malloc(bytes);
+  double* nv = (double*)malloc(bytes);
+  double* z = (double*)malloc(bytes);
+  double* s = (double*)malloc(bytes);
+  double* p = (double*)malloc(bytes);
+  int status = OR_NOT_CONVERGED;
+  int32_t it = 0;
+  double bnorm = nrm2(n, b);
+  double thresh = rtol * bnorm > atol ? rtol * bnorm : atol;
+  double rnorm = 0.0;
+
+  /* M^{-1} as a pointwise scale */
+  if (precond == 1) {
+    or_diag(n, rowptr, col, val, dinv);
+    for (int32_t i = 0; i < n; ++i) {
+      if (!(dinv[i] > 0.0)) {
+        out_info[0] = 0;
+        out_info[1] = OR_NOT_SPD;
+        out_res[0] = out_res[1] = NAN;
+        status = OR_NOT_SPD;
+        goto out;
+      }
+      dinv[i] = 1.0 / dinv[i];
+    }
+  } else {
+    for (int32_t i = 0; i < n; ++i) dinv[i] = 1.0;
+  }
+
+  if (!use_x0)
+    for (int32_t i = 0; i < n; ++i) x[i] = 0.0;
+
+  if (bnorm == 0.0) {
+    for (int32_t i = 0; i < n; ++i) x[i] = 0.0;
+    out_info[0] = 0;
+    out_info[1] = OR_OK;
+    out_res[0] = 0.0;
+    out_res[1] = 0.0;
+    status = OR_OK;
+    goto out;
+  }
+
+  for (int32_t restart = 0; restart <= max_restarts; ++restart) {
+    /* r = b - A x ; u = M^{-1} r ; w = A u ; z = s = p = 0 */
+    or_spmv(n, rowptr, col, val, x, nv);
+    for (int32_t i = 0; i < n; ++i) r[i] = b[i] - nv[i];
+    for (int32_t i = 0; i < n; ++i) u[i] = dinv[i] * r[i];
+    or_spmv(n, rowptr, col, val, u, w);
+    for (int32_t i = 0; i < n; ++i) z[i] = s[i] = p[i] = 0.0;
+    rnorm = nrm2(n, r);
+    status = OR_NOT_CONVERGED;
+    if (!isfinite(rnorm)) { status = OR_BREAKDOWN; break; }
+    if (rnorm <= thresh) { status = OR_OK; }
+
+    double gamma_prev = 0.0, alpha_prev = 0.0;
+    int first = 1;
+    while (status == OR_NOT_CONVERGED) {
+      double gamma = dot(n, r, u);
+      double delta = dot(n, w, u);
+      rnorm = nrm2(n, r);
+      if (!isfinite(gamma) || !isfinite(delta) || !isfinite(rnorm)) { status = OR_BREAKDOWN; break; }
+      if (rnorm <= thresh) { status = OR_OK; break; }
+      if (it >= max_iter) break;
+      if (!(gamma > 0.0)) { status = OR_NOT_SPD; break; }
+      double beta, denom;
+      if (first) {
+        beta = 0.0;
+        denom = delta;
+      } else {
+        beta = gamma / gamma_prev;
+        denom = delta - beta * gamma / alpha_prev;
+      }
+      if (!isfinite(denom)) { status = OR_BREAKDOWN; break; }
+      if (!(denom > 0.0)) { status = OR_NOT_SPD; break; }
+      double alpha = gamma / denom;
+      for (int32_t i = 0; i < n; ++i) m[i] = dinv[i] * w[i];
+      or_spmv(n, rowptr, col, val, m, nv);
+      for (int32_t i = 0; i < n; ++i) z[i] = nv[i] + beta * z[i];
+      for (int32_t i = 0; i < n; ++i) s[i] = w[i] + beta * s[i];
+      for (int32_t i = 0; i < n; ++i) p[i] = u[i] + beta * p[i];
+      for (int32_t i = 0; i < n; ++i) x[i] += alpha * p[i];
+      for (int32_t i = 0; i < n; ++i) r[i] -= alpha * s[i];
+      for (int32_t i = 0; i < n; ++i) w[i] -= alpha * z[i];
+      for (int32_t i = 0; i < n; ++i) u[i] = dinv[i] * r[i];
+      gamma_prev = gamma;
+      alpha_prev = alpha;
+      first = 0;
+      ++it;
+    }
+    if (status != OR_OK) break;
+    /* true residual check */
+    or_spmv(n, rowptr, col, val, x, nv);
+    for (int32_t i = 0; i < n; ++i) r[i] = b[i] - nv[i];
+    double tnorm = nrm2(n, r);
+    if (tnorm <= 2.0 * thresh) break;
+    if (!isfinite(tnorm)) { status = OR_BREAKDOWN; break; }
+    if (restart == max_restarts || it >= max_iter) { status = OR_NOT_CONVERGED; break; }
+  }
+
+  /* final relative residuals */
+  or_spmv(n, rowptr, col, val, x, nv);
+  for (int32_t i = 0; i < n; ++i) r[i] = b[i] - nv[i];
+  out_info[0] = it;
+  out_info[1] = status;
+  out_res[0] = rnorm / bnorm;
+  out_res[1] = nrm2(n, r) / bnorm;
+
+out:
+  free(dinv); free(r); free(u); free(w); free(m); free(nv); free(z); free(s); free(p);
+  return status;
+}
+
 /* Fixed-k unpreconditioned CG (the setting of Sec. 4.2 / Tab. 7): exactly  */
 /* k iterations of Algorithm 1 with no convergence test.                    */
 void or_cg_fixed(int32_t n, const int32_t* rowptr, const int32_t* col,

@@ -190,6 +190,104 @@ def test_pcg_ggt_special_cases():
     assert ig["status"] == 0 and ig["iters"] == 1
 
 
+# ---------------------------------------------------------------- pipelined PCG
+
+def _krylov_minimiser(A, b, dinv, k):
+    """Independent statement of what the k-th PCG iterate is (x0 = 0): the
+    minimiser of the A-norm error over the preconditioned Krylov space
+    span{M^-1 b, (M^-1 A) M^-1 b, ...} of dimension k, from an orthonormal
+    basis of that space and the k x k Galerkin system."""
+    v = dinv * b
+    cols = []
+    for _ in range(k):
+        cols.append(v / np.linalg.norm(v))
+        v = dinv * (A @ cols[-1])
+    V, _ = np.linalg.qr(np.stack(cols, axis=1))
+    y = np.linalg.solve(V.T @ A @ V, V.T @ b)
+    return V @ y
+
+
+@pytest.mark.parametrize("fn", ["pcg", "pcg_pipelined"])
+@pytest.mark.parametrize("precond", ["jacobi", "none"])
+def test_pcg_iterates_are_krylov_minimisers(fn, precond):
+    rp, c, v = I.diffusion2d_random(6, 3)
+    n = 36
+    A = dense(rp, c, v)
+    b = I.rhs_uniform(n, 11)
+    dinv = 1.0 / np.diag(A) if precond == "jacobi" else np.ones(n)
+    for k in range(1, 8):
+        x, info = getattr(oracle, fn)(rp, c, v, b, rtol=0.0, max_iter=k, precond=precond)
+        assert info["iters"] == k and info["status_name"] == "NOT_CONVERGED"
+        xk = _krylov_minimiser(A, b, dinv, k)
+        assert np.linalg.norm(x - xk) <= 1e-9 * np.linalg.norm(xk), (fn, k)
+
+
+def test_pipelined_finite_termination_and_eigenvector():
+    rng = np.random.default_rng(5)
+    n = 12
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(np.linspace(1.0, 9.0, n)) @ Q.T
+    As = sp.csr_matrix(A)
+    rp, c, v = As.indptr.astype(np.int32), As.indices.astype(np.int32), As.data
+    b = rng.uniform(-1, 1, n)
+    x, info = oracle.pcg_pipelined(rp, c, v, b, rtol=0.0, max_iter=n, precond="none")
+    xs = np.linalg.solve(A, b)
+    assert info["iters"] == n
+    assert np.linalg.norm(x - xs) <= 1e-9 * np.linalg.norm(xs)
+    # a Poisson eigenvector (constant diagonal 4, so also one of D^-1 A) takes one step
+    N = 16
+    rp, c, v = I.poisson2d(N)
+    p = np.arange(1, N + 1)
+    vec = np.outer(np.sin(3 * np.pi * p / (N + 1)), np.sin(2 * np.pi * p / (N + 1))).ravel()
+    mu = 4 * math.sin(2 * math.pi / (2 * (N + 1))) ** 2 + 4 * math.sin(3 * math.pi / (2 * (N + 1))) ** 2
+    x, info = oracle.pcg_pipelined(rp, c, v, vec, rtol=1e-13)
+    assert info["status"] == 0 and info["iters"] == 1
+    assert np.allclose(x, vec / mu, rtol=0, atol=1e-12 * np.abs(vec / mu).max())
+
+
+def test_pipelined_vs_sparse_lu_poisson64():
+    rp, c, v = I.poisson2d(64)
+    b = I.rhs_uniform(4096, 0)
+    x, info = oracle.pcg_pipelined(rp, c, v, b, rtol=1e-10)
+    xs = sp.linalg.spsolve(sp.csr_matrix((v, c, rp)).tocsc(), b)
+    assert info["status"] == 0
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-8
+    assert info["true_rel_res"] <= 2e-10
+    _, ref = oracle.pcg(rp, c, v, b, rtol=1e-10)
+    assert abs(info["iters"] - ref["iters"]) <= 2
+
+
+def test_pipelined_edge_cases():
+    rp, c, v = I.poisson2d(6)
+    n = 36
+    x, info = oracle.pcg_pipelined(rp, c, v, np.zeros(n))
+    assert info["status"] == 0 and info["iters"] == 0 and not x.any()
+    v2 = v.copy()
+    v2[rp[3]:rp[4]][c[rp[3]:rp[4]] == 3] = -1.0
+    _, info = oracle.pcg_pipelined(rp, c, v2, np.ones(n))
+    assert info["status_name"] == "NOT_SPD" and info["iters"] == 0
+    # [[1,2],[2,1]], b = (1,-1): u = b, w = A u = (-1,1), p^T A p = (w,u) = -2
+    rpi = np.array([0, 2, 4], np.int32)
+    ci = np.array([0, 1, 0, 1], np.int32)
+    vi = np.array([1.0, 2.0, 2.0, 1.0])
+    _, info = oracle.pcg_pipelined(rpi, ci, vi, np.array([1.0, -1.0]))
+    assert info["status_name"] == "NOT_SPD" and info["iters"] == 0
+    b = I.rhs_uniform(n, 0)
+    _, info = oracle.pcg_pipelined(rp, c, v, b, rtol=1e-14, max_iter=2)
+    assert info["status_name"] == "NOT_CONVERGED" and info["iters"] == 2
+    _, info = oracle.pcg_pipelined(rp, c, v, b, max_iter=0)
+    assert info["status_name"] == "NOT_CONVERGED" and info["iters"] == 0
+    bn = b.copy()
+    bn[4] = np.nan
+    _, info = oracle.pcg_pipelined(rp, c, v, bn)
+    assert info["status_name"] == "BREAKDOWN"
+    xs = np.linalg.solve(dense(rp, c, v), b)
+    _, info = oracle.pcg_pipelined(rp, c, v, b, x0=xs, rtol=1e-10)
+    assert info["status"] == 0 and info["iters"] <= 1
+    with pytest.raises(ValueError):
+        oracle.pcg_pipelined(rp, c, v, b, precond="ggt")
+
+
 def test_cg_fixed_matches_naive_torch_loop():
     torch = pytest.importorskip("torch")
     rp, c, v = I.poisson2d(10)
