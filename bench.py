@@ -166,7 +166,25 @@ def _profile_fem_list(dev, max_iter):
     return {"iters_max": int(np.atleast_1d(info.iters).max())}
 
 
+def _profile_2d_512(dev, max_iter, pipelined):
+    """2D 512^2 sigma = 1 (262,144 rows, in L2): Jacobi-PCG as one
+    cooperative launch, standard (three grid barriers per iteration) or
+    pipelined (one)."""
+    import torch
+
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import sla
+    rp, c, v = I.diffusion2d_random(512, 11, 1.0)
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    vt = torch.from_numpy(v).to(dev)
+    bt = torch.from_numpy(I.rhs_uniform(len(rp) - 1, 12)).to(dev)
+    x, info = sla.cg(A, vt, bt, rtol=1e-8, max_iter=max_iter, max_restarts=0, pipelined=pipelined)
+    return {"iters": info.iters, "status": info.status}
+
+
 PROFILE_ROWS = {
+    "coop_2d_512": lambda dev, mi: _profile_2d_512(dev, mi, False),
+    "pipe_2d_512": lambda dev, mi: _profile_2d_512(dev, mi, True),
     "bicgstab_convdiff3d_128": _profile_bicgstab,
     "fem_list_512": _profile_fem_list,
     "factor_3d_128": _profile_factor,
@@ -373,9 +391,41 @@ def extra_rows(dev, args, peak):
                                    "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
                                    "fp64_tflops": fl / (ms / 1e3) / 1e12,
                                    "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+    out["pipelined_vs_standard"] = pipelined_rows(dev)
     out["learned_vs_jacobi"] = learned_vs_jacobi(dev)
     out["inverse_512_16rhs"] = inverse_rows(dev, peak)
     return out
+
+
+def pipelined_rows(dev):
+    """Jacobi-PCG in one cooperative launch: the standard form (three grid
+    barriers per iteration) against the pipelined form (one merged reduction
+    and one barrier per iteration), on the 2D Poisson 64^2 system (rtol
+    1e-10) and on variable-coefficient systems of 2D 512^2 and 3D 64^3
+    (sigma = 1, rtol 1e-8).  Median of 3 solves after one warm-up each."""
+    import torch
+
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import sla
+    cases = [("poisson2d_64", lambda: I.poisson2d(64), 1e-10),
+             ("diffusion2d_512", lambda: I.diffusion2d_random(512, 11, 1.0), 1e-8),
+             ("diffusion3d_64", lambda: I.diffusion3d_random(64, 1), 1e-8)]
+    res = {}
+    for name, gen, rtol in cases:
+        rp, c, v = gen()
+        n, nnz = len(rp) - 1, int(rp[-1])
+        A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+        vt = torch.from_numpy(v).to(dev)
+        bt = torch.from_numpy(I.rhs_uniform(n, 12)).to(dev)
+        row = {}
+        for tag, kw in (("standard", {}), ("pipelined", {"pipelined": True})):
+            ms, (x, info) = _time(lambda: sla.cg(A, vt, bt, rtol=rtol, **kw))
+            row[tag] = {"ms": ms, "iters": info.iters, "status": info.status,
+                        "us_per_iter": 1e3 * ms / max(info.iters, 1), "true_rel_res": info.true_rel_res}
+        row["speedup"] = row["standard"]["ms"] / row["pipelined"]["ms"]
+        row["n"], row["nnz"], row["rtol"] = n, nnz, rtol
+        res[name] = row
+    return res
 
 
 def inverse_rows(dev, peak, N=512, k=16):

@@ -67,6 +67,15 @@ extern "C" {
                                    use the per-phase kernels (graph or host
                                    loop) even at sizes where the solve would
                                    run as one cooperative launch             */
+#define SLA_FLAG_CG_PIPELINED 4 /* sla_cg and sla_adjoint_backward (method
+                                   SLA_ADJ_CG), Jacobi or no preconditioner:
+                                   pipelined PCG (Ghysels-Vanroose) -- the
+                                   three inner products of an iteration form
+                                   one reduction, one grid barrier per
+                                   iteration -- in one cooperative launch at
+                                   every size.  Not with SLA_FLAG_HOST_LOOP or
+                                   SLA_FLAG_NO_COOP (SLA_ERR_INVALID).  Needs
+                                   the SLA_WS_CG_PIPELINED workspace in sla_cg */
 
 /* Workspace kinds for sla_workspace_size(). */
 #define SLA_WS_CG 1
@@ -76,6 +85,7 @@ extern "C" {
 #define SLA_WS_COO 5            /* sla_coo_to_csr (pass the COO entry count as nnz) */
 #define SLA_WS_CG_GGT 7         /* sla_cg_ggt: pass the entry count of G as nnz */
 #define SLA_WS_SPMV_MERGE 9     /* sla_spmv_merge                              */
+#define SLA_WS_CG_PIPELINED 10  /* sla_cg with SLA_FLAG_CG_PIPELINED          */
 #define SLA_WS_CG_MULTI 8       /* sla_cg_multi / sla_adjoint_backward_multi:
                                    batch = number of right-hand sides k       */
 #define SLA_WS_BATCHED 6        /* batched CG: n = rows per system (shared
@@ -226,7 +236,13 @@ int32_t sla_spmv(const sla_csr* A, const double* val, const double* x,
  * launched one by one on `stream` and the call returns after the loop has
  * ended (it synchronises `stream`).  A grid barrier that waits more than
  * about 2 s ends the solve with SLA_ERR_TIMEOUT in *info.
- * Workspace: sla_workspace_size(SLA_WS_CG, n, nnz, 1, &bytes). */
+ * With SLA_FLAG_CG_PIPELINED the solve is the pipelined PCG of Ghysels and
+ * Vanroose (the merged-reduction CG variant named in App. C): the same
+ * exits, restarts and info record, iterates equal to the standard ones in
+ * exact arithmetic (so iteration counts agree to within rounding), one
+ * cooperative launch with one grid barrier per iteration whatever n is.
+ * Workspace: sla_workspace_size(SLA_WS_CG, n, nnz, 1, &bytes), or
+ * SLA_WS_CG_PIPELINED with SLA_FLAG_CG_PIPELINED. */
 int32_t sla_cg(const sla_csr* A, const double* val, const double* b,
                double* x, const sla_opts* opts, sla_info* info, void* ws,
                size_t ws_bytes, void* stream);

@@ -257,8 +257,15 @@ int or_pcg(int32_t n, const int32_t* rowptr, const int32_t* col,
 /* beta q of the general method; both equal M^{-1} r in exact arithmetic,  */
 /* and q is then not needed.  Exits and restarts as in pcg_core: the       */
 /* recursive-residual test, then the true residual with at most            */
-/* max_restarts restarts from the current x; NOT_SPD when gamma <= 0 or    */
-/* the denominator (= p^T A p) <= 0, BREAKDOWN on a non-finite scalar.     */
+/* max_restarts restarts from the current x; NOT_SPD when gamma <= 0, or   */
+/* when the denominator (= p^T A p) is <= 0 on the first step of a start   */
+/* (there it is u^T A u from a fresh product); BREAKDOWN on a non-finite   */
+/* scalar.  Reading: a denominator <= 0 on a later step comes from the     */
+/* recurrences for w, s, z, whose rounding errors grow near the attainable */
+/* accuracy (the known weakness of the pipelined method, which restarts or */
+/* "residual replacement" cure), not from an indefinite A, so it leads to  */
+/* the true-residual check: accepted within twice the target, else a       */
+/* restart from x while restarts remain, else NOT_CONVERGED.               */
 /* precond: 0 none, 1 Jacobi.                                              */
 /* ---------------------------------------------------------------------- */
 int or_pcg_pipelined(int32_t n, const int32_t* rowptr, const int32_t* col,
@@ -343,7 +350,11 @@ int or_pcg_pipelined(int32_t n, const int32_t* rowptr, const int32_t* col,
         denom = delta - beta * gamma / alpha_prev;
       }
       if (!isfinite(denom)) { status = OR_BREAKDOWN; break; }
-      if (!(denom > 0.0)) { status = OR_NOT_SPD; break; }
+      if (!(denom > 0.0)) {
+        if (first) { status = OR_NOT_SPD; break; }
+        status = OR_OK;  /* recurrences exhausted: to the true-residual check */
+        break;
+      }
       double alpha = gamma / denom;
       for (int32_t i = 0; i < n; ++i) m[i] = dinv[i] * w[i];
       or_spmv(n, rowptr, col, val, m, nv);
@@ -364,7 +375,7 @@ int or_pcg_pipelined(int32_t n, const int32_t* rowptr, const int32_t* col,
     or_spmv(n, rowptr, col, val, x, nv);
     for (int32_t i = 0; i < n; ++i) r[i] = b[i] - nv[i];
     double tnorm = nrm2(n, r);
-    if (tnorm <= 2.0 * thresh) break;
+    if (tnorm <= 2.0 * thresh) { status = OR_OK; break; }
     if (!isfinite(tnorm)) { status = OR_BREAKDOWN; break; }
     if (restart == max_restarts || it >= max_iter) { status = OR_NOT_CONVERGED; break; }
   }

@@ -28,6 +28,7 @@ SLA_PRECOND_GGT = 2
 
 SLA_FLAG_HOST_LOOP = 1
 SLA_FLAG_NO_COOP = 2
+SLA_FLAG_CG_PIPELINED = 4
 
 SLA_WS_CG = 1
 SLA_WS_BICGSTAB = 2
@@ -38,6 +39,7 @@ SLA_WS_BATCHED = 6
 SLA_WS_CG_GGT = 7
 SLA_WS_CG_MULTI = 8
 SLA_WS_SPMV_MERGE = 9
+SLA_WS_CG_PIPELINED = 10
 SLA_SPMV_ROWS = 0
 SLA_SPMV_MERGE = 1
 SLA_MULTI_MAX_RHS = 32

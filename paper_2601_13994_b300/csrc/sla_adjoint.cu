@@ -111,7 +111,9 @@ extern "C" int32_t sla_adjoint_backward(const sla_csr* A, const sla_csr_t* AT, c
   if (opts->precond != SLA_PRECOND_NONE && opts->precond != SLA_PRECOND_JACOBI) return SLA_ERR_INVALID;
   size_t need = 0;
   workspace_bytes(SLA_WS_ADJOINT, n, nnz, 1, &need);
-  int rc = validate_solve_args(A, val, grad_x, grad_b, opts, info, ws, ws_bytes, need);
+  const int allowed = SLA_FLAG_HOST_LOOP | SLA_FLAG_NO_COOP |
+                      (method == SLA_ADJ_CG ? SLA_FLAG_CG_PIPELINED : 0);
+  int rc = validate_solve_args(A, val, grad_x, grad_b, opts, info, ws, ws_bytes, need, allowed);
   if (rc != SLA_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   sla_opts o = *opts;

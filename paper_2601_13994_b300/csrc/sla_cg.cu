@@ -564,11 +564,19 @@ int run_host_loop(const CgPtrs& P, const KrylovDesc& desc, K1Launch k1, int g1, 
 
 bool use_cg_coop(long long n, bool ggt);
 int launch_cg_coop(const KrylovDesc& desc, void* ws, cudaStream_t s, bool* launched);
+int launch_cg_pipe(const KrylovDesc& desc, void* ws, cudaStream_t s, bool* launched);
 
 // allow_graph = false: where the cooperative launch is not taken, drive the
 // loop from the host (no graph objects), as the allocation-free entry needs.
 int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags, bool allow_graph = true) {
   const int n = desc.n;
+  if (flags & SLA_FLAG_CG_PIPELINED) {
+    // pipelined PCG (sla_cg_pipe.cu): cooperative only, at every size
+    bool launched = false;
+    const int rc = launch_cg_pipe(desc, ws, s, &launched);
+    if (rc != SLA_OK) return rc;
+    return launched ? SLA_OK : SLA_ERR_CUDA;
+  }
   if (!(flags & (SLA_FLAG_HOST_LOOP | SLA_FLAG_NO_COOP)) && use_cg_coop(n, false)) {
     // one cooperative launch per solve (sla_cg_coop.cu) where the device runs it
     bool launched = false;
@@ -618,7 +626,7 @@ int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags, bool 
 
 int validate_solve_args(const sla_csr* A, const double* val, const double* b, const double* x,
                         const sla_opts* o, const sla_info* info, const void* ws, size_t ws_bytes,
-                        size_t need) {
+                        size_t need, int allowed_flags) {
   if (A == nullptr || o == nullptr || info == nullptr) return SLA_ERR_INVALID;
   if (A->n < 0 || A->nnz < 0) return SLA_ERR_INVALID;
   if (A->n > 0 && (A->rowptr == nullptr || b == nullptr || x == nullptr)) return SLA_ERR_INVALID;
@@ -626,7 +634,9 @@ int validate_solve_args(const sla_csr* A, const double* val, const double* b, co
   if (A->n > 0 && (const void*)b == (const void*)x) return SLA_ERR_INVALID;
   if (!(o->rtol >= 0.0) || !(o->atol >= 0.0) || o->max_iter < 0 || o->max_restarts < 0 ||
       o->max_restarts > 16 || (o->use_x0 != 0 && o->use_x0 != 1) ||
-      (o->flags & ~(SLA_FLAG_HOST_LOOP | SLA_FLAG_NO_COOP)) != 0)
+      (o->flags & ~allowed_flags) != 0)
+    return SLA_ERR_INVALID;
+  if ((o->flags & SLA_FLAG_CG_PIPELINED) && (o->flags & (SLA_FLAG_HOST_LOOP | SLA_FLAG_NO_COOP)))
     return SLA_ERR_INVALID;
   if (ws == nullptr || ((uintptr_t)ws & 255u) != 0 || ws_bytes < need) return SLA_ERR_WORKSPACE;
   return SLA_OK;
@@ -639,9 +649,12 @@ using namespace sla;
 extern "C" int32_t sla_cg(const sla_csr* A, const double* val, const double* b, double* x,
                           const sla_opts* opts, sla_info* info, void* ws, size_t ws_bytes,
                           void* stream) {
-  if (A == nullptr) return SLA_ERR_INVALID;
-  const size_t need = cg_layout(A->n > 0 ? A->n : 0).total;
-  int rc = validate_solve_args(A, val, b, x, opts, info, ws, ws_bytes, need);
+  if (A == nullptr || opts == nullptr) return SLA_ERR_INVALID;
+  const int nn = A->n > 0 ? A->n : 0;
+  const size_t need =
+      (opts->flags & SLA_FLAG_CG_PIPELINED) ? cg_pipe_layout(nn).total : cg_layout(nn).total;
+  int rc = validate_solve_args(A, val, b, x, opts, info, ws, ws_bytes, need,
+                               SLA_FLAG_HOST_LOOP | SLA_FLAG_NO_COOP | SLA_FLAG_CG_PIPELINED);
   if (rc != SLA_OK) return rc;
   if (opts->precond != SLA_PRECOND_NONE && opts->precond != SLA_PRECOND_JACOBI) return SLA_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
@@ -713,7 +726,8 @@ extern "C" int32_t sla_cg_noalloc(const sla_csr* A, const double* val, const dou
   int rc = noalloc_scratch(&ws);
   if (rc != SLA_OK) return rc;
   const size_t need = cg_layout(A->n > 0 ? A->n : 0).total;
-  rc = validate_solve_args(A, val, b, x, opts, info, ws, kNoallocScratchBytes, need);
+  rc = validate_solve_args(A, val, b, x, opts, info, ws, kNoallocScratchBytes, need,
+                           SLA_FLAG_HOST_LOOP | SLA_FLAG_NO_COOP);
   if (rc != SLA_OK) return rc;
   if (opts->precond != SLA_PRECOND_NONE && opts->precond != SLA_PRECOND_JACOBI) return SLA_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;

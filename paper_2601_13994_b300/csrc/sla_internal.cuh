@@ -416,9 +416,10 @@ cudaError_t add_kernel(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
                        cudaGraphNode_t* out, const void* fn, int grid, int block, void** args,
                        unsigned smem = 0);
 int write_info(sla_info* info, sla_info v, cudaStream_t s);
+// allowed_flags: the SLA_FLAG_* bits the entry point accepts.
 int validate_solve_args(const sla_csr* A, const double* val, const double* b, const double* x,
                         const sla_opts* o, const sla_info* info, const void* ws, size_t ws_bytes,
-                        size_t need);
+                        size_t need, int allowed_flags = SLA_FLAG_HOST_LOOP | SLA_FLAG_NO_COOP);
 
 // Device-wide exclusive scan of int32 (sla_pattern.cu): tmp needs
 // scan_tmp_ints(n) ints; *total (device, may be null) receives the sum.

@@ -77,6 +77,26 @@ constexpr CgLayout cg_layout(int n) {
   return L;
 }
 
+// Pipelined Jacobi PCG (sla_cg_pipe.cu): descriptor, state, partials, the
+// per-row records (r, w, z, s, p, dinv: 6 doubles a row), two m buffers.
+struct CgPipeLayout {
+  size_t desc, state, part, rec, m0, m1, total;
+};
+
+constexpr CgPipeLayout cg_pipe_layout(int n) {
+  CgPipeLayout L{};
+  size_t o = 0;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  L.desc = o;  o += al256(sizeof(KrylovDesc));
+  L.state = o; o += al256(sizeof(KrylovState));
+  L.part = o;  o += al256(sizeof(double) * kMaxBlocks * kPartSlots);
+  L.rec = o;   o += al256(sizeof(double) * 6 * nn);
+  L.m0 = o;    o += al256(sizeof(double) * nn);
+  L.m1 = o;    o += al256(sizeof(double) * nn);
+  L.total = o;
+  return L;
+}
+
 // BiCGStab: descriptor, state, partials, then r, r^, p, p^, v, s, s^, t, dinv.
 struct BiLayout {
   size_t desc, state, part, vec, vec_stride, total;
@@ -131,9 +151,11 @@ size_t spmv_merge_ws_bytes(int n, long long nnz);
 size_t transpose_ws_bytes(int n, int nnz);
 size_t coo_ws_bytes(int n, long long m);
 
-// Adjoint: the larger of the CG scratch and BiCGStab scratch + valT.
+// Adjoint: the larger of the CG scratch (either form) and BiCGStab scratch
+// + valT.
 inline size_t adjoint_ws_bytes(int n, int nnz) {
-  const size_t a = cg_layout(n).total;
+  const size_t a0 = cg_layout(n).total, a1 = cg_pipe_layout(n).total;
+  const size_t a = a0 > a1 ? a0 : a1;
   const size_t b = al256(bicg_layout(n).total) + al256(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
   return a > b ? a : b;
 }
@@ -144,6 +166,9 @@ inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
   switch (kind) {
     case SLA_WS_CG:
       *out = cg_layout(n).total;
+      return true;
+    case SLA_WS_CG_PIPELINED:
+      *out = cg_pipe_layout(n).total;
       return true;
     case SLA_WS_BICGSTAB:
       *out = bicg_layout(n).total;

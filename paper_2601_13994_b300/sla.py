@@ -209,16 +209,20 @@ def spmv(A: CSRMatrix, val: torch.Tensor, x: torch.Tensor, out: torch.Tensor | N
 _PRECOND = {"none": L.SLA_PRECOND_NONE, "jacobi": L.SLA_PRECOND_JACOBI}
 
 
-def _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, n, graph=True, cooperative=True):
+def _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, n, graph=True, cooperative=True,
+          pipelined=False):
     mi = default_max_iter(n) if max_iter is None else int(max_iter)
     if precond not in _PRECOND:
         raise ValueError("precond must be one of %s" % sorted(_PRECOND))
-    flags = (0 if graph else L.SLA_FLAG_HOST_LOOP) | (0 if cooperative else L.SLA_FLAG_NO_COOP)
+    if pipelined and not (graph and cooperative):
+        raise ValueError("pipelined=True runs as one cooperative launch: graph and cooperative must stay True")
+    flags = ((0 if graph else L.SLA_FLAG_HOST_LOOP) | (0 if cooperative else L.SLA_FLAG_NO_COOP)
+             | (L.SLA_FLAG_CG_PIPELINED if pipelined else 0))
     return L.SlaOpts(float(rtol), float(atol), mi, int(max_restarts), _PRECOND[precond], int(use_x0), flags)
 
 
 def _krylov(fn_name: str, ws_kind: int, A: CSRMatrix, val, b, rtol, atol, max_iter, precond, x0,
-            max_restarts, out, graph, cooperative=True):
+            max_restarts, out, graph, cooperative=True, pipelined=False):
     _need(val, torch.float64, A.device, "val", A.nnz)
     _need(b, torch.float64, A.device, "b", A.n)
     if out is None:
@@ -233,7 +237,7 @@ def _krylov(fn_name: str, ws_kind: int, A: CSRMatrix, val, b, rtol, atol, max_it
             x.copy_(x0)
         use_x0 = 1
     info = torch.empty((1, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
-    o = _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, A.n, graph, cooperative)
+    o = _opts(rtol, atol, max_iter, max_restarts, precond, use_x0, A.n, graph, cooperative, pipelined)
     ws = workspace(ws_kind, A.n, A.nnz, 1, A.device)
     fn = getattr(L.lib(), fn_name)
     L.check(fn_name, fn(ctypes.byref(A.c), _ptr(val), _ptr(b), _ptr(x), ctypes.byref(o), info.data_ptr(),
@@ -254,15 +258,19 @@ def bicgstab(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 
 def cg(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10, atol: float = 0.0,
        max_iter: int | None = None, precond: str = "jacobi", x0: torch.Tensor | None = None,
        max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True,
-       cooperative: bool = True):
+       cooperative: bool = True, pipelined: bool = False):
     """Preconditioned CG for SPD A (Algorithm 1, one process).  Returns
     (x, SolveInfo).  Up to 2.5 Mi rows the solve is one cooperative kernel
     launch (``cooperative=False`` opts out); otherwise, with ``graph=True``,
     it is one graph launch.  Nothing synchronises until the info is read;
     ``graph=False`` launches the per-phase kernels from a host loop
-    (synchronising the stream)."""
-    return _krylov("sla_cg", L.SLA_WS_CG, A, val, b, rtol, atol, max_iter, precond, x0, max_restarts, out,
-                   graph, cooperative)
+    (synchronising the stream).  ``pipelined=True``: the pipelined PCG of
+    Ghysels and Vanroose (the three inner products of an iteration in one
+    reduction, one grid barrier per iteration; App. C's roadmap for the
+    reduction latency) as one cooperative launch at any size."""
+    ws_kind = L.SLA_WS_CG_PIPELINED if pipelined else L.SLA_WS_CG
+    return _krylov("sla_cg", ws_kind, A, val, b, rtol, atol, max_iter, precond, x0, max_restarts, out,
+                   graph, cooperative, pipelined)
 
 
 # ---------------------------------------------------------------------------
@@ -364,15 +372,18 @@ _ADJ = {"cg": L.SLA_ADJ_CG, "bicgstab": L.SLA_ADJ_BICGSTAB}
 def adjoint_backward(A: CSRMatrix, val: torch.Tensor, x: torch.Tensor, grad_x: torch.Tensor, *,
                      method: str = "cg", rtol: float = 1e-10, atol: float = 0.0,
                      max_iter: int | None = None, precond: str = "jacobi", max_restarts: int = 2,
-                     graph: bool = True, cooperative: bool = True):
-    """Solve A^T lambda = grad_x; returns (grad_b = lambda, grad_val, SolveInfo)."""
+                     graph: bool = True, cooperative: bool = True, pipelined: bool = False):
+    """Solve A^T lambda = grad_x; returns (grad_b = lambda, grad_val, SolveInfo).
+    ``pipelined=True`` (method "cg" only) solves with the pipelined PCG."""
+    if pipelined and method != "cg":
+        raise ValueError("pipelined=True is a CG variant (method='cg')")
     _need(val, torch.float64, A.device, "val", A.nnz)
     _need(x, torch.float64, A.device, "x", A.n)
     _need(grad_x, torch.float64, A.device, "grad_x", A.n)
     gb = torch.empty(A.n, dtype=torch.float64, device=A.device)
     gv = torch.empty(A.nnz, dtype=torch.float64, device=A.device)
     info = torch.empty((1, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
-    o = _opts(rtol, atol, max_iter, max_restarts, precond, 0, A.n, graph, cooperative)
+    o = _opts(rtol, atol, max_iter, max_restarts, precond, 0, A.n, graph, cooperative, pipelined)
     atp = None
     if method == "bicgstab":
         transpose_of(A)

@@ -62,6 +62,38 @@ def test_workspace_size_query():
         L.workspace_size(L.SLA_WS_CG, -1, 10)
 
 
+def test_pipelined_flag_arguments_rejected_without_launch():
+    """SLA_FLAG_CG_PIPELINED: only sla_cg and the CG adjoint accept it, never
+    with the host loop or without the cooperative form, and sla_cg then
+    needs the larger SLA_WS_CG_PIPELINED workspace (checked before any
+    launch, so fake pointers serve)."""
+    lib = L.lib()
+    n = 1000
+    wp = L.workspace_size(L.SLA_WS_CG_PIPELINED, n, 5000)
+    wc = L.workspace_size(L.SLA_WS_CG, n, 5000)
+    assert wp % 256 == 0 and wp > wc and wp >= 8 * 8 * n
+    assert L.workspace_size(L.SLA_WS_ADJOINT, n, 5000) >= wp
+    fake = ctypes.c_void_p(0x1000)
+    ws = ctypes.c_void_p(0x100000)
+    A = L.SlaCsr(n, 5000, fake, fake)
+    P = L.SLA_FLAG_CG_PIPELINED
+    for extra in (L.SLA_FLAG_HOST_LOOP, L.SLA_FLAG_NO_COOP):
+        o = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0, P | extra)
+        assert lib.sla_cg(ctypes.byref(A), fake, fake, ctypes.c_void_p(0x2000), ctypes.byref(o), fake,
+                          ws, wp, None) == L.SLA_ERR_INVALID
+    o = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0, P)
+    assert lib.sla_cg(ctypes.byref(A), fake, fake, ctypes.c_void_p(0x2000), ctypes.byref(o), fake,
+                      ws, wc, None) == L.SLA_ERR_WORKSPACE
+    assert lib.sla_bicgstab(ctypes.byref(A), fake, fake, ctypes.c_void_p(0x2000), ctypes.byref(o), fake,
+                            ws, 1 << 30, None) == L.SLA_ERR_INVALID
+    assert lib.sla_adjoint_backward(ctypes.byref(A), None, fake, fake, fake, ctypes.c_void_p(0x2000),
+                                    ctypes.c_void_p(0x3000), L.SLA_ADJ_BICGSTAB, ctypes.byref(o), fake,
+                                    ws, 1 << 30, None) == L.SLA_ERR_INVALID
+    o8 = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0, 8)
+    assert lib.sla_cg(ctypes.byref(A), fake, fake, ctypes.c_void_p(0x2000), ctypes.byref(o8), fake,
+                      ws, 1 << 30, None) == L.SLA_ERR_INVALID
+
+
 def test_bad_arguments_rejected_without_launch():
     lib = L.lib()
     A = L.SlaCsr(10, 20, None, None)

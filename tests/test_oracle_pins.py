@@ -286,6 +286,14 @@ def test_pipelined_edge_cases():
     assert info["status"] == 0 and info["iters"] <= 1
     with pytest.raises(ValueError):
         oracle.pcg_pipelined(rp, c, v, b, precond="ggt")
+    # below the recurrences' attainable accuracy: the late p^T A p <= 0 is
+    # rounding (A is SPD), so the true-residual check and restarts take over
+    rp, c, v = I.poisson2d(30)
+    b = I.rhs_uniform(900, 4)
+    _, info = oracle.pcg_pipelined(rp, c, v, b, rtol=1e-15, max_restarts=0)
+    assert info["status_name"] == "NOT_CONVERGED" and info["true_rel_res"] <= 1e-10
+    _, info = oracle.pcg_pipelined(rp, c, v, b, rtol=1e-15, max_restarts=3)
+    assert info["status_name"] == "OK" and info["true_rel_res"] <= 2e-15
 
 
 def test_cg_fixed_matches_naive_torch_loop():
