@@ -22,6 +22,9 @@ Function map (paper passage each one follows):
   coo_to_csr        COO ingest of SparseTensor(val, row, col, shape) (App. B)
   grad_values       dL/dA_ij = -lambda_i x_j on the pattern (Eq. 3)
   adjoint_backward  A^T lambda = g, grad_b = lambda, grad_val (Eq. 2-3)
+Modules: ``oracle.mpnn`` (learned factor), ``oracle.inverse`` (Sec. 4.6
+inverse problem), ``oracle.nonlinear`` (Newton solve and its adjoint
+gradient, Sec. 3.2).
 """
 from __future__ import annotations
 

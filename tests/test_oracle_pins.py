@@ -735,3 +735,71 @@ def test_inverse_torch_assembly_matches_oracle_on_cpu():
     vt.backward(torch.tensor(gv))
     ref = OI.chain_theta(th, rp, c, gv)
     assert np.max(np.abs(t.grad.numpy() - ref)) <= 1e-14 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------- nonlinear adjoint (Sec. 3.2)
+
+def _nl_case(N, seed):
+    rng = np.random.default_rng(seed)
+    theta = 0.5 * rng.standard_normal((N, N))
+    f = 1.0 + 0.5 * rng.uniform(-1, 1, N * N)
+    return theta, f
+
+
+def test_nonlinear_newton_manufactured_solution():
+    """f built from a chosen u_e with the dense A(theta): Newton from 0 must
+    return u_e, with quadratic convergence at the end."""
+    from oracle import inverse as OI
+    from oracle import nonlinear as ON
+    N, gamma = 7, 10.0
+    theta, _ = _nl_case(N, 1)
+    rng = np.random.default_rng(2)
+    ue = rng.uniform(0.0, 2.0, N * N)
+    A = OI.dense(*OI.assemble(theta))
+    h2 = 1.0 / (N + 1) ** 2
+    f = (A @ ue) / h2 + gamma * ue ** 3
+    u, hist = ON.newton(theta, f, gamma, tol=1e-14)
+    assert np.linalg.norm(u - ue) <= 1e-12 * np.linalg.norm(ue)
+    assert len(hist) <= 12
+    # quadratic: ||F_{k+1}|| <= C ||F_k||^2 once in the basin
+    k = max(i for i in range(1, len(hist) - 1) if hist[i] > 1e-10 * hist[0]) if len(hist) > 3 else 1
+    assert hist[k + 1] <= 10.0 * hist[k] ** 2 / hist[0] + 1e-13 * hist[0]
+
+
+def test_nonlinear_single_cell_closed_form():
+    """N = 1: A = [4 kappa] (four boundary faces), h^2 = 1/4:
+    4 kappa u + (gamma u^3 - f)/4 = 0 and, by implicit differentiation,
+    du/dtheta = -4 kappa u / (4 kappa + 3 gamma u^2 / 4)."""
+    from oracle import nonlinear as ON
+    for th, gamma, f, ut in ((0.3, 2.0, 5.0, 0.1), (-0.7, 10.0, 3.0, -0.2), (0.0, 0.0, 4.0, 0.0)):
+        theta = np.array([[th]])
+        kap = math.exp(th)
+        roots = np.roots([gamma / 4.0, 0.0, 4.0 * kap, -f / 4.0]) if gamma > 0 else np.array([f / (16 * kap)])
+        u_exact = float(np.real(roots[np.abs(np.imag(roots)) < 1e-12][0]))
+        L, g, u = ON.loss_and_grad(theta, np.array([f]), gamma, np.array([ut]))
+        assert abs(u[0] - u_exact) <= 1e-13 * max(1.0, abs(u_exact))
+        dudt = -4 * kap * u_exact / (4 * kap + 3 * gamma * u_exact ** 2 / 4)
+        assert abs(L - (u_exact - ut) ** 2) <= 1e-14
+        assert abs(g[0, 0] - 2 * (u_exact - ut) * dudt) <= 1e-12 * max(1.0, abs(dudt))
+
+
+def test_nonlinear_adjoint_central_differences():
+    """dL/dtheta from one adjoint solve at u* against central differences
+    of the Newton loss (eps = 1e-5, the paper's FD check, Tab. 5)."""
+    from oracle import nonlinear as ON
+    N, gamma = 6, 10.0
+    theta, f = _nl_case(N, 3)
+    theta_t, _ = _nl_case(N, 4)
+    ut, _ = ON.newton(theta_t, f, gamma, tol=1e-14)
+    L, g, _ = ON.loss_and_grad(theta, f, gamma, ut)
+    rng = np.random.default_rng(5)
+    eps = 1e-5
+    for _ in range(3):
+        d = rng.standard_normal(theta.shape)
+        fd = (ON.loss(theta + eps * d, f, gamma, ut) - ON.loss(theta - eps * d, f, gamma, ut)) / (2 * eps)
+        assert abs(fd - float((g * d).sum())) <= 1e-6 * abs(fd)
+    for (q, p) in ((0, 0), (2, 3), (5, 1)):
+        e = np.zeros_like(theta)
+        e[q, p] = 1.0
+        fd = (ON.loss(theta + eps * e, f, gamma, ut) - ON.loss(theta - eps * e, f, gamma, ut)) / (2 * eps)
+        assert abs(fd - g[q, p]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(g).max())
