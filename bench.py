@@ -392,9 +392,43 @@ def extra_rows(dev, args, peak):
                                    "fp64_tflops": fl / (ms / 1e3) / 1e12,
                                    "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
     out["pipelined_vs_standard"] = pipelined_rows(dev)
+    out["nonlinear_newton_512"] = nonlinear_row(dev)
     out["learned_vs_jacobi"] = learned_vs_jacobi(dev)
     out["inverse_512_16rhs"] = inverse_rows(dev, peak)
     return out
+
+
+def nonlinear_row(dev, N=512):
+    """Sec. 3.2 / Tab. 5 nonlinear path on 512^2 cells: Newton from u = 0 on
+    F = A(theta) u + h^2 (gamma u^3 - f) (gamma = 10, theta a smooth random
+    field), every step's Jacobian from coloured Jacobian-vector products and
+    its solve by Jacobi-PCG (rtol 1e-10), to ||F|| <= 1e-10 ||F(0)||; then the
+    backward pass, one adjoint solve plus one vector-Jacobian product.
+    Median of 3 after one warm-up, CUDA events around forward and backward."""
+    import torch
+
+    from paper_2601_13994_b300 import nonlinear as NL
+    P = NL.SemilinearDiffusion(N=N, device=dev)
+    opts = dict(tol=1e-10, lin_rtol=1e-10)
+    ut = P.target(**opts)
+    fw, bw = [], []
+    for rep in range(4):
+        th = P.theta0.clone().requires_grad_(True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        L = P.loss(th, ut, **opts)
+        e1.record()
+        L.backward()
+        e2.record()
+        e2.synchronize()
+        if rep:
+            fw.append(e0.elapsed_time(e1))
+            bw.append(e1.elapsed_time(e2))
+    info = P.jac.last_info
+    return {"n": P.n, "gamma": P.gamma, "colours": P.jac.ncolours, "newton_iters": info.newton_iters,
+            "krylov_iters": info.krylov_iters, "residual_drop": info.residual_norms[-1] / info.residual_norms[0],
+            "forward_ms": statistics.median(fw), "backward_ms": statistics.median(bw), "loss": float(L.detach()),
+            "backward_over_forward": statistics.median(bw) / statistics.median(fw)}
 
 
 def pipelined_rows(dev):

@@ -477,6 +477,20 @@ int32_t sla_segment_sum(int32_t nseg, const int32_t* segptr,
                         const int32_t* idx, const double* val, double* out,
                         void* stream);
 
+/* Distance-2 colouring of the columns of a CSR pattern, for sparse
+ * Jacobians from Jacobian-vector products (the Newton solves of the
+ * nonlinear adjoint, Sec. 3.2; Curtis-Powell-Reid): columns that share a row
+ * get different colours, so one product per colour, with a tangent of ones
+ * on that colour's columns, yields every entry: J_ij is component i of the
+ * product for colour[j].  Greedy in column order (smallest colour free of
+ * the columns sharing a row).  HOST arrays: rowptr [n+1], col [nnz] (read),
+ * colour [n] (written, values 0 .. *ncolours-1).  SLA_ERR_INVALID for a
+ * malformed pattern (decreasing rowptr, column out of range).  Synchronous;
+ * no device work. */
+int32_t sla_colour_columns(int32_t n, const int32_t* rowptr,
+                           const int32_t* col, int32_t* colour,
+                           int32_t* ncolours);
+
 /* out[k] = val[perm[k]] for k < nnz: the values of A^T in CSR-of-A^T order,
  * or gradients mapped back to the caller's COO order (perm of
  * sla_coo_to_csr).  Device arrays; asynchronous. */

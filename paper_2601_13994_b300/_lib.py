@@ -123,6 +123,8 @@ def lib() -> ctypes.CDLL:
             L.sla_segment_sum.restype = i32
             L.sla_gather_values.argtypes = [i64, P, P, P, P]
             L.sla_gather_values.restype = i32
+            L.sla_colour_columns.argtypes = [i32, P, P, P, ctypes.POINTER(i32)]
+            L.sla_colour_columns.restype = i32
             L.sla_grad_values.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, P]
             L.sla_grad_values.restype = i32
             L.sla_adjoint_backward.argtypes = [ctypes.POINTER(SlaCsr), ctypes.POINTER(SlaCsrT), P, P, P, P,

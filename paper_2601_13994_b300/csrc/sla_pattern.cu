@@ -12,6 +12,8 @@
 // Both are built on a stable LSD radix sort of (uint32 key, uint32 value)
 // pairs and a device-wide exclusive scan, written here; every result is
 // deterministic (integer work, or sums in a fixed order).
+#include <vector>
+
 #include "sla_internal.cuh"
 #include "sla_workspace.h"
 
@@ -480,5 +482,59 @@ extern "C" int32_t sla_coo_to_csr(int32_t n, int64_t m, const int64_t* row, cons
   if (rc != SLA_OK) return rc;
   coo_status_kernel<<<1, 1, 0, s>>>(bad, total, nnz_out, segptr, m);
   SLA_CUDA_TRY(cudaGetLastError());
+  return SLA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Distance-2 column colouring (host).  Two columns that share a row get
+// different colours, so that one Jacobian-vector product per colour -- with
+// the tangent equal to 1 on the colour's columns -- recovers every entry of
+// a sparse Jacobian with this pattern (Curtis, Powell and Reid, 1974): entry
+// (i, j) is component i of the product for colour(j).  Greedy in increasing
+// column order, each column taking the smallest colour that no column
+// sharing a row with it has yet.  O(sum over rows of length^2) work.
+// ---------------------------------------------------------------------------
+extern "C" int32_t sla_colour_columns(int32_t n, const int32_t* rowptr, const int32_t* col,
+                                      int32_t* colour, int32_t* ncolours) {
+  if (n < 0 || ncolours == nullptr) return SLA_ERR_INVALID;
+  *ncolours = 0;
+  if (n == 0) return SLA_OK;
+  if (rowptr == nullptr || colour == nullptr || rowptr[0] != 0) return SLA_ERR_INVALID;
+  for (int32_t i = 0; i < n; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return SLA_ERR_INVALID;
+  const int32_t nnz = rowptr[n];
+  if (nnz > 0 && col == nullptr) return SLA_ERR_INVALID;
+  for (int32_t k = 0; k < nnz; ++k)
+    if (col[k] < 0 || col[k] >= n) return SLA_ERR_INVALID;
+  // rows of each column (the pattern of A^T), by counting sort
+  std::vector<int32_t> cptr((size_t)n + 1, 0), crow((size_t)(nnz > 0 ? nnz : 1));
+  for (int32_t k = 0; k < nnz; ++k) ++cptr[(size_t)col[k] + 1];
+  for (int32_t j = 0; j < n; ++j) cptr[(size_t)j + 1] += cptr[j];
+  {
+    std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+    for (int32_t i = 0; i < n; ++i)
+      for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) crow[(size_t)fill[col[k]]++] = i;
+  }
+  // mark[c] == j + 1: colour c is taken by a column sharing a row with j
+  std::vector<int32_t> mark;
+  int32_t used = 0;
+  for (int32_t j = 0; j < n; ++j) colour[j] = -1;
+  for (int32_t j = 0; j < n; ++j) {
+    for (int32_t q = cptr[j]; q < cptr[(size_t)j + 1]; ++q) {
+      const int32_t i = crow[q];
+      for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+        const int32_t c = colour[col[k]];
+        if (c >= 0) mark[c] = j + 1;
+      }
+    }
+    int32_t c = 0;
+    while (c < used && mark[c] == j + 1) ++c;
+    if (c == used) {
+      ++used;
+      mark.push_back(0);
+    }
+    colour[j] = c;
+  }
+  *ncolours = used;
   return SLA_OK;
 }

@@ -306,6 +306,21 @@ def transpose_of(A: CSRMatrix):
     return t
 
 
+def colour_columns(rowptr, col):
+    """Distance-2 colouring of a CSR pattern's columns (host arrays, the C
+    library's greedy ``sla_colour_columns``): returns (colour int32 [n],
+    number of colours).  Columns that share a row differ in colour."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    c = np.ascontiguousarray(col, dtype=np.int32)
+    n = rp.size - 1
+    colour = np.empty(max(n, 1), dtype=np.int32)
+    k = ctypes.c_int32(0)
+    L.check("sla_colour_columns", L.lib().sla_colour_columns(
+        n, rp.ctypes.data_as(ctypes.c_void_p), c.ctypes.data_as(ctypes.c_void_p) if c.size else None,
+        colour.ctypes.data_as(ctypes.c_void_p), ctypes.byref(k)))
+    return colour[:n], int(k.value)
+
+
 def gather_values(perm: torch.Tensor, val: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
     """out[k] = val[perm[k]]."""
     m = perm.numel()

@@ -6,6 +6,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2601_13994_b300 import _lib as L
@@ -191,3 +192,42 @@ def test_spmv_scheme_rule_and_merge_argument_checks():
     assert lib.sla_spmv_merge(ctypes.byref(A), fake, fake, ctypes.c_void_p(0x2000), None, 0,
                               None) == L.SLA_ERR_WORKSPACE
     assert L.workspace_size(L.SLA_WS_SPMV_MERGE, 10, 20) >= 4 * 256
+
+
+def test_column_colouring_is_a_distance2_colouring():
+    """sla_colour_columns (host): columns sharing a row never share a colour,
+    on the 2D/3D stencils, an FEM pattern and a random pattern with empty
+    rows; the 5-point stencil needs at least 5 colours (a row has 5 columns);
+    malformed patterns are rejected."""
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import sla
+    rng = np.random.default_rng(0)
+    rows = []
+    for i in range(300):
+        k = 0 if i % 17 == 0 else int(rng.integers(1, 12))
+        rows.append(np.unique(rng.integers(0, 300, size=k)))
+    rp_r = np.concatenate([[0], np.cumsum([r.size for r in rows])]).astype(np.int32)
+    c_r = np.concatenate(rows).astype(np.int32)
+    pats = [I.poisson2d(40)[:2], I.diffusion3d_random(9, 1)[:2], I.fem_p1_laplacian(30, 2)[:2], (rp_r, c_r)]
+    for rp, c in pats:
+        colour, k = sla.colour_columns(rp, c)
+        n = len(rp) - 1
+        assert colour.shape == (n,) and colour.min() >= 0 and colour.max() == k - 1
+        maxlen = int(np.diff(rp).max())
+        assert maxlen <= k <= maxlen * maxlen
+        for i in range(n):
+            cs = colour[c[rp[i]:rp[i + 1]]]
+            assert np.unique(cs).size == cs.size
+    assert sla.colour_columns(*I.poisson2d(40)[:2])[1] >= 5
+    assert sla.colour_columns(np.zeros(1, np.int32), np.zeros(0, np.int32))[1] == 0
+    lib = L.lib()
+    k = ctypes.c_int32(0)
+    out = np.empty(2, np.int32)
+    bad_rp = np.array([0, 2, 1], np.int32)
+    bad_c = np.array([0, 1], np.int32)
+    assert lib.sla_colour_columns(2, bad_rp.ctypes.data_as(ctypes.c_void_p), bad_c.ctypes.data_as(ctypes.c_void_p),
+                                  out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(k)) == L.SLA_ERR_INVALID
+    rp2 = np.array([0, 1, 2], np.int32)
+    c2 = np.array([0, 5], np.int32)
+    assert lib.sla_colour_columns(2, rp2.ctypes.data_as(ctypes.c_void_p), c2.ctypes.data_as(ctypes.c_void_p),
+                                  out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(k)) == L.SLA_ERR_INVALID
