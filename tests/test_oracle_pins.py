@@ -803,3 +803,80 @@ def test_nonlinear_adjoint_central_differences():
         e[q, p] = 1.0
         fd = (ON.loss(theta + eps * e, f, gamma, ut) - ON.loss(theta - eps * e, f, gamma, ut)) / (2 * eps)
         assert abs(fd - g[q, p]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(g).max())
+
+
+# ---------------------------------------------------------------- eigenvalue path (Sec. 3.2, Eq. 4)
+
+def _laplacian_1d(n):
+    rp, c, v = [0], [], []
+    for i in range(n):
+        for j, a in ((i - 1, -1.0), (i, 2.0), (i + 1, -1.0)):
+            if 0 <= j < n:
+                c.append(j)
+                v.append(a)
+        rp.append(len(c))
+    return np.array(rp, np.int32), np.array(c, np.int32), np.array(v)
+
+
+def test_eigen_oracle_closed_forms():
+    """1D Laplacian: lambda_j = 4 sin^2(j pi / 2(n+1)), v_j(i) ~ sin(j pi i/(n+1));
+    2D Poisson: the six smallest of 4 sin^2(a pi/2(N+1)) + 4 sin^2(b pi/2(N+1))."""
+    from oracle import eigen as OE
+    n, k = 40, 6
+    rp, c, v = _laplacian_1d(n)
+    lam, V = OE.smallest_eigenpairs(rp, c, v, k)
+    j = np.arange(1, k + 1)
+    assert np.abs(lam - 4 * np.sin(j * np.pi / (2 * (n + 1))) ** 2).max() <= 1e-13
+    i = np.arange(1, n + 1)
+    for q in range(k):
+        ref = np.sin((q + 1) * np.pi * i / (n + 1))
+        ref /= np.linalg.norm(ref)
+        assert abs(abs(ref @ V[:, q]) - 1.0) <= 1e-12
+        assert V[np.argmax(np.abs(V[:, q])), q] > 0
+    N = 12
+    rp, c, v = I.poisson2d(N)
+    lam, _ = OE.smallest_eigenpairs(rp, c, v, k)
+    a = np.arange(1, N + 1)
+    allv = np.sort((4 * np.sin(a[:, None] * np.pi / (2 * (N + 1))) ** 2
+                    + 4 * np.sin(a[None, :] * np.pi / (2 * (N + 1))) ** 2).ravel())
+    assert np.abs(lam - allv[:k]).max() <= 1e-12
+
+
+def test_hellmann_feynman_closed_form_and_central_differences():
+    """Eq. 4: on the 1D Laplacian d lambda_j / d A_ii = v_j(i)^2 =
+    2/(n+1) sin^2(j pi i/(n+1)); on a variable-coefficient system the
+    gradient of L = sum_j w_j lambda_j matches central differences along
+    symmetric perturbations of the stored entries (eps = 1e-5; Tab. 5
+    reports 2.1e-6)."""
+    from oracle import eigen as OE
+    n, k = 30, 4
+    rp, c, v = _laplacian_1d(n)
+    lam, V = OE.smallest_eigenpairs(rp, c, v, k)
+    for q in range(k):
+        g = np.zeros(k)
+        g[q] = 1.0
+        gv = OE.eigenvalue_grad_values(rp, c, V, g)
+        for i in range(n):
+            e = [e for e in range(rp[i], rp[i + 1]) if c[e] == i][0]
+            ref = 2.0 / (n + 1) * np.sin((q + 1) * np.pi * (i + 1) / (n + 1)) ** 2
+            assert abs(gv[e] - ref) <= 1e-13
+    rp, c, v = I.diffusion2d_random(7, 3)
+    k = 6
+    lam, V = OE.smallest_eigenpairs(rp, c, v, k)
+    assert np.diff(lam).min() > 1e-3  # simple eigenvalues
+    w = np.random.default_rng(1).uniform(0.5, 1.5, k)
+    gv = OE.eigenvalue_grad_values(rp, c, V, w)
+    A = OE.dense(rp, c, v)
+    rng = np.random.default_rng(2)
+    eps = 1e-5
+    for _ in range(4):
+        D = np.zeros_like(A)
+        rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+        d = rng.standard_normal(len(v))
+        D[rows, c] = d
+        D = 0.5 * (D + D.T)
+        dv = D[rows, c]
+        lp = np.linalg.eigvalsh(A + eps * D)[:k]
+        lm = np.linalg.eigvalsh(A - eps * D)[:k]
+        fd = float(w @ (lp - lm)) / (2 * eps)
+        assert abs(fd - float(gv @ dv)) <= 1e-6 * abs(fd)
