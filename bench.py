@@ -182,7 +182,21 @@ def _profile_2d_512(dev, max_iter, pipelined):
     return {"iters": info.iters, "status": info.status}
 
 
+def _profile_eigsh(dev, max_iter):
+    """LOBPCG for the 6 smallest eigenpairs of the 2D 128^2 variable-
+    coefficient system (sigma = 1), max_iter iterations."""
+    import torch
+
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import sla
+    rp, c, v = I.diffusion2d_random(128, 11, 1.0)
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    lam, V, info = sla.eigsh(A, torch.from_numpy(v).to(dev), 6, tol=1e-8, max_iter=max_iter, strict=None)
+    return {"iters": info.iters, "status": info.status}
+
+
 PROFILE_ROWS = {
+    "eigsh_2d_128": _profile_eigsh,
     "coop_2d_512": lambda dev, mi: _profile_2d_512(dev, mi, False),
     "pipe_2d_512": lambda dev, mi: _profile_2d_512(dev, mi, True),
     "bicgstab_convdiff3d_128": _profile_bicgstab,
@@ -393,9 +407,31 @@ def extra_rows(dev, args, peak):
                                    "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
     out["pipelined_vs_standard"] = pipelined_rows(dev)
     out["nonlinear_newton_512"] = nonlinear_row(dev)
+    out["eigsh_2d_128_k6"] = eigen_row(dev)
     out["learned_vs_jacobi"] = learned_vs_jacobi(dev)
     out["inverse_512_16rhs"] = inverse_rows(dev, peak)
     return out
+
+
+def eigen_row(dev, N=128, k=6):
+    """Sec. 3.2 / Tab. 5 eigenvalue path: the 6 smallest eigenpairs of the
+    2D 128^2 variable-coefficient system (sigma = 1) by LOBPCG with the
+    Jacobi preconditioner to relative residual 1e-8, then the Hellmann-
+    Feynman gradient of sum(lambda) on the pattern.  Median of 3 after one
+    warm-up (the call synchronises its stream)."""
+    import torch
+
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import sla
+    rp, c, v = I.diffusion2d_random(N, 11, 1.0)
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    vt = torch.from_numpy(v).to(dev)
+    ms, (lam, V, info) = _time(lambda: sla.eigsh(A, vt, k, tol=1e-8))
+    g = torch.ones(k, dtype=torch.float64, device=dev)
+    gms, _ = _time(lambda: sla.eig_grad_values(A, V, g), reps=5)
+    return {"n": len(rp) - 1, "k": k, "s": ms / 1e3, "iters": info.iters, "status": info.status,
+            "us_per_iter": 1e3 * ms / max(info.iters, 1), "true_rel_res": info.true_rel_res,
+            "lambda": [float(x) for x in lam.cpu()], "grad_ms": gms}
 
 
 def nonlinear_row(dev, N=512):

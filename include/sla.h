@@ -86,6 +86,9 @@ extern "C" {
 #define SLA_WS_CG_GGT 7         /* sla_cg_ggt: pass the entry count of G as nnz */
 #define SLA_WS_SPMV_MERGE 9     /* sla_spmv_merge                              */
 #define SLA_WS_CG_PIPELINED 10  /* sla_cg with SLA_FLAG_CG_PIPELINED          */
+#define SLA_WS_EIGSH 11         /* sla_eigsh: batch = k (1..SLA_EIG_MAX_K)     */
+
+#define SLA_EIG_MAX_K 8         /* largest k of sla_eigsh                      */
 #define SLA_WS_CG_MULTI 8       /* sla_cg_multi / sla_adjoint_backward_multi:
                                    batch = number of right-hand sides k       */
 #define SLA_WS_BATCHED 6        /* batched CG: n = rows per system (shared
@@ -496,6 +499,39 @@ int32_t sla_colour_columns(int32_t n, const int32_t* rowptr,
  * sla_coo_to_csr).  Device arrays; asynchronous. */
 int32_t sla_gather_values(int64_t nnz, const int32_t* perm, const double* val,
                           double* out, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Eigenvalues (Sec. 3.2 "Eigenvalue problems", Eq. 4; LOBPCG, Sec. 3.3) */
+/* ------------------------------------------------------------------ */
+
+/* The k smallest eigenpairs of symmetric positive definite A by LOBPCG
+ * (Knyazev 2001) with the Jacobi preconditioner (opts->precond) or none.
+ * k in 1..SLA_EIG_MAX_K, k <= n.  The iteration carries min(k + 2, n)
+ * vectors (two guard vectors, so that a cluster split at the k-th
+ * eigenvalue does not stall the last wanted pair).  opts: rtol = the
+ * convergence tolerance (> 0): stop when ||A x_i - theta_i x_i|| <= rtol
+ * |theta_i| ||x_i|| for the k wanted pairs;
+ * max_iter = iteration cap; use_x0 = 1: V holds the start block [n][k]
+ * (row-major), else a fixed pseudo-random block (splitmix64 of the entry
+ * index); flags must be 0.  Outputs (device): lambda [k] ascending, V [n][k]
+ * row-major with unit columns, *info: iters, status (OK, NOT_CONVERGED,
+ * NOT_SPD for a non-positive diagonal with Jacobi, BREAKDOWN when the
+ * search space loses rank below k), rel_res = the largest relative
+ * residual of the last iteration, true_rel_res = the same from a fresh
+ * product at exit.  Host-driven: three kernels per iteration (SpMM; Gram
+ * sums + Rayleigh-Ritz in the last block; update), the device state read
+ * every 8 iterations; the call synchronises `stream` before returning.
+ * Workspace: sla_workspace_size(SLA_WS_EIGSH, n, nnz, k, &bytes). */
+int32_t sla_eigsh(const sla_csr* A, const double* val, int32_t k,
+                  double* lambda, double* V, const sla_opts* opts,
+                  sla_info* info, void* ws, size_t ws_bytes, void* stream);
+
+/* Hellmann-Feynman gradient of the eigenvalues on the pattern (Eq. 4):
+ * grad_val[e] = sum_i g[i] V[row_e][i] V[col_e][i], with V [n][k] the unit
+ * eigenvectors (row-major) and g [k] = dL/dlambda (device arrays).  Exact
+ * for simple eigenvalues.  Asynchronous on `stream`. */
+int32_t sla_eig_grad_values(const sla_csr* A, int32_t k, const double* V,
+                            const double* g, double* grad_val, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Linear adjoint backward (Eq. 2-3)                                     */

@@ -1,0 +1,819 @@
+// sla_eig.cu -- the k smallest eigenpairs of a symmetric positive definite
+// CSR matrix by LOBPCG (the eigensolver Sec. 3.3 names, Knyazev 2001) with
+// the Jacobi preconditioner, and the Hellmann-Feynman eigenvalue gradient
+// d lambda / d A_ij = v_i v_j on the pattern (Sec. 3.2, Eq. 4).
+//
+// One iteration, with X the current Ritz block (n x kb, X^T X = I), W = D^{-1}
+// R the preconditioned residuals and P the previous search directions:
+//   S = [X W P], AS = [AX AW AP]  (AW = A W is the iteration's SpMM; AX and
+//   AP are carried);
+//   G = S^T S, H = S^T A S over the m active columns (kb, 2kb or 3kb);
+//   Rayleigh-Ritz: the kb smallest eigenpairs (theta, C) of H c = theta G c;
+//   X' = S C, AX' = AS C, P' = S[:, kb:] C[kb:, :], AP' likewise;
+//   R = AX' - X' diag(theta), converged when ||r_i|| <= tol |theta_i| ||x_i||
+//   for the k wanted pairs; W' = D^{-1} R.
+// Soft locking: a pair whose residual has met the tolerance keeps its X
+// column but its W and P columns leave the basis (their rows and columns of
+// G and H are zeroed, so the scaling gives them no weight) -- otherwise the
+// rounding noise of a converged pair's residual, scaled to unit norm,
+// degrades the other pairs (1D Laplacian n = 200, k = 6: the largest
+// residual fell to 2.7e-8 and then rose to 1e-6 without locking).
+// The block carries kb = min(k + 2, n) vectors, two guard vectors beyond
+// the k wanted, so that a cluster of eigenvalues split at the k-th does not
+// stall the last wanted vector (3D 32^3 with lambda_5..7 = 0.0934, 0.0938,
+// 0.0950 and k = 6: without guards LOBPCG took from 551 to more than 3000
+// iterations depending on the start block; with two, 316-458).
+// The Rayleigh-Ritz step is solved robustly without a Cholesky factor: the
+// columns of S are scaled to unit norm, the scaled G is diagonalised, its
+// directions with eigenvalues below 1e-12 of the largest are dropped (near
+// dependence between X, W and P, which grows as the iteration converges),
+// and the projected H is diagonalised -- both small symmetric eigenproblems
+// (m <= 30) by cyclic Jacobi rotations in one thread block, with the
+// round-robin ordering that makes the m/2 rotations of a step independent.
+//
+// Kernels of an iteration: SpMM (A W), Gram (block partial sums of G and H;
+// the last block to arrive adds them in a fixed order and runs the
+// Rayleigh-Ritz step), update (X', P', R, W' and the residual norms; the
+// last block takes the convergence decision).  The host launches them in a
+// loop and reads the device state every few iterations; once the state says
+// done, further launches return at once.  S and AS are row-major [n][3k]
+// and double-buffered (the update reads one pair and writes the other).
+#include <algorithm>
+#include <cmath>
+
+#include "sla_internal.cuh"
+#include "sla_workspace.h"
+
+namespace sla {
+
+constexpr int kEigMaxK = SLA_EIG_MAX_K;          // wanted pairs, at most 8
+constexpr int kEigMaxB = kEigMaxK + 2;           // block with two guard vectors
+constexpr int kEigMaxM = 3 * kEigMaxB;           // 30 columns of S
+constexpr int kEigLd = kEigMaxM + 1;      // leading dimension of the small matrices
+constexpr int kEigThreads = 256;
+constexpr int kEigTile = 32;              // rows of S staged per Gram tile
+constexpr int kEigPairs = kEigMaxM * (kEigMaxM + 1) / 2;
+constexpr int kEigPollEvery = 8;
+
+struct EigDesc {
+  int n, nnz, k, kb, ld, max_iter, precond, use_x0;
+  double tol;
+  const int* rowptr;
+  const int* col;
+  const double* val;
+  double* lambda;
+  double* V;
+  sla_info* info;
+};
+
+struct EigState {
+  int m;      // columns of S in the next Rayleigh-Ritz step
+  int cur;    // which S / AS buffer holds the current block
+  int iters, done, status, rank, bad;
+  unsigned active;  // bit j: pair j not yet converged (its W, P in the basis)
+  double maxres;
+  unsigned ticket_gram, ticket_upd, ticket_fin;
+};
+
+struct EigPtrs {
+  EigDesc* d;
+  EigState* st;
+  double* dinv;
+  double* S[2];
+  double* AS[2];
+  double* gpart;   // [blocks][2 * kEigPairs]
+  double* upart;   // [blocks + 1][2 * kEigMaxB]
+  double* C;       // [kEigMaxM][kEigMaxB]
+  double* theta;   // [kEigMaxM]
+};
+
+size_t eig_ws_bytes(int n, int k, int* gram_blocks, int* upd_blocks);
+
+// Counter-based start block when no initial guess is given: splitmix64 of
+// the entry index, mapped to [-1, 1).
+__device__ __forceinline__ double eig_start_value(unsigned long long idx) {
+  unsigned long long z = idx + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+__global__ void eig_arm_kernel(EigState* st) {
+  st->m = 0;
+  st->cur = 0;
+  st->iters = 0;
+  st->done = 0;
+  st->status = SLA_NOT_CONVERGED;
+  st->rank = 0;
+  st->bad = 0;
+  st->active = 0xffffffffu;
+  st->maxres = NAN;
+  st->ticket_gram = st->ticket_upd = st->ticket_fin = 0u;
+}
+
+// D^{-1} (or ones) and the start block X0 into S[0][:, 0:kb]: the caller's
+// k columns with use_x0, the counter-based values otherwise and for guards.
+__global__ void eig_init_kernel(EigPtrs P) {
+  const EigDesc& d = *P.d;
+  const int n = d.n, k = d.k, kb = d.kb, ld = d.ld;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double di = 1.0;
+    if (d.precond == SLA_PRECOND_JACOBI) {
+      double diag = 0.0;
+      for (int e = d.rowptr[i]; e < d.rowptr[i + 1]; ++e)
+        if (d.col[e] == i) diag += d.val[e];
+      if (!(diag > 0.0)) atomicOr(&P.st->bad, 1);
+      di = 1.0 / diag;
+    }
+    P.dinv[i] = di;
+    double* s = P.S[0] + (size_t)i * ld;
+    for (int j = 0; j < kb; ++j)
+      s[j] = (d.use_x0 && j < k) ? d.V[(size_t)i * k + j] : eig_start_value((unsigned long long)i * kb + j);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) P.st->m = kb;
+}
+
+// Y[:, dst_off + j] = A X[:, src_off + j], j < kb, one row per thread.
+// mode 0: X of S[cur] -> AS[cur] (start); 1: W of S[cur] -> AW in AS[cur];
+// 2: X of S[cur] -> AS[cur ^ 1][:, 0:kb] (the final residual check).
+__global__ void __launch_bounds__(kEigThreads) eig_spmm_kernel(EigPtrs P, int mode) {
+  const EigDesc& d = *P.d;
+  const EigState& st = *P.st;
+  if (mode != 2 && (st.done || st.bad)) return;
+  const int n = d.n, kb = d.kb, ld = d.ld, cur = st.cur;
+  const double* X = P.S[cur] + (mode == 1 ? kb : 0);
+  double* Y = (mode == 2 ? P.AS[cur ^ 1] : P.AS[cur]) + (mode == 1 ? kb : 0);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double acc[kEigMaxB];
+#pragma unroll
+    for (int j = 0; j < kEigMaxB; ++j) acc[j] = 0.0;
+    const int a = __ldg(d.rowptr + i), e = __ldg(d.rowptr + i + 1);
+    for (int q = a; q < e; ++q) {
+      const double v = __ldg(d.val + q);
+      const double* xr = X + (size_t)__ldg(d.col + q) * ld;
+#pragma unroll
+      for (int j = 0; j < kEigMaxB; ++j)
+        if (j < kb) acc[j] = fma(v, xr[j], acc[j]);
+    }
+    double* yr = Y + (size_t)i * ld;
+#pragma unroll
+    for (int j = 0; j < kEigMaxB; ++j)
+      if (j < kb) yr[j] = acc[j];
+  }
+}
+
+// ---------------------------------------------------------------- Rayleigh-Ritz
+
+// Eigen-decomposition of the symmetric m x m matrix A (shared, leading
+// dimension kEigLd) by cyclic Jacobi rotations: on return the diagonal of A
+// holds the eigenvalues and the columns of V the eigenvectors.  Round-robin
+// pairing: in step r of a sweep, position x holds index 0 (x = 0) or
+// 1 + (x - 1 + r) mod (m' - 1), and positions x and m' - 1 - x form a pair,
+// so the m'/2 rotations of a step touch disjoint rows and columns.  A pair
+// is rotated only while |a_pq| > 1e-15 sqrt|a_pp a_qq| (the threshold rule
+// of cyclic Jacobi); the first sweep that rotates nothing ends the solve.
+// (An absolute floor on |a_pq| -- 1e-18 or 1e-16 of the largest diagonal
+// entry of the scaled Gram matrix -- was measured: LOBPCG then stalled at a
+// residual of 1.4e-7 on the 1D Laplacian, n = 200, k = 6.)
+__device__ void eig_jacobi(double* A, double* V, int m, double* rot, int* s_any) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int q = tid; q < m * kEigLd; q += nt) V[q] = 0.0;
+  __syncthreads();
+  for (int q = tid; q < m; q += nt) V[q * kEigLd + q] = 1.0;
+  const int mp = m + (m & 1);
+  const int npair = mp / 2;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    if (tid == 0) *s_any = 0;
+    __syncthreads();
+    for (int r = 0; r < mp - 1; ++r) {
+      if (tid < npair) {
+        const int x1 = tid, x2 = mp - 1 - tid;
+        int p = x1 == 0 ? 0 : 1 + (x1 - 1 + r) % (mp - 1);
+        int q = x2 == 0 ? 0 : 1 + (x2 - 1 + r) % (mp - 1);
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        double c = 1.0, s = 0.0;
+        if (q < m) {
+          const double apq = A[p * kEigLd + q];
+          const double app = A[p * kEigLd + p], aqq = A[q * kEigLd + q];
+          if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && apq != 0.0) {
+            const double th = (aqq - app) / (2.0 * apq);
+            double t;
+            if (fabs(th) > 1e150) t = 0.5 / th;
+            else t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+            *s_any = 1;
+          }
+        }
+        rot[4 * tid] = (double)p;
+        rot[4 * tid + 1] = (double)q;
+        rot[4 * tid + 2] = c;
+        rot[4 * tid + 3] = s;
+      }
+      __syncthreads();
+      // rows p, q of A (A <- J^T A)
+      for (int w = tid; w < npair * m; w += nt) {
+        const int t = w / m, j = w - t * m;
+        const double s = rot[4 * t + 3];
+        if (s == 0.0) continue;
+        const int p = (int)rot[4 * t], q = (int)rot[4 * t + 1];
+        const double c = rot[4 * t + 2];
+        const double ap = A[p * kEigLd + j], aq = A[q * kEigLd + j];
+        A[p * kEigLd + j] = c * ap - s * aq;
+        A[q * kEigLd + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns p, q of A and V (A <- A J, V <- V J)
+      for (int w = tid; w < npair * m; w += nt) {
+        const int t = w / m, i = w - t * m;
+        const double s = rot[4 * t + 3];
+        if (s == 0.0) continue;
+        const int p = (int)rot[4 * t], q = (int)rot[4 * t + 1];
+        const double c = rot[4 * t + 2];
+        const double ap = A[i * kEigLd + p], aq = A[i * kEigLd + q];
+        A[i * kEigLd + p] = c * ap - s * aq;
+        A[i * kEigLd + q] = s * ap + c * aq;
+        const double vp = V[i * kEigLd + p], vq = V[i * kEigLd + q];
+        V[i * kEigLd + p] = c * vp - s * vq;
+        V[i * kEigLd + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    if (*s_any == 0) break;
+    __syncthreads();
+  }
+}
+
+struct EigSmem {
+  double G[kEigMaxM * kEigLd];
+  double H[kEigMaxM * kEigLd];
+  double U[kEigMaxM * kEigLd];
+  double B[kEigMaxM * kEigLd];
+  double T[kEigMaxM * kEigLd];
+  double scale[kEigMaxM];
+  double rot[4 * (kEigMaxM / 2 + 1)];
+  int keep[kEigMaxM];
+  int sel[kEigMaxM];
+  int nkeep;
+  int any;
+};
+
+// Rayleigh-Ritz in one block: G, H (full, shared) -> C [m][k] and theta [k]
+// (k = the block size kb)
+// in global memory; returns the number of kept directions.
+__device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* theta) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int j = tid; j < m; j += nt) {
+    const double g = sm.G[j * kEigLd + j];
+    sm.scale[j] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+  }
+  __syncthreads();
+  for (int q = tid; q < m * m; q += nt) {
+    const int i = q / m, j = q - i * m;
+    const double f = sm.scale[i] * sm.scale[j];
+    sm.G[i * kEigLd + j] *= f;
+    sm.H[i * kEigLd + j] *= f;
+  }
+  __syncthreads();
+  eig_jacobi(sm.G, sm.U, m, sm.rot, &sm.any);  // scaled G = U diag(g) U^T
+  if (tid == 0) {
+    double gmax = 0.0;
+    for (int j = 0; j < m; ++j) gmax = fmax(gmax, sm.G[j * kEigLd + j]);
+    int r = 0;
+    for (int j = 0; j < m; ++j)
+      if (sm.G[j * kEigLd + j] > 1e-12 * gmax) sm.keep[r++] = j;
+    sm.nkeep = r;
+  }
+  __syncthreads();
+  const int r = sm.nkeep;
+  // B = U[:, keep] diag(g)^{-1/2}  (m x r)
+  for (int q = tid; q < m * r; q += nt) {
+    const int i = q / r, j = q - i * r;
+    const int c = sm.keep[j];
+    sm.B[i * kEigLd + j] = sm.U[i * kEigLd + c] / sqrt(sm.G[c * kEigLd + c]);
+  }
+  __syncthreads();
+  // T = H B (m x r), then H2 = B^T T (r x r) into G
+  for (int q = tid; q < m * r; q += nt) {
+    const int i = q / r, j = q - i * r;
+    double s = 0.0;
+    for (int l = 0; l < m; ++l) s = fma(sm.H[i * kEigLd + l], sm.B[l * kEigLd + j], s);
+    sm.T[i * kEigLd + j] = s;
+  }
+  __syncthreads();
+  for (int q = tid; q < r * r; q += nt) {
+    const int i = q / r, j = q - i * r;
+    double s = 0.0;
+    for (int l = 0; l < m; ++l) s = fma(sm.B[l * kEigLd + i], sm.T[l * kEigLd + j], s);
+    sm.G[i * kEigLd + j] = s;
+  }
+  __syncthreads();
+  // symmetrise (rounding), then H2 = Y diag(theta) Y^T with Y in U
+  for (int q = tid; q < r * r; q += nt) {
+    const int i = q / r, j = q - i * r;
+    if (i < j) {
+      const double s = 0.5 * (sm.G[i * kEigLd + j] + sm.G[j * kEigLd + i]);
+      sm.G[i * kEigLd + j] = s;
+      sm.G[j * kEigLd + i] = s;
+    }
+  }
+  __syncthreads();
+  eig_jacobi(sm.G, sm.U, r, sm.rot, &sm.any);
+  if (tid == 0) {
+    // the k smallest Ritz values, ascending (selection by rank; ties by index)
+    for (int i = 0; i < r; ++i) {
+      const double ti = sm.G[i * kEigLd + i];
+      int rank = 0;
+      for (int j = 0; j < r; ++j) {
+        const double tj = sm.G[j * kEigLd + j];
+        if (tj < ti || (tj == ti && j < i)) ++rank;
+      }
+      sm.sel[rank] = i;
+    }
+  }
+  __syncthreads();
+  const int kk = r < k ? r : k;
+  for (int j = tid; j < kk; j += nt) theta[j] = sm.G[sm.sel[j] * kEigLd + sm.sel[j]];
+  // C = diag(scale) B Y[:, sel]  (m x k)
+  for (int q = tid; q < m * kk; q += nt) {
+    const int i = q / kk, j = q - i * kk;
+    const int c = sm.sel[j];
+    double s = 0.0;
+    for (int l = 0; l < r; ++l) s = fma(sm.B[i * kEigLd + l], sm.U[l * kEigLd + c], s);
+    C[i * kEigMaxB + j] = sm.scale[i] * s;
+  }
+  __syncthreads();
+  return r;
+}
+
+// G = S^T S and H = S^T (A S) over the m active columns (upper triangles),
+// per block, then the last block adds all blocks' partials in block order
+// and runs the Rayleigh-Ritz step.
+__global__ void __launch_bounds__(kEigThreads) eig_gram_kernel(EigPtrs P) {
+  const EigDesc& d = *P.d;
+  EigState* st = P.st;
+  if (st->done || st->bad) return;
+  // the row tiles and the Rayleigh-Ritz scratch share the shared memory
+  __shared__ union {
+    struct {
+      double S[kEigTile * kEigMaxM];
+      double A[kEigTile * kEigMaxM];
+    } tile;
+    EigSmem rr;
+  } u;
+  __shared__ bool s_last;
+  double* tS = u.tile.S;
+  double* tA = u.tile.A;
+  EigSmem& sm = u.rr;
+  const int n = d.n, kb = d.kb, ld = d.ld, m = st->m, cur = st->cur;
+  const int npairs = m * (m + 1) / 2;
+  const double* S = P.S[cur];
+  const double* AS = P.AS[cur];
+  const int tid = threadIdx.x;
+  // this thread's pairs (a <= b): t = tid and tid + 256
+  int pa[2] = {0, 0}, pb[2] = {0, 0};
+  for (int h = 0; h < 2; ++h) {
+    const int t = tid + h * kEigThreads;
+    if (t < npairs) {
+      int a = 0, rem = t;
+      while (rem >= m - a) {
+        rem -= m - a;
+        ++a;
+      }
+      pa[h] = a;
+      pb[h] = a + rem;
+    }
+  }
+  double g[2] = {0.0, 0.0}, hh[2] = {0.0, 0.0};
+  const int tiles = (n + kEigTile - 1) / kEigTile;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int r0 = tile * kEigTile;
+    const int rows = min(kEigTile, n - r0);
+    __syncthreads();
+    for (int q = tid; q < rows * m; q += kEigThreads) {
+      const int i = q / m, j = q - i * m;
+      tS[i * kEigMaxM + j] = S[(size_t)(r0 + i) * ld + j];
+      tA[i * kEigMaxM + j] = AS[(size_t)(r0 + i) * ld + j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (tid + h * kEigThreads < npairs) {
+        const int a = pa[h], b = pb[h];
+        for (int i = 0; i < rows; ++i) {
+          const double sa = tS[i * kEigMaxM + a];
+          g[h] = fma(sa, tS[i * kEigMaxM + b], g[h]);
+          hh[h] = fma(sa, tA[i * kEigMaxM + b], hh[h]);
+        }
+      }
+    }
+  }
+  double* mine = P.gpart + (size_t)blockIdx.x * 2 * kEigPairs;
+  for (int h = 0; h < 2; ++h) {
+    const int t = tid + h * kEigThreads;
+    if (t < npairs) {
+      mine[t] = g[h];
+      mine[kEigPairs + t] = hh[h];
+    }
+  }
+  if (!last_block_arrive(&st->ticket_gram, &s_last)) return;
+  const unsigned active = st->active;
+  // fixed-order totals into the full symmetric G and H (the tiles are dead);
+  // the W and P columns of converged pairs are zeroed (soft locking)
+  for (int h = 0; h < 2; ++h) {
+    const int t = tid + h * kEigThreads;
+    if (t < npairs) {
+      double sg = 0.0, sh = 0.0;
+#pragma unroll 8
+      for (int b = 0; b < (int)gridDim.x; ++b) {
+        const double* pb2 = P.gpart + (size_t)b * 2 * kEigPairs;
+        sg += __ldcg(pb2 + t);
+        sh += __ldcg(pb2 + kEigPairs + t);
+      }
+      const int a = pa[h], b = pb[h];
+      const bool la = a >= kb && !((active >> ((a - kb) % kb)) & 1u);
+      const bool lb = b >= kb && !((active >> ((b - kb) % kb)) & 1u);
+      if (la || lb) sg = sh = 0.0;
+      sm.G[a * kEigLd + b] = sg;
+      sm.G[b * kEigLd + a] = sg;
+      sm.H[a * kEigLd + b] = sh;
+      sm.H[b * kEigLd + a] = sh;
+    }
+  }
+  __syncthreads();
+  const int r = eig_rayleigh_ritz(sm, m, kb, P.C, P.theta);
+  if (tid == 0) {
+    st->rank = r;
+    if (r < kb) {
+      st->status = SLA_BREAKDOWN;
+      st->done = 1;
+    }
+  }
+}
+
+// X' = S C, AX' = AS C, P' = S[:, kb:m] C[kb:m], AP' likewise, R = AX' - X'
+// diag(theta), W' = D^{-1} R, into the other buffer pair; per-block sums of
+// ||r_i||^2 and ||x_i||^2; the last block takes the convergence decision on
+// the k wanted pairs.
+__global__ void __launch_bounds__(kEigThreads) eig_update_kernel(EigPtrs P) {
+  const EigDesc& d = *P.d;
+  EigState* st = P.st;
+  if (st->done || st->bad) return;
+  __shared__ double sC[kEigMaxM * kEigMaxB];
+  __shared__ double sT[kEigMaxB];
+  __shared__ double red[2 * kEigMaxB * (kEigThreads / 32)];
+  __shared__ bool s_last;
+  const int n = d.n, k = d.k, kb = d.kb, ld = d.ld, m = st->m, cur = st->cur;
+  const int tid = threadIdx.x;
+  for (int q = tid; q < m * kEigMaxB; q += kEigThreads) sC[q] = P.C[q];
+  if (tid < kb) sT[tid] = P.theta[tid];
+  __syncthreads();
+  const double* S = P.S[cur];
+  const double* AS = P.AS[cur];
+  double* Sn = P.S[cur ^ 1];
+  double* ASn = P.AS[cur ^ 1];
+  double rr[kEigMaxB], xx[kEigMaxB];
+#pragma unroll
+  for (int j = 0; j < kEigMaxB; ++j) rr[j] = xx[j] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + tid; i < n; i += gridDim.x * blockDim.x) {
+    const double* s = S + (size_t)i * ld;
+    const double* as = AS + (size_t)i * ld;
+    double* sn = Sn + (size_t)i * ld;
+    double* asn = ASn + (size_t)i * ld;
+    const double di = P.dinv[i];
+    // two passes over the output columns keep the accumulators in registers
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      constexpr int kH = kEigMaxB / 2;
+      double x[kH], ax[kH], p[kH], ap[kH];
+#pragma unroll
+      for (int j = 0; j < kH; ++j) x[j] = ax[j] = p[j] = ap[j] = 0.0;
+      for (int a = 0; a < m; ++a) {
+        const double sa = s[a], asa = as[a];
+        const double* c = sC + a * kEigMaxB + h * kH;
+        if (a < kb) {
+#pragma unroll
+          for (int j = 0; j < kH; ++j) {
+            x[j] = fma(sa, c[j], x[j]);
+            ax[j] = fma(asa, c[j], ax[j]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < kH; ++j) {
+            p[j] = fma(sa, c[j], p[j]);
+            ap[j] = fma(asa, c[j], ap[j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kH; ++j) {
+        const int jj = h * kH + j;
+        if (jj < kb) {
+          const double xj = x[j] + p[j], axj = ax[j] + ap[j];
+          const double rj = axj - sT[jj] * xj;
+          sn[jj] = xj;
+          asn[jj] = axj;
+          sn[kb + jj] = di * rj;
+          sn[2 * kb + jj] = p[j];
+          asn[2 * kb + jj] = ap[j];
+          rr[jj] = fma(rj, rj, rr[jj]);
+          xx[jj] = fma(xj, xj, xx[jj]);
+        }
+      }
+    }
+  }
+  // block sums of the 2 kb values: warp shuffles, then warp totals in shared
+  const int w = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int j = 0; j < kEigMaxB; ++j) {
+    for (int o = 16; o > 0; o >>= 1) {
+      rr[j] += __shfl_xor_sync(0xffffffffu, rr[j], o);
+      xx[j] += __shfl_xor_sync(0xffffffffu, xx[j], o);
+    }
+    if (lane == 0) {
+      red[(2 * j) * (kEigThreads / 32) + w] = rr[j];
+      red[(2 * j + 1) * (kEigThreads / 32) + w] = xx[j];
+    }
+  }
+  __syncthreads();
+  if (tid < 2 * kb) {
+    double sum = 0.0;
+    for (int q = 0; q < kEigThreads / 32; ++q) sum += red[tid * (kEigThreads / 32) + q];
+    P.upart[(size_t)blockIdx.x * 2 * kEigMaxB + tid] = sum;
+  }
+  if (!last_block_arrive(&st->ticket_upd, &s_last)) return;
+  // one thread per value adds the blocks' partials in block order
+  if (tid < 2 * kb) {
+    double sum = 0.0;
+#pragma unroll 8
+    for (int b = 0; b < (int)gridDim.x; ++b) sum += __ldcg(P.upart + (size_t)b * 2 * kEigMaxB + tid);
+    red[tid] = sum;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double worst = 0.0;
+    bool finite = true;
+    unsigned act = 0u;
+    for (int j = 0; j < kb; ++j) {
+      const double r2 = red[2 * j], x2 = red[2 * j + 1];
+      const double res = sqrt(r2) / (fabs(sT[j]) * sqrt(x2));
+      if (!isfinite(res)) finite = false;
+      if (j < k) worst = fmax(worst, res);
+      if (!(res <= d.tol)) act |= 1u << j;
+    }
+    st->active = act;
+    st->maxres = worst;
+    st->cur = cur ^ 1;
+    if (m > kb) st->iters += 1;
+    st->m = (m == kb) ? 2 * kb : 3 * kb;
+    if (!finite) {
+      st->status = SLA_BREAKDOWN;
+      st->done = 1;
+    } else if (worst <= d.tol) {
+      st->status = SLA_OK;
+      st->done = 1;
+    } else if (st->iters >= d.max_iter) {
+      st->status = SLA_NOT_CONVERGED;
+      st->done = 1;
+    }
+  }
+}
+
+// Final: lambda, the true residuals ||A x_i - theta_i x_i|| / (|theta_i|
+// ||x_i||) of the k wanted pairs from a fresh product (AS[cur ^ 1][:, 0:kb]),
+// the info record, and V = the first k columns of X with unit norm.  Two
+// launches: sums, then the scaled copy.
+__global__ void __launch_bounds__(kEigThreads) eig_final_kernel(EigPtrs P, int phase) {
+  const EigDesc& d = *P.d;
+  EigState* st = P.st;
+  __shared__ double red[2 * kEigMaxK * (kEigThreads / 32)];
+  __shared__ double snorm[kEigMaxK];
+  __shared__ bool s_last;
+  const int n = d.n, k = d.k, ld = d.ld, cur = st->cur;
+  const int tid = threadIdx.x;
+  const double* X = P.S[cur];
+  const double* AX = P.AS[cur ^ 1];
+  if (phase == 1) {
+    if (st->bad) return;
+    if (tid < k) snorm[tid] = P.upart[(size_t)gridDim.x * 2 * kEigMaxB + tid];
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + tid; i < n; i += gridDim.x * blockDim.x)
+      for (int j = 0; j < k; ++j) d.V[(size_t)i * k + j] = X[(size_t)i * ld + j] * snorm[j];
+    return;
+  }
+  double rr[kEigMaxK], xx[kEigMaxK];
+#pragma unroll
+  for (int j = 0; j < kEigMaxK; ++j) rr[j] = xx[j] = 0.0;
+  if (!st->bad) {
+    for (int i = blockIdx.x * blockDim.x + tid; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
+      for (int j = 0; j < kEigMaxK; ++j) {
+        if (j < k) {
+          const double xj = X[(size_t)i * ld + j];
+          const double rj = AX[(size_t)i * ld + j] - P.theta[j] * xj;
+          rr[j] = fma(rj, rj, rr[j]);
+          xx[j] = fma(xj, xj, xx[j]);
+        }
+      }
+    }
+  }
+  const int w = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int j = 0; j < kEigMaxK; ++j) {
+    for (int o = 16; o > 0; o >>= 1) {
+      rr[j] += __shfl_xor_sync(0xffffffffu, rr[j], o);
+      xx[j] += __shfl_xor_sync(0xffffffffu, xx[j], o);
+    }
+    if (lane == 0) {
+      red[(2 * j) * (kEigThreads / 32) + w] = rr[j];
+      red[(2 * j + 1) * (kEigThreads / 32) + w] = xx[j];
+    }
+  }
+  __syncthreads();
+  if (tid < 2 * k) {
+    double sum = 0.0;
+    for (int q = 0; q < kEigThreads / 32; ++q) sum += red[tid * (kEigThreads / 32) + q];
+    P.upart[(size_t)blockIdx.x * 2 * kEigMaxB + tid] = sum;
+  }
+  if (!last_block_arrive(&st->ticket_fin, &s_last)) return;
+  if (tid < 2 * k) {
+    double sum = 0.0;
+#pragma unroll 8
+    for (int b = 0; b < (int)gridDim.x; ++b) sum += __ldcg(P.upart + (size_t)b * 2 * kEigMaxB + tid);
+    red[tid] = sum;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    sla_info inf;
+    inf.iters = st->iters;
+    if (st->bad) {
+      inf.status = SLA_NOT_SPD;
+      inf.rel_res = NAN;
+      inf.true_rel_res = NAN;
+    } else {
+      double worst = 0.0;
+      for (int j = 0; j < k; ++j) {
+        const double r2 = red[2 * j], x2 = red[2 * j + 1];
+        const double nx = sqrt(x2);
+        worst = fmax(worst, sqrt(r2) / (fabs(P.theta[j]) * nx));
+        // 1 / ||x_j|| for the copy, after the partials
+        P.upart[(size_t)gridDim.x * 2 * kEigMaxB + j] = 1.0 / nx;
+        d.lambda[j] = P.theta[j];
+      }
+      inf.status = st->status;
+      inf.rel_res = st->maxres;
+      inf.true_rel_res = worst;
+    }
+    *d.info = inf;
+  }
+}
+
+// Hellmann-Feynman gradient (Eq. 4): out[e] = sum_i g_i V[row_e][i]
+// V[col_e][i], one row per thread.
+__global__ void eig_grad_kernel(int n, int k, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                const double* __restrict__ V, const double* __restrict__ g,
+                                double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double w[kEigMaxK];
+#pragma unroll
+    for (int j = 0; j < kEigMaxK; ++j) w[j] = j < k ? __ldg(g + j) * __ldg(V + (size_t)i * k + j) : 0.0;
+    for (int e = __ldg(rowptr + i); e < __ldg(rowptr + i + 1); ++e) {
+      const double* vc = V + (size_t)__ldg(col + e) * k;
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < kEigMaxK; ++j)
+        if (j < k) s = fma(w[j], __ldg(vc + j), s);
+      out[e] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host
+
+namespace {
+int eig_grid(int n, int cap) {
+  const long long b = ((long long)n + kEigThreads - 1) / kEigThreads;
+  return (int)std::max(1LL, std::min<long long>(b, cap));
+}
+}  // namespace
+
+// Block size of a k-pair solve: two guard vectors, at most n.
+int eig_block(int n, int k) { return std::min(k + 2, std::max(n, k)); }
+
+size_t eig_ws_bytes(int n, int k, int* gram_blocks, int* upd_blocks) {
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  const int gb = std::max(1, std::min((n + kEigTile - 1) / kEigTile, 296));
+  const int ub = eig_grid(n, 1024);
+  if (gram_blocks) *gram_blocks = gb;
+  if (upd_blocks) *upd_blocks = ub;
+  size_t o = 0;
+  o += al256(sizeof(EigDesc));
+  o += al256(sizeof(EigState));
+  o += al256(sizeof(double) * nn);                     // dinv
+  const size_t kb = (size_t)eig_block(n, k);
+  o += 4 * al256(sizeof(double) * nn * 3 * kb);         // S[2], AS[2]
+  o += al256(sizeof(double) * (size_t)gb * 2 * kEigPairs);
+  o += al256(sizeof(double) * ((size_t)ub + 1) * 2 * kEigMaxB);
+  o += al256(sizeof(double) * kEigMaxM * kEigMaxB);
+  o += al256(sizeof(double) * kEigMaxM);
+  return o;
+}
+
+}  // namespace sla
+
+using namespace sla;
+
+extern "C" int32_t sla_eigsh(const sla_csr* A, const double* val, int32_t k, double* lambda, double* V,
+                             const sla_opts* opts, sla_info* info, void* ws, size_t ws_bytes, void* stream) {
+  if (A == nullptr || opts == nullptr || info == nullptr) return SLA_ERR_INVALID;
+  const int n = A->n;
+  if (n < 1 || k < 1 || k > kEigMaxK || k > n) return SLA_ERR_INVALID;
+  if (A->nnz < 0 || A->rowptr == nullptr || (A->nnz > 0 && (A->col == nullptr || val == nullptr)))
+    return SLA_ERR_INVALID;
+  if (lambda == nullptr || V == nullptr) return SLA_ERR_INVALID;
+  if (!(opts->rtol > 0.0) || opts->max_iter < 0 || (opts->use_x0 != 0 && opts->use_x0 != 1) ||
+      (opts->precond != SLA_PRECOND_NONE && opts->precond != SLA_PRECOND_JACOBI) || opts->flags != 0)
+    return SLA_ERR_INVALID;
+  int gb = 0, ub = 0;
+  const size_t need = eig_ws_bytes(n, k, &gb, &ub);
+  if (ws == nullptr || ((uintptr_t)ws & 255u) != 0 || ws_bytes < need) return SLA_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  // carve the workspace (the order of eig_ws_bytes)
+  const size_t nn = (size_t)n;
+  const int kb = eig_block(n, k);
+  char* p = (char*)ws;
+  EigPtrs P;
+  P.d = (EigDesc*)p;           p += al256(sizeof(EigDesc));
+  P.st = (EigState*)p;         p += al256(sizeof(EigState));
+  P.dinv = (double*)p;         p += al256(sizeof(double) * nn);
+  for (int b = 0; b < 2; ++b) {
+    P.S[b] = (double*)p;       p += al256(sizeof(double) * nn * 3 * (size_t)kb);
+    P.AS[b] = (double*)p;      p += al256(sizeof(double) * nn * 3 * (size_t)kb);
+  }
+  P.gpart = (double*)p;        p += al256(sizeof(double) * (size_t)gb * 2 * kEigPairs);
+  P.upart = (double*)p;        p += al256(sizeof(double) * ((size_t)ub + 1) * 2 * kEigMaxB);
+  P.C = (double*)p;            p += al256(sizeof(double) * kEigMaxM * kEigMaxB);
+  P.theta = (double*)p;
+  EigDesc d = {};
+  d.n = n;
+  d.nnz = A->nnz;
+  d.k = k;
+  d.kb = kb;
+  d.ld = 3 * kb;
+  d.max_iter = opts->max_iter;
+  d.precond = opts->precond;
+  d.use_x0 = opts->use_x0;
+  d.tol = opts->rtol;
+  d.rowptr = A->rowptr;
+  d.col = A->col;
+  d.val = val;
+  d.lambda = lambda;
+  d.V = V;
+  d.info = info;
+  SLA_CUDA_TRY(cudaMemcpyAsync(P.d, &d, sizeof(d), cudaMemcpyHostToDevice, s));
+  eig_arm_kernel<<<1, 1, 0, s>>>(P.st);
+  eig_init_kernel<<<eig_grid(n, 1024), kEigThreads, 0, s>>>(P);
+  // start: Rayleigh-Ritz on X0 alone, then W = D^{-1} R
+  eig_spmm_kernel<<<eig_grid(n, 4096), kEigThreads, 0, s>>>(P, 0);
+  eig_gram_kernel<<<gb, kEigThreads, 0, s>>>(P);
+  eig_update_kernel<<<ub, kEigThreads, 0, s>>>(P);
+  SLA_CUDA_TRY(cudaGetLastError());
+  for (long long it = 0; it < (long long)opts->max_iter; ++it) {
+    eig_spmm_kernel<<<eig_grid(n, 4096), kEigThreads, 0, s>>>(P, 1);
+    eig_gram_kernel<<<gb, kEigThreads, 0, s>>>(P);
+    eig_update_kernel<<<ub, kEigThreads, 0, s>>>(P);
+    if ((it + 1) % kEigPollEvery == 0) {
+      int done = 0;
+      SLA_CUDA_TRY(cudaMemcpyAsync(&done, &P.st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SLA_CUDA_TRY(cudaStreamSynchronize(s));
+      if (done) break;
+      int bad = 0;
+      SLA_CUDA_TRY(cudaMemcpyAsync(&bad, &P.st->bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SLA_CUDA_TRY(cudaStreamSynchronize(s));
+      if (bad) break;
+    }
+  }
+  eig_spmm_kernel<<<eig_grid(n, 4096), kEigThreads, 0, s>>>(P, 2);
+  eig_final_kernel<<<ub, kEigThreads, 0, s>>>(P, 0);
+  eig_final_kernel<<<ub, kEigThreads, 0, s>>>(P, 1);
+  SLA_CUDA_TRY(cudaGetLastError());
+  SLA_CUDA_TRY(cudaStreamSynchronize(s));
+  return SLA_OK;
+}
+
+extern "C" int32_t sla_eig_grad_values(const sla_csr* A, int32_t k, const double* V, const double* g,
+                                       double* grad_val, void* stream) {
+  if (A == nullptr || k < 1 || k > kEigMaxK || A->n < 0 || A->nnz < 0) return SLA_ERR_INVALID;
+  if (A->n == 0 || A->nnz == 0) return SLA_OK;
+  if (A->rowptr == nullptr || A->col == nullptr || V == nullptr || g == nullptr || grad_val == nullptr)
+    return SLA_ERR_INVALID;
+  eig_grad_kernel<<<eig_grid(A->n, 4096), kEigThreads, 0, (cudaStream_t)stream>>>(A->n, k, A->rowptr, A->col,
+                                                                                  V, g, grad_val);
+  SLA_CUDA_TRY(cudaGetLastError());
+  return SLA_OK;
+}

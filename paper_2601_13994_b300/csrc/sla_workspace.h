@@ -144,6 +144,9 @@ constexpr GgtLayout ggt_layout(int n, int nnz_g) {
 // Several right-hand sides sharing one matrix (sla_multi.cu).
 size_t multi_ws_bytes(int n, int k);
 
+// LOBPCG (sla_eig.cu): k = block size; optional outputs: grid sizes.
+size_t eig_ws_bytes(int n, int k, int* gram_blocks, int* upd_blocks);
+
 // Merge-path SpMV carries (sla_spmv_merge.cu).
 size_t spmv_merge_ws_bytes(int n, long long nnz);
 
@@ -169,6 +172,10 @@ inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
       return true;
     case SLA_WS_CG_PIPELINED:
       *out = cg_pipe_layout(n).total;
+      return true;
+    case SLA_WS_EIGSH:
+      if (batch < 1 || batch > SLA_EIG_MAX_K) return false;
+      *out = eig_ws_bytes(n, batch, nullptr, nullptr);
       return true;
     case SLA_WS_BICGSTAB:
       *out = bicg_layout(n).total;

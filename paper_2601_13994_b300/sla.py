@@ -415,6 +415,76 @@ class SolveError(RuntimeError):
     pass
 
 
+# ---------------------------------------------------------------------------
+# Eigenvalues (Sec. 3.2 "Eigenvalue problems", Eq. 4)
+# ---------------------------------------------------------------------------
+
+def eig_grad_values(A: CSRMatrix, V: torch.Tensor, g: torch.Tensor) -> torch.Tensor:
+    """Hellmann-Feynman gradient on the pattern (Eq. 4): out[e] = sum_i
+    g_i V[row_e, i] V[col_e, i]; V [n, k] unit eigenvectors, g [k]."""
+    k = V.shape[1]
+    _need(V, torch.float64, A.device, "V", A.n * k)
+    _need(g, torch.float64, A.device, "g", k)
+    out = torch.empty(A.nnz, dtype=torch.float64, device=A.device)
+    L.check("sla_eig_grad_values", L.lib().sla_eig_grad_values(
+        ctypes.byref(A.c), k, V.data_ptr(), g.data_ptr(), out.data_ptr(), _stream_ptr(A.device)))
+    return out
+
+
+class _Eigsh(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, val, A, k, opts, box):
+        _need(val, torch.float64, A.device, "val", A.nnz)
+        lam = torch.empty(k, dtype=torch.float64, device=A.device)
+        V = torch.empty((A.n, k), dtype=torch.float64, device=A.device)
+        use_x0 = 0
+        if opts["v0"] is not None:
+            _need(opts["v0"], torch.float64, A.device, "v0", A.n * k)
+            V.copy_(opts["v0"].reshape(A.n, k))
+            use_x0 = 1
+        mi = opts["max_iter"] if opts["max_iter"] is not None else 20000
+        o = L.SlaOpts(float(opts["tol"]), 0.0, int(mi), 0, _PRECOND[opts["precond"]], use_x0, 0)
+        info = torch.empty((1, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
+        ws = workspace(L.SLA_WS_EIGSH, A.n, A.nnz, k, A.device)
+        L.check("sla_eigsh", L.lib().sla_eigsh(ctypes.byref(A.c), val.detach().data_ptr(), k, lam.data_ptr(),
+                                               V.data_ptr(), ctypes.byref(o), info.data_ptr(), ws.data_ptr(),
+                                               ws.numel(), _stream_ptr(A.device)))
+        box["info"] = SolveInfo(info)
+        ctx.A = A
+        ctx.save_for_backward(V)
+        ctx.mark_non_differentiable(V)
+        return lam, V
+
+    @staticmethod
+    def backward(ctx, glam, gV):
+        (V,) = ctx.saved_tensors
+        if gV is not None and bool(gV.abs().max() > 0):
+            raise NotImplementedError("eigenvector gradients are not provided: the eigenvalue path "
+                                      "differentiates the eigenvalues (Hellmann-Feynman, Eq. 4)")
+        gval = eig_grad_values(ctx.A, V, glam.contiguous().to(torch.float64))
+        return gval, None, None, None, None
+
+
+def eigsh(A: CSRMatrix, val: torch.Tensor, k: int = 6, *, tol: float = 1e-8, max_iter: int | None = None,
+          precond: str = "jacobi", v0: torch.Tensor | None = None, strict: bool | None = True):
+    """The k smallest eigenpairs of SPD A by LOBPCG (Sec. 3.3; Knyazev 2001)
+    with the Jacobi preconditioner.  Returns (lambda [k] ascending,
+    V [n, k] unit columns, SolveInfo).  lambda is differentiable w.r.t. val
+    by the Hellmann-Feynman gradient v_i v_j on the pattern (Eq. 4; simple
+    eigenvalues); V carries no gradient.  strict=True raises on a failed
+    solve, False warns, None skips the check."""
+    if not 1 <= k <= L.SLA_EIG_MAX_K:
+        raise ValueError("k must be in 1..%d" % L.SLA_EIG_MAX_K)
+    if precond not in _PRECOND:
+        raise ValueError("precond must be one of %s" % sorted(_PRECOND))
+    box = {}
+    lam, V = _Eigsh.apply(val, A, int(k), {"tol": tol, "max_iter": max_iter, "precond": precond, "v0": v0}, box)
+    info = box["info"]
+    if strict is not None:
+        _check_info(info, "eigsh", strict)
+    return lam, V, info
+
+
 def _check_info(info: SolveInfo, what: str, strict: bool):
     if info.status != L.SLA_OK:
         msg = "%s: %s after %d iterations (rel_res %.3e)" % (what, info.status_name, info.iters, info.rel_res)
@@ -498,6 +568,11 @@ class SparseTensor:
 
     def matvec(self, x: torch.Tensor) -> torch.Tensor:
         return spmv(self.A, self.csr_values().detach(), x.contiguous())
+
+    def eigsh(self, k: int = 6, **kw):
+        """The k smallest eigenpairs (LOBPCG); eigenvalues differentiable
+        w.r.t. the COO values (Eq. 4)."""
+        return eigsh(self.A, self.csr_values(), k, **kw)
 
 
 # ---------------------------------------------------------------------------

@@ -231,3 +231,31 @@ def test_column_colouring_is_a_distance2_colouring():
     c2 = np.array([0, 5], np.int32)
     assert lib.sla_colour_columns(2, rp2.ctypes.data_as(ctypes.c_void_p), c2.ctypes.data_as(ctypes.c_void_p),
                                   out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(k)) == L.SLA_ERR_INVALID
+
+
+def test_eigsh_arguments_rejected_without_launch():
+    """sla_eigsh / sla_eig_grad_values argument checks (before any launch)."""
+    lib = L.lib()
+    fake = ctypes.c_void_p(0x1000)
+    ws = ctypes.c_void_p(0x100000)
+    n = 100
+    A = L.SlaCsr(n, 300, fake, fake)
+    need = L.workspace_size(L.SLA_WS_EIGSH, n, 300, 6)
+    assert need >= 4 * 8 * n * 18
+    with pytest.raises(L.SlaError):
+        L.workspace_size(L.SLA_WS_EIGSH, n, 300, 9)
+    ok = L.SlaOpts(1e-8, 0.0, 100, 0, 1, 0, 0)
+    out = ctypes.c_void_p(0x2000)
+    for k in (0, 9, n + 1):
+        assert lib.sla_eigsh(ctypes.byref(A), fake, k, out, out, ctypes.byref(ok), fake, ws, need,
+                             None) == L.SLA_ERR_INVALID
+    for bad in (L.SlaOpts(0.0, 0.0, 100, 0, 1, 0, 0), L.SlaOpts(1e-8, 0.0, -1, 0, 1, 0, 0),
+                L.SlaOpts(1e-8, 0.0, 100, 0, 2, 0, 0), L.SlaOpts(1e-8, 0.0, 100, 0, 1, 0, 1)):
+        assert lib.sla_eigsh(ctypes.byref(A), fake, 6, out, out, ctypes.byref(bad), fake, ws, need,
+                             None) == L.SLA_ERR_INVALID
+    assert lib.sla_eigsh(ctypes.byref(A), fake, 6, out, out, ctypes.byref(ok), fake, ws, need - 256,
+                         None) == L.SLA_ERR_WORKSPACE
+    assert lib.sla_eigsh(ctypes.byref(A), fake, 6, None, out, ctypes.byref(ok), fake, ws, need,
+                         None) == L.SLA_ERR_INVALID
+    assert lib.sla_eig_grad_values(ctypes.byref(A), 0, fake, fake, fake, None) == L.SLA_ERR_INVALID
+    assert lib.sla_eig_grad_values(ctypes.byref(A), 9, fake, fake, fake, None) == L.SLA_ERR_INVALID
