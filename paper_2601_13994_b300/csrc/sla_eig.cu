@@ -166,79 +166,105 @@ __global__ void __launch_bounds__(kEigThreads) eig_spmm_kernel(EigPtrs P, int mo
 // ---------------------------------------------------------------- Rayleigh-Ritz
 
 // Eigen-decomposition of the symmetric m x m matrix A (shared, leading
-// dimension kEigLd) by cyclic Jacobi rotations: on return the diagonal of A
-// holds the eigenvalues and the columns of V the eigenvectors.  Round-robin
-// pairing: in step r of a sweep, position x holds index 0 (x = 0) or
-// 1 + (x - 1 + r) mod (m' - 1), and positions x and m' - 1 - x form a pair,
-// so the m'/2 rotations of a step touch disjoint rows and columns.  A pair
-// is rotated only while |a_pq| > 1e-15 sqrt|a_pp a_qq| (the threshold rule
-// of cyclic Jacobi); the first sweep that rotates nothing ends the solve.
-// (An absolute floor on |a_pq| -- 1e-18 or 1e-16 of the largest diagonal
-// entry of the scaled Gram matrix -- was measured: LOBPCG then stalled at a
+// dimension kEigLd) by cyclic Jacobi rotations in precision T: on return the
+// diagonal of A holds the eigenvalues and the columns of V the eigenvectors.
+// Round-robin pairing: in step r of a sweep, position x holds index 0
+// (x = 0) or 1 + (x - 1 + r) mod (m' - 1), and positions x and m' - 1 - x
+// form a pair, so the m'/2 rotations of a step touch disjoint rows and
+// columns.  A pair is rotated only while |a_pq| > rel sqrt|a_pp a_qq| (the
+// threshold rule of cyclic Jacobi) and |a_pq| > floor_rel max_j |a_jj|; the
+// first sweep that rotates nothing, or sweep max_sweeps, ends the solve.
+// (In FP64 no floor is used: an absolute floor of 1e-18 or 1e-16 of the
+// largest diagonal entry of the scaled Gram matrix made LOBPCG stall at a
 // residual of 1.4e-7 on the 1D Laplacian, n = 200, k = 6.)
-__device__ void eig_jacobi(double* A, double* V, int m, double* rot, int* s_any) {
+template <class T>
+__device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps, T* rot, int* s_any,
+                           T* s_floor) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int q = tid; q < m * kEigLd; q += nt) V[q] = 0.0;
+  for (int q = tid; q < m * kEigLd; q += nt) V[q] = T(0);
   __syncthreads();
-  for (int q = tid; q < m; q += nt) V[q * kEigLd + q] = 1.0;
+  for (int q = tid; q < m; q += nt) V[q * kEigLd + q] = T(1);
+  if (tid == 0) {
+    T dmax = T(0);
+    for (int j = 0; j < m; ++j) dmax = fmax(dmax, fabs(A[j * kEigLd + j]));
+    *s_floor = floor_rel * dmax;
+  }
+  __syncthreads();
+  const T floor_abs = *s_floor;
   const int mp = m + (m & 1);
   const int npair = mp / 2;
-  for (int sweep = 0; sweep < 30; ++sweep) {
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (tid == 0) *s_any = 0;
     __syncthreads();
     for (int r = 0; r < mp - 1; ++r) {
       if (tid < npair) {
         const int x1 = tid, x2 = mp - 1 - tid;
-        int p = x1 == 0 ? 0 : 1 + (x1 - 1 + r) % (mp - 1);
-        int q = x2 == 0 ? 0 : 1 + (x2 - 1 + r) % (mp - 1);
+        // 1 + (x - 1 + r) mod (m' - 1) without a division (x - 1 + r < 2 (m' - 1))
+        int p = x1 - 1 + r, q = x2 - 1 + r;
+        if (p >= mp - 1) p -= mp - 1;
+        if (q >= mp - 1) q -= mp - 1;
+        p = x1 == 0 ? 0 : 1 + p;
+        q = x2 == 0 ? 0 : 1 + q;
         if (p > q) {
           const int t = p;
           p = q;
           q = t;
         }
-        double c = 1.0, s = 0.0;
+        T c = T(1), s = T(0);
         if (q < m) {
-          const double apq = A[p * kEigLd + q];
-          const double app = A[p * kEigLd + p], aqq = A[q * kEigLd + q];
-          if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && apq != 0.0) {
-            const double th = (aqq - app) / (2.0 * apq);
-            double t;
-            if (fabs(th) > 1e150) t = 0.5 / th;
-            else t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
+          const T apq = A[p * kEigLd + q];
+          const T app = A[p * kEigLd + p], aqq = A[q * kEigLd + q];
+          // |a_pq| > rel sqrt|a_pp a_qq| without the square root; then, with
+          // d = a_qq - a_pp and e = 2 a_pq, tan = sgn(d e) |e| / (|d| +
+          // sqrt(d^2 + e^2)) (the smaller root of t^2 + 2 (d/e) t - 1 = 0),
+          // cos = 1 / sqrt(1 + tan^2): one square root, one division, one
+          // reciprocal square root -- the rotation is on every step's
+          // critical path
+          if (apq * apq > rel * rel * fabs(app * aqq) && fabs(apq) > floor_abs) {
+            const T d = aqq - app, e = T(2) * apq;
+            const T ad = fabs(d), ae = fabs(e);
+            const T big = fmax(ad, ae), small = fmin(ad, ae);
+            const T rr = small / big;
+            const T hyp = big * sqrt(T(1) + rr * rr);
+            T t = ae / (ad + hyp);
+            if ((d < T(0)) != (e < T(0))) t = -t;
+            c = rsqrt(T(1) + t * t);
             s = t * c;
             *s_any = 1;
           }
         }
-        rot[4 * tid] = (double)p;
-        rot[4 * tid + 1] = (double)q;
+        rot[4 * tid] = (T)p;
+        rot[4 * tid + 1] = (T)q;
         rot[4 * tid + 2] = c;
         rot[4 * tid + 3] = s;
       }
       __syncthreads();
-      // rows p, q of A (A <- J^T A)
-      for (int w = tid; w < npair * m; w += nt) {
-        const int t = w / m, j = w - t * m;
-        const double s = rot[4 * t + 3];
-        if (s == 0.0) continue;
+      // rows p, q of A (A <- J^T A): a warp per pair, a lane per column
+      // (m <= 30 < 32; no integer division, which runs on the slow
+      // special-function pipe)
+      const int wp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+      for (int t = wp; t < npair; t += nw) {
+        const T s = rot[4 * t + 3];
+        if (s == T(0) || lane >= m) continue;
         const int p = (int)rot[4 * t], q = (int)rot[4 * t + 1];
-        const double c = rot[4 * t + 2];
-        const double ap = A[p * kEigLd + j], aq = A[q * kEigLd + j];
+        const T c = rot[4 * t + 2];
+        const int j = lane;
+        const T ap = A[p * kEigLd + j], aq = A[q * kEigLd + j];
         A[p * kEigLd + j] = c * ap - s * aq;
         A[q * kEigLd + j] = s * ap + c * aq;
       }
       __syncthreads();
       // columns p, q of A and V (A <- A J, V <- V J)
-      for (int w = tid; w < npair * m; w += nt) {
-        const int t = w / m, i = w - t * m;
-        const double s = rot[4 * t + 3];
-        if (s == 0.0) continue;
+      for (int t = wp; t < npair; t += nw) {
+        const int i = lane;
+        const T s = rot[4 * t + 3];
+        if (s == T(0) || i >= m) continue;
         const int p = (int)rot[4 * t], q = (int)rot[4 * t + 1];
-        const double c = rot[4 * t + 2];
-        const double ap = A[i * kEigLd + p], aq = A[i * kEigLd + q];
+        const T c = rot[4 * t + 2];
+        const T ap = A[i * kEigLd + p], aq = A[i * kEigLd + q];
         A[i * kEigLd + p] = c * ap - s * aq;
         A[i * kEigLd + q] = s * ap + c * aq;
-        const double vp = V[i * kEigLd + p], vq = V[i * kEigLd + q];
+        const T vp = V[i * kEigLd + p], vq = V[i * kEigLd + q];
         V[i * kEigLd + p] = c * vp - s * vq;
         V[i * kEigLd + q] = s * vp + c * vq;
       }
@@ -249,6 +275,25 @@ __device__ void eig_jacobi(double* A, double* V, int m, double* rot, int* s_any)
   }
 }
 
+// Y = op(X) Z for m x m shared matrices (op = transpose when tx), all
+// threads of the block: a warp per output row, a lane per column; Y must not
+// alias X or Z.
+__device__ void eig_matmul(double* Y, const double* X, const double* Z, int m, bool tx) {
+  const int j = threadIdx.x & 31;
+  if (j < m) {
+    for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5) {
+      double s = 0.0;
+      if (tx) {
+        for (int l = 0; l < m; ++l) s = fma(X[l * kEigLd + i], Z[l * kEigLd + j], s);
+      } else {
+        for (int l = 0; l < m; ++l) s = fma(X[i * kEigLd + l], Z[l * kEigLd + j], s);
+      }
+      Y[i * kEigLd + j] = s;
+    }
+  }
+  __syncthreads();
+}
+
 struct EigSmem {
   double G[kEigMaxM * kEigLd];
   double H[kEigMaxM * kEigLd];
@@ -257,11 +302,57 @@ struct EigSmem {
   double T[kEigMaxM * kEigLd];
   double scale[kEigMaxM];
   double rot[4 * (kEigMaxM / 2 + 1)];
+  float Af[kEigMaxM * kEigLd];
+  float Vf[kEigMaxM * kEigLd];
+  float rotf[4 * (kEigMaxM / 2 + 1)];
   int keep[kEigMaxM];
   int sel[kEigMaxM];
   int nkeep;
   int any;
+  double floor_d;
+  float floor_f;
 };
+
+// Mixed-precision symmetric eigensolver for the Rayleigh-Ritz step: FP32
+// Jacobi sweeps (the FP32 pipe is 64 times the FP64 one) to a basis V0 that
+// nearly diagonalises A; two steps of symmetric orthogonalisation in FP64,
+// V <- V (3I - V^T V)/2, each squaring V0's loss of orthogonality (~1e-7);
+// the congruence A1 = V^T A V, nearly diagonal; FP64 Jacobi sweeps on A1,
+// which converge quadratically from there (two or three); the eigenvectors
+// V V1.  A (overwritten with its eigenvalues on the diagonal) and V as in
+// eig_jacobi; S1, S2: m x m scratch.
+__device__ void eig_eigh(double* A, double* V, int m, double* S1, double* S2, EigSmem& sm) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int q = tid; q < m * kEigLd; q += nt) sm.Af[q] = (float)A[q];
+  __syncthreads();
+  eig_jacobi<float>(sm.Af, sm.Vf, m, 1e-7f, 1e-9f, 12, sm.rotf, &sm.any, &sm.floor_f);
+  for (int q = tid; q < m * kEigLd; q += nt) S1[q] = (double)sm.Vf[q];
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    eig_matmul(S2, S1, S1, m, true);  // M = V^T V
+    for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
+      for (int j = threadIdx.x & 31; j < m; j += 32) {
+      S2[i * kEigLd + j] = (i == j ? 1.5 : 0.0) - 0.5 * S2[i * kEigLd + j];
+    }
+    __syncthreads();
+    eig_matmul(V, S1, S2, m, false);  // V (3I - M) / 2
+    for (int q = tid; q < m * kEigLd; q += nt) S1[q] = V[q];
+    __syncthreads();
+  }
+  eig_matmul(S2, A, S1, m, false);  // A V
+  eig_matmul(A, S1, S2, m, true);   // V^T A V
+  for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
+    for (int j = threadIdx.x & 31; j < m; j += 32) {
+    if (i < j) {
+      const double x = 0.5 * (A[i * kEigLd + j] + A[j * kEigLd + i]);
+      A[i * kEigLd + j] = x;
+      A[j * kEigLd + i] = x;
+    }
+  }
+  __syncthreads();
+  eig_jacobi<double>(A, S2, m, 1e-15, 0.0, 30, sm.rot, &sm.any, &sm.floor_d);
+  eig_matmul(V, S1, S2, m, false);  // V0 V1
+}
 
 // Rayleigh-Ritz in one block: G, H (full, shared) -> C [m][k] and theta [k]
 // (k = the block size kb)
@@ -273,14 +364,14 @@ __device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* t
     sm.scale[j] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
   }
   __syncthreads();
-  for (int q = tid; q < m * m; q += nt) {
-    const int i = q / m, j = q - i * m;
+  for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
+    for (int j = threadIdx.x & 31; j < m; j += 32) {
     const double f = sm.scale[i] * sm.scale[j];
     sm.G[i * kEigLd + j] *= f;
     sm.H[i * kEigLd + j] *= f;
   }
   __syncthreads();
-  eig_jacobi(sm.G, sm.U, m, sm.rot, &sm.any);  // scaled G = U diag(g) U^T
+  eig_eigh(sm.G, sm.U, m, sm.B, sm.T, sm);  // scaled G = U diag(g) U^T
   if (tid == 0) {
     double gmax = 0.0;
     for (int j = 0; j < m; ++j) gmax = fmax(gmax, sm.G[j * kEigLd + j]);
@@ -292,30 +383,30 @@ __device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* t
   __syncthreads();
   const int r = sm.nkeep;
   // B = U[:, keep] diag(g)^{-1/2}  (m x r)
-  for (int q = tid; q < m * r; q += nt) {
-    const int i = q / r, j = q - i * r;
+  for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
+    for (int j = threadIdx.x & 31; j < r; j += 32) {
     const int c = sm.keep[j];
     sm.B[i * kEigLd + j] = sm.U[i * kEigLd + c] / sqrt(sm.G[c * kEigLd + c]);
   }
   __syncthreads();
   // T = H B (m x r), then H2 = B^T T (r x r) into G
-  for (int q = tid; q < m * r; q += nt) {
-    const int i = q / r, j = q - i * r;
+  for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
+    for (int j = threadIdx.x & 31; j < r; j += 32) {
     double s = 0.0;
     for (int l = 0; l < m; ++l) s = fma(sm.H[i * kEigLd + l], sm.B[l * kEigLd + j], s);
     sm.T[i * kEigLd + j] = s;
   }
   __syncthreads();
-  for (int q = tid; q < r * r; q += nt) {
-    const int i = q / r, j = q - i * r;
+  for (int i = threadIdx.x >> 5; i < r; i += blockDim.x >> 5)
+    for (int j = threadIdx.x & 31; j < r; j += 32) {
     double s = 0.0;
     for (int l = 0; l < m; ++l) s = fma(sm.B[l * kEigLd + i], sm.T[l * kEigLd + j], s);
     sm.G[i * kEigLd + j] = s;
   }
   __syncthreads();
   // symmetrise (rounding), then H2 = Y diag(theta) Y^T with Y in U
-  for (int q = tid; q < r * r; q += nt) {
-    const int i = q / r, j = q - i * r;
+  for (int i = threadIdx.x >> 5; i < r; i += blockDim.x >> 5)
+    for (int j = threadIdx.x & 31; j < r; j += 32) {
     if (i < j) {
       const double s = 0.5 * (sm.G[i * kEigLd + j] + sm.G[j * kEigLd + i]);
       sm.G[i * kEigLd + j] = s;
@@ -323,7 +414,7 @@ __device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* t
     }
   }
   __syncthreads();
-  eig_jacobi(sm.G, sm.U, r, sm.rot, &sm.any);
+  eig_eigh(sm.G, sm.U, r, sm.H, sm.T, sm);
   if (tid == 0) {
     // the k smallest Ritz values, ascending (selection by rank; ties by index)
     for (int i = 0; i < r; ++i) {
@@ -340,8 +431,8 @@ __device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* t
   const int kk = r < k ? r : k;
   for (int j = tid; j < kk; j += nt) theta[j] = sm.G[sm.sel[j] * kEigLd + sm.sel[j]];
   // C = diag(scale) B Y[:, sel]  (m x k)
-  for (int q = tid; q < m * kk; q += nt) {
-    const int i = q / kk, j = q - i * kk;
+  for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
+    for (int j = threadIdx.x & 31; j < kk; j += 32) {
     const int c = sm.sel[j];
     double s = 0.0;
     for (int l = 0; l < r; ++l) s = fma(sm.B[i * kEigLd + l], sm.U[l * kEigLd + c], s);
@@ -395,8 +486,8 @@ __global__ void __launch_bounds__(kEigThreads) eig_gram_kernel(EigPtrs P) {
     const int r0 = tile * kEigTile;
     const int rows = min(kEigTile, n - r0);
     __syncthreads();
-    for (int q = tid; q < rows * m; q += kEigThreads) {
-      const int i = q / m, j = q - i * m;
+    for (int i = threadIdx.x >> 5; i < rows; i += blockDim.x >> 5)
+      for (int j = threadIdx.x & 31; j < m; j += 32) {
       tS[i * kEigMaxM + j] = S[(size_t)(r0 + i) * ld + j];
       tA[i * kEigMaxM + j] = AS[(size_t)(r0 + i) * ld + j];
     }
