@@ -353,7 +353,9 @@ def extra_rows(dev, args, peak):
     vt = torch.from_numpy(v).to(dev)
     bt = torch.from_numpy(I.rhs_uniform(n, 5)).to(dev)
     ms, (x, info) = _time(lambda: sla.bicgstab(A, vt, bt, rtol=1e-8))
-    bpi = 2 * (12 * nnz + 4 * (n + 1)) + 200 * n
+    # two SpMVs with A D^{-1} + 20 vector streams a row (p: r, p, v, p; v = A p: p,
+    # r^, v; s: r, v, s; t = A s: s, s, t; x: x^, p, s, t, r^, x^, r)
+    bpi = 2 * (12 * nnz + 4 * (n + 1)) + 160 * n
     gbs = bpi * info.iters / (ms / 1e3) / 1e9
     out["bicgstab_convdiff3d_128_pe10"] = {"s": ms / 1e3, "iters": info.iters, "status": info.status,
                                            "gbs": gbs, "frac_of_measured_hbm": gbs / peak,

@@ -127,7 +127,7 @@ extern "C" int32_t sla_adjoint_backward(const sla_csr* A, const sla_csr_t* AT, c
                                                                  AT->perm_t == nullptr)))
       return SLA_ERR_INVALID;
     // valT in the workspace, after the BiCGStab scratch
-    const size_t off = al256(bicg_layout(n).total);
+    const size_t off = bicg_ws_bytes(n, nnz);
     double* valT = (double*)((char*)ws + off);
     rc = launch_gather_values(nnz, AT->perm_t, val, valT, s);
     if (rc != SLA_OK) return rc;

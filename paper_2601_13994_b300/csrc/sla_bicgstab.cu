@@ -39,7 +39,14 @@ struct BiPtrs {
   KrylovState* st;
   double* part;
   double *r, *rh, *p, *ph, *v, *s, *sh, *t, *dinv;
+  double* valh;  // A D^{-1}: the values with each column scaled by D^{-1}
 };
+
+// The matrix the iteration multiplies: A D^{-1} with the Jacobi
+// preconditioner (x in the iteration is then x^ = D x), A itself without.
+__device__ __forceinline__ const double* bicg_vals(const BiPtrs& P, const KrylovDesc& d) {
+  return d.precond == SLA_PRECOND_JACOBI ? P.valh : d.val;
+}
 
 struct VSmem {
   double red[4 * kVT + 4];
@@ -128,6 +135,29 @@ __global__ void __launch_bounds__(kVT) bicg_init_kernel(BiPtrs P) {
   }
 }
 
+// Right preconditioning folded into the matrix: A^ = A D^{-1} (each column j
+// scaled by dinv_j) and x^ = D x, so that the iteration needs neither p^ =
+// D^{-1} p nor s^ = D^{-1} s -- two vectors and two products a row fewer
+// (BiCGStab on A^ with x = D^{-1} x^ is right-preconditioned BiCGStab).
+// After bicg_init_kernel (which needs every dinv and the caller's x).
+__global__ void __launch_bounds__(kVT) bicg_scale_kernel(BiPtrs P) {
+  const KrylovDesc d = *P.d;
+  if (d.precond != SLA_PRECOND_JACOBI || __ldcg(&P.st->bad_diag)) return;
+  const int n = d.n;
+  for (int i = blockIdx.x * kVT + threadIdx.x; i < n; i += gridDim.x * kVT) {
+    for (int k = __ldg(d.rowptr + i); k < __ldg(d.rowptr + i + 1); ++k)
+      P.valh[k] = __ldg(d.val + k) * __ldg(P.dinv + __ldg(d.col + k));
+    d.x[i] = d.x[i] / P.dinv[i];
+  }
+}
+
+// x = D^{-1} x^ at exit (after the final residual, which gathers x^).
+__global__ void __launch_bounds__(kVT) bicg_unscale_kernel(BiPtrs P) {
+  const KrylovDesc d = *P.d;
+  if (d.precond != SLA_PRECOND_JACOBI || __ldcg(&P.st->bad_diag) || __ldcg(&P.st->zero_rhs)) return;
+  for (int i = blockIdx.x * kVT + threadIdx.x; i < d.n; i += gridDim.x * kVT) d.x[i] *= P.dinv[i];
+}
+
 // -------------------------------------------------------------- KA
 __global__ void __launch_bounds__(kVT) bicg_p_kernel(BiPtrs P) {
   if (__ldcg(&P.st->phase) != kPhaseRun) return;
@@ -135,7 +165,7 @@ __global__ void __launch_bounds__(kVT) bicg_p_kernel(BiPtrs P) {
   const double beta = __ldcg(&P.st->beta), omega = __ldcg(&P.st->omega);
   const int stride = gridDim.x * kVT;
   for (int i0 = blockIdx.x * kVT + threadIdx.x; i0 < n; i0 += kU * stride) {
-    double ri[kU], pi[kU], vi[kU], di[kU];
+    double ri[kU], pi[kU], vi[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int i = i0 + u * stride;
@@ -143,36 +173,32 @@ __global__ void __launch_bounds__(kVT) bicg_p_kernel(BiPtrs P) {
         ri[u] = __ldg(P.r + i);
         pi[u] = P.p[i];
         vi[u] = __ldg(P.v + i);
-        di[u] = __ldg(P.dinv + i);
       }
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int i = i0 + u * stride;
-      if (i < n) {
-        const double pn = fma(beta, fma(-omega, vi[u], pi[u]), ri[u]);
-        P.p[i] = pn;
-        P.ph[i] = di[u] * pn;
-      }
+      if (i < n) P.p[i] = fma(beta, fma(-omega, vi[u], pi[u]), ri[u]);
     }
   }
 }
 
 // -------------------------------------------------------------- KB / KD
-// which == 0: v = A p^, partial r^.v ;  which == 1: t = A s^, partials t.t, t.s
+// which == 0: v = A^ p, partial r^.v ;  which == 1: t = A^ s, partials t.t, t.s
+// (A^ = A D^{-1}; r^ here is the shadow residual r0, not a preconditioned vector)
 // run(x, aux, epi) performs y = A x through one of the SpMV schemes.
 template <int which, int NT, int M, class Run>
 __device__ __forceinline__ void bicg_spmv_body(const BiPtrs& P, double (&red)[M], bool* s_last, Run&& run) {
   double a0 = 0.0, a1 = 0.0;
   if (which == 0) {
     double* __restrict__ v = P.v;
-    run(P.ph, P.rh, [&](int row, double y, double rhr) {
+    run(P.p, P.rh, [&](int row, double y, double rhr) {
       v[row] = y;
       a0 = fma(rhr, y, a0);
     });
   } else {
     double* __restrict__ t = P.t;
-    run(P.sh, P.s, [&](int row, double y, double sr) {
+    run(P.s, P.s, [&](int row, double y, double sr) {
       t[row] = y;
       a0 = fma(y, y, a0);
       a1 = fma(y, sr, a1);
@@ -220,7 +246,7 @@ __global__ void __launch_bounds__(tma::kThreads, 3) bicg_spmv_tma_kernel(BiPtrs 
   if (__ldcg(&P.st->phase) != kPhaseRun) return;
   const KrylovDesc d = *P.d;
   bicg_spmv_body<which, tma::kThreads>(P, sm.red, &sm.last, [&](const double* x, const double* aux, auto&& epi) {
-    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, x, aux, sm, &P.st->err, epi);
+    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, bicg_vals(P, d), x, aux, sm, &P.st->err, epi);
   });
 }
 
@@ -231,7 +257,7 @@ __global__ void __launch_bounds__(kRowThreads) bicg_spmv_rows_kernel(BiPtrs P) {
   if (__ldcg(&P.st->phase) != kPhaseRun) return;
   const KrylovDesc d = *P.d;
   bicg_spmv_body<which, kRowThreads>(P, red, &s_last, [&](const double* x, const double* aux, auto&& epi) {
-    csr_rows(d.n, d.rowptr, d.col, d.val, x, aux, epi);
+    csr_rows(d.n, d.rowptr, d.col, bicg_vals(P, d), x, aux, epi);
   });
 }
 
@@ -244,14 +270,13 @@ __global__ void __launch_bounds__(kVT) bicg_s_kernel(BiPtrs P) {
   const int stride = gridDim.x * kVT;
   double ss0 = 0.0, ss1 = 0.0;
   for (int i0 = blockIdx.x * kVT + threadIdx.x; i0 < n; i0 += kU * stride) {
-    double ri[kU], vi[kU], di[kU];
+    double ri[kU], vi[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int i = i0 + u * stride;
       if (i < n) {
         ri[u] = __ldg(P.r + i);
         vi[u] = __ldg(P.v + i);
-        di[u] = __ldg(P.dinv + i);
       }
     }
 #pragma unroll
@@ -260,7 +285,6 @@ __global__ void __launch_bounds__(kVT) bicg_s_kernel(BiPtrs P) {
       if (i < n) {
         const double sn = fma(-alpha, vi[u], ri[u]);
         P.s[i] = sn;
-        P.sh[i] = di[u] * sn;
         if (u & 1) ss1 = fma(sn, sn, ss1);
         else ss0 = fma(sn, sn, ss0);
       }
@@ -275,7 +299,7 @@ __global__ void __launch_bounds__(kVT) bicg_s_kernel(BiPtrs P) {
     KrylovState& s = *P.st;
     s.iters += 1;
     s.ss = acc[0];
-    if (sqrt(acc[0]) <= s.thresh) {  // half-step exit: x += alpha p^ in KE
+    if (sqrt(acc[0]) <= s.thresh) {  // half-step exit: x^ += alpha p in KE
       s.rr = acc[0];
       s.status = SLA_OK;
       s.phase = kPhaseHalf;
@@ -296,14 +320,13 @@ bicg_x_kernel(BiPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
     const double alpha = __ldcg(&P.st->alpha), omega = __ldcg(&P.st->omega);
     double rr1 = 0.0, rh1 = 0.0;
     for (int i0 = blockIdx.x * kVT + threadIdx.x; i0 < n; i0 += kU * stride) {
-      double xi[kU], phi[kU], shi[kU], si[kU], ti[kU], rhi[kU];
+      double xi[kU], phi[kU], si[kU], ti[kU], rhi[kU];
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
         const int i = i0 + u * stride;
         if (i < n) {
           xi[u] = d.x[i];
-          phi[u] = __ldg(P.ph + i);
-          shi[u] = __ldg(P.sh + i);
+          phi[u] = __ldg(P.p + i);
           si[u] = __ldg(P.s + i);
           ti[u] = __ldg(P.t + i);
           rhi[u] = __ldg(P.rh + i);
@@ -313,7 +336,7 @@ bicg_x_kernel(BiPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
       for (int u = 0; u < kU; ++u) {
         const int i = i0 + u * stride;
         if (i < n) {
-          d.x[i] = fma(omega, shi[u], fma(alpha, phi[u], xi[u]));
+          d.x[i] = fma(omega, si[u], fma(alpha, phi[u], xi[u]));
           const double rn = fma(-omega, ti[u], si[u]);
           P.r[i] = rn;
           if (u & 1) {
@@ -331,10 +354,10 @@ bicg_x_kernel(BiPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
   } else if (phase == kPhaseHalf) {
     const double alpha = __ldcg(&P.st->alpha);
     for (int i = blockIdx.x * kVT + threadIdx.x; i < n; i += stride)
-      d.x[i] = fma(alpha, __ldg(P.ph + i), d.x[i]);
+      d.x[i] = fma(alpha, __ldg(P.p + i), d.x[i]);
   } else if (phase == kPhaseCheck) {
     for (int i = blockIdx.x * kVT + threadIdx.x; i < n; i += stride) {
-      const double ti = d.b[i] - row_dot(d.rowptr, d.col, d.val, d.x, i);
+      const double ti = d.b[i] - row_dot(d.rowptr, d.col, bicg_vals(P, d), d.x, i);
       P.r[i] = ti;
       P.rh[i] = ti;
       P.p[i] = 0.0;
@@ -430,7 +453,7 @@ __global__ void __launch_bounds__(kVT) bicg_final_kernel(BiPtrs P) {
     if (zero_rhs) {
       d.x[i] = 0.0;
     } else if (!bad) {
-      const double ti = d.b[i] - row_dot(d.rowptr, d.col, d.val, d.x, i);
+      const double ti = d.b[i] - row_dot(d.rowptr, d.col, bicg_vals(P, d), d.x, i);
       acc[0] = fma(ti, ti, acc[0]);
     }
   }
@@ -511,17 +534,18 @@ int build_graph(BiPtrs P, const SpmvKernels& k, int gs, int gv, cudaGraphExec_t*
   do {
     cudaGraphConditionalHandle h;
     if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
-    cudaGraphNode_t n_init, n_while, na, nb, nc, nd, ne, n_final;
+    cudaGraphNode_t n_init, n_scale, n_while, na, nb, nc, nd, ne, n_final, n_unscale;
     void* a[] = {&P};
     int use_cond = 1;
     void* ae[] = {&P, &h, &use_cond};
     if (add_kernel(g, nullptr, 0, &n_init, (const void*)bicg_init_kernel, gv, kVT, a) != cudaSuccess) break;
+    if (add_kernel(g, &n_init, 1, &n_scale, (const void*)bicg_scale_kernel, gv, kVT, a) != cudaSuccess) break;
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    if (cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp) != cudaSuccess) break;
+    if (cudaGraphAddNode(&n_while, g, &n_scale, nullptr, 1, &cp) != cudaSuccess) break;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     if (add_kernel(body, nullptr, 0, &na, (const void*)bicg_p_kernel, gv, kVT, a) != cudaSuccess) break;
     if (add_kernel(body, &na, 1, &nb, k.kb, gs, k.threads, a, k.smem) != cudaSuccess) break;
@@ -529,6 +553,8 @@ int build_graph(BiPtrs P, const SpmvKernels& k, int gs, int gv, cudaGraphExec_t*
     if (add_kernel(body, &nc, 1, &nd, k.kd, gs, k.threads, a, k.smem) != cudaSuccess) break;
     if (add_kernel(body, &nd, 1, &ne, (const void*)bicg_x_kernel, gv, kVT, ae) != cudaSuccess) break;
     if (add_kernel(g, &n_while, 1, &n_final, (const void*)bicg_final_kernel, gv, kVT, a) != cudaSuccess) break;
+    if (add_kernel(g, &n_final, 1, &n_unscale, (const void*)bicg_unscale_kernel, gv, kVT, a) != cudaSuccess)
+      break;
     if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) break;
     rc = SLA_OK;
   } while (0);
@@ -540,6 +566,7 @@ int run_host_loop(BiPtrs P, const KrylovDesc& desc, const SpmvKernels& k, int gs
   void* a[] = {&P};
   bicg_write_desc_kernel<<<1, 1, 0, s>>>(P.d, desc, P.st);
   bicg_init_kernel<<<gv, kVT, 0, s>>>(P);
+  bicg_scale_kernel<<<gv, kVT, 0, s>>>(P);
   const long long cap = 2LL * desc.max_iter + 3LL * desc.max_restarts + 8;
   for (long long body = 0; body < cap; ++body) {
     bicg_p_kernel<<<gv, kVT, 0, s>>>(P);
@@ -555,6 +582,7 @@ int run_host_loop(BiPtrs P, const KrylovDesc& desc, const SpmvKernels& k, int gs
     }
   }
   bicg_final_kernel<<<gv, kVT, 0, s>>>(P);
+  bicg_unscale_kernel<<<gv, kVT, 0, s>>>(P);
   SLA_CUDA_TRY(cudaGetLastError());
   SLA_CUDA_TRY(cudaStreamSynchronize(s));
   return SLA_OK;
@@ -582,6 +610,7 @@ int launch_bicgstab(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags)
   for (int j = 0; j < 9; ++j) vecs[j] = (double*)(base + L.vec + (size_t)j * L.vec_stride);
   P.r = vecs[0]; P.rh = vecs[1]; P.p = vecs[2]; P.ph = vecs[3]; P.v = vecs[4];
   P.s = vecs[5]; P.sh = vecs[6]; P.t = vecs[7]; P.dinv = vecs[8];
+  P.valh = (double*)(base + al256(L.total));
   const int dev = current_device();
   int gs, gv;
   const SpmvKernels sk = spmv_kernels(desc.n);
@@ -638,7 +667,7 @@ extern "C" int32_t sla_bicgstab(const sla_csr* A, const double* val, const doubl
                                 const sla_opts* opts, sla_info* info, void* ws, size_t ws_bytes,
                                 void* stream) {
   if (A == nullptr) return SLA_ERR_INVALID;
-  const size_t need = bicg_layout(A->n > 0 ? A->n : 0).total;
+  const size_t need = bicg_ws_bytes(A->n > 0 ? A->n : 0, A->nnz > 0 ? A->nnz : 0);
   int rc = validate_solve_args(A, val, b, x, opts, info, ws, ws_bytes, need);
   if (rc != SLA_OK) return rc;
   if (opts->precond != SLA_PRECOND_NONE && opts->precond != SLA_PRECOND_JACOBI) return SLA_ERR_INVALID;

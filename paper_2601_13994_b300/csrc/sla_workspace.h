@@ -114,6 +114,11 @@ constexpr BiLayout bicg_layout(int n) {
   return L;
 }
 
+// BiCGStab scratch: the layout above, then A D^{-1} (nnz doubles).
+inline size_t bicg_ws_bytes(int n, int nnz) {
+  return al256(bicg_layout(n).total) + al256(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+}
+
 // Batched solves (sla_batched.cu); argument = total rows of the batch.
 size_t batched_ws_bytes(long long total_rows);
 
@@ -159,7 +164,7 @@ size_t coo_ws_bytes(int n, long long m);
 inline size_t adjoint_ws_bytes(int n, int nnz) {
   const size_t a0 = cg_layout(n).total, a1 = cg_pipe_layout(n).total;
   const size_t a = a0 > a1 ? a0 : a1;
-  const size_t b = al256(bicg_layout(n).total) + al256(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  const size_t b = bicg_ws_bytes(n, nnz) + al256(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
   return a > b ? a : b;
 }
 
@@ -178,7 +183,7 @@ inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
       *out = eig_ws_bytes(n, batch, nullptr, nullptr);
       return true;
     case SLA_WS_BICGSTAB:
-      *out = bicg_layout(n).total;
+      *out = bicg_ws_bytes(n, nnz);
       return true;
     case SLA_WS_ADJOINT:
       *out = adjoint_ws_bytes(n, nnz);
