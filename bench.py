@@ -34,10 +34,11 @@ sys.path.insert(0, ROOT)
 METRIC = "PCG time to rel-res 1e-8 & SpMV GB/s vs 8 TB/s; learned vs Jacobi-PCG speedup"
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6400.0
-# DRAM bytes (read + write) of one PCG iteration at 256^3, summed over the
-# three kernels of one ncu --set full capture (profiles/pcg_iteration_diffusion3d_256.md);
-# valid only for these kernels and this size.
-TRAFFIC_PER_ITER_256 = 3.130e9  # ncu dram__bytes_read+write of K1+K2+K3, one iteration (profiles/)
+# DRAM bytes (read + write) of one PCG iteration, scaled to 256^3: the three
+# kernels (K1 TMA SpMV, K2, K3 of CG on D^-1/2 A D^-1/2) captured by ncu at 176^3
+# (the capture size rule) and scaled by rows (profiles/pcg_iteration_diffusion3d_256.md);
+# valid only for these kernels.
+TRAFFIC_PER_ITER_256 = 2.828e9  # 918,981,632 B at 176^3 x (256/176)^3
 FP64_PEAK_TFLOPS = 1.203  # 2 DFMA/clk/SM (ncu peak_sustained) x 148 SMs x 2 flop x 2.032 GHz
 
 
@@ -218,9 +219,11 @@ def workload(N: int):
 
 
 def bytes_per_iter(n: int, nnz: int) -> int:
-    """Algorithmic bytes of one fused Jacobi-PCG iteration (int32 CSR, FP64):
-    12 nnz + 4 (n+1) for the matrix, 13 n-vectors of 8 bytes."""
-    return 12 * nnz + 4 * (n + 1) + 104 * n
+    """Algorithmic bytes of one Jacobi-PCG iteration as the per-phase kernels
+    run it (int32 CSR, FP64; CG on D^-1/2 A D^-1/2): 12 nnz + 4 (n+1) for the
+    matrix, 12 n-vector streams of 8 bytes (K1: p, q; K2: x rw, r rw, p, q,
+    diag; K3: r, p rw)."""
+    return 12 * nnz + 4 * (n + 1) + 96 * n
 
 
 def flops_per_iter(n: int, nnz: int) -> int:

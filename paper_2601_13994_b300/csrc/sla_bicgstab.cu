@@ -656,6 +656,7 @@ KrylovDesc make_desc(const sla_csr* A, const double* val, const double* b, doubl
   d.max_restarts = o->max_restarts;
   d.precond = o->precond;
   d.use_x0 = o->use_x0;
+  d.sym_scale = o->precond == SLA_PRECOND_JACOBI ? 1 : 0;  // read by the CG kernels only
   return d;
 }
 

@@ -18,8 +18,16 @@
 // workspace, so the instantiated graph depends only on the workspace address
 // and the sizes and is cached.
 //
+// With the Jacobi preconditioner the kernels run CG on the symmetrically
+// scaled system A^ = D^{-1/2} A D^{-1/2}, x^ = D^{1/2} x, b^ = D^{-1/2} b (its
+// values written once per solve): the iterates are those of Jacobi PCG (r^ =
+// D^{-1/2} r, p^ = D^{1/2} p, r^.r^ = r.z), but z = D^{-1} r is never formed,
+// and the stopping test keeps ||r||^2 = sum_i d_i r^_i^2.
+//
 // Algorithmic bytes per iteration (int32 CSR, FP64): 12 nnz + 4 (n+1)
-// + 104 n  (K1: p, q; K2: x rw, r rw, p, q, dinv, z w; K3: z, p rw).
+// + 96 n  (K1: p, q; K2: x rw, r rw, p, q, diag; K3: r, p rw); without the
+// scaling (no preconditioner, or the allocation-free entry) + 104 n (K2 reads
+// dinv and writes z, K3 reads z).
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -40,8 +48,14 @@ struct CgPtrs {
   double* z;
   double* p;
   double* q;
-  double* dinv;
+  double* dinv;  // D^{-1}; with sym_scale the diagonal d itself
+  double* ahat;  // values of D^{-1/2} A D^{-1/2} (sym_scale)
 };
+
+// sym_scale: z holds s = d^{-1/2}.
+__device__ __forceinline__ const double* cg_vals(const CgPtrs& P, const KrylovDesc& d) {
+  return d.sym_scale ? P.ahat : d.val;
+}
 
 // Writes the per-call descriptor and zeroes the ticket counters, so that a
 // workspace whose memory held anything before still starts every solve with
@@ -83,6 +97,20 @@ __global__ void __launch_bounds__(kVecThreads) cg_init_kernel(CgPtrs P) {
     }
     const double bi = d.b[i];
     const double ri = bi - ax;
+    acc[0] = fma(bi, bi, acc[0]);
+    acc[1] = fma(ri, ri, acc[1]);
+    if (d.sym_scale) {
+      // r^ = s r with s = d^{-1/2}; p^ = r^; r.z = r^.r^
+      if (!(diag > 0.0)) acc[3] = 1.0;
+      const double si = rsqrt(diag);
+      const double rh = si * ri;
+      P.dinv[i] = diag;
+      P.z[i] = si;
+      P.r[i] = rh;
+      P.p[i] = rh;
+      acc[2] = fma(rh, rh, acc[2]);
+      continue;
+    }
     double di = 1.0;
     if (d.precond == SLA_PRECOND_JACOBI) {
       if (!(diag > 0.0)) acc[3] = 1.0;
@@ -93,8 +121,6 @@ __global__ void __launch_bounds__(kVecThreads) cg_init_kernel(CgPtrs P) {
     P.r[i] = ri;
     P.z[i] = zi;
     P.p[i] = zi;
-    acc[0] = fma(bi, bi, acc[0]);
-    acc[1] = fma(ri, ri, acc[1]);
     acc[2] = fma(ri, zi, acc[2]);
   }
   if (!d.use_x0) {
@@ -139,6 +165,28 @@ __global__ void __launch_bounds__(kVecThreads) cg_init_kernel(CgPtrs P) {
       s.phase = kPhaseDone;
     }
   }
+}
+
+// sym_scale: A^ = D^{-1/2} A D^{-1/2} (a_ij s_i s_j) and x^ = D^{1/2} x =
+// x d s.  After cg_init_kernel (which needs every s and the caller's x).
+__global__ void __launch_bounds__(kVecThreads) cg_scale_kernel(CgPtrs P) {
+  const KrylovDesc d = *P.d;
+  if (!d.sym_scale || __ldcg(&P.st->bad_diag)) return;
+  const double* __restrict__ sv = P.z;
+  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < d.n; i += gridDim.x * kVecThreads) {
+    const double si = sv[i];
+    for (int k = __ldg(d.rowptr + i); k < __ldg(d.rowptr + i + 1); ++k)
+      P.ahat[k] = __ldg(d.val + k) * si * sv[__ldg(d.col + k)];
+    d.x[i] = d.x[i] * (P.dinv[i] * si);
+  }
+}
+
+// sym_scale: x = D^{-1/2} x^ at exit, before the final residual.
+__global__ void __launch_bounds__(kVecThreads) cg_unscale_kernel(CgPtrs P) {
+  const KrylovDesc d = *P.d;
+  if (!d.sym_scale || __ldcg(&P.st->bad_diag) || __ldcg(&P.st->zero_rhs)) return;
+  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < d.n; i += gridDim.x * kVecThreads)
+    d.x[i] *= P.z[i];
 }
 
 // ---------------------------------------------------------------- K1
@@ -188,7 +236,7 @@ __global__ void __launch_bounds__(kTileThreads) cg_spmv_pq_kernel(CgPtrs P) {
   k1_body<kTileThreads>(P, sm.val, &s_last, [&](auto&& epi) {
     const int ntiles = (d.n + kTileRows - 1) / kTileRows;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
-      spmv_tile(t, d.n, d.rowptr, d.col, d.val, p, sm,
+      spmv_tile(t, d.n, d.rowptr, d.col, cg_vals(P, d), p, sm,
                 [&](int row, double s) { epi(row, s, __ldg(p + row)); });
   });
 }
@@ -202,7 +250,7 @@ __global__ void __launch_bounds__(tma::kThreads, 3) cg_spmv_pq_tma_kernel(CgPtrs
   if (__ldcg(&P.st->phase) != kPhaseRun) return;
   const KrylovDesc d = *P.d;
   k1_body<tma::kThreads>(P, sm.red, &sm.last, [&](auto&& epi) {
-    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, d.val, P.p, P.p, sm, &P.st->err, epi);
+    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, cg_vals(P, d), P.p, P.p, sm, &P.st->err, epi);
   });
 }
 
@@ -212,7 +260,8 @@ __global__ void __launch_bounds__(kRowThreads) cg_spmv_pq_rows_kernel(CgPtrs P) 
   __shared__ bool s_last;
   if (__ldcg(&P.st->phase) != kPhaseRun) return;
   const KrylovDesc d = *P.d;
-  k1_body<kRowThreads>(P, red, &s_last, [&](auto&& epi) { csr_rows(d.n, d.rowptr, d.col, d.val, P.p, P.p, epi); });
+  k1_body<kRowThreads>(P, red, &s_last,
+                       [&](auto&& epi) { csr_rows(d.n, d.rowptr, d.col, cg_vals(P, d), P.p, P.p, epi); });
 }
 
 // ---------------------------------------------------------------- K2
@@ -230,6 +279,41 @@ __global__ void __launch_bounds__(kVecThreads) cg_update_kernel(CgPtrs P) {
   const double* __restrict__ dinv = P.dinv;
   double rz0 = 0.0, rz1 = 0.0, rr0 = 0.0, rr1 = 0.0;
   const int stride = gridDim.x * kVecThreads;
+  if (d.sym_scale) {
+    // x^ += alpha p^, r^ -= alpha q^; r.z = r^.r^, ||r||^2 = sum d r^^2
+    const double* __restrict__ dg = P.dinv;
+    for (int i0 = blockIdx.x * kVecThreads + threadIdx.x; i0 < n; i0 += kUnroll * stride) {
+      double pi[kUnroll], qi[kUnroll], di[kUnroll], xi[kUnroll], ri[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * stride;
+        if (i < n) {
+          pi[u] = __ldg(p + i);
+          qi[u] = __ldg(q + i);
+          di[u] = __ldg(dg + i);
+          xi[u] = x[i];
+          ri[u] = r[i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * stride;
+        if (i < n) {
+          const double rn = fma(-alpha, qi[u], ri[u]);
+          x[i] = fma(alpha, pi[u], xi[u]);
+          r[i] = rn;
+          const double rn2 = rn * rn;
+          if (u & 1) {
+            rz1 += rn2;
+            rr1 = fma(di[u], rn2, rr1);
+          } else {
+            rz0 += rn2;
+            rr0 = fma(di[u], rn2, rr0);
+          }
+        }
+      }
+    }
+  } else
   for (int i0 = blockIdx.x * kVecThreads + threadIdx.x; i0 < n; i0 += kUnroll * stride) {
     double pi[kUnroll], qi[kUnroll], di[kUnroll], xi[kUnroll], ri[kUnroll];
 #pragma unroll
@@ -307,7 +391,7 @@ cg_pupdate_kernel(CgPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
   double v[2] = {0.0, 0.0};  // tt, rz of the check pass
   if (phase == kPhaseRun) {
     const double beta = __ldcg(&P.st->beta);
-    const double* __restrict__ z = P.z;
+    const double* __restrict__ z = d.sym_scale ? P.r : P.z;  // p^ = r^ + beta p^ when scaled
     double* __restrict__ p = P.p;
     for (int i0 = blockIdx.x * kVecThreads + threadIdx.x; i0 < n; i0 += kUnroll * stride) {
       double zi[kUnroll], pi[kUnroll];
@@ -324,6 +408,22 @@ cg_pupdate_kernel(CgPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
         const int i = i0 + u * stride;
         if (i < n) p[i] = fma(beta, pi[u], zi[u]);
       }
+    }
+  } else if (phase == kPhaseCheck && d.sym_scale) {
+    // t^ = b^ - A^ x^ = s (b - A x); ||t||^2 = sum d t^^2, t.z = t^.t^
+    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride) {
+      const double si = P.z[i];
+      const double th = d.b[i] * si - row_dot(d.rowptr, d.col, P.ahat, d.x, i);
+      P.r[i] = th;
+      P.p[i] = th;
+      const double th2 = th * th;
+      v[0] = fma(P.dinv[i], th2, v[0]);
+      v[1] += th2;
+    }
+    block_sums<kVecThreads, 2>(v, sm.red);
+    if (threadIdx.x == 0) {
+      P.part[0 * kMaxBlocks + blockIdx.x] = v[0];
+      P.part[1 * kMaxBlocks + blockIdx.x] = v[1];
     }
   } else if (phase == kPhaseCheck) {
     for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += stride) {
@@ -490,15 +590,17 @@ int build_graph(CgPtrs P, K1Launch k1, int g1, int gv, cudaGraphExec_t* exec) {
   do {
     cudaGraphConditionalHandle h;
     if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
-    cudaGraphNode_t n_init, n_while, n1, n2, n3, n_final;
+    cudaGraphNode_t n_init, n_scale, n_while, n1, n2, n3, n_unscale, n_final;
     void* a_init[] = {&P};
     if (add_kernel(g, nullptr, 0, &n_init, (const void*)cg_init_kernel, gv, kVecThreads, a_init) != cudaSuccess) break;
+    if (add_kernel(g, &n_init, 1, &n_scale, (const void*)cg_scale_kernel, gv, kVecThreads, a_init) != cudaSuccess)
+      break;
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    if (cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp) != cudaSuccess) break;
+    if (cudaGraphAddNode(&n_while, g, &n_scale, nullptr, 1, &cp) != cudaSuccess) break;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     int use_cond = 1;
     void* a1[] = {&P};
@@ -506,7 +608,11 @@ int build_graph(CgPtrs P, K1Launch k1, int g1, int gv, cudaGraphExec_t* exec) {
     if (add_kernel(body, nullptr, 0, &n1, k1.fn, g1, k1.threads, a1, k1.smem) != cudaSuccess) break;
     if (add_kernel(body, &n1, 1, &n2, (const void*)cg_update_kernel, gv, kVecThreads, a1) != cudaSuccess) break;
     if (add_kernel(body, &n2, 1, &n3, (const void*)cg_pupdate_kernel, gv, kVecThreads, a3) != cudaSuccess) break;
-    if (add_kernel(g, &n_while, 1, &n_final, (const void*)cg_final_kernel, gv, kVecThreads, a_init) != cudaSuccess) break;
+    if (add_kernel(g, &n_while, 1, &n_unscale, (const void*)cg_unscale_kernel, gv, kVecThreads, a_init) !=
+        cudaSuccess)
+      break;
+    if (add_kernel(g, &n_unscale, 1, &n_final, (const void*)cg_final_kernel, gv, kVecThreads, a_init) != cudaSuccess)
+      break;
     if (cudaGraphInstantiate(exec, g, 0) != cudaSuccess) break;
     rc = SLA_OK;
   } while (0);
@@ -543,6 +649,7 @@ int run_host_loop(const CgPtrs& P, const KrylovDesc& desc, K1Launch k1, int g1, 
                   cudaStream_t s) {
   cg_write_desc_kernel<<<1, 1, 0, s>>>(P.d, desc, P.st);
   cg_init_kernel<<<gv, kVecThreads, 0, s>>>(P);
+  cg_scale_kernel<<<gv, kVecThreads, 0, s>>>(P);
   const long long cap = (long long)desc.max_iter + 2LL * desc.max_restarts + 8;
   for (long long body = 0; body < cap; ++body) {
     void* a1[] = {const_cast<CgPtrs*>(&P)};
@@ -556,6 +663,7 @@ int run_host_loop(const CgPtrs& P, const KrylovDesc& desc, K1Launch k1, int g1, 
       if (phase == kPhaseDone) break;
     }
   }
+  cg_unscale_kernel<<<gv, kVecThreads, 0, s>>>(P);
   cg_final_kernel<<<gv, kVecThreads, 0, s>>>(P);
   SLA_CUDA_TRY(cudaGetLastError());
   SLA_CUDA_TRY(cudaStreamSynchronize(s));
@@ -595,6 +703,7 @@ int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags, bool 
   P.p = (double*)(base + L.p);
   P.q = (double*)(base + L.q);
   P.dinv = (double*)(base + L.dinv);
+  P.ahat = (double*)(base + al256(L.total));
   const int dev = current_device();
   const int kind = spmv_kind(n);
   const K1Launch k1 = k1_launch(kind);
@@ -651,8 +760,8 @@ extern "C" int32_t sla_cg(const sla_csr* A, const double* val, const double* b, 
                           void* stream) {
   if (A == nullptr || opts == nullptr) return SLA_ERR_INVALID;
   const int nn = A->n > 0 ? A->n : 0;
-  const size_t need =
-      (opts->flags & SLA_FLAG_CG_PIPELINED) ? cg_pipe_layout(nn).total : cg_layout(nn).total;
+  const size_t need = (opts->flags & SLA_FLAG_CG_PIPELINED) ? cg_pipe_layout(nn).total
+                                                            : cg_ws_bytes(nn, A->nnz > 0 ? A->nnz : 0);
   int rc = validate_solve_args(A, val, b, x, opts, info, ws, ws_bytes, need,
                                SLA_FLAG_HOST_LOOP | SLA_FLAG_NO_COOP | SLA_FLAG_CG_PIPELINED);
   if (rc != SLA_OK) return rc;
@@ -679,6 +788,7 @@ extern "C" int32_t sla_cg(const sla_csr* A, const double* val, const double* b, 
   d.max_restarts = opts->max_restarts;
   d.precond = opts->precond;
   d.use_x0 = opts->use_x0;
+  d.sym_scale = opts->precond == SLA_PRECOND_JACOBI ? 1 : 0;
   return launch_cg(d, ws, s, opts->flags);
 }
 
@@ -752,6 +862,7 @@ extern "C" int32_t sla_cg_noalloc(const sla_csr* A, const double* val, const dou
   d.max_restarts = opts->max_restarts;
   d.precond = opts->precond;
   d.use_x0 = opts->use_x0;
+  d.sym_scale = 0;  // the fixed scratch has no room for the scaled values
   // one cooperative launch, else plain launches from a host loop: no graph
   // objects are created either way
   return launch_cg(d, ws, s, opts->flags, /*allow_graph=*/false);

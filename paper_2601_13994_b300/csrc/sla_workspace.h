@@ -42,7 +42,10 @@ struct KrylovDesc {
   const int* g_rowptr;
   const int* g_col;
   const double* g_val;
-  int nnz_g, pad_g;
+  int nnz_g;
+  // CG per-phase kernels (sla_cg.cu) with the Jacobi preconditioner: 1 = run
+  // CG on D^{-1/2} A D^{-1/2} (its values in the workspace), 0 = PCG on A
+  int sym_scale;
 };
 
 // Device-side solver scalars.  Counters are reset by the last block of the
@@ -75,6 +78,12 @@ constexpr CgLayout cg_layout(int n) {
   L.dinv = o;  o += vec;
   L.total = o;
   return L;
+}
+
+// CG scratch of the per-phase kernels: the layout above, then the values of
+// D^{-1/2} A D^{-1/2} (nnz doubles).
+inline size_t cg_ws_bytes(int n, int nnz) {
+  return al256(cg_layout(n).total) + al256(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
 }
 
 // Pipelined Jacobi PCG (sla_cg_pipe.cu): descriptor, state, partials, the
@@ -162,7 +171,7 @@ size_t coo_ws_bytes(int n, long long m);
 // Adjoint: the larger of the CG scratch (either form) and BiCGStab scratch
 // + valT.
 inline size_t adjoint_ws_bytes(int n, int nnz) {
-  const size_t a0 = cg_layout(n).total, a1 = cg_pipe_layout(n).total;
+  const size_t a0 = cg_ws_bytes(n, nnz), a1 = cg_pipe_layout(n).total;
   const size_t a = a0 > a1 ? a0 : a1;
   const size_t b = bicg_ws_bytes(n, nnz) + al256(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
   return a > b ? a : b;
@@ -173,7 +182,7 @@ inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
   (void)batch;
   switch (kind) {
     case SLA_WS_CG:
-      *out = cg_layout(n).total;
+      *out = cg_ws_bytes(n, nnz);
       return true;
     case SLA_WS_CG_PIPELINED:
       *out = cg_pipe_layout(n).total;

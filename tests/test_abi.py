@@ -72,7 +72,9 @@ def test_pipelined_flag_arguments_rejected_without_launch():
     n = 1000
     wp = L.workspace_size(L.SLA_WS_CG_PIPELINED, n, 5000)
     wc = L.workspace_size(L.SLA_WS_CG, n, 5000)
-    assert wp % 256 == 0 and wp > wc and wp >= 8 * 8 * n
+    assert wp % 256 == 0 and wc % 256 == 0 and wp >= 8 * 8 * n
+    # the CG workspace holds 5 n-vectors and the scaled values (nnz doubles)
+    assert wc >= 8 * (5 * n + 5000)
     assert L.workspace_size(L.SLA_WS_ADJOINT, n, 5000) >= wp
     fake = ctypes.c_void_p(0x1000)
     ws = ctypes.c_void_p(0x100000)
@@ -84,7 +86,7 @@ def test_pipelined_flag_arguments_rejected_without_launch():
                           ws, wp, None) == L.SLA_ERR_INVALID
     o = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0, P)
     assert lib.sla_cg(ctypes.byref(A), fake, fake, ctypes.c_void_p(0x2000), ctypes.byref(o), fake,
-                      ws, wc, None) == L.SLA_ERR_WORKSPACE
+                      ws, wp - 256, None) == L.SLA_ERR_WORKSPACE
     assert lib.sla_bicgstab(ctypes.byref(A), fake, fake, ctypes.c_void_p(0x2000), ctypes.byref(o), fake,
                             ws, 1 << 30, None) == L.SLA_ERR_INVALID
     assert lib.sla_adjoint_backward(ctypes.byref(A), None, fake, fake, fake, ctypes.c_void_p(0x2000),
