@@ -23,13 +23,15 @@
 // stall the last wanted vector (3D 32^3 with lambda_5..7 = 0.0934, 0.0938,
 // 0.0950 and k = 6: without guards LOBPCG took from 551 to more than 3000
 // iterations depending on the start block; with two, 316-458).
-// The Rayleigh-Ritz step is solved robustly without a Cholesky factor: the
-// columns of S are scaled to unit norm, the scaled G is diagonalised, its
-// directions with eigenvalues below 1e-12 of the largest are dropped (near
-// dependence between X, W and P, which grows as the iteration converges),
-// and the projected H is diagonalised -- both small symmetric eigenproblems
-// (m <= 30) by cyclic Jacobi rotations in one thread block, with the
-// round-robin ordering that makes the m/2 rotations of a step independent.
+// The Rayleigh-Ritz step: the columns of S are scaled to unit norm; a basis
+// B with B^T G B = I comes from the Cholesky factor of the scaled G (B =
+// L^{-T}), or -- when a pivot shows near dependence between X, W and P,
+// which grows as the iteration converges -- from its eigendecomposition with
+// the directions below 1e-12 of the largest eigenvalue dropped; the
+// projected H = B^T H B is then diagonalised.  The small symmetric
+// eigenproblems (m <= 30) run in one thread block: FP32 cyclic Jacobi sweeps
+// with the round-robin ordering that makes the m/2 rotations of a step
+// independent, then FP64 orthogonalisation and FP64 sweeps (eig_eigh).
 //
 // Kernels of an iteration: SpMM (A W), Gram (block partial sums of G and H;
 // the last block to arrive adds them in a fixed order and runs the
@@ -301,6 +303,7 @@ struct EigSmem {
   double B[kEigMaxM * kEigLd];
   double T[kEigMaxM * kEigLd];
   double scale[kEigMaxM];
+  double scale2[kEigMaxM];
   double rot[4 * (kEigMaxM / 2 + 1)];
   float Af[kEigMaxM * kEigLd];
   float Vf[kEigMaxM * kEigLd];
@@ -371,24 +374,80 @@ __device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* t
     sm.H[i * kEigLd + j] *= f;
   }
   __syncthreads();
-  eig_eigh(sm.G, sm.U, m, sm.B, sm.T, sm);  // scaled G = U diag(g) U^T
+  // A basis B (m x r) with B^T G B = I.  First try the Cholesky factor of the
+  // scaled G over its nonzero columns (the locked ones are zero): B = L^{-T}.
+  // Where a pivot falls below 1e-10 (directions closer than ~1e-5 rad, which
+  // the factor would amplify), diagonalise G instead and drop its directions
+  // below 1e-12 of the largest eigenvalue.
   if (tid == 0) {
-    double gmax = 0.0;
-    for (int j = 0; j < m; ++j) gmax = fmax(gmax, sm.G[j * kEigLd + j]);
-    int r = 0;
+    int a = 0;
     for (int j = 0; j < m; ++j)
-      if (sm.G[j * kEigLd + j] > 1e-12 * gmax) sm.keep[r++] = j;
-    sm.nkeep = r;
+      if (sm.scale[j] > 0.0) sm.keep[a++] = j;
+    sm.nkeep = a;
+    sm.any = 0;  // Cholesky failed
   }
   __syncthreads();
-  const int r = sm.nkeep;
-  // B = U[:, keep] diag(g)^{-1/2}  (m x r)
-  for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
-    for (int j = threadIdx.x & 31; j < r; j += 32) {
-    const int c = sm.keep[j];
-    sm.B[i * kEigLd + j] = sm.U[i * kEigLd + c] / sqrt(sm.G[c * kEigLd + c]);
-  }
+  const int ma = sm.nkeep;
+  for (int i = threadIdx.x >> 5; i < ma; i += blockDim.x >> 5)
+    for (int j = threadIdx.x & 31; j < ma; j += 32) sm.U[i * kEigLd + j] = sm.G[sm.keep[i] * kEigLd + sm.keep[j]];
   __syncthreads();
+  for (int j = 0; j < ma; ++j) {
+    if (tid == 0) {
+      const double piv = sm.U[j * kEigLd + j];
+      if (!(piv > 1e-10)) sm.any = 1;
+      const double l = sqrt(fmax(piv, 1e-300));
+      sm.U[j * kEigLd + j] = l;
+      sm.scale2[j] = 1.0 / l;
+    }
+    __syncthreads();
+    if (sm.any) break;
+    for (int i = j + 1 + tid; i < ma; i += nt) sm.U[i * kEigLd + j] *= sm.scale2[j];
+    __syncthreads();
+    for (int i = j + 1 + (threadIdx.x >> 5); i < ma; i += blockDim.x >> 5)
+      for (int c = j + 1 + (threadIdx.x & 31); c <= i; c += 32)
+        sm.U[i * kEigLd + c] = fma(-sm.U[i * kEigLd + j], sm.U[c * kEigLd + j], sm.U[i * kEigLd + c]);
+    __syncthreads();
+  }
+  int r;
+  if (!sm.any) {
+    // column c of L^{-1} by forward substitution (thread c), into T
+    for (int c = tid; c < ma; c += nt) {
+      for (int i = 0; i < c; ++i) sm.T[i * kEigLd + c] = 0.0;
+      for (int i = c; i < ma; ++i) {
+        double acc = (i == c) ? 1.0 : 0.0;
+        for (int l = c; l < i; ++l) acc = fma(-sm.U[i * kEigLd + l], sm.T[l * kEigLd + c], acc);
+        sm.T[i * kEigLd + c] = acc * sm.scale2[i];
+      }
+    }
+    __syncthreads();
+    // B[keep[a]][b] = (L^{-1})[b][a]; zero rows for the locked columns
+    for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
+      for (int j = threadIdx.x & 31; j < ma; j += 32) sm.B[i * kEigLd + j] = 0.0;
+    __syncthreads();
+    for (int a = threadIdx.x >> 5; a < ma; a += blockDim.x >> 5)
+      for (int b = threadIdx.x & 31; b < ma; b += 32) sm.B[sm.keep[a] * kEigLd + b] = sm.T[b * kEigLd + a];
+    __syncthreads();
+    r = ma;
+  } else {
+    eig_eigh(sm.G, sm.U, m, sm.B, sm.T, sm);  // scaled G = U diag(g) U^T
+    if (tid == 0) {
+      double gmax = 0.0;
+      for (int j = 0; j < m; ++j) gmax = fmax(gmax, sm.G[j * kEigLd + j]);
+      int rr = 0;
+      for (int j = 0; j < m; ++j)
+        if (sm.G[j * kEigLd + j] > 1e-12 * gmax) sm.keep[rr++] = j;
+      sm.nkeep = rr;
+    }
+    __syncthreads();
+    r = sm.nkeep;
+    // B = U[:, keep] diag(g)^{-1/2}  (m x r)
+    for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
+      for (int j = threadIdx.x & 31; j < r; j += 32) {
+        const int c = sm.keep[j];
+        sm.B[i * kEigLd + j] = sm.U[i * kEigLd + c] / sqrt(sm.G[c * kEigLd + c]);
+      }
+    __syncthreads();
+  }
   // T = H B (m x r), then H2 = B^T T (r x r) into G
   for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
     for (int j = threadIdx.x & 31; j < r; j += 32) {
