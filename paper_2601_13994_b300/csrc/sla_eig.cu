@@ -56,6 +56,7 @@ constexpr int kEigThreads = 256;
 constexpr int kEigTile = 32;              // rows of S staged per Gram tile
 constexpr int kEigPairs = kEigMaxM * (kEigMaxM + 1) / 2;
 constexpr int kEigPollEvery = 8;
+constexpr int kRrBlocks = (2 * kEigPairs + 31) / 32;  // blocks of the Gram totals
 
 struct EigDesc {
   int n, nnz, k, kb, ld, max_iter, precond, use_x0;
@@ -84,6 +85,7 @@ struct EigPtrs {
   double* S[2];
   double* AS[2];
   double* gpart;   // [blocks][2 * kEigPairs]
+  double* gtot;    // [2 * kEigPairs]
   double* upart;   // [blocks + 1][2 * kEigMaxB]
   double* C;       // [kEigMaxM][kEigMaxB]
   double* theta;   // [kEigMaxM]
@@ -144,8 +146,14 @@ __global__ void __launch_bounds__(kEigThreads) eig_spmm_kernel(EigPtrs P, int mo
   const EigState& st = *P.st;
   if (mode != 2 && (st.done || st.bad)) return;
   const int n = d.n, kb = d.kb, ld = d.ld, cur = st.cur;
-  const double* X = P.S[cur] + (mode == 1 ? kb : 0);
-  double* Y = (mode == 2 ? P.AS[cur ^ 1] : P.AS[cur]) + (mode == 1 ? kb : 0);
+  // every 16th iteration A X is recomputed too (X and W are adjacent columns),
+  // so that the carried A X (A X' = A S C) cannot drift far from the product
+  const bool refresh = mode == 1 && (st.iters & 15) == 15;
+  const int parts = refresh ? 2 : 1;
+  for (int part = 0; part < parts; ++part) {
+  const int off = (mode == 1 && !refresh) ? kb : part * kb;
+  const double* X = P.S[cur] + off;
+  double* Y = (mode == 2 ? P.AS[cur ^ 1] : P.AS[cur]) + off;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double acc[kEigMaxB];
 #pragma unroll
@@ -162,6 +170,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_spmm_kernel(EigPtrs P, int mo
 #pragma unroll
     for (int j = 0; j < kEigMaxB; ++j)
       if (j < kb) yr[j] = acc[j];
+  }
   }
 }
 
@@ -508,19 +517,9 @@ __global__ void __launch_bounds__(kEigThreads) eig_gram_kernel(EigPtrs P) {
   const EigDesc& d = *P.d;
   EigState* st = P.st;
   if (st->done || st->bad) return;
-  // the row tiles and the Rayleigh-Ritz scratch share the shared memory
-  __shared__ union {
-    struct {
-      double S[kEigTile * kEigMaxM];
-      double A[kEigTile * kEigMaxM];
-    } tile;
-    EigSmem rr;
-  } u;
-  __shared__ bool s_last;
-  double* tS = u.tile.S;
-  double* tA = u.tile.A;
-  EigSmem& sm = u.rr;
-  const int n = d.n, kb = d.kb, ld = d.ld, m = st->m, cur = st->cur;
+  __shared__ double tS[kEigTile * kEigMaxM];
+  __shared__ double tA[kEigTile * kEigMaxM];
+  const int n = d.n, ld = d.ld, m = st->m, cur = st->cur;
   const int npairs = m * (m + 1) / 2;
   const double* S = P.S[cur];
   const double* AS = P.AS[cur];
@@ -571,29 +570,50 @@ __global__ void __launch_bounds__(kEigThreads) eig_gram_kernel(EigPtrs P) {
       mine[kEigPairs + t] = hh[h];
     }
   }
+}
+
+// Totals of the Gram partials of the gb blocks -- 2 npairs values -- then
+// the Rayleigh-Ritz step in the last block to arrive.  Block c adds values
+// 32c .. 32c + 31: a warp per 4 values, lane l summing blocks l, l + 32, ...,
+// then a fixed butterfly (the same bits run to run; spread over blocks so
+// that the loads are not serialised in one block).
+__global__ void __launch_bounds__(kEigThreads) eig_rr_kernel(EigPtrs P, int gb) {
+  const EigDesc& d = *P.d;
+  EigState* st = P.st;
+  if (st->done || st->bad) return;
+  __shared__ EigSmem sm;
+  __shared__ bool s_last;
+  const int kb = d.kb, m = st->m;
+  const int npairs = m * (m + 1) / 2;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int q = 0; q < 4; ++q) {
+    const int v = blockIdx.x * 32 + w * 4 + q;  // value: G pairs, then H pairs
+    if (v >= 2 * npairs) break;
+    const int off = v < npairs ? v : kEigPairs + (v - npairs);
+    double s = 0.0;
+    for (int b = lane; b < gb; b += 32) s += __ldcg(P.gpart + (size_t)b * 2 * kEigPairs + off);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) P.gtot[v] = s;
+  }
   if (!last_block_arrive(&st->ticket_gram, &s_last)) return;
   const unsigned active = st->active;
-  // fixed-order totals into the full symmetric G and H (the tiles are dead);
-  // the W and P columns of converged pairs are zeroed (soft locking)
-  for (int h = 0; h < 2; ++h) {
-    const int t = tid + h * kEigThreads;
-    if (t < npairs) {
-      double sg = 0.0, sh = 0.0;
-#pragma unroll 8
-      for (int b = 0; b < (int)gridDim.x; ++b) {
-        const double* pb2 = P.gpart + (size_t)b * 2 * kEigPairs;
-        sg += __ldcg(pb2 + t);
-        sh += __ldcg(pb2 + kEigPairs + t);
-      }
-      const int a = pa[h], b = pb[h];
-      const bool la = a >= kb && !((active >> ((a - kb) % kb)) & 1u);
-      const bool lb = b >= kb && !((active >> ((b - kb) % kb)) & 1u);
-      if (la || lb) sg = sh = 0.0;
-      sm.G[a * kEigLd + b] = sg;
-      sm.G[b * kEigLd + a] = sg;
-      sm.H[a * kEigLd + b] = sh;
-      sm.H[b * kEigLd + a] = sh;
+  // the full symmetric G and H; the W and P columns of converged pairs are
+  // zeroed (soft locking)
+  for (int t = tid; t < npairs; t += kEigThreads) {
+    int a = 0, rem = t;
+    while (rem >= m - a) {
+      rem -= m - a;
+      ++a;
     }
+    const int b = a + rem;
+    double sg = __ldcg(P.gtot + t), sh = __ldcg(P.gtot + npairs + t);
+    const bool la = a >= kb && !((active >> ((a - kb) % kb)) & 1u);
+    const bool lb = b >= kb && !((active >> ((b - kb) % kb)) & 1u);
+    if (la || lb) sg = sh = 0.0;
+    sm.G[a * kEigLd + b] = sg;
+    sm.G[b * kEigLd + a] = sg;
+    sm.H[a * kEigLd + b] = sh;
+    sm.H[b * kEigLd + a] = sh;
   }
   __syncthreads();
   const int r = eig_rayleigh_ritz(sm, m, kb, P.C, P.theta);
@@ -868,6 +888,7 @@ size_t eig_ws_bytes(int n, int k, int* gram_blocks, int* upd_blocks) {
   const size_t kb = (size_t)eig_block(n, k);
   o += 4 * al256(sizeof(double) * nn * 3 * kb);         // S[2], AS[2]
   o += al256(sizeof(double) * (size_t)gb * 2 * kEigPairs);
+  o += al256(sizeof(double) * 2 * kEigPairs);
   o += al256(sizeof(double) * ((size_t)ub + 1) * 2 * kEigMaxB);
   o += al256(sizeof(double) * kEigMaxM * kEigMaxB);
   o += al256(sizeof(double) * kEigMaxM);
@@ -906,6 +927,7 @@ extern "C" int32_t sla_eigsh(const sla_csr* A, const double* val, int32_t k, dou
     P.AS[b] = (double*)p;      p += al256(sizeof(double) * nn * 3 * (size_t)kb);
   }
   P.gpart = (double*)p;        p += al256(sizeof(double) * (size_t)gb * 2 * kEigPairs);
+  P.gtot = (double*)p;         p += al256(sizeof(double) * 2 * kEigPairs);
   P.upart = (double*)p;        p += al256(sizeof(double) * ((size_t)ub + 1) * 2 * kEigMaxB);
   P.C = (double*)p;            p += al256(sizeof(double) * kEigMaxM * kEigMaxB);
   P.theta = (double*)p;
@@ -931,11 +953,13 @@ extern "C" int32_t sla_eigsh(const sla_csr* A, const double* val, int32_t k, dou
   // start: Rayleigh-Ritz on X0 alone, then W = D^{-1} R
   eig_spmm_kernel<<<eig_grid(n, 4096), kEigThreads, 0, s>>>(P, 0);
   eig_gram_kernel<<<gb, kEigThreads, 0, s>>>(P);
+  eig_rr_kernel<<<kRrBlocks, kEigThreads, 0, s>>>(P, gb);
   eig_update_kernel<<<ub, kEigThreads, 0, s>>>(P);
   SLA_CUDA_TRY(cudaGetLastError());
   for (long long it = 0; it < (long long)opts->max_iter; ++it) {
     eig_spmm_kernel<<<eig_grid(n, 4096), kEigThreads, 0, s>>>(P, 1);
     eig_gram_kernel<<<gb, kEigThreads, 0, s>>>(P);
+    eig_rr_kernel<<<kRrBlocks, kEigThreads, 0, s>>>(P, gb);
     eig_update_kernel<<<ub, kEigThreads, 0, s>>>(P);
     if ((it + 1) % kEigPollEvery == 0) {
       int done = 0;
