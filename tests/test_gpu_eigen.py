@@ -134,3 +134,25 @@ def test_eigsh_at_128():
     assert info.status == 0 and info.true_rel_res <= 2e-8
     ref = np.sort(spla.eigsh(sp.csr_matrix((v, c, rp), shape=(n, n)), k=6, sigma=0, which="LM")[0])
     assert np.abs(lam.cpu().numpy() - ref).max() <= 1e-10 * ref.max()
+
+
+@pytest.mark.parametrize("n,k", [(4, 4), (6, 4), (10, 8), (3, 1)])
+def test_eigsh_tiny_systems(n, k):
+    """n <= k + 2: the block spans (nearly) the whole space, the Gram matrix
+    is rank-deficient by construction (its Cholesky factor fails and the
+    eigendecomposition route drops the dependent directions); every wanted
+    pair still matches the dense eigensolve."""
+    rng = np.random.default_rng(n * 10 + k)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    M = Q @ np.diag(np.linspace(1.0, 3.0, n)) @ Q.T
+    rp = np.arange(0, n * n + 1, n, dtype=np.int32)
+    c = np.tile(np.arange(n, dtype=np.int32), n)
+    v = M.reshape(-1)
+    A = csr(rp, c)
+    lam, V, info = sla.eigsh(A, to_dev(v), k, tol=1e-10)
+    lo, Vo = OE.smallest_eigenpairs(rp, c, v, k)
+    assert info.status == 0
+    assert np.abs(lam.cpu().numpy() - lo).max() <= 1e-12 * lo.max()
+    Vn = V.cpu().numpy()
+    for i in range(k):
+        assert abs(abs(float(Vn[:, i] @ Vo[:, i])) - 1.0) <= 1e-10
