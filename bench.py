@@ -746,7 +746,9 @@ def run_ours(args):
     fpi = flops_per_iter(n, nnz)
     fp64_tf = fpi * it / (ms_max / 1e3) / 1e12
     spmv_gbs = spmv_bytes(n, nnz) / (spmv_ms / 1e3) / 1e9
-    launches = args.steps * (1 + 2 + 3 * (it + 1))
+    # per solve: descriptor write, init, scale (D^-1/2 A D^-1/2), unscale, final, and
+    # three kernels per loop body (the iterations and the true-residual check)
+    launches = args.steps * (1 + 4 + 3 * (it + 1))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
