@@ -44,7 +44,6 @@
 // only m (and x in the residual checks) is gathered across threads, always
 // after a barrier and through plain (coherent) loads.
 #include <cmath>
-#include <mutex>
 
 #include "sla_coop.cuh"
 

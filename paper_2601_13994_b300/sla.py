@@ -468,8 +468,9 @@ class _Eigsh(torch.autograd.Function):
 def eigsh(A: CSRMatrix, val: torch.Tensor, k: int = 6, *, tol: float = 1e-8, max_iter: int | None = None,
           precond: str = "jacobi", v0: torch.Tensor | None = None, strict: bool | None = True):
     """The k smallest eigenpairs of SPD A by LOBPCG (Sec. 3.3; Knyazev 2001)
-    with the Jacobi preconditioner.  Returns (lambda [k] ascending,
-    V [n, k] unit columns, SolveInfo).  lambda is differentiable w.r.t. val
+    with the Jacobi preconditioner (k <= 8; max_iter defaults to 20000
+    iterations).  Returns (lambda [k] ascending, V [n, k] unit columns,
+    SolveInfo).  lambda is differentiable w.r.t. val
     by the Hellmann-Feynman gradient v_i v_j on the pattern (Eq. 4; simple
     eigenvalues); V carries no gradient.  strict=True raises on a failed
     solve, False warns, None skips the check."""
