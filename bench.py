@@ -405,7 +405,13 @@ def extra_rows(dev, args, peak):
     fl = 0.0
     for s, m in enumerate(mats):
         fl += (2 * int(m[0][-1]) + 14 * (len(m[0]) - 1)) * int(its[s])
+    # the team launch with the standard and with the pipelined PCG (config bit 64)
+    ms_std, _ = _time(lambda: sla.cg_batched_list(P, vt, bt, rtol=1e-8, config=0))
+    ms_pipe, _ = _time(lambda: sla.cg_batched_list(P, vt, bt, rtol=1e-8, config=64))
     out["batched_list_512_fem"] = {"s": ms / 1e3, "total_rows": P.total_rows, "iters_mean": float(its.mean()),
+                                   "tuned_config": sla.tuned_configs().get(
+                                       ("list", P.n_max, P.total_rows, P.total_nnz, P.batch)),
+                                   "teams_standard_s": ms_std / 1e3, "teams_pipelined_s": ms_pipe / 1e3,
                                    "iters_max": int(its.max()),
                                    "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
                                    "fp64_tflops": fl / (ms / 1e3) / 1e12,

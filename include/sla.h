@@ -596,7 +596,11 @@ int32_t sla_cg_batched_shared(const sla_csr* A, int32_t batch,
  * while the rest of the GPU idles; a team that reaches the small systems
  * splits into single CTAs, which take them one each (vectors in the
  * workspace).  config bit 32 turns the teams off (the persistent single-CTA
- * kernel above takes every system).  Still no host synchronisation.
+ * kernel above takes every system).  config bit 64 (with the teams on)
+ * solves the team systems by the pipelined PCG of SLA_FLAG_CG_PIPELINED
+ * instead (one merged reduction and one team barrier per iteration; results
+ * agree with the standard form to rounding); single CTAs keep the standard
+ * form.  Still no host synchronisation.
  * Workspace: SLA_WS_BATCHED with (total_rows, 1). */
 int32_t sla_cg_batched_list(int32_t batch, int32_t n_max, int32_t total_rows,
                             const int32_t* n_off, const int32_t* nnz_off,

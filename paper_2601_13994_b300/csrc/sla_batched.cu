@@ -255,8 +255,10 @@ int launch_batched(const BatchDesc& d0, bool use_smem, cudaStream_t s) {
 
 // config: low 4 bits = block size code (1: 256, 2: 512, 3: 1024; 0: auto),
 // bit 4 = keep the vectors in global memory even when they fit on chip,
-// bit 5 = no block teams for the large systems of a list.
+// bit 5 = no block teams for the large systems of a list, bit 6 = the block
+// teams solve their systems by the pipelined PCG (sla_cg_pipe.cuh).
 constexpr int kConfigNoTeams = 32;
+constexpr int kConfigPipelined = 64;
 // Systems of a list with at least kTeamMinNnz entries are solved by teams of
 // blocks; the team launch is made when some system can have that many
 // (n_max >= kTeamMinRows).
@@ -326,13 +328,14 @@ size_t team_scratch_bytes();
 int launch_batched_teams(int batch, int min_nnz, const int* rowptr, const int* col, const int* n_off,
                          const int* nnz_off, const int* order, const double* val, const double* b, double* x,
                          sla_info* info, double* gvec, void* scratch, double rtol, double atol, int max_iter,
-                         int max_restarts, int precond, int use_x0, cudaStream_t s, bool* launched);
+                         int max_restarts, int precond, int use_x0, bool pipelined, cudaStream_t s,
+                         bool* launched);
 
-// Workspace: scheduling counter | block-team scratch | 5 doubles per row of
+// Workspace: scheduling counter | block-team scratch | 8 doubles per row of
 // the batch (used by the systems whose vectors do not fit in shared memory,
 // and by the systems the teams solve).
 size_t batched_ws_bytes(long long total_rows) {
-  return 256 + team_scratch_bytes() + al256((size_t)5 * sizeof(double) * (size_t)(total_rows > 0 ? total_rows : 1));
+  return 256 + team_scratch_bytes() + al256((size_t)8 * sizeof(double) * (size_t)(total_rows > 0 ? total_rows : 1));
 }
 
 double* batched_gvec(void* ws) { return (double*)((char*)ws + 256 + team_scratch_bytes()); }
@@ -407,7 +410,8 @@ extern "C" int32_t sla_cg_batched_list(int32_t batch, int32_t n_max, int32_t tot
     bool launched = false;
     const int rc = launch_batched_teams(batch, kTeamMinNnz, rowptr, col, n_off, nnz_off, order, val, b, x, info,
                                         d.gvec, (char*)ws + 256, opts->rtol, opts->atol, opts->max_iter,
-                                        opts->max_restarts, opts->precond, opts->use_x0, s, &launched);
+                                        opts->max_restarts, opts->precond, opts->use_x0,
+                                        (config & kConfigPipelined) != 0, s, &launched);
     if (rc != SLA_OK) return rc;
     if (launched) return SLA_OK;  // the team launch also solved the small systems
   }

@@ -33,6 +33,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "sla_cg_pipe.cuh"
 #include "sla_coop.cuh"
 
 namespace sla {
@@ -647,7 +648,7 @@ struct TeamBatchArgs {
   const double* b;
   double* x;
   sla_info* info;
-  double* gvec;       // 5 doubles per row of the batch, at 5 * n_off[s]
+  double* gvec;       // per row of the batch: 5 doubles at 5 n_off[s], or 8 at 8 n_off[s] (pipelined)
   unsigned* counters; // [teams] barrier counters, zero at launch
   int* slots;         // [teams] queue position handed to each team
   unsigned* next;     // queue counter, zero at launch
@@ -683,9 +684,26 @@ __device__ __forceinline__ long long team_system_desc(const TeamBatchArgs& B, in
 // system a team meets turns it into single blocks, which take the rest of
 // the queue one system per block (the queue is largest first, so from then
 // on every system is small), so no block waits while others finish.
+// PIPE: the systems solved by teams take the pipelined PCG (one merged
+// reduction and one team barrier per iteration, sla_cg_pipe.cuh); single
+// blocks keep the standard form, whose barriers are block barriers and
+// whose FP64 work per row is smaller.  The vectors of a system start at
+// 8 row0 with PIPE (so that the 8-double records of a team system and the
+// 5 vectors of a single-block system never overlap), else at 5 row0.
+template <bool PIPE>
+__device__ __forceinline__ bool batch_solve(const KrylovDesc& sd, double* gvec, long long row0, Team& tm,
+                                            CoopSmem& sm, CoopState& s, PipeState& ps) {
+  const size_t n = (size_t)sd.n;
+  double* vec = gvec + (PIPE ? 8 : 5) * (size_t)row0;
+  if (PIPE && tm.size > 1) return pipe_team_solve(sd, vec, vec + 6 * n, vec + 7 * n, tm, false, sm, ps);
+  return jacobi_team_solve(sd, vec, vec + n, vec + 2 * n, vec + 3 * n, vec + 4 * n, tm, false, sm, s);
+}
+
+template <bool PIPE>
 __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) batched_team_kernel(TeamBatchArgs B) {
   __shared__ CoopSmem sm;
   __shared__ CoopState s;
+  __shared__ PipeState ps;
   __shared__ KrylovDesc sd;
   __shared__ long long s_row0;
   __shared__ int s_k;
@@ -712,9 +730,7 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) batched_team_ker
       if (rank == 0) first = s_k;
       break;
     }
-    const size_t n = (size_t)sd.n;
-    double* vec = B.gvec + 5 * (size_t)row0;
-    if (!jacobi_team_solve(sd, vec, vec + n, vec + 2 * n, vec + 3 * n, vec + 4 * n, tm, false, sm, s)) return;
+    if (!batch_solve<PIPE>(sd, B.gvec, row0, tm, sm, s, ps)) return;
   }
   // single mode: every block solves whole systems on its own
   Team solo{GridSync{nullptr, 0u}, 1, 0, nullptr, B.err};
@@ -728,9 +744,7 @@ __global__ void __launch_bounds__(kCoopThreads, kCoopMinBlocks) batched_team_ker
     __syncthreads();
     const long long row0 = s_row0;
     if (row0 < 0) return;
-    const size_t n = (size_t)sd.n;
-    double* vec = B.gvec + 5 * (size_t)row0;
-    if (!jacobi_team_solve(sd, vec, vec + n, vec + 2 * n, vec + 3 * n, vec + 4 * n, solo, false, sm, s)) return;
+    if (!batch_solve<PIPE>(sd, B.gvec, row0, solo, sm, s, ps)) return;
     __syncthreads();  // sd and s_row0 are rewritten for the next system
   }
 }
@@ -772,7 +786,7 @@ namespace {
 std::mutex g_coop_mu;
 // resident blocks per SM of each kernel per device (0: not yet queried,
 // -1: the device has no cooperative launch)
-int g_occ_cg[64] = {}, g_occ_ggt[64] = {}, g_occ_team[64] = {};
+int g_occ_cg[64] = {}, g_occ_ggt[64] = {}, g_occ_team[64] = {}, g_occ_team_pipe[64] = {};
 }  // namespace
 
 int coop_occupancy_of(int dev, int* cache, const void* fn) {
@@ -865,11 +879,13 @@ size_t team_scratch_bytes() {
 int launch_batched_teams(int batch, int min_nnz, const int* rowptr, const int* col, const int* n_off,
                          const int* nnz_off, const int* order, const double* val, const double* b, double* x,
                          sla_info* info, double* gvec, void* scratch, double rtol, double atol, int max_iter,
-                         int max_restarts, int precond, int use_x0, cudaStream_t s, bool* launched) {
+                         int max_restarts, int precond, int use_x0, bool pipelined, cudaStream_t s,
+                         bool* launched) {
   *launched = false;
   const int dev = current_device();
   if (dev < 0 || dev >= 64) return SLA_OK;
-  const int occ = coop_occupancy_of(dev, g_occ_team, (const void*)batched_team_kernel);
+  const void* fn = pipelined ? (const void*)batched_team_kernel<true> : (const void*)batched_team_kernel<false>;
+  const int occ = coop_occupancy_of(dev, pipelined ? g_occ_team_pipe : g_occ_team, fn);
   if (occ <= 0) return SLA_OK;
   int grid = num_sms(dev) * occ;
   if (grid > kCoopMaxGrid) grid = kCoopMaxGrid;
@@ -908,8 +924,7 @@ int launch_batched_teams(int batch, int min_nnz, const int* rowptr, const int* c
   team_info_prefill_kernel<<<(batch + 255) / 256, 256, 0, s>>>(batch, info);
   SLA_CUDA_TRY(cudaGetLastError());
   void* args[] = {&B};
-  SLA_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)batched_team_kernel, dim3(grid), dim3(kCoopThreads),
-                                           args, 0, s));
+  SLA_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCoopThreads), args, 0, s));
   *launched = true;
   return SLA_OK;
 }

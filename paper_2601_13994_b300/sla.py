@@ -583,7 +583,7 @@ class SparseTensor:
 # 256/512/1024 threads, vectors on chip / in global; for lists also without
 # block teams for the large systems (bit 32)
 BATCH_CONFIGS = (1, 2, 3, 1 | 16, 2 | 16, 3 | 16)
-LIST_CONFIGS = BATCH_CONFIGS + (1 | 32, 2 | 32, 3 | 32)
+LIST_CONFIGS = BATCH_CONFIGS + (1 | 32, 2 | 32, 3 | 32, 64)
 
 
 class CSRList:

@@ -125,6 +125,44 @@ def test_distinct_patterns_with_block_teams():
         assert np.array_equal(x2.cpu().numpy(), xh), name
 
 
+def test_distinct_patterns_pipelined_teams():
+    """config bit 64: the systems with at least 32768 entries by teams on the
+    pipelined PCG, per system against the oracle's pipelined PCG (solution
+    and iteration count), the small ones by single blocks on the standard
+    form, against the oracle's PCG; with and without a processing order
+    (with fewer systems than teams, every team takes one system from the
+    queue, so each large system is a team's either way), a zero right-hand
+    side, and deterministic across repeats."""
+    mats = I.fem_list(10, seed0=2200, n_lo=200, n_hi=3000)
+    mats.insert(2, I.diffusion2d_random(120, 41))     # 71520 entries: a team system
+    mats.append(I.diffusion3d_random(25, 42))         # 105625 entries: a team system
+    mats.insert(5, I.fem_list(1, seed0=2299, n_lo=500, n_hi=600)[0])
+    P = sla.CSRList([(rp, c) for rp, c, _ in mats])
+    vals = np.concatenate([v for _, _, v in mats])
+    bs = [I.rhs_uniform(len(rp) - 1, 90 + s) for s, (rp, _, _) in enumerate(mats)]
+    bs[5][:] = 0.0
+    bt = to_dev(np.concatenate(bs))
+    for order in (P.order, None):
+        P.order = order
+        x, info = sla.cg_batched_list(P, to_dev(vals), bt, rtol=1e-10, config=64)
+        torch.cuda.synchronize()
+        xh = x.cpu().numpy()
+        st, its = np.atleast_1d(info.status), np.atleast_1d(info.iters)
+        assert st[5] == 0 and its[5] == 0 and not xh[P.n_off_h[5]:P.n_off_h[6]].any()
+        for s, (rp, c, v) in enumerate(mats):
+            if s == 5:
+                continue
+            xo, io = oracle.pcg_pipelined(rp, c, v, bs[s], rtol=1e-10)
+            xs, js = oracle.pcg(rp, c, v, bs[s], rtol=1e-10)
+            if int(rp[-1]) < 32768:
+                xo, io = xs, js  # a single block: the standard form
+            assert st[s] == io["status"] == 0, s
+            assert rel(xh[P.n_off_h[s]:P.n_off_h[s + 1]], xo) <= 1e-8, s
+            assert abs(int(its[s]) - io["iters"]) <= 2, (s, its[s], io["iters"])
+        x2, _ = sla.cg_batched_list(P, to_dev(vals), bt, rtol=1e-10, config=64)
+        assert np.array_equal(x2.cpu().numpy(), xh)
+
+
 def test_graph_capture_and_replay():
     B, N = 8, 16
     rp, c, vals = I.batched_shared_2d(N, B, seed0=11, sigma=0.5)
