@@ -880,3 +880,73 @@ def test_hellmann_feynman_closed_form_and_central_differences():
         lm = np.linalg.eigvalsh(A - eps * D)[:k]
         fd = float(w @ (lp - lm)) / (2 * eps)
         assert abs(fd - float(gv @ dv)) <= 1e-6 * abs(fd)
+
+
+def _eig_loss(A, k, glam, gV):
+    """L = sum_j glam_j lambda_j + sum_j gV_j^T v_j for the k smallest pairs
+    of a dense matrix (symmetric: eigh; else eig, real parts), each v_j of
+    unit norm with its largest-magnitude entry positive."""
+    if np.array_equal(A, A.T):
+        lam, V = np.linalg.eigh(A)
+    else:
+        lam, V = np.linalg.eig(A)
+        o = np.argsort(lam.real)
+        lam, V = lam.real[o], V.real[:, o]
+    lam, V = lam[:k], V[:, :k] / np.linalg.norm(V[:, :k], axis=0)
+    for j in range(k):
+        if V[np.argmax(np.abs(V[:, j])), j] < 0:
+            V[:, j] = -V[:, j]
+    return float(glam @ lam) + float(np.sum(gV * V))
+
+
+def test_eigenvector_adjoint_diagonal_closed_form():
+    """A = diag(d), d distinct: v_j = e_j and the deflated solve is diagonal,
+    mu_j[m] = gV_j[m] / (d_m - d_j) for m != j, mu_j[j] = 0."""
+    from oracle import eigen as OE
+    rng = np.random.default_rng(5)
+    n, k = 9, 4
+    d = np.sort(rng.uniform(1.0, 5.0, n))
+    rp = np.arange(n + 1, dtype=np.int32)
+    c = np.arange(n, dtype=np.int32)
+    lam, V = OE.smallest_eigenpairs(rp, c, d, k)
+    assert np.array_equal(V, np.eye(n)[:, :k])
+    gV = rng.standard_normal((n, k))
+    mu = OE.eigenvector_adjoint(rp, c, d, lam, V, gV)
+    for j in range(k):
+        ref = np.array([0.0 if m == j else gV[m, j] / (d[m] - d[j]) for m in range(n)])
+        assert np.abs(mu[:, j] - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_eigenvector_gradient_central_differences():
+    """The full gradient (Hellmann-Feynman plus the deflated-solve
+    eigenvector part) of L = sum glam_j lambda_j + sum gV_j^T v_j against
+    central differences (eps = 1e-5, as Tab. 5): along symmetric
+    perturbations of the stored entries, and along single off-diagonal
+    entries (a non-symmetric perturbation: the right eigenvectors), which
+    tells -mu_a v_b from its transpose -mu_b v_a."""
+    from oracle import eigen as OE
+    rp, c, v = I.diffusion2d_random(6, 8)
+    n, k = len(rp) - 1, 4
+    lam, _ = OE.smallest_eigenpairs(rp, c, v, k + 1)
+    assert np.diff(lam).min() > 1e-2
+    rng = np.random.default_rng(9)
+    glam = rng.uniform(0.5, 1.5, k)
+    gV = rng.standard_normal((n, k))
+    g = OE.eigen_loss_grad(rp, c, v, k, glam, gV)
+    A = OE.dense(rp, c, v)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    eps = 1e-5
+    for _ in range(3):
+        D = np.zeros_like(A)
+        D[rows, c] = rng.standard_normal(len(v))
+        D = 0.5 * (D + D.T)
+        fd = (_eig_loss(A + eps * D, k, glam, gV) - _eig_loss(A - eps * D, k, glam, gV)) / (2 * eps)
+        assert abs(fd - float(g @ D[rows, c])) <= 1e-6 * abs(fd)
+    off = [e for e in range(len(v)) if rows[e] != c[e]]
+    for e in rng.choice(off, 4, replace=False):
+        D = np.zeros_like(A)
+        D[rows[e], c[e]] = 1.0
+        fd = (_eig_loss(A + eps * D, k, glam, gV) - _eig_loss(A - eps * D, k, glam, gV)) / (2 * eps)
+        et = [t for t in range(len(v)) if rows[t] == c[e] and c[t] == rows[e]][0]
+        assert abs(fd - g[e]) <= 1e-6 * max(abs(fd), 1e-3), (e, fd, g[e])
+        assert abs(g[e] - g[et]) > 1e-3 * abs(fd)  # the transpose differs: the check can tell them apart
