@@ -87,6 +87,7 @@ extern "C" {
 #define SLA_WS_SPMV_MERGE 9     /* sla_spmv_merge                              */
 #define SLA_WS_CG_PIPELINED 10  /* sla_cg with SLA_FLAG_CG_PIPELINED          */
 #define SLA_WS_EIGSH 11         /* sla_eigsh: batch = k (1..SLA_EIG_MAX_K)     */
+#define SLA_WS_EIG_ADJOINT 12   /* sla_eig_vector_adjoint: batch = k           */
 
 #define SLA_EIG_MAX_K 8         /* largest k of sla_eigsh                      */
 #define SLA_WS_CG_MULTI 8       /* sla_cg_multi / sla_adjoint_backward_multi:
@@ -532,6 +533,50 @@ int32_t sla_eigsh(const sla_csr* A, const double* val, int32_t k,
  * for simple eigenvalues.  Asynchronous on `stream`. */
 int32_t sla_eig_grad_values(const sla_csr* A, int32_t k, const double* V,
                             const double* g, double* grad_val, void* stream);
+
+/* Eigenvector adjoint (Sec. 3.2: one deflated linear solve per pair).  For
+ * the unit eigenvectors V [n][k] (row-major) of symmetric A with simple
+ * eigenvalues lambda [k] and upstream gradients gV [n][k] = dL/dV, writes
+ * mu [n][k]: column j solves (A - lambda_j I) mu_j = (I - v_j v_j^T) gV_j
+ * with v_j^T mu_j = 0 -- the adjoint of the constrained residual
+ * (A v - lambda v, (v^T v - 1)/2), whose multiplier on the normalisation
+ * is eliminated.  The eigenvector part of dL/dA is then -mu_j[a] v_j[b]
+ * (sla_eig_vector_grad_values); the eigenvalue part is Eq. 4.  mu_j is the
+ * closed form sum_{l != j} (v_l^T gV_j) / (lambda_l - lambda_j) v_l over
+ * the other given pairs plus the solution in span(V)^perp, found by CG on
+ * (I - V V^T)(A - lambda_j I)(I - V V^T) with the preconditioner
+ * (I - V V^T) D^{-1} (I - V V^T), D = diag(A) (opts->precond JACOBI) or I
+ * (NONE): SPD there when lambda_j lies below every eigenvalue not in V, as
+ * for the k smallest pairs of sla_eigsh.  All k solves in one cooperative
+ * launch (three bounded grid barriers per iteration; asynchronous).
+ * opts: rtol, atol (stop when ||r_j|| <= max(rtol ||b_j||, atol), b_j =
+ * (I - V V^T) gV_j), max_iter, precond; use_x0 and flags must be 0.
+ * info [k] (device): per pair iters, status (OK; NOT_CONVERGED; NOT_SPD for
+ * a non-positive diagonal with Jacobi or a non-positive curvature, i.e.
+ * lambda_j not below the spectrum outside V; BREAKDOWN for a non-finite
+ * scalar or a repeated eigenvalue, |lambda_l - lambda_j| <= 1e-12
+ * max(|lambda_l|, |lambda_j|), where the gradient is not defined and the
+ * pair l is left out; SLA_ERR_TIMEOUT when a barrier ran out), rel_res =
+ * the recursive ||r_j|| / ||b_j||, true_rel_res = ||b_j - (A - lambda_j I)
+ * y_j|| / ||b_j|| for the span(V)^perp part y_j.  b_j with ||b_j|| <=
+ * 64 eps ||gV_j|| (gV_j in span(V), or k = n) is rounding noise: y_j = 0,
+ * no iteration, both residuals reported as 0.
+ * Returns SLA_ERR_CUDA when the device has no cooperative launch.
+ * Workspace: sla_workspace_size(SLA_WS_EIG_ADJOINT, n, nnz, k, &bytes). */
+int32_t sla_eig_vector_adjoint(const sla_csr* A, const double* val, int32_t k,
+                               const double* lambda, const double* V,
+                               const double* gV, double* mu,
+                               const sla_opts* opts, sla_info* info,
+                               void* ws, size_t ws_bytes, void* stream);
+
+/* Eigenvector part of the gradient on the pattern: grad_val[e] = -sum_j
+ * mu[row_e][j] V[col_e][j] (accumulate = 1: subtracted from grad_val
+ * instead of overwriting it).  mu, V [n][k] row-major device arrays.
+ * Asynchronous on `stream`. */
+int32_t sla_eig_vector_grad_values(const sla_csr* A, int32_t k,
+                                   const double* mu, const double* V,
+                                   double* grad_val, int32_t accumulate,
+                                   void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Linear adjoint backward (Eq. 2-3)                                     */

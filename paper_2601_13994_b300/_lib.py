@@ -41,6 +41,7 @@ SLA_WS_CG_MULTI = 8
 SLA_WS_SPMV_MERGE = 9
 SLA_WS_CG_PIPELINED = 10
 SLA_WS_EIGSH = 11
+SLA_WS_EIG_ADJOINT = 12
 SLA_EIG_MAX_K = 8
 SLA_SPMV_ROWS = 0
 SLA_SPMV_MERGE = 1
@@ -132,6 +133,11 @@ def lib() -> ctypes.CDLL:
             L.sla_eigsh.restype = i32
             L.sla_eig_grad_values.argtypes = [ctypes.POINTER(SlaCsr), i32, P, P, P, P]
             L.sla_eig_grad_values.restype = i32
+            L.sla_eig_vector_adjoint.argtypes = [ctypes.POINTER(SlaCsr), P, i32, P, P, P, P,
+                                                 ctypes.POINTER(SlaOpts), P, P, ctypes.c_size_t, P]
+            L.sla_eig_vector_adjoint.restype = i32
+            L.sla_eig_vector_grad_values.argtypes = [ctypes.POINTER(SlaCsr), i32, P, P, P, i32, P]
+            L.sla_eig_vector_grad_values.restype = i32
             L.sla_grad_values.argtypes = [ctypes.POINTER(SlaCsr), P, P, P, P]
             L.sla_grad_values.restype = i32
             L.sla_adjoint_backward.argtypes = [ctypes.POINTER(SlaCsr), ctypes.POINTER(SlaCsrT), P, P, P, P,

@@ -41,6 +41,7 @@
 // done, further launches return at once.  S and AS are row-major [n][3k]
 // and double-buffered (the update reads one pair and writes the other).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "sla_internal.cuh"
@@ -754,10 +755,18 @@ __global__ void __launch_bounds__(kEigThreads) eig_update_kernel(EigPtrs P) {
   }
 }
 
+// (|x|, index) order of the sign rule: the larger magnitude, on a tie the
+// smaller index -- a total order, so any reduction order picks the same entry.
+__device__ __forceinline__ bool eig_sign_better(double a, int ia, double b, int ib) {
+  return a > b || (a == b && ia < ib);
+}
+
 // Final: lambda, the true residuals ||A x_i - theta_i x_i|| / (|theta_i|
 // ||x_i||) of the k wanted pairs from a fresh product (AS[cur ^ 1][:, 0:kb]),
-// the info record, and V = the first k columns of X with unit norm.  Two
-// launches: sums, then the scaled copy.
+// the info record, and V = the first k columns of X with unit norm and the
+// sign that makes each column's largest-magnitude entry positive (the first
+// such entry on a tie), so that V is a smooth function of A near a simple
+// eigenvalue.  Two launches: sums and the sign entries, then the scaled copy.
 __global__ void __launch_bounds__(kEigThreads) eig_final_kernel(EigPtrs P, int phase) {
   const EigDesc& d = *P.d;
   EigState* st = P.st;
@@ -776,9 +785,13 @@ __global__ void __launch_bounds__(kEigThreads) eig_final_kernel(EigPtrs P, int p
       for (int j = 0; j < k; ++j) d.V[(size_t)i * k + j] = X[(size_t)i * ld + j] * snorm[j];
     return;
   }
-  double rr[kEigMaxK], xx[kEigMaxK];
+  double rr[kEigMaxK], xx[kEigMaxK], bx[kEigMaxK];
+  int bi[kEigMaxK];
 #pragma unroll
-  for (int j = 0; j < kEigMaxK; ++j) rr[j] = xx[j] = 0.0;
+  for (int j = 0; j < kEigMaxK; ++j) {
+    rr[j] = xx[j] = bx[j] = 0.0;
+    bi[j] = INT_MAX;
+  }
   if (!st->bad) {
     for (int i = blockIdx.x * blockDim.x + tid; i < n; i += gridDim.x * blockDim.x) {
 #pragma unroll
@@ -788,11 +801,34 @@ __global__ void __launch_bounds__(kEigThreads) eig_final_kernel(EigPtrs P, int p
           const double rj = AX[(size_t)i * ld + j] - P.theta[j] * xj;
           rr[j] = fma(rj, rj, rr[j]);
           xx[j] = fma(xj, xj, xx[j]);
+          if (eig_sign_better(fabs(xj), i, fabs(bx[j]), bi[j])) {
+            bx[j] = xj;
+            bi[j] = i;
+          }
         }
       }
     }
   }
   const int w = tid >> 5, lane = tid & 31;
+  // the sign entry of each column: warp, then block (partials after upart's)
+  __shared__ double s_bx[kEigMaxK][kEigThreads / 32];
+  __shared__ int s_bi[kEigMaxK][kEigThreads / 32];
+  double* spart = P.upart + ((size_t)gridDim.x + 1) * 2 * kEigMaxB;
+#pragma unroll
+  for (int j = 0; j < kEigMaxK; ++j) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ox = __shfl_xor_sync(0xffffffffu, bx[j], o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi[j], o);
+      if (eig_sign_better(fabs(ox), oi, fabs(bx[j]), bi[j])) {
+        bx[j] = ox;
+        bi[j] = oi;
+      }
+    }
+    if (lane == 0) {
+      s_bx[j][w] = bx[j];
+      s_bi[j][w] = bi[j];
+    }
+  }
 #pragma unroll
   for (int j = 0; j < kEigMaxK; ++j) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -809,13 +845,37 @@ __global__ void __launch_bounds__(kEigThreads) eig_final_kernel(EigPtrs P, int p
     double sum = 0.0;
     for (int q = 0; q < kEigThreads / 32; ++q) sum += red[tid * (kEigThreads / 32) + q];
     P.upart[(size_t)blockIdx.x * 2 * kEigMaxB + tid] = sum;
+  } else if (tid >= 32 && tid < 32 + k) {
+    const int j = tid - 32;
+    double x = s_bx[j][0];
+    int ix = s_bi[j][0];
+    for (int q = 1; q < kEigThreads / 32; ++q)
+      if (eig_sign_better(fabs(s_bx[j][q]), s_bi[j][q], fabs(x), ix)) {
+        x = s_bx[j][q];
+        ix = s_bi[j][q];
+      }
+    spart[(size_t)blockIdx.x * 2 * kEigMaxK + 2 * j] = x;
+    spart[(size_t)blockIdx.x * 2 * kEigMaxK + 2 * j + 1] = (double)ix;
   }
   if (!last_block_arrive(&st->ticket_fin, &s_last)) return;
+  __shared__ double s_sign[kEigMaxK];
   if (tid < 2 * k) {
     double sum = 0.0;
 #pragma unroll 8
     for (int b = 0; b < (int)gridDim.x; ++b) sum += __ldcg(P.upart + (size_t)b * 2 * kEigMaxB + tid);
     red[tid] = sum;
+  } else if (tid >= 32 && tid < 32 + k) {
+    const int j = tid - 32;
+    double x = 0.0, ix = 2147483647.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      const double bx2 = __ldcg(spart + (size_t)b * 2 * kEigMaxK + 2 * j);
+      const double bi2 = __ldcg(spart + (size_t)b * 2 * kEigMaxK + 2 * j + 1);
+      if (fabs(bx2) > fabs(x) || (fabs(bx2) == fabs(x) && bi2 < ix)) {
+        x = bx2;
+        ix = bi2;
+      }
+    }
+    s_sign[j] = x < 0.0 ? -1.0 : 1.0;
   }
   __syncthreads();
   if (tid == 0) {
@@ -831,8 +891,8 @@ __global__ void __launch_bounds__(kEigThreads) eig_final_kernel(EigPtrs P, int p
         const double r2 = red[2 * j], x2 = red[2 * j + 1];
         const double nx = sqrt(x2);
         worst = fmax(worst, sqrt(r2) / (fabs(P.theta[j]) * nx));
-        // 1 / ||x_j|| for the copy, after the partials
-        P.upart[(size_t)gridDim.x * 2 * kEigMaxB + j] = 1.0 / nx;
+        // sign / ||x_j|| for the copy, after the partials
+        P.upart[(size_t)gridDim.x * 2 * kEigMaxB + j] = s_sign[j] / nx;
         d.lambda[j] = P.theta[j];
       }
       inf.status = st->status;
@@ -889,7 +949,8 @@ size_t eig_ws_bytes(int n, int k, int* gram_blocks, int* upd_blocks) {
   o += 4 * al256(sizeof(double) * nn * 3 * kb);         // S[2], AS[2]
   o += al256(sizeof(double) * (size_t)gb * 2 * kEigPairs);
   o += al256(sizeof(double) * 2 * kEigPairs);
-  o += al256(sizeof(double) * ((size_t)ub + 1) * 2 * kEigMaxB);
+  // update partials + the totals, then the final kernel's sign partials
+  o += al256(sizeof(double) * (((size_t)ub + 1) * 2 * kEigMaxB + (size_t)ub * 2 * kEigMaxK));
   o += al256(sizeof(double) * kEigMaxM * kEigMaxB);
   o += al256(sizeof(double) * kEigMaxM);
   return o;
@@ -928,7 +989,8 @@ extern "C" int32_t sla_eigsh(const sla_csr* A, const double* val, int32_t k, dou
   }
   P.gpart = (double*)p;        p += al256(sizeof(double) * (size_t)gb * 2 * kEigPairs);
   P.gtot = (double*)p;         p += al256(sizeof(double) * 2 * kEigPairs);
-  P.upart = (double*)p;        p += al256(sizeof(double) * ((size_t)ub + 1) * 2 * kEigMaxB);
+  P.upart = (double*)p;
+  p += al256(sizeof(double) * (((size_t)ub + 1) * 2 * kEigMaxB + (size_t)ub * 2 * kEigMaxK));
   P.C = (double*)p;            p += al256(sizeof(double) * kEigMaxM * kEigMaxB);
   P.theta = (double*)p;
   EigDesc d = {};

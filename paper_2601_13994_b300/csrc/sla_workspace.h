@@ -161,6 +161,9 @@ size_t multi_ws_bytes(int n, int k);
 // LOBPCG (sla_eig.cu): k = block size; optional outputs: grid sizes.
 size_t eig_ws_bytes(int n, int k, int* gram_blocks, int* upd_blocks);
 
+// Eigenvector adjoint (sla_eig_adjoint.cu): k pairs.
+size_t eigvec_ws_bytes(int n, int k);
+
 // Merge-path SpMV carries (sla_spmv_merge.cu).
 size_t spmv_merge_ws_bytes(int n, long long nnz);
 
@@ -190,6 +193,10 @@ inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
     case SLA_WS_EIGSH:
       if (batch < 1 || batch > SLA_EIG_MAX_K) return false;
       *out = eig_ws_bytes(n, batch, nullptr, nullptr);
+      return true;
+    case SLA_WS_EIG_ADJOINT:
+      if (batch < 1 || batch > SLA_EIG_MAX_K) return false;
+      *out = eigvec_ws_bytes(n, batch);
       return true;
     case SLA_WS_BICGSTAB:
       *out = bicg_ws_bytes(n, nnz);

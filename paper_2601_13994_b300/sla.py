@@ -431,6 +431,43 @@ def eig_grad_values(A: CSRMatrix, V: torch.Tensor, g: torch.Tensor) -> torch.Ten
     return out
 
 
+def eig_vector_adjoint(A: CSRMatrix, val: torch.Tensor, lam: torch.Tensor, V: torch.Tensor, gV: torch.Tensor, *,
+                       rtol: float = 1e-10, atol: float = 0.0, max_iter: int | None = None,
+                       precond: str = "jacobi"):
+    """The deflated solve of Sec. 3.2 for each of the k pairs: mu [n, k],
+    column j with (A - lam_j I) mu_j = (I - v_j v_j^T) gV_j, v_j^T mu_j = 0.
+    Returns (mu, SolveInfo with k records)."""
+    k = V.shape[1]
+    _need(val, torch.float64, A.device, "val", A.nnz)
+    for t, name, m in ((lam, "lambda", k), (V, "V", A.n * k), (gV, "gV", A.n * k)):
+        _need(t, torch.float64, A.device, name, m)
+    mu = torch.empty((A.n, k), dtype=torch.float64, device=A.device)
+    mi = max_iter if max_iter is not None else 10 * A.n
+    o = L.SlaOpts(float(rtol), float(atol), int(mi), 0, _PRECOND[precond], 0, 0)
+    info = torch.empty((k, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
+    ws = workspace(L.SLA_WS_EIG_ADJOINT, A.n, A.nnz, k, A.device)
+    L.check("sla_eig_vector_adjoint", L.lib().sla_eig_vector_adjoint(
+        ctypes.byref(A.c), val.data_ptr(), k, lam.data_ptr(), V.data_ptr(), gV.data_ptr(), mu.data_ptr(),
+        ctypes.byref(o), info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(A.device)))
+    return mu, SolveInfo(info)
+
+
+def eig_vector_grad_values(A: CSRMatrix, mu: torch.Tensor, V: torch.Tensor, out: torch.Tensor | None = None):
+    """Eigenvector part of dL/dA on the pattern: -sum_j mu[row_e, j]
+    V[col_e, j], added to `out` when given."""
+    k = V.shape[1]
+    _need(V, torch.float64, A.device, "V", A.n * k)
+    _need(mu, torch.float64, A.device, "mu", A.n * k)
+    acc = out is not None
+    if out is None:
+        out = torch.empty(A.nnz, dtype=torch.float64, device=A.device)
+    else:
+        _need(out, torch.float64, A.device, "out", A.nnz)
+    L.check("sla_eig_vector_grad_values", L.lib().sla_eig_vector_grad_values(
+        ctypes.byref(A.c), k, mu.data_ptr(), V.data_ptr(), out.data_ptr(), int(acc), _stream_ptr(A.device)))
+    return out
+
+
 class _Eigsh(torch.autograd.Function):
     @staticmethod
     def forward(ctx, val, A, k, opts, box):
@@ -451,35 +488,48 @@ class _Eigsh(torch.autograd.Function):
                                                ws.numel(), _stream_ptr(A.device)))
         box["info"] = SolveInfo(info)
         ctx.A = A
-        ctx.save_for_backward(V)
-        ctx.mark_non_differentiable(V)
+        ctx.opts = opts
+        ctx.box = box
+        ctx.save_for_backward(val, lam, V)
         return lam, V
 
     @staticmethod
     def backward(ctx, glam, gV):
-        (V,) = ctx.saved_tensors
-        if gV is not None and bool(gV.abs().max() > 0):
-            raise NotImplementedError("eigenvector gradients are not provided: the eigenvalue path "
-                                      "differentiates the eigenvalues (Hellmann-Feynman, Eq. 4)")
+        val, lam, V = ctx.saved_tensors
+        if glam is None:
+            glam = torch.zeros_like(lam)
         gval = eig_grad_values(ctx.A, V, glam.contiguous().to(torch.float64))
+        if gV is not None and bool(gV.abs().max() > 0):
+            mu, info = eig_vector_adjoint(ctx.A, val.detach(), lam, V, gV.contiguous().to(torch.float64),
+                                          rtol=ctx.opts["adjoint_rtol"], precond=ctx.opts["precond"])
+            ctx.box["adjoint_info"] = info
+            st = np.atleast_1d(info.status)
+            if (st != L.SLA_OK).any():
+                raise SolveError("eigsh backward: the deflated eigenvector solve ended with %s"
+                                 % info.status_name)
+            eig_vector_grad_values(ctx.A, mu, V, out=gval)
         return gval, None, None, None, None
 
 
 def eigsh(A: CSRMatrix, val: torch.Tensor, k: int = 6, *, tol: float = 1e-8, max_iter: int | None = None,
-          precond: str = "jacobi", v0: torch.Tensor | None = None, strict: bool | None = True):
+          precond: str = "jacobi", v0: torch.Tensor | None = None, strict: bool | None = True,
+          adjoint_rtol: float = 1e-10):
     """The k smallest eigenpairs of SPD A by LOBPCG (Sec. 3.3; Knyazev 2001)
     with the Jacobi preconditioner (k <= 8; max_iter defaults to 20000
-    iterations).  Returns (lambda [k] ascending, V [n, k] unit columns,
-    SolveInfo).  lambda is differentiable w.r.t. val
-    by the Hellmann-Feynman gradient v_i v_j on the pattern (Eq. 4; simple
-    eigenvalues); V carries no gradient.  strict=True raises on a failed
+    iterations).  Returns (lambda [k] ascending, V [n, k] unit columns, each
+    with its largest-magnitude entry positive, SolveInfo).  Both are
+    differentiable w.r.t. val (simple eigenvalues): lambda by the
+    Hellmann-Feynman gradient v_i v_j on the pattern (Eq. 4), V by one
+    deflated solve per pair (sla_eig_vector_adjoint, to adjoint_rtol; a
+    failed solve raises SolveError).  strict=True raises on a failed
     solve, False warns, None skips the check."""
     if not 1 <= k <= L.SLA_EIG_MAX_K:
         raise ValueError("k must be in 1..%d" % L.SLA_EIG_MAX_K)
     if precond not in _PRECOND:
         raise ValueError("precond must be one of %s" % sorted(_PRECOND))
     box = {}
-    lam, V = _Eigsh.apply(val, A, int(k), {"tol": tol, "max_iter": max_iter, "precond": precond, "v0": v0}, box)
+    lam, V = _Eigsh.apply(val, A, int(k), {"tol": tol, "max_iter": max_iter, "precond": precond, "v0": v0,
+                                           "adjoint_rtol": adjoint_rtol}, box)
     info = box["info"]
     if strict is not None:
         _check_info(info, "eigsh", strict)
@@ -571,8 +621,9 @@ class SparseTensor:
         return spmv(self.A, self.csr_values().detach(), x.contiguous())
 
     def eigsh(self, k: int = 6, **kw):
-        """The k smallest eigenpairs (LOBPCG); eigenvalues differentiable
-        w.r.t. the COO values (Eq. 4)."""
+        """The k smallest eigenpairs (LOBPCG); eigenvalues (Eq. 4) and
+        eigenvectors (one deflated solve per pair) differentiable w.r.t. the
+        COO values."""
         return eigsh(self.A, self.csr_values(), k, **kw)
 
 

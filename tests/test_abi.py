@@ -261,3 +261,36 @@ def test_eigsh_arguments_rejected_without_launch():
                          None) == L.SLA_ERR_INVALID
     assert lib.sla_eig_grad_values(ctypes.byref(A), 0, fake, fake, fake, None) == L.SLA_ERR_INVALID
     assert lib.sla_eig_grad_values(ctypes.byref(A), 9, fake, fake, fake, None) == L.SLA_ERR_INVALID
+
+
+def test_eig_vector_adjoint_arguments_rejected_without_launch():
+    """sla_eig_vector_adjoint / sla_eig_vector_grad_values argument checks
+    (before any launch) and the workspace kind's range."""
+    lib = L.lib()
+    fake = ctypes.c_void_p(0x1000)
+    ws = ctypes.c_void_p(0x100000)
+    n = 100
+    A = L.SlaCsr(n, 300, fake, fake)
+    need = L.workspace_size(L.SLA_WS_EIG_ADJOINT, n, 300, 6)
+    assert need >= 3 * 8 * n * 6
+    for kb in (0, 9):
+        with pytest.raises(L.SlaError):
+            L.workspace_size(L.SLA_WS_EIG_ADJOINT, n, 300, kb)
+    ok = L.SlaOpts(1e-10, 0.0, 100, 0, 1, 0, 0)
+
+    def call(k=6, opts=ok, lam=fake, V=fake, gV=fake, mu=fake, w=ws, nb=need):
+        return lib.sla_eig_vector_adjoint(ctypes.byref(A), fake, k, lam, V, gV, mu, ctypes.byref(opts), fake,
+                                          w, nb, None)
+    for k in (0, 9, n + 1):
+        assert call(k=k) == L.SLA_ERR_INVALID
+    for bad in (L.SlaOpts(-1.0, 0.0, 100, 0, 1, 0, 0), L.SlaOpts(1e-8, -1.0, 100, 0, 1, 0, 0),
+                L.SlaOpts(1e-8, 0.0, -1, 0, 1, 0, 0), L.SlaOpts(1e-8, 0.0, 100, 0, 2, 0, 0),
+                L.SlaOpts(1e-8, 0.0, 100, 0, 1, 1, 0), L.SlaOpts(1e-8, 0.0, 100, 0, 1, 0, 1)):
+        assert call(opts=bad) == L.SLA_ERR_INVALID
+    for kw in ({"lam": None}, {"V": None}, {"gV": None}, {"mu": None}):
+        assert call(**kw) == L.SLA_ERR_INVALID
+    assert call(nb=need - 256) == L.SLA_ERR_WORKSPACE
+    assert call(w=ctypes.c_void_p(0x100010)) == L.SLA_ERR_WORKSPACE
+    for k, acc in ((0, 0), (9, 0), (6, 2)):
+        assert lib.sla_eig_vector_grad_values(ctypes.byref(A), k, fake, fake, fake, acc,
+                                              None) == L.SLA_ERR_INVALID
