@@ -196,8 +196,28 @@ def _profile_eigsh(dev, max_iter):
     return {"iters": info.iters, "status": info.status}
 
 
+def _profile_eigvec(dev, max_iter):
+    """The eigenvector adjoint of the 6 smallest pairs of the 2D 128^2
+    variable-coefficient system (sigma = 1): LOBPCG to 1e-8 (20000
+    iterations at most), then one cooperative launch of the six deflated
+    solves, at most max_iter iterations, for a random dL/dV (seed 5)."""
+    import torch
+
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import sla
+    rp, c, v = I.diffusion2d_random(128, 11, 1.0)
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    vt = torch.from_numpy(v).to(dev)
+    lam, V, _ = sla.eigsh(A, vt, 6, tol=1e-8, max_iter=20000, strict=None)
+    gV = torch.from_numpy(np.random.default_rng(5).standard_normal((len(rp) - 1, 6))).to(dev)
+    mu, info = sla.eig_vector_adjoint(A, vt, lam, V, gV, rtol=1e-10, max_iter=max_iter)
+    torch.cuda.synchronize()
+    return {"iters": [int(x) for x in np.atleast_1d(info.iters)], "status": [int(x) for x in np.atleast_1d(info.status)]}
+
+
 PROFILE_ROWS = {
     "eigsh_2d_128": _profile_eigsh,
+    "eigvec_adjoint_2d_128": _profile_eigvec,
     "coop_2d_512": lambda dev, mi: _profile_2d_512(dev, mi, False),
     "pipe_2d_512": lambda dev, mi: _profile_2d_512(dev, mi, True),
     "bicgstab_convdiff3d_128": _profile_bicgstab,
@@ -428,8 +448,10 @@ def eigen_row(dev, N=128, k=6):
     """Sec. 3.2 / Tab. 5 eigenvalue path: the 6 smallest eigenpairs of the
     2D 128^2 variable-coefficient system (sigma = 1) by LOBPCG with the
     Jacobi preconditioner to relative residual 1e-8, then the Hellmann-
-    Feynman gradient of sum(lambda) on the pattern.  Median of 3 after one
-    warm-up (the call synchronises its stream)."""
+    Feynman gradient of sum(lambda) on the pattern, and the eigenvector
+    adjoint for a random dL/dV (the six deflated solves to 1e-10 in one
+    cooperative launch, then -mu v^T on the pattern).  Median of 3 after one
+    warm-up (the eigsh call synchronises its stream)."""
     import torch
 
     from paper_2601_13994_b300 import inputs as I
@@ -440,9 +462,18 @@ def eigen_row(dev, N=128, k=6):
     ms, (lam, V, info) = _time(lambda: sla.eigsh(A, vt, k, tol=1e-8))
     g = torch.ones(k, dtype=torch.float64, device=dev)
     gms, _ = _time(lambda: sla.eig_grad_values(A, V, g), reps=5)
+    gV = torch.from_numpy(np.random.default_rng(5).standard_normal((len(rp) - 1, k))).to(dev)
+
+    def vec_backward():
+        mu, inf = sla.eig_vector_adjoint(A, vt, lam, V, gV, rtol=1e-10)
+        return sla.eig_vector_grad_values(A, mu, V), inf
+    vms, (_, vinfo) = _time(vec_backward)
     return {"n": len(rp) - 1, "k": k, "s": ms / 1e3, "iters": info.iters, "status": info.status,
             "us_per_iter": 1e3 * ms / max(info.iters, 1), "true_rel_res": info.true_rel_res,
-            "lambda": [float(x) for x in lam.cpu()], "grad_ms": gms}
+            "lambda": [float(x) for x in lam.cpu()], "grad_ms": gms,
+            "eigvec_adjoint_ms": vms, "eigvec_adjoint_iters": [int(x) for x in np.atleast_1d(vinfo.iters)],
+            "eigvec_adjoint_status": [int(x) for x in np.atleast_1d(vinfo.status)],
+            "eigvec_adjoint_us_per_iter": 1e3 * vms / max(int(np.max(vinfo.iters)), 1)}
 
 
 def nonlinear_row(dev, N=512):
