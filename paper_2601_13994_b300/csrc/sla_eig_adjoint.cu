@@ -13,8 +13,9 @@
 // y_j is found by CG on P (A - lambda_j I) P with P = I - V V^T and the
 // preconditioner P D^{-1} P (D = diag A, or I).
 //
-// One cooperative launch solves all k systems together: 8 lanes per row
-// (lane j = pair j), three grid barriers per iteration (the SpMV gathers p
+// One cooperative launch solves all k systems together: a group of lanes
+// per row (lane j = pair j; 1, 2, 4 or 8 lanes, the kernel is instantiated
+// per k), three grid barriers per iteration (the SpMV gathers p
 // at other blocks' rows; two reductions of k projections onto V plus two
 // inner products per pair).  Every block adds the partial sums in the same
 // order, so every block takes the same per-pair decisions.
@@ -31,12 +32,14 @@ namespace {
 
 constexpr int kEvK = SLA_EIG_MAX_K;
 constexpr int kEvThreads = 512;
-constexpr int kEvLanes = 8;                      // one lane per pair
-constexpr int kEvRows = kEvThreads / kEvLanes;   // rows a block takes per pass
+constexpr int kEvLanes = 8;                      // stride of a slot in the partials
 constexpr int kEvNv = kEvK + 2;                  // per lane: k projections, two sums
 constexpr int kEvS0 = kEvK, kEvS1 = kEvK + 1;    // slots of the two sums
 constexpr int kEvPart = kEvNv * kEvLanes;        // doubles of one block partial
-constexpr int kEvChunks = kEvThreads / kEvPart;  // threads per value in the totals
+constexpr int kEvChunks = 16;                    // most block ranges in the totals
+
+// Lanes per row for k pairs (a power of two, so that a warp holds whole rows).
+__host__ __device__ constexpr int ev_lanes(int k) { return k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : 8; }
 constexpr int kEvMaxGrid = 512;
 // |lambda_l - lambda_j| <= this * max(|lambda_l|, |lambda_j|): a repeated
 // eigenvalue, where the eigenvector gradient is not defined.
@@ -76,41 +79,59 @@ struct EvSmem {
   int flag;
 };
 
-// Block sums of acc[slot] per pair lane: out[slot * 8 + pair], fixed order
-// (the four rows of a warp by two butterflies, then the warps in order).
+// The live values of a reduction for k pairs: slots 0..k-1 (projections)
+// and the two sums, lanes 0..k-1; live index t -> partial index.
+template <int K>
+__device__ __forceinline__ int ev_live(int t) {
+  const int v = t / K, l = t % K;
+  return (v < K ? v : kEvK + (v - K)) * kEvLanes + l;
+}
+
+// Block sums of acc[slot] per pair lane: out[slot * 8 + pair] for the live
+// values, fixed order (the rows of a warp by butterflies, then the warps in
+// order).
+template <int K>
 __device__ __forceinline__ void ev_block_sums(double (&acc)[kEvNv], EvSmem& sm, double* out) {
+  constexpr int L = ev_lanes(K);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int v = 0; v < kEvNv; ++v) {
+    if (v >= K && v < kEvK) continue;  // projection slots beyond k
     double a = acc[v];
-    a += __shfl_xor_sync(0xffffffffu, a, 8);
-    a += __shfl_xor_sync(0xffffffffu, a, 16);
-    if (lane < kEvLanes) sm.red[warp][v * kEvLanes + lane] = a;
+#pragma unroll
+    for (int o = L; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane < K) sm.red[warp][v * kEvLanes + lane] = a;
   }
   __syncthreads();
-  if (threadIdx.x < kEvPart) {
+  if (threadIdx.x < (K + 2) * K) {
+    const int idx = ev_live<K>(threadIdx.x);
     double s = 0.0;
-    for (int w = 0; w < kEvThreads / 32; ++w) s += sm.red[w][threadIdx.x];
-    out[threadIdx.x] = s;
+    for (int w = 0; w < kEvThreads / 32; ++w) s += sm.red[w][idx];
+    out[idx] = s;
   }
 }
 
-// sm.tot = the sum over the G block partials, in the same order in every
-// block (kEvChunks contiguous ranges, then the ranges in order).
+// sm.tot = the sum over the G block partials of the live values, in the
+// same order in every block (contiguous ranges of blocks, then the ranges
+// in order).
+template <int K>
 __device__ __forceinline__ void ev_totals(const double* part, int G, EvSmem& sm) {
+  constexpr int NL = (K + 2) * K;
+  constexpr int CH = kEvThreads / NL < kEvChunks ? kEvThreads / NL : kEvChunks;
   const int t = threadIdx.x;
-  if (t < kEvChunks * kEvPart) {
-    const int v = t % kEvPart, c = t / kEvPart;
-    const int b0 = (int)((long long)G * c / kEvChunks), b1 = (int)((long long)G * (c + 1) / kEvChunks);
+  if (t < CH * NL) {
+    const int idx = ev_live<K>(t % NL), c = t / NL;
+    const int b0 = (int)((long long)G * c / CH), b1 = (int)((long long)G * (c + 1) / CH);
     double s = 0.0;
-    for (int b = b0; b < b1; ++b) s += __ldcg(part + (size_t)b * kEvPart + v);
-    sm.chunk[c][v] = s;
+    for (int b = b0; b < b1; ++b) s += __ldcg(part + (size_t)b * kEvPart + idx);
+    sm.chunk[c][idx] = s;
   }
   __syncthreads();
-  if (t < kEvPart) {
+  if (t < NL) {
+    const int idx = ev_live<K>(t);
     double s = 0.0;
-    for (int c = 0; c < kEvChunks; ++c) s += sm.chunk[c][t];
-    sm.tot[t] = s;
+    for (int c = 0; c < CH; ++c) s += sm.chunk[c][idx];
+    sm.tot[idx] = s;
   }
   __syncthreads();
 }
@@ -120,11 +141,13 @@ __global__ void ev_arm_kernel(unsigned* count, int* err) {
   *err = 0;
 }
 
+template <int K>
 __global__ void __launch_bounds__(kEvThreads, 1) eigvec_adjoint_kernel(EvArgs a) {
   __shared__ EvSmem sm;
   GridSync gs{a.count, 0u};
-  const int G = gridDim.x, k = a.k, n = a.n;
-  const int j = threadIdx.x & (kEvLanes - 1), slot = threadIdx.x / kEvLanes;
+  constexpr int k = K, L = ev_lanes(K), kEvRows = kEvThreads / L;
+  const int G = gridDim.x, n = a.n;
+  const int j = threadIdx.x & (L - 1), slot = threadIdx.x / L;
   const bool on = j < k;
   const double lam_j = on ? __ldg(a.lambda + j) : 0.0;
   const size_t ks = (size_t)k;
@@ -160,10 +183,10 @@ __global__ void __launch_bounds__(kEvThreads, 1) eigvec_adjoint_kernel(EvArgs a)
       acc[kEvS0] = fma(g, g, acc[kEvS0]);
     }
   }
-  ev_block_sums(acc, sm, a.part1 + (size_t)blockIdx.x * kEvPart);
+  ev_block_sums<K>(acc, sm, a.part1 + (size_t)blockIdx.x * kEvPart);
   if (!sync()) return;
-  ev_totals(a.part1, G, sm);
-  if (threadIdx.x < kEvLanes) {
+  ev_totals<K>(a.part1, G, sm);
+  if (threadIdx.x < K) {
     const int jj = threadIdx.x;
     for (int l = 0; l < kEvK; ++l) sm.C[l][jj] = sm.tot[l * kEvLanes + jj];
     const bool bad = sm.tot[kEvS1 * kEvLanes] > 0.0;
@@ -193,13 +216,13 @@ __global__ void __launch_bounds__(kEvThreads, 1) eigvec_adjoint_kernel(EvArgs a)
     acc[kEvS0] = fma(b, u, acc[kEvS0]);
     acc[kEvS1] = fma(b, b, acc[kEvS1]);
   }
-  ev_block_sums(acc, sm, a.part2 + (size_t)blockIdx.x * kEvPart);
+  ev_block_sums<K>(acc, sm, a.part2 + (size_t)blockIdx.x * kEvPart);
   if (!sync()) return;
 
   for (int it = 0;; ++it) {
     // decisions from (V^T u, r.u, r.r); z = u - V (V^T u), p = z + beta p
-    ev_totals(a.part2, G, sm);
-    if (threadIdx.x < kEvLanes) {
+    ev_totals<K>(a.part2, G, sm);
+    if (threadIdx.x < K) {
       const int jj = threadIdx.x;
       const double ru = sm.tot[kEvS0 * kEvLanes + jj], rr = sm.tot[kEvS1 * kEvLanes + jj];
       sm.rr[jj] = rr;
@@ -259,12 +282,12 @@ __global__ void __launch_bounds__(kEvThreads, 1) eigvec_adjoint_kernel(EvArgs a)
         if (l < k) acc[l] = fma(__ldg(vi + l), qv, acc[l]);
       acc[kEvS0] = fma(pi, qv, acc[kEvS0]);
     }
-    ev_block_sums(acc, sm, a.part1 + (size_t)blockIdx.x * kEvPart);
+    ev_block_sums<K>(acc, sm, a.part1 + (size_t)blockIdx.x * kEvPart);
     if (!sync()) return;
 
     // alpha = rho / p.q; y += alpha p, r -= alpha P q; sums for the next step
-    ev_totals(a.part1, G, sm);
-    if (threadIdx.x < kEvLanes) {
+    ev_totals<K>(a.part1, G, sm);
+    if (threadIdx.x < K) {
       const int jj = threadIdx.x;
       double al = 0.0;
       if (sm.active[jj]) {
@@ -300,7 +323,7 @@ __global__ void __launch_bounds__(kEvThreads, 1) eigvec_adjoint_kernel(EvArgs a)
       acc[kEvS0] = fma(rv, u, acc[kEvS0]);
       acc[kEvS1] = fma(rv, rv, acc[kEvS1]);
     }
-    ev_block_sums(acc, sm, a.part2 + (size_t)blockIdx.x * kEvPart);
+    ev_block_sums<K>(acc, sm, a.part2 + (size_t)blockIdx.x * kEvPart);
     if (!sync()) return;
   }
 
@@ -318,9 +341,9 @@ __global__ void __launch_bounds__(kEvThreads, 1) eigvec_adjoint_kernel(EvArgs a)
     const double t = b - fma(-lam_j, a.mu[o], s);
     acc[kEvS1] = fma(t, t, acc[kEvS1]);
   }
-  ev_block_sums(acc, sm, a.part1 + (size_t)blockIdx.x * kEvPart);
+  ev_block_sums<K>(acc, sm, a.part1 + (size_t)blockIdx.x * kEvPart);
   if (!sync()) return;
-  ev_totals(a.part1, G, sm);
+  ev_totals<K>(a.part1, G, sm);
 
   // mu = y + sum_{l != j} C[l][j] / (lambda_l - lambda_j) v_l
   double coef[kEvK];
@@ -388,7 +411,20 @@ __global__ void eigvec_grad_kernel(int n, int k, const int* __restrict__ rowptr,
   }
 }
 
-int g_occ_ev[64] = {};
+int g_occ_ev[kEvK + 1][64] = {};
+
+const void* ev_kernel(int k) {
+  switch (k) {
+    case 1: return (const void*)eigvec_adjoint_kernel<1>;
+    case 2: return (const void*)eigvec_adjoint_kernel<2>;
+    case 3: return (const void*)eigvec_adjoint_kernel<3>;
+    case 4: return (const void*)eigvec_adjoint_kernel<4>;
+    case 5: return (const void*)eigvec_adjoint_kernel<5>;
+    case 6: return (const void*)eigvec_adjoint_kernel<6>;
+    case 7: return (const void*)eigvec_adjoint_kernel<7>;
+    default: return (const void*)eigvec_adjoint_kernel<8>;
+  }
+}
 
 struct EvLayout {
   size_t ctl, dinv, r, p, q, part1, part2, total;
@@ -433,9 +469,11 @@ extern "C" int32_t sla_eig_vector_adjoint(const sla_csr* A, const double* val, i
   if (ws == nullptr || ((uintptr_t)ws & 255u) != 0 || ws_bytes < Lw.total) return SLA_ERR_WORKSPACE;
   const int dev = current_device();
   if (dev < 0 || dev >= 64) return SLA_ERR_CUDA;
-  const int occ = coop_occupancy_of(dev, g_occ_ev, (const void*)eigvec_adjoint_kernel);
+  const void* fn = ev_kernel(k);
+  const int occ = coop_occupancy_of(dev, g_occ_ev[k], fn);
   if (occ < 1) return SLA_ERR_CUDA;  // no cooperative launch on this device
-  const long long want = ((long long)n + kEvRows - 1) / kEvRows;
+  const int rows = kEvThreads / ev_lanes(k);
+  const long long want = ((long long)n + rows - 1) / rows;
   const int grid = (int)std::max(1LL, std::min<long long>({want, (long long)num_sms(dev) * std::min(occ, 2),
                                                            (long long)kEvMaxGrid}));
   cudaStream_t s = (cudaStream_t)stream;
@@ -465,7 +503,7 @@ extern "C" int32_t sla_eig_vector_adjoint(const sla_csr* A, const double* val, i
   a.part2 = (double*)(w + Lw.part2);
   ev_arm_kernel<<<1, 1, 0, s>>>(a.count, a.err);
   void* args[] = {&a};
-  SLA_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)eigvec_adjoint_kernel, dim3(grid), dim3(kEvThreads), args,
+  SLA_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kEvThreads), args,
                                            0, s));
   ev_finish_kernel<<<1, 32, 0, s>>>(a.err, info, k);
   SLA_CUDA_TRY(cudaGetLastError());
