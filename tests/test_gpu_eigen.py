@@ -262,3 +262,31 @@ def test_eigsh_eigenvector_gradient_matches_oracle_and_fd():
         fd = (lp - lm) / (2 * eps)
         errs.append(abs(fd - float(g @ D[rows, c])) / abs(fd))
     assert max(errs) <= 1e-5, errs
+
+
+def test_coo_eigsh_eigenvector_gradient_with_duplicates():
+    """SparseTensor.eigsh from COO with some entries split into two
+    duplicates (summed on ingest): d L / d val of each duplicate equals the
+    oracle's gradient at the summed CSR entry, for L = sum gV_j^T v_j +
+    sum lambda_j."""
+    rp, c, v = I.diffusion2d_random(10, 41)
+    n, k = len(rp) - 1, 3
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    rng = np.random.default_rng(42)
+    dup = rng.choice(len(v), 40, replace=False)
+    r2 = np.concatenate([rows, rows[dup]])
+    c2 = np.concatenate([c, c[dup]])
+    v2 = np.concatenate([v, np.zeros(len(dup))])
+    v2[dup] *= 0.5
+    v2[len(v):] = v[dup] * 0.5
+    src = np.concatenate([np.arange(len(v)), dup])  # CSR entry of each COO entry
+    o = rng.permutation(len(v2))
+    r2, c2, v2, src = r2[o], c2[o], v2[o], src[o]
+    val = torch.from_numpy(v2).cuda().requires_grad_(True)
+    T = sla.SparseTensor(val, torch.from_numpy(r2.astype(np.int64)).cuda(),
+                         torch.from_numpy(c2.astype(np.int64)).cuda(), (n, n))
+    gV = rng.standard_normal((n, k))
+    lam, V, _ = T.eigsh(k, tol=1e-12, max_iter=20000, strict=None)
+    ((to_dev(gV) * V).sum() + lam.sum()).backward()
+    go = OE.eigen_loss_grad(rp, c, v, k, np.ones(k), gV)
+    assert np.abs(val.grad.cpu().numpy() - go[src]).max() <= 1e-7 * np.abs(go).max()
