@@ -773,8 +773,19 @@ def run_ours(args):
         e2e_ms = max_over_ranks(k0.elapsed_time(k1) / args.steps, world, dev)
         h2d = rp.nbytes + c.nbytes + v.nbytes + b.nbytes
         d2h = 8 * n + 24  # x and the info record
+        # the host-to-device copies alone (the link is shared with the other
+        # GPUs of the host, so their rate varies between machines and runs)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for d_t, h_t in ((d_rp, h_rp), (d_c, h_c), (d_v, h_v), (d_b, h_b)):
+            d_t.copy_(h_t, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        h2d_ms = c0.elapsed_time(c1)
         e2e = {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "iters": inf.iters}
+               "d2h_bytes_per_step": int(d2h), "iters": inf.iters,
+               "h2d_ms": h2d_ms, "h2d_gbs": h2d / (h2d_ms / 1e3) / 1e9}
 
     peak, peak_kind = measured_peaks()
     it = statistics.median(iters_all)
