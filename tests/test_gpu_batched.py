@@ -283,14 +283,16 @@ def test_full_size_shared_1024_systems_64():
 
 
 @pytest.mark.slow
-def test_full_size_fem_list_512():
+@pytest.mark.parametrize("config", [0, 64])
+def test_full_size_fem_list_512(config):
     """512 jittered, holed P1 FEM Laplacians with n log-uniform in [1e3, 5e4]
-    (+1e-3 I), rtol 1e-8, in one launch."""
+    (+1e-3 I), rtol 1e-8, in one launch; also with the team systems on the
+    pipelined PCG (config bit 64)."""
     mats = I.fem_list(512, seed0=2000)
     P = sla.CSRList([(rp, c) for rp, c, _ in mats])
     vals = np.concatenate([v for _, _, v in mats])
     bs = [I.rhs_uniform(len(rp) - 1, 3000 + s) for s, (rp, _, _) in enumerate(mats)]
-    x, info = sla.cg_batched_list(P, to_dev(vals), to_dev(np.concatenate(bs)), rtol=1e-8)
+    x, info = sla.cg_batched_list(P, to_dev(vals), to_dev(np.concatenate(bs)), rtol=1e-8, config=config)
     torch.cuda.synchronize()
     xh = x.cpu().numpy()
     assert (np.atleast_1d(info.status) == 0).all()
@@ -299,5 +301,13 @@ def test_full_size_fem_list_512():
         r = bs[s] - oracle.spmv(rp, c, v, xs[s])
         assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(bs[s])
     big = int(np.argmax([len(m[0]) for m in mats]))
-    _per_system_check([m[0] for m in mats], [m[1] for m in mats], [m[2] for m in mats], bs, xs, info, 1e-8,
-                      iters_tol=5, idx=[0, 1, big])
+    if config == 0:
+        _per_system_check([m[0] for m in mats], [m[1] for m in mats], [m[2] for m in mats], bs, xs, info,
+                          1e-8, iters_tol=5, idx=[0, 1, big])
+        return
+    # the team systems ran the pipelined PCG: against the oracle's pipelined PCG
+    its = np.atleast_1d(info.iters)
+    rp, c, v = mats[big]
+    assert int(rp[-1]) >= 32768
+    xo, io = oracle.pcg_pipelined(rp, c, v, bs[big], rtol=1e-8)
+    assert io["status"] == 0 and rel(xs[big], xo) <= 1e-7 and abs(int(its[big]) - io["iters"]) <= 5
