@@ -567,6 +567,80 @@ def test_mpnn_loss_zero_for_exact_factor_and_gradcheck():
     assert torch.autograd.gradcheck(f, ts, eps=1e-6, atol=1e-6, rtol=1e-5, fast_mode=True)
 
 
+def _mpnn_path3_case():
+    """A 3-node path graph and hand-chosen weights for which every step of the
+    network can be followed on paper (the design: scaled entries, three node
+    features, an input layer, three residual message-passing layers, the head
+    on tril(A), G = D^{-1/2} Gt)."""
+    # A = [[4, -2, 0], [-2, 4, -1], [0, -1, 4]]: d = 4 everywhere, so
+    # e_01 = e_10 = -2/4 = -0.5 and e_12 = e_21 = -1/4 = -0.25
+    rp = np.array([0, 2, 5, 7], np.int32)
+    c = np.array([0, 1, 0, 1, 2, 1, 2], np.int32)
+    v = np.array([4.0, -2.0, -2.0, 4.0, -1.0, -1.0, 4.0])
+    from oracle import mpnn
+    P = {k: np.zeros(s) for k, s in mpnn.param_shapes().items()}
+    W = mpnn.WIDTH
+    # input layer: h0 = relu(sum|e|), h1 = relu(sum e + 1), h2 = relu(deg/8)
+    P["W0"][0, 0] = 1.0
+    P["W0"][1, 1] = 1.0
+    P["b0"][1] = 1.0
+    P["W0"][2, 2] = 1.0
+    # layer 0: h3 += relu(-agg(h0)); layer 1: h4 += relu(-agg(h3));
+    # layer 2: h5 += relu(h1 + agg(h4) - 0.3)   (agg_i = sum_{j != i} e_ij h_j)
+    P["W_0"][3, W + 0] = -1.0
+    P["W_1"][4, W + 3] = -1.0
+    P["W_2"][5, 1] = 1.0
+    P["W_2"][5, W + 4] = 1.0
+    P["c_2"][5] = -0.3
+    # head: P0 = h5, Q0 = h3, ue0 = -1, v0 = 1; Q1 = h0 + 0.1, v1 = -2;
+    # R0 = h4 - 0.1, vd0 = 1
+    P["Uh"][0, 5] = 1.0
+    P["Uh"][W + 0, 3] = 1.0
+    P["ue"][0] = -1.0
+    P["v"][0] = 1.0
+    P["Uh"][W + 1, 0] = 1.0
+    P["bh"][W + 1] = 0.1
+    P["v"][1] = -2.0
+    P["Uh"][2 * W + 0, 4] = 1.0
+    P["bh"][2 * W + 0] = -0.1
+    P["vd"][0] = 1.0
+    return rp, c, v, P
+
+
+def test_mpnn_forward_hand_worked_path3():
+    """The oracle's forward against values worked out by hand.
+
+    Features (sum|e|, sum e, deg/8): node 0 (0.5, -0.5, 1/8), node 1
+    (0.75, -0.75, 2/8), node 2 (0.25, -0.25, 1/8), so
+    h0 = (0.5, 0.75, 0.25), h1 = (0.5, 0.25, 0.75).
+    Layer 0, agg(h0) with messages from the neighbour j:
+      node 0: e_01 h0_1 = -0.5 * 0.75 = -0.375
+      node 1: e_10 h0_0 + e_12 h0_2 = -0.25 - 0.0625 = -0.3125
+      node 2: e_21 h0_1 = -0.25 * 0.75 = -0.1875      -> h3 = (0.375, 0.3125, 0.1875)
+    Layer 1, agg(h3): -0.15625, -0.1875 - 0.046875, -0.078125
+                                                     -> h4 = (0.15625, 0.234375, 0.078125)
+    Layer 2, agg(h4): -0.1171875, -0.078125 - 0.01953125, -0.05859375
+      h5 = relu(h1 + agg - 0.3) = (0.0828125, 0, 0.39140625)
+    Head, entry (1, 0): relu(h5_1 + h3_0 + 0.5) = 0.875, relu(h0_0 + 0.1) = 0.6,
+      theta = 0.875 - 2 * 0.6 = -0.325
+    entry (2, 1): relu(h5_2 + h3_1 + 0.25) = 0.95390625, relu(h0_1 + 0.1) = 0.85,
+      theta = 0.95390625 - 1.7 = -0.74609375
+    diagonal: theta_ii = relu(h4_i - 0.1) = (0.05625, 0.134375, 0)
+    G = D^{-1/2} Gt with D^{-1/2} = 1/2, CSR order (0,0) (1,0) (1,1) (2,1) (2,2).
+
+    A message taken from the row's own node instead of the neighbour, the
+    two sums of the features swapped, or the e_ij term of the head dropped
+    each changes at least one of these values by more than 0.01."""
+    from oracle import mpnn
+    rp, c, v, P = _mpnn_path3_case()
+    grp, gcol, gv = mpnn.forward(P, rp, c, v)
+    assert grp.tolist() == [0, 1, 3, 5]
+    assert gcol.tolist() == [0, 0, 1, 1, 2]
+    want = np.array([0.5 * math.exp(0.05625), 0.5 * -0.325, 0.5 * math.exp(0.134375),
+                     0.5 * -0.74609375, 0.5 * math.exp(0.0)])
+    assert np.allclose(gv.numpy(), want, rtol=1e-14, atol=1e-15)
+
+
 def test_mpnn_permutation_equivariance():
     from oracle import mpnn
     rp, c, v = I.diffusion2d_random(5, 3)
