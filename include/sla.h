@@ -596,6 +596,9 @@ int32_t sla_grad_values(const sla_csr* A, const double* lambda,
  * of A); its values are gathered into the workspace.
  * opts: tolerance of the adjoint solve relative to ||grad_x|| (use_x0 is
  * ignored: lambda starts at 0); *info receives the adjoint solve's record.
+ * grad_b must differ from x and grad_x (lambda is written into grad_b before
+ * the gradient pass reads x), and grad_val must overlap neither x nor
+ * grad_b: SLA_ERR_INVALID otherwise, nothing enqueued.
  * Workspace: SLA_WS_ADJOINT.  Asynchronous (graph launch + one kernel). */
 int32_t sla_adjoint_backward(const sla_csr* A, const sla_csr_t* AT,
                              const double* val, const double* x,
@@ -674,7 +677,7 @@ int32_t sla_grad_values_batched(int32_t batch, int32_t shared_pattern,
 /* Largest n accepted by sla_cg_noalloc. */
 #define SLA_NOALLOC_MAX_N 393216
 
-/* Same solve as sla_cg (same kernels, same results), for callers that cannot
+/* The Jacobi-PCG solve of sla_cg, for callers that cannot
  * allocate device memory at the time they solve: code that runs inside a
  * framework's allocator or memory hook (a cudaMalloc there would re-enter the
  * allocator), serving or real-time hosts that reserve all device memory at
@@ -687,19 +690,27 @@ int32_t sla_grad_values_batched(int32_t batch, int32_t shared_pattern,
  * enqueues nothing.  The call never calls cudaMalloc, cudaFree or any
  * allocating routine.
  *
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls on a device share the one array, which keeps the last
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing), so an address never
+ * outlives a context reset.  The first call on a device can also load the
+ * library's device code there; make it before any stream capture.  All calls
+ * on a device share the one array, which keeps the last
  * call's contents (everything a solve needs zeroed is cleared at its start):
  * calls that overlap on the GPU -- different streams, threads or processes
  * sharing the context -- race and must be serialised by the caller.
  *
  * Systems that sla_cg solves in one cooperative launch are solved the same
- * way here (the call returns without synchronising); the others -- and every
- * call with SLA_FLAG_HOST_LOOP or SLA_FLAG_NO_COOP -- are driven from the
- * host as with SLA_FLAG_HOST_LOOP (no graph objects are created) and the call
- * returns after the solve has finished on `stream`.  Other arguments, options
- * and the *info record behave as for sla_cg. */
+ * way here, with the same kernel and the same results (the call returns
+ * without synchronising).  The others -- and every call with
+ * SLA_FLAG_HOST_LOOP or SLA_FLAG_NO_COOP -- are driven from the host (no
+ * graph objects are created) with the per-phase kernels in their unscaled
+ * form (z = D^-1 r in the scratch array; the fixed array has no room for
+ * D^-1/2 A D^-1/2), so they can differ from sla_cg's per-phase path by
+ * rounding and by a few iterations; the call then returns after the solve
+ * has finished on `stream`.  That host-driven form polls and synchronises
+ * `stream`, so it returns SLA_ERR_INVALID, enqueueing nothing, while
+ * `stream` is being captured.  Other arguments, options and the *info
+ * record behave as for sla_cg. */
 int32_t sla_cg_noalloc(const sla_csr* A, const double* val, const double* b,
                        double* x, const sla_opts* opts, sla_info* info,
                        void* stream);

@@ -108,6 +108,13 @@ extern "C" int32_t sla_adjoint_backward(const sla_csr* A, const sla_csr_t* AT, c
   const int n = A->n, nnz = A->nnz;
   if (n > 0 && x == nullptr) return SLA_ERR_INVALID;
   if (nnz > 0 && grad_val == nullptr) return SLA_ERR_INVALID;
+  // the adjoint solve writes lambda into grad_b before the gradient pass
+  // reads x, so grad_b must not alias x; grad_val must overlap neither
+  if (n > 0 && (const void*)grad_b == (const void*)x) return SLA_ERR_INVALID;
+  if (n > 0 && nnz > 0 &&
+      (ranges_overlap(grad_val, 8 * (size_t)nnz, x, 8 * (size_t)n) ||
+       ranges_overlap(grad_val, 8 * (size_t)nnz, grad_b, 8 * (size_t)n)))
+    return SLA_ERR_INVALID;
   if (opts->precond != SLA_PRECOND_NONE && opts->precond != SLA_PRECOND_JACOBI) return SLA_ERR_INVALID;
   size_t need = 0;
   workspace_bytes(SLA_WS_ADJOINT, n, nnz, 1, &need);

@@ -691,7 +691,14 @@ int launch_cg(const KrylovDesc& desc, void* ws, cudaStream_t s, int flags, bool 
     const int rc = launch_cg_coop(desc, ws, s, &launched);
     if (rc != SLA_OK || launched) return rc;
   }
-  if (!allow_graph) flags |= SLA_FLAG_HOST_LOOP;
+  if (!allow_graph) {
+    // the host-driven loop polls and synchronises the stream, which a
+    // stream capture does not allow: refuse before enqueueing anything
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SLA_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return SLA_ERR_INVALID;
+    flags |= SLA_FLAG_HOST_LOOP;
+  }
   const CgLayout L = cg_layout(n);
   char* base = (char*)ws;
   CgPtrs P;
@@ -807,23 +814,15 @@ static constexpr size_t kNoallocScratchBytes = sla::cg_layout(SLA_NOALLOC_MAX_N)
 static __device__ __align__(256) unsigned char sla_noalloc_scratch[kNoallocScratchBytes];
 
 namespace {
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[64] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device.  In host code the array's name is only a host-side stand-in,
-// never a device address, so it is resolved with cudaGetSymbolAddress.
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, never a device address, so
+// it is resolved with cudaGetSymbolAddress -- on every call (it allocates
+// nothing), so that an address never outlives the context it came from.
 int noalloc_scratch(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SLA_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (g_noalloc_addr[dev] == nullptr) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, sla_noalloc_scratch) != cudaSuccess || p == nullptr)
-      return SLA_ERR_CUDA;
-    g_noalloc_addr[dev] = p;
-  }
-  *out = g_noalloc_addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, sla_noalloc_scratch) != cudaSuccess || p == nullptr)
+    return SLA_ERR_CUDA;
+  *out = p;
   return SLA_OK;
 }
 }  // namespace

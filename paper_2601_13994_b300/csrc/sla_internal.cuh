@@ -24,6 +24,12 @@ constexpr int kWarp = 32;
 // Round up to a multiple of 256 bytes (workspace carving granularity).
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// True when the byte ranges [a, a + na) and [b, b + nb) share a byte.
+inline bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return na > 0 && nb > 0 && x < y + nb && y < x + na;
+}
+
 // Device properties cached per device ordinal.
 int num_sms(int device);
 int current_device();

@@ -896,6 +896,10 @@ extern "C" int32_t sla_adjoint_backward_multi(const sla_csr* A, const double* va
   if (A->nnz > 0 && grad_val == nullptr) return SLA_ERR_INVALID;
   if (A->n > 0 && ((const void*)x == (const void*)grad_b || (const void*)grad_x == (const void*)grad_b))
     return SLA_ERR_INVALID;
+  if (A->n > 0 && A->nnz > 0 && k > 0 &&
+      (ranges_overlap(grad_val, 8 * (size_t)A->nnz, x, 8 * (size_t)A->n * k) ||
+       ranges_overlap(grad_val, 8 * (size_t)A->nnz, grad_b, 8 * (size_t)A->n * k)))
+    return SLA_ERR_INVALID;
   MultiDesc d;
   int rc = make_multi_desc(A, val, k, grad_x, grad_b, opts, info, ws, ws_bytes, &d);
   if (rc != SLA_OK) return rc;

@@ -128,6 +128,31 @@ def test_bad_arguments_rejected_without_launch():
                       ctypes.c_void_p(0x100000), 1 << 20, None) == L.SLA_ERR_INVALID
 
 
+def test_adjoint_rejects_aliased_outputs_without_launch():
+    """lambda is written into grad_b before the gradient pass reads x, so
+    grad_b aliasing x, or grad_val overlapping x or grad_b, is rejected
+    before anything is enqueued (fake pointers: a launch would fault)."""
+    lib = L.lib()
+    fake = ctypes.c_void_p(0x1000)
+    A = L.SlaCsr(10, 20, fake, fake)
+    o = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0, 0)
+    ws, big = ctypes.c_void_p(0x100000), ctypes.c_size_t(1 << 40)
+    x, gx, gb, gv = 0x10000, 0x20000, 0x30000, 0x40000
+
+    def call(x, gx, gb, gv):
+        return lib.sla_adjoint_backward(ctypes.byref(A), None, fake, ctypes.c_void_p(x), ctypes.c_void_p(gx),
+                                        ctypes.c_void_p(gb), ctypes.c_void_p(gv), L.SLA_ADJ_CG,
+                                        ctypes.byref(o), fake, ws, big, None)
+    assert call(x, gx, x, gv) == L.SLA_ERR_INVALID             # grad_b == x
+    assert call(x, gx, gx, gv) == L.SLA_ERR_INVALID            # grad_b == grad_x
+    assert call(x, gx, gb, x + 8 * 9) == L.SLA_ERR_INVALID     # grad_val overlaps x's last entry
+    assert call(x, gx, gb, gb - 8 * 19) == L.SLA_ERR_INVALID   # grad_val's last entry is grad_b[0]
+    # the multi-RHS adjoint applies the same rule over its k columns
+    assert lib.sla_adjoint_backward_multi(ctypes.byref(A), fake, 4, ctypes.c_void_p(x), ctypes.c_void_p(gx),
+                                          ctypes.c_void_p(gb), ctypes.c_void_p(x + 8 * 39), ctypes.byref(o),
+                                          fake, ws, big, None) == L.SLA_ERR_INVALID
+
+
 def test_multi_rhs_arguments_rejected_without_launch():
     lib = L.lib()
     fake = ctypes.c_void_p(0x1000)

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2601_13994_b300 import _lib as L
 from paper_2601_13994_b300 import inputs as I
 from paper_2601_13994_b300 import sla
@@ -61,19 +62,26 @@ def test_noalloc_matches_workspace_entry_point_two_calls():
     A = sla.CSRMatrix.from_numpy(rp, c, device="cuda")
     val = torch.from_numpy(v).cuda()
     for seed in (5, 6):  # two calls in a row on the shared array
-        b = torch.from_numpy(I.rhs_uniform(n, seed)).cuda()
+        bh = I.rhs_uniform(n, seed)
+        b = torch.from_numpy(bh).cuda()
         x_ref, (it_ref, st_ref, _) = _solve_workspace(A, val, b, 1e-10)
+        # and the oracle's solution, converged well below the solve's tolerance
+        x_or, io = oracle.pcg(rp, c, v, bh, rtol=1e-13)
+        assert io["status"] == 0
         x_na, (it_na, st_na, _) = _solve_noalloc(A, val, b, 1e-10)
         assert st_ref == st_na == L.SLA_OK
         assert it_na == it_ref
         err = float(torch.linalg.norm(x_na - x_ref) / torch.linalg.norm(x_ref))
         assert err <= REL_TOL, err
+        xo = torch.from_numpy(x_or).cuda()
+        assert float(torch.linalg.norm(x_na - xo) / torch.linalg.norm(xo)) <= REL_TOL
         # the host-driven per-phase kernels (what sizes beyond the cooperative
         # launch take) on the same array
         x_h, (it_h, st_h, _) = _solve_noalloc(A, val, b, 1e-10, flags=L.SLA_FLAG_NO_COOP)
         assert st_h == L.SLA_OK and abs(it_h - it_ref) <= 2
         err = float(torch.linalg.norm(x_h - x_ref) / torch.linalg.norm(x_ref))
         assert err <= REL_TOL, err
+        assert float(torch.linalg.norm(x_h - xo) / torch.linalg.norm(xo)) <= REL_TOL
 
 
 def test_noalloc_rejects_sizes_beyond_the_array():
