@@ -22,6 +22,10 @@ Function map (paper passage each one follows):
   coo_to_csr        COO ingest of SparseTensor(val, row, col, shape) (App. B)
   grad_values       dL/dA_ij = -lambda_i x_j on the pattern (Eq. 3)
   adjoint_backward  A^T lambda = g, grad_b = lambda, grad_val (Eq. 2-3)
+  pcg_omp           ``pcg`` (Jacobi / none) with its loops spread over the
+                    host's cores by OpenMP (``sla_oracle_omp.c``): the
+                    all-core CPU baseline; differs from ``pcg`` in the
+                    summation order of the inner products only
 Modules: ``oracle.mpnn`` (learned factor), ``oracle.inverse`` (Sec. 4.6
 inverse problem), ``oracle.nonlinear`` (Newton solve and its adjoint
 gradient, Sec. 3.2).
@@ -38,20 +42,50 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sla_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_OMP_SRC = os.path.join(_HERE, "sla_oracle_omp.c")
+_OMP_LIB_PATH = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_omp_lib = None
 
 STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NOT_SPD", -1: "INVALID"}
 
 
 def build(force: bool = False) -> str:
-    """Compile sla_oracle.c into liboracle.so (gcc, -O2 -ffp-contract=off)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
-                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
+    """Compile sla_oracle.c into liboracle.so (gcc, -O2 -ffp-contract=off)
+    and sla_oracle_omp.c into liboracle_omp.so (the same flags + -fopenmp)."""
+    for src, lib, extra in ((_SRC, _LIB_PATH, []), (_OMP_SRC, _OMP_LIB_PATH, ["-fopenmp"])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            tmp = lib + ".tmp%d" % os.getpid()
+            subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", *extra,
+                                   "-shared", "-fPIC", "-o", tmp, src, "-lm"])
+            os.replace(tmp, lib)
     return _LIB_PATH
+
+
+def _load_omp():
+    global _omp_lib
+    with _lock:
+        if _omp_lib is None:
+            build()
+            lib = ctypes.CDLL(_OMP_LIB_PATH)
+            P = ctypes.c_void_p
+            i32 = ctypes.c_int32
+            d = ctypes.c_double
+            lib.or_omp_threads.argtypes = []
+            lib.or_omp_threads.restype = ctypes.c_int
+            lib.or_omp_spmv.argtypes = [i32, P, P, P, P, P]
+            lib.or_omp_spmv.restype = None
+            lib.or_omp_pcg.argtypes = [i32, P, P, P, P, P, d, d, i32, i32, i32, i32, i32, P, P]
+            lib.or_omp_pcg.restype = ctypes.c_int
+            _omp_lib = lib
+    return _omp_lib
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP oracle uses (OMP_NUM_THREADS, else the cores this
+    process may run on)."""
+    return int(_load_omp().or_omp_threads())
 
 
 def _load():
@@ -145,6 +179,29 @@ def pcg(rowptr, col, val, b, rtol=1e-10, atol=0.0, max_iter=None, precond="jacob
                    None if gr is None else _p(gr), None if gc is None else _p(gc),
                    None if gv is None else _p(gv), _p(info), _p(res))
     return x, _info(info, res)
+
+
+def pcg_omp(rowptr, col, val, b, rtol=1e-10, atol=0.0, max_iter=None, precond="jacobi", x0=None,
+            max_restarts=2, threads=None):
+    """Jacobi (or unpreconditioned) PCG of ``pcg`` on the host's cores
+    (OpenMP; ``threads`` None: every core this process may run on).
+    Returns (x, info) with info["threads"] the thread count used."""
+    if threads is None:
+        threads = len(os.sched_getaffinity(0))
+    if precond not in ("jacobi", "none"):
+        raise ValueError("pcg_omp supports precond 'jacobi' or 'none'")
+    rowptr, col, val, b = _i32(rowptr), _i32(col), _f64(val), _f64(b)
+    n = rowptr.shape[0] - 1
+    x = np.zeros(n) if x0 is None else _f64(x0).copy()
+    info = np.zeros(2, np.int32)
+    res = np.zeros(2)
+    mi = default_max_iter(n) if max_iter is None else int(max_iter)
+    lib = _load_omp()
+    lib.or_omp_pcg(n, _p(rowptr), _p(col), _p(val), _p(b), _p(x), rtol, atol, mi, max_restarts,
+                   0 if x0 is None else 1, _PRECOND[precond], int(threads), _p(info), _p(res))
+    out = _info(info, res)
+    out["threads"] = int(lib.or_omp_threads())
+    return x, out
 
 
 def pcg_pipelined(rowptr, col, val, b, rtol=1e-10, atol=0.0, max_iter=None, precond="jacobi",

@@ -10,7 +10,7 @@ import torch
 import oracle
 from paper_2601_13994_b300 import inputs as I
 from paper_2601_13994_b300 import sla
-from tests.gpu_util import csr, rel, to_dev
+from tests.gpu_util import csr, elementwise_rel, rel, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -42,7 +42,9 @@ def test_config1_adjoint_matches_oracle():
     gb, gv, info = oracle.adjoint_backward(rp, c, v, xo, 2 * xo, rtol=1e-13)
     assert rel(x.detach().cpu().numpy(), xo) <= 1e-8
     assert rel(bt.grad.cpu().numpy(), gb) <= GRAD_TOL
+    assert elementwise_rel(bt.grad.cpu().numpy(), gb) <= GRAD_TOL
     assert rel(vt.grad.cpu().numpy(), gv) <= GRAD_TOL
+    assert elementwise_rel(vt.grad.cpu().numpy(), gv) <= GRAD_TOL
 
 
 def test_autograd_graph_has_one_node():
@@ -84,6 +86,7 @@ def test_adjoint_vs_dense_formula(kind):
     assert rel(gv.cpu().numpy(), -lam[rows] * xs[c]) <= 1e-9
     gbo, gvo, _ = oracle.adjoint_backward(rp, c, v, xs, g, method=method, rtol=1e-13)
     assert rel(gv.cpu().numpy(), gvo) <= GRAD_TOL
+    assert elementwise_rel(gv.cpu().numpy(), gvo) <= GRAD_TOL
 
 
 @pytest.mark.parametrize("kind", ["spd", "nonsym"])
@@ -158,7 +161,9 @@ def test_sparse_tensor_coo_api_gradients_in_coo_order():
     gbo, gvo, _ = oracle.adjoint_backward(orp, oc, ov, xo, 2 * xo, rtol=1e-13)
     assert rel(x.detach().cpu().numpy(), xo) <= 1e-8
     assert rel(vt.grad.cpu().numpy(), gvo[operm]) <= GRAD_TOL
+    assert elementwise_rel(vt.grad.cpu().numpy(), gvo[operm]) <= GRAD_TOL
     assert rel(b.grad.cpu().numpy(), gbo) <= GRAD_TOL
+    assert elementwise_rel(b.grad.cpu().numpy(), gbo) <= GRAD_TOL
 
 
 @pytest.mark.slow

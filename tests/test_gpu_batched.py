@@ -8,7 +8,7 @@ import torch
 import oracle
 from paper_2601_13994_b300 import inputs as I
 from paper_2601_13994_b300 import sla
-from tests.gpu_util import csr, rel, to_dev
+from tests.gpu_util import csr, elementwise_rel, rel, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -22,6 +22,17 @@ def _per_system_check(rp, c, vals, bs, x, info, rtol, iters_tol=2, idx=None):
         assert st[s] == io["status"] == 0, s
         assert rel(x[s], xo) <= 1e-8, s
         assert abs(int(its[s]) - io["iters"]) <= iters_tol, (s, its[s], io["iters"])
+
+
+def _vs_oracle_xstar(rps, cs, vals, bs, xs, idx):
+    """Sampled systems of a full-size batch solved at rtol 1e-10 against the
+    oracle's solution at rtol 1e-13, element by element (max-norm relative
+    to max |x*|) and in norm, both to 1e-8."""
+    for s in idx:
+        xo, io = oracle.pcg(rps[s], cs[s], vals[s], bs[s], rtol=1e-13)
+        assert io["status"] == 0, s
+        assert elementwise_rel(xs[s], xo) <= 1e-8, s
+        assert rel(xs[s], xo) <= 1e-8, s
 
 
 def test_shared_pattern_matches_oracle_per_system():
@@ -260,7 +271,9 @@ def test_batched_adjoint_matches_single_solves():
         xo, _ = oracle.pcg(rp, c, vals[s], b[s].detach().cpu().numpy(), rtol=1e-13)
         gb, gv, _ = oracle.adjoint_backward(rp, c, vals[s], xo, 2 * xo, rtol=1e-13)
         assert rel(b.grad[s].cpu().numpy(), gb) <= 1e-6
+        assert elementwise_rel(b.grad[s].cpu().numpy(), gb) <= 1e-6
         assert rel(v.grad[s].cpu().numpy(), gv) <= 1e-6
+        assert elementwise_rel(v.grad[s].cpu().numpy(), gv) <= 1e-6
 
 
 @pytest.mark.slow
@@ -280,6 +293,12 @@ def test_full_size_shared_1024_systems_64():
         r = b[s] - oracle.spmv(rp, c, vals[s], xh[s])
         assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(b[s])
     _per_system_check([rp] * B, [c] * B, vals, b, xh, info, 1e-8, idx=[0, 1, 511, 1023])
+    # the same launch at rtol 1e-10 against the oracle's x* on 16 systems
+    x10, i10 = sla.cg_batched(csr(rp, c), to_dev(vals), to_dev(b), rtol=1e-10)
+    torch.cuda.synchronize()
+    assert (np.atleast_1d(i10.status) == 0).all()
+    idx = sorted(set(np.random.default_rng(8).choice(B, 14, replace=False).tolist()) | {0, B - 1})
+    _vs_oracle_xstar([rp] * B, [c] * B, vals, b, x10.cpu().numpy(), idx)
 
 
 @pytest.mark.slow
@@ -304,6 +323,16 @@ def test_full_size_fem_list_512(config):
     if config == 0:
         _per_system_check([m[0] for m in mats], [m[1] for m in mats], [m[2] for m in mats], bs, xs, info,
                           1e-8, iters_tol=5, idx=[0, 1, big])
+        # the same launch at rtol 1e-10 against the oracle's x* on 16 systems,
+        # the four largest (block teams) among them
+        x10, i10 = sla.cg_batched_list(P, to_dev(vals), to_dev(np.concatenate(bs)), rtol=1e-10)
+        torch.cuda.synchronize()
+        assert (np.atleast_1d(i10.status) == 0).all()
+        xh10 = x10.cpu().numpy()
+        x10s = [xh10[P.n_off_h[s]:P.n_off_h[s + 1]] for s in range(len(mats))]
+        sizes = np.array([len(m[0]) for m in mats])
+        idx = set(np.argsort(sizes)[-4:].tolist()) | set(np.random.default_rng(9).choice(len(mats), 12, replace=False).tolist())
+        _vs_oracle_xstar([m[0] for m in mats], [m[1] for m in mats], [m[2] for m in mats], bs, x10s, sorted(idx))
         return
     # the team systems ran the pipelined PCG: against the oracle's pipelined PCG
     its = np.atleast_1d(info.iters)

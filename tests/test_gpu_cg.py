@@ -10,7 +10,7 @@ import torch
 import oracle
 from paper_2601_13994_b300 import inputs as I
 from paper_2601_13994_b300 import sla
-from tests.gpu_util import csr, rel, to_dev
+from tests.gpu_util import csr, rel, sampled_errors, stored_oracle, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -141,6 +141,43 @@ def test_full_size_diffusion3d_256_true_residual():
     true_rel = np.linalg.norm(r) / np.linalg.norm(b)
     assert true_rel <= 2e-8
     assert abs(true_rel - info["true_rel_res"]) <= 1e-3 * true_rel
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("N", [128, 256, 464])
+def test_full_size_diffusion3d_matches_stored_oracle_solution(N):
+    """The 3D variable-coefficient configurations at full size against the
+    oracle's own solution (rtol 1e-12, stored at 256 sampled indices by
+    tests/golden/make_golden.py), element by element on the sample.
+
+    Solved at rtol 1e-11: the solution error is the residual times up to the
+    condition number, which grows as N^2 (at 64^3 the sampled error is 13x
+    the rtol), so rtol 1e-10 would not certify 1e-8 at 256^3 and beyond; the
+    bar stays 1e-8 and the tolerance is tightened instead.  128^3 runs both
+    in the cooperative launch (its default) and as the per-phase graph;
+    256^3 and 464^3 take the graph with the TMA SpMV pipeline, the bench's
+    configuration.  The rtol 1e-8 solve must also take the oracle's
+    iteration count to within 2 %."""
+    g = stored_oracle("oracle_diffusion3d_%d.json" % N)
+    rp, c, v = I.diffusion3d_random(N, 1)
+    n = N ** 3
+    b = I.rhs_uniform(n, 11)
+    A = csr(rp, c)
+    vt, bt = to_dev(v), to_dev(b)
+    del v
+    modes = [{}, {"cooperative": False}] if N == 128 else [{}]
+    for kw in modes:
+        x, info = sla.cg(A, vt, bt, rtol=1e-11, **kw)
+        torch.cuda.synchronize()
+        assert info.status == 0, (kw, info.as_dict())
+        emax, enorm = sampled_errors(x.cpu().numpy(), g)
+        assert emax <= 1e-8 and enorm <= 1e-8, (kw, emax, enorm)
+        del x
+    x8, i8 = sla.cg(A, vt, bt, rtol=1e-8)
+    torch.cuda.synchronize()
+    io = g["pcg_rtol_1e-8"]["iters"]
+    assert i8.status == 0 and abs(i8.iters - io) <= max(2, io // 50), (i8.iters, io)
+    assert i8.true_rel_res <= 2e-8
 
 
 def test_host_loop_mode_reproduces_graph_mode():

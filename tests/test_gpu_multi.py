@@ -12,7 +12,7 @@ import oracle.inverse as OI
 from paper_2601_13994_b300 import inputs as I
 from paper_2601_13994_b300 import sla
 from paper_2601_13994_b300.inverse import InverseProblem
-from tests.gpu_util import csr, rel, to_dev
+from tests.gpu_util import csr, elementwise_rel, rel, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -114,8 +114,10 @@ def test_multi_adjoint_matches_oracle():
     for j in range(k):
         lam, g1, _ = oracle.adjoint_backward(rp, c, v, Xn[j], G[j], method="cg", rtol=1e-13)
         assert rel(gb[j], lam) <= GRAD_TOL
+        assert elementwise_rel(gb[j], lam) <= GRAD_TOL
         ref_gv += g1
     assert rel(gv, ref_gv) <= GRAD_TOL
+    assert elementwise_rel(gv, ref_gv) <= GRAD_TOL
     # the gradient pass alone, from the same lambda and x, is the sum of the
     # per-column Eq. 3 products
     ref2 = sum(oracle.grad_values(rp, c, gb[j], Xn[j]) for j in range(k))
@@ -138,8 +140,10 @@ def test_solve_multi_autograd_against_oracle():
         xj, _ = oracle.pcg(rp, c, v, B[j], rtol=1e-14)
         lam, g1, _ = oracle.adjoint_backward(rp, c, v, xj, W[j], method="cg", rtol=1e-14)
         assert rel(bt.grad[j].cpu().numpy(), lam) <= GRAD_TOL
+        assert elementwise_rel(bt.grad[j].cpu().numpy(), lam) <= GRAD_TOL
         gv_ref += g1
     assert rel(vt.grad.cpu().numpy(), gv_ref) <= GRAD_TOL
+    assert elementwise_rel(vt.grad.cpu().numpy(), gv_ref) <= GRAD_TOL
 
 
 def test_inverse_gradient_32_matches_oracle_and_fd():
@@ -160,6 +164,7 @@ def test_inverse_gradient_32_matches_oracle_and_fd():
     assert abs(float(L) - Lo) <= 1e-9 * Lo
     g = g.cpu().numpy()
     assert rel(g, go) <= GRAD_TOL
+    assert elementwise_rel(g, go) <= GRAD_TOL
     rng = np.random.default_rng(3)
     eps = 1e-5
     for _ in range(3):

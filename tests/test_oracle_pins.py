@@ -1024,3 +1024,52 @@ def test_eigenvector_gradient_central_differences():
         et = [t for t in range(len(v)) if rows[t] == c[e] and c[t] == rows[e]][0]
         assert abs(fd - g[e]) <= 1e-6 * max(abs(fd), 1e-3), (e, fd, g[e])
         assert abs(g[e] - g[et]) > 1e-3 * abs(fd)  # the transpose differs: the check can tell them apart
+
+
+# ---------------------------------------------------------------- all-core (OpenMP) oracle PCG
+
+@pytest.mark.parametrize("threads", [1, 4])
+def test_pcg_omp_matches_lu_and_single_thread_oracle(threads):
+    """The OpenMP build of the oracle's Jacobi-PCG: same steps as pcg, so the
+    solution matches dense LU and the single-threaded oracle's to rounding,
+    and the iteration count to within a few (only the inner products'
+    summation order differs)."""
+    rp, c, v = I.diffusion3d_random(14, 5)
+    n = len(rp) - 1
+    b = I.rhs_uniform(n, 6)
+    xs = np.linalg.solve(dense(rp, c, v), b)
+    for pc in ("jacobi", "none"):
+        x, io = oracle.pcg_omp(rp, c, v, b, rtol=1e-12, precond=pc, threads=threads)
+        assert io["threads"] == threads
+        xo, ioo = oracle.pcg(rp, c, v, b, rtol=1e-12, precond=pc)
+        assert io["status"] == 0 and ioo["status"] == 0
+        assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+        assert np.linalg.norm(x - xo) <= 1e-10 * np.linalg.norm(xo)
+        assert abs(io["iters"] - ioo["iters"]) <= 2
+        assert io["true_rel_res"] <= 2e-12
+
+
+def test_pcg_omp_edge_cases_match_oracle():
+    rp, c, v = I.poisson2d(6)
+    n = 36
+    # b = 0: x = 0 after 0 iterations, OK
+    x, io = oracle.pcg_omp(rp, c, v, np.zeros(n), threads=2)
+    assert io["status"] == 0 and io["iters"] == 0 and not x.any()
+    # non-positive diagonal: NOT_SPD before iterating, as the oracle
+    v2 = v.copy()
+    v2[(np.repeat(np.arange(n), np.diff(rp)) == 3) & (c == 3)] = -1.0
+    _, io = oracle.pcg_omp(rp, c, v2, np.ones(n), threads=2)
+    _, ioo = oracle.pcg(rp, c, v2, np.ones(n))
+    assert io["status"] == ioo["status"] == 3 and io["iters"] == 0
+    # iteration cap
+    b = I.rhs_uniform(n, 2)
+    _, io = oracle.pcg_omp(rp, c, v, b, rtol=1e-15, max_iter=3, max_restarts=0, threads=2)
+    _, ioo = oracle.pcg(rp, c, v, b, rtol=1e-15, max_iter=3, max_restarts=0)
+    assert io["status"] == ioo["status"] == 1 and io["iters"] == ioo["iters"] == 3
+    # indefinite: p^T A p <= 0 -> NOT_SPD
+    rpi = np.array([0, 2, 4], np.int32)
+    ci = np.array([0, 1, 0, 1], np.int32)
+    vi = np.array([1.0, 3.0, 3.0, 1.0])
+    _, io = oracle.pcg_omp(rpi, ci, vi, np.array([1.0, -1.0]), precond="none", threads=2)
+    _, ioo = oracle.pcg(rpi, ci, vi, np.array([1.0, -1.0]), precond="none")
+    assert io["status"] == ioo["status"] == 3
