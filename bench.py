@@ -3,17 +3,18 @@
 
 Workload (one step = one full solve, inputs resident in HBM): the 3D 7-point
 variable-coefficient diffusion operator on an N^3 interior grid (default
-N = 256: n = 16,777,216 unknowns, nnz = 117,047,296), face coefficients
-exp(N(0,1)) from seed 1, b ~ U[-1,1] from seed 11, Jacobi-preconditioned CG
-from x0 = 0 to relative residual 1e-8 (recursive residual, then the true
-residual is recomputed).  The working set (~2.2 GB) is far larger than L2,
-so no flush is needed between steps.
+N = 464, the largest configuration: n = 99,897,344 unknowns, nnz =
+697,989,632), face coefficients exp(N(0,1)) from seed 1, b ~ U[-1,1] from
+seed 11, Jacobi-preconditioned CG from x0 = 0 to relative residual 1e-8
+(recursive residual, then the true residual is recomputed).  The working set
+(~20 GB) is far larger than L2, so no flush is needed between steps.
 
 Ranks (torchrun) are independent replicas: each solves its own copy, no
 collective touches the data path (the solve does not shard on one box).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle instead, on bounded samples of the same workload.
+oracle instead (its OpenMP build on every host core), on bounded samples of
+the same workload.
 """
 from __future__ import annotations
 
@@ -34,12 +35,18 @@ sys.path.insert(0, ROOT)
 METRIC = "PCG time to rel-res 1e-8 & SpMV GB/s vs 8 TB/s; learned vs Jacobi-PCG speedup"
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6400.0
-# DRAM bytes (read + write) of one PCG iteration, scaled to 256^3: the three
-# kernels (K1 TMA SpMV, K2, K3 of CG on D^-1/2 A D^-1/2) captured by ncu at 176^3
-# (the capture size rule) and scaled by rows (profiles/pcg_iteration_diffusion3d_256.md);
+# DRAM bytes (read + write) of one PCG iteration of the three per-phase kernels
+# (K1 TMA SpMV, K2, K3 of CG on D^-1/2 A D^-1/2), captured by ncu at 176^3 (a
+# small case under the capture size rule) and scaled by rows to the bench's
+# N (traffic grows in proportion to the rows; profiles/pcg_iteration_diffusion3d_256.md);
 # valid only for these kernels.
-TRAFFIC_PER_ITER_256 = 2.828e9  # 918,981,632 B at 176^3 x (256/176)^3
-FP64_PEAK_TFLOPS = 1.203  # 2 DFMA/clk/SM (ncu peak_sustained) x 148 SMs x 2 flop x 2.032 GHz
+TRAFFIC_PER_ITER_176 = 918981632
+# FP64 peak: derived, not measured by the driver: 2 DFMA per clock per SM
+# (ncu's peak_sustained for the FP64 pipe) x 148 SMs x 2 flop x 2.032 GHz.  A
+# dependent-FMA probe of this project measured 1.10 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.203
+FP64_PEAK_KIND = ("derived: 2 DFMA/clk/SM (ncu FP64 pipe peak) x 148 SMs x 2 flop x 2.032 GHz; "
+                  "a DFMA probe measured 1.10 TFLOP/s")
 
 
 def parse():
@@ -48,12 +55,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--size", type=int, default=256, help="grid side N of the N^3 system")
+    ap.add_argument("--size", type=int, default=464, help="grid side N of the N^3 system")
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--cpu-iters", type=int, default=0,
-                    help="oracle iterations per CPU sample (0: pick ~15 s of work)")
+                    help="oracle iterations per CPU sample (0: pick from a time budget of ~10 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="end-to-end steps timed (at most --steps; each copies the inputs in)")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the solver kernels from a host loop instead of one graph (profiling)")
     ap.add_argument("--max-iter", type=int, default=None,
@@ -328,19 +337,68 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def cpu_sample(rp, c, v, b, iters_per_sample: int):
-    """Times the oracle (single thread, as it stands) on `iters_per_sample`
-    Jacobi-PCG iterations of the full system; returns seconds per iteration."""
+def bench_config(N: int, n: int, nnz: int, rtol: float) -> dict:
+    """The workload description both arms print (same keys, same values)."""
+    return {"workload": "diffusion3d_%d_jacobi_pcg_rtol%.0e" % (N, rtol), "n": n, "nnz": nnz,
+            "precond": "jacobi", "x0": "zero",
+            "l2": "inputs larger than L2 (%.1f GB working set)" % ((12 * nnz + 4 * n + 7 * 8 * n) / 1e9),
+            "parallelism": "replicas"}
+
+
+def host_cores() -> int:
+    """Cores this process may run on (the all-core CPU baseline's threads)."""
+    return len(os.sched_getaffinity(0))
+
+
+def cpu_run(rp, c, v, b, iters: int, threads: int) -> float:
+    """Seconds of one oracle run of `iters` Jacobi-PCG iterations on the full
+    system (set-up, the iterations and the final residual), as it stands:
+    threads == 1 the single-threaded oracle, else its OpenMP build."""
     import oracle
     t0 = time.perf_counter()
-    _, info = oracle.pcg(rp, c, v, b, rtol=0.0, atol=0.0, max_iter=iters_per_sample, max_restarts=0)
-    dt = time.perf_counter() - t0
-    return dt / max(1, info["iters"]), info["iters"]
+    if threads == 1:
+        _, info = oracle.pcg(rp, c, v, b, rtol=0.0, atol=0.0, max_iter=iters, max_restarts=0)
+    else:
+        _, info = oracle.pcg_omp(rp, c, v, b, rtol=0.0, atol=0.0, max_iter=iters, max_restarts=0,
+                                 threads=threads)
+    assert info["iters"] == iters, info
+    return time.perf_counter() - t0
 
 
-def pick_cpu_iters(n: int) -> int:
-    # about 0.3 s per iteration at n = 16.8M on one core: ~15 s of work
-    return int(max(3, min(200, 15.0 / (n * 2.1e-8 + 1e-4))))
+class CpuLeg:
+    """Time to solution of the oracle on a bounded sample of the workload: a
+    1-iteration run and k-iteration runs give the cost of one iteration
+    (difference quotient) and the fixed cost of a solve (set-up, initial and
+    final residual); time to solution = fixed + per-iteration x the solve's
+    iteration count (the oracle's own from tests/golden when stored)."""
+
+    def __init__(self, rp, c, v, b, threads: int, budget_s: float):
+        self.args = (rp, c, v, b)
+        self.threads = threads
+        t1 = cpu_run(rp, c, v, b, 1, threads)
+        # a 1-iteration run costs about 3 iterations' worth (set-up + final residual)
+        self.k = int(max(2, min(400, budget_s / max(t1 / 3.0, 1e-6))))
+        self.t1 = t1
+        self.per_iter = []
+
+    def sample(self, k: int | None = None) -> float:
+        k = k or self.k
+        tk = cpu_run(*self.args, k, self.threads)
+        s = max(tk - self.t1, 0.0) / (k - 1) if k > 1 else tk / 3.0
+        self.per_iter.append(s)
+        return s
+
+    def summary(self, iters: int, iters_src: str, N: int) -> dict:
+        s = statistics.median(self.per_iter)
+        fixed = max(self.t1 - s, 0.0)
+        return {"value": fixed + s * iters, "unit": "s", "cores": self.threads, "kind": "oracle",
+                "seconds_per_iteration": s, "fixed_seconds": fixed,
+                "sample": "%s oracle (%s) on the full %d^3 system: a 1-iteration run and %d run(s) of %d "
+                          "iterations give %.3f s/iteration and %.2f s of fixed cost; time to solution = "
+                          "fixed + s/iteration x %d iterations (%s)"
+                          % ("single-threaded" if self.threads == 1 else "OpenMP (%d threads)" % self.threads,
+                             "oracle/sla_oracle.c" if self.threads == 1 else "oracle/sla_oracle_omp.c",
+                             N, len(self.per_iter), self.k, s, fixed, iters, iters_src)}
 
 
 def _time(fn, reps=3, warm=1):
@@ -384,17 +442,24 @@ def extra_rows(dev, args, peak):
                                            "gbs": gbs, "frac_of_measured_hbm": gbs / peak,
                                            "bytes_per_iter": bpi}
     del A, vt, bt, x
-    # adjoint backward at the bench size: A^T lambda = 2x (L = sum x^2) + gradient pass
-    rp, c, v, b = workload(args.size)
+    # 3D 256^3 (the previous headline size): the PCG solve with its roofline,
+    # then the adjoint backward A^T lambda = 2x (L = sum x^2) + gradient pass
+    N2 = 256
+    rp, c, v, b = workload(N2)
     n, nnz = len(rp) - 1, int(rp[-1])
     A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
     vt = torch.from_numpy(v).to(dev)
     bt = torch.from_numpy(b).to(dev)
-    x, _ = sla.cg(A, vt, bt, rtol=args.rtol)
+    ms, (x, info) = _time(lambda: sla.cg(A, vt, bt, rtol=args.rtol))
+    gbs = bytes_per_iter(n, nnz) * info.iters / (ms / 1e3) / 1e9
+    out["pcg_diffusion3d_%d" % N2] = {"s": ms / 1e3, "iters": info.iters, "status": info.status,
+                                      "true_rel_res": info.true_rel_res, "gbs": gbs,
+                                      "frac_of_measured_hbm": gbs / peak,
+                                      "frac_of_8tbs": gbs / NOMINAL_HBM_GBS}
     g = 2 * x
     ms, (gb, gv, info) = _time(lambda: sla.adjoint_backward(A, vt, x, g, rtol=args.rtol))
-    out["adjoint_backward_diffusion3d_%d" % args.size] = {"s": ms / 1e3, "iters": info.iters,
-                                                          "status": info.status}
+    out["adjoint_backward_diffusion3d_%d" % N2] = {"s": ms / 1e3, "iters": info.iters,
+                                                   "status": info.status}
     del A, vt, bt, x, g, gb, gv
     # batched, shared pattern: 1024 systems on the 64^2 five-point pattern
     B, N = 1024, 64
@@ -614,6 +679,10 @@ def learned_vs_jacobi(dev, systems=48, steps=800, lr=3e-3, n_lo=64, n_hi=128, ev
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands, timed on the host's cores
+    (its OpenMP build on every core this process may use; the line's value),
+    each step a bounded sample of the workload, plus one bounded sample of
+    the single-threaded oracle.  Rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -622,28 +691,34 @@ def run_reference(args):
     n, nnz = len(rp) - 1, int(rp[-1])
     g = golden(N)
     iters_solve = g["pcg_rtol_1e-8"]["iters"] if g else None
-    k = args.cpu_iters or pick_cpu_iters(n)
+    iters_src = "the oracle's own at rtol 1e-8, tests/golden" if g else "unknown: no stored oracle count"
+    cores = host_cores()
+    # the timed steps share ~90 s of CPU work
+    leg = CpuLeg(rp, c, v, b, cores, budget_s=90.0 / max(1, args.steps))
+    if args.cpu_iters:
+        leg.k = max(2, args.cpu_iters)
     for _ in range(args.warmup):
-        cpu_sample(rp, c, v, b, max(1, k // 5))
-    per = []
+        cpu_run(rp, c, v, b, 2, cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s, _ = cpu_sample(rp, c, v, b, k)
-        per.append(s)
+        leg.sample()
     wall = time.perf_counter() - t0
-    s_iter = statistics.median(per)
-    value = s_iter * iters_solve if iters_solve else None
+    base = leg.summary(iters_solve or 0, iters_src, N)
+    single = None
+    if not args.no_cpu_baseline:
+        one = CpuLeg(rp, c, v, b, 1, budget_s=12.0)
+        one.sample()
+        single = one.summary(iters_solve or 0, iters_src, N)
+    value = base["value"] if iters_solve else None
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "diffusion3d_%d_jacobi_pcg_rtol%.0e" % (N, args.rtol), "n": n, "nnz": nnz},
-        "seconds_per_iteration": s_iter,
-        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
-                         "sample": "%d Jacobi-PCG iterations of the oracle on the full %d^3 system per step; "
-                                   "time to solution = median s/iteration x the oracle's own iteration "
-                                   "count at rtol 1e-8 (%s, tests/golden)" % (k, N, iters_solve)},
+        "config": bench_config(N, n, nnz, args.rtol),
+        "seconds_per_iteration": base["seconds_per_iteration"],
+        "cpu_baseline": base,
+        "cpu_baseline_single_thread": single,
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -762,15 +837,16 @@ def run_ours(args):
 
         e2e_step()
         torch.cuda.synchronize(dev)
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
         k0 = torch.cuda.Event(enable_timing=True)
         k1 = torch.cuda.Event(enable_timing=True)
         k0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             inf = e2e_step()
         k1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-        e2e_ms = max_over_ranks(k0.elapsed_time(k1) / args.steps, world, dev)
+        e2e_ms = max_over_ranks(k0.elapsed_time(k1) / e2e_steps, world, dev)
         h2d = rp.nbytes + c.nbytes + v.nbytes + b.nbytes
         d2h = 8 * n + 24  # x and the info record
         # the host-to-device copies alone (the link is shared with the other
@@ -784,7 +860,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         h2d_ms = c0.elapsed_time(c1)
         e2e = {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "iters": inf.iters,
+               "d2h_bytes_per_step": int(d2h), "iters": inf.iters, "steps": e2e_steps,
                "h2d_ms": h2d_ms, "h2d_gbs": h2d / (h2d_ms / 1e3) / 1e9}
 
     peak, peak_kind = measured_peaks()
@@ -798,18 +874,21 @@ def run_ours(args):
     # three kernels per loop body (the iterations and the true-residual check)
     launches = args.steps * (1 + 4 + 3 * (it + 1))
 
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g = golden(N)
-        k = args.cpu_iters or pick_cpu_iters(n)
-        s_iter, done = cpu_sample(rp, c, v, b, k)
         oracle_iters = g["pcg_rtol_1e-8"]["iters"] if g else None
-        used = oracle_iters if oracle_iters else it
-        cpu = {"value": s_iter * used, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": "%d Jacobi-PCG iterations of the single-threaded FP64 oracle on the full "
-                         "%d^3 system (%.2f s/iteration), scaled by %s iteration count %d"
-                         % (done, N, s_iter, "the oracle's own (tests/golden)" if oracle_iters else
-                            "the GPU solve's", used)}
+        used = oracle_iters if oracle_iters else int(it)
+        src = "the oracle's own at rtol 1e-8, tests/golden" if oracle_iters else "the GPU solve's"
+        # all host cores (OpenMP build), then one core (the plain oracle); ~10-15 s each
+        legs = []
+        for threads, budget in ((host_cores(), 10.0), (1, 12.0)):
+            leg = CpuLeg(rp, c, v, b, threads, budget_s=budget)
+            if args.cpu_iters:
+                leg.k = max(2, args.cpu_iters)
+            leg.sample()
+            legs.append(leg.summary(used, src, N))
+        cpu, cpu1 = legs
     extra = None
     if rank == 0 and world == 1 and not args.no_extra:
         extra = extra_rows(dev, args, peak)
@@ -819,24 +898,23 @@ def run_ours(args):
         "metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "diffusion3d_%d_jacobi_pcg_rtol%.0e" % (N, args.rtol), "n": n, "nnz": nnz,
-                   "precond": "jacobi", "x0": "zero", "l2": "inputs larger than L2 (%.1f GB working set)"
-                   % ((12 * nnz + 4 * n + 7 * 8 * n) / 1e9), "parallelism": "replicas"},
+        "config": bench_config(N, n, nnz, args.rtol),
         "iters": it, "status": sorted(set(status_all)), "true_rel_res": true_rel,
         "pcg_gbs": achieved, "pcg_frac_of_8tbs": achieved / NOMINAL_HBM_GBS,
         "spmv_gbs": spmv_gbs, "spmv_frac_of_8tbs": spmv_gbs / NOMINAL_HBM_GBS,
         "spmv_ms": spmv_ms,
-        "fp64": {"achieved_tflops": fp64_tf, "peak_tflops": FP64_PEAK_TFLOPS,
+        "fp64": {"achieved_tflops": fp64_tf, "peak_tflops": FP64_PEAK_TFLOPS, "peak_kind": FP64_PEAK_KIND,
                  "frac": fp64_tf / FP64_PEAK_TFLOPS, "flops_per_iter": fpi},
         "roofline": {"kernel": "Jacobi-PCG iteration (cg_spmv_pq + cg_update + cg_pupdate)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "bytes_per_launch": bpi,
-                     "traffic": TRAFFIC_PER_ITER_256 if N == 256 else None,
-                     "traffic_unit": "bytes per iteration (3 kernels)"},
+                     "traffic": TRAFFIC_PER_ITER_176 * (N / 176.0) ** 3 if N >= 176 else None,
+                     "traffic_unit": "bytes per iteration (3 kernels), ncu at 176^3 scaled by rows"},
         "roofline_spmv": {"kernel": "spmv_tma_kernel", "bound": "hbm", "achieved": spmv_gbs, "peak": peak,
                           "unit": "GB/s", "frac": spmv_gbs / peak, "bytes_per_launch": spmv_bytes(n, nnz)},
         "cpu_baseline": cpu,
+        "cpu_baseline_single_thread": cpu1,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": int(launches),

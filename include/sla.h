@@ -82,6 +82,8 @@ extern "C" {
 #define SLA_WS_BICGSTAB 2
 #define SLA_WS_ADJOINT 3        /* sla_adjoint_backward                        */
 #define SLA_WS_TRANSPOSE 4      /* sla_csr_transpose                           */
+#define SLA_WS_LIST_TRANSPOSE 13 /* sla_csr_list_transpose: n = total rows,
+                                   nnz = total entries of the list          */
 #define SLA_WS_COO 5            /* sla_coo_to_csr (pass the COO entry count as nnz) */
 #define SLA_WS_CG_GGT 7         /* sla_cg_ggt: pass the entry count of G as nnz */
 #define SLA_WS_SPMV_MERGE 9     /* sla_spmv_merge                              */
@@ -657,6 +659,72 @@ int32_t sla_cg_batched_list(int32_t batch, int32_t n_max, int32_t total_rows,
                             const int32_t* order, const sla_opts* opts,
                             sla_info* info, int32_t config, void* ws,
                             size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Batched BiCGStab in one persistent launch (the nonsymmetric members of  */
+/* a SparseTensor batch or SparseTensorList, Sec. 3.1 and App. B)          */
+/* ------------------------------------------------------------------ */
+
+/* Each system is solved by one CTA running the complete BiCGStab of
+ * sla_bicgstab (van der Vorst, r^ = r0, right Jacobi preconditioning, exit
+ * at the half step when ||s|| meets the target; the same breakdown tests,
+ * true-residual check, restarts and statuses; info[s] per system, a zero
+ * or non-finite diagonal with Jacobi giving status SLA_ERR_INVALID with NaN
+ * residuals in that system's record only).  Persistent CTAs take systems
+ * from a counter (in `order` for lists, largest first by default), so a
+ * converged system frees its CTA for the next.  The seven n-vectors of a
+ * system (r, r^, D^-1 p, A D^-1 p, D^-1 s, A D^-1 s, D^-1) stay in shared
+ * memory as far as they fit, the rest in the workspace.
+ * config: 0 = automatic; low 4 bits 1/2/3 = 256/512/1024 threads per CTA;
+ * config | 16 = every vector in the workspace; other bits SLA_ERR_INVALID.
+ * opts->flags must be 0.  The call only enqueues kernels (no host
+ * synchronisation).  b and x must differ.
+ * Shared pattern: val [batch, nnz], b and x [batch, n] row-major.
+ * Workspace: SLA_WS_BATCHED with (n, batch). */
+int32_t sla_bicgstab_batched_shared(const sla_csr* A, int32_t batch,
+                                    const double* val, const double* b,
+                                    double* x, const sla_opts* opts,
+                                    sla_info* info, int32_t config, void* ws,
+                                    size_t ws_bytes, void* stream);
+
+/* Distinct patterns in the concatenated layout of sla_cg_batched_list
+ * (n_off, nnz_off, rowptr back to back, local columns, optional order);
+ * every system on one CTA (no block teams).
+ * Workspace: SLA_WS_BATCHED with (total_rows, 1). */
+int32_t sla_bicgstab_batched_list(int32_t batch, int32_t n_max,
+                                  int32_t total_rows, const int32_t* n_off,
+                                  const int32_t* nnz_off,
+                                  const int32_t* rowptr, const int32_t* col,
+                                  const double* val, const double* b,
+                                  double* x, const int32_t* order,
+                                  const sla_opts* opts, sla_info* info,
+                                  int32_t config, void* ws, size_t ws_bytes,
+                                  void* stream);
+
+/* CSR of A_s^T for every system of a list (Eq. 3 needs A^T lambda = dL/dx
+ * per system): the same concatenated layout as the input (rowptrT: the
+ * per-system row pointers of the transposes back to back, total_rows +
+ * batch entries; colT: local columns; permT: for each entry of A_s^T the
+ * index into the concatenated values, so valT = val[permT] is one
+ * sla_gather_values call over all systems).
+ * Within a row of A_s^T the entries keep increasing column order (stable),
+ * bit for bit what sla_csr_transpose gives for each system alone.  Outputs
+ * must not alias the inputs.  Workspace: SLA_WS_LIST_TRANSPOSE with
+ * (total_rows, total_nnz).  Asynchronous. */
+int32_t sla_csr_list_transpose(int32_t batch, int32_t total_rows,
+                               int32_t total_nnz, const int32_t* n_off,
+                               const int32_t* nnz_off, const int32_t* rowptr,
+                               const int32_t* col, int32_t* rowptrT,
+                               int32_t* colT, int32_t* permT, void* ws,
+                               size_t ws_bytes, void* stream);
+
+/* out[s, m] = val[s, perm[m]] for every system s of a shared pattern
+ * (val, out [batch, nnz]): the values of every A_s^T in CSR-of-A^T order
+ * (perm = perm_t of sla_csr_transpose).  out must not overlap val.
+ * Device arrays; asynchronous. */
+int32_t sla_gather_values_batched(int32_t batch, int64_t nnz,
+                                  const int32_t* perm, const double* val,
+                                  double* out, void* stream);
 
 /* Batched Eq. 3 gradient: grad_val[s, k] = -lambda[s, i] x[s, col k] for the
  * entries k of row i of system s.  shared_pattern = 1: (n, nnz, rowptr,

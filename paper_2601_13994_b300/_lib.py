@@ -42,6 +42,7 @@ SLA_WS_SPMV_MERGE = 9
 SLA_WS_CG_PIPELINED = 10
 SLA_WS_EIGSH = 11
 SLA_WS_EIG_ADJOINT = 12
+SLA_WS_LIST_TRANSPOSE = 13
 SLA_EIG_MAX_K = 8
 SLA_SPMV_ROWS = 0
 SLA_SPMV_MERGE = 1
@@ -151,6 +152,16 @@ def lib() -> ctypes.CDLL:
             L.sla_cg_batched_list.restype = i32
             L.sla_grad_values_batched.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, P]
             L.sla_grad_values_batched.restype = i32
+            L.sla_bicgstab_batched_shared.argtypes = [ctypes.POINTER(SlaCsr), i32, P, P, P,
+                                                      ctypes.POINTER(SlaOpts), P, i32, P, ctypes.c_size_t, P]
+            L.sla_bicgstab_batched_shared.restype = i32
+            L.sla_bicgstab_batched_list.argtypes = [i32, i32, i32, P, P, P, P, P, P, P, P,
+                                                    ctypes.POINTER(SlaOpts), P, i32, P, ctypes.c_size_t, P]
+            L.sla_bicgstab_batched_list.restype = i32
+            L.sla_csr_list_transpose.argtypes = [i32, i32, i32, P, P, P, P, P, P, P, P, ctypes.c_size_t, P]
+            L.sla_csr_list_transpose.restype = i32
+            L.sla_gather_values_batched.argtypes = [i32, i64, P, P, P, P]
+            L.sla_gather_values_batched.restype = i32
             L.sla_cg_ggt.argtypes = [ctypes.POINTER(SlaCsr), P, ctypes.POINTER(SlaCsr), P, ctypes.POINTER(SlaCsrT),
                                      P, P, ctypes.POINTER(SlaOpts), P, P, ctypes.c_size_t, P]
             L.sla_cg_ggt.restype = i32

@@ -346,6 +346,71 @@ __global__ void segment_sum_kernel(int nseg, const int* __restrict__ seg, const 
   }
 }
 
+// ---------------------------------------------- transpose of a pattern list
+// The list (per-system row pointers back to back, local columns, offsets
+// n_off / nnz_off) is the block-diagonal matrix whose global column of a
+// local entry (s, i, c) is n_off[s] + c.  Sorting all entries by that key
+// (stably) gives each system's transposed entries, in order, exactly in the
+// system's own entry range [nnz_off[s], nnz_off[s+1]): every key of system s
+// lies in [n_off[s], n_off[s+1]).
+
+// system of global position p, given offsets off[0..batch] (off[batch] > p)
+__device__ __forceinline__ int list_system(const int* __restrict__ off, int batch, long long p) {
+  int lo = 0, hi = batch;  // off[lo] <= p < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= p) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// keys = global column, vals = global entry index, rows = global row
+__global__ void list_keys_kernel(int batch, int total_rows, const int* __restrict__ n_off,
+                                 const int* __restrict__ nnz_off, const int* __restrict__ rowptr,
+                                 const int* __restrict__ col, unsigned* keys, unsigned* vals,
+                                 unsigned* rows) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total_rows; g += stride) {
+    const int s = list_system(n_off, batch, g);
+    const int n0 = n_off[s], e0 = nnz_off[s];
+    const int* rp = rowptr + n0 + s;
+    const int i = (int)(g - n0);
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      keys[e0 + k] = (unsigned)(n0 + col[e0 + k]);
+      vals[e0 + k] = (unsigned)(e0 + k);
+      rows[e0 + k] = (unsigned)g;
+    }
+  }
+}
+
+// list-layout row pointers of the transposes from the global boundaries
+// ptr[0..total_rows]: row j of system s starts at ptr[n_off[s] + j] - nnz_off[s]
+__global__ void list_rowptr_kernel(int batch, int total_rows, const int* __restrict__ n_off,
+                                   const int* __restrict__ nnz_off, const int* __restrict__ ptr,
+                                   int* rowptrT) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total_rows; g += stride) {
+    const int s = list_system(n_off, batch, g);
+    rowptrT[g + s] = ptr[g] - nnz_off[s];
+  }
+  // each system's closing entry (its entry count; the only entry of an empty system)
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < batch; s += stride)
+    rowptrT[n_off[s + 1] + s] = nnz_off[s + 1] - nnz_off[s];
+}
+
+__global__ void list_finish_kernel(int batch, long long nnz, const int* __restrict__ n_off,
+                                   const int* __restrict__ nnz_off, const unsigned* __restrict__ sorted_vals,
+                                   const unsigned* __restrict__ rows, int* colT, int* permT) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nnz; p += stride) {
+    const int s = list_system(nnz_off, batch, p);
+    const unsigned k = sorted_vals[p];
+    permT[p] = (int)k;
+    colT[p] = (int)rows[k] - n_off[s];
+  }
+}
+
 int grid_for(long long n) {
   return persistent_grid(current_device(), (n + 255) / 256, 8, 1 << 20);
 }
@@ -378,6 +443,11 @@ PatternLayout pattern_layout(long long m, int n) {
 }  // namespace
 
 size_t transpose_ws_bytes(int n, int nnz) { return pattern_layout(nnz, n).total; }
+
+// list transpose: the transpose layout over all entries + the global boundaries
+size_t list_transpose_ws_bytes(int total_rows, int total_nnz) {
+  return pattern_layout(total_nnz, total_rows).total + al256(4 * ((size_t)(total_rows > 0 ? total_rows : 0) + 1));
+}
 
 long long scan_tmp_ints(long long n) { return scan_tiles(n) + 1; }
 
@@ -414,6 +484,49 @@ extern "C" int32_t sla_csr_transpose(const sla_csr* A, int32_t* rowptrT, int32_t
   unsigned* rows = (unsigned*)(base + L.extra);
   entry_rows_kernel<<<grid_for(n), 256, 0, s>>>(n, A->rowptr, rows);
   transpose_finish_kernel<<<grid_for(nnz), 256, 0, s>>>(nnz, ks, vs, rows, colT, permT);
+  SLA_CUDA_TRY(cudaGetLastError());
+  return SLA_OK;
+}
+
+extern "C" int32_t sla_csr_list_transpose(int32_t batch, int32_t total_rows, int32_t total_nnz,
+                                          const int32_t* n_off, const int32_t* nnz_off,
+                                          const int32_t* rowptr, const int32_t* col,
+                                          int32_t* rowptrT, int32_t* colT, int32_t* permT,
+                                          void* ws, size_t ws_bytes, void* stream) {
+  if (batch < 0 || total_rows < 0 || total_nnz < 0) return SLA_ERR_INVALID;
+  if (batch == 0) return total_rows == 0 && total_nnz == 0 ? SLA_OK : SLA_ERR_INVALID;
+  if (n_off == nullptr || nnz_off == nullptr || rowptr == nullptr || rowptrT == nullptr)
+    return SLA_ERR_INVALID;
+  if (total_nnz > 0 && (col == nullptr || colT == nullptr || permT == nullptr)) return SLA_ERR_INVALID;
+  if ((const void*)rowptr == (const void*)rowptrT || (total_nnz > 0 && (const void*)col == (const void*)colT))
+    return SLA_ERR_INVALID;
+  const PatternLayout L = pattern_layout(total_nnz, total_rows);
+  if (ws == nullptr || ((uintptr_t)ws & 255u) || ws_bytes < list_transpose_ws_bytes(total_rows, total_nnz))
+    return SLA_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)ws;
+  int* ptr = (int*)(base + L.total);
+  SortBufs B{(unsigned*)(base + L.k0), (unsigned*)(base + L.v0), (unsigned*)(base + L.k1),
+             (unsigned*)(base + L.v1), (int*)(base + L.hist), (int*)(base + L.scan_tmp)};
+  unsigned* rows = (unsigned*)(base + L.extra);
+  const unsigned* vs = B.v0;
+  if (total_nnz > 0) {
+    list_keys_kernel<<<grid_for(total_rows), 256, 0, s>>>(batch, total_rows, n_off, nnz_off, rowptr, col,
+                                                           B.k0, B.v0, rows);
+    unsigned* ks = nullptr;
+    unsigned* vres = nullptr;
+    int rc = radix_sort(B, total_nnz, key_bits(total_rows > 0 ? total_rows - 1 : 0), &ks, &vres, s);
+    if (rc != SLA_OK) return rc;
+    boundaries_kernel<<<grid_for((long long)total_nnz + 1), 256, 0, s>>>(total_nnz, total_rows, ks, ptr);
+    vs = vres;
+  } else {
+    SLA_CUDA_TRY(cudaMemsetAsync(ptr, 0, sizeof(int) * ((size_t)total_rows + 1), s));
+  }
+  list_rowptr_kernel<<<grid_for((long long)total_rows + batch), 256, 0, s>>>(batch, total_rows, n_off,
+                                                                              nnz_off, ptr, rowptrT);
+  if (total_nnz > 0)
+    list_finish_kernel<<<grid_for(total_nnz), 256, 0, s>>>(batch, total_nnz, n_off, nnz_off, vs, rows,
+                                                            colT, permT);
   SLA_CUDA_TRY(cudaGetLastError());
   return SLA_OK;
 }

@@ -169,6 +169,7 @@ size_t spmv_merge_ws_bytes(int n, long long nnz);
 
 // Pattern utilities (sla_pattern.cu).
 size_t transpose_ws_bytes(int n, int nnz);
+size_t list_transpose_ws_bytes(int total_rows, int total_nnz);
 size_t coo_ws_bytes(int n, long long m);
 
 // Adjoint: the larger of the CG scratch (either form) and BiCGStab scratch
@@ -206,6 +207,9 @@ inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
       return true;
     case SLA_WS_TRANSPOSE:
       *out = transpose_ws_bytes(n, nnz);
+      return true;
+    case SLA_WS_LIST_TRANSPOSE:
+      *out = list_transpose_ws_bytes(n, nnz);  // n = total rows, nnz = total entries
       return true;
     case SLA_WS_COO:
       *out = coo_ws_bytes(n, nnz);

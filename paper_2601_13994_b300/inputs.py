@@ -220,6 +220,81 @@ def batched_shared_2d(N: int, batch: int, seed0: int, sigma: float = 0.5):
 
 
 # ---------------------------------------------------------------------------
+# 2D convection-diffusion batches (nonsymmetric: the BiCGStab batches)
+# ---------------------------------------------------------------------------
+
+def convdiff2d_rect(cx: np.ndarray, cy: np.ndarray, wx: float, wy: float):
+    """Five-point operator of -div(c grad u) + w . grad u on an Ny x Nx
+    interior grid (unit spacing, Dirichlet boundary), convection by first
+    order upwinding.  ``cx`` (Ny, Nx+1) and ``cy`` (Ny+1, Nx) are the face
+    coefficients as in ``diffusion2d``; (wx, wy) the cell Peclet numbers per
+    axis, of either sign.  Unknown i = p + Nx q.  The neighbour upstream
+    along x (west for wx > 0, east for wx < 0) gets -|wx| on top of its
+    diffusion coefficient and the diagonal gets +|wx| (likewise along y), so
+    A is a diagonally dominant, nonsymmetric M-matrix; the five-point pattern
+    does not depend on (wx, wy)."""
+    Ny, Nx = cx.shape[0], cx.shape[1] - 1
+    assert cy.shape == (Ny + 1, Nx)
+    n = Nx * Ny
+    q, p = np.divmod(np.arange(n, dtype=np.int64), Nx)
+    w = cx[q, p]
+    e = cx[q, p + 1]
+    s = cy[q, p]
+    nn = cy[q + 1, p]
+    i = np.arange(n, dtype=np.int64)
+    ax, ay = abs(wx), abs(wy)
+    cols = np.stack([i - Nx, i - 1, i, i + 1, i + Nx], axis=1)
+    vals = np.stack([-s - max(wy, 0.0), -w - max(wx, 0.0), w + e + s + nn + ax + ay,
+                     -e - max(-wx, 0.0), -nn - max(-wy, 0.0)], axis=1)
+    mask = np.stack([q > 0, p > 0, np.ones(n, bool), p < Nx - 1, q < Ny - 1], axis=1)
+    return _compress(cols, vals, mask)
+
+
+def convdiff2d_random(Nx: int, Ny: int, seed: int, sigma: float = 0.5, pe_max: float = 10.0):
+    """One seeded system of ``convdiff2d_rect``: from ``default_rng(seed)``
+    the x-faces, then the y-faces (exp(N(0, sigma^2))), then the velocity
+    direction theta ~ U[0, 2 pi) and cell Peclet magnitude ~ U[0, pe_max]."""
+    rng = np.random.default_rng(seed)
+    cx = np.exp(sigma * rng.standard_normal((Ny, Nx + 1)))
+    cy = np.exp(sigma * rng.standard_normal((Ny + 1, Nx)))
+    theta = rng.uniform(0.0, 2.0 * math.pi)
+    pe = rng.uniform(0.0, pe_max)
+    return convdiff2d_rect(cx, cy, pe * math.cos(theta), pe * math.sin(theta))
+
+
+def batched_convdiff_2d(N: int, batch: int, seed0: int, sigma: float = 0.5, pe_max: float = 10.0):
+    """``batch`` nonsymmetric convection-diffusion systems on one shared
+    N x N five-point pattern, system k from seed ``seed0 + k``.  Returns
+    (rowptr, col, val[batch, nnz])."""
+    vals = None
+    rowptr = col = None
+    for k in range(batch):
+        rp, c, v = convdiff2d_random(N, N, seed0 + k, sigma, pe_max)
+        if vals is None:
+            rowptr, col = rp, c
+            vals = np.empty((batch, v.shape[0]))
+        vals[k] = v
+    return rowptr, col, vals
+
+
+def convdiff_list(count: int, seed0: int, n_lo: float = 1e3, n_hi: float = 5e4,
+                  sigma: float = 0.5, pe_max: float = 10.0):
+    """``count`` nonsymmetric systems with distinct patterns: system k draws,
+    from ``default_rng(seed0 + k)``, a size log-uniform in [n_lo, n_hi] and
+    an aspect ratio log-uniform in [1/2, 2], giving an Nx x Ny rectangle,
+    then is ``convdiff2d_random(Nx, Ny, seed0 + k)``."""
+    out = []
+    for k in range(count):
+        rng = np.random.default_rng(seed0 + k)
+        target = math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))
+        aspect = math.exp(rng.uniform(math.log(0.5), math.log(2.0)))
+        Nx = max(2, int(round(math.sqrt(target * aspect))))
+        Ny = max(2, int(round(target / Nx)))
+        out.append(convdiff2d_random(Nx, Ny, seed0 + k, sigma, pe_max))
+    return out
+
+
+# ---------------------------------------------------------------------------
 # P1 finite elements on jittered, holed triangulations (distinct patterns)
 # ---------------------------------------------------------------------------
 

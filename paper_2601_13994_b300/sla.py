@@ -662,6 +662,28 @@ class CSRList:
         self.nnz_off = torch.from_numpy(self.nnz_off_h.astype(np.int32)).to(dev)
         self.order = torch.from_numpy(np.argsort(-np.asarray(nnzs), kind="stable").astype(np.int32)).to(dev)
         self.device = self.rowptr.device
+        self._transpose = None
+
+    def transpose(self):
+        """(CSRList of the A_s^T, permT) with valT = val[permT] over the
+        concatenated values (sla_csr_list_transpose; computed once)."""
+        if self._transpose is None:
+            T = object.__new__(CSRList)
+            for k in ("batch", "n_off_h", "nnz_off_h", "n_max", "total_rows", "total_nnz", "n_off", "nnz_off",
+                      "order", "device"):
+                setattr(T, k, getattr(self, k))
+            T.rowptr = torch.empty_like(self.rowptr)
+            T.col = torch.empty(max(self.total_nnz, 1), dtype=torch.int32, device=self.device)
+            permT = torch.empty(max(self.total_nnz, 1), dtype=torch.int32, device=self.device)
+            ws = _scratch(L.SLA_WS_LIST_TRANSPOSE, self.total_rows, self.total_nnz, self.device)
+            L.check("sla_csr_list_transpose", L.lib().sla_csr_list_transpose(
+                self.batch, self.total_rows, self.total_nnz, self.n_off.data_ptr(), self.nnz_off.data_ptr(),
+                self.rowptr.data_ptr(), self.col.data_ptr(), T.rowptr.data_ptr(), T.col.data_ptr(),
+                permT.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(self.device)))
+            T.col = T.col[:self.total_nnz]
+            T._transpose = None
+            self._transpose = (T, permT[:self.total_nnz])
+        return self._transpose
 
 
 _tune_cache: dict = {}
@@ -727,6 +749,80 @@ def cg_batched_list(P: CSRList, val: torch.Tensor, b: torch.Tensor, *, rtol: flo
     return x, SolveInfo(info)
 
 
+# BiCGStab batches: 256/512/1024 threads, vectors on chip as far as they fit / in global
+BICG_BATCH_CONFIGS = (1, 2, 3, 1 | 16, 2 | 16, 3 | 16)
+
+
+def bicgstab_batched(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10,
+                     atol: float = 0.0, max_iter: int | None = None, precond: str = "jacobi",
+                     x0: torch.Tensor | None = None, max_restarts: int = 2, config: int | str = "auto",
+                     out: torch.Tensor | None = None):
+    """B nonsymmetric systems on one pattern by BiCGStab: val [B, nnz], b
+    [B, n] -> x [B, n], SolveInfo (B records).  One persistent launch;
+    config "tune" runs the autotuner."""
+    B = b.shape[0]
+    _need(val, torch.float64, A.device, "val", B * A.nnz)
+    _need(b, torch.float64, A.device, "b", B * A.n)
+    x = torch.empty((B, A.n), dtype=torch.float64, device=A.device) if out is None else out
+    use_x0 = 0
+    if x0 is not None:
+        x.copy_(x0)
+        use_x0 = 1
+    info = torch.empty((B, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
+    o = _batched_opts(rtol, atol, max_iter, max_restarts, precond, use_x0, A.n)
+    ws = workspace(L.SLA_WS_BATCHED, A.n, A.nnz, B, A.device)
+
+    def run(cfg):
+        L.check("sla_bicgstab_batched_shared", L.lib().sla_bicgstab_batched_shared(
+            ctypes.byref(A.c), B, val.data_ptr(), b.data_ptr(), x.data_ptr(), ctypes.byref(o), info.data_ptr(),
+            cfg, ws.data_ptr(), ws.numel(), _stream_ptr(A.device)))
+
+    cfg = _resolve_config(config, ("bicg_shared", A.n, A.nnz, B), run, x, x0, BICG_BATCH_CONFIGS)
+    run(cfg)
+    return x, SolveInfo(info)
+
+
+def bicgstab_batched_list(P: CSRList, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10,
+                          atol: float = 0.0, max_iter: int | None = None, precond: str = "jacobi",
+                          x0: torch.Tensor | None = None, max_restarts: int = 2, config: int | str = "auto",
+                          out: torch.Tensor | None = None):
+    """Distinct nonsymmetric patterns (concatenated values / right-hand
+    sides) by BiCGStab in one persistent launch; returns (x concatenated,
+    SolveInfo with B records)."""
+    _need(val, torch.float64, P.device, "val", P.total_nnz)
+    _need(b, torch.float64, P.device, "b", P.total_rows)
+    x = torch.empty(P.total_rows, dtype=torch.float64, device=P.device) if out is None else out
+    use_x0 = 0
+    if x0 is not None:
+        x.copy_(x0)
+        use_x0 = 1
+    info = torch.empty((P.batch, L.INFO_BYTES), dtype=torch.uint8, device=P.device)
+    o = _batched_opts(rtol, atol, max_iter, max_restarts, precond, use_x0, P.n_max)
+    ws = workspace(L.SLA_WS_BATCHED, P.total_rows, P.total_nnz, 1, P.device)
+
+    def run(cfg):
+        L.check("sla_bicgstab_batched_list", L.lib().sla_bicgstab_batched_list(
+            P.batch, P.n_max, P.total_rows, P.n_off.data_ptr(), P.nnz_off.data_ptr(), P.rowptr.data_ptr(),
+            P.col.data_ptr(), val.data_ptr(), b.data_ptr(), x.data_ptr(),
+            None if P.order is None else P.order.data_ptr(), ctypes.byref(o),
+            info.data_ptr(), cfg, ws.data_ptr(), ws.numel(), _stream_ptr(P.device)))
+
+    cfg = _resolve_config(config, ("bicg_list", P.n_max, P.total_rows, P.total_nnz, P.batch), run, x, x0,
+                          BICG_BATCH_CONFIGS)
+    run(cfg)
+    return x, SolveInfo(info)
+
+
+def gather_values_batched(perm: torch.Tensor, val: torch.Tensor) -> torch.Tensor:
+    """out[s, m] = val[s, perm[m]] for val [B, nnz] (the values of every
+    A_s^T of a shared pattern, perm = permT of csr_transpose)."""
+    B, nnz = val.shape
+    out = torch.empty_like(val)
+    L.check("sla_gather_values_batched", L.lib().sla_gather_values_batched(
+        B, nnz, perm.data_ptr(), val.data_ptr(), out.data_ptr(), _stream_ptr(val.device)))
+    return out
+
+
 def _resolve_config(config, key, run, x, x0, candidates=BATCH_CONFIGS):
     """'auto': cached tuned choice if any, else the library's heuristic (0);
     'tune': time every kernel variant on this batch (two runs each, CUDA
@@ -777,27 +873,85 @@ def grad_values_batched_list(P: CSRList, lam: torch.Tensor, x: torch.Tensor) -> 
     return g
 
 
+_BATCH_SOLVERS = {"cg": (lambda *a, **k: cg_batched(*a, **k)), "bicgstab": (lambda *a, **k: bicgstab_batched(*a, **k))}
+_LIST_SOLVERS = {"cg": (lambda *a, **k: cg_batched_list(*a, **k)),
+                 "bicgstab": (lambda *a, **k: bicgstab_batched_list(*a, **k))}
+
+
+def _transposed_pattern(A: CSRMatrix) -> CSRMatrix:
+    """CSRMatrix of A^T's pattern (cached on A with its permT)."""
+    t = getattr(A, "_transpose_matrix", None)
+    if t is None:
+        rpT, cT, _ = transpose_of(A)
+        t = CSRMatrix(rpT, cT, check=False)
+        A._transpose_matrix = t
+    return t
+
+
 class BatchedSolve(torch.autograd.Function):
-    """x[s] = A_s^{-1} b[s] for a batch on one shared SPD pattern, with the
-    adjoint backward: one batched CG for all lambda_s, one gradient pass."""
+    """x[s] = A_s^{-1} b[s] for a batch on one shared pattern, with the
+    adjoint backward (Eq. 3 per system): one batched solve of A_s^T lambda_s
+    = dL/dx_s for all systems (CG on A for SPD systems; BiCGStab on the
+    shared CSR of A^T with every system's values gathered for nonsymmetric
+    ones), then one gradient pass."""
 
     @staticmethod
-    def forward(ctx, val, b, A, kw, strict):
-        x, info = cg_batched(A, val.detach().contiguous(), b.detach().contiguous(), **kw)
+    def forward(ctx, val, b, A, method, kw, strict):
+        x, info = _BATCH_SOLVERS[method](A, val.detach().contiguous(), b.detach().contiguous(), **kw)
         if strict is not None:
             _check_batch(info, "batched forward", strict)
         ctx.save_for_backward(val, x)
-        ctx.A, ctx.kw, ctx.strict = A, kw, strict
+        ctx.A, ctx.method, ctx.kw, ctx.strict = A, method, kw, strict
         return x
 
     @staticmethod
     def backward(ctx, gx):
         val, x = ctx.saved_tensors
         kw = {k: v for k, v in ctx.kw.items() if k not in ("x0", "out")}
-        lam, info = cg_batched(ctx.A, val.detach().contiguous(), gx.contiguous().to(torch.float64), **kw)
+        v = val.detach().contiguous()
+        g = gx.contiguous().to(torch.float64)
+        if ctx.method == "cg":
+            lam, info = cg_batched(ctx.A, v, g, **kw)
+        else:
+            AT = _transposed_pattern(ctx.A)
+            valT = gather_values_batched(transpose_of(ctx.A)[2], v.view(x.shape[0], -1))
+            lam, info = bicgstab_batched(AT, valT, g, **kw)
         if ctx.strict is not None:
             _check_batch(info, "batched adjoint", ctx.strict)
-        return grad_values_batched_shared(ctx.A, lam, x), lam, None, None, None
+        return grad_values_batched_shared(ctx.A, lam, x), lam, None, None, None, None
+
+
+class BatchedListSolve(torch.autograd.Function):
+    """Distinct patterns (the paper's SparseTensorList, Sec. 3.1 and Tab. 1):
+    x_s = A_s^{-1} b_s for every system in one launch, each with its own
+    gradient (Eq. 3): one batched solve of A_s^T lambda_s = dL/dx_s (CG on
+    A_s, or BiCGStab on the list's transposes), then -lambda_s,i x_s,j on
+    every pattern.  Values and right-hand sides are concatenated."""
+
+    @staticmethod
+    def forward(ctx, val, b, P, method, kw, strict):
+        x, info = _LIST_SOLVERS[method](P, val.detach().contiguous(), b.detach().contiguous(), **kw)
+        if strict is not None:
+            _check_batch(info, "batched list forward", strict)
+        ctx.save_for_backward(val, x)
+        ctx.P, ctx.method, ctx.kw, ctx.strict = P, method, kw, strict
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        val, x = ctx.saved_tensors
+        kw = {k: v for k, v in ctx.kw.items() if k not in ("x0", "out")}
+        v = val.detach().contiguous()
+        g = gx.contiguous().to(torch.float64)
+        if ctx.method == "cg":
+            lam, info = cg_batched_list(ctx.P, v, g, **kw)
+        else:
+            PT, permT = ctx.P.transpose()
+            valT = gather_values(permT, v)
+            lam, info = bicgstab_batched_list(PT, valT, g, **kw)
+        if ctx.strict is not None:
+            _check_batch(info, "batched list adjoint", ctx.strict)
+        return grad_values_batched_list(ctx.P, lam, x), lam, None, None, None, None
 
 
 def _check_batch(info: SolveInfo, what: str, strict: bool):
@@ -812,11 +966,23 @@ def _check_batch(info: SolveInfo, what: str, strict: bool):
         warnings.warn(msg)
 
 
-def solve_batched(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, strict: bool | None = True,
-                  **kw) -> torch.Tensor:
-    """Differentiable batched SPD solve on a shared pattern: val [B, nnz],
-    b [B, n] -> x [B, n]."""
-    return BatchedSolve.apply(val, b, A, kw, strict)
+def solve_batched(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, method: str = "cg",
+                  strict: bool | None = True, **kw) -> torch.Tensor:
+    """Differentiable batched solve on a shared pattern: val [B, nnz], b
+    [B, n] -> x [B, n]; method "cg" (SPD) or "bicgstab" (nonsymmetric)."""
+    if method not in _BATCH_SOLVERS:
+        raise ValueError("method must be 'cg' or 'bicgstab'")
+    return BatchedSolve.apply(val, b, A, method, kw, strict)
+
+
+def solve_batched_list(P: CSRList, val: torch.Tensor, b: torch.Tensor, *, method: str = "cg",
+                       strict: bool | None = True, **kw) -> torch.Tensor:
+    """Differentiable solve of a list of distinct patterns (concatenated
+    val [total_nnz], b [total_rows] -> x [total_rows]); every system gets
+    its own gradient.  method "cg" (SPD) or "bicgstab" (nonsymmetric)."""
+    if method not in _LIST_SOLVERS:
+        raise ValueError("method must be 'cg' or 'bicgstab'")
+    return BatchedListSolve.apply(val, b, P, method, kw, strict)
 
 
 # ---------------------------------------------------------------------------

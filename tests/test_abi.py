@@ -153,6 +153,49 @@ def test_adjoint_rejects_aliased_outputs_without_launch():
                                           fake, ws, big, None) == L.SLA_ERR_INVALID
 
 
+def test_batched_bicgstab_and_list_transpose_reject_bad_arguments_without_launch():
+    lib = L.lib()
+    fake = ctypes.c_void_p(0x1000)
+    A = L.SlaCsr(10, 20, fake, fake)
+    o = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0, 0)
+    ws, big = ctypes.c_void_p(0x100000), ctypes.c_size_t(1 << 40)
+    x = ctypes.c_void_p(0x2000)
+
+    def shared(batch=4, opts=o, b=fake, xx=x, cfg=0, w=ws, nb=big):
+        return lib.sla_bicgstab_batched_shared(ctypes.byref(A), batch, fake, b, xx, ctypes.byref(opts), fake,
+                                               cfg, w, nb, None)
+    assert shared(batch=-1) == L.SLA_ERR_INVALID
+    assert shared(batch=0) == L.SLA_OK                                      # nothing to do
+    assert shared(xx=fake) == L.SLA_ERR_INVALID                             # b == x
+    assert shared(cfg=32) == L.SLA_ERR_INVALID                              # unknown config bit
+    assert shared(cfg=4) == L.SLA_ERR_INVALID                               # unknown block size code
+    flags = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0, L.SLA_FLAG_HOST_LOOP)
+    assert shared(opts=flags) == L.SLA_ERR_INVALID                          # flags not offered
+    ggt = L.SlaOpts(1e-8, 0.0, 100, 2, L.SLA_PRECOND_GGT, 0, 0)
+    assert shared(opts=ggt) == L.SLA_ERR_INVALID
+    need = L.workspace_size(L.SLA_WS_BATCHED, 10, 20, 4)
+    assert shared(nb=need - 1) == L.SLA_ERR_WORKSPACE
+    assert shared(w=ctypes.c_void_p(0x100010)) == L.SLA_ERR_WORKSPACE
+    assert lib.sla_bicgstab_batched_list(3, 10, 30, None, fake, fake, fake, fake, fake, x, None,
+                                         ctypes.byref(o), fake, 0, ws, big, None) == L.SLA_ERR_INVALID
+    assert lib.sla_bicgstab_batched_list(3, 10, 30, fake, fake, fake, fake, fake, fake, fake, None,
+                                         ctypes.byref(o), fake, 0, ws, big, None) == L.SLA_ERR_INVALID
+    # list transpose: empty list, null pointers, aliasing, workspace
+    assert lib.sla_csr_list_transpose(0, 0, 0, None, None, None, None, None, None, None, None, 0,
+                                      None) == L.SLA_OK
+    assert lib.sla_csr_list_transpose(2, 10, 20, fake, fake, fake, fake, None, x, x, ws, big,
+                                      None) == L.SLA_ERR_INVALID
+    assert lib.sla_csr_list_transpose(2, 10, 20, fake, fake, fake, fake, fake, x, ctypes.c_void_p(0x3000),
+                                      ws, big, None) == L.SLA_ERR_INVALID        # rowptrT == rowptr
+    lt = L.workspace_size(L.SLA_WS_LIST_TRANSPOSE, 10, 20)
+    assert lt >= L.workspace_size(L.SLA_WS_TRANSPOSE, 10, 20)
+    assert lib.sla_csr_list_transpose(2, 10, 20, fake, fake, fake, fake, ctypes.c_void_p(0x4000), x,
+                                      ctypes.c_void_p(0x3000), ws, lt - 1, None) == L.SLA_ERR_WORKSPACE
+    # batched gather: overlapping output
+    assert lib.sla_gather_values_batched(2, 20, fake, x, ctypes.c_void_p(0x2000 + 8 * 39), None) == L.SLA_ERR_INVALID
+    assert lib.sla_gather_values_batched(-1, 20, fake, x, fake, None) == L.SLA_ERR_INVALID
+
+
 def test_multi_rhs_arguments_rejected_without_launch():
     lib = L.lib()
     fake = ctypes.c_void_p(0x1000)

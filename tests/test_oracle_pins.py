@@ -1073,3 +1073,43 @@ def test_pcg_omp_edge_cases_match_oracle():
     _, io = oracle.pcg_omp(rpi, ci, vi, np.array([1.0, -1.0]), precond="none", threads=2)
     _, ioo = oracle.pcg(rpi, ci, vi, np.array([1.0, -1.0]), precond="none")
     assert io["status"] == ioo["status"] == 3
+
+
+# ---------------------------------------------------------------- nonsymmetric batch generators
+
+def test_convdiff2d_generator_is_diffusion_plus_upwind():
+    """With zero velocity the rectangle generator is the diffusion operator
+    (square case: the same CSR as diffusion2d); with velocity w the
+    difference is the first-order upwind matrix: +|w_x| + |w_y| on the
+    diagonal, -|w_x| on the upstream x-neighbour, -|w_y| on the upstream
+    y-neighbour, nothing downstream."""
+    rng = np.random.default_rng(0)
+    N = 5
+    cx = np.exp(rng.standard_normal((N, N + 1)))
+    cy = np.exp(rng.standard_normal((N + 1, N)))
+    d0 = I.diffusion2d(cx, cy)
+    c0 = I.convdiff2d_rect(cx, cy, 0.0, 0.0)
+    for a, b in zip(d0, c0):
+        assert np.array_equal(a, b)
+    Ny, Nx = 3, 4
+    cx = np.exp(rng.standard_normal((Ny, Nx + 1)))
+    cy = np.exp(rng.standard_normal((Ny + 1, Nx)))
+    for wx, wy in ((2.5, -1.5), (-3.0, 0.7)):
+        D = dense(*I.convdiff2d_rect(cx, cy, 0.0, 0.0))
+        C = dense(*I.convdiff2d_rect(cx, cy, wx, wy))
+        U = np.zeros_like(D)
+        for q in range(Ny):
+            for p in range(Nx):
+                i = p + Nx * q
+                U[i, i] = abs(wx) + abs(wy)
+                up_x = p - 1 if wx > 0 else p + 1
+                up_y = q - 1 if wy > 0 else q + 1
+                if 0 <= up_x < Nx:
+                    U[i, up_x + Nx * q] = -abs(wx)
+                if 0 <= up_y < Ny:
+                    U[i, p + Nx * up_y] = -abs(wy)
+        assert np.allclose(C - D, U, rtol=0, atol=1e-14)
+        assert not np.allclose(C, C.T)
+        # weak diagonal dominance everywhere, strict on the boundary rows
+        off = np.abs(C).sum(axis=1) - np.abs(np.diag(C))
+        assert (np.diag(C) - off >= -1e-12).all() and (np.diag(C) - off > 1e-12).any()
