@@ -67,6 +67,12 @@ def _load_omp():
     global _omp_lib
     with _lock:
         if _omp_lib is None:
+            # threads that wait at the end of a parallel loop sleep instead of
+            # spinning (read when the OpenMP runtime loads): with a core taken
+            # by another process, spinning threads slowed an 8-thread run of a
+            # 64^3 system 10x; at the benchmark's sizes a loop runs for
+            # milliseconds, so the wake-up costs nothing measurable
+            os.environ.setdefault("OMP_WAIT_POLICY", "passive")
             build()
             lib = ctypes.CDLL(_OMP_LIB_PATH)
             P = ctypes.c_void_p
