@@ -16,10 +16,18 @@ from tests.gpu_util import csr, elementwise_rel, rel, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def _check_systems(rps, cs, vals, bs, xs, info, rtol, idx=None, iters_tol=0.05):
+# BiCGStab's iteration count is sensitive to rounding: on the 40 systems of
+# the shared-pattern test, the oracle's own count moved by up to 9 % (88 ->
+# 96) when b was perturbed by 1e-15 relative noise.  The GPU sums in another
+# order, so its count is held to the oracle's within that spread (12 %, at
+# least 3); the solution itself is held to 1e-8 element by element.
+ITERS_TOL = 0.12
+
+
+def _check_systems(rps, cs, vals, bs, xs, info, rtol, idx=None, iters_tol=ITERS_TOL):
     """Each system against the oracle: its solution x* (rtol 1e-13) element
     by element and in norm to 1e-8, its status, and its iteration count at
-    the same rtol to within max(3, 5 %)."""
+    the same rtol to within the rounding spread (ITERS_TOL)."""
     its = np.atleast_1d(info.iters)
     st = np.atleast_1d(info.status)
     idx = range(len(bs)) if idx is None else idx
