@@ -498,6 +498,9 @@ int or_bicgstab(int32_t n, const int32_t* rowptr, const int32_t* col,
       if (omega == 0.0) { status = OR_BREAKDOWN; break; }
       rho_prev = rho;
     }
+    /* a start that already meets the stopping test is converged (as in
+       pcg_core): the loop above then runs no iteration */
+    if (status == OR_NOT_CONVERGED && rnorm <= thresh) status = OR_OK;
     if (status != OR_OK) break;
     or_spmv(n, rowptr, col, val, x, t);
     for (int32_t i = 0; i < n; ++i) r[i] = b[i] - t[i];

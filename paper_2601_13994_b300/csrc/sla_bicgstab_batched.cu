@@ -182,6 +182,7 @@ __device__ void bicg_system(const BicgBatchDesc& d, int n, const int* __restrict
       const double snorm = sqrt(a2[0]);
       if (snorm <= thresh) {  // half-step exit: x += alpha p^
         for (int i = tid; i < n; i += NT) x[i] = fma(alpha, ph[i], x[i]);
+        __syncthreads();  // the true residual next gathers other threads' x
         rnorm = snorm;
         status = SLA_OK;
         break;
@@ -229,6 +230,8 @@ __device__ void bicg_system(const BicgBatchDesc& d, int n, const int* __restrict
       rho_prev = rho;
       rho = a4[1];
     }
+    // a start that already meets the stopping test is converged
+    if (status == SLA_NOT_CONVERGED && rnorm <= thresh) status = SLA_OK;
     if (status != SLA_OK) break;
     // true residual
     double tt[1] = {0.0};

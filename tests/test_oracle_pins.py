@@ -1113,3 +1113,21 @@ def test_convdiff2d_generator_is_diffusion_plus_upwind():
         # weak diagonal dominance everywhere, strict on the boundary rows
         off = np.abs(C).sum(axis=1) - np.abs(np.diag(C))
         assert (np.diag(C) - off >= -1e-12).all() and (np.diag(C) - off > 1e-12).any()
+
+
+def test_bicgstab_warm_start_at_the_solution_is_converged():
+    """A start that already meets the stopping test ||r|| <= max(rtol ||b||,
+    atol) is converged after 0 iterations, for BiCGStab as for PCG."""
+    rp, c, v = I.convdiff3d(6, 10.0)
+    b = I.rhs_uniform(len(rp) - 1, 3)
+    xs = np.linalg.solve(dense(rp, c, v), b)
+    x, io = oracle.bicgstab(rp, c, v, b, rtol=1e-8, x0=xs)
+    assert io["status"] == 0 and io["iters"] == 0 and np.array_equal(x, xs)
+    rp2, c2, v2 = I.poisson2d(6)
+    b2 = I.rhs_uniform(36, 3)
+    xs2 = np.linalg.solve(dense(rp2, c2, v2), b2)
+    _, io2 = oracle.pcg(rp2, c2, v2, b2, rtol=1e-8, x0=xs2)
+    assert io2["status"] == 0 and io2["iters"] == 0
+    # a start that does not meet it still iterates
+    x, io = oracle.bicgstab(rp, c, v, b, rtol=1e-8, x0=0.5 * xs)
+    assert io["status"] == 0 and io["iters"] > 0
