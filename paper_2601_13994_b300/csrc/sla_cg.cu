@@ -241,16 +241,27 @@ __global__ void __launch_bounds__(kTileThreads) cg_spmv_pq_kernel(CgPtrs P) {
   });
 }
 
-// K1 on the TMA-pipelined tiles (see sla_tma.cuh).  Three blocks per SM: the
-// p.q epilogue and the state update need more than the 56 registers of four
-// blocks (spills measured 1 % slower in PCG).
-__global__ void __launch_bounds__(tma::kThreads, 3) cg_spmv_pq_tma_kernel(CgPtrs P) {
+// K1 on the TMA-pipelined tiles (see sla_tma.cuh), four blocks per SM.  The
+// matrix comes from the device descriptor through a shared-memory record
+// (tma::MatShared): with the descriptor's fields in registers, the p.q
+// epilogue and the state update needed 68 registers (three blocks per SM;
+// forced to 56 they spilled).
+__global__ void __launch_bounds__(tma::kThreads, 4) cg_spmv_pq_tma_kernel(CgPtrs P) {
   extern __shared__ __align__(128) unsigned char dsm[];
   tma::Smem& sm = *reinterpret_cast<tma::Smem*>(dsm);
+  __shared__ tma::MatRecord mat;
   if (__ldcg(&P.st->phase) != kPhaseRun) return;
-  const KrylovDesc d = *P.d;
+  if (threadIdx.x == 0) {
+    const KrylovDesc* d = P.d;
+    mat.n = d->n;
+    mat.nnz = d->nnz;
+    mat.rowptr = d->rowptr;
+    mat.col = d->col;
+    mat.val = d->sym_scale ? (const void*)P.ahat : (const void*)d->val;
+  }
+  __syncthreads();
   k1_body<tma::kThreads>(P, sm.red, &sm.last, [&](auto&& epi) {
-    tma::spmv_pipeline(d.n, d.nnz, d.rowptr, d.col, cg_vals(P, d), P.p, P.p, sm, &P.st->err, epi);
+    tma::spmv_pipeline_m<1, double>(tma::MatShared<double>{&mat}, P.p, P.p, sm, &P.st->err, epi);
   });
 }
 

@@ -191,12 +191,11 @@ __device__ __forceinline__ void two_row_sum(int a, int m, int e, ColAt&& col_at,
 // by all kThreads threads of the block, with `sm` in dynamic shared memory.
 // The producer warp returns from this function as soon as its copies have
 // landed; nothing after the call may rely on its values.
-template <int RPT = 1, class V, class XAt, class AuxAt, class Epi>
-__device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restrict__ rowptr,
-                                              const int* __restrict__ col,
-                                              const V* __restrict__ val, XAt x, AuxAt aux,
-                                              SmemT<V, RPT>& sm, int* err, Epi&& epi) {
+template <int RPT = 1, class V, class Mat, class XAt, class AuxAt, class Epi>
+__device__ __forceinline__ void spmv_pipeline_m(const Mat& mat, XAt x, AuxAt aux, SmemT<V, RPT>& sm, int* err,
+                                                Epi&& epi) {
   using X = decltype(gather_at(x, 0));
+  const int n = mat.n(), nnz = mat.nnz();
   static_assert(RPT == 1 || RPT == 2, "one or two rows per consumer thread");
   constexpr int kVE = 16 / (int)sizeof(V);  // values per 16 bytes
   constexpr int kTR = kRows * RPT;          // rows per tile
@@ -211,8 +210,8 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
   }
   __syncthreads();
   const int ntiles = (n + kTR - 1) / kTR;
-  const bool aligned = ((reinterpret_cast<uintptr_t>(rowptr) | reinterpret_cast<uintptr_t>(col) |
-                         reinterpret_cast<uintptr_t>(val)) & 15u) == 0;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(mat.rowptr()) | reinterpret_cast<uintptr_t>(mat.col()) |
+                         reinterpret_cast<uintptr_t>(mat.val())) & 15u) == 0;
   if (warp == kConsumerWarps) {
     // ---------------- producer warp
     // The row-pointer bounds of the next 32 tiles are loaded by the 32 lanes
@@ -225,8 +224,8 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
       int k0l = 0, k1l = 0;
       if (tl < ntiles) {
         const int r0 = tl * kTR;
-        k0l = __ldg(rowptr + r0);
-        k1l = __ldg(rowptr + r0 + min(kTR, n - r0));
+        k0l = __ldg(mat.rowptr() + r0);
+        k1l = __ldg(mat.rowptr() + r0 + min(kTR, n - r0));
       }
       for (int j = 0; j < 32; ++j) {
         const int t = tb + j * gridDim.x;
@@ -266,9 +265,9 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
               const unsigned bc = (unsigned)(kb_c - ka_c) * 4u;
               const unsigned bv = (unsigned)(kb_v - ka_v) * (unsigned)sizeof(V);
               mbar_arrive_expect_tx(&sm.full[s], (unsigned)(kTR * 4) + bc + bv);
-              bulk_g2s(S.rp, rowptr + r0, kTR * 4, &sm.full[s]);
-              if (bc) bulk_g2s(S.col, col + ka_c, bc, &sm.full[s]);
-              if (bv) bulk_g2s(S.val, val + ka_v, bv, &sm.full[s]);
+              bulk_g2s(S.rp, mat.rowptr() + r0, kTR * 4, &sm.full[s]);
+              if (bc) bulk_g2s(S.col, mat.col() + ka_c, bc, &sm.full[s]);
+              if (bv) bulk_g2s(S.val, mat.val() + ka_v, bv, &sm.full[s]);
             } else {
               mbar_arrive(&sm.full[s]);
             }
@@ -301,8 +300,8 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
     const int r0 = S.hdr[6], nr = S.hdr[7];
     if (mode == 0) {
       const int k1 = S.hdr[1], ka_c = S.hdr[2], kb_c = S.hdr[3], ka_v = S.hdr[4], kb_v = S.hdr[5];
-      auto col_at = [&](int kk) { return kk < kb_c ? S.col[kk - ka_c] : __ldg(col + kk); };
-      auto val_at = [&](int kk) { return as_x<X>(kk < kb_v ? S.val[kk - ka_v] : __ldg(val + kk)); };
+      auto col_at = [&](int kk) { return kk < kb_c ? S.col[kk - ka_c] : __ldg(mat.col() + kk); };
+      auto val_at = [&](int kk) { return as_x<X>(kk < kb_v ? S.val[kk - ka_v] : __ldg(mat.val() + kk)); };
       if constexpr (RPT == 1) {
         const auto av = aux_at(aux, r0 + tid);
         const int a = S.rp[tid];
@@ -322,13 +321,62 @@ __device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restr
       }
     } else {
       for (int rr = warp; rr < nr; rr += kConsumerWarps) {
-        const X acc = warp_row(rowptr, col, val, x, r0 + rr, lane);
+        const X acc = warp_row(mat.rowptr(), mat.col(), mat.val(), x, r0 + rr, lane);
         if (lane == 0) epi(r0 + rr, acc, aux_at(aux, r0 + rr));
       }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&sm.empty[s]);
   }
+}
+
+
+// The matrix of a pipeline by value: for kernels that receive it as launch
+// parameters (the standalone SpMV), where the fields cost no registers.
+template <class V>
+struct MatByValue {
+  int n_, nnz_;
+  const int* rp_;
+  const int* c_;
+  const V* v_;
+  __device__ __forceinline__ int n() const { return n_; }
+  __device__ __forceinline__ int nnz() const { return nnz_; }
+  __device__ __forceinline__ const int* rowptr() const { return rp_; }
+  __device__ __forceinline__ const int* col() const { return c_; }
+  __device__ __forceinline__ const V* val() const { return v_; }
+};
+
+// The matrix of a pipeline read from a small shared-memory record at every
+// use, for kernels that find it in a device-side descriptor (one captured
+// graph serves every call): loaded from device memory, the pointers would
+// stay live in registers through the whole tile loop although only the
+// producer and the rare fallback paths use them; the volatile shared loads
+// keep them out of the loop's registers.  With this record the PCG kernel
+// K1 (SpMV + p.q) fits the 56 registers of four blocks per SM without
+// spilling.
+struct MatRecord {
+  int n, nnz;
+  const int* rowptr;
+  const int* col;
+  const void* val;
+};
+
+template <class V>
+struct MatShared {
+  const volatile MatRecord* r;
+  __device__ __forceinline__ int n() const { return r->n; }
+  __device__ __forceinline__ int nnz() const { return r->nnz; }
+  __device__ __forceinline__ const int* rowptr() const { return r->rowptr; }
+  __device__ __forceinline__ const int* col() const { return r->col; }
+  __device__ __forceinline__ const V* val() const { return (const V*)r->val; }
+};
+
+template <int RPT = 1, class V, class XAt, class AuxAt, class Epi>
+__device__ __forceinline__ void spmv_pipeline(int n, int nnz, const int* __restrict__ rowptr,
+                                              const int* __restrict__ col,
+                                              const V* __restrict__ val, XAt x, AuxAt aux,
+                                              SmemT<V, RPT>& sm, int* err, Epi&& epi) {
+  spmv_pipeline_m<RPT, V>(MatByValue<V>{n, nnz, rowptr, col, val}, x, aux, sm, err, epi);
 }
 
 }  // namespace tma
