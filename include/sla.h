@@ -620,9 +620,14 @@ int32_t sla_adjoint_backward(const sla_csr* A, const sla_csr_t* AT,
  * batch and a converged system frees its CTA for the next.  The Krylov
  * vectors stay in shared memory when 5 n doubles fit, else in the
  * workspace.  config: 0 = automatic; low 4 bits 1/2/3 = 256/512/1024
- * threads per CTA, bit 4 set = vectors in global memory, bit 32 (lists) = no
- * block teams for the large systems (the autotuner in
- * the Python layer times these).  The call only enqueues kernels (no host
+ * threads per CTA, value 16 = vectors in global memory, bits 8-9 = log2 of the
+ * threads per row in the SpMVs (1, 2, 4, 8: a row summed by that many adjacent
+ * threads, then a fixed butterfly), bits 10-11 = log2 of the systems per CTA
+ * (1, 2, 4: each solved by NT / SPC threads with a named barrier of their
+ * own; only with one thread per row), value 32 (lists) = no block teams
+ * for the large systems; bits 8-11 shape the single-CTA kernel (for lists
+ * with the teams off); other bits SLA_ERR_INVALID (the autotuner in the
+ * Python layer times these shapes per batch).  The call only enqueues kernels (no host
  * synchronisation), so it can be captured in a CUDA graph.
  * Shared pattern: val [batch, nnz], b and x [batch, n] row-major.
  * Workspace: SLA_WS_BATCHED with (n, batch). */

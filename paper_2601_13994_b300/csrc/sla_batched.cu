@@ -43,10 +43,50 @@ struct BatchDesc {
                               // solved by block teams (0: none)
 };
 
-template <int NT>
-struct BSmem {
-  double red[2 * NT + 2];
-  int sys;
+// The threads that solve one system: the whole CTA (SPC = 1), or one of SPC
+// equal slices of it (systems per CTA), which synchronise on a named barrier
+// of their own -- slices finish their systems at different times, so no
+// CTA-wide barrier may be used once SPC > 1.
+template <int GT, int SPC>
+struct Grp {
+  int id;  // slice 0 .. SPC-1
+  int t;   // thread index in the slice
+  __device__ __forceinline__ void sync() const {
+    if constexpr (SPC == 1) {
+      __syncthreads();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(id + 1), "r"(GT) : "memory");
+    }
+  }
+};
+
+// block_sums over the GT threads of a group (same parking scheme and the
+// same fixed order, so SPC = 1 gives block_sums' bits).
+template <int GT, int SPC, int NV, int M>
+__device__ __forceinline__ void group_sums(const Grp<GT, SPC>& g, double (&v)[NV], double (&sh)[M]) {
+  static_assert(GT % kWarp == 0 && GT <= 1024 && NV <= GT / kWarp, "group size");
+  static_assert(M >= NV * GT + NV, "reduction scratch too small");
+  const int lane = g.t & 31, w = g.t >> 5;
+  g.sync();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) sh[j * GT + g.t] = v[j];
+  g.sync();
+  if (w < NV) {
+    const double* col = sh + w * GT + lane;
+    double s = col[0];
+#pragma unroll
+    for (int k = 1; k < GT / kWarp; ++k) s += col[kWarp * k];
+    s = warp_sum(s);
+    if (lane == 0) sh[NV * GT + w] = s;
+  }
+  g.sync();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = sh[NV * GT + j];
+}
+
+template <int GT>
+struct BRed {
+  double red[2 * GT + 2];
 };
 
 // Sum of row i of (rp, cl, v) times w, entries in order.  w may live in
@@ -62,20 +102,51 @@ __device__ __forceinline__ double brow(const int* __restrict__ rp, const int* __
   return acc;
 }
 
-template <int NT>
-__device__ void solve_system(const BatchDesc& d, int n, const int* __restrict__ rp,
+// f(i, (A w)_i) for every row i of the system.  TPR = 1: a row per thread
+// (the sum in entry order).  TPR > 1 (threads per row): TPR adjacent threads
+// of a warp share a row, thread j taking entries a + j, a + j + TPR, ...,
+// then a fixed xor butterfly; f runs in the slice's first thread.  The pass
+// count is the same for every thread of the group, so the shuffles always
+// see full warps.  Long rows are where more threads per row pay; the
+// autotuner measures it per batch.
+template <int GT, int TPR, class F>
+__device__ __forceinline__ void rows_apply(int gt, int n, const int* __restrict__ rp, const int* __restrict__ cl,
+                                           const double* __restrict__ v, const double* w, F&& f) {
+  if constexpr (TPR == 1) {
+    for (int i = gt; i < n; i += GT) f(i, brow(rp, cl, v, w, i));
+  } else {
+    static_assert(TPR == 2 || TPR == 4 || TPR == 8, "threads per row");
+    constexpr int RPP = GT / TPR;  // rows per pass
+    const int sub = gt & (TPR - 1);
+    const int passes = (n + RPP - 1) / RPP;
+    for (int k = 0; k < passes; ++k) {
+      const int i = gt / TPR + k * RPP;
+      double acc = 0.0;
+      if (i < n) {
+        const int a = __ldg(rp + i), e = __ldg(rp + i + 1);
+        for (int kk = a + sub; kk < e; kk += TPR) acc = fma(__ldg(v + kk), w[__ldg(cl + kk)], acc);
+      }
+#pragma unroll
+      for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (i < n && sub == 0) f(i, acc);
+    }
+  }
+}
+
+template <int GT, int SPC, int TPR>
+__device__ void solve_system(const BatchDesc& d, const Grp<GT, SPC>& g, int n, const int* __restrict__ rp,
                              const int* __restrict__ cl, const double* __restrict__ v,
                              const double* __restrict__ b, double* __restrict__ x, double* vec,
-                             BSmem<NT>& sm, sla_info* info) {
+                             BRed<GT>& sm, sla_info* info) {
   double* r = vec;
   double* z = vec + n;
   double* p = vec + 2 * (size_t)n;
   double* q = vec + 3 * (size_t)n;
   double* dinv = vec + 4 * (size_t)n;
-  const int t = threadIdx.x;
+  const int t = g.t;
   // ---- init: dinv, r = b - A x0, bnorm, bad diagonal
   double acc[2] = {0.0, 0.0};  // bb, bad
-  for (int i = t; i < n; i += NT) {
+  for (int i = t; i < n; i += GT) {
     double diag = 0.0;
     for (int k = __ldg(rp + i); k < __ldg(rp + i + 1); ++k)
       if (__ldg(cl + k) == i) diag += __ldg(v + k);
@@ -88,7 +159,7 @@ __device__ void solve_system(const BatchDesc& d, int n, const int* __restrict__ 
     if (!d.use_x0) x[i] = 0.0;
     acc[0] = fma(b[i], b[i], acc[0]);
   }
-  block_sums<NT, 2>(acc, sm.red);
+  group_sums(g, acc, sm.red);
   const double bnorm = sqrt(acc[0]);
   const double thresh = fmax(d.rtol * bnorm, d.atol);
   sla_info inf{0, SLA_NOT_CONVERGED, 0.0, 0.0};
@@ -97,7 +168,7 @@ __device__ void solve_system(const BatchDesc& d, int n, const int* __restrict__ 
     return;
   }
   if (bnorm == 0.0) {
-    for (int i = t; i < n; i += NT) x[i] = 0.0;
+    for (int i = t; i < n; i += GT) x[i] = 0.0;
     if (t == 0) *info = sla_info{0, SLA_OK, 0.0, 0.0};
     return;
   }
@@ -106,16 +177,16 @@ __device__ void solve_system(const BatchDesc& d, int n, const int* __restrict__ 
   for (int restart = 0; restart <= d.max_restarts; ++restart) {
     // r = b - A x ; z = dinv r ; p = z ; rho = r.z
     double s2[2] = {0.0, 0.0};  // rz, rr
-    for (int i = t; i < n; i += NT) {
-      const double ri = b[i] - brow(rp, cl, v, x, i);
+    rows_apply<GT, TPR>(t, n, rp, cl, v, x, [&](int i, double ax) {
+      const double ri = b[i] - ax;
       const double zi = dinv[i] * ri;
       r[i] = ri;
       z[i] = zi;
       p[i] = zi;
       s2[0] = fma(ri, zi, s2[0]);
       s2[1] = fma(ri, ri, s2[1]);
-    }
-    block_sums<NT, 2>(s2, sm.red);  // also orders the p writes before the SpMV
+    });
+    group_sums(g, s2, sm.red);  // also orders the p writes before the SpMV
     double rho = s2[0];
     rnorm = sqrt(s2[1]);
     status = SLA_NOT_CONVERGED;
@@ -125,17 +196,16 @@ __device__ void solve_system(const BatchDesc& d, int n, const int* __restrict__ 
     }
     while (!(rnorm <= thresh) && it < d.max_iter) {
       double pq[1] = {0.0};
-      for (int i = t; i < n; i += NT) {
-        const double qi = brow(rp, cl, v, p, i);
+      rows_apply<GT, TPR>(t, n, rp, cl, v, p, [&](int i, double qi) {
         q[i] = qi;
         pq[0] = fma(p[i], qi, pq[0]);
-      }
-      block_sums<NT, 1>(pq, sm.red);
+      });
+      group_sums(g, pq, sm.red);
       if (!isfinite(pq[0])) { status = SLA_BREAKDOWN; break; }
       if (!(pq[0] > 0.0)) { status = SLA_NOT_SPD; break; }
       const double alpha = rho / pq[0];
       double u[2] = {0.0, 0.0};  // rz, rr
-      for (int i = t; i < n; i += NT) {
+      for (int i = t; i < n; i += GT) {
         x[i] = fma(alpha, p[i], x[i]);
         const double ri = fma(-alpha, q[i], r[i]);
         const double zi = dinv[i] * ri;
@@ -144,7 +214,7 @@ __device__ void solve_system(const BatchDesc& d, int n, const int* __restrict__ 
         u[0] = fma(ri, zi, u[0]);
         u[1] = fma(ri, ri, u[1]);
       }
-      block_sums<NT, 2>(u, sm.red);
+      group_sums(g, u, sm.red);
       const double rho_new = u[0];
       rnorm = sqrt(u[1]);
       ++it;
@@ -152,19 +222,19 @@ __device__ void solve_system(const BatchDesc& d, int n, const int* __restrict__ 
       if (rnorm <= thresh) { status = SLA_OK; break; }
       if (!(rho_new > 0.0)) { status = SLA_NOT_SPD; break; }
       const double beta = rho_new / rho;
-      for (int i = t; i < n; i += NT) p[i] = fma(beta, p[i], z[i]);
-      __syncthreads();
+      for (int i = t; i < n; i += GT) p[i] = fma(beta, p[i], z[i]);
+      g.sync();
       rho = rho_new;
     }
     if (rnorm <= thresh) status = SLA_OK;
     if (status != SLA_OK) break;
     // true residual
     double tt[1] = {0.0};
-    for (int i = t; i < n; i += NT) {
-      const double ti = b[i] - brow(rp, cl, v, x, i);
+    rows_apply<GT, TPR>(t, n, rp, cl, v, x, [&](int i, double ax) {
+      const double ti = b[i] - ax;
       tt[0] = fma(ti, ti, tt[0]);
-    }
-    block_sums<NT, 1>(tt, sm.red);
+    });
+    group_sums(g, tt, sm.red);
     if (sqrt(tt[0]) <= 2.0 * thresh) break;
     if (restart == d.max_restarts) {
       status = SLA_NOT_CONVERGED;
@@ -172,11 +242,11 @@ __device__ void solve_system(const BatchDesc& d, int n, const int* __restrict__ 
     }
   }
   double tt[1] = {0.0};
-  for (int i = t; i < n; i += NT) {
-    const double ti = b[i] - brow(rp, cl, v, x, i);
+  rows_apply<GT, TPR>(t, n, rp, cl, v, x, [&](int i, double ax) {
+    const double ti = b[i] - ax;
     tt[0] = fma(ti, ti, tt[0]);
-  }
-  block_sums<NT, 1>(tt, sm.red);
+  });
+  group_sums(g, tt, sm.red);
   inf.iters = it;
   inf.status = status;
   inf.rel_res = rnorm / bnorm;
@@ -184,15 +254,20 @@ __device__ void solve_system(const BatchDesc& d, int n, const int* __restrict__ 
   if (t == 0) *info = inf;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) batched_pcg_kernel(BatchDesc d) {
+// NT threads per CTA, SPC systems per CTA at a time (NT / SPC threads each),
+// TPR threads per row in the SpMVs.
+template <int NT, int SPC, int TPR>
+__global__ void __launch_bounds__(NT, 1024 / NT) batched_pcg_kernel(BatchDesc d) {
+  constexpr int GT = NT / SPC;
   extern __shared__ __align__(16) double dyn[];
-  __shared__ BSmem<NT> sm;
+  __shared__ BRed<GT> red[SPC];
+  __shared__ int sys[SPC];
+  const Grp<GT, SPC> g{(int)threadIdx.x / GT, (int)threadIdx.x % GT};
   for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) sm.sys = (int)atomicAdd(d.next, 1u);
-    __syncthreads();
-    const int k = sm.sys;
+    g.sync();
+    if (g.t == 0) sys[g.id] = (int)atomicAdd(d.next, 1u);
+    g.sync();
+    const int k = sys[g.id];
     if (k >= d.batch) break;
     const int s = d.order ? d.order[k] : k;
     int n;
@@ -220,12 +295,12 @@ __global__ void __launch_bounds__(NT) batched_pcg_kernel(BatchDesc d) {
       b = d.b + n0;
       x = d.x + n0;
     }
-    double* vec = n <= d.smem_rows ? dyn : d.gvec + 5 * row0;
-    solve_system<NT>(d, n, rp, cl, v, b, x, vec, sm, d.info + s);
+    double* vec = n <= d.smem_rows ? dyn + (size_t)g.id * 5 * d.smem_rows : d.gvec + 5 * row0;
+    solve_system<GT, SPC, TPR>(d, g, n, rp, cl, v, b, x, vec, red[g.id], d.info + s);
   }
 }
 
-template <int NT>
+template <int NT, int SPC, int TPR>
 int launch_batched(const BatchDesc& d0, bool use_smem, cudaStream_t s) {
   BatchDesc d = d0;
   static int smem_limit = 0;
@@ -234,21 +309,21 @@ int launch_batched(const BatchDesc& d0, bool use_smem, cudaStream_t s) {
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, current_device());
     smem_limit = v > 0 ? v : 48 * 1024;
   }
-  const int static_bytes = (int)sizeof(BSmem<NT>) + 1024;
-  int rows = use_smem ? (smem_limit - static_bytes) / (5 * (int)sizeof(double)) : 0;
+  const int static_bytes = (int)(SPC * (sizeof(BRed<NT / SPC>) + sizeof(int))) + 1024;
+  int rows = use_smem ? (smem_limit - static_bytes) / (5 * SPC * (int)sizeof(double)) : 0;
   if (rows > d.n_max) rows = d.n_max;
   if (rows < 0) rows = 0;
   d.smem_rows = rows;
-  const size_t dyn = (size_t)rows * 5 * sizeof(double);
-  SLA_CUDA_TRY(cudaFuncSetAttribute(batched_pcg_kernel<NT>,
+  const size_t dyn = (size_t)rows * 5 * SPC * sizeof(double);
+  SLA_CUDA_TRY(cudaFuncSetAttribute(batched_pcg_kernel<NT, SPC, TPR>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_pcg_kernel<NT>, NT, dyn) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_pcg_kernel<NT, SPC, TPR>, NT, dyn) !=
           cudaSuccess || per_sm <= 0)
     per_sm = 1;
-  const int grid = persistent_grid(current_device(), d.batch, per_sm, kMaxBlocks);
+  const int grid = persistent_grid(current_device(), (d.batch + SPC - 1) / SPC, per_sm, kMaxBlocks);
   SLA_CUDA_TRY(cudaMemsetAsync(d.next, 0, sizeof(unsigned), s));
-  batched_pcg_kernel<NT><<<grid, NT, dyn, s>>>(d);
+  batched_pcg_kernel<NT, SPC, TPR><<<grid, NT, dyn, s>>>(d);
   SLA_CUDA_TRY(cudaGetLastError());
   return SLA_OK;
 }
@@ -256,23 +331,42 @@ int launch_batched(const BatchDesc& d0, bool use_smem, cudaStream_t s) {
 // config: low 4 bits = block size code (1: 256, 2: 512, 3: 1024; 0: auto),
 // bit 4 = keep the vectors in global memory even when they fit on chip,
 // bit 5 = no block teams for the large systems of a list, bit 6 = the block
-// teams solve their systems by the pipelined PCG (sla_cg_pipe.cuh).
+// teams solve their systems by the pipelined PCG (sla_cg_pipe.cuh),
+// bits 8-9 = log2 of the threads per row (1, 2, 4, 8), bits 10-11 = log2 of
+// the systems per CTA (1, 2, 4; with one thread per row).
 constexpr int kConfigNoTeams = 32;
 constexpr int kConfigPipelined = 64;
+constexpr int kConfigKnown = 15 | 16 | kConfigNoTeams | kConfigPipelined | (3 << 8) | (3 << 10);
 // Systems of a list with at least kTeamMinNnz entries are solved by teams of
 // blocks; the team launch is made when some system can have that many
 // (n_max >= kTeamMinRows).
 constexpr int kTeamMinNnz = 32768;
 constexpr int kTeamMinRows = 2048;
 
+template <int NT>
+int dispatch_shape(const BatchDesc& d, bool use_smem, int tpr_log2, int spc_log2, cudaStream_t s) {
+  if (spc_log2 != 0 && tpr_log2 != 0) return SLA_ERR_INVALID;  // systems per CTA with one thread per row
+  switch (spc_log2 == 0 ? tpr_log2 : 4 + spc_log2) {
+    case 0: return launch_batched<NT, 1, 1>(d, use_smem, s);
+    case 1: return launch_batched<NT, 1, 2>(d, use_smem, s);
+    case 2: return launch_batched<NT, 1, 4>(d, use_smem, s);
+    case 3: return launch_batched<NT, 1, 8>(d, use_smem, s);
+    case 5: return launch_batched<NT, 2, 1>(d, use_smem, s);
+    case 6: return launch_batched<NT, 4, 1>(d, use_smem, s);
+    default: return SLA_ERR_INVALID;
+  }
+}
+
 int dispatch(const BatchDesc& d, int config, cudaStream_t s) {
+  if (config & ~kConfigKnown) return SLA_ERR_INVALID;
   int code = config & 15;
   const bool use_smem = ((config >> 4) & 1) == 0;
+  const int tpr_log2 = (config >> 8) & 3, spc_log2 = (config >> 10) & 3;
   if (code == 0) code = d.n_max >= 2048 ? 2 : 1;
   switch (code) {
-    case 1: return launch_batched<256>(d, use_smem, s);
-    case 2: return launch_batched<512>(d, use_smem, s);
-    case 3: return launch_batched<1024>(d, use_smem, s);
+    case 1: return dispatch_shape<256>(d, use_smem, tpr_log2, spc_log2, s);
+    case 2: return dispatch_shape<512>(d, use_smem, tpr_log2, spc_log2, s);
+    case 3: return dispatch_shape<1024>(d, use_smem, tpr_log2, spc_log2, s);
     default: return SLA_ERR_INVALID;
   }
 }
@@ -382,6 +476,7 @@ extern "C" int32_t sla_cg_batched_list(int32_t batch, int32_t n_max, int32_t tot
                                        sla_info* info, int32_t config, void* ws, size_t ws_bytes,
                                        void* stream) {
   if (batch < 0 || n_max < 0 || total_rows < 0 || check_opts(opts) != SLA_OK) return SLA_ERR_INVALID;
+  if (config & ~kConfigKnown) return SLA_ERR_INVALID;
   if (batch == 0) return SLA_OK;
   if (n_off == nullptr || nnz_off == nullptr || rowptr == nullptr || col == nullptr ||
       val == nullptr || b == nullptr || x == nullptr || info == nullptr)

@@ -8,6 +8,8 @@ given by its values on a sparsity pattern (App. B)."""
 from __future__ import annotations
 
 import ctypes
+import json
+import os
 import threading
 from dataclasses import dataclass
 
@@ -631,10 +633,31 @@ class SparseTensor:
 # Batched solves in one persistent launch (shared pattern / distinct patterns)
 # ---------------------------------------------------------------------------
 
-# 256/512/1024 threads, vectors on chip / in global; for lists also without
-# block teams for the large systems (bit 32)
-BATCH_CONFIGS = (1, 2, 3, 1 | 16, 2 | 16, 3 | 16)
-LIST_CONFIGS = BATCH_CONFIGS + (1 | 32, 2 | 32, 3 | 32, 64)
+# The batched CG's launch shapes the autotuner searches (sla_cg_batched_*
+# config): 256/512/1024 threads per CTA (codes 1/2/3), vectors on chip or in
+# global memory (bit 4 = 16), threads per row 2/4/8 (bits 8-9 = log2), systems
+# per CTA 2/4 (bits 10-11 = log2); for lists also without the block teams for
+# the large systems (bit 5 = 32; the other shape bits act on the single-CTA
+# kernel, so they are searched with the teams off) and the teams on the
+# pipelined PCG (bit 6 = 64).
+TPR_SHIFT, SPC_SHIFT = 8, 10
+BATCH_CONFIGS = ((1, 2, 3, 1 | 16, 2 | 16, 3 | 16)
+                 + tuple(c | (t << TPR_SHIFT) for c in (1, 2, 3) for t in (1, 2, 3))
+                 + tuple(c | (k << SPC_SHIFT) for c in (1, 2, 3) for k in (1, 2)))
+LIST_CONFIGS = ((1, 2, 3, 1 | 16, 2 | 16, 64)
+                + (1 | 32, 2 | 32, 3 | 32)
+                + tuple(c | 32 | (t << TPR_SHIFT) for c in (2, 3) for t in (1, 2))
+                + tuple(c | 32 | (1 << SPC_SHIFT) for c in (2, 3)))
+
+
+def config_shape(config: int) -> dict:
+    """The launch shape a batched-CG config word selects."""
+    code = config & 15
+    return {"threads_per_cta": {0: "auto", 1: 256, 2: 512, 3: 1024}.get(code, "?"),
+            "vectors": "global" if config & 16 else "shared memory where they fit",
+            "threads_per_row": 1 << ((config >> TPR_SHIFT) & 3),
+            "systems_per_cta": 1 << ((config >> SPC_SHIFT) & 3),
+            "block_teams": not (config & 32), "pipelined_teams": bool(config & 64)}
 
 
 class CSRList:
@@ -687,6 +710,63 @@ class CSRList:
 
 
 _tune_cache: dict = {}
+_tune_loaded = False
+
+
+def _tune_file() -> str:
+    """Where tuned launch shapes persist: $SLA_TUNE_CACHE, else
+    ~/.cache/paper_2601_13994_b300/tune.json."""
+    return os.environ.get("SLA_TUNE_CACHE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "paper_2601_13994_b300", "tune.json")
+
+
+def _device_tag() -> str:
+    try:
+        return torch.cuda.get_device_name(torch.cuda.current_device()).replace(" ", "_")
+    except Exception:  # no device: the tag only names the cache entries
+        return "unknown"
+
+
+def _tune_key_str(key) -> str:
+    return "|".join([_device_tag()] + [str(k) for k in key])
+
+
+def _load_tune_file():
+    """Reads the persisted choices once per process (keys: device|kind|shape)."""
+    global _tune_loaded
+    if _tune_loaded:
+        return
+    _tune_loaded = True
+    try:
+        with open(_tune_file()) as f:
+            saved = json.load(f)
+    except (OSError, ValueError):
+        return
+    tag = _device_tag() + "|"
+    for k, v in saved.items():
+        if not k.startswith(tag) or not isinstance(v, int):
+            continue
+        parts = k[len(tag):].split("|")
+        key = tuple(int(p) if p.lstrip("-").isdigit() else p for p in parts)
+        _tune_cache.setdefault(key, v)
+
+
+def _save_tune_choice(key, cfg: int):
+    path = _tune_file()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        try:
+            with open(path) as f:
+                saved = json.load(f)
+        except (OSError, ValueError):
+            saved = {}
+        saved[_tune_key_str(key)] = int(cfg)
+        tmp = path + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(saved, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass  # a read-only home: the choice stays in this process
 
 
 def _batched_opts(rtol, atol, max_iter, max_restarts, precond, use_x0, n):
@@ -829,6 +909,7 @@ def _resolve_config(config, key, run, x, x0, candidates=BATCH_CONFIGS):
     events) and cache the fastest under the batch's shape key."""
     if isinstance(config, int):
         return config
+    _load_tune_file()
     if config == "auto":
         return _tune_cache.get(key, 0)
     if config != "tune":
@@ -849,6 +930,7 @@ def _resolve_config(config, key, run, x, x0, candidates=BATCH_CONFIGS):
         if min(times) < best_t:
             best, best_t = cfg, min(times)
     _tune_cache[key] = best
+    _save_tune_choice(key, best)
     return best
 
 

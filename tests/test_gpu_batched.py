@@ -87,6 +87,92 @@ def test_all_kernel_variants_agree():
     assert rel(tuned.cpu().numpy(), res[1][0].cpu().numpy()) <= 1e-9
 
 
+def test_launch_shapes_threads_per_row_and_systems_per_cta():
+    """Every launch shape the autotuner searches solves every system to the
+    oracle's tolerance.  Several systems per CTA run each system on a slice
+    of NT / SPC threads with its own named barrier and the same reduction
+    tree as a CTA of that size, so their bits equal that shape's (512
+    threads as two slices = 256 threads); more threads per row change the
+    summation order of each row only."""
+    B, N = 18, 24
+    rp, c, vals = I.batched_shared_2d(N, B, seed0=5, sigma=0.5)
+    b = I.rhs_uniform(N * N, 4, batch=B)
+    A = csr(rp, c)
+    v, bt = to_dev(vals), to_dev(b)
+    res = {}
+    for cfg in sla.BATCH_CONFIGS:
+        x, info = sla.cg_batched(A, v, bt, rtol=1e-10, config=cfg)
+        torch.cuda.synchronize()
+        res[cfg] = (x.cpu().numpy(), np.atleast_1d(info.iters).copy(), np.atleast_1d(info.status).copy())
+        assert (res[cfg][2] == 0).all(), (cfg, sla.config_shape(cfg))
+    S = sla.SPC_SHIFT
+    for cfg, same in (((2 | 1 << S), 1), ((3 | 1 << S), 2), ((3 | 2 << S), 1)):
+        assert np.array_equal(res[cfg][0], res[same][0]) and np.array_equal(res[cfg][1], res[same][1]), cfg
+    for cfg in sla.BATCH_CONFIGS:
+        assert rel(res[cfg][0], res[1][0]) <= 1e-9, cfg
+    x8, i8 = sla.cg_batched(A, v, bt, rtol=1e-10, config=1 | 3 << sla.TPR_SHIFT)   # 8 threads per row
+    torch.cuda.synchronize()
+    _per_system_check([rp] * B, [c] * B, vals, b, x8.cpu().numpy(), i8, 1e-10)
+    with pytest.raises(sla.L.SlaError):   # systems per CTA with more than one thread per row
+        sla.cg_batched(A, v, bt, rtol=1e-10, config=2 | 1 << S | 1 << sla.TPR_SHIFT)
+    with pytest.raises(sla.L.SlaError):   # unknown bit
+        sla.cg_batched(A, v, bt, rtol=1e-10, config=2 | 1 << 12)
+
+
+@pytest.mark.parametrize("cfg", [2 | 1 << 10, 1 | 2 << 10, 3 | 2 << 8])
+def test_mixed_statuses_with_launch_shapes(cfg):
+    """A slice whose system ends at once (b = 0, a bad diagonal) takes the
+    next system while its sibling slice is still iterating."""
+    B, N = 9, 20
+    rp, c, vals = I.batched_shared_2d(N, B, seed0=7, sigma=0.5)
+    b = I.rhs_uniform(N * N, 1, batch=B)
+    b[1] = 0.0
+    diag = np.nonzero(c == np.repeat(np.arange(N * N), np.diff(rp)))[0]
+    vals[3, diag[10]] = -1.0
+    x, info = sla.cg_batched(csr(rp, c), to_dev(vals), to_dev(b), rtol=1e-10, config=cfg)
+    torch.cuda.synchronize()
+    st = np.atleast_1d(info.status)
+    assert st[1] == 0 and np.atleast_1d(info.iters)[1] == 0 and not x[1].any()
+    assert sla.L.STATUS_NAMES[int(st[3])] == "NOT_SPD"
+    for s in (0, 2, 4, 5, 6, 7, 8):
+        xo, _ = oracle.pcg(rp, c, vals[s], b[s], rtol=1e-13)
+        assert st[s] == 0 and rel(x[s].cpu().numpy(), xo) <= 1e-8, s
+
+
+def test_list_launch_shapes_match_oracle():
+    mats = I.fem_list(20, seed0=2200, n_lo=100, n_hi=3000)
+    P = sla.CSRList([(rp, c) for rp, c, _ in mats])
+    vals = np.concatenate([v for _, _, v in mats])
+    bs = [I.rhs_uniform(len(rp) - 1, 90 + s) for s, (rp, _, _) in enumerate(mats)]
+    bt = to_dev(np.concatenate(bs))
+    for cfg in sla.LIST_CONFIGS:
+        x, info = sla.cg_batched_list(P, to_dev(vals), bt, rtol=1e-10, config=cfg)
+        torch.cuda.synchronize()
+        xh = x.cpu().numpy()
+        xs = [xh[P.n_off_h[s]:P.n_off_h[s + 1]] for s in range(len(mats))]
+        _per_system_check([m[0] for m in mats], [m[1] for m in mats], [m[2] for m in mats], bs, xs, info,
+                          1e-10, iters_tol=3, idx=[0, 7, 19])
+
+
+def test_tuned_choice_persists(tmp_path, monkeypatch):
+    """config='tune' writes its choice to the cache file; a new process (the
+    in-memory cache cleared) reads it back for config='auto'."""
+    monkeypatch.setenv("SLA_TUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.setattr(sla, "_tune_cache", {})
+    monkeypatch.setattr(sla, "_tune_loaded", False)
+    B, N = 8, 16
+    rp, c, vals = I.batched_shared_2d(N, B, seed0=3, sigma=0.5)
+    A = csr(rp, c)
+    v, bt = to_dev(vals), to_dev(I.rhs_uniform(N * N, 2, batch=B))
+    sla.cg_batched(A, v, bt, rtol=1e-10, config="tune")
+    key = ("shared", N * N, int(rp[-1]), B)
+    chosen = sla.tuned_configs()[key]
+    assert chosen in sla.BATCH_CONFIGS and (tmp_path / "tune.json").exists()
+    monkeypatch.setattr(sla, "_tune_cache", {})
+    monkeypatch.setattr(sla, "_tune_loaded", False)
+    assert sla._resolve_config("auto", key, None, None, None) == chosen
+
+
 def test_distinct_patterns_match_oracle():
     mats = I.fem_list(30, seed0=2000, n_lo=100, n_hi=3000)
     mats.append(I.diffusion2d_random(80, 9))         # 6400 rows: vectors off chip
