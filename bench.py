@@ -471,12 +471,15 @@ def extra_rows(dev, args, peak):
     ms, (x, info) = _time(lambda: sla.cg_batched(A, vt, bt, rtol=1e-8))
     its = np.atleast_1d(info.iters)
     fl = float((2 * int(rp[-1]) + 14 * N * N) * its.sum())
+    tuned = sla.tuned_configs().get(("shared", N * N, int(rp[-1]), B))
     out["batched_shared_1024x64x64"] = {"s": ms / 1e3, "iters_mean": float(its.mean()),
                                         "iters_max": int(its.max()),
                                         "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
                                         "fp64_tflops": fl / (ms / 1e3) / 1e12,
                                         "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
-                                        "config": {str(k): v for k, v in sla.tuned_configs().items()}}
+                                        "tuned_config": tuned,
+                                        "tuned_shape": sla.config_shape(tuned) if tuned is not None else None,
+                                        "candidates": len(sla.BATCH_CONFIGS)}
     del A, vt, bt, x
     # batched, distinct patterns: 512 P1 FEM systems, n log-uniform in [1e3, 5e4]
     mats = I.fem_list(512, seed0=2000)
@@ -493,19 +496,69 @@ def extra_rows(dev, args, peak):
     # the team launch with the standard and with the pipelined PCG (config bit 64)
     ms_std, _ = _time(lambda: sla.cg_batched_list(P, vt, bt, rtol=1e-8, config=0))
     ms_pipe, _ = _time(lambda: sla.cg_batched_list(P, vt, bt, rtol=1e-8, config=64))
+    tuned = sla.tuned_configs().get(("list", P.n_max, P.total_rows, P.total_nnz, P.batch))
     out["batched_list_512_fem"] = {"s": ms / 1e3, "total_rows": P.total_rows, "iters_mean": float(its.mean()),
-                                   "tuned_config": sla.tuned_configs().get(
-                                       ("list", P.n_max, P.total_rows, P.total_nnz, P.batch)),
+                                   "tuned_config": tuned,
+                                   "tuned_shape": sla.config_shape(tuned) if tuned is not None else None,
+                                   "candidates": len(sla.LIST_CONFIGS),
                                    "teams_standard_s": ms_std / 1e3, "teams_pipelined_s": ms_pipe / 1e3,
                                    "iters_max": int(its.max()),
                                    "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
                                    "fp64_tflops": fl / (ms / 1e3) / 1e12,
                                    "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+    del P, vt, bt, x
+    out.update(batched_bicgstab_rows(dev))
     out["pipelined_vs_standard"] = pipelined_rows(dev)
     out["nonlinear_newton_512"] = nonlinear_row(dev)
     out["eigsh_2d_128_k6"] = eigen_row(dev)
     out["learned_vs_jacobi"] = learned_vs_jacobi(dev)
     out["inverse_512_16rhs"] = inverse_rows(dev, peak)
+    return out
+
+
+def batched_bicgstab_rows(dev):
+    """Nonsymmetric batches by BiCGStab in one persistent launch (rtol 1e-8,
+    tuned block size / vector placement): 1024 2D upwind convection-diffusion
+    systems on one 64 x 64 five-point pattern (faces exp(N(0, 0.5^2)), cell
+    Peclet up to 10 in a random direction, seeds 1000 + s), and 512 such
+    systems on rectangles with n log-uniform in [1e3, 5e4] (seeds 5000 + s).
+    FP64 operations per iteration and row: 2 SpMVs (2 nnz/n) + 15."""
+    import torch
+
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import sla
+    out = {}
+    B, N = 1024, 64
+    rp, c, vals = I.batched_convdiff_2d(N, B, seed0=1000)
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    vt = torch.from_numpy(vals).to(dev)
+    bt = torch.from_numpy(I.rhs_uniform(N * N, 7, batch=B)).to(dev)
+    sla.bicgstab_batched(A, vt, bt, rtol=1e-8, config="tune")
+    ms, (x, info) = _time(lambda: sla.bicgstab_batched(A, vt, bt, rtol=1e-8))
+    its = np.atleast_1d(info.iters)
+    fl = float((2 * 2 * int(rp[-1]) + 2 * 15 * N * N) * its.sum())
+    out["bicgstab_batched_shared_1024x64x64"] = {
+        "s": ms / 1e3, "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+        "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
+        "fp64_tflops": fl / (ms / 1e3) / 1e12, "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+        "tuned_config": sla.tuned_configs().get(("bicg_shared", N * N, int(rp[-1]), B))}
+    del A, vt, bt, x
+    mats = I.convdiff_list(512, seed0=5000)
+    P = sla.CSRList([(m[0], m[1]) for m in mats], device=dev)
+    vt = torch.from_numpy(np.concatenate([m[2] for m in mats])).to(dev)
+    bt = torch.from_numpy(np.concatenate([I.rhs_uniform(len(m[0]) - 1, 6000 + s)
+                                          for s, m in enumerate(mats)])).to(dev)
+    sla.bicgstab_batched_list(P, vt, bt, rtol=1e-8, config="tune")
+    ms, (x, info) = _time(lambda: sla.bicgstab_batched_list(P, vt, bt, rtol=1e-8))
+    its = np.atleast_1d(info.iters)
+    fl = 0.0
+    for s, m in enumerate(mats):
+        fl += (2 * 2 * int(m[0][-1]) + 2 * 15 * (len(m[0]) - 1)) * int(its[s])
+    out["bicgstab_batched_list_512_convdiff"] = {
+        "s": ms / 1e3, "total_rows": P.total_rows, "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+        "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
+        "fp64_tflops": fl / (ms / 1e3) / 1e12, "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+        "tuned_config": sla.tuned_configs().get(("bicg_list", P.n_max, P.total_rows, P.total_nnz, P.batch))}
     return out
 
 
@@ -654,6 +707,7 @@ def learned_vs_jacobi(dev, systems=48, steps=800, lr=3e-3, n_lo=64, n_hi=128, ev
     from paper_2601_13994_b300 import learned as LP
     from paper_2601_13994_b300 import sla
     model = LP.LearnedPreconditioner(device=dev, seed=0)
+    zero = LP.LearnedPreconditioner(device=dev, seed=0)  # untrained: zero head
     t0 = time.perf_counter()
     hist = LP.train(model, systems=systems, steps=steps, lr=lr, n_lo=n_lo, n_hi=n_hi, log_every=max(1, steps // 8))
     torch.cuda.synchronize()
@@ -670,11 +724,24 @@ def learned_vs_jacobi(dev, systems=48, steps=800, lr=3e-3, n_lo=64, n_hi=128, ev
         ms_j, (xj, ij) = _time(lambda: sla.cg(A, vt, bt, rtol=1e-8))
         ms_f, fac = _time(lambda: model.factor(A, vt))
         ms_g, (xg, ig) = _time(lambda: sla.cg_ggt(A, vt, fac[0], fac[1], bt, rtol=1e-8))
+        # the same G-PCG with the factor of an untrained network (zero head:
+        # G = D^{-1/2}, normalisation keeps it, i.e. Jacobi through the G
+        # kernels) and with the classical FSAI factor on the same pattern
+        ms_z, zfac = _time(lambda: zero.factor(A, vt))
+        ms_gz, (_, iz) = _time(lambda: sla.cg_ggt(A, vt, zfac[0], zfac[1], bt, rtol=1e-8))
+        ms_ff, ffac = _time(lambda: LP.fsai_factor(A, vt))
+        ms_gf, (_, iff) = _time(lambda: sla.cg_ggt(A, vt, ffac[0], ffac[1], bt, rtol=1e-8))
         out[name] = {"jacobi_s": ms_j / 1e3, "jacobi_iters": ij.iters, "learned_s": ms_g / 1e3,
                      "learned_iters": ig.iters, "learned_status": ig.status,
                      "learned_true_rel_res": ig.true_rel_res, "factor_s": ms_f / 1e3,
                      "iters_ratio": ij.iters / max(1, ig.iters), "speedup_solve": ms_j / ms_g,
-                     "speedup_with_factor": ms_j / (ms_g + ms_f)}
+                     "speedup_with_factor": ms_j / (ms_g + ms_f),
+                     "zero_head": {"s": ms_gz / 1e3, "iters": iz.iters, "status": iz.status,
+                                   "factor_s": ms_z / 1e3},
+                     "fsai": {"s": ms_gf / 1e3, "iters": iff.iters, "status": iff.status,
+                              "factor_s": ms_ff / 1e3, "jacobi_fallback_columns": ffac[2],
+                              "speedup_with_factor": ms_j / (ms_gf + ms_ff)},
+                     "learned_vs_fsai_with_factor": (ms_gf + ms_ff) / (ms_g + ms_f)}
     return out
 
 

@@ -362,6 +362,22 @@ int32_t sla_ggt_loss_grad(const sla_csr* A, const double* val, const sla_csr* G,
                           double* dG, void* ws, size_t ws_bytes, void* stream);
 size_t sla_ggt_loss_ws(int32_t n);
 
+/* The factored sparse approximate inverse (FSAI; Kolotilina and Yeremin)
+ * on the pattern G of tril(A) (sla_tril_pattern): the classical,
+ * non-learned factor of M^{-1} = G G^T, against which the learned factor is
+ * measured (Sec. 5 names learned preconditioners as future work).  Column j
+ * of G solves A[P, P] y = e_1 on its rows P = {i >= j : A_ij != 0} and is
+ * y / sqrt(y_1), so diag(G^T A G) = I.  A: SPD, columns ascending within
+ * each row.  GT: sla_csr_transpose of G.  One thread per column; the block
+ * A[P, P] is factored by Cholesky in local memory.  A column with more than
+ * 12 entries, or whose block does not factor, gets the Jacobi column
+ * 1/sqrt(A_jj) and is counted in *fallbacks (device int, optional, zeroed
+ * by the call).  g_out (device, nnz_g) in G's CSR order; must not overlap
+ * val.  Asynchronous. */
+int32_t sla_fsai_factor(const sla_csr* A, const double* val, const sla_csr* G,
+                        const sla_csr_t* GT, double* g_out, int32_t* fallbacks,
+                        void* stream);
+
 /* Column normalisation of the factor (applied when the learned factor is
  * formed for a solve): every entry G_ij of column j is divided by
  * sqrt((G^T A G)_jj), (G^T A G)_jj = sum over the entries G_ij, G_kj of

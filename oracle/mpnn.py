@@ -151,6 +151,26 @@ def column_normalize(grp, gcol, g_val, rp, c, v):
     return out
 
 
+def fsai_factor(rp, c, v):
+    """The factored sparse approximate inverse on the pattern of tril(A)
+    (Kolotilina and Yeremin), the classical non-learned G of M^{-1} = G G^T
+    that the learned factor is compared with: column i of G solves
+    A[P, P] y = e_1 on P = {j >= i : A_ji != 0} (ascending, i first) and is
+    y / sqrt(y_1), so that (G^T A G)_ii = 1.  Dense numpy per column.
+    Returns G as a dense [n, n] array."""
+    n = len(rp) - 1
+    A = np.zeros((n, n))
+    for i in range(n):
+        for k in range(rp[i], rp[i + 1]):
+            A[i, c[k]] += v[k]
+    G = np.zeros((n, n))
+    for i in range(n):
+        P = [j for j in range(i, n) if A[j, i] != 0.0]
+        y = np.linalg.solve(A[np.ix_(P, P)], np.eye(len(P))[0])
+        G[P, i] = y / np.sqrt(y[0])
+    return G
+
+
 def ggt_apply(grp, gcol, g_val, u):
     """y = G (G^T u) with G given on a CSR pattern (differentiable in g_val, u)."""
     n = len(grp) - 1

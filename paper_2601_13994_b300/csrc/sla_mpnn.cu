@@ -1109,8 +1109,92 @@ __global__ void __launch_bounds__(256) ggt_normalize_kernel(int n, const int* __
     }
   }
 }
+// The factored sparse approximate inverse (Kolotilina and Yeremin) on the
+// pattern of G = tril(A): one thread per column j (row j of the CSR of G^T,
+// whose entries list the rows P = {i >= j : A_ij != 0} in ascending order,
+// j first).  The |P| x |P| block A[P, P] is gathered by binary search in A's
+// rows, factored by Cholesky (a principal block of an SPD matrix) and
+// solved for y with A[P, P] y = e_1; the column is y / sqrt(y_1), so that
+// (G^T A G)_jj = 1.  Columns with more than kFsaiMaxP entries, or a block
+// whose factorisation fails, get the Jacobi column 1/sqrt(A_jj) and are
+// counted in *fallbacks.
+constexpr int kFsaiMaxP = 12;
+
+__global__ void __launch_bounds__(128) fsai_kernel(int n, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ col, const double* __restrict__ val,
+                                                   const int* __restrict__ rpt, const int* __restrict__ rowt,
+                                                   const int* __restrict__ perm, double* g_out,
+                                                   int* fallbacks) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const int a = __ldg(rpt + j), e = __ldg(rpt + j + 1);
+    const int m = e - a;
+    double L[kFsaiMaxP * (kFsaiMaxP + 1) / 2];  // packed lower triangle, row-major
+    double y[kFsaiMaxP];
+    bool ok = m >= 1 && m <= kFsaiMaxP && __ldg(rowt + a) == j;
+    if (ok) {
+      // L = chol(A[P, P]), row by row
+      for (int r = 0; r < m && ok; ++r) {
+        const int pr = __ldg(rowt + a + r);
+        for (int q = 0; q <= r; ++q) {
+          double sum = a_entry(rowptr, col, val, pr, __ldg(rowt + a + q));
+          for (int t = 0; t < q; ++t) sum -= L[r * (r + 1) / 2 + t] * L[q * (q + 1) / 2 + t];
+          if (q < r) {
+            L[r * (r + 1) / 2 + q] = sum / L[q * (q + 1) / 2 + q];
+          } else {
+            if (!(sum > 0.0) || !isfinite(sum)) {
+              ok = false;
+              break;
+            }
+            L[r * (r + 1) / 2 + r] = sqrt(sum);
+          }
+        }
+      }
+    }
+    if (ok) {
+      // L L^T y = e_1: forward (z = L^{-1} e_1), then backward
+      for (int r = 0; r < m; ++r) {
+        double sum = r == 0 ? 1.0 : 0.0;
+        for (int t = 0; t < r; ++t) sum -= L[r * (r + 1) / 2 + t] * y[t];
+        y[r] = sum / L[r * (r + 1) / 2 + r];
+      }
+      for (int r = m - 1; r >= 0; --r) {
+        double sum = y[r];
+        for (int t = r + 1; t < m; ++t) sum -= L[t * (t + 1) / 2 + r] * y[t];
+        y[r] = sum / L[r * (r + 1) / 2 + r];
+      }
+      ok = y[0] > 0.0 && isfinite(y[0]);
+    }
+    if (ok) {
+      const double inv = 1.0 / sqrt(y[0]);
+      for (int r = 0; r < m; ++r) g_out[__ldg(perm + a + r)] = y[r] * inv;
+    } else {
+      const double d = a_entry(rowptr, col, val, j, j);
+      for (int r = 0; r < m; ++r)
+        g_out[__ldg(perm + a + r)] = (__ldg(rowt + a + r) == j && d > 0.0) ? 1.0 / sqrt(d) : 0.0;
+      if (fallbacks) atomicAdd(fallbacks, 1);
+    }
+  }
+}
 }  // namespace
 }  // namespace sla
+
+extern "C" int32_t sla_fsai_factor(const sla_csr* A, const double* val, const sla_csr* G, const sla_csr_t* GT,
+                                   double* g_out, int32_t* fallbacks, void* stream) {
+  if (A == nullptr || G == nullptr || GT == nullptr || A->n != G->n || A->n < 0 || G->nnz < 0)
+    return SLA_ERR_INVALID;
+  if (A->n == 0 || G->nnz == 0) return SLA_OK;
+  if (A->rowptr == nullptr || A->col == nullptr || val == nullptr || GT->rowptr_t == nullptr ||
+      GT->col_t == nullptr || GT->perm_t == nullptr || g_out == nullptr)
+    return SLA_ERR_INVALID;
+  if (ranges_overlap(val, 8 * (size_t)A->nnz, g_out, 8 * (size_t)G->nnz)) return SLA_ERR_INVALID;
+  const int n = A->n;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (fallbacks) SLA_CUDA_TRY(cudaMemsetAsync(fallbacks, 0, sizeof(int32_t), s));
+  fsai_kernel<<<grid_rows(n, 128), 128, 0, s>>>(n, A->rowptr, A->col, val, GT->rowptr_t, GT->col_t, GT->perm_t,
+                                                g_out, fallbacks);
+  MP_LAUNCH_CHECK();
+  return SLA_OK;
+}
 
 extern "C" int32_t sla_ggt_normalize(const sla_csr* A, const double* val, const sla_csr* G, const sla_csr_t* GT,
                                      const double* g_val, double* g_out, void* stream) {

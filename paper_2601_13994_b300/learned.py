@@ -77,6 +77,7 @@ def _bind():
         "sla_ggt_loss_grad": ([CSR, P, CSR, P, CSRT, P, P, P, P, P, sz, P], i32),
         "sla_ggt_loss_ws": ([i32], sz),
         "sla_ggt_normalize": ([CSR, P, CSR, CSRT, P, P, P], i32),
+        "sla_fsai_factor": ([CSR, P, CSR, CSRT, P, P, P], i32),
         "sla_adam_step": ([i32, P, P, P, P, f32, f32, f32, f32, i32, f32, P, P], i32),
         "sla_to_bf16": ([i32, P, P, P], i32),
     }
@@ -349,6 +350,40 @@ class LearnedPreconditioner:
             x2, info2 = sla.cg(A, val, b, rtol=rtol, x0=x)
             return x2, info2, True
         return x, info, False
+
+
+def tril_pattern(A: sla.CSRMatrix) -> sla.CSRMatrix:
+    """The pattern of tril(A) as a CSRMatrix with its CSR of G^T (cached on A)."""
+    G = getattr(A, "_tril_pattern", None)
+    if G is None:
+        lib = _bind()
+        dev, n = A.device, A.n
+        grp = torch.empty(n + 1, dtype=torch.int32, device=dev)
+        gcol = torch.empty(max(A.nnz, 1), dtype=torch.int32, device=dev)
+        gsrc = torch.empty(max(A.nnz, 1), dtype=torch.int32, device=dev)
+        nnz_g = torch.empty(1, dtype=torch.int32, device=dev)
+        ws = torch.empty(max(int(lib.sla_tril_pattern_ws(n)), 256), dtype=torch.uint8, device=dev)
+        _chk("sla_tril_pattern", lib.sla_tril_pattern(ctypes.byref(A.c), grp.data_ptr(), gcol.data_ptr(),
+                                                     gsrc.data_ptr(), nnz_g.data_ptr(), ws.data_ptr(),
+                                                     ws.numel(), sla._stream_ptr(dev)))
+        m = int(nnz_g.item())
+        G = sla.CSRMatrix(grp, gcol[:m].clone(), check=False)
+        sla.transpose_of(G)
+        A._tril_pattern = G
+    return G
+
+
+def fsai_factor(A: sla.CSRMatrix, val: torch.Tensor):
+    """The factored sparse approximate inverse on tril(A) (sla_fsai_factor):
+    the classical factor of M^{-1} = G G^T the learned one is compared with.
+    Returns (G pattern, G values FP64, columns that fell back to Jacobi)."""
+    G = tril_pattern(A)
+    gv = torch.empty(max(G.nnz, 1), dtype=torch.float64, device=A.device)
+    fb = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _chk("sla_fsai_factor", _bind().sla_fsai_factor(ctypes.byref(A.c), val.data_ptr(), ctypes.byref(G.c),
+                                                    ctypes.byref(G._transpose_c), gv.data_ptr(), fb.data_ptr(),
+                                                    sla._stream_ptr(A.device)))
+    return G, gv[:G.nnz], int(fb.item())
 
 
 def training_system(k: int, n_lo: int = 64, n_hi: int = 128, seed0: int = 100000):

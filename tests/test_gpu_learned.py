@@ -101,6 +101,47 @@ def test_forward_and_gradients_match_oracle(mat):
         assert rel(gk, go) <= 2e-3, (k, rel(gk, go))
 
 
+@pytest.mark.parametrize("mat", ["var2d", "var3d", "fem", "dense"])
+def test_fsai_factor_matches_oracle(mat):
+    """sla_fsai_factor (the classical factor the learned one is measured
+    against) equals the oracle's column-by-column definition; with every
+    entry stored (dense A) it is the exact factor, G G^T = A^{-1}, and PCG
+    with it converges in one iteration."""
+    if mat == "var2d":
+        rp, c, v = I.diffusion2d_random(11, 5, 1.5)
+    elif mat == "var3d":
+        rp, c, v = I.diffusion3d_random(6, 7)
+    elif mat == "fem":
+        rp, c, v = I.fem_p1_laplacian(9, 4)
+    else:
+        rng = np.random.default_rng(2)
+        n = 10
+        X = rng.standard_normal((n, n))
+        M = X @ X.T + n * np.eye(n)
+        rp = np.arange(0, n * n + 1, n, dtype=np.int32)
+        c = np.tile(np.arange(n, dtype=np.int32), n)
+        v = M.reshape(-1).copy()
+    n = len(rp) - 1
+    A = csr(rp, c)
+    G, gv, fb = LP.fsai_factor(A, to_dev(v))
+    assert fb == 0
+    Go = OM.fsai_factor(rp, c, v)
+    grp, gcol, g = G.rowptr.cpu().numpy(), G.col.cpu().numpy(), gv.cpu().numpy()
+    rows = np.repeat(np.arange(n), np.diff(grp))
+    assert np.allclose(g, Go[rows, gcol], rtol=1e-12, atol=1e-14)
+    assert np.count_nonzero(Go) == len(g)
+    # the solve applies G's values stored in FP32 (G32 G32^T), as does the oracle here
+    b = I.rhs_uniform(n, 3)
+    x, info = sla.cg_ggt(A, to_dev(v), G, gv, to_dev(b), rtol=1e-12)
+    g32 = g.astype(np.float32).astype(np.float64)
+    xo, io = oracle.pcg(rp, c, v, b, rtol=1e-12, precond="ggt", G=(grp, gcol, g32))
+    assert info.status == 0 and io["status"] == 0
+    assert rel(x.cpu().numpy(), xo) <= 1e-8 and abs(info.iters - io["iters"]) <= 2
+    if mat == "dense":
+        # G G^T = A^{-1} up to the FP32 storage of G: a handful of iterations
+        assert info.iters <= 4
+
+
 def test_loss_gradient_wrt_g_matches_oracle():
     import torch as T
     rp, c, v = I.diffusion2d_random(12, 6)

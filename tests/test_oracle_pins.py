@@ -661,17 +661,28 @@ def test_mpnn_permutation_equivariance():
 
 
 def _fsai_factor(rp, c, v):
-    """Factored sparse approximate inverse on the pattern of tril(A), built
-    column by column from its published definition: column i solves
-    A[P, P] y = e_1 on P = {j >= i : A_ji != 0} and is divided by sqrt(y_1)."""
-    n = len(rp) - 1
-    A = dense(rp, c, v)
-    G = np.zeros((n, n))
-    for i in range(n):
-        P = [j for j in range(i, n) if A[j, i] != 0.0]
-        y = np.linalg.solve(A[np.ix_(P, P)], np.eye(len(P))[0])
-        G[P, i] = y / np.sqrt(y[0])
-    return G
+    from oracle import mpnn
+    return mpnn.fsai_factor(rp, c, v)
+
+
+def test_fsai_factor_is_exact_on_a_full_pattern():
+    """With every entry of A stored, the pattern of tril(A) is the full
+    lower triangle, and the FSAI factor is exact: G G^T = A^{-1}; on a
+    sparse pattern it has unit columns in the A-norm, diag(G^T A G) = I."""
+    rng = np.random.default_rng(3)
+    n = 9
+    X = rng.standard_normal((n, n))
+    A = X @ X.T + n * np.eye(n)
+    S = sp.csr_matrix(A)
+    S.sort_indices()
+    G = _fsai_factor(S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data)
+    assert np.allclose(np.tril(G), G, atol=0)
+    assert np.allclose(G @ G.T @ A, np.eye(n), rtol=0, atol=1e-12)
+    rp, c, v = I.diffusion2d_random(6, 4)
+    Gs = _fsai_factor(rp, c, v)
+    Ad = dense(rp, c, v)
+    assert np.allclose(np.diag(Gs.T @ Ad @ Gs), 1.0, rtol=0, atol=1e-13)
+    assert np.array_equal(Gs != 0, np.tril(Ad) != 0)
 
 
 def _csr_of(G):
