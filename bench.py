@@ -680,6 +680,10 @@ def inverse_rows(dev, peak, N=512, k=16):
     n, nnz = P.n, P.A.nnz
     bpi = 12 * nnz + 4 * (n + 1) + 104 * n * k
     gbs = bpi * int(its.max()) / (ms_m / 1e3) / 1e9
+    # FP64 flops: every column's SpMV (2 nnz) and vector work (14 n) for the
+    # iterations that column ran
+    fl = float(sum((2 * nnz + 14 * n) * int(i) for i in its))
+    fp64_tf = fl / (ms_m / 1e3) / 1e12
     th0 = torch.zeros((N, N), dtype=torch.float64, device=dev)
 
     def step():
@@ -692,6 +696,7 @@ def inverse_rows(dev, peak, N=512, k=16):
     return {"n": n, "k": k, "multi_s": ms_m / 1e3, "iters_max": int(its.max()), "iters_mean": float(its.mean()),
             "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
             "us_per_iter": ms_m * 1e3 / int(its.max()), "gbs_model": gbs, "frac_of_measured_hbm": gbs / peak,
+            "fp64_tflops": fp64_tf, "fp64_frac": fp64_tf / FP64_PEAK_TFLOPS,
             "bytes_per_iter": bpi, "singles_s": ms_s / 1e3,
             "singles_iters": [int(o[1].iters) for o in outs], "speedup_vs_singles": ms_s / ms_m,
             "step_s": ms_step / 1e3, "loss_theta0": float(L)}
