@@ -760,6 +760,76 @@ int32_t sla_grad_values_batched(int32_t batch, int32_t shared_pattern,
                                 void* stream);
 
 /* ------------------------------------------------------------------ */
+/* Distributed layer (Sec. 3.3, Eqs. 5-6; Algorithm 1 of App. C), with    */
+/* its P row-block partitions emulated on one GPU                         */
+/* ------------------------------------------------------------------ */
+
+/* Layout (built on the host by the Python layer, device arrays here):
+ * partition p owns rows [row_off[p], row_off[p+1]); its extended local
+ * vector holds its |O_p| owned entries, then its halo H_p (the sorted
+ * global columns outside O_p that its rows reference); all partitions'
+ * extended vectors lie back to back (total_ext entries), src[e] = the global
+ * index extended entry e holds.  The local matrices of all partitions form
+ * one CSR with n rows and columns in the extended space (col_ext). */
+
+/* The halo exchange H (Eq. 5): x_ext[e] = x[src[e]] -- every partition's
+ * owned entries and the values its halo receives from their owners.  x
+ * [n], x_ext [total_ext], distinct.  Asynchronous. */
+int32_t sla_dist_halo_gather(int64_t total_ext, const int32_t* src,
+                             const double* x, double* x_ext, void* stream);
+
+/* The transposed halo exchange H^T (Eq. 6): g_x[i] = g_ext[own_pos[i]] +
+ * sum over t in [hptr[i], hptr[i+1]) of g_ext[hlist[t]], i.e. each owner
+ * sums the halo gradients its entry received from every partition that
+ * holds it (hlist ordered by partition, then halo position: a fixed
+ * order).  own_pos [n], hptr [n+1], hlist [hptr[n]] device int32; g_ext
+ * [total_ext] and g_x [n] distinct.  Asynchronous. */
+int32_t sla_dist_halo_scatter(int32_t n, const int32_t* own_pos,
+                              const int32_t* hptr, const int32_t* hlist,
+                              const double* g_ext, double* g_x, void* stream);
+
+/* All-reduced inner products (Algorithm 1's all_reduce): for j < k (1..3),
+ * each partition's local sum of a[j] . b[j] over its rows (a fixed-shape
+ * reduction of 8 block partials), then the sum over partitions in order
+ * 0..P-1 into out[j] (device [k]); rank_part (device [k][P], optional)
+ * receives the per-partition sums.  a, b: HOST arrays of k device pointers
+ * to [n] vectors; row_off device [P+1]; partial: device scratch of 8 P k
+ * doubles.  Asynchronous. */
+int32_t sla_dist_dots(int32_t P, const int32_t* row_off, int32_t k,
+                      const double* const* a, const double* const* b,
+                      double* partial, double* out, double* rank_part,
+                      void* stream);
+
+/* D^{-1} of the distributed matrix: A_ii is the entry of row i whose
+ * extended column is own_pos[i]; *bad (device int, zeroed by the call) = 1
+ * if some A_ii <= 0.  Asynchronous. */
+int32_t sla_dist_diag_inv(int32_t n, const int32_t* rowptr,
+                          const int32_t* col_ext, const double* val,
+                          const int32_t* own_pos, double* dinv, int32_t* bad,
+                          void* stream);
+
+/* Algorithm 1's local steps with the Jacobi preconditioner, all partitions
+ * at once (alpha, beta are the all-reduced scalars, passed by value):
+ * start: r = b - y (y = A x), z = D^{-1} r, p = z;
+ * update: x += alpha p, r -= alpha q, z = D^{-1} r;
+ * direction: p = z + beta p.  Device [n] vectors; asynchronous. */
+int32_t sla_dist_cg_start(int32_t n, const double* b, const double* y,
+                          const double* dinv, double* r, double* z, double* p,
+                          void* stream);
+int32_t sla_dist_cg_update(int32_t n, double alpha, const double* p,
+                           const double* q, const double* dinv, double* x,
+                           double* r, double* z, void* stream);
+int32_t sla_dist_cg_direction(int32_t n, double beta, const double* z,
+                              double* p, void* stream);
+
+/* Value gradient of y = A_local x_ext on every partition's own entries (no
+ * communication): out[k] = gy[i] * x_ext[col_ext[k]] for the entries k of
+ * row i.  Asynchronous. */
+int32_t sla_dist_outer_values(int32_t n, const int32_t* rowptr,
+                              const int32_t* col_ext, const double* gy,
+                              const double* x_ext, double* out, void* stream);
+
+/* ------------------------------------------------------------------ */
 /* Allocation-free CG (no counterpart in the paper)                      */
 /* ------------------------------------------------------------------ */
 

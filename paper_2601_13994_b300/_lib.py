@@ -162,6 +162,19 @@ def lib() -> ctypes.CDLL:
             L.sla_csr_list_transpose.restype = i32
             L.sla_gather_values_batched.argtypes = [i32, i64, P, P, P, P]
             L.sla_gather_values_batched.restype = i32
+            PP = ctypes.POINTER(ctypes.c_void_p)
+            d = ctypes.c_double
+            for name, args in (("sla_dist_halo_gather", [i64, P, P, P, P]),
+                               ("sla_dist_halo_scatter", [i32, P, P, P, P, P, P]),
+                               ("sla_dist_dots", [i32, P, i32, PP, PP, P, P, P, P]),
+                               ("sla_dist_diag_inv", [i32, P, P, P, P, P, P, P]),
+                               ("sla_dist_cg_start", [i32, P, P, P, P, P, P, P]),
+                               ("sla_dist_cg_update", [i32, d, P, P, P, P, P, P, P]),
+                               ("sla_dist_cg_direction", [i32, d, P, P, P]),
+                               ("sla_dist_outer_values", [i32, P, P, P, P, P, P])):
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = i32
             L.sla_cg_ggt.argtypes = [ctypes.POINTER(SlaCsr), P, ctypes.POINTER(SlaCsr), P, ctypes.POINTER(SlaCsrT),
                                      P, P, ctypes.POINTER(SlaOpts), P, P, ctypes.c_size_t, P]
             L.sla_cg_ggt.restype = i32
