@@ -508,6 +508,7 @@ def extra_rows(dev, args, peak):
                                    "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
     del P, vt, bt, x
     out.update(batched_bicgstab_rows(dev))
+    out["distributed_emulated_diffusion3d_64_p8"] = distributed_row(dev)
     out["pipelined_vs_standard"] = pipelined_rows(dev)
     out["nonlinear_newton_512"] = nonlinear_row(dev)
     out["eigsh_2d_128_k6"] = eigen_row(dev)
@@ -560,6 +561,31 @@ def batched_bicgstab_rows(dev):
         "fp64_tflops": fl / (ms / 1e3) / 1e12, "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
         "tuned_config": sla.tuned_configs().get(("bicg_list", P.n_max, P.total_rows, P.total_nnz, P.batch))}
     return out
+
+
+def distributed_row(dev, N=64, P=8):
+    """Sec. 3.3's distributed CG (Algorithm 1) with 8 row-block partitions
+    emulated on one GPU, on the 3D 64^3 variable-coefficient system at rtol
+    1e-8, against the single-system solve: iterations, time (the emulation
+    reads its two all-reduced scalars on the host every iteration, as the
+    algorithm's ranks receive them) and the halo sizes."""
+    import torch
+
+    from paper_2601_13994_b300 import distributed as D
+    from paper_2601_13994_b300 import inputs as I
+    from paper_2601_13994_b300 import sla
+    rp, c, v = I.diffusion3d_random(N, 1)
+    n = len(rp) - 1
+    vt = torch.from_numpy(v).to(dev)
+    bt = torch.from_numpy(I.rhs_uniform(n, 11)).to(dev)
+    DA = D.DistributedMatrix(rp, c, P, device=dev)
+    ms_d, (xd, inf) = _time(lambda: D.dist_cg(DA, vt, bt, rtol=1e-8))
+    A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+    ms_s, (xs, ins) = _time(lambda: sla.cg(A, vt, bt, rtol=1e-8))
+    return {"n": n, "partitions": P, "halo_sizes": inf["halo_sizes"], "halo_fraction": sum(inf["halo_sizes"]) / n,
+            "dist_s": ms_d / 1e3, "dist_iters": inf["iters"], "dist_status": inf["status"],
+            "dist_true_rel_res": inf["true_rel_res"], "single_s": ms_s / 1e3, "single_iters": ins.iters,
+            "max_abs_diff": float((xd - xs).abs().max())}
 
 
 def eigen_row(dev, N=128, k=6):

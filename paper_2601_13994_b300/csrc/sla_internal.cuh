@@ -248,6 +248,25 @@ __device__ __forceinline__ auto gather_at(F& f, int c) -> decltype(f(c)) {
   return f(c);
 }
 
+// acc = fma(v, x, acc) in the threads where `on` holds, as a predicated
+// instruction: threads without the predicate issue no FP64 operation.  (A
+// guarded fma in C++ -- `if (j < rem) acc = fma(...)` in an unrolled loop --
+// was measured to execute in every thread, 8.93 DFMA per row in the PCG
+// SpMV where 7.97 were needed: the compiler evaluates it unconditionally and
+// keeps the old value where the guard fails.)
+__device__ __forceinline__ double fma_if(bool on, double v, double x, double acc) {
+  asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\t@p fma.rn.f64 %0, %1, %2, %0;\n\t}"
+      : "+d"(acc)
+      : "d"(v), "d"(x), "r"((unsigned)on));
+  return acc;
+}
+__device__ __forceinline__ float fma_if(bool on, float v, float x, float acc) {
+  asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\t@p fma.rn.f32 %0, %1, %2, %0;\n\t}"
+      : "+f"(acc)
+      : "f"(v), "f"(x), "r"((unsigned)on));
+  return acc;
+}
+
 template <int B = kGatherBatch, class ColAt, class ValAt, class XAt>
 __device__ __forceinline__ auto row_sum_batched(int a, int e, ColAt&& col_at, ValAt&& val_at, XAt&& x)
     -> decltype(gather_at(x, 0)) {
@@ -272,20 +291,20 @@ __device__ __forceinline__ auto row_sum_batched(int a, int e, ColAt&& col_at, Va
     int c[B];
     T v[B], xv[B];
 #pragma unroll
-    for (int j = 0; j < B; ++j)
+    for (int j = 0; j < B; ++j) {
+      v[j] = T(0);
+      xv[j] = T(0);
       if (j < rem) {
         c[j] = col_at(k0 + j);
         v[j] = val_at(k0 + j);
       }
+    }
 #pragma unroll
     for (int j = 0; j < B; ++j)
       if (j < rem) xv[j] = gather_at(x, c[j]);
-    // explicit exit: the FP64 pipe must not see the padding lanes
+    // predicated: the FP64 pipe must not see the padding entries
 #pragma unroll
-    for (int j = 0; j < B; ++j) {
-      if (j >= rem) break;
-      acc = fma(v[j], xv[j], acc);
-    }
+    for (int j = 0; j < B; ++j) acc = fma_if(j < rem, v[j], xv[j], acc);
   }
   return acc;
 }

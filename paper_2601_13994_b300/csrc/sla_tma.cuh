@@ -142,9 +142,9 @@ __device__ __forceinline__ auto warp_row(const int* __restrict__ rowptr, const i
 
 // Sums of two adjacent rows whose entries are [a, m) and [m, e): the column
 // indices and values of up to kPairBatch entries of the pair are read first, their x
-// gathers issued back to back, then each row's FMAs run in entry order with
-// explicit exits (no padding FMA reaches the FP64 pipe); pairs with more
-// entries continue one entry at a time.
+// gathers issued back to back, then each row's FMAs run in entry order as
+// predicated instructions (no padding FMA reaches the FP64 pipe); pairs
+// with more entries continue one entry at a time.
 template <class X, class ColAt, class ValAt, class XAt>
 __device__ __forceinline__ void two_row_sum(int a, int m, int e, ColAt&& col_at, ValAt&& val_at, XAt&& x,
                                             X& acc0, X& acc1) {
@@ -155,27 +155,24 @@ __device__ __forceinline__ void two_row_sum(int a, int m, int e, ColAt&& col_at,
   int c[B];
   X v[B], xv[B];
 #pragma unroll
-  for (int j = 0; j < B; ++j)
+  for (int j = 0; j < B; ++j) {
+    v[j] = X(0);
+    xv[j] = X(0);
     if (j < cnt) {
       c[j] = col_at(a + j);
       v[j] = val_at(a + j);
     }
+  }
 #pragma unroll
   for (int j = 0; j < B; ++j)
     if (j < cnt) xv[j] = gather_at(x, c[j]);
   const int n0 = m - a;  // entries of the first row
+  // predicated (fma_if): no padding FMA reaches the FP64 pipe
 #pragma unroll
-  for (int jj = 0; jj < B; ++jj) {
-    if (jj >= n0 || jj >= cnt) break;
-    acc0 = fma(v[jj], xv[jj], acc0);
-  }
+  for (int jj = 0; jj < B; ++jj) acc0 = fma_if(jj < n0 && jj < cnt, v[jj], xv[jj], acc0);
   for (int k = a + B; k < m; ++k) acc0 = fma(val_at(k), gather_at(x, col_at(k)), acc0);
 #pragma unroll
-  for (int jj = 0; jj < B; ++jj) {
-    if (jj < n0) continue;
-    if (jj >= cnt) break;
-    acc1 = fma(v[jj], xv[jj], acc1);
-  }
+  for (int jj = 0; jj < B; ++jj) acc1 = fma_if(jj >= n0 && jj < cnt, v[jj], xv[jj], acc1);
   for (int k = max(m, a + B); k < e; ++k) acc1 = fma(val_at(k), gather_at(x, col_at(k)), acc1);
 }
 
