@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_spmm_kernel(EigPtrs P, int mo
 // residual of 1.4e-7 on the 1D Laplacian, n = 200, k = 6.)
 template <class T>
 __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps, T* rot, int* s_any,
-                           T* s_floor) {
+                           T* s_floor, unsigned short* items) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int q = tid; q < m * kEigLd; q += nt) V[q] = T(0);
   __syncthreads();
@@ -205,6 +205,20 @@ __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps
   const T floor_abs = *s_floor;
   const int mp = m + (m & 1);
   const int npair = mp / 2;
+  // work items of a step: (row pair, column pair) blocks, then (row of V,
+  // pair); x << 8 | y
+  for (int t = tid; t < npair * npair + m * npair; t += nt) {
+    int x, y;
+    if (t < npair * npair) {
+      x = t / npair;
+      y = t - x * npair;
+    } else {
+      x = (t - npair * npair) / npair;
+      y = (t - npair * npair) - x * npair;
+    }
+    items[t] = (unsigned short)((x << 8) | y);
+  }
+  __syncthreads();
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (tid == 0) *s_any = 0;
     __syncthreads();
@@ -251,34 +265,44 @@ __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps
         rot[4 * tid + 3] = s;
       }
       __syncthreads();
-      // rows p, q of A (A <- J^T A): a warp per pair, a lane per column
-      // (m <= 30 < 32; no integer division, which runs on the slow
-      // special-function pipe)
-      const int wp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-      for (int t = wp; t < npair; t += nw) {
-        const T s = rot[4 * t + 3];
-        if (s == T(0) || lane >= m) continue;
-        const int p = (int)rot[4 * t], q = (int)rot[4 * t + 1];
-        const T c = rot[4 * t + 2];
-        const int j = lane;
-        const T ap = A[p * kEigLd + j], aq = A[q * kEigLd + j];
-        A[p * kEigLd + j] = c * ap - s * aq;
-        A[q * kEigLd + j] = s * ap + c * aq;
-      }
-      __syncthreads();
-      // columns p, q of A and V (A <- A J, V <- V J)
-      for (int t = wp; t < npair; t += nw) {
-        const int i = lane;
-        const T s = rot[4 * t + 3];
-        if (s == T(0) || i >= m) continue;
-        const int p = (int)rot[4 * t], q = (int)rot[4 * t + 1];
-        const T c = rot[4 * t + 2];
-        const T ap = A[i * kEigLd + p], aq = A[i * kEigLd + q];
-        A[i * kEigLd + p] = c * ap - s * aq;
-        A[i * kEigLd + q] = s * ap + c * aq;
-        const T vp = V[i * kEigLd + p], vq = V[i * kEigLd + q];
-        V[i * kEigLd + p] = c * vp - s * vq;
-        V[i * kEigLd + q] = s * vp + c * vq;
+      // A <- J^T A J and V <- V J in one pass.  The step's rotations act on
+      // disjoint pairs, so every element of A lies in one 2 x 2 block
+      // (pair a's rows) x (pair b's columns), which one thread rotates on
+      // both sides in registers; every (row of V, pair) is one item too.
+      // Items come from a table built once per solve (no integer division
+      // in the step, which would run on the special-function pipe).
+      const int nitems = npair * npair + m * npair;
+      for (int t = tid; t < nitems; t += nt) {
+        const int it = items[t];
+        const int x = it >> 8, y = it & 255;
+        if (t < npair * npair) {
+          // block: row pair x, column pair y
+          const T sa = rot[4 * x + 3], sb = rot[4 * y + 3];
+          if (sa == T(0) && sb == T(0)) continue;
+          const int pa = (int)rot[4 * x], qa = (int)rot[4 * x + 1];
+          const int pb = (int)rot[4 * y], qb = (int)rot[4 * y + 1];
+          const T ca = rot[4 * x + 2], cb = rot[4 * y + 2];
+          const bool hq = qa < m, hqb = qb < m;
+          const T m00 = A[pa * kEigLd + pb], m01 = hqb ? A[pa * kEigLd + qb] : T(0);
+          const T m10 = hq ? A[qa * kEigLd + pb] : T(0), m11 = (hq && hqb) ? A[qa * kEigLd + qb] : T(0);
+          // rows: p' = c p - s q, q' = s p + c q
+          const T r00 = ca * m00 - sa * m10, r01 = ca * m01 - sa * m11;
+          const T r10 = sa * m00 + ca * m10, r11 = sa * m01 + ca * m11;
+          // columns likewise
+          A[pa * kEigLd + pb] = cb * r00 - sb * r01;
+          if (hqb) A[pa * kEigLd + qb] = sb * r00 + cb * r01;
+          if (hq) A[qa * kEigLd + pb] = cb * r10 - sb * r11;
+          if (hq && hqb) A[qa * kEigLd + qb] = sb * r10 + cb * r11;
+        } else {
+          // V row x, column pair y
+          const T sb = rot[4 * y + 3];
+          if (sb == T(0)) continue;
+          const int pb = (int)rot[4 * y], qb = (int)rot[4 * y + 1];
+          const T cb = rot[4 * y + 2];
+          const T vp = V[x * kEigLd + pb], vq = V[x * kEigLd + qb];
+          V[x * kEigLd + pb] = cb * vp - sb * vq;
+          V[x * kEigLd + qb] = sb * vp + cb * vq;
+        }
       }
       __syncthreads();
     }
@@ -320,6 +344,7 @@ struct EigSmem {
   float rotf[4 * (kEigMaxM / 2 + 1)];
   int keep[kEigMaxM];
   int sel[kEigMaxM];
+  unsigned short items[(kEigMaxM / 2) * (kEigMaxM / 2) + kEigMaxM * (kEigMaxM / 2)];
   int nkeep;
   int any;
   double floor_d;
@@ -338,7 +363,7 @@ __device__ void eig_eigh(double* A, double* V, int m, double* S1, double* S2, Ei
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int q = tid; q < m * kEigLd; q += nt) sm.Af[q] = (float)A[q];
   __syncthreads();
-  eig_jacobi<float>(sm.Af, sm.Vf, m, 1e-7f, 1e-9f, 12, sm.rotf, &sm.any, &sm.floor_f);
+  eig_jacobi<float>(sm.Af, sm.Vf, m, 1e-7f, 1e-9f, 12, sm.rotf, &sm.any, &sm.floor_f, sm.items);
   for (int q = tid; q < m * kEigLd; q += nt) S1[q] = (double)sm.Vf[q];
   __syncthreads();
   for (int pass = 0; pass < 2; ++pass) {
@@ -363,7 +388,7 @@ __device__ void eig_eigh(double* A, double* V, int m, double* S1, double* S2, Ei
     }
   }
   __syncthreads();
-  eig_jacobi<double>(A, S2, m, 1e-15, 0.0, 30, sm.rot, &sm.any, &sm.floor_d);
+  eig_jacobi<double>(A, S2, m, 1e-15, 0.0, 30, sm.rot, &sm.any, &sm.floor_d, sm.items);
   eig_matmul(V, S1, S2, m, false);  // V0 V1
 }
 
@@ -484,17 +509,16 @@ __device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* t
   }
   __syncthreads();
   eig_eigh(sm.G, sm.U, r, sm.H, sm.T, sm);
-  if (tid == 0) {
-    // the k smallest Ritz values, ascending (selection by rank; ties by index)
-    for (int i = 0; i < r; ++i) {
-      const double ti = sm.G[i * kEigLd + i];
-      int rank = 0;
-      for (int j = 0; j < r; ++j) {
-        const double tj = sm.G[j * kEigLd + j];
-        if (tj < ti || (tj == ti && j < i)) ++rank;
-      }
-      sm.sel[rank] = i;
+  // the k smallest Ritz values, ascending (selection by rank, ties by
+  // index; thread i ranks value i)
+  for (int i = tid; i < r; i += nt) {
+    const double ti = sm.G[i * kEigLd + i];
+    int rank = 0;
+    for (int j = 0; j < r; ++j) {
+      const double tj = sm.G[j * kEigLd + j];
+      if (tj < ti || (tj == ti && j < i)) ++rank;
     }
+    sm.sel[rank] = i;
   }
   __syncthreads();
   const int kk = r < k ? r : k;

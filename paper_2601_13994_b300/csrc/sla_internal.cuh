@@ -267,7 +267,11 @@ __device__ __forceinline__ float fma_if(bool on, float v, float x, float acc) {
   return acc;
 }
 
-template <int B = kGatherBatch, class ColAt, class ValAt, class XAt>
+// FullWarp: every lane of the warp calls this together, once per row (the
+// TMA pipeline's consumers); the remainder then issues only as many FMAs as
+// the warp's longest remainder needs, behind warp-uniform guards, so a warp
+// of rows with 7 entries (4 + 3) issues 7 FMAs per row, not 8.
+template <int B = kGatherBatch, bool FullWarp = false, class ColAt, class ValAt, class XAt>
 __device__ __forceinline__ auto row_sum_batched(int a, int e, ColAt&& col_at, ValAt&& val_at, XAt&& x)
     -> decltype(gather_at(x, 0)) {
   using T = decltype(gather_at(x, 0));
@@ -286,7 +290,9 @@ __device__ __forceinline__ auto row_sum_batched(int a, int e, ColAt&& col_at, Va
 #pragma unroll
     for (int j = 0; j < B; ++j) acc = fma(v[j], xv[j], acc);
   }
-  const int rem = e - k0;
+  const int rem = e - k0;  // 0 .. B-1
+  // every lane reaches this once (after its own main loop)
+  const int rmax = FullWarp ? __reduce_max_sync(0xffffffffu, rem) : B - 1;
   if (rem > 0) {
     int c[B];
     T v[B], xv[B];
@@ -302,9 +308,13 @@ __device__ __forceinline__ auto row_sum_batched(int a, int e, ColAt&& col_at, Va
 #pragma unroll
     for (int j = 0; j < B; ++j)
       if (j < rem) xv[j] = gather_at(x, c[j]);
-    // predicated: the FP64 pipe must not see the padding entries
+    // predicated, and (FullWarp) no further than the warp's longest
+    // remainder: the FP64 pipe must not see the padding entries
 #pragma unroll
-    for (int j = 0; j < B; ++j) acc = fma_if(j < rem, v[j], xv[j], acc);
+    for (int j = 0; j < B - 1; ++j) {
+      if (j >= rmax) break;
+      acc = fma_if(j < rem, v[j], xv[j], acc);
+    }
   }
   return acc;
 }

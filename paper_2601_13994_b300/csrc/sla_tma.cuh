@@ -303,7 +303,8 @@ __device__ __forceinline__ void spmv_pipeline_m(const Mat& mat, XAt x, AuxAt aux
         const auto av = aux_at(aux, r0 + tid);
         const int a = S.rp[tid];
         const int e = (tid + 1 < kRows) ? S.rp[tid + 1] : k1;
-        const X acc = row_sum_batched(a, e, col_at, val_at, x);
+        // every consumer lane sums one row of the tile: whole warps
+        const X acc = row_sum_batched<kGatherBatch, true>(a, e, col_at, val_at, x);
         epi(r0 + tid, acc, av);
       } else {
         const int i0 = 2 * tid;

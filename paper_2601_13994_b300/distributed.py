@@ -125,9 +125,9 @@ class DistributedMatrix:
         self.layout = lay
         self.total_ext = lay["total_ext"]
         self.halo_sizes = lay["n_halo"].tolist()
-        dev = torch.device(device)
+        self.row_off = _i32(self.row_off_h, torch.device(device))
+        dev = self.row_off.device  # with its index (cuda:0), as the tensors report it
         self.device = dev
-        self.row_off = _i32(self.row_off_h, dev)
         self.src = _i32(lay["src"], dev)
         self.own_pos = _i32(lay["own_pos"], dev)
         self.hptr = _i32(lay["hptr"], dev)
