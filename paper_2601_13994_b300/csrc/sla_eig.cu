@@ -189,6 +189,41 @@ __global__ void __launch_bounds__(kEigThreads) eig_spmm_kernel(EigPtrs P, int mo
 // (In FP64 no floor is used: an absolute floor of 1e-18 or 1e-16 of the
 // largest diagonal entry of the scaled Gram matrix made LOBPCG stall at a
 // residual of 1.4e-7 on the 1D Laplacian, n = 200, k = 6.)
+// The Jacobi rotation (c, s) that annihilates a_pq, from d = a_qq - a_pp and
+// e = 2 a_pq: tan = sgn(d e) |e| / (|d| + sqrt(d^2 + e^2)) (the smaller root
+// of t^2 + 2 (d/e) t - 1 = 0), cos = 1 / sqrt(1 + tan^2), sin = tan cos.
+// In FP32 directly.  In FP64 the tangent is taken in FP32 (the special-
+// function unit, against FP64 division and square-root sequences at two
+// lanes per clock per SM -- this computation is on every step's critical
+// path) and (c, s) are then scaled to unit norm by two Newton steps of
+// y <- y (3 - (c^2 + s^2) y^2) / 2 in FP64, so the rotation is orthogonal to
+// FP64 rounding; its angle is accurate to FP32, i.e. it leaves a_pq at
+// ~1e-7 of its value, and the sweeps repeat until every a_pq passes the
+// FP64 threshold (convergence is then linear with rate ~1e-7 per sweep).
+__device__ __forceinline__ void rotation_of(float d, float e, float& c, float& s) {
+  const float ad = fabsf(d), ae = fabsf(e);
+  const float big = fmaxf(ad, ae), small = fminf(ad, ae);
+  const float rr = small / big;
+  const float hyp = big * sqrtf(1.0f + rr * rr);
+  float t = ae / (ad + hyp);
+  if ((d < 0.0f) != (e < 0.0f)) t = -t;
+  c = rsqrtf(1.0f + t * t);
+  s = t * c;
+}
+__device__ __forceinline__ void rotation_of(double d, double e, double& c, double& s) {
+  float cf, sf;
+  rotation_of((float)d, (float)e, cf, sf);
+  c = (double)cf;
+  s = (double)sf;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double nrm = c * c + s * s;
+    const double y = 0.5 * (3.0 - nrm);  // 1/sqrt(nrm) to second order, nrm = 1 + O(1e-7)
+    c *= y;
+    s *= y;
+  }
+}
+
 template <class T>
 __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps, T* rot, int* s_any,
                            T* s_floor, unsigned short* items) {
@@ -247,15 +282,7 @@ __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps
           // reciprocal square root -- the rotation is on every step's
           // critical path
           if (apq * apq > rel * rel * fabs(app * aqq) && fabs(apq) > floor_abs) {
-            const T d = aqq - app, e = T(2) * apq;
-            const T ad = fabs(d), ae = fabs(e);
-            const T big = fmax(ad, ae), small = fmin(ad, ae);
-            const T rr = small / big;
-            const T hyp = big * sqrt(T(1) + rr * rr);
-            T t = ae / (ad + hyp);
-            if ((d < T(0)) != (e < T(0))) t = -t;
-            c = rsqrt(T(1) + t * t);
-            s = t * c;
+            rotation_of(aqq - app, T(2) * apq, c, s);
             *s_any = 1;
           }
         }
@@ -430,9 +457,14 @@ __device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* t
     if (tid == 0) {
       const double piv = sm.U[j * kEigLd + j];
       if (!(piv > 1e-10)) sm.any = 1;
-      const double l = sqrt(fmax(piv, 1e-300));
-      sm.U[j * kEigLd + j] = l;
-      sm.scale2[j] = 1.0 / l;
+      // 1/sqrt(piv): FP32 estimate, two Newton steps in FP64 (piv in
+      // (1e-10, 1] here: the scaled Gram matrix has a unit diagonal)
+      const double pv = fmax(piv, 1e-300);
+      double y = (double)rsqrtf((float)pv);
+      y = y * (1.5 - 0.5 * pv * y * y);
+      y = y * (1.5 - 0.5 * pv * y * y);
+      sm.U[j * kEigLd + j] = pv * y;
+      sm.scale2[j] = y;
     }
     __syncthreads();
     if (sm.any) break;
