@@ -438,9 +438,15 @@ def extra_rows(dev, args, peak):
     # r^, v; s: r, v, s; t = A s: s, s, t; x: x^, p, s, t, r^, x^, r)
     bpi = 2 * (12 * nnz + 4 * (n + 1)) + 160 * n
     gbs = bpi * info.iters / (ms / 1e3) / 1e9
+    # the algorithmic model of a BiCGStab iteration the scope table gives:
+    # two SpMVs and about 23 streams of n doubles
+    bpi_model = 2 * (12 * nnz + 4 * n) + 23 * 8 * n
+    gbs_model = bpi_model * info.iters / (ms / 1e3) / 1e9
     out["bicgstab_convdiff3d_128_pe10"] = {"s": ms / 1e3, "iters": info.iters, "status": info.status,
                                            "gbs": gbs, "frac_of_measured_hbm": gbs / peak,
-                                           "bytes_per_iter": bpi}
+                                           "bytes_per_iter": bpi,
+                                           "bytes_per_iter_scope_model": bpi_model,
+                                           "frac_of_measured_hbm_scope_model": gbs_model / peak}
     del A, vt, bt, x
     # 3D 256^3 (the previous headline size): the PCG solve with its roofline,
     # then the adjoint backward A^T lambda = 2x (L = sum x^2) + gradient pass
