@@ -40,7 +40,7 @@ FALLBACK_HBM_GBS = 6400.0
 # small case under the capture size rule) and scaled by rows to the bench's
 # N (traffic grows in proportion to the rows; profiles/pcg_iteration_diffusion3d_256.md);
 # valid only for these kernels.
-TRAFFIC_PER_ITER_176 = 918981632
+TRAFFIC_PER_ITER_176 = 923460608  # K1 561.1 MB + K2 271.1 MB + K3 91.3 MB, after K1's four-blocks-per-SM change
 # FP64 peak: derived, not measured by the driver: 2 DFMA per clock per SM
 # (ncu's peak_sustained for the FP64 pipe) x 148 SMs x 2 flop x 2.032 GHz.  A
 # dependent-FMA probe of this project measured 1.10 TFLOP/s.
