@@ -561,11 +561,17 @@ def batched_bicgstab_rows(dev):
     fl = 0.0
     for s, m in enumerate(mats):
         fl += (2 * 2 * int(m[0][-1]) + 2 * 15 * (len(m[0]) - 1)) * int(its[s])
+    # one CTA per system (1024 threads, vectors in the workspace) against the
+    # default block teams (3 blocks from 32768 entries)
+    ms_cta, _ = _time(lambda: sla.bicgstab_batched_list(P, vt, bt, rtol=1e-8, config=3 | 16 | 32))
+    ms_team, _ = _time(lambda: sla.bicgstab_batched_list(P, vt, bt, rtol=1e-8, config=0))
+    tuned = sla.tuned_configs().get(("bicg_list", P.n_max, P.total_rows, P.total_nnz, P.batch))
     out["bicgstab_batched_list_512_convdiff"] = {
         "s": ms / 1e3, "total_rows": P.total_rows, "iters_mean": float(its.mean()), "iters_max": int(its.max()),
         "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
         "fp64_tflops": fl / (ms / 1e3) / 1e12, "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
-        "tuned_config": sla.tuned_configs().get(("bicg_list", P.n_max, P.total_rows, P.total_nnz, P.batch))}
+        "tuned_config": tuned, "tuned_shape": sla.bicg_list_shape(tuned) if tuned is not None else None,
+        "candidates": len(sla.BICG_LIST_CONFIGS), "one_cta_s": ms_cta / 1e3, "teams_default_s": ms_team / 1e3}
     return out
 
 

@@ -709,8 +709,19 @@ int32_t sla_bicgstab_batched_shared(const sla_csr* A, int32_t batch,
                                     size_t ws_bytes, void* stream);
 
 /* Distinct patterns in the concatenated layout of sla_cg_batched_list
- * (n_off, nnz_off, rowptr back to back, local columns, optional order);
- * every system on one CTA (no block teams).
+ * (n_off, nnz_off, rowptr back to back, local columns, optional order).
+ * A single CTA runs at one SM's FP64 rate, so by default (config bit 32
+ * clear, n_max >= 2048, a device with cooperative launch) the systems with
+ * at least a threshold of entries are solved by teams of blocks of one
+ * cooperative launch (the same recurrence; team sums added in a fixed
+ * order; 512 threads per block, every vector in the workspace), and the
+ * rest of the queue by single blocks of that launch.  A team barrier that
+ * waits longer than its bound sets status SLA_ERR_TIMEOUT in the records
+ * of the systems left unsolved.
+ * config: bit 32 = one CTA per system, shaped by the low 5 bits as for
+ * the shared pattern; without it, bits 8-9 = team size (0: 3 blocks, 1: 2,
+ * 2: 4, 3: 6), bits 10-11 = entry threshold (0: 32768, 1: 16384,
+ * 2: 65536, 3: 131072); other bits SLA_ERR_INVALID.
  * Workspace: SLA_WS_BATCHED with (total_rows, 1). */
 int32_t sla_bicgstab_batched_list(int32_t batch, int32_t n_max,
                                   int32_t total_rows, const int32_t* n_off,

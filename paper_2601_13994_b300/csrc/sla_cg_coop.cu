@@ -865,12 +865,31 @@ __global__ void team_info_prefill_kernel(int batch, sla_info* info) {
     info[sys] = sla_info{0, SLA_ERR_TIMEOUT, NAN, NAN};
 }
 
-// Team scratch inside the batched workspace: counters, slots, queue counter,
-// partials for up to kMaxTeams teams.
-constexpr int kMaxTeams = kCoopMaxGrid / kTeamBlocks;
 size_t team_scratch_bytes() {
-  return al256(sizeof(unsigned) * kMaxTeams) + al256(sizeof(int) * kMaxTeams) + 256 +
-         al256(sizeof(double) * kMaxTeams * 8 * kTeamBlocks) + 256;
+  return al256(sizeof(unsigned) * kCoopMaxGrid) + al256(sizeof(int) * kCoopMaxGrid) + 256 +
+         al256(sizeof(double) * 8 * kCoopMaxGrid);
+}
+
+TeamScratch team_scratch(void* scratch) {
+  char* base = (char*)scratch;
+  TeamScratch t;
+  t.counters = (unsigned*)base;
+  base += al256(sizeof(unsigned) * kCoopMaxGrid);
+  t.slots = (int*)base;
+  base += al256(sizeof(int) * kCoopMaxGrid);
+  t.next = (unsigned*)base;
+  t.err = (int*)(base + 128);
+  base += 256;
+  t.parts = (double*)base;
+  return t;
+}
+
+int team_scratch_arm(void* scratch, int batch, sla_info* info, cudaStream_t s) {
+  const TeamScratch t = team_scratch(scratch);
+  SLA_CUDA_TRY(cudaMemsetAsync(scratch, 0, (char*)t.parts - (char*)scratch, s));
+  team_info_prefill_kernel<<<(batch + 255) / 256, 256, 0, s>>>(batch, info);
+  SLA_CUDA_TRY(cudaGetLastError());
+  return SLA_OK;
 }
 
 // Solves the systems of a concatenated batch with at least min_nnz entries
@@ -891,7 +910,7 @@ int launch_batched_teams(int batch, int min_nnz, const int* rowptr, const int* c
   if (grid > kCoopMaxGrid) grid = kCoopMaxGrid;
   grid -= grid % kTeamBlocks;
   if (grid < kTeamBlocks) return SLA_OK;
-  char* base = (char*)scratch;
+  const TeamScratch ts = team_scratch(scratch);
   TeamBatchArgs B;
   B.batch = batch;
   B.min_nnz = min_nnz;
@@ -905,14 +924,11 @@ int launch_batched_teams(int batch, int min_nnz, const int* rowptr, const int* c
   B.x = x;
   B.info = info;
   B.gvec = gvec;
-  B.counters = (unsigned*)base;
-  base += al256(sizeof(unsigned) * kMaxTeams);
-  B.slots = (int*)base;
-  base += al256(sizeof(int) * kMaxTeams);
-  B.next = (unsigned*)base;
-  B.err = (int*)(base + 128);
-  base += 256;
-  B.parts = (double*)base;
+  B.counters = ts.counters;
+  B.slots = ts.slots;
+  B.next = ts.next;
+  B.err = ts.err;
+  B.parts = ts.parts;
   B.rtol = rtol;
   B.atol = atol;
   B.max_iter = max_iter;
@@ -920,9 +936,8 @@ int launch_batched_teams(int batch, int min_nnz, const int* rowptr, const int* c
   B.precond = precond;
   B.use_x0 = use_x0;
   // counters, queue and error flag start at zero
-  SLA_CUDA_TRY(cudaMemsetAsync(scratch, 0, (char*)B.parts - (char*)scratch, s));
-  team_info_prefill_kernel<<<(batch + 255) / 256, 256, 0, s>>>(batch, info);
-  SLA_CUDA_TRY(cudaGetLastError());
+  const int rc = team_scratch_arm(scratch, batch, info, s);
+  if (rc != SLA_OK) return rc;
   void* args[] = {&B};
   SLA_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCoopThreads), args, 0, s));
   *launched = true;

@@ -73,6 +73,24 @@ __device__ __forceinline__ bool coop_sums(double (&v)[NV], Team& tm, int& buf, C
   return true;
 }
 
+// Block-team scratch at the head of the batched workspace: a barrier counter
+// and a queue slot per team (at most kCoopMaxGrid teams), the queue counter,
+// the error flag, and 2 x 4 partial sums per block of the launch (a team of
+// G blocks with index q uses parts[8 G q, 8 G (q + 1))).
+struct TeamScratch {
+  unsigned* counters;
+  int* slots;
+  unsigned* next;
+  int* err;
+  double* parts;
+};
+size_t team_scratch_bytes();
+TeamScratch team_scratch(void* scratch);
+// Zeroes the counters, slots, queue counter and error flag of the scratch and
+// marks systems [0, batch) as timed out (a system no block reached keeps that
+// record; each solve overwrites its own), on stream s.
+int team_scratch_arm(void* scratch, int batch, sla_info* info, cudaStream_t s);
+
 // Grid size of a cooperative solve over n rows at `occ` resident blocks per
 // SM (one row per thread in every phase).
 inline int coop_grid(int dev, int n, int occ) {

@@ -831,6 +831,21 @@ def cg_batched_list(P: CSRList, val: torch.Tensor, b: torch.Tensor, *, rtol: flo
 
 # BiCGStab batches: 256/512/1024 threads, vectors on chip as far as they fit / in global
 BICG_BATCH_CONFIGS = (1, 2, 3, 1 | 16, 2 | 16, 3 | 16)
+# Lists: one CTA per system (bit 32), or block teams for the large systems:
+# team size code << 8 (3, 2, 4, 6 blocks), entry threshold code << 10
+# (32768, 16384, 65536, 131072 entries).
+BICG_TEAM_SIZES, BICG_TEAM_MIN_NNZ = (3, 2, 4, 6), (32768, 16384, 65536, 131072)
+BICG_LIST_CONFIGS = ((1 | 32, 2 | 32, 3 | 32, 1 | 16 | 32, 2 | 16 | 32, 3 | 16 | 32)
+                     + tuple((t << 8) | (m << 10) for t in range(4) for m in range(3)))
+
+
+def bicg_list_shape(config: int) -> dict:
+    """The launch shape a batched-BiCGStab list config word selects."""
+    if config & 32:
+        return {"block_teams": False, "threads_per_cta": {0: "auto", 1: 256, 2: 512, 3: 1024}.get(config & 15, "?"),
+                "vectors": "global" if config & 16 else "shared memory where they fit"}
+    return {"block_teams": True, "team_blocks": BICG_TEAM_SIZES[(config >> 8) & 3],
+            "team_min_nnz": BICG_TEAM_MIN_NNZ[(config >> 10) & 3], "threads_per_cta": 512, "vectors": "global"}
 
 
 def bicgstab_batched(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 1e-10,
@@ -867,8 +882,9 @@ def bicgstab_batched_list(P: CSRList, val: torch.Tensor, b: torch.Tensor, *, rto
                           x0: torch.Tensor | None = None, max_restarts: int = 2, config: int | str = "auto",
                           out: torch.Tensor | None = None):
     """Distinct nonsymmetric patterns (concatenated values / right-hand
-    sides) by BiCGStab in one persistent launch; returns (x concatenated,
-    SolveInfo with B records)."""
+    sides) by BiCGStab in one launch (the large systems by teams of blocks
+    unless config has bit 32; see BICG_LIST_CONFIGS); returns (x
+    concatenated, SolveInfo with B records)."""
     _need(val, torch.float64, P.device, "val", P.total_nnz)
     _need(b, torch.float64, P.device, "b", P.total_rows)
     x = torch.empty(P.total_rows, dtype=torch.float64, device=P.device) if out is None else out
@@ -888,7 +904,7 @@ def bicgstab_batched_list(P: CSRList, val: torch.Tensor, b: torch.Tensor, *, rto
             info.data_ptr(), cfg, ws.data_ptr(), ws.numel(), _stream_ptr(P.device)))
 
     cfg = _resolve_config(config, ("bicg_list", P.n_max, P.total_rows, P.total_nnz, P.batch), run, x, x0,
-                          BICG_BATCH_CONFIGS)
+                          BICG_LIST_CONFIGS)
     run(cfg)
     return x, SolveInfo(info)
 

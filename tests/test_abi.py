@@ -180,6 +180,10 @@ def test_batched_bicgstab_and_list_transpose_reject_bad_arguments_without_launch
                                          ctypes.byref(o), fake, 0, ws, big, None) == L.SLA_ERR_INVALID
     assert lib.sla_bicgstab_batched_list(3, 10, 30, fake, fake, fake, fake, fake, fake, fake, None,
                                          ctypes.byref(o), fake, 0, ws, big, None) == L.SLA_ERR_INVALID
+    for cfg in (64, 1 << 12, 1 << 4 | 1 << 7):                              # unknown list config bits
+        assert lib.sla_bicgstab_batched_list(3, 10, 30, fake, fake, fake, fake, fake, fake, x, None,
+                                             ctypes.byref(o), fake, cfg, ws, big, None) == L.SLA_ERR_INVALID
+    assert shared(cfg=1 << 8) == L.SLA_ERR_INVALID                          # team bits: lists only
     # list transpose: empty list, null pointers, aliasing, workspace
     assert lib.sla_csr_list_transpose(0, 0, 0, None, None, None, None, None, None, None, None, 0,
                                       None) == L.SLA_OK

@@ -131,11 +131,49 @@ def test_distinct_patterns_match_oracle():
     xh = x.cpu().numpy()
     xs = [xh[P.n_off_h[s]:P.n_off_h[s + 1]] for s in range(len(mats))]
     _check_systems([m[0] for m in mats], [m[1] for m in mats], [m[2] for m in mats], bs, xs, info, 1e-10)
-    # every vector in the workspace: the same bits
-    x16, _ = sla.bicgstab_batched_list(P, to_dev(vals), to_dev(np.concatenate(bs)), rtol=1e-10, config=2 | 16)
-    x2, _ = sla.bicgstab_batched_list(P, to_dev(vals), to_dev(np.concatenate(bs)), rtol=1e-10, config=2)
+    # one CTA per system, every vector in the workspace or on chip: the same bits
+    x16, _ = sla.bicgstab_batched_list(P, to_dev(vals), to_dev(np.concatenate(bs)), rtol=1e-10, config=2 | 16 | 32)
+    x2, _ = sla.bicgstab_batched_list(P, to_dev(vals), to_dev(np.concatenate(bs)), rtol=1e-10, config=2 | 32)
     torch.cuda.synchronize()
     assert torch.equal(x16, x2)
+
+
+def test_list_block_teams_match_oracle():
+    """The large systems of a list solved by teams of blocks of one
+    cooperative launch (sums of the team's blocks in a fixed order), the
+    small ones by single blocks of the same launch: every team size (2, 3,
+    4, 6 blocks) and entry threshold against the oracle per system, and
+    against one CTA per system."""
+    mats = I.convdiff_list(24, seed0=700, n_lo=100, n_hi=3000)
+    mats += [I.convdiff2d_random(200, 160, 11),   # 32000 rows, ~159 k entries: a team at every threshold
+             I.convdiff2d_random(150, 120, 12),   # 18000 rows, ~90 k entries
+             I.convdiff2d_random(100, 75, 13),    # 7500 rows, ~37 k entries
+             I.convdiff2d_random(73, 71, 14)]     # 5183 rows (not a multiple of any team's threads)
+    P = sla.CSRList([(rp, c) for rp, c, _ in mats])
+    vals = to_dev(np.concatenate([v for _, _, v in mats]))
+    bs = [I.rhs_uniform(len(rp) - 1, 80 + s) for s, (rp, _, _) in enumerate(mats)]
+    bt = to_dev(np.concatenate(bs))
+    xo = [oracle.bicgstab(rp, c, v, b, rtol=1e-13)[0] for (rp, c, v), b in zip(mats, bs)]
+    xc, ic = sla.bicgstab_batched_list(P, vals, bt, rtol=1e-10, config=3 | 32)
+    torch.cuda.synchronize()
+    xc = xc.cpu().numpy()
+    for cfg in [(t << 8) | (m << 10) for t in range(4) for m in range(4)]:
+        x, info = sla.bicgstab_batched_list(P, vals, bt, rtol=1e-10, config=cfg)
+        torch.cuda.synchronize()
+        assert (np.atleast_1d(info.status) == 0).all(), (cfg, info.status)
+        xh = x.cpu().numpy()
+        for s in range(len(mats)):
+            xs = xh[P.n_off_h[s]:P.n_off_h[s + 1]]
+            assert elementwise_rel(xs, xo[s]) <= 1e-8, (cfg, s)
+        # both meet rtol 1e-10 on their own; their solutions agree to the
+        # same 1e-8 as each does with the oracle's x*
+        assert rel(xh, xc) <= 1e-8, cfg
+        if cfg == 0:
+            _check_systems([m[0] for m in mats], [m[1] for m in mats], [m[2] for m in mats], bs,
+                           [xh[P.n_off_h[s]:P.n_off_h[s + 1]] for s in range(len(mats))], info, 1e-10)
+    shape = sla.bicg_list_shape(2 << 8 | 1 << 10)
+    assert shape["block_teams"] and shape["team_blocks"] == 4 and shape["team_min_nnz"] == 16384
+    assert not sla.bicg_list_shape(3 | 32)["block_teams"]
 
 
 def test_graph_capture_and_replay():
