@@ -3,25 +3,21 @@
 // The paper's GPU-native backend offers BiCGStab (van der Vorst 1992) for
 // nonsymmetric systems (Sec. 1, Sec. 3.1); it gives no variant, so this is the
 // textbook right-preconditioned form with shadow residual r^ = r0 and the
-// Jacobi preconditioner M = diag(A), folded into the matrix (A^ = A D^-1,
-// iterate x^ = D x).  Four kernels an iteration:
+// Jacobi preconditioner M = diag(A):
 //
-//   KB  v = A^ p ,  partial r^.v                 -> alpha = rho / r^.v
-//   KC  s = r - alpha v ; |s|^2, r^.s            -> half-step exit test
-//   KD  t = A^ s ,  partial t.t, t.s, r^.t       -> omega = t.s / t.t,
-//       the next rho = r^.s - omega r^.t (= r^.(s - omega t) = r^.r_new by
-//       distributivity: the same inner product, summed in two parts), and
-//       beta = (rho_next / rho)(alpha / omega)
-//   KE  x^ += alpha p + omega s ; r = s - omega t ; p = r + beta (p - omega v);
-//       |r|^2                                    -> convergence
+//   rho = r^.r ; beta = (rho / rho_prev)(alpha / omega)
+//   KA  p = r + beta (p - omega v) ;  p^ = M^-1 p
+//   KB  v = A p^ ,  partial r^.v              -> alpha = rho / r^.v
+//   KC  s = r - alpha v ; s^ = M^-1 s ; |s|^2 -> half-step exit test
+//   KD  t = A s^ ,  partial t.t, t.s          -> omega = t.s / t.t
+//   KE  x += alpha p^ + omega s^ ; r = s - omega t ; |r|^2, r^.r
+//                                             -> convergence, next beta
 //
-// The direction update of the next iteration rides in KE because beta is
-// known once KD's reduction ends; p = r at a start or restart.  The same
-// device state machine, graph WHILE loop / host loop, descriptor,
-// true-residual check and restart rule as the CG solver; KB and KD are the
-// TMA-pipelined (or row-per-thread) SpMV with dot-product epilogues.
+// The same device state machine, graph WHILE loop / host loop, descriptor,
+// true-residual check and restart rule as the CG solver.  KB and KD are the
+// TMA-pipelined SpMV with dot-product epilogues.
 //
-// Algorithmic bytes per iteration: 2 (12 nnz + 4 (n+1)) + 152 n.
+// Algorithmic bytes per iteration: 2 (12 nnz + 4 (n+1)) + 200 n.
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -89,7 +85,8 @@ __global__ void __launch_bounds__(kVT) bicg_init_kernel(BiPtrs P) {
     P.dinv[i] = di;
     P.r[i] = ri;
     P.rh[i] = ri;
-    P.p[i] = ri;  // p = r at a start
+    P.p[i] = 0.0;
+    P.v[i] = 0.0;
     acc[0] = fma(bi, bi, acc[0]);
     acc[1] = fma(ri, ri, acc[1]);
   }
@@ -161,13 +158,38 @@ __global__ void __launch_bounds__(kVT) bicg_unscale_kernel(BiPtrs P) {
   for (int i = blockIdx.x * kVT + threadIdx.x; i < d.n; i += gridDim.x * kVT) d.x[i] *= P.dinv[i];
 }
 
+// -------------------------------------------------------------- KA
+__global__ void __launch_bounds__(kVT) bicg_p_kernel(BiPtrs P) {
+  if (__ldcg(&P.st->phase) != kPhaseRun) return;
+  const int n = P.d->n;
+  const double beta = __ldcg(&P.st->beta), omega = __ldcg(&P.st->omega);
+  const int stride = gridDim.x * kVT;
+  for (int i0 = blockIdx.x * kVT + threadIdx.x; i0 < n; i0 += kU * stride) {
+    double ri[kU], pi[kU], vi[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = i0 + u * stride;
+      if (i < n) {
+        ri[u] = __ldg(P.r + i);
+        pi[u] = P.p[i];
+        vi[u] = __ldg(P.v + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = i0 + u * stride;
+      if (i < n) P.p[i] = fma(beta, fma(-omega, vi[u], pi[u]), ri[u]);
+    }
+  }
+}
+
 // -------------------------------------------------------------- KB / KD
 // which == 0: v = A^ p, partial r^.v ;  which == 1: t = A^ s, partials t.t, t.s
 // (A^ = A D^{-1}; r^ here is the shadow residual r0, not a preconditioned vector)
 // run(x, aux, epi) performs y = A x through one of the SpMV schemes.
 template <int which, int NT, int M, class Run>
 __device__ __forceinline__ void bicg_spmv_body(const BiPtrs& P, double (&red)[M], bool* s_last, Run&& run) {
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  double a0 = 0.0, a1 = 0.0;
   if (which == 0) {
     double* __restrict__ v = P.v;
     run(P.p, P.rh, [&](int row, double y, double rhr) {
@@ -176,26 +198,20 @@ __device__ __forceinline__ void bicg_spmv_body(const BiPtrs& P, double (&red)[M]
     });
   } else {
     double* __restrict__ t = P.t;
-    const double* __restrict__ rh = P.rh;
     run(P.s, P.s, [&](int row, double y, double sr) {
       t[row] = y;
       a0 = fma(y, y, a0);
       a1 = fma(y, sr, a1);
-      a2 = fma(__ldg(rh + row), y, a2);
     });
   }
   double acc[2] = {a0, a1};
   block_sums<NT, 2>(acc, red);
-  double acc2[1] = {a2};
-  if (which == 1) block_sums<NT, 1>(acc2, red);
   if (threadIdx.x == 0) {
     P.part[blockIdx.x] = acc[0];
     P.part[kMaxBlocks + blockIdx.x] = acc[1];
-    if (which == 1) P.part[2 * kMaxBlocks + blockIdx.x] = acc2[0];
   }
   if (!last_block_arrive(&P.st->cnt[which == 0 ? 1 : 3], s_last)) return;
   reduce_partials<NT, 2>(P.part, kMaxBlocks, gridDim.x, acc, red);
-  if (which == 1) reduce_partials<NT, 1>(P.part + 2 * kMaxBlocks, kMaxBlocks, gridDim.x, acc2, red);
   if (threadIdx.x == 0) {
     KrylovState& s = *P.st;
     if (__ldcg(&s.err) != 0) {
@@ -210,7 +226,7 @@ __device__ __forceinline__ void bicg_spmv_body(const BiPtrs& P, double (&red)[M]
         s.alpha = s.rho / rv;
       }
     } else {
-      const double tt = acc[0], ts = acc[1], rt = acc2[0];
+      const double tt = acc[0], ts = acc[1];
       s.tt = tt;
       s.ts = ts;
       if (!isfinite(tt) || !isfinite(ts) || tt == 0.0) {
@@ -218,9 +234,6 @@ __device__ __forceinline__ void bicg_spmv_body(const BiPtrs& P, double (&red)[M]
         s.phase = kPhaseDone;
       } else {
         s.omega = ts / tt;
-        // r^.r_new with r_new = s - omega t, summed as r^.s - omega r^.t
-        s.rho_next = s.rs - s.omega * rt;
-        s.beta = (s.rho_next / s.rho) * (s.alpha / s.omega);
       }
     }
   }
@@ -255,16 +268,15 @@ __global__ void __launch_bounds__(kVT) bicg_s_kernel(BiPtrs P) {
   const int n = P.d->n;
   const double alpha = __ldcg(&P.st->alpha);
   const int stride = gridDim.x * kVT;
-  double ss0 = 0.0, ss1 = 0.0, rs0 = 0.0, rs1 = 0.0;
+  double ss0 = 0.0, ss1 = 0.0;
   for (int i0 = blockIdx.x * kVT + threadIdx.x; i0 < n; i0 += kU * stride) {
-    double ri[kU], vi[kU], hi[kU];
+    double ri[kU], vi[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int i = i0 + u * stride;
       if (i < n) {
         ri[u] = __ldg(P.r + i);
         vi[u] = __ldg(P.v + i);
-        hi[u] = __ldg(P.rh + i);
       }
     }
 #pragma unroll
@@ -273,29 +285,20 @@ __global__ void __launch_bounds__(kVT) bicg_s_kernel(BiPtrs P) {
       if (i < n) {
         const double sn = fma(-alpha, vi[u], ri[u]);
         P.s[i] = sn;
-        if (u & 1) {
-          ss1 = fma(sn, sn, ss1);
-          rs1 = fma(hi[u], sn, rs1);
-        } else {
-          ss0 = fma(sn, sn, ss0);
-          rs0 = fma(hi[u], sn, rs0);
-        }
+        if (u & 1) ss1 = fma(sn, sn, ss1);
+        else ss0 = fma(sn, sn, ss0);
       }
     }
   }
-  double acc[2] = {ss0 + ss1, rs0 + rs1};
-  block_sums<kVT, 2>(acc, sm.red);
-  if (threadIdx.x == 0) {
-    P.part[blockIdx.x] = acc[0];
-    P.part[kMaxBlocks + blockIdx.x] = acc[1];
-  }
+  double acc[1] = {ss0 + ss1};
+  block_sums<kVT, 1>(acc, sm.red);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = acc[0];
   if (!last_block_arrive(&P.st->cnt[2], &sm.last)) return;
-  reduce_partials<kVT, 2>(P.part, kMaxBlocks, gridDim.x, acc, sm.red);
+  reduce_partials<kVT, 1>(P.part, kMaxBlocks, gridDim.x, acc, sm.red);
   if (threadIdx.x == 0) {
     KrylovState& s = *P.st;
     s.iters += 1;
     s.ss = acc[0];
-    s.rs = acc[1];
     if (sqrt(acc[0]) <= s.thresh) {  // half-step exit: x^ += alpha p in KE
       s.rr = acc[0];
       s.status = SLA_OK;
@@ -314,19 +317,19 @@ bicg_x_kernel(BiPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
   const int stride = gridDim.x * kVT;
   double acc[2] = {0.0, 0.0};
   if (phase == kPhaseRun) {
-    const double alpha = __ldcg(&P.st->alpha), omega = __ldcg(&P.st->omega), beta = __ldcg(&P.st->beta);
-    double rr1 = 0.0;
+    const double alpha = __ldcg(&P.st->alpha), omega = __ldcg(&P.st->omega);
+    double rr1 = 0.0, rh1 = 0.0;
     for (int i0 = blockIdx.x * kVT + threadIdx.x; i0 < n; i0 += kU * stride) {
-      double xi[kU], phi[kU], si[kU], ti[kU], vi[kU];
+      double xi[kU], phi[kU], si[kU], ti[kU], rhi[kU];
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
         const int i = i0 + u * stride;
         if (i < n) {
           xi[u] = d.x[i];
-          phi[u] = P.p[i];
+          phi[u] = __ldg(P.p + i);
           si[u] = __ldg(P.s + i);
           ti[u] = __ldg(P.t + i);
-          vi[u] = __ldg(P.v + i);
+          rhi[u] = __ldg(P.rh + i);
         }
       }
 #pragma unroll
@@ -336,14 +339,18 @@ bicg_x_kernel(BiPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
           d.x[i] = fma(omega, si[u], fma(alpha, phi[u], xi[u]));
           const double rn = fma(-omega, ti[u], si[u]);
           P.r[i] = rn;
-          // the next direction: p = r + beta (p - omega v)
-          P.p[i] = fma(beta, fma(-omega, vi[u], phi[u]), rn);
-          if (u & 1) rr1 = fma(rn, rn, rr1);
-          else acc[0] = fma(rn, rn, acc[0]);
+          if (u & 1) {
+            rr1 = fma(rn, rn, rr1);
+            rh1 = fma(rhi[u], rn, rh1);
+          } else {
+            acc[0] = fma(rn, rn, acc[0]);
+            acc[1] = fma(rhi[u], rn, acc[1]);
+          }
         }
       }
     }
     acc[0] += rr1;
+    acc[1] += rh1;
   } else if (phase == kPhaseHalf) {
     const double alpha = __ldcg(&P.st->alpha);
     for (int i = blockIdx.x * kVT + threadIdx.x; i < n; i += stride)
@@ -353,7 +360,8 @@ bicg_x_kernel(BiPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
       const double ti = d.b[i] - row_dot(d.rowptr, d.col, bicg_vals(P, d), d.x, i);
       P.r[i] = ti;
       P.rh[i] = ti;
-      P.p[i] = ti;  // p = r at a restart
+      P.p[i] = 0.0;
+      P.v[i] = 0.0;
       acc[0] = fma(ti, ti, acc[0]);
     }
   }
@@ -370,7 +378,7 @@ bicg_x_kernel(BiPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
   if (threadIdx.x == 0) {
     KrylovState& s = *P.st;
     if (phase == kPhaseRun) {
-      const double rr = acc[0], rho_new = s.rho_next;
+      const double rr = acc[0], rho_new = acc[1];
       s.rr = rr;
       if (!isfinite(rr)) {
         s.status = SLA_BREAKDOWN;
@@ -390,6 +398,8 @@ bicg_x_kernel(BiPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
         if (!isfinite(rho_new) || fabs(rho_new) < 1e-300) {
           s.status = SLA_BREAKDOWN;
           s.phase = kPhaseDone;
+        } else {
+          s.beta = (s.rho / s.rho_prev) * (s.alpha / s.omega);
         }
       }
     } else if (phase == kPhaseHalf) {
@@ -416,6 +426,7 @@ bicg_x_kernel(BiPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
           s.status = SLA_BREAKDOWN;
           s.phase = kPhaseDone;
         } else {
+          s.beta = tt;
           s.phase = kPhaseRun;
         }
       }
@@ -523,7 +534,7 @@ int build_graph(BiPtrs P, const SpmvKernels& k, int gs, int gv, cudaGraphExec_t*
   do {
     cudaGraphConditionalHandle h;
     if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
-    cudaGraphNode_t n_init, n_scale, n_while, nb, nc, nd, ne, n_final, n_unscale;
+    cudaGraphNode_t n_init, n_scale, n_while, na, nb, nc, nd, ne, n_final, n_unscale;
     void* a[] = {&P};
     int use_cond = 1;
     void* ae[] = {&P, &h, &use_cond};
@@ -536,7 +547,8 @@ int build_graph(BiPtrs P, const SpmvKernels& k, int gs, int gv, cudaGraphExec_t*
     cp.conditional.size = 1;
     if (cudaGraphAddNode(&n_while, g, &n_scale, nullptr, 1, &cp) != cudaSuccess) break;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if (add_kernel(body, nullptr, 0, &nb, k.kb, gs, k.threads, a, k.smem) != cudaSuccess) break;
+    if (add_kernel(body, nullptr, 0, &na, (const void*)bicg_p_kernel, gv, kVT, a) != cudaSuccess) break;
+    if (add_kernel(body, &na, 1, &nb, k.kb, gs, k.threads, a, k.smem) != cudaSuccess) break;
     if (add_kernel(body, &nb, 1, &nc, (const void*)bicg_s_kernel, gv, kVT, a) != cudaSuccess) break;
     if (add_kernel(body, &nc, 1, &nd, k.kd, gs, k.threads, a, k.smem) != cudaSuccess) break;
     if (add_kernel(body, &nd, 1, &ne, (const void*)bicg_x_kernel, gv, kVT, ae) != cudaSuccess) break;
@@ -557,6 +569,7 @@ int run_host_loop(BiPtrs P, const KrylovDesc& desc, const SpmvKernels& k, int gs
   bicg_scale_kernel<<<gv, kVT, 0, s>>>(P);
   const long long cap = 2LL * desc.max_iter + 3LL * desc.max_restarts + 8;
   for (long long body = 0; body < cap; ++body) {
+    bicg_p_kernel<<<gv, kVT, 0, s>>>(P);
     SLA_CUDA_TRY(cudaLaunchKernel(k.kb, dim3(gs), dim3(k.threads), a, k.smem, s));
     bicg_s_kernel<<<gv, kVT, 0, s>>>(P);
     SLA_CUDA_TRY(cudaLaunchKernel(k.kd, dim3(gs), dim3(k.threads), a, k.smem, s));

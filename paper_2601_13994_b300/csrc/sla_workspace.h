@@ -53,7 +53,6 @@ struct KrylovDesc {
 struct KrylovState {
   double rho, pq, rr, bnorm, thresh, alpha, beta, omega;
   double rho_prev, tt, ts, ss;
-  double rs, rho_next;  // BiCGStab: r^.s and the next rho = r^.s - omega r^.t
   int iters, status, phase, restarts, body, zero_rhs, bad_diag, err;
   int fresh_p, pad2;
   unsigned cnt[8];
