@@ -54,6 +54,8 @@ constexpr int kEigMaxB = kEigMaxK + 2;           // block with two guard vectors
 constexpr int kEigMaxM = 3 * kEigMaxB;           // 30 columns of S
 constexpr int kEigLd = kEigMaxM + 1;      // leading dimension of the small matrices
 constexpr int kEigThreads = 256;
+// The update kernel's block (one thread per row and output column)
+constexpr int kEigUpdThreads = 256;
 constexpr int kEigTile = 32;              // rows of S staged per Gram tile
 constexpr int kEigPairs = kEigMaxM * (kEigMaxM + 1) / 2;
 constexpr int kEigPollEvery = 8;
@@ -338,25 +340,6 @@ __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps
   }
 }
 
-// Y = op(X) Z for m x m shared matrices (op = transpose when tx), all
-// threads of the block: a warp per output row, a lane per column; Y must not
-// alias X or Z.
-__device__ void eig_matmul(double* Y, const double* X, const double* Z, int m, bool tx) {
-  const int j = threadIdx.x & 31;
-  if (j < m) {
-    for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5) {
-      double s = 0.0;
-      if (tx) {
-        for (int l = 0; l < m; ++l) s = fma(X[l * kEigLd + i], Z[l * kEigLd + j], s);
-      } else {
-        for (int l = 0; l < m; ++l) s = fma(X[i * kEigLd + l], Z[l * kEigLd + j], s);
-      }
-      Y[i * kEigLd + j] = s;
-    }
-  }
-  __syncthreads();
-}
-
 struct EigSmem {
   double G[kEigMaxM * kEigLd];
   double H[kEigMaxM * kEigLd];
@@ -366,8 +349,15 @@ struct EigSmem {
   double scale[kEigMaxM];
   double scale2[kEigMaxM];
   double rot[4 * (kEigMaxM / 2 + 1)];
-  float Af[kEigMaxM * kEigLd];
-  float Vf[kEigMaxM * kEigLd];
+  union {
+    struct {
+      float Af[kEigMaxM * kEigLd];
+      float Vf[kEigMaxM * kEigLd];
+    } f;                           // the FP32 Jacobi stage
+    double R[kEigMaxM * kEigLd];   // then the refinement's I - X^T X and E
+  } u;
+  double lam[kEigMaxM];
+  double nrm[2 * (kEigThreads / 32)];
   float rotf[4 * (kEigMaxM / 2 + 1)];
   int keep[kEigMaxM];
   int sel[kEigMaxM];
@@ -378,45 +368,199 @@ struct EigSmem {
   float floor_f;
 };
 
+// Y = op(X) Z + (add ? X : 0) for m x m shared matrices (op = transpose when
+// tx; add only with !tx), the m^2 outputs spread over all threads of the
+// block (one output, an m-long FMA chain, per thread at m <= 16; two at
+// m <= 22, ...); Y must not alias X or Z.
+__device__ void eig_mm(double* Y, const double* X, const double* Z, int m, bool tx, bool add = false) {
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int i = t / m, j = t - i * m;
+    double s = add ? X[i * kEigLd + j] : 0.0;
+    if (tx) {
+      for (int l = 0; l < m; ++l) s = fma(X[l * kEigLd + i], Z[l * kEigLd + j], s);
+    } else {
+      for (int l = 0; l < m; ++l) s = fma(X[i * kEigLd + l], Z[l * kEigLd + j], s);
+    }
+    Y[i * kEigLd + j] = s;
+  }
+  __syncthreads();
+}
+
+// Block totals of two values (every thread gets them).
+__device__ __forceinline__ void eig_sum2(double& a, double& b, EigSmem& sm) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sm.nrm[2 * w] = a;
+    sm.nrm[2 * w + 1] = b;
+  }
+  __syncthreads();
+  a = 0.0;
+  b = 0.0;
+  for (int k = 0; k < nw; ++k) {
+    a += sm.nrm[2 * k];
+    b += sm.nrm[2 * k + 1];
+  }
+  __syncthreads();
+}
+
+// Iterative refinement of an approximate eigendecomposition of the symmetric
+// m x m matrix A (Ogita and Aishima 2018, "Iterative refinement for
+// symmetric eigenvalue decomposition").  With X the approximate eigenvectors
+// (columns), R = I - X^T X and S = X^T A X, the exact eigenvectors are
+// X (I + E) for a small E; to first order, (I + E)^T (I - R) (I + E) = I and
+// (I + E)^T S (I + E) = D diagonal give
+//   E_ii = r_ii / 2,  d_i = s_ii / (1 - r_ii),
+//   E_ij = (s_ij + d_j r_ij) / (d_j - d_i)  (i != j),
+// and X <- X + X E squares the error of X, as long as d_i and d_j are
+// further apart than delta = 2 (||S - D|| + ||A|| ||R||) (Frobenius norms,
+// bounds of the 2-norms); for a closer pair only the orthogonality part,
+// E_ij = r_ij / 2, is applied.  A step is 3 m^3 FMAs in 3 passes, where the
+// FP64 Jacobi sweeps it replaces took m - 1 dependent rotation steps per
+// sweep, and two or three sweeps.
+// A pair that starts within delta (delta is large at the first step, ~||A||
+// times the FP32 basis's loss of orthogonality) is resolved at a later step,
+// once the other pairs' corrections have shrunk delta below its gap; each
+// step squares its error from there.  Only a pair that stays within delta
+// (a true cluster at this precision) is left coupled.
+// In: A; X in V (and Y, S, R scratch).  Out: the refined X in V and S =
+// X^T A X, with the eigenvalues on its diagonal.  True when the off-diagonal
+// of S and R reached rounding level; false when they did not within
+// kEigRefineSteps steps (the caller then finishes with Jacobi sweeps on S).
+constexpr int kEigRefineSteps = 6;
+
+// (i, j), i <= j, of entry t of the upper triangle of an m x m matrix in row
+// order (row r starts at r m - r (r - 1) / 2): the smaller root of the
+// quadratic in FP32, then an exact integer correction.
+__device__ __forceinline__ void eig_tri_index(int t, int m, int& i, int& j) {
+  const float b = 2.0f * (float)m + 1.0f;
+  int r = (int)((b - sqrtf(fmaxf(b * b - 8.0f * (float)t, 0.0f))) * 0.5f);
+  if (r < 0) r = 0;
+  while (r > 0 && r * m - r * (r - 1) / 2 > t) --r;
+  while ((r + 1) * m - (r + 1) * r / 2 <= t) ++r;
+  i = r;
+  j = t - (r * m - r * (r - 1) / 2) + r;
+}
+
+__device__ bool eig_refine(const double* A, double* V, double* Y, double* S, double* R, int m, EigSmem& sm) {
+  const int tid = threadIdx.x, nt = blockDim.x, mm = m * m;
+  double a2 = 0.0, unused = 0.0;
+  for (int t = tid; t < mm; t += nt) {
+    const int i = t / m, j = t - i * m;
+    a2 = fma(A[i * kEigLd + j], A[i * kEigLd + j], a2);
+  }
+  eig_sum2(a2, unused, sm);
+  const double anorm = sqrt(a2);
+  // rounding level of S = X^T (A X) and of I - X^T X: m-term dot products
+  // over m^2 entries, with a margin
+  const double tol = 64.0 * m * 1.1102230246251565e-16;
+  double* X = V;
+  bool done = false;
+  for (int step = 0;; ++step) {
+    eig_mm(Y, A, X, m, false);  // Y = A X
+    // S = X^T Y and R = I - X^T X in one pass over their upper triangles
+    // (both symmetric; S to rounding: its lower triangle is the mirror); d_i;
+    // the two norms
+    double off2 = 0.0, r2 = 0.0;
+    for (int t = tid; t < m * (m + 1) / 2; t += nt) {
+      int i, j;
+      eig_tri_index(t, m, i, j);
+      double sv = 0.0, g = 0.0;
+      for (int l = 0; l < m; ++l) {
+        const double xi = X[l * kEigLd + i];
+        sv = fma(xi, Y[l * kEigLd + j], sv);
+        g = fma(xi, X[l * kEigLd + j], g);
+      }
+      const double rv = (i == j ? 1.0 : 0.0) - g;
+      S[i * kEigLd + j] = sv;
+      S[j * kEigLd + i] = sv;
+      R[i * kEigLd + j] = rv;
+      R[j * kEigLd + i] = rv;
+      if (i != j) {
+        off2 = fma(2.0 * sv, sv, off2);
+        r2 = fma(2.0 * rv, rv, r2);
+      } else {
+        r2 = fma(rv, rv, r2);
+        sm.lam[i] = sv / g;
+      }
+    }
+    eig_sum2(off2, r2, sm);  // also the barrier before S, R and lam are read
+    const double off = sqrt(off2), rn = sqrt(r2);
+    if (off <= tol * anorm && rn <= tol) {
+      done = true;
+      break;
+    }
+    if (step == kEigRefineSteps) break;
+    const double delta = 2.0 * (off + anorm * rn);
+    // E in place of R
+    for (int t = tid; t < mm; t += nt) {
+      const int i = t / m, j = t - i * m;
+      const double rv = R[i * kEigLd + j];
+      double e = 0.5 * rv;
+      if (i != j) {
+        const double di = sm.lam[i], dj = sm.lam[j];
+        const double den = dj - di;
+        if (fabs(den) > delta) {
+          // 1 / den: FP32 reciprocal and one Newton-Raphson step
+          // y <- y + y (1 - den y) in FP64 (relative error ~1e-14, ample for
+          // a correction of size |E|) within FP32's range, FP64 division
+          // outside it
+          double y;
+          if (fabs(den) > 1e-30 && fabs(den) < 1e30) {
+            y = (double)__frcp_rn((float)den);
+            y = fma(y, fma(-den, y, 1.0), y);
+          } else {
+            y = 1.0 / den;
+          }
+          e = (S[i * kEigLd + j] + dj * rv) * y;
+        }
+      }
+      R[i * kEigLd + j] = e;
+    }
+    __syncthreads();
+    eig_mm(Y, X, R, m, false, true);  // X + X E
+    double* t = X;
+    X = Y;
+    Y = t;
+  }
+  if (X != V) {
+    for (int q = tid; q < m * kEigLd; q += nt) V[q] = X[q];
+    __syncthreads();
+  }
+  return done;
+}
+
 // Mixed-precision symmetric eigensolver for the Rayleigh-Ritz step: FP32
-// Jacobi sweeps (the FP32 pipe is 64 times the FP64 one) to a basis V0 that
-// nearly diagonalises A; two steps of symmetric orthogonalisation in FP64,
-// V <- V (3I - V^T V)/2, each squaring V0's loss of orthogonality (~1e-7);
-// the congruence A1 = V^T A V, nearly diagonal; FP64 Jacobi sweeps on A1,
-// which converge quadratically from there (two or three); the eigenvectors
-// V V1.  A (overwritten with its eigenvalues on the diagonal) and V as in
-// eig_jacobi; S1, S2: m x m scratch.
+// Jacobi sweeps (the FP32 pipe is 64 times the FP64 one) to eigenvectors
+// accurate to ~1e-7 ||A|| / gap, then the FP64 iterative refinement above
+// (two steps for well-separated eigenvalues, a few more for the close
+// smallest Ritz values, a last pass confirming); where it does not reach
+// rounding level (a cluster closer than its delta), FP64 Jacobi sweeps on
+// the refined S = X^T A X, which is diagonal but for that cluster, and the
+// eigenvectors X V1.  A (overwritten with its eigenvalues on
+// the diagonal) and V as in eig_jacobi; S1, S2: m x m scratch.
 __device__ void eig_eigh(double* A, double* V, int m, double* S1, double* S2, EigSmem& sm) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int q = tid; q < m * kEigLd; q += nt) sm.Af[q] = (float)A[q];
+  for (int q = tid; q < m * kEigLd; q += nt) sm.u.f.Af[q] = (float)A[q];
   __syncthreads();
-  eig_jacobi<float>(sm.Af, sm.Vf, m, 1e-7f, 1e-9f, 12, sm.rotf, &sm.any, &sm.floor_f, sm.items);
-  for (int q = tid; q < m * kEigLd; q += nt) S1[q] = (double)sm.Vf[q];
+  eig_jacobi<float>(sm.u.f.Af, sm.u.f.Vf, m, 1e-7f, 1e-9f, 12, sm.rotf, &sm.any, &sm.floor_f, sm.items);
+  for (int q = tid; q < m * kEigLd; q += nt) V[q] = (double)sm.u.f.Vf[q];
   __syncthreads();
-  for (int pass = 0; pass < 2; ++pass) {
-    eig_matmul(S2, S1, S1, m, true);  // M = V^T V
-    for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
-      for (int j = threadIdx.x & 31; j < m; j += 32) {
-      S2[i * kEigLd + j] = (i == j ? 1.5 : 0.0) - 0.5 * S2[i * kEigLd + j];
-    }
-    __syncthreads();
-    eig_matmul(V, S1, S2, m, false);  // V (3I - M) / 2
-    for (int q = tid; q < m * kEigLd; q += nt) S1[q] = V[q];
-    __syncthreads();
-  }
-  eig_matmul(S2, A, S1, m, false);  // A V
-  eig_matmul(A, S1, S2, m, true);   // V^T A V
-  for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
-    for (int j = threadIdx.x & 31; j < m; j += 32) {
-    if (i < j) {
-      const double x = 0.5 * (A[i * kEigLd + j] + A[j * kEigLd + i]);
-      A[i * kEigLd + j] = x;
-      A[j * kEigLd + i] = x;
-    }
+  const bool done = eig_refine(A, V, S1, S2, sm.u.R, m, sm);
+  // A <- S (symmetrised: the Jacobi sweeps read one triangle's pairs)
+  for (int t = tid; t < m * m; t += nt) {
+    const int i = t / m, j = t - i * m;
+    A[i * kEigLd + j] = done ? S2[i * kEigLd + j] : 0.5 * (S2[i * kEigLd + j] + S2[j * kEigLd + i]);
   }
   __syncthreads();
+  if (done) return;
   eig_jacobi<double>(A, S2, m, 1e-15, 0.0, 30, sm.rot, &sm.any, &sm.floor_d, sm.items);
-  eig_matmul(V, S1, S2, m, false);  // V0 V1
+  eig_mm(S1, V, S2, m, false);  // X V1
+  for (int q = tid; q < m * kEigLd; q += nt) V[q] = S1[q];
+  __syncthreads();
 }
 
 // Rayleigh-Ritz in one block: G, H (full, shared) -> C [m][k] and theta [k]
@@ -686,100 +830,114 @@ __global__ void __launch_bounds__(kEigThreads) eig_rr_kernel(EigPtrs P, int gb) 
 // X' = S C, AX' = AS C, P' = S[:, kb:m] C[kb:m], AP' likewise, R = AX' - X'
 // diag(theta), W' = D^{-1} R, into the other buffer pair; per-block sums of
 // ||r_i||^2 and ||x_i||^2; the last block takes the convergence decision on
-// the k wanted pairs.
-__global__ void __launch_bounds__(kEigThreads) eig_update_kernel(EigPtrs P) {
+// the kb pairs.  Tiles of RT = NT / kb rows: the tile's rows of S and AS
+// (contiguous, RT ld doubles each) are copied to shared memory with
+// coalesced loads, then thread t < RT kb computes row t / kb, output column
+// t mod kb from there (the same column in every tile, so its norms are per
+// column).  A thread per row reading its own row from global memory issued
+// 32 addresses 8 ld bytes apart per load and waited on each (61 us a launch
+// at 2D 128^2, kb = 8, against 34 us for the Gram kernel's tiles).
+template <int NT>
+__global__ void __launch_bounds__(NT) eig_update_kernel(EigPtrs P) {
   const EigDesc& d = *P.d;
   EigState* st = P.st;
   if (st->done || st->bad) return;
   __shared__ double sC[kEigMaxM * kEigMaxB];
   __shared__ double sT[kEigMaxB];
-  __shared__ double red[2 * kEigMaxB * (kEigThreads / 32)];
+  // S and AS tiles, row stride ld + 1 (odd: rows fall in different banks);
+  // RT (ld + 1) <= NT / kb (3 kb + 1) <= 4 NT doubles each
+  __shared__ double tS[4 * NT];
+  __shared__ double tA[4 * NT];
+  __shared__ double red[2 * NT];
+  __shared__ double tot_s[2 * kEigMaxB];
   __shared__ bool s_last;
   const int n = d.n, k = d.k, kb = d.kb, ld = d.ld, m = st->m, cur = st->cur;
-  const int tid = threadIdx.x;
-  for (int q = tid; q < m * kEigMaxB; q += kEigThreads) sC[q] = P.C[q];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  for (int q = tid; q < m * kEigMaxB; q += NT) sC[q] = P.C[q];
   if (tid < kb) sT[tid] = P.theta[tid];
-  __syncthreads();
   const double* S = P.S[cur];
   const double* AS = P.AS[cur];
   double* Sn = P.S[cur ^ 1];
   double* ASn = P.AS[cur ^ 1];
-  double rr[kEigMaxB], xx[kEigMaxB];
-#pragma unroll
-  for (int j = 0; j < kEigMaxB; ++j) rr[j] = xx[j] = 0.0;
-  for (int i = blockIdx.x * blockDim.x + tid; i < n; i += gridDim.x * blockDim.x) {
-    const double* s = S + (size_t)i * ld;
-    const double* as = AS + (size_t)i * ld;
-    double* sn = Sn + (size_t)i * ld;
-    double* asn = ASn + (size_t)i * ld;
-    const double di = P.dinv[i];
-    // two passes over the output columns keep the accumulators in registers
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      constexpr int kH = kEigMaxB / 2;
-      double x[kH], ax[kH], p[kH], ap[kH];
-#pragma unroll
-      for (int j = 0; j < kH; ++j) x[j] = ax[j] = p[j] = ap[j] = 0.0;
-      for (int a = 0; a < m; ++a) {
-        const double sa = s[a], asa = as[a];
-        const double* c = sC + a * kEigMaxB + h * kH;
-        if (a < kb) {
-#pragma unroll
-          for (int j = 0; j < kH; ++j) {
-            x[j] = fma(sa, c[j], x[j]);
-            ax[j] = fma(asa, c[j], ax[j]);
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < kH; ++j) {
-            p[j] = fma(sa, c[j], p[j]);
-            ap[j] = fma(asa, c[j], ap[j]);
-          }
-        }
+  const int RT = NT / kb, lp = ld + 1;
+  const bool active = tid < RT * kb;
+  const int r = tid / kb, j = tid - r * kb;
+  const int tiles = (n + RT - 1) / RT;
+  double rr = 0.0, xx = 0.0;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int r0 = tile * RT;
+    const int rows = min(RT, n - r0);
+    __syncthreads();  // the previous tile's reads are done (and sC, sT written)
+    const double* s0 = S + (size_t)r0 * ld;
+    const double* a0 = AS + (size_t)r0 * ld;
+    for (int q = tid; q < rows * ld; q += NT) {
+      const int rr_ = q / ld, cc = q - rr_ * ld;
+      tS[rr_ * lp + cc] = s0[q];
+      tA[rr_ * lp + cc] = a0[q];
+    }
+    __syncthreads();
+    if (active && r < rows) {
+      const double th = sT[j];
+      const double* ts = tS + r * lp;
+      const double* ta = tA + r * lp;
+      double x = 0.0, ax = 0.0, p = 0.0, ap = 0.0;
+      for (int a = 0; a < kb; ++a) {
+        const double c = sC[a * kEigMaxB + j];
+        x = fma(ts[a], c, x);
+        ax = fma(ta[a], c, ax);
       }
-#pragma unroll
-      for (int j = 0; j < kH; ++j) {
-        const int jj = h * kH + j;
-        if (jj < kb) {
-          const double xj = x[j] + p[j], axj = ax[j] + ap[j];
-          const double rj = axj - sT[jj] * xj;
-          sn[jj] = xj;
-          asn[jj] = axj;
-          sn[kb + jj] = di * rj;
-          sn[2 * kb + jj] = p[j];
-          asn[2 * kb + jj] = ap[j];
-          rr[jj] = fma(rj, rj, rr[jj]);
-          xx[jj] = fma(xj, xj, xx[jj]);
-        }
+      for (int a = kb; a < m; ++a) {
+        const double c = sC[a * kEigMaxB + j];
+        p = fma(ts[a], c, p);
+        ap = fma(ta[a], c, ap);
       }
+      const int i = r0 + r;
+      const double xj = x + p, axj = ax + ap;
+      const double rj = axj - th * xj;
+      double* sn = Sn + (size_t)i * ld;
+      double* asn = ASn + (size_t)i * ld;
+      sn[j] = xj;
+      asn[j] = axj;
+      sn[kb + j] = P.dinv[i] * rj;
+      sn[2 * kb + j] = p;
+      asn[2 * kb + j] = ap;
+      rr = fma(rj, rj, rr);
+      xx = fma(xj, xj, xx);
     }
   }
-  // block sums of the 2 kb values: warp shuffles, then warp totals in shared
-  const int w = tid >> 5, lane = tid & 31;
+  // block sums per column: the threads of column c (c, c + kb, ...), in order
+  red[tid] = rr;
+  red[NT + tid] = xx;
+  __syncthreads();
+  if (tid < 2 * kb) {
+    const int c = tid >> 1, which = tid & 1;
+    double sum = 0.0;
+    for (int t = c; t < RT * kb; t += kb) sum += red[which * NT + t];
+    P.upart[(size_t)blockIdx.x * 2 * kEigMaxB + tid] = sum;
+  }
+  if (!last_block_arrive(&st->ticket_upd, &s_last)) return;
+  // the blocks' partials: thread t adds blocks t, t + NT, ... in order, then
+  // a fixed butterfly over the lanes and the warps in order
+  double tot[2 * kEigMaxB];
 #pragma unroll
-  for (int j = 0; j < kEigMaxB; ++j) {
-    for (int o = 16; o > 0; o >>= 1) {
-      rr[j] += __shfl_xor_sync(0xffffffffu, rr[j], o);
-      xx[j] += __shfl_xor_sync(0xffffffffu, xx[j], o);
-    }
-    if (lane == 0) {
-      red[(2 * j) * (kEigThreads / 32) + w] = rr[j];
-      red[(2 * j + 1) * (kEigThreads / 32) + w] = xx[j];
-    }
+  for (int v = 0; v < 2 * kEigMaxB; ++v) tot[v] = 0.0;
+  for (int b = tid; b < (int)gridDim.x; b += NT) {
+    const double* pb = P.upart + (size_t)b * 2 * kEigMaxB;
+#pragma unroll
+    for (int v = 0; v < 2 * kEigMaxB; ++v)
+      if (v < 2 * kb) tot[v] += __ldcg(pb + v);
+  }
+  __syncthreads();  // red is rewritten below
+#pragma unroll
+  for (int v = 0; v < 2 * kEigMaxB; ++v) {
+    for (int o = 16; o > 0; o >>= 1) tot[v] += __shfl_xor_sync(0xffffffffu, tot[v], o);
+    if (lane == 0) red[v * (NT / 32) + w] = tot[v];
   }
   __syncthreads();
   if (tid < 2 * kb) {
     double sum = 0.0;
-    for (int q = 0; q < kEigThreads / 32; ++q) sum += red[tid * (kEigThreads / 32) + q];
-    P.upart[(size_t)blockIdx.x * 2 * kEigMaxB + tid] = sum;
-  }
-  if (!last_block_arrive(&st->ticket_upd, &s_last)) return;
-  // one thread per value adds the blocks' partials in block order
-  if (tid < 2 * kb) {
-    double sum = 0.0;
-#pragma unroll 8
-    for (int b = 0; b < (int)gridDim.x; ++b) sum += __ldcg(P.upart + (size_t)b * 2 * kEigMaxB + tid);
-    red[tid] = sum;
+    for (int q = 0; q < NT / 32; ++q) sum += red[tid * (NT / 32) + q];
+    tot_s[tid] = sum;
   }
   __syncthreads();
   if (tid == 0) {
@@ -787,7 +945,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_update_kernel(EigPtrs P) {
     bool finite = true;
     unsigned act = 0u;
     for (int j = 0; j < kb; ++j) {
-      const double r2 = red[2 * j], x2 = red[2 * j + 1];
+      const double r2 = tot_s[2 * j], x2 = tot_s[2 * j + 1];
       const double res = sqrt(r2) / (fabs(sT[j]) * sqrt(x2));
       if (!isfinite(res)) finite = false;
       if (j < k) worst = fmax(worst, res);
@@ -982,8 +1140,8 @@ __global__ void eig_grad_kernel(int n, int k, const int* __restrict__ rowptr, co
 // ---------------------------------------------------------------- host
 
 namespace {
-int eig_grid(int n, int cap) {
-  const long long b = ((long long)n + kEigThreads - 1) / kEigThreads;
+int eig_grid(int n, int cap, int threads = kEigThreads) {
+  const long long b = ((long long)n + threads - 1) / threads;
   return (int)std::max(1LL, std::min<long long>(b, cap));
 }
 }  // namespace
@@ -994,7 +1152,9 @@ int eig_block(int n, int k) { return std::min(k + 2, std::max(n, k)); }
 size_t eig_ws_bytes(int n, int k, int* gram_blocks, int* upd_blocks) {
   const size_t nn = (size_t)(n > 0 ? n : 1);
   const int gb = std::max(1, std::min((n + kEigTile - 1) / kEigTile, 296));
-  const int ub = eig_grid(n, 1024);
+  // update blocks: one tile of kEigUpdThreads / kb rows each, at most 4096
+  const long long rt = std::max(1, kEigUpdThreads / eig_block(n, k));
+  const int ub = (int)std::max(1LL, std::min<long long>(((long long)n + rt - 1) / rt, 4096));
   if (gram_blocks) *gram_blocks = gb;
   if (upd_blocks) *upd_blocks = ub;
   size_t o = 0;
@@ -1072,13 +1232,13 @@ extern "C" int32_t sla_eigsh(const sla_csr* A, const double* val, int32_t k, dou
   eig_spmm_kernel<<<eig_grid(n, 4096), kEigThreads, 0, s>>>(P, 0);
   eig_gram_kernel<<<gb, kEigThreads, 0, s>>>(P);
   eig_rr_kernel<<<kRrBlocks, kEigThreads, 0, s>>>(P, gb);
-  eig_update_kernel<<<ub, kEigThreads, 0, s>>>(P);
+  eig_update_kernel<kEigUpdThreads><<<ub, kEigUpdThreads, 0, s>>>(P);
   SLA_CUDA_TRY(cudaGetLastError());
   for (long long it = 0; it < (long long)opts->max_iter; ++it) {
     eig_spmm_kernel<<<eig_grid(n, 4096), kEigThreads, 0, s>>>(P, 1);
     eig_gram_kernel<<<gb, kEigThreads, 0, s>>>(P);
     eig_rr_kernel<<<kRrBlocks, kEigThreads, 0, s>>>(P, gb);
-    eig_update_kernel<<<ub, kEigThreads, 0, s>>>(P);
+    eig_update_kernel<kEigUpdThreads><<<ub, kEigUpdThreads, 0, s>>>(P);
     if ((it + 1) % kEigPollEvery == 0) {
       int done = 0;
       SLA_CUDA_TRY(cudaMemcpyAsync(&done, &P.st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
