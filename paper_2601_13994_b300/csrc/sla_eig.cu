@@ -852,7 +852,7 @@ __global__ void __launch_bounds__(NT) eig_update_kernel(EigPtrs P) {
   __shared__ double tot_s[2 * kEigMaxB];
   __shared__ bool s_last;
   const int n = d.n, k = d.k, kb = d.kb, ld = d.ld, m = st->m, cur = st->cur;
-  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x;
   for (int q = tid; q < m * kEigMaxB; q += NT) sC[q] = P.C[q];
   if (tid < kb) sT[tid] = P.theta[tid];
   const double* S = P.S[cur];
@@ -916,28 +916,33 @@ __global__ void __launch_bounds__(NT) eig_update_kernel(EigPtrs P) {
     P.upart[(size_t)blockIdx.x * 2 * kEigMaxB + tid] = sum;
   }
   if (!last_block_arrive(&st->ticket_upd, &s_last)) return;
-  // the blocks' partials: thread t adds blocks t, t + NT, ... in order, then
-  // a fixed butterfly over the lanes and the warps in order
-  double tot[2 * kEigMaxB];
-#pragma unroll
-  for (int v = 0; v < 2 * kEigMaxB; ++v) tot[v] = 0.0;
-  for (int b = tid; b < (int)gridDim.x; b += NT) {
-    const double* pb = P.upart + (size_t)b * 2 * kEigMaxB;
-#pragma unroll
-    for (int v = 0; v < 2 * kEigMaxB; ++v)
-      if (v < 2 * kb) tot[v] += __ldcg(pb + v);
-  }
-  __syncthreads();  // red is rewritten below
-#pragma unroll
-  for (int v = 0; v < 2 * kEigMaxB; ++v) {
-    for (int o = 16; o > 0; o >>= 1) tot[v] += __shfl_xor_sync(0xffffffffu, tot[v], o);
-    if (lane == 0) red[v * (NT / 32) + w] = tot[v];
+  // the blocks' partials, value-major: thread t < 12 * 2 kb sums value t / 12
+  // over blocks t mod 12, t mod 12 + 12, ... in order, then one thread per
+  // value adds its 12 chunk sums in order.  (A warp-wide FP64 add holds the
+  // SM's FP64 pipe for 16 cycles whatever its useful lanes, so a butterfly
+  // over lanes for each of the 2 kb values cost more than the sums
+  // themselves: 17k of the last block's 35k cycles.)
+  constexpr int kChunks = 12;
+  static_assert(kChunks * 2 * kEigMaxB <= NT, "one thread per (value, chunk)");
+  const int nv = 2 * kb;
+  if (tid < kChunks * nv) {
+    const int v = tid / kChunks, c = tid - v * kChunks;
+    double sum = 0.0;
+    for (int b = c; b < (int)gridDim.x; b += kChunks) sum += __ldcg(P.upart + (size_t)b * 2 * kEigMaxB + v);
+    red[tid] = sum;
   }
   __syncthreads();
-  if (tid < 2 * kb) {
+  if (tid < nv) {
     double sum = 0.0;
-    for (int q = 0; q < NT / 32; ++q) sum += red[tid * (NT / 32) + q];
+    for (int c = 0; c < kChunks; ++c) sum += red[tid * kChunks + c];
     tot_s[tid] = sum;
+  }
+  __syncthreads();
+  // each pair's relative residual by a thread of its own (FP64 square roots
+  // and divisions are long sequences on the FP64 pipe), then the decision
+  if (tid < kb) {
+    const double r2 = tot_s[2 * tid], x2 = tot_s[2 * tid + 1];
+    red[tid] = sqrt(r2) / (fabs(sT[tid]) * sqrt(x2));
   }
   __syncthreads();
   if (tid == 0) {
@@ -945,8 +950,7 @@ __global__ void __launch_bounds__(NT) eig_update_kernel(EigPtrs P) {
     bool finite = true;
     unsigned act = 0u;
     for (int j = 0; j < kb; ++j) {
-      const double r2 = tot_s[2 * j], x2 = tot_s[2 * j + 1];
-      const double res = sqrt(r2) / (fabs(sT[j]) * sqrt(x2));
+      const double res = red[j];
       if (!isfinite(res)) finite = false;
       if (j < k) worst = fmax(worst, res);
       if (!(res <= d.tol)) act |= 1u << j;
