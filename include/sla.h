@@ -302,6 +302,27 @@ int32_t sla_mp_dense_fwd(int32_t n, int32_t K1, const float* X1, int32_t K2,
                          const float* bias, const float* R, int32_t relu,
                          float* Ypre, float* Y, void* stream);
 
+/* The same layer with the kernel chosen: SLA_MP_DENSE_SIMT (FP32 FMAs on
+ * the CUDA cores, each output the sequential sum over k from the bias),
+ * SLA_MP_DENSE_TC (tcgen05 tensor cores: each FP32 activation split
+ * exactly into three BF16 pieces against the BF16 weights, FP32
+ * accumulation in TMEM, bias added after; requires K1, K2 multiples of 4,
+ * M a multiple of 16 up to 96 and 16-byte aligned X1, X2, R, Ypre, Y, else
+ * SLA_ERR_INVALID) or SLA_MP_DENSE_AUTO (the library's choice).  The two
+ * kernels agree to FP32 rounding (the order of the additions differs). */
+#define SLA_MP_DENSE_AUTO 0
+#define SLA_MP_DENSE_SIMT 1
+#define SLA_MP_DENSE_TC 2
+int32_t sla_mp_dense_fwd_ex(int32_t n, int32_t K1, const float* X1, int32_t K2,
+                            const float* X2, int32_t M, const void* W_bf16,
+                            const float* bias, const float* R, int32_t relu,
+                            float* Ypre, float* Y, int32_t kernel, void* stream);
+
+/* Nonzero in *out when a tensor-core dense launch's bounded mbarrier wait
+ * ran out since the last call (that launch stopped early and its outputs
+ * are incomplete); synchronous, resets the flag. */
+int32_t sla_mp_tc_errors(int32_t* out);
+
 /* dX = base + dY W[:, col0 : col0 + K] (W has wstride columns; base
  * optional [n x K]). */
 int32_t sla_mp_dense_bwdx(int32_t n, int32_t M, const float* dY, int32_t K,

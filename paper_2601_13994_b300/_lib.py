@@ -46,6 +46,9 @@ SLA_WS_LIST_TRANSPOSE = 13
 SLA_EIG_MAX_K = 8
 SLA_SPMV_ROWS = 0
 SLA_SPMV_MERGE = 1
+SLA_MP_DENSE_AUTO = 0
+SLA_MP_DENSE_SIMT = 1
+SLA_MP_DENSE_TC = 2
 SLA_MULTI_MAX_RHS = 32
 
 SLA_ADJ_CG = 0

@@ -887,15 +887,38 @@ extern "C" size_t sla_tril_pattern_ws(int32_t n) {
   return al256(sizeof(int) * ((size_t)n + 1)) + al256(sizeof(int) * (size_t)scan_tmp_ints(n + 1));
 }
 
+namespace sla {
+// sla_mp_tc.cu: the tensor-core form of the dense layer
+bool mp_dense_tc_applies(int K1, const float* X1, int K2, const float* X2, int M, const float* R,
+                         const float* Ypre, const float* Y);
+int mp_dense_fwd_tc(int n, int K1, const float* X1, int K2, const float* X2, int M, const __nv_bfloat16* W,
+                    const float* bias, const float* R, int relu, float* Ypre, float* Y, cudaStream_t s);
+}  // namespace sla
+
 extern "C" int32_t sla_mp_dense_fwd(int32_t n, int32_t K1, const float* X1, int32_t K2, const float* X2,
                                     int32_t M, const void* W_bf16, const float* bias, const float* R,
                                     int32_t relu, float* Ypre, float* Y, void* stream) {
+  return sla_mp_dense_fwd_ex(n, K1, X1, K2, X2, M, W_bf16, bias, R, relu, Ypre, Y, SLA_MP_DENSE_AUTO, stream);
+}
+
+extern "C" int32_t sla_mp_dense_fwd_ex(int32_t n, int32_t K1, const float* X1, int32_t K2, const float* X2,
+                                       int32_t M, const void* W_bf16, const float* bias, const float* R,
+                                       int32_t relu, float* Ypre, float* Y, int32_t kernel, void* stream) {
   if (n < 0 || K1 < 0 || K2 < 0 || K1 + K2 < 1 || K1 + K2 > kMaxK || M < 1 || M > kMaxM) return SLA_ERR_INVALID;
+  if (kernel != SLA_MP_DENSE_AUTO && kernel != SLA_MP_DENSE_SIMT && kernel != SLA_MP_DENSE_TC)
+    return SLA_ERR_INVALID;
+  const bool tc_ok = mp_dense_tc_applies(K1, X1, K2, X2, M, R, Ypre, Y);
+  if (kernel == SLA_MP_DENSE_TC && !tc_ok) return SLA_ERR_INVALID;
   if (n == 0) return SLA_OK;
   if (!W_bf16 || !Y || (K1 && !X1) || (K2 && !X2)) return SLA_ERR_INVALID;
   const int nm = (M + 31) / 32;
   cudaStream_t s = (cudaStream_t)stream;
   const __nv_bfloat16* Wb = (const __nv_bfloat16*)W_bf16;
+  // automatic: the tensor cores wherever their form applies (2.1 M rows,
+  // B300: K = 64 -> 32 outputs 458 -> 286 us, K = 32 -> 96 outputs 571 ->
+  // 344 us); the CUDA cores for the rest (the 3-feature input layer)
+  if (kernel == SLA_MP_DENSE_TC || (kernel == SLA_MP_DENSE_AUTO && tc_ok))
+    return mp_dense_fwd_tc(n, K1, X1, K2, X2, M, Wb, bias, R, relu, Ypre, Y, s);
   if (nm == 1) {
     // register-tiled form for 32 outputs: 2.1 M rows, K = 64, 483 -> 374 us
     // (B300); for the 96-wide head it measured slower (584 vs 521 us: 116

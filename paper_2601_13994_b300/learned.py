@@ -66,6 +66,8 @@ def _bind():
         "sla_tril_pattern": ([CSR, P, P, P, P, P, sz, P], i32),
         "sla_tril_pattern_ws": ([i32], sz),
         "sla_mp_dense_fwd": ([i32, i32, P, i32, P, i32, P, P, P, i32, P, P, P], i32),
+        "sla_mp_dense_fwd_ex": ([i32, i32, P, i32, P, i32, P, P, P, i32, P, P, i32, P], i32),
+        "sla_mp_tc_errors": ([P], i32),
         "sla_mp_dense_bwdx": ([i32, i32, P, i32, P, i32, i32, P, P, P], i32),
         "sla_mp_dense_bwdw": ([i32, i32, P, i32, P, i32, P, P, P, P, sz, P], i32),
         "sla_mp_dense_bwdw_ws": ([i32, i32], sz),

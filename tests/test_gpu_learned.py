@@ -201,3 +201,69 @@ def test_trained_factor_on_unseen_1024_system():
     r = bt - sla.spmv(A, vt, xg)
     assert float(r.norm() / bt.norm()) <= 2e-8
     assert rel(xg.cpu().numpy(), xj.cpu().numpy()) <= 1e-5
+
+
+@pytest.mark.parametrize("n,K1,K2,M,relu,res,pre", [
+    (300, 32, 32, 32, 1, 1, 1),     # a message-passing layer: [H | Agg] W^T, relu, residual (3 tiles, ragged)
+    (129, 32, 0, 96, 0, 0, 0),      # the head's [P | Q | R] = H Uh^T + bh (a 1-row tail tile)
+    (70000, 32, 32, 32, 1, 1, 0),   # many tiles per CTA
+    (77, 4, 0, 16, 1, 0, 1),        # K padded to 16, M = 16, one partial tile
+])
+def test_dense_layer_tensor_cores_match_definition(n, K1, K2, M, relu, res, pre):
+    """The dense layer on the tcgen05 tensor cores (FP32 activations split
+    into three BF16 pieces, BF16 weights, FP32 accumulation in TMEM) against
+    its definition Y = relu([X1 | X2] W^T + b) + R in FP64 and against the
+    CUDA-core kernel, element by element."""
+    import ctypes
+    lib = LP._bind()
+    g = np.random.default_rng(n + M)
+    X1 = g.standard_normal((n, K1)).astype(np.float32)
+    X2 = g.standard_normal((n, K2)).astype(np.float32) if K2 else None
+    W = torch.from_numpy(0.2 * g.standard_normal((M, K1 + K2))).to(torch.bfloat16)
+    b = g.standard_normal(M).astype(np.float32)
+    R = g.standard_normal((n, M)).astype(np.float32) if res else None
+    Xc = np.concatenate([X1, X2], 1) if K2 else X1
+    ypre = Xc.astype(np.float64) @ W.double().numpy().T + b
+    y = (np.maximum(ypre, 0.0) if relu else ypre) + (R if res else 0.0)
+    out = {}
+    dev = {k: (torch.from_numpy(a).cuda() if a is not None else None) for k, a in
+           (("X1", X1), ("X2", X2), ("b", b), ("R", R))}
+    Wd = W.cuda()
+    for kern in (LP.L.SLA_MP_DENSE_SIMT, LP.L.SLA_MP_DENSE_TC):
+        Y = torch.full((n, M), float("nan"), device="cuda")
+        Yp = torch.full((n, M), float("nan"), device="cuda") if pre else None
+        ptr = lambda t: t.data_ptr() if t is not None else None
+        rc = lib.sla_mp_dense_fwd_ex(n, K1, ptr(dev["X1"]), K2, ptr(dev["X2"]), M, Wd.data_ptr(), ptr(dev["b"]),
+                                     ptr(dev["R"]), relu, ptr(Yp), Y.data_ptr(), kern, None)
+        torch.cuda.synchronize()
+        assert rc == 0, (kern, rc)
+        out[kern] = (Y.cpu().double().numpy(), Yp.cpu().double().numpy() if pre else None)
+    flag = ctypes.c_int32(-1)
+    assert lib.sla_mp_tc_errors(ctypes.byref(flag)) == 0 and flag.value == 0
+    scale = np.abs(y).max()
+    for kern, (Y, Yp) in out.items():
+        assert np.abs(Y - y).max() <= 1e-6 * scale, (kern, np.abs(Y - y).max() / scale)
+        if pre:
+            assert np.abs(Yp - ypre).max() <= 1e-6 * np.abs(ypre).max()
+    ts, tt = out[LP.L.SLA_MP_DENSE_SIMT][0], out[LP.L.SLA_MP_DENSE_TC][0]
+    assert np.abs(ts - tt).max() <= 1e-6 * scale
+
+
+def test_dense_layer_tensor_core_shape_rules():
+    """The tensor-core form takes K1, K2 multiples of 4 and M a multiple of
+    16 (up to 96); other shapes are refused for it and run on the CUDA cores
+    under automatic selection (the 3-feature input layer)."""
+    lib = LP._bind()
+    n = 40
+    X = torch.randn(n, 3, device="cuda")
+    W = torch.randn(32, 3, device="cuda").to(torch.bfloat16)
+    Y = torch.empty(n, 32, device="cuda")
+    assert lib.sla_mp_dense_fwd_ex(n, 3, X.data_ptr(), 0, None, 32, W.data_ptr(), None, None, 1, None,
+                                   Y.data_ptr(), LP.L.SLA_MP_DENSE_TC, None) == LP.L.SLA_ERR_INVALID
+    assert lib.sla_mp_dense_fwd_ex(n, 3, X.data_ptr(), 0, None, 32, W.data_ptr(), None, None, 1, None,
+                                   Y.data_ptr(), LP.L.SLA_MP_DENSE_AUTO, None) == 0
+    torch.cuda.synchronize()
+    ref = torch.relu(X.double() @ W.double().t())
+    assert float((Y.double() - ref).abs().max()) <= 1e-6 * float(ref.abs().max())
+    assert lib.sla_mp_dense_fwd_ex(n, 3, X.data_ptr(), 0, None, 32, W.data_ptr(), None, None, 1, None,
+                                   Y.data_ptr(), 7, None) == LP.L.SLA_ERR_INVALID
