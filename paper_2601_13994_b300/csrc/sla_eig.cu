@@ -43,6 +43,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cooperative_groups.h>
 
 #include "sla_internal.cuh"
 #include "sla_workspace.h"
@@ -59,7 +60,17 @@ constexpr int kEigUpdThreads = 256;
 constexpr int kEigTile = 32;              // rows of S staged per Gram tile
 constexpr int kEigPairs = kEigMaxM * (kEigMaxM + 1) / 2;
 constexpr int kEigPollEvery = 8;
-constexpr int kRrBlocks = (2 * kEigPairs + 31) / 32;  // blocks of the Gram totals
+// The Rayleigh-Ritz step runs on one thread-block cluster of kRrCluster
+// CTAs (one SM each): every CTA holds the small matrices in its own shared
+// memory and repeats the sequential parts (Cholesky, the FP32 Jacobi sweeps),
+// whose results are bit-identical in every CTA since they are the same
+// operations on the same data; the dense m x m products -- FP64-bound on one
+// SM, whose FP64 pipe retires two lane operations per clock -- are split by
+// columns (CTA c owns the columns j with j mod kRrCluster = c) and the owned
+// columns are written to every CTA's copy through distributed shared memory.
+constexpr int kRrCluster = 8;
+// blocks of the Gram totals (32 values each), a whole number of clusters
+constexpr int kRrBlocks = ((2 * kEigPairs + 31) / 32 + kRrCluster - 1) / kRrCluster * kRrCluster;
 
 struct EigDesc {
   int n, nnz, k, kb, ld, max_iter, precond, use_x0;
@@ -357,6 +368,7 @@ struct EigSmem {
     double R[kEigMaxM * kEigLd];   // then the refinement's I - X^T X and E
   } u;
   double lam[kEigMaxM];
+  double xpart[2 * kRrCluster];  // every CTA's parts of the refinement's two norms
   double nrm[2 * (kEigThreads / 32)];
   float rotf[4 * (kEigMaxM / 2 + 1)];
   int keep[kEigMaxM];
@@ -367,6 +379,19 @@ struct EigSmem {
   double floor_d;
   float floor_f;
 };
+
+// Cluster barrier of the Rayleigh-Ritz CTAs (every thread of every CTA
+// calls it; it also orders their shared-memory writes, local and remote).
+__device__ __forceinline__ void rr_sync() { cooperative_groups::this_cluster().sync(); }
+// The same shared-memory object in CTA `rank` of the cluster.
+template <class T>
+__device__ __forceinline__ T* rr_peer(T* p, int rank) {
+  return cooperative_groups::this_cluster().map_shared_rank(p, rank);
+}
+// Columns of an ncols-wide matrix owned by CTA `rank`: rank, rank + kRrCluster, ...
+__device__ __forceinline__ int rr_owned(int ncols, int rank) {
+  return ncols > rank ? (ncols - rank + kRrCluster - 1) / kRrCluster : 0;
+}
 
 // Y = op(X) Z + (add ? X : 0) for m x m shared matrices (op = transpose when
 // tx; add only with !tx), the m^2 outputs spread over all threads of the
@@ -445,7 +470,8 @@ __device__ __forceinline__ void eig_tri_index(int t, int m, int& i, int& j) {
   j = t - (r * m - r * (r - 1) / 2) + r;
 }
 
-__device__ bool eig_refine(const double* A, double* V, double* Y, double* S, double* R, int m, EigSmem& sm) {
+__device__ bool eig_refine(const double* A, double* V, double* Y, double* S, double* R, int m, EigSmem& sm,
+                           int rank) {
   const int tid = threadIdx.x, nt = blockDim.x, mm = m * m;
   double a2 = 0.0, unused = 0.0;
   for (int t = tid; t < mm; t += nt) {
@@ -457,17 +483,26 @@ __device__ bool eig_refine(const double* A, double* V, double* Y, double* S, dou
   // rounding level of S = X^T (A X) and of I - X^T X: m-term dot products
   // over m^2 entries, with a margin
   const double tol = 64.0 * m * 1.1102230246251565e-16;
-  double* X = V;
+  // this CTA's columns j = rank + kRrCluster jj, jj < nown; item t of a
+  // column phase is (row t / nown, column jj = t mod nown)
+  const int nown = rr_owned(m, rank);
+  double* X = V;  // every CTA holds all of X
   bool done = false;
   for (int step = 0;; ++step) {
-    eig_mm(Y, A, X, m, false);  // Y = A X
-    // S = X^T Y and R = I - X^T X in one pass over their upper triangles
-    // (both symmetric; S to rounding: its lower triangle is the mirror); d_i;
-    // the two norms
+    // Y = A X, the owned columns
+    for (int t = tid; t < m * nown; t += nt) {
+      const int i = t / nown, j = rank + kRrCluster * (t - (t / nown) * nown);
+      double s = 0.0;
+      for (int l = 0; l < m; ++l) s = fma(A[i * kEigLd + l], X[l * kEigLd + j], s);
+      Y[i * kEigLd + j] = s;
+    }
+    __syncthreads();
+    // S = X^T Y and R = I - X^T X, the owned columns; d_i of the owned
+    // diagonal entries; this CTA's parts of the two norms.  (S_ij and S_ji
+    // are two roundings of x_i^T A x_j; R is symmetric bit for bit.)
     double off2 = 0.0, r2 = 0.0;
-    for (int t = tid; t < m * (m + 1) / 2; t += nt) {
-      int i, j;
-      eig_tri_index(t, m, i, j);
+    for (int t = tid; t < m * nown; t += nt) {
+      const int i = t / nown, j = rank + kRrCluster * (t - (t / nown) * nown);
       double sv = 0.0, g = 0.0;
       for (int l = 0; l < m; ++l) {
         const double xi = X[l * kEigLd + i];
@@ -476,18 +511,31 @@ __device__ bool eig_refine(const double* A, double* V, double* Y, double* S, dou
       }
       const double rv = (i == j ? 1.0 : 0.0) - g;
       S[i * kEigLd + j] = sv;
-      S[j * kEigLd + i] = sv;
       R[i * kEigLd + j] = rv;
-      R[j * kEigLd + i] = rv;
-      if (i != j) {
-        off2 = fma(2.0 * sv, sv, off2);
-        r2 = fma(2.0 * rv, rv, r2);
+      r2 = fma(rv, rv, r2);
+      if (i != j) off2 = fma(sv, sv, off2);
+      else sm.lam[i] = sv / g;
+    }
+    eig_sum2(off2, r2, sm);
+    // every CTA gets the owned d_i and the two parts of every CTA
+    for (int t = tid; t < kRrCluster * (nown + 1); t += nt) {
+      const int dst = t / (nown + 1), q = t - dst * (nown + 1);
+      if (q < nown) {
+        const int j = rank + kRrCluster * q;
+        rr_peer(sm.lam, dst)[j] = sm.lam[j];
       } else {
-        r2 = fma(rv, rv, r2);
-        sm.lam[i] = sv / g;
+        double* xp = rr_peer(sm.xpart, dst);
+        xp[2 * rank] = off2;
+        xp[2 * rank + 1] = r2;
       }
     }
-    eig_sum2(off2, r2, sm);  // also the barrier before S, R and lam are read
+    rr_sync();
+    off2 = 0.0;
+    r2 = 0.0;
+    for (int c = 0; c < kRrCluster; ++c) {  // the same order in every CTA
+      off2 += sm.xpart[2 * c];
+      r2 += sm.xpart[2 * c + 1];
+    }
     const double off = sqrt(off2), rn = sqrt(r2);
     if (off <= tol * anorm && rn <= tol) {
       done = true;
@@ -495,9 +543,9 @@ __device__ bool eig_refine(const double* A, double* V, double* Y, double* S, dou
     }
     if (step == kEigRefineSteps) break;
     const double delta = 2.0 * (off + anorm * rn);
-    // E in place of R
-    for (int t = tid; t < mm; t += nt) {
-      const int i = t / m, j = t - i * m;
+    // E in place of R, the owned columns
+    for (int t = tid; t < m * nown; t += nt) {
+      const int i = t / nown, j = rank + kRrCluster * (t - (t / nown) * nown);
       const double rv = R[i * kEigLd + j];
       double e = 0.5 * rv;
       if (i != j) {
@@ -521,11 +569,27 @@ __device__ bool eig_refine(const double* A, double* V, double* Y, double* S, dou
       R[i * kEigLd + j] = e;
     }
     __syncthreads();
-    eig_mm(Y, X, R, m, false, true);  // X + X E
+    // X + X E, the owned columns, into every CTA's Y (no CTA reads Y again
+    // in this step; every CTA still reads its X here)
+    for (int t = tid; t < m * nown; t += nt) {
+      const int i = t / nown, j = rank + kRrCluster * (t - (t / nown) * nown);
+      double s = X[i * kEigLd + j];
+      for (int l = 0; l < m; ++l) s = fma(X[i * kEigLd + l], R[l * kEigLd + j], s);
+      for (int dst = 0; dst < kRrCluster; ++dst) rr_peer(Y, dst)[i * kEigLd + j] = s;
+    }
+    rr_sync();
     double* t = X;
     X = Y;
     Y = t;
   }
+  // all of S in every CTA
+  for (int t = tid; t < m * nown; t += nt) {
+    const int i = t / nown, j = rank + kRrCluster * (t - (t / nown) * nown);
+    const double v = S[i * kEigLd + j];
+    for (int dst = 0; dst < kRrCluster; ++dst)
+      if (dst != rank) rr_peer(S, dst)[i * kEigLd + j] = v;
+  }
+  rr_sync();
   if (X != V) {
     for (int q = tid; q < m * kEigLd; q += nt) V[q] = X[q];
     __syncthreads();
@@ -542,18 +606,19 @@ __device__ bool eig_refine(const double* A, double* V, double* Y, double* S, dou
 // the refined S = X^T A X, which is diagonal but for that cluster, and the
 // eigenvectors X V1.  A (overwritten with its eigenvalues on
 // the diagonal) and V as in eig_jacobi; S1, S2: m x m scratch.
-__device__ void eig_eigh(double* A, double* V, int m, double* S1, double* S2, EigSmem& sm) {
+__device__ void eig_eigh(double* A, double* V, int m, double* S1, double* S2, EigSmem& sm, int rank) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int q = tid; q < m * kEigLd; q += nt) sm.u.f.Af[q] = (float)A[q];
   __syncthreads();
   eig_jacobi<float>(sm.u.f.Af, sm.u.f.Vf, m, 1e-7f, 1e-9f, 12, sm.rotf, &sm.any, &sm.floor_f, sm.items);
   for (int q = tid; q < m * kEigLd; q += nt) V[q] = (double)sm.u.f.Vf[q];
   __syncthreads();
-  const bool done = eig_refine(A, V, S1, S2, sm.u.R, m, sm);
-  // A <- S (symmetrised: the Jacobi sweeps read one triangle's pairs)
+  const bool done = eig_refine(A, V, S1, S2, sm.u.R, m, sm, rank);
+  // A <- S symmetrised (S_ij and S_ji are two roundings of the same product;
+  // the Jacobi sweeps read one triangle's pairs)
   for (int t = tid; t < m * m; t += nt) {
     const int i = t / m, j = t - i * m;
-    A[i * kEigLd + j] = done ? S2[i * kEigLd + j] : 0.5 * (S2[i * kEigLd + j] + S2[j * kEigLd + i]);
+    A[i * kEigLd + j] = 0.5 * (S2[i * kEigLd + j] + S2[j * kEigLd + i]);
   }
   __syncthreads();
   if (done) return;
@@ -566,7 +631,7 @@ __device__ void eig_eigh(double* A, double* V, int m, double* S1, double* S2, Ei
 // Rayleigh-Ritz in one block: G, H (full, shared) -> C [m][k] and theta [k]
 // (k = the block size kb)
 // in global memory; returns the number of kept directions.
-__device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* theta) {
+__device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* theta, int rank) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int j = tid; j < m; j += nt) {
     const double g = sm.G[j * kEigLd + j];
@@ -640,7 +705,7 @@ __device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* t
     __syncthreads();
     r = ma;
   } else {
-    eig_eigh(sm.G, sm.U, m, sm.B, sm.T, sm);  // scaled G = U diag(g) U^T
+    eig_eigh(sm.G, sm.U, m, sm.B, sm.T, sm, rank);  // scaled G = U diag(g) U^T
     if (tid == 0) {
       double gmax = 0.0;
       for (int j = 0; j < m; ++j) gmax = fmax(gmax, sm.G[j * kEigLd + j]);
@@ -659,21 +724,26 @@ __device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* t
       }
     __syncthreads();
   }
-  // T = H B (m x r), then H2 = B^T T (r x r) into G
-  for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
-    for (int j = threadIdx.x & 31; j < r; j += 32) {
-    double s = 0.0;
-    for (int l = 0; l < m; ++l) s = fma(sm.H[i * kEigLd + l], sm.B[l * kEigLd + j], s);
-    sm.T[i * kEigLd + j] = s;
+  // T = H B (m x r), then H2 = B^T T (r x r) into G: the owned columns of
+  // T, then the owned columns of H2 into every CTA's G (after a cluster
+  // barrier: until then a CTA may still read its G to build B)
+  {
+    const int nown = rr_owned(r, rank);
+    for (int t = tid; t < m * nown; t += nt) {
+      const int i = t / nown, j = rank + kRrCluster * (t - (t / nown) * nown);
+      double s = 0.0;
+      for (int l = 0; l < m; ++l) s = fma(sm.H[i * kEigLd + l], sm.B[l * kEigLd + j], s);
+      sm.T[i * kEigLd + j] = s;
+    }
+    rr_sync();
+    for (int t = tid; t < r * nown; t += nt) {
+      const int i = t / nown, j = rank + kRrCluster * (t - (t / nown) * nown);
+      double s = 0.0;
+      for (int l = 0; l < m; ++l) s = fma(sm.B[l * kEigLd + i], sm.T[l * kEigLd + j], s);
+      for (int dst = 0; dst < kRrCluster; ++dst) rr_peer(sm.G, dst)[i * kEigLd + j] = s;
+    }
+    rr_sync();
   }
-  __syncthreads();
-  for (int i = threadIdx.x >> 5; i < r; i += blockDim.x >> 5)
-    for (int j = threadIdx.x & 31; j < r; j += 32) {
-    double s = 0.0;
-    for (int l = 0; l < m; ++l) s = fma(sm.B[l * kEigLd + i], sm.T[l * kEigLd + j], s);
-    sm.G[i * kEigLd + j] = s;
-  }
-  __syncthreads();
   // symmetrise (rounding), then H2 = Y diag(theta) Y^T with Y in U
   for (int i = threadIdx.x >> 5; i < r; i += blockDim.x >> 5)
     for (int j = threadIdx.x & 31; j < r; j += 32) {
@@ -684,7 +754,7 @@ __device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* t
     }
   }
   __syncthreads();
-  eig_eigh(sm.G, sm.U, r, sm.H, sm.T, sm);
+  eig_eigh(sm.G, sm.U, r, sm.H, sm.T, sm, rank);
   // the k smallest Ritz values, ascending (selection by rank, ties by
   // index; thread i ranks value i)
   for (int i = tid; i < r; i += nt) {
@@ -698,9 +768,10 @@ __device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* t
   }
   __syncthreads();
   const int kk = r < k ? r : k;
-  for (int j = tid; j < kk; j += nt) theta[j] = sm.G[sm.sel[j] * kEigLd + sm.sel[j]];
-  // C = diag(scale) B Y[:, sel]  (m x k)
-  for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
+  if (rank == 0)
+    for (int j = tid; j < kk; j += nt) theta[j] = sm.G[sm.sel[j] * kEigLd + sm.sel[j]];
+  // C = diag(scale) B Y[:, sel]  (m x k); CTA c writes the rows i = c mod kRrCluster
+  for (int i = rank + kRrCluster * (threadIdx.x >> 5); i < m; i += kRrCluster * (blockDim.x >> 5))
     for (int j = threadIdx.x & 31; j < kk; j += 32) {
     const int c = sm.sel[j];
     double s = 0.0;
@@ -774,11 +845,11 @@ __global__ void __launch_bounds__(kEigThreads) eig_gram_kernel(EigPtrs P) {
 }
 
 // Totals of the Gram partials of the gb blocks -- 2 npairs values -- then
-// the Rayleigh-Ritz step in the last block to arrive.  Block c adds values
+// the Rayleigh-Ritz step in the last cluster to arrive (all of its CTAs).  Block c adds values
 // 32c .. 32c + 31: a warp per 4 values, lane l summing blocks l, l + 32, ...,
 // then a fixed butterfly (the same bits run to run; spread over blocks so
 // that the loads are not serialised in one block).
-__global__ void __launch_bounds__(kEigThreads) eig_rr_kernel(EigPtrs P, int gb) {
+__global__ void __cluster_dims__(kRrCluster, 1, 1) __launch_bounds__(kEigThreads, 1) eig_rr_kernel(EigPtrs P, int gb) {
   const EigDesc& d = *P.d;
   EigState* st = P.st;
   if (st->done || st->bad) return;
@@ -796,7 +867,28 @@ __global__ void __launch_bounds__(kEigThreads) eig_rr_kernel(EigPtrs P, int gb) 
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) P.gtot[v] = s;
   }
-  if (!last_block_arrive(&st->ticket_gram, &s_last)) return;
+  // cluster arrival: every CTA's totals are written and fenced before the
+  // barrier; CTA 0 of each cluster then takes a ticket, and the cluster
+  // whose ticket is the last one runs the Rayleigh-Ritz step.  The flag is
+  // written into every CTA's own shared memory, so no CTA reads another's
+  // after the barrier (the other clusters leave at once).
+  const int rank = (int)cooperative_groups::this_cluster().block_rank();
+  __syncthreads();
+  if (tid == 0) __threadfence();
+  rr_sync();
+  if (rank == 0 && tid == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(&st->ticket_gram, 1u);
+    const bool last = t == gridDim.x / kRrCluster - 1;
+    if (last) {
+      __threadfence();
+      st->ticket_gram = 0u;
+    }
+    for (int dst = 0; dst < kRrCluster; ++dst) *rr_peer(&s_last, dst) = last;
+  }
+  rr_sync();
+  if (!s_last) return;
+  __threadfence();
   const unsigned active = st->active;
   // the full symmetric G and H; the W and P columns of converged pairs are
   // zeroed (soft locking)
@@ -817,8 +909,8 @@ __global__ void __launch_bounds__(kEigThreads) eig_rr_kernel(EigPtrs P, int gb) 
     sm.H[b * kEigLd + a] = sh;
   }
   __syncthreads();
-  const int r = eig_rayleigh_ritz(sm, m, kb, P.C, P.theta);
-  if (tid == 0) {
+  const int r = eig_rayleigh_ritz(sm, m, kb, P.C, P.theta, rank);
+  if (rank == 0 && tid == 0) {
     st->rank = r;
     if (r < kb) {
       st->status = SLA_BREAKDOWN;
