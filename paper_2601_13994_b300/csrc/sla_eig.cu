@@ -628,6 +628,24 @@ __device__ void eig_eigh(double* A, double* V, int m, double* S1, double* S2, Ei
   __syncthreads();
 }
 
+// Pivot j of the Cholesky factor of the scaled Gram matrix (in sm.U), by
+// one thread: sets sm.any when the pivot is not above 1e-10, stores L_jj in
+// the diagonal and 1 / L_jj in sm.scale2[j].
+constexpr int kEigCholItems = (kEigMaxM * (kEigMaxM + 1) / 2 + kEigThreads - 1) / kEigThreads;
+
+__device__ __forceinline__ void eig_chol_pivot(EigSmem& sm, int j) {
+  const double piv = sm.U[j * kEigLd + j];
+  if (!(piv > 1e-10)) sm.any = 1;
+  // 1/sqrt(piv): FP32 estimate, two Newton steps in FP64 (piv in
+  // (1e-10, 1] here: the scaled Gram matrix has a unit diagonal)
+  const double pv = fmax(piv, 1e-300);
+  double y = (double)rsqrtf((float)pv);
+  y = y * (1.5 - 0.5 * pv * y * y);
+  y = y * (1.5 - 0.5 * pv * y * y);
+  sm.U[j * kEigLd + j] = pv * y;
+  sm.scale2[j] = y;
+}
+
 // Rayleigh-Ritz in one block: G, H (full, shared) -> C [m][k] and theta [k]
 // (k = the block size kb)
 // in global memory; returns the number of kept directions.
@@ -662,40 +680,64 @@ __device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* t
   for (int i = threadIdx.x >> 5; i < ma; i += blockDim.x >> 5)
     for (int j = threadIdx.x & 31; j < ma; j += 32) sm.U[i * kEigLd + j] = sm.G[sm.keep[i] * kEigLd + sm.keep[j]];
   __syncthreads();
+  // Right-looking, two block barriers a column: column j of L is scaled, then
+  // the trailing update runs, in which thread 0 -- the updater of entry
+  // (j + 1, j + 1) -- also takes pivot j + 1 (the same operations in the
+  // same order as a pivot step of its own, one barrier fewer).
+  if (tid == 0 && ma > 0) eig_chol_pivot(sm, 0);
+  __syncthreads();
   for (int j = 0; j < ma; ++j) {
-    if (tid == 0) {
-      const double piv = sm.U[j * kEigLd + j];
-      if (!(piv > 1e-10)) sm.any = 1;
-      // 1/sqrt(piv): FP32 estimate, two Newton steps in FP64 (piv in
-      // (1e-10, 1] here: the scaled Gram matrix has a unit diagonal)
-      const double pv = fmax(piv, 1e-300);
-      double y = (double)rsqrtf((float)pv);
-      y = y * (1.5 - 0.5 * pv * y * y);
-      y = y * (1.5 - 0.5 * pv * y * y);
-      sm.U[j * kEigLd + j] = pv * y;
-      sm.scale2[j] = y;
-    }
-    __syncthreads();
     if (sm.any) break;
     for (int i = j + 1 + tid; i < ma; i += nt) sm.U[i * kEigLd + j] *= sm.scale2[j];
     __syncthreads();
     for (int i = j + 1 + (threadIdx.x >> 5); i < ma; i += blockDim.x >> 5)
-      for (int c = j + 1 + (threadIdx.x & 31); c <= i; c += 32)
+      for (int c = j + 1 + (threadIdx.x & 31); c <= i; c += 32) {
         sm.U[i * kEigLd + c] = fma(-sm.U[i * kEigLd + j], sm.U[c * kEigLd + j], sm.U[i * kEigLd + c]);
+        if (c == j + 1 && i == j + 1) eig_chol_pivot(sm, j + 1);
+      }
     __syncthreads();
   }
   int r;
   if (!sm.any) {
-    // column c of L^{-1} by forward substitution (thread c), into T
-    for (int c = tid; c < ma; c += nt) {
-      for (int i = 0; i < c; ++i) sm.T[i * kEigLd + c] = 0.0;
-      for (int i = c; i < ma; ++i) {
-        double acc = (i == c) ? 1.0 : 0.0;
-        for (int l = c; l < i; ++l) acc = fma(-sm.U[i * kEigLd + l], sm.T[l * kEigLd + c], acc);
-        sm.T[i * kEigLd + c] = acc * sm.scale2[i];
+    // T = L^{-1} by right-looking substitution: entry (i, c), i >= c, of the
+    // packed lower triangle is owned by one thread (at most
+    // kEigCholItems), which keeps its running value a_ic = delta_ic -
+    // sum_{l < done} L_il T_lc in a register; at step l every owner with
+    // i > l subtracts L_il T_lc (the same FMAs in the same order as the
+    // row-by-row substitution), and the owners of row l + 1, now complete,
+    // publish T_{l+1,c} = a / L_{l+1,l+1}: one block barrier a row
+    // (forward substitution by one thread per column ran chains of m^2 / 2
+    // dependent FMAs).
+    int ei[kEigCholItems], ec[kEigCholItems];
+    double ea[kEigCholItems];
+#pragma unroll
+    for (int h = 0; h < kEigCholItems; ++h) {
+      const int e = tid + h * nt;
+      ei[h] = -1;
+      ec[h] = 0;
+      ea[h] = 0.0;
+      if (e < ma * (ma + 1) / 2) {
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= e) ++i;
+        ei[h] = i;
+        ec[h] = e - i * (i + 1) / 2;
+        ea[h] = ei[h] == ec[h] ? 1.0 : 0.0;
+        if (i == 0) sm.T[0] = ea[h] * sm.scale2[0];
       }
     }
+    for (int q = tid; q < ma * ma; q += nt) {  // the strict upper triangle is zero
+      const int i = q / ma, c = q - i * ma;
+      if (c > i) sm.T[i * kEigLd + c] = 0.0;
+    }
     __syncthreads();
+    for (int l = 0; l + 1 < ma; ++l) {
+#pragma unroll
+      for (int h = 0; h < kEigCholItems; ++h) {
+        if (ei[h] > l && ec[h] <= l) ea[h] = fma(-sm.U[ei[h] * kEigLd + l], sm.T[l * kEigLd + ec[h]], ea[h]);
+        if (ei[h] == l + 1) sm.T[ei[h] * kEigLd + ec[h]] = ea[h] * sm.scale2[ei[h]];
+      }
+      __syncthreads();
+    }
     // B[keep[a]][b] = (L^{-1})[b][a]; zero rows for the locked columns
     for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
       for (int j = threadIdx.x & 31; j < ma; j += 32) sm.B[i * kEigLd + j] = 0.0;
