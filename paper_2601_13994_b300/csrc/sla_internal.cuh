@@ -162,15 +162,30 @@ __device__ __forceinline__ bool grid_sync(GridSync& g, unsigned members, int* er
 }
 
 // Fixed-order sums of NV partial arrays part[j*stride + 0..m) by one block
-// (strided per thread, then block_sums).
+// (strided per thread, then block_sums).  The loads of four strides of every
+// array are issued before their adds (this runs in the last block of a
+// kernel, on the critical path between kernels: one L2 round trip per four
+// strides instead of one per value); the adds keep the strided order.
 template <int NT, int NV, int M>
 __device__ __forceinline__ void reduce_partials(const double* part, int stride, int m,
                                                 double (&out)[NV], double (&sh)[M]) {
+  constexpr int kU = 4;
 #pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < m; i += NT) s += __ldcg(part + j * stride + i);
-    out[j] = s;
+  for (int j = 0; j < NV; ++j) out[j] = 0.0;
+  for (int i0 = threadIdx.x; i0 < m; i0 += kU * NT) {
+    double v[NV][kU];
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int i = i0 + u * NT;
+        v[j][u] = i < m ? __ldcg(part + j * stride + i) : 0.0;
+      }
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (i0 + u * NT < m) out[j] += v[j][u];
   }
   block_sums<NT, NV>(out, sh);
 }
