@@ -163,6 +163,18 @@ const char* sla_status_string(int32_t code);
 int32_t sla_selftest_grid_barrier(int32_t blocks, int32_t absent, int64_t budget_cycles,
                                   int32_t rounds, int32_t* word, void* stream);
 
+/* FP64 FMA throughput probe (no counterpart in the paper: the measured
+ * denominator of the FP64 fractions that the solvers report, since the FP64
+ * pipe is a co-limit of every Krylov kernel on this part).  Launches
+ * blocks_per_sm x (SM count) blocks of 256 threads, each thread running 8
+ * independent FMA chains of `iters` steps; *flops (host) receives the
+ * floating-point operations enqueued (2 per FMA).  out: DEVICE double[1],
+ * written only in a case that cannot occur (it keeps the work from being
+ * dropped).  The caller times the launch on `stream` (CUDA events).  Returns
+ * SLA_ERR_INVALID (nothing enqueued) for iters < 1, blocks_per_sm outside
+ * [1, 64] or a null pointer.  Asynchronous. */
+int32_t sla_fp64_probe(int32_t iters, int32_t blocks_per_sm, double* out, int64_t* flops, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Workspace size query                                                 */
 /* ------------------------------------------------------------------ */

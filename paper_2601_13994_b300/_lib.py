@@ -191,6 +191,8 @@ def lib() -> ctypes.CDLL:
             L.sla_cg_noalloc.restype = i32
             L.sla_selftest_grid_barrier.argtypes = [i32, i32, ctypes.c_int64, i32, P, P]
             L.sla_selftest_grid_barrier.restype = i32
+            L.sla_fp64_probe.argtypes = [i32, i32, P, ctypes.POINTER(ctypes.c_int64), P]
+            L.sla_fp64_probe.restype = i32
             _lib = L
     return _lib
 

@@ -47,6 +47,29 @@ int num_sms(int device) {
   return g_sms[device];
 }
 
+// FP64 FMA throughput probe: kFp64Chains independent FMA chains per thread
+// (enough in flight to keep the pipe busy at full occupancy), each step
+// y <- y * m + c with |m| < 1 so the values stay bounded; the chains' sum is
+// written only if it equals an impossible value, so the work cannot be
+// dropped.
+constexpr int kFp64Chains = 8;
+constexpr int kFp64Threads = 256;
+
+__global__ void __launch_bounds__(kFp64Threads) fp64_probe_kernel(int iters, double* out) {
+  double y[kFp64Chains];
+  const double m = 0.999999, c = 1e-7;
+#pragma unroll
+  for (int k = 0; k < kFp64Chains; ++k) y[k] = 1.0 + 1e-3 * k + 1e-9 * threadIdx.x;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kFp64Chains; ++k) y[k] = fma(y[k], m, c);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < kFp64Chains; ++k) sum += y[k];
+  if (sum == -1.0) out[0] = sum;
+}
+
 // Pattern validation: one thread per row, every load bounds-checked.
 __global__ void csr_check_kernel(int n, int nnz, const int* __restrict__ rowptr,
                                  const int* __restrict__ col, int* ok) {
@@ -119,3 +142,13 @@ int32_t sla_csr_check(const sla_csr* A, int32_t* ok, void* stream) {
 }
 
 }  // extern "C"
+
+extern "C" int32_t sla_fp64_probe(int32_t iters, int32_t blocks_per_sm, double* out, int64_t* flops, void* stream) {
+  if (iters < 1 || blocks_per_sm < 1 || blocks_per_sm > 64 || out == nullptr || flops == nullptr)
+    return SLA_ERR_INVALID;
+  const int grid = sla::num_sms(sla::current_device()) * blocks_per_sm;
+  sla::fp64_probe_kernel<<<grid, sla::kFp64Threads, 0, (cudaStream_t)stream>>>(iters, out);
+  SLA_CUDA_TRY(cudaGetLastError());
+  *flops = 2LL * sla::kFp64Chains * iters * (long long)grid * sla::kFp64Threads;
+  return SLA_OK;
+}

@@ -27,6 +27,30 @@ def _stream_ptr(device: torch.device) -> int:
     return torch.cuda.current_stream(device).cuda_stream
 
 
+def fp64_peak_tflops(device: torch.device | str = "cuda", iters: int = 4096, blocks_per_sm: int = 8,
+                     reps: int = 5) -> float:
+    """Measured FP64 FMA throughput of the device (TFLOP/s): the library's
+    probe kernel (independent FMA chains on every SM at full occupancy),
+    timed with CUDA events on the current stream, best of `reps` after one
+    warm-up launch."""
+    dev = torch.device(device)
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    flops = ctypes.c_int64(0)
+    st = _stream_ptr(dev)
+    L.check("sla_fp64_probe", L.lib().sla_fp64_probe(iters, blocks_per_sm, out.data_ptr(), ctypes.byref(flops), st))
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        L.check("sla_fp64_probe", L.lib().sla_fp64_probe(iters, blocks_per_sm, out.data_ptr(), ctypes.byref(flops),
+                                                         st))
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return flops.value / (best / 1e3) / 1e12
+
+
 def _ptr(t: torch.Tensor | None) -> int | None:
     return None if t is None else t.data_ptr()
 
