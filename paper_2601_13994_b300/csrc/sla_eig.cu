@@ -239,7 +239,7 @@ __device__ __forceinline__ void rotation_of(double d, double e, double& c, doubl
 
 template <class T>
 __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps, T* rot, int* s_any,
-                           T* s_floor, unsigned short* items) {
+                           T* s_floor, unsigned short* items, int* stepf) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int q = tid; q < m * kEigLd; q += nt) V[q] = T(0);
   __syncthreads();
@@ -268,7 +268,10 @@ __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps
   }
   __syncthreads();
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // stepf[r]: a rotation in step r of this sweep (written only in step r's
+    // rotation phase, read after its barrier, cleared here)
     if (tid == 0) *s_any = 0;
+    for (int q = tid; q < mp - 1; q += nt) stepf[q] = 0;
     __syncthreads();
     for (int r = 0; r < mp - 1; ++r) {
       if (tid < npair) {
@@ -297,6 +300,7 @@ __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps
           if (apq * apq > rel * rel * fabs(app * aqq) && fabs(apq) > floor_abs) {
             rotation_of(aqq - app, T(2) * apq, c, s);
             *s_any = 1;
+            stepf[r] = 1;
           }
         }
         rot[4 * tid] = (T)p;
@@ -305,6 +309,10 @@ __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps
         rot[4 * tid + 3] = s;
       }
       __syncthreads();
+      // a step without a rotation leaves A and V as they are (the sweep that
+      // ends the solve is all such steps): its applies and second barrier
+      // are skipped, by every thread alike
+      if (stepf[r] == 0) continue;
       // A <- J^T A J and V <- V J in one pass.  The step's rotations act on
       // disjoint pairs, so every element of A lies in one 2 x 2 block
       // (pair a's rows) x (pair b's columns), which one thread rotates on
@@ -374,6 +382,7 @@ struct EigSmem {
   int keep[kEigMaxM];
   int sel[kEigMaxM];
   unsigned short items[(kEigMaxM / 2) * (kEigMaxM / 2) + kEigMaxM * (kEigMaxM / 2)];
+  int stepf[kEigMaxM];  // the Jacobi sweeps' per-step "rotated" flags
   int nkeep;
   int any;
   double floor_d;
@@ -610,7 +619,7 @@ __device__ void eig_eigh(double* A, double* V, int m, double* S1, double* S2, Ei
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int q = tid; q < m * kEigLd; q += nt) sm.u.f.Af[q] = (float)A[q];
   __syncthreads();
-  eig_jacobi<float>(sm.u.f.Af, sm.u.f.Vf, m, 1e-7f, 1e-9f, 12, sm.rotf, &sm.any, &sm.floor_f, sm.items);
+  eig_jacobi<float>(sm.u.f.Af, sm.u.f.Vf, m, 1e-7f, 1e-9f, 12, sm.rotf, &sm.any, &sm.floor_f, sm.items, sm.stepf);
   for (int q = tid; q < m * kEigLd; q += nt) V[q] = (double)sm.u.f.Vf[q];
   __syncthreads();
   const bool done = eig_refine(A, V, S1, S2, sm.u.R, m, sm, rank);
@@ -622,7 +631,7 @@ __device__ void eig_eigh(double* A, double* V, int m, double* S1, double* S2, Ei
   }
   __syncthreads();
   if (done) return;
-  eig_jacobi<double>(A, S2, m, 1e-15, 0.0, 30, sm.rot, &sm.any, &sm.floor_d, sm.items);
+  eig_jacobi<double>(A, S2, m, 1e-15, 0.0, 30, sm.rot, &sm.any, &sm.floor_d, sm.items, sm.stepf);
   eig_mm(S1, V, S2, m, false);  // X V1
   for (int q = tid; q < m * kEigLd; q += nt) V[q] = S1[q];
   __syncthreads();
