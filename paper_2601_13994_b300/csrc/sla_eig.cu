@@ -214,13 +214,19 @@ __global__ void __launch_bounds__(kEigThreads) eig_spmm_kernel(EigPtrs P, int mo
 // ~1e-7 of its value, and the sweeps repeat until every a_pq passes the
 // FP64 threshold (convergence is then linear with rate ~1e-7 per sweep).
 __device__ __forceinline__ void rotation_of(float d, float e, float& c, float& s) {
+  // special-function reciprocals and reciprocal square roots only (no IEEE
+  // division or square-root sequences on the step's critical path): the
+  // angle need only be accurate to a few FP32 ulps -- the sweeps repeat
+  // until a_pq passes the threshold, and the FP64 refinement that follows
+  // squares what error remains
   const float ad = fabsf(d), ae = fabsf(e);
   const float big = fmaxf(ad, ae), small = fminf(ad, ae);
-  const float rr = small / big;
-  const float hyp = big * sqrtf(1.0f + rr * rr);
-  float t = ae / (ad + hyp);
+  const float rr = __fdividef(small, big);  // in [0, 1]
+  const float h2 = fmaf(rr, rr, 1.0f);      // in [1, 2]
+  const float hyp = big * (h2 * rsqrtf(h2));
+  float t = __fdividef(ae, ad + hyp);       // in [0, 1]
   if ((d < 0.0f) != (e < 0.0f)) t = -t;
-  c = rsqrtf(1.0f + t * t);
+  c = rsqrtf(fmaf(t, t, 1.0f));
   s = t * c;
 }
 __device__ __forceinline__ void rotation_of(double d, double e, double& c, double& s) {
@@ -267,13 +273,36 @@ __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps
     items[t] = (unsigned short)((x << 8) | y);
   }
   __syncthreads();
+  // The V update of a step runs in the next step's first phase, on warps 1..
+  // of the block while warp 0 computes that step's rotations (the rotations
+  // are double-buffered by step parity; V is read by no rotation), so the
+  // second phase applies only A's blocks.  A step whose rotations are all
+  // the identity leaves A and V as they are and skips its second phase.
+  const int nblk = npair * npair, nv = m * npair;
+  bool vpend = false;  // the previous step's V update is still to be applied
+  int vpar = 0;        // its rotation buffer
+  auto apply_v = [&](const T* rt) {
+    for (int t = tid - kWarp; t < nv; t += nt - kWarp) {
+      const int it = items[nblk + t];
+      const int x = it >> 8, y = it & 255;
+      const T sb = rt[4 * y + 3];
+      if (sb == T(0)) continue;
+      const int pb = (int)rt[4 * y], qb = (int)rt[4 * y + 1];
+      const T cb = rt[4 * y + 2];
+      const T vp = V[x * kEigLd + pb], vq = V[x * kEigLd + qb];
+      V[x * kEigLd + pb] = cb * vp - sb * vq;
+      V[x * kEigLd + qb] = sb * vp + cb * vq;
+    }
+  };
+  int g = 0;  // steps so far (the rotation buffer is g & 1)
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     // stepf[r]: a rotation in step r of this sweep (written only in step r's
     // rotation phase, read after its barrier, cleared here)
     if (tid == 0) *s_any = 0;
     for (int q = tid; q < mp - 1; q += nt) stepf[q] = 0;
     __syncthreads();
-    for (int r = 0; r < mp - 1; ++r) {
+    for (int r = 0; r < mp - 1; ++r, ++g) {
+      T* rc = rot + (g & 1) * 4 * (kEigMaxM / 2 + 1);
       if (tid < npair) {
         const int x1 = tid, x2 = mp - 1 - tid;
         // 1 + (x - 1 + r) mod (m' - 1) without a division (x - 1 + r < 2 (m' - 1))
@@ -294,8 +323,7 @@ __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps
           // |a_pq| > rel sqrt|a_pp a_qq| without the square root; then, with
           // d = a_qq - a_pp and e = 2 a_pq, tan = sgn(d e) |e| / (|d| +
           // sqrt(d^2 + e^2)) (the smaller root of t^2 + 2 (d/e) t - 1 = 0),
-          // cos = 1 / sqrt(1 + tan^2): one square root, one division, one
-          // reciprocal square root -- the rotation is on every step's
+          // cos = 1 / sqrt(1 + tan^2) -- the rotation is on every step's
           // critical path
           if (apq * apq > rel * rel * fabs(app * aqq) && fabs(apq) > floor_abs) {
             rotation_of(aqq - app, T(2) * apq, c, s);
@@ -303,58 +331,52 @@ __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps
             stepf[r] = 1;
           }
         }
-        rot[4 * tid] = (T)p;
-        rot[4 * tid + 1] = (T)q;
-        rot[4 * tid + 2] = c;
-        rot[4 * tid + 3] = s;
+        rc[4 * tid] = (T)p;
+        rc[4 * tid + 1] = (T)q;
+        rc[4 * tid + 2] = c;
+        rc[4 * tid + 3] = s;
+      } else if (tid >= kWarp && vpend) {
+        apply_v(rot + vpar * 4 * (kEigMaxM / 2 + 1));
       }
       __syncthreads();
-      // a step without a rotation leaves A and V as they are (the sweep that
-      // ends the solve is all such steps): its applies and second barrier
-      // are skipped, by every thread alike
+      vpend = false;
       if (stepf[r] == 0) continue;
-      // A <- J^T A J and V <- V J in one pass.  The step's rotations act on
-      // disjoint pairs, so every element of A lies in one 2 x 2 block
-      // (pair a's rows) x (pair b's columns), which one thread rotates on
-      // both sides in registers; every (row of V, pair) is one item too.
-      // Items come from a table built once per solve (no integer division
-      // in the step, which would run on the special-function pipe).
-      const int nitems = npair * npair + m * npair;
-      for (int t = tid; t < nitems; t += nt) {
+      // A <- J^T A J in one pass.  The step's rotations act on disjoint
+      // pairs, so every element of A lies in one 2 x 2 block (pair a's rows)
+      // x (pair b's columns), which one thread rotates on both sides in
+      // registers.  Items come from a table built once per solve (no integer
+      // division in the step, which would run on the special-function pipe).
+      for (int t = tid; t < nblk; t += nt) {
         const int it = items[t];
         const int x = it >> 8, y = it & 255;
-        if (t < npair * npair) {
-          // block: row pair x, column pair y
-          const T sa = rot[4 * x + 3], sb = rot[4 * y + 3];
-          if (sa == T(0) && sb == T(0)) continue;
-          const int pa = (int)rot[4 * x], qa = (int)rot[4 * x + 1];
-          const int pb = (int)rot[4 * y], qb = (int)rot[4 * y + 1];
-          const T ca = rot[4 * x + 2], cb = rot[4 * y + 2];
-          const bool hq = qa < m, hqb = qb < m;
-          const T m00 = A[pa * kEigLd + pb], m01 = hqb ? A[pa * kEigLd + qb] : T(0);
-          const T m10 = hq ? A[qa * kEigLd + pb] : T(0), m11 = (hq && hqb) ? A[qa * kEigLd + qb] : T(0);
-          // rows: p' = c p - s q, q' = s p + c q
-          const T r00 = ca * m00 - sa * m10, r01 = ca * m01 - sa * m11;
-          const T r10 = sa * m00 + ca * m10, r11 = sa * m01 + ca * m11;
-          // columns likewise
-          A[pa * kEigLd + pb] = cb * r00 - sb * r01;
-          if (hqb) A[pa * kEigLd + qb] = sb * r00 + cb * r01;
-          if (hq) A[qa * kEigLd + pb] = cb * r10 - sb * r11;
-          if (hq && hqb) A[qa * kEigLd + qb] = sb * r10 + cb * r11;
-        } else {
-          // V row x, column pair y
-          const T sb = rot[4 * y + 3];
-          if (sb == T(0)) continue;
-          const int pb = (int)rot[4 * y], qb = (int)rot[4 * y + 1];
-          const T cb = rot[4 * y + 2];
-          const T vp = V[x * kEigLd + pb], vq = V[x * kEigLd + qb];
-          V[x * kEigLd + pb] = cb * vp - sb * vq;
-          V[x * kEigLd + qb] = sb * vp + cb * vq;
-        }
+        // block: row pair x, column pair y
+        const T sa = rc[4 * x + 3], sb = rc[4 * y + 3];
+        if (sa == T(0) && sb == T(0)) continue;
+        const int pa = (int)rc[4 * x], qa = (int)rc[4 * x + 1];
+        const int pb = (int)rc[4 * y], qb = (int)rc[4 * y + 1];
+        const T ca = rc[4 * x + 2], cb = rc[4 * y + 2];
+        const bool hq = qa < m, hqb = qb < m;
+        const T m00 = A[pa * kEigLd + pb], m01 = hqb ? A[pa * kEigLd + qb] : T(0);
+        const T m10 = hq ? A[qa * kEigLd + pb] : T(0), m11 = (hq && hqb) ? A[qa * kEigLd + qb] : T(0);
+        // rows: p' = c p - s q, q' = s p + c q
+        const T r00 = ca * m00 - sa * m10, r01 = ca * m01 - sa * m11;
+        const T r10 = sa * m00 + ca * m10, r11 = sa * m01 + ca * m11;
+        // columns likewise
+        A[pa * kEigLd + pb] = cb * r00 - sb * r01;
+        if (hqb) A[pa * kEigLd + qb] = sb * r00 + cb * r01;
+        if (hq) A[qa * kEigLd + pb] = cb * r10 - sb * r11;
+        if (hq && hqb) A[qa * kEigLd + qb] = sb * r10 + cb * r11;
       }
+      vpend = true;
+      vpar = g & 1;
       __syncthreads();
     }
     if (*s_any == 0) break;
+    __syncthreads();
+  }
+  // the last step's V update
+  if (vpend) {
+    if (tid >= kWarp) apply_v(rot + vpar * 4 * (kEigMaxM / 2 + 1));
     __syncthreads();
   }
 }
@@ -367,7 +389,7 @@ struct EigSmem {
   double T[kEigMaxM * kEigLd];
   double scale[kEigMaxM];
   double scale2[kEigMaxM];
-  double rot[4 * (kEigMaxM / 2 + 1)];
+  double rot[2 * 4 * (kEigMaxM / 2 + 1)];  // the Jacobi rotations, two steps
   union {
     struct {
       float Af[kEigMaxM * kEigLd];
@@ -378,7 +400,7 @@ struct EigSmem {
   double lam[kEigMaxM];
   double xpart[2 * kRrCluster];  // every CTA's parts of the refinement's two norms
   double nrm[2 * (kEigThreads / 32)];
-  float rotf[4 * (kEigMaxM / 2 + 1)];
+  float rotf[2 * 4 * (kEigMaxM / 2 + 1)];
   int keep[kEigMaxM];
   int sel[kEigMaxM];
   unsigned short items[(kEigMaxM / 2) * (kEigMaxM / 2) + kEigMaxM * (kEigMaxM / 2)];
