@@ -29,14 +29,16 @@
 // which grows as the iteration converges -- from its eigendecomposition with
 // the directions below 1e-12 of the largest eigenvalue dropped; the
 // projected H = B^T H B is then diagonalised.  The small symmetric
-// eigenproblems (m <= 30) run in one thread block: FP32 cyclic Jacobi sweeps
-// with the round-robin ordering that makes the m/2 rotations of a step
-// independent, then FP64 orthogonalisation and FP64 sweeps (eig_eigh).
+// eigenproblems (m <= 30) are FP32 cyclic Jacobi sweeps with the round-robin
+// ordering that makes the m/2 rotations of a step independent, then FP64
+// iterative refinement (eig_eigh).  The whole step runs on one thread-block
+// cluster: every CTA repeats the sequential parts on its own copy of the
+// small matrices, and the FP64 products are split over the CTAs.
 //
-// Kernels of an iteration: SpMM (A W), Gram (block partial sums of G and H;
-// the last block to arrive adds them in a fixed order and runs the
-// Rayleigh-Ritz step), update (X', P', R, W' and the residual norms; the
-// last block takes the convergence decision).  The host launches them in a
+// Kernels of an iteration: SpMM (A W), Gram (block partial sums of G and H),
+// Gram totals (fixed-order sums over the Gram blocks; the last cluster to
+// arrive runs the Rayleigh-Ritz step), update (X', P', R, W' and the
+// residual norms; the last block takes the convergence decision).  The host launches them in a
 // loop and reads the device state every few iterations; once the state says
 // done, further launches return at once.  S and AS are row-major [n][3k]
 // and double-buffered (the update reads one pair and writes the other).
@@ -273,8 +275,8 @@ __device__ void eig_jacobi(T* A, T* V, int m, T rel, T floor_rel, int max_sweeps
     items[t] = (unsigned short)((x << 8) | y);
   }
   __syncthreads();
-  // The V update of a step runs in the next step's first phase, on warps 1..
-  // of the block while warp 0 computes that step's rotations (the rotations
+  // The V update of a step runs in the next step's first phase, on every
+  // warp but the first while warp 0 computes that step's rotations (the rotations
   // are double-buffered by step parity; V is read by no rotation), so the
   // second phase applies only A's blocks.  A step whose rotations are all
   // the identity leaves A and V as they are and skips its second phase.
