@@ -858,9 +858,14 @@ __device__ int eig_rayleigh_ritz(EigSmem& sm, int m, int k, double* C, double* t
 }
 
 // G = S^T S and H = S^T (A S) over the m active columns (upper triangles),
-// per block, then the last block adds all blocks' partials in block order
-// and runs the Rayleigh-Ritz step.
-__global__ void __launch_bounds__(kEigThreads) eig_gram_kernel(EigPtrs P) {
+// per block; the Gram-totals kernel adds all blocks' partials in block order.
+// One pair (a, b) per thread (kEigGramThreads >= 465 pairs at m = 30): with
+// 256 threads and two pairs for some, the last warps' second pairs ran alone
+// at the end of every tile.
+constexpr int kEigGramThreads = 512;
+static_assert(kEigGramThreads >= kEigPairs, "one Gram pair per thread");
+
+__global__ void __launch_bounds__(kEigGramThreads) eig_gram_kernel(EigPtrs P) {
   const EigDesc& d = *P.d;
   EigState* st = P.st;
   if (st->done || st->bad) return;
@@ -871,21 +876,19 @@ __global__ void __launch_bounds__(kEigThreads) eig_gram_kernel(EigPtrs P) {
   const double* S = P.S[cur];
   const double* AS = P.AS[cur];
   const int tid = threadIdx.x;
-  // this thread's pairs (a <= b): t = tid and tid + 256
-  int pa[2] = {0, 0}, pb[2] = {0, 0};
-  for (int h = 0; h < 2; ++h) {
-    const int t = tid + h * kEigThreads;
-    if (t < npairs) {
-      int a = 0, rem = t;
-      while (rem >= m - a) {
-        rem -= m - a;
-        ++a;
-      }
-      pa[h] = a;
-      pb[h] = a + rem;
+  // this thread's pair (a <= b)
+  int pa = 0, pb = 0;
+  const bool has = tid < npairs;
+  if (has) {
+    int a = 0, rem = tid;
+    while (rem >= m - a) {
+      rem -= m - a;
+      ++a;
     }
+    pa = a;
+    pb = a + rem;
   }
-  double g[2] = {0.0, 0.0}, hh[2] = {0.0, 0.0};
+  double g = 0.0, hh = 0.0;
   const int tiles = (n + kEigTile - 1) / kEigTile;
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int r0 = tile * kEigTile;
@@ -897,25 +900,18 @@ __global__ void __launch_bounds__(kEigThreads) eig_gram_kernel(EigPtrs P) {
       tA[i * kEigMaxM + j] = AS[(size_t)(r0 + i) * ld + j];
     }
     __syncthreads();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (tid + h * kEigThreads < npairs) {
-        const int a = pa[h], b = pb[h];
-        for (int i = 0; i < rows; ++i) {
-          const double sa = tS[i * kEigMaxM + a];
-          g[h] = fma(sa, tS[i * kEigMaxM + b], g[h]);
-          hh[h] = fma(sa, tA[i * kEigMaxM + b], hh[h]);
-        }
+    if (has) {
+      for (int i = 0; i < rows; ++i) {
+        const double sa = tS[i * kEigMaxM + pa];
+        g = fma(sa, tS[i * kEigMaxM + pb], g);
+        hh = fma(sa, tA[i * kEigMaxM + pb], hh);
       }
     }
   }
   double* mine = P.gpart + (size_t)blockIdx.x * 2 * kEigPairs;
-  for (int h = 0; h < 2; ++h) {
-    const int t = tid + h * kEigThreads;
-    if (t < npairs) {
-      mine[t] = g[h];
-      mine[kEigPairs + t] = hh[h];
-    }
+  if (has) {
+    mine[tid] = g;
+    mine[kEigPairs + tid] = hh;
   }
 }
 
@@ -1401,13 +1397,13 @@ extern "C" int32_t sla_eigsh(const sla_csr* A, const double* val, int32_t k, dou
   eig_init_kernel<<<eig_grid(n, 1024), kEigThreads, 0, s>>>(P);
   // start: Rayleigh-Ritz on X0 alone, then W = D^{-1} R
   eig_spmm_kernel<<<eig_grid(n, 4096), kEigThreads, 0, s>>>(P, 0);
-  eig_gram_kernel<<<gb, kEigThreads, 0, s>>>(P);
+  eig_gram_kernel<<<gb, kEigGramThreads, 0, s>>>(P);
   eig_rr_kernel<<<kRrBlocks, kEigThreads, 0, s>>>(P, gb);
   eig_update_kernel<kEigUpdThreads><<<ub, kEigUpdThreads, 0, s>>>(P);
   SLA_CUDA_TRY(cudaGetLastError());
   for (long long it = 0; it < (long long)opts->max_iter; ++it) {
     eig_spmm_kernel<<<eig_grid(n, 4096), kEigThreads, 0, s>>>(P, 1);
-    eig_gram_kernel<<<gb, kEigThreads, 0, s>>>(P);
+    eig_gram_kernel<<<gb, kEigGramThreads, 0, s>>>(P);
     eig_rr_kernel<<<kRrBlocks, kEigThreads, 0, s>>>(P, gb);
     eig_update_kernel<kEigUpdThreads><<<ub, kEigUpdThreads, 0, s>>>(P);
     if ((it + 1) % kEigPollEvery == 0) {
