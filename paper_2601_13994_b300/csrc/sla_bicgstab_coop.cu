@@ -376,10 +376,12 @@ int g_occ_bicg[64] = {};
 
 // Largest n solved by the cooperative BiCGStab, from the measured crossover
 // with the graph of per-phase kernels (B300, 3D convection-diffusion Pe 10,
-// us per iteration cooperative vs graph): 32^3 26.5 vs 34.2, 64^3 40.9 vs
-// 54.9, 96^3 98.5 vs 98.3, 128^3 198.6 vs 182.6 -- two SpMV phases per
-// iteration at 1024 threads per SM lose to the graph's kernels above ~1 M rows.
-constexpr long long kCoopMaxNBicg = 7LL << 17;  // 896 Ki rows
+// us per iteration cooperative vs graph, the graph on A D^{-1} with the
+// preconditioner folded in): 32^3 27.1 vs 37.0, 48^3 32.0 vs 44.1, 64^3 41.4
+// vs 52.4, 80^3 56.1 vs 66.1, 96^3 94.1 vs 92.4, 128^3 186.6 vs 159.4 -- two
+// SpMV phases per iteration at 1024 threads per SM lose to the graph's
+// kernels from somewhat under 1 M rows.
+constexpr long long kCoopMaxNBicg = 3LL << 18;  // 768 Ki rows
 
 bool use_bicg_coop(long long n) { return use_coop(n, kCoopMaxNBicg); }
 

@@ -276,7 +276,7 @@ def bicgstab(A: CSRMatrix, val: torch.Tensor, b: torch.Tensor, *, rtol: float = 
              max_restarts: int = 2, out: torch.Tensor | None = None, graph: bool = True,
              cooperative: bool = True):
     """Right-preconditioned BiCGStab for nonsymmetric A.  Returns (x, SolveInfo).
-    Up to 896 Ki rows one cooperative launch (``cooperative=False`` opts out)."""
+    Up to 768 Ki rows one cooperative launch (``cooperative=False`` opts out)."""
     return _krylov("sla_bicgstab", L.SLA_WS_BICGSTAB, A, val, b, rtol, atol, max_iter, precond, x0,
                    max_restarts, out, graph, cooperative)
 

@@ -104,7 +104,7 @@ def test_half_step_exit_and_host_loop():
     lambda: I.convdiff3d(64, 1.0),
 ])
 def test_cooperative_matches_oracle_and_graph(gen):
-    """BiCGStab as one cooperative launch (the default up to 896 Ki rows)
+    """BiCGStab as one cooperative launch (the default up to 768 Ki rows)
     against the oracle and the graph of per-phase kernels: several blocks and
     ragged tails; deterministic on its own."""
     rp, c, v = gen()
