@@ -25,11 +25,12 @@ def exact(rp, c, v, b):
     return spl.spsolve(sp.csr_matrix((v, c, rp)).tocsc(), b)
 
 
+@pytest.mark.parametrize("coop", [True, False])
 @pytest.mark.parametrize("N,pe", [(16, 10.0), (24, 1.0), (33, 10.0)])
-def test_convdiff_matches_oracle_and_lu(N, pe):
+def test_convdiff_matches_oracle_and_lu(N, pe, coop):
     rp, c, v = I.convdiff3d(N, pe)
     b = I.rhs_uniform(N ** 3, N)
-    x, info = gpu_bicg(rp, c, v, b, rtol=1e-10)
+    x, info = gpu_bicg(rp, c, v, b, rtol=1e-10, cooperative=coop)
     xo, io = oracle.bicgstab(rp, c, v, b, rtol=1e-10)
     assert info["status"] == 0 and io["status"] == 0
     xs = exact(rp, c, v, b)
@@ -48,31 +49,36 @@ def test_spd_system_agrees_with_cg():
     assert rel(x, xc.cpu().numpy()) <= 1e-8
 
 
-def test_bicgstab_edge_cases_match_oracle():
+@pytest.mark.parametrize("coop", [True, False])
+def test_bicgstab_edge_cases_match_oracle(coop):
+    """Zero right-hand side, a zero diagonal entry, the iteration cap, a
+    non-finite right-hand side, no preconditioner and a warm start at the
+    solution, through the cooperative launch and through the graph of
+    per-phase kernels (the path of the large systems)."""
     rp, c, v = I.convdiff3d(5)
     n = 125
-    x, info = gpu_bicg(rp, c, v, np.zeros(n))
+    x, info = gpu_bicg(rp, c, v, np.zeros(n), cooperative=coop)
     assert info["status"] == 0 and info["iters"] == 0 and not x.any()
     v0 = v.copy()
     v0[(c == 0) & (np.arange(len(c)) < rp[1])] = 0.0
-    _, info = gpu_bicg(rp, c, v0, np.ones(n))
+    _, info = gpu_bicg(rp, c, v0, np.ones(n), cooperative=coop)
     _, io = oracle.bicgstab(rp, c, v0, np.ones(n))
     assert info["status"] == io["status"] == -1
     b = I.rhs_uniform(n, 1)
-    _, info = gpu_bicg(rp, c, v, b, rtol=1e-15, max_iter=1)
+    _, info = gpu_bicg(rp, c, v, b, rtol=1e-15, max_iter=1, cooperative=coop)
     _, io = oracle.bicgstab(rp, c, v, b, rtol=1e-15, max_iter=1)
     assert info["status_name"] == io["status_name"] == "NOT_CONVERGED"
     assert info["iters"] == io["iters"] == 1
     bn = b.copy(); bn[0] = np.inf
-    _, info = gpu_bicg(rp, c, v, bn)
+    _, info = gpu_bicg(rp, c, v, bn, cooperative=coop)
     assert info["status_name"] == "BREAKDOWN"
     # unpreconditioned, and a warm start at the solution
-    x, info = gpu_bicg(rp, c, v, b, rtol=1e-11, precond="none")
+    x, info = gpu_bicg(rp, c, v, b, rtol=1e-11, precond="none", cooperative=coop)
     xo, io = oracle.bicgstab(rp, c, v, b, rtol=1e-11, precond="none")
     assert info["status"] == 0 and rel(x, exact(rp, c, v, b)) <= 1e-8
     assert abs(info["iters"] - io["iters"]) <= 2
     xs = exact(rp, c, v, b)
-    x, inf = sla.bicgstab(csr(rp, c), to_dev(v), to_dev(b), x0=to_dev(xs), rtol=1e-10)
+    x, inf = sla.bicgstab(csr(rp, c), to_dev(v), to_dev(b), x0=to_dev(xs), rtol=1e-10, cooperative=coop)
     assert inf.status == 0 and inf.iters <= 1
 
 

@@ -65,47 +65,53 @@ def test_fem_and_unpreconditioned():
         assert abs(info["iters"] - io["iters"]) <= max(2, io["iters"] // 50)
 
 
-def test_edge_cases_match_oracle():
+@pytest.mark.parametrize("coop", [True, False])
+def test_edge_cases_match_oracle(coop):
+    """b = 0 (with a discarded warm start), a negative diagonal, an
+    indefinite system, iteration caps, NaN, a warm start at the solution,
+    n = 1 and atol-only stopping, through the cooperative launch and through
+    the graph of per-phase kernels (the path of the large systems)."""
     rp, c, v = I.poisson2d(6)
     n = 36
     # b = 0 (also with a warm start, which must be discarded)
-    x, info = gpu_cg(rp, c, v, np.zeros(n))
+    x, info = gpu_cg(rp, c, v, np.zeros(n), cooperative=coop)
     assert info["status"] == 0 and info["iters"] == 0 and not x.any()
     A = csr(rp, c)
     x0 = to_dev(np.ones(n))
-    xx, inf = sla.cg(A, to_dev(v), to_dev(np.zeros(n)), x0=x0)
+    xx, inf = sla.cg(A, to_dev(v), to_dev(np.zeros(n)), x0=x0, cooperative=coop)
     assert inf.status == 0 and not xx.cpu().numpy().any()
     # non-positive diagonal -> NOT_SPD, NaN residuals
     v2 = v.copy()
     v2[rp[3]:rp[4]][c[rp[3]:rp[4]] == 3] = -1.0
-    _, info = gpu_cg(rp, c, v2, np.ones(n))
+    _, info = gpu_cg(rp, c, v2, np.ones(n), cooperative=coop)
     _, io = oracle.pcg(rp, c, v2, np.ones(n))
     assert info["status_name"] == io["status_name"] == "NOT_SPD"
     assert np.isnan(info["rel_res"])
     # indefinite, positive diagonal -> p^T A p <= 0
     rpi = np.array([0, 2, 4], np.int32); ci = np.array([0, 1, 0, 1], np.int32)
     vi = np.array([1.0, 2.0, 2.0, 1.0])
-    _, info = gpu_cg(rpi, ci, vi, np.array([1.0, -1.0]))
+    _, info = gpu_cg(rpi, ci, vi, np.array([1.0, -1.0]), cooperative=coop)
     assert info["status_name"] == "NOT_SPD"
     # iteration cap
     b = I.rhs_uniform(n, 0)
-    _, info = gpu_cg(rp, c, v, b, rtol=1e-14, max_iter=2)
+    _, info = gpu_cg(rp, c, v, b, rtol=1e-14, max_iter=2, cooperative=coop)
     _, io = oracle.pcg(rp, c, v, b, rtol=1e-14, max_iter=2)
     assert info["status_name"] == io["status_name"] == "NOT_CONVERGED" and info["iters"] == 2
-    _, info = gpu_cg(rp, c, v, b, rtol=1e-14, max_iter=0)
+    _, info = gpu_cg(rp, c, v, b, rtol=1e-14, max_iter=0, cooperative=coop)
     assert info["status_name"] == "NOT_CONVERGED" and info["iters"] == 0
     # NaN in b
     bn = b.copy(); bn[4] = np.nan
-    _, info = gpu_cg(rp, c, v, bn)
+    _, info = gpu_cg(rp, c, v, bn, cooperative=coop)
     assert info["status_name"] == "BREAKDOWN"
     # warm start from the exact solution
     xs = exact(rp, c, v, b)
-    x, inf = sla.cg(csr(rp, c), to_dev(v), to_dev(b), x0=to_dev(xs), rtol=1e-10)
+    x, inf = sla.cg(csr(rp, c), to_dev(v), to_dev(b), x0=to_dev(xs), rtol=1e-10, cooperative=coop)
     assert inf.status == 0 and inf.iters <= 1
     # n = 1 and atol-only stopping
-    x, info = gpu_cg(np.array([0, 1], np.int32), np.array([0], np.int32), np.array([4.0]), np.array([2.0]))
+    x, info = gpu_cg(np.array([0, 1], np.int32), np.array([0], np.int32), np.array([4.0]), np.array([2.0]),
+                     cooperative=coop)
     assert info["status"] == 0 and abs(x[0] - 0.5) < 1e-15
-    x, info = gpu_cg(rp, c, v, b, rtol=0.0, atol=1e-6)
+    x, info = gpu_cg(rp, c, v, b, rtol=0.0, atol=1e-6, cooperative=coop)
     _, io = oracle.pcg(rp, c, v, b, rtol=0.0, atol=1e-6)
     assert info["status"] == 0 and abs(info["iters"] - io["iters"]) <= 1
 
