@@ -96,6 +96,9 @@ extern "C" {
                                    batch = number of right-hand sides k       */
 #define SLA_WS_BATCHED 6        /* batched CG: n = rows per system (shared
                                    pattern) or total rows with batch = 1 (list) */
+#define SLA_WS_ADJOINT_BATCHED 14 /* sla_adjoint_backward_batched_*: (n, nnz,
+                                   batch) per system of a shared pattern, or
+                                   (total rows, total entries, 1) for a list */
 
 /* Adjoint solve methods (sla_adjoint_backward). */
 #define SLA_ADJ_CG 0            /* A symmetric: A^T = A, CG on A               */
@@ -802,6 +805,54 @@ int32_t sla_grad_values_batched(int32_t batch, int32_t shared_pattern,
                                 const int32_t* nnz_off, const double* lambda,
                                 const double* x, double* grad_val,
                                 void* stream);
+
+/* Batched backward pass of x_s = A_s^{-1} b_s (Eq. 3 for every system of a
+ * batch, Sec. 3.1): one batched solve of A_s^T lambda_s = grad_x[s] for all
+ * systems, then grad_b = lambda and grad_val[s, k] = -lambda[s, i] x[s, col k]
+ * on each system's own entries (sla_grad_values_batched).
+ * method SLA_ADJ_CG: every A_s symmetric, batched CG on the A_s themselves
+ * (sla_cg_batched_*); AT may be NULL.  method SLA_ADJ_BICGSTAB: batched
+ * BiCGStab on the CSR of A^T (sla_bicgstab_batched_*), every system's
+ * values gathered into the workspace first.
+ * opts: tolerances of the adjoint solves relative to ||grad_x[s]||; use_x0
+ * is ignored (lambda starts at 0); flags must be 0.  info[s] receives
+ * system s's adjoint solve record.  config: the launch shape of the
+ * method's batched solver (0 = automatic; the bits of sla_cg_batched_* or
+ * sla_bicgstab_batched_*).  x is the forward solution.  grad_b must overlap
+ * neither x nor grad_x, and grad_val neither x nor grad_b: SLA_ERR_INVALID
+ * otherwise, nothing enqueued.  Device arrays; asynchronous (no host
+ * synchronisation: the launches can be captured in a CUDA graph).
+ *
+ * Shared pattern: A (n, nnz, rowptr, col) with AT = sla_csr_transpose of A
+ * for BiCGStab; val and grad_val [batch, nnz]; x, grad_x, grad_b [batch, n]
+ * row-major.  Workspace: SLA_WS_ADJOINT_BATCHED with (n, nnz, batch). */
+int32_t sla_adjoint_backward_batched_shared(const sla_csr* A, const sla_csr_t* AT,
+                                            int32_t batch, const double* val,
+                                            const double* x, const double* grad_x,
+                                            double* grad_b, double* grad_val,
+                                            int32_t method, const sla_opts* opts,
+                                            sla_info* info, int32_t config,
+                                            void* ws, size_t ws_bytes, void* stream);
+
+/* Distinct patterns in the concatenated layout of sla_cg_batched_list
+ * (n_off, nnz_off, rowptr back to back, local columns, optional order);
+ * total_nnz = nnz_off[batch].  For BiCGStab, rowptr_t, col_t and perm_t are
+ * the list's transposes from sla_csr_list_transpose (the same offsets
+ * serve, since A_s^T has A_s's size and entry count); NULL for CG.  val,
+ * grad_val [total_nnz]; x, grad_x, grad_b [total_rows].
+ * Workspace: SLA_WS_ADJOINT_BATCHED with (total_rows, total_nnz, 1). */
+int32_t sla_adjoint_backward_batched_list(int32_t batch, int32_t n_max,
+                                          int32_t total_rows, int32_t total_nnz,
+                                          const int32_t* n_off, const int32_t* nnz_off,
+                                          const int32_t* rowptr, const int32_t* col,
+                                          const int32_t* rowptr_t, const int32_t* col_t,
+                                          const int32_t* perm_t, const double* val,
+                                          const double* x, const double* grad_x,
+                                          double* grad_b, double* grad_val,
+                                          const int32_t* order, int32_t method,
+                                          const sla_opts* opts, sla_info* info,
+                                          int32_t config, void* ws, size_t ws_bytes,
+                                          void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Distributed layer (Sec. 3.3, Eqs. 5-6; Algorithm 1 of App. C), with    */

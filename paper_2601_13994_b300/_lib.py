@@ -43,6 +43,7 @@ SLA_WS_CG_PIPELINED = 10
 SLA_WS_EIGSH = 11
 SLA_WS_EIG_ADJOINT = 12
 SLA_WS_LIST_TRANSPOSE = 13
+SLA_WS_ADJOINT_BATCHED = 14
 SLA_EIG_MAX_K = 8
 SLA_SPMV_ROWS = 0
 SLA_SPMV_MERGE = 1
@@ -165,6 +166,14 @@ def lib() -> ctypes.CDLL:
             L.sla_csr_list_transpose.restype = i32
             L.sla_gather_values_batched.argtypes = [i32, i64, P, P, P, P]
             L.sla_gather_values_batched.restype = i32
+            L.sla_adjoint_backward_batched_shared.argtypes = [ctypes.POINTER(SlaCsr), ctypes.POINTER(SlaCsrT), i32,
+                                                              P, P, P, P, P, i32, ctypes.POINTER(SlaOpts), P, i32,
+                                                              P, ctypes.c_size_t, P]
+            L.sla_adjoint_backward_batched_shared.restype = i32
+            L.sla_adjoint_backward_batched_list.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P, P, P, P, P, P,
+                                                            P, i32, ctypes.POINTER(SlaOpts), P, i32, P,
+                                                            ctypes.c_size_t, P]
+            L.sla_adjoint_backward_batched_list.restype = i32
             PP = ctypes.POINTER(ctypes.c_void_p)
             d = ctypes.c_double
             for name, args in (("sla_dist_halo_gather", [i64, P, P, P, P]),

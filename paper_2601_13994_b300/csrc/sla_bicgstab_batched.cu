@@ -561,6 +561,16 @@ __global__ void gather_batched_kernel(int batch, long long nnz, const int* __res
 }
 
 }  // namespace
+
+// The argument checks of sla_bicgstab_batched_* that need no pointer: its
+// options and the config word of the layout (shared pattern or list).
+// The batched adjoint runs them before it enqueues the values gather.
+int bicg_batched_precheck(const sla_opts* opts, int config, bool list) {
+  if (check_opts(opts) != SLA_OK) return SLA_ERR_INVALID;
+  if (config & ~(list ? kConfigList : kConfigShared)) return SLA_ERR_INVALID;
+  return (config & 15) <= 3 ? SLA_OK : SLA_ERR_INVALID;
+}
+
 }  // namespace sla
 
 using namespace sla;

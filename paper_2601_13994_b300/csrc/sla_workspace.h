@@ -131,6 +131,13 @@ inline size_t bicg_ws_bytes(int n, int nnz) {
 // Batched solves (sla_batched.cu); argument = total rows of the batch.
 size_t batched_ws_bytes(long long total_rows);
 
+// Batched adjoint (sla_adjoint_batched.cu): the batched solve's scratch,
+// then the values of every A_s^T (total entries of the batch, doubles).
+inline size_t adjoint_batched_ws_bytes(long long total_rows, long long total_nnz) {
+  return al256(batched_ws_bytes(total_rows)) +
+         al256(sizeof(double) * (size_t)(total_nnz > 0 ? total_nnz : 1));
+}
+
 // G G^T-preconditioned CG: descriptor, state, partials, r, z, p, q, t, then
 // the FP32 values of G and of G^T (nnz_g floats each).
 struct GgtLayout {
@@ -225,6 +232,10 @@ inline bool workspace_bytes(int kind, int n, int nnz, int batch, size_t* out) {
       return true;
     case SLA_WS_BATCHED:
       *out = batched_ws_bytes((long long)n * (batch > 0 ? batch : 1));
+      return true;
+    case SLA_WS_ADJOINT_BATCHED:
+      *out = adjoint_batched_ws_bytes((long long)n * (batch > 0 ? batch : 1),
+                                      (long long)nnz * (batch > 0 ? batch : 1));
       return true;
     default:
       return false;

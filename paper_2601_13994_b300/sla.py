@@ -995,27 +995,94 @@ def grad_values_batched_list(P: CSRList, lam: torch.Tensor, x: torch.Tensor) -> 
     return g
 
 
+def _adjoint_config(config, key) -> int:
+    """Launch shape of a batched adjoint solve: an int as given; otherwise
+    the choice tuned for the forward solve of the same shape, else 0."""
+    if isinstance(config, int):
+        return config
+    if config not in ("auto", "tune"):
+        raise ValueError("config must be an int, 'auto' or 'tune'")
+    _load_tune_file()
+    return _tune_cache.get(key, 0)
+
+
+def adjoint_backward_batched(A: CSRMatrix, val: torch.Tensor, x: torch.Tensor, grad_x: torch.Tensor, *,
+                             method: str = "cg", rtol: float = 1e-10, atol: float = 0.0,
+                             max_iter: int | None = None, precond: str = "jacobi", max_restarts: int = 2,
+                             config: int | str = "auto"):
+    """Eq. 3 for every system of a shared-pattern batch in one call
+    (sla_adjoint_backward_batched_shared): A_s^T lambda_s = grad_x[s] by one
+    batched CG (symmetric A_s) or BiCGStab (on the CSR of A^T) launch, then
+    the gradients of all systems.  val [B, nnz], x and grad_x [B, n];
+    returns (grad_b = lambda [B, n], grad_val [B, nnz], SolveInfo with B
+    records)."""
+    if method not in _ADJ:
+        raise ValueError("method must be 'cg' or 'bicgstab'")
+    B = x.shape[0]
+    _need(val, torch.float64, A.device, "val", B * A.nnz)
+    _need(x, torch.float64, A.device, "x", B * A.n)
+    _need(grad_x, torch.float64, A.device, "grad_x", B * A.n)
+    gb = torch.empty((B, A.n), dtype=torch.float64, device=A.device)
+    gv = torch.empty((B, A.nnz), dtype=torch.float64, device=A.device)
+    info = torch.empty((B, L.INFO_BYTES), dtype=torch.uint8, device=A.device)
+    o = _batched_opts(rtol, atol, max_iter, max_restarts, precond, 0, A.n)
+    atp = None
+    if method == "bicgstab":
+        transpose_of(A)
+        atp = ctypes.byref(A._transpose_c)
+    cfg = _adjoint_config(config, ("shared" if method == "cg" else "bicg_shared", A.n, A.nnz, B))
+    ws = workspace(L.SLA_WS_ADJOINT_BATCHED, A.n, A.nnz, B, A.device)
+    L.check("sla_adjoint_backward_batched_shared", L.lib().sla_adjoint_backward_batched_shared(
+        ctypes.byref(A.c), atp, B, val.data_ptr(), x.data_ptr(), grad_x.data_ptr(), gb.data_ptr(),
+        gv.data_ptr(), _ADJ[method], ctypes.byref(o), info.data_ptr(), cfg, ws.data_ptr(), ws.numel(),
+        _stream_ptr(A.device)))
+    return gb, gv, SolveInfo(info)
+
+
+def adjoint_backward_batched_list(P: CSRList, val: torch.Tensor, x: torch.Tensor, grad_x: torch.Tensor, *,
+                                  method: str = "cg", rtol: float = 1e-10, atol: float = 0.0,
+                                  max_iter: int | None = None, precond: str = "jacobi", max_restarts: int = 2,
+                                  config: int | str = "auto"):
+    """Eq. 3 for every system of a list of distinct patterns in one call
+    (sla_adjoint_backward_batched_list; BiCGStab on the list's transposes
+    from sla_csr_list_transpose).  val [total_nnz], x and grad_x
+    [total_rows]; returns (grad_b = lambda, grad_val, SolveInfo with B
+    records)."""
+    if method not in _ADJ:
+        raise ValueError("method must be 'cg' or 'bicgstab'")
+    _need(val, torch.float64, P.device, "val", P.total_nnz)
+    _need(x, torch.float64, P.device, "x", P.total_rows)
+    _need(grad_x, torch.float64, P.device, "grad_x", P.total_rows)
+    gb = torch.empty(P.total_rows, dtype=torch.float64, device=P.device)
+    gv = torch.empty(max(P.total_nnz, 1), dtype=torch.float64, device=P.device)[:P.total_nnz]
+    info = torch.empty((P.batch, L.INFO_BYTES), dtype=torch.uint8, device=P.device)
+    o = _batched_opts(rtol, atol, max_iter, max_restarts, precond, 0, P.n_max)
+    rpT = cT = permT = None
+    if method == "bicgstab":
+        PT, pT = P.transpose()
+        rpT, cT, permT = PT.rowptr.data_ptr(), PT.col.data_ptr(), pT.data_ptr()
+    key = ("list" if method == "cg" else "bicg_list", P.n_max, P.total_rows, P.total_nnz, P.batch)
+    cfg = _adjoint_config(config, key)
+    ws = workspace(L.SLA_WS_ADJOINT_BATCHED, P.total_rows, P.total_nnz, 1, P.device)
+    L.check("sla_adjoint_backward_batched_list", L.lib().sla_adjoint_backward_batched_list(
+        P.batch, P.n_max, P.total_rows, P.total_nnz, P.n_off.data_ptr(), P.nnz_off.data_ptr(),
+        P.rowptr.data_ptr(), P.col.data_ptr(), rpT, cT, permT, val.data_ptr(), x.data_ptr(), grad_x.data_ptr(),
+        gb.data_ptr(), gv.data_ptr(), None if P.order is None else P.order.data_ptr(), _ADJ[method],
+        ctypes.byref(o), info.data_ptr(), cfg, ws.data_ptr(), ws.numel(), _stream_ptr(P.device)))
+    return gb, gv, SolveInfo(info)
+
+
 _BATCH_SOLVERS = {"cg": (lambda *a, **k: cg_batched(*a, **k)), "bicgstab": (lambda *a, **k: bicgstab_batched(*a, **k))}
 _LIST_SOLVERS = {"cg": (lambda *a, **k: cg_batched_list(*a, **k)),
                  "bicgstab": (lambda *a, **k: bicgstab_batched_list(*a, **k))}
 
 
-def _transposed_pattern(A: CSRMatrix) -> CSRMatrix:
-    """CSRMatrix of A^T's pattern (cached on A with its permT)."""
-    t = getattr(A, "_transpose_matrix", None)
-    if t is None:
-        rpT, cT, _ = transpose_of(A)
-        t = CSRMatrix(rpT, cT, check=False)
-        A._transpose_matrix = t
-    return t
-
-
 class BatchedSolve(torch.autograd.Function):
     """x[s] = A_s^{-1} b[s] for a batch on one shared pattern, with the
-    adjoint backward (Eq. 3 per system): one batched solve of A_s^T lambda_s
-    = dL/dx_s for all systems (CG on A for SPD systems; BiCGStab on the
-    shared CSR of A^T with every system's values gathered for nonsymmetric
-    ones), then one gradient pass."""
+    adjoint backward (Eq. 3 per system) in one library call: one batched
+    solve of A_s^T lambda_s = dL/dx_s for all systems (CG on A for SPD
+    systems; BiCGStab on the shared CSR of A^T with every system's values
+    gathered for nonsymmetric ones), then one gradient pass."""
 
     @staticmethod
     def forward(ctx, val, b, A, method, kw, strict):
@@ -1030,17 +1097,11 @@ class BatchedSolve(torch.autograd.Function):
     def backward(ctx, gx):
         val, x = ctx.saved_tensors
         kw = {k: v for k, v in ctx.kw.items() if k not in ("x0", "out")}
-        v = val.detach().contiguous()
         g = gx.contiguous().to(torch.float64)
-        if ctx.method == "cg":
-            lam, info = cg_batched(ctx.A, v, g, **kw)
-        else:
-            AT = _transposed_pattern(ctx.A)
-            valT = gather_values_batched(transpose_of(ctx.A)[2], v.view(x.shape[0], -1))
-            lam, info = bicgstab_batched(AT, valT, g, **kw)
+        lam, gval, info = adjoint_backward_batched(ctx.A, val.detach().contiguous(), x, g, method=ctx.method, **kw)
         if ctx.strict is not None:
             _check_batch(info, "batched adjoint", ctx.strict)
-        return grad_values_batched_shared(ctx.A, lam, x), lam, None, None, None, None
+        return gval.view(val.shape), lam, None, None, None, None
 
 
 class BatchedListSolve(torch.autograd.Function):
@@ -1063,17 +1124,12 @@ class BatchedListSolve(torch.autograd.Function):
     def backward(ctx, gx):
         val, x = ctx.saved_tensors
         kw = {k: v for k, v in ctx.kw.items() if k not in ("x0", "out")}
-        v = val.detach().contiguous()
         g = gx.contiguous().to(torch.float64)
-        if ctx.method == "cg":
-            lam, info = cg_batched_list(ctx.P, v, g, **kw)
-        else:
-            PT, permT = ctx.P.transpose()
-            valT = gather_values(permT, v)
-            lam, info = bicgstab_batched_list(PT, valT, g, **kw)
+        lam, gval, info = adjoint_backward_batched_list(ctx.P, val.detach().contiguous(), x, g,
+                                                        method=ctx.method, **kw)
         if ctx.strict is not None:
             _check_batch(info, "batched list adjoint", ctx.strict)
-        return grad_values_batched_list(ctx.P, lam, x), lam, None, None, None, None
+        return gval, lam, None, None, None, None
 
 
 def _check_batch(info: SolveInfo, what: str, strict: bool):

@@ -200,6 +200,60 @@ def test_batched_bicgstab_and_list_transpose_reject_bad_arguments_without_launch
     assert lib.sla_gather_values_batched(-1, 20, fake, x, fake, None) == L.SLA_ERR_INVALID
 
 
+def test_batched_adjoint_arguments_rejected_without_launch():
+    """sla_adjoint_backward_batched_*: every rejection comes before the first
+    enqueue (fake pointers: a launch would fault), including a BiCGStab
+    config or option that the batched solver would refuse only after the
+    values gather."""
+    lib = L.lib()
+    fake = ctypes.c_void_p(0x1000)
+    A = L.SlaCsr(10, 20, fake, fake)
+    AT = L.SlaCsrT(fake, fake, fake)
+    o = L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0, 0)
+    ws, big = ctypes.c_void_p(0x100000), ctypes.c_size_t(1 << 40)
+    x, gx, gb, gv = 0x10000, 0x20000, 0x30000, 0x40000       # 4 systems: 40 rows, 80 entries
+
+    def shared(x=x, gx=gx, gb=gb, gv=gv, method=L.SLA_ADJ_CG, opts=o, at=None, cfg=0, w=ws, nb=big, batch=4):
+        return lib.sla_adjoint_backward_batched_shared(
+            ctypes.byref(A), None if at is None else ctypes.byref(at), batch, fake, ctypes.c_void_p(x),
+            ctypes.c_void_p(gx), ctypes.c_void_p(gb), ctypes.c_void_p(gv), method, ctypes.byref(opts), fake,
+            cfg, w, nb, None)
+    assert shared(batch=0) == L.SLA_OK
+    assert shared(batch=-1) == L.SLA_ERR_INVALID
+    assert shared(method=7) == L.SLA_ERR_INVALID
+    assert shared(opts=L.SlaOpts(1e-8, 0.0, 100, 2, 1, 0, L.SLA_FLAG_HOST_LOOP)) == L.SLA_ERR_INVALID
+    assert shared(gb=x) == L.SLA_ERR_INVALID                    # grad_b == x
+    assert shared(gb=gx + 8 * 39) == L.SLA_ERR_INVALID          # grad_b starts at grad_x's last entry
+    assert shared(gv=x + 8 * 39) == L.SLA_ERR_INVALID           # grad_val overlaps x's last entry
+    assert shared(gv=gb - 8 * 79) == L.SLA_ERR_INVALID          # grad_val's last entry is grad_b[0]
+    need = L.workspace_size(L.SLA_WS_ADJOINT_BATCHED, 10, 20, 4)
+    assert need >= L.workspace_size(L.SLA_WS_BATCHED, 10, 20, 4) + 8 * 80 and need % 256 == 0
+    assert shared(nb=need - 1) == L.SLA_ERR_WORKSPACE
+    assert shared(w=ctypes.c_void_p(0x100010)) == L.SLA_ERR_WORKSPACE
+    bic = L.SLA_ADJ_BICGSTAB
+    assert shared(method=bic) == L.SLA_ERR_INVALID              # no transpose
+    assert shared(method=bic, at=AT, cfg=32) == L.SLA_ERR_INVALID        # team bits: lists only
+    assert shared(method=bic, at=AT, cfg=4) == L.SLA_ERR_INVALID         # unknown block size code
+    assert shared(method=bic, at=AT, opts=L.SlaOpts(-1.0, 0.0, 100, 2, 1, 0, 0)) == L.SLA_ERR_INVALID
+    assert shared(method=bic, at=AT, opts=L.SlaOpts(1e-8, 0.0, 100, 2, L.SLA_PRECOND_GGT, 0, 0)) == \
+        L.SLA_ERR_INVALID
+
+    def lst(n_off=fake, rpt=fake, gb=gb, gv=gv, method=bic, cfg=0, nb=big):
+        return lib.sla_adjoint_backward_batched_list(
+            4, 10, 40, 80, n_off, fake, fake, fake, rpt, fake, fake, fake, ctypes.c_void_p(x),
+            ctypes.c_void_p(gx), ctypes.c_void_p(gb), ctypes.c_void_p(gv), None, method, ctypes.byref(o), fake,
+            cfg, ws, nb, None)
+    assert lst(n_off=None) == L.SLA_ERR_INVALID
+    assert lst(rpt=None) == L.SLA_ERR_INVALID                   # BiCGStab needs the transposes
+    assert lst(cfg=64) == L.SLA_ERR_INVALID                     # unknown list config bit
+    assert lst(gb=x + 8) == L.SLA_ERR_INVALID
+    assert lst(gv=gb + 8 * 39) == L.SLA_ERR_INVALID
+    assert lst(method=-1) == L.SLA_ERR_INVALID
+    need_l = L.workspace_size(L.SLA_WS_ADJOINT_BATCHED, 40, 80, 1)
+    assert need_l == need
+    assert lst(nb=need_l - 1) == L.SLA_ERR_WORKSPACE
+
+
 def test_multi_rhs_arguments_rejected_without_launch():
     lib = L.lib()
     fake = ctypes.c_void_p(0x1000)
