@@ -387,15 +387,22 @@ int32_t sla_mp_head_bwd(int32_t n, const int32_t* g_rowptr, const int32_t* g_col
                         void* stream);
 size_t sla_mp_head_bwd_ws(int32_t n);
 
-/* Training loss of the factor on one system (FP64):
- *   loss[0] = (x* - G G^T u)^T A (x* - G G^T u) / (x*^T u),  loss[1] = -2 / (x*^T u)
- * with x* = A^{-1} u, and dG = dloss/dg_val on the pattern of G
- * (g_i s_j + u_i h_j with s = G^T u, g = -2 A e / (x*^T u), h = G^T g).
- * Workspace: sla_ggt_loss_ws(n) bytes. */
+/* Training loss of the factor on one system (FP64), with x* = A^{-1} u and
+ * y = G G^T u:
+ *   loss[0] = (x* - k y)^T A (x* - k y) / (x*^T u),  loss[1] = -2 k / (x*^T u)
+ * mode 0: k = 1 (the A-norm error of G G^T u itself);
+ * mode 1: k = x*^T A y / y^T A y, the scale that minimises it (0 if y = 0):
+ *   the error of the best multiple of G G^T, the preconditioner as PCG
+ *   sees it (PCG's iterates do not change when M is scaled).
+ * dG = dloss/dg_val on the pattern of G: g_i s_j + u_i h_j with s = G^T u,
+ * g = -2 k A e / (x*^T u), e = x* - k y, h = G^T g (in mode 1 the total
+ * derivative, since dloss/dk = 0 at the minimising k).  Other modes:
+ * SLA_ERR_INVALID.  Workspace: sla_ggt_loss_ws(n) bytes. */
 int32_t sla_ggt_loss_grad(const sla_csr* A, const double* val, const sla_csr* G,
                           const double* g_val, const sla_csr_t* GT,
-                          const double* u, const double* xstar, double* loss,
-                          double* dG, void* ws, size_t ws_bytes, void* stream);
+                          const double* u, const double* xstar, int32_t mode,
+                          double* loss, double* dG, void* ws, size_t ws_bytes,
+                          void* stream);
 size_t sla_ggt_loss_ws(int32_t n);
 
 /* The factored sparse approximate inverse (FSAI; Kolotilina and Yeremin)

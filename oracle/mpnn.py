@@ -19,8 +19,13 @@ autograd for the gradients, the design the CUDA kernels implement:
       Gt_ii = exp(theta_ii), Gt_ij = theta_ij,  G = D^{-1/2} Gt  (row scaling),
   so that G G^T = D^{-1/2} Gt Gt^T D^{-1/2}; with v = vd = 0, G = D^{-1/2} and
   G G^T is the Jacobi preconditioner exactly.
-* Training loss for one system and right-hand side b with x* = A^{-1} b:
-      loss = (x* - G G^T b)^T A (x* - G G^T b) / (x*^T A x*).
+* Training loss for one system and right-hand side b with x* = A^{-1} b and
+  y = G G^T b:
+      loss = (x* - k y)^T A (x* - k y) / (x*^T A x*),
+  with k = 1, or in the scale-free form k = x*^T A y / y^T A y, the k that
+  minimises it (the error of the best multiple of G G^T; PCG's iterates do
+  not change when the preconditioner is scaled).  Its gradient here is
+  autograd's through k as well.
 * Column normalisation of the factor the network proposes (applied when the
   factor is formed for a solve): column j of G is divided by
   sqrt((G^T A G)_jj) = sqrt(sum_{i,k} G_ij A_ik G_kj), so that diag(G^T A G)
@@ -180,23 +185,33 @@ def ggt_apply(grp, gcol, g_val, u):
     return torch.zeros(n, dtype=torch.float64).index_add(0, rows, g_val * s[cols])  # G s
 
 
-def loss(grp, gcol, g_val, rp, c, v, b, xstar):
-    """(x* - G G^T b)^T A (x* - G G^T b) / (x*^T A x*)."""
+def loss(grp, gcol, g_val, rp, c, v, b, xstar, scale_free=False):
+    """(x* - k y)^T A (x* - k y) / (x*^T A x*), y = G G^T b; k = 1, or with
+    scale_free the minimising k = x*^T A y / y^T A y (0 when y = 0)."""
     n = len(rp) - 1
     rows = torch.tensor(np.repeat(np.arange(n), np.diff(rp)))
     cols = torch.tensor(np.asarray(c, np.int64))
     vt = torch.tensor(v)
     bt = torch.as_tensor(b, dtype=torch.float64)
     xs = torch.as_tensor(xstar, dtype=torch.float64)
-    err = xs - ggt_apply(grp, gcol, g_val, bt)
-    Ae = torch.zeros(n, dtype=torch.float64).index_add(0, rows, vt * err[cols])
-    return (err @ Ae) / (xs @ bt)
+
+    def amul(z):
+        return torch.zeros(n, dtype=torch.float64).index_add(0, rows, vt * z[cols])
+
+    y = ggt_apply(grp, gcol, g_val, bt)
+    if scale_free:
+        Ay = amul(y)
+        yAy = y @ Ay
+        k = (xs @ Ay) / yAy if float(yAy) > 0.0 else torch.zeros((), dtype=torch.float64)
+        y = k * y
+    err = xs - y
+    return (err @ amul(err)) / (xs @ bt)
 
 
-def loss_and_grads(params: dict, rp, c, v, b, xstar):
+def loss_and_grads(params: dict, rp, c, v, b, xstar, scale_free=False):
     """Loss and its gradient w.r.t. every parameter (autograd, float64)."""
     P = {k: torch.tensor(np.asarray(t, np.float64), requires_grad=True) for k, t in params.items()}
     grp, gcol, gv = forward(P, rp, c, v)
-    L = loss(grp, gcol, gv, rp, c, v, b, xstar)
+    L = loss(grp, gcol, gv, rp, c, v, b, xstar, scale_free)
     L.backward()
     return float(L.detach()), {k: t.grad.numpy().copy() for k, t in P.items()}, gv.detach().numpy()

@@ -784,11 +784,13 @@ __global__ void sub_kernel(int n, const double* __restrict__ a, const double* __
     out[i] = a[i] - b[i];
 }
 
-// one block: c = xs.u, num = e.Ae; loss = num / c; scale = -2 / c
+// one block: c = xs.u, num = e.Ae; loss = num / c; scale = -2 kappa / c
+// (kappa = 1 without a scale, else *kap)
 __global__ void __launch_bounds__(1024) loss_scalars_kernel(int n, const double* __restrict__ xs,
                                                             const double* __restrict__ u,
                                                             const double* __restrict__ err,
                                                             const double* __restrict__ Ae,
+                                                            const double* __restrict__ kap,
                                                             double* __restrict__ out) {
   __shared__ double red[2 * 1024 + 2];
   double acc[2] = {0.0, 0.0};
@@ -798,9 +800,34 @@ __global__ void __launch_bounds__(1024) loss_scalars_kernel(int n, const double*
   }
   block_sums<1024, 2>(acc, red);
   if (threadIdx.x == 0) {
+    const double k = kap != nullptr ? *kap : 1.0;
     out[0] = acc[1] / acc[0];
-    out[1] = -2.0 / acc[0];
+    out[1] = -2.0 * k / acc[0];
   }
+}
+
+// one block: the scale of y that minimises (xs - k y)^T A (xs - k y):
+// k = xs.Ay / y.Ay (0 when y.Ay = 0, i.e. y = 0)
+__global__ void __launch_bounds__(1024) loss_kappa_kernel(int n, const double* __restrict__ xs,
+                                                          const double* __restrict__ y,
+                                                          const double* __restrict__ Ay,
+                                                          double* __restrict__ kap) {
+  __shared__ double red[2 * 1024 + 2];
+  double acc[2] = {0.0, 0.0};
+  for (int i = threadIdx.x; i < n; i += 1024) {
+    acc[0] = fma(xs[i], Ay[i], acc[0]);
+    acc[1] = fma(y[i], Ay[i], acc[1]);
+  }
+  block_sums<1024, 2>(acc, red);
+  if (threadIdx.x == 0) *kap = acc[1] > 0.0 ? acc[0] / acc[1] : 0.0;
+}
+
+// err = xs - k y
+__global__ void sub_scaled_kernel(int n, const double* __restrict__ xs, const double* __restrict__ y,
+                                  const double* __restrict__ kap, double* __restrict__ out) {
+  const double k = *kap;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = fma(-k, y[i], xs[i]);
 }
 
 __global__ void scale_kernel(int n, const double* __restrict__ s, const double* __restrict__ a,
@@ -1058,13 +1085,16 @@ extern "C" int32_t sla_mp_head_bwd(int32_t n, const int32_t* g_rowptr, const int
 
 extern "C" size_t sla_ggt_loss_ws(int32_t n) { return 6 * al256(sizeof(double) * (size_t)(n > 0 ? n : 1)) + 256; }
 
-// loss[0] = (x* - G G^T u)^T A (x* - G G^T u) / (x*^T u), loss[1] = -2 / (x*^T u);
-// dG = dloss/dG on the pattern of G.
+// loss[0] = (x* - k y)^T A (x* - k y) / (x*^T u) with y = G G^T u, k = 1
+// (mode 0) or the minimising k = x*^T A y / y^T A y (mode 1);
+// loss[1] = -2 k / (x*^T u); dG = dloss/dG on the pattern of G (in mode 1
+// the gradient with k held at its optimum, where dloss/dk = 0).
 extern "C" int32_t sla_ggt_loss_grad(const sla_csr* A, const double* val, const sla_csr* G,
                                      const double* g_val, const sla_csr_t* GT, const double* u,
-                                     const double* xstar, double* loss, double* dG, void* ws,
+                                     const double* xstar, int32_t mode, double* loss, double* dG, void* ws,
                                      size_t ws_bytes, void* stream) {
   if (A == nullptr || G == nullptr || GT == nullptr || A->n != G->n || A->n < 0) return SLA_ERR_INVALID;
+  if (mode != 0 && mode != 1) return SLA_ERR_INVALID;
   const int n = A->n;
   if (ws == nullptr || ws_bytes < sla_ggt_loss_ws(n) || ((uintptr_t)ws & 255u)) return SLA_ERR_WORKSPACE;
   if (n == 0) return SLA_OK;
@@ -1079,9 +1109,17 @@ extern "C" int32_t sla_ggt_loss_grad(const sla_csr* A, const double* val, const 
   const int gr = grid_rows(n, 256);
   spmv_perm_kernel<<<gr, 256, 0, s>>>(n, GT->rowptr_t, GT->col_t, g_val, GT->perm_t, u, sv);      // s = G^T u
   spmv_perm_kernel<<<gr, 256, 0, s>>>(n, G->rowptr, G->col, g_val, nullptr, sv, y);               // y = G s
-  sub_kernel<<<gr, 256, 0, s>>>(n, xstar, y, err);                                                  // e
+  double* kap = nullptr;
+  if (mode == 1) {
+    kap = (double*)((char*)ws + 6 * vb);
+    spmv_perm_kernel<<<gr, 256, 0, s>>>(n, A->rowptr, A->col, val, nullptr, y, Ae);                // A y
+    loss_kappa_kernel<<<1, 1024, 0, s>>>(n, xstar, y, Ae, kap);                                     // k
+    sub_scaled_kernel<<<gr, 256, 0, s>>>(n, xstar, y, kap, err);                                    // e = x* - k y
+  } else {
+    sub_kernel<<<gr, 256, 0, s>>>(n, xstar, y, err);                                                // e = x* - y
+  }
   spmv_perm_kernel<<<gr, 256, 0, s>>>(n, A->rowptr, A->col, val, nullptr, err, Ae);                // A e
-  loss_scalars_kernel<<<1, 1024, 0, s>>>(n, xstar, u, err, Ae, loss);
+  loss_scalars_kernel<<<1, 1024, 0, s>>>(n, xstar, u, err, Ae, kap, loss);
   scale_kernel<<<gr, 256, 0, s>>>(n, loss, Ae, g);                                                  // g
   spmv_perm_kernel<<<gr, 256, 0, s>>>(n, GT->rowptr_t, GT->col_t, g_val, GT->perm_t, g, h);       // h = G^T g
   outer2_kernel<<<gr, 256, 0, s>>>(n, G->rowptr, G->col, g, sv, u, h, dG);

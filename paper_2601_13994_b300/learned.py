@@ -76,7 +76,7 @@ def _bind():
         "sla_mp_head_fwd": ([i32, P, P, P, P, P, P, P, P, P, P, P, P], i32),
         "sla_mp_head_bwd": ([i32, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, sz, P], i32),
         "sla_mp_head_bwd_ws": ([i32], sz),
-        "sla_ggt_loss_grad": ([CSR, P, CSR, P, CSRT, P, P, P, P, P, sz, P], i32),
+        "sla_ggt_loss_grad": ([CSR, P, CSR, P, CSRT, P, P, i32, P, P, P, sz, P], i32),
         "sla_ggt_loss_ws": ([i32], sz),
         "sla_ggt_normalize": ([CSR, P, CSR, CSRT, P, P, P], i32),
         "sla_fsai_factor": ([CSR, P, CSR, CSRT, P, P, P], i32),
@@ -261,14 +261,16 @@ class LearnedPreconditioner:
         return gr.g_val[:gr.nnz_g]
 
     # -------------------------------------------------------------- loss + backward
-    def loss_grad(self, gr: _Graph, b: torch.Tensor, xstar: torch.Tensor):
-        """Loss (device FP64 scalar) and dloss/dG (gr.dG)."""
+    def loss_grad(self, gr: _Graph, b: torch.Tensor, xstar: torch.Tensor, scale_free: bool = False):
+        """Loss (device FP64 scalar) and dloss/dG (gr.dG).  scale_free: the
+        A-norm error of the best multiple of G G^T b (sla_ggt_loss_grad
+        mode 1), which PCG cannot tell from G G^T itself."""
         lib = _bind()
         ws = self._scratch("loss", lib.sla_ggt_loss_ws(gr.n))
         _chk("sla_ggt_loss_grad", lib.sla_ggt_loss_grad(
             ctypes.byref(gr.A.c), gr.val.data_ptr(), ctypes.byref(gr.G.c), gr.g_val.data_ptr(),
-            ctypes.byref(gr.G._transpose_c), b.data_ptr(), xstar.data_ptr(), gr.loss.data_ptr(), gr.dG.data_ptr(),
-            ws.data_ptr(), ws.numel(), sla._stream_ptr(self.dev)))
+            ctypes.byref(gr.G._transpose_c), b.data_ptr(), xstar.data_ptr(), 1 if scale_free else 0,
+            gr.loss.data_ptr(), gr.dG.data_ptr(), ws.data_ptr(), ws.numel(), sla._stream_ptr(self.dev)))
         return gr.loss[0]
 
     def backward(self, gr: _Graph):
@@ -399,13 +401,44 @@ def training_system(k: int, n_lo: int = 64, n_hi: int = 128, seed0: int = 100000
     return I.diffusion2d_random(N, seed0 + k, sigma)
 
 
+def evaluate(model: LearnedPreconditioner, systems: int = 48, n_lo: int = 64, n_hi: int = 128,
+             seed0: int = 100000, rhs: int = 2, normalize: bool = True, scale_free: bool = True,
+             fsai: bool = False) -> float:
+    """Mean training loss of the factor over the training systems (rhs fresh
+    b ~ N(0, I) each, x* by the library's CG at rtol 1e-10): by default the
+    scale-free loss of the column-normalised factor, i.e. of the
+    preconditioner as PCG uses it.  fsai=True evaluates the classical FSAI
+    factor (already normalised) on the same pattern instead."""
+    dev = model.dev
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed0 + 7)
+    acc = []
+    for k in range(systems):
+        rp, c, v = training_system(k, n_lo, n_hi, seed0)
+        A = sla.CSRMatrix.from_numpy(rp, c, device=dev)
+        vt = torch.from_numpy(v).to(dev)
+        gr = model.graph(A, vt)
+        if fsai:
+            gr.g_val[:gr.nnz_g].copy_(fsai_factor(A, vt)[1])
+        else:
+            model.forward(gr, inference=True)
+            if normalize:
+                model.normalize(gr, gr.g_val[:gr.nnz_g])
+        for _ in range(rhs):
+            b = torch.randn(A.n, dtype=torch.float64, device=dev, generator=gen)
+            xs, _ = sla.cg(A, vt, b, rtol=1e-10)
+            acc.append(model.loss_grad(gr, b, xs, scale_free).clone())
+    return float(torch.stack(acc).mean())
+
+
 def train(model: LearnedPreconditioner, systems: int = 64, steps: int = 400, lr: float = 3e-3,
           n_lo: int = 64, n_hi: int = 128, seed0: int = 100000, log_every: int = 50, clip: float = 1.0,
-          verbose: bool = False):
+          verbose: bool = False, scale_free: bool = False):
     """Trains on `systems` generated systems for `steps` steps; every step
     draws one system and a fresh b ~ N(0, I), solves it with the library's
-    CG (rtol 1e-10) for x*, and takes one Adam step on the loss.  Returns
-    the loss history (host floats, every `log_every` steps averaged)."""
+    CG (rtol 1e-10) for x*, and takes one Adam step on the loss (the
+    scale-free loss with scale_free=True).  Returns the loss history (host
+    floats, every `log_every` steps averaged)."""
     dev = model.dev
     pool = []
     for k in range(systems):
@@ -423,7 +456,7 @@ def train(model: LearnedPreconditioner, systems: int = 64, steps: int = 400, lr:
         b = torch.randn(A.n, dtype=torch.float64, device=dev, generator=gen)
         xs, info = sla.cg(A, vt, b, rtol=1e-10)
         model.forward(gr)
-        loss = model.loss_grad(gr, b, xs)
+        loss = model.loss_grad(gr, b, xs, scale_free)
         model.backward(gr)
         model.adam(lr=lr, clip=clip)
         acc.append(loss)

@@ -9,7 +9,7 @@ from oracle import mpnn as OM
 from paper_2601_13994_b300 import inputs as I
 from paper_2601_13994_b300 import learned as LP
 from paper_2601_13994_b300 import sla
-from tests.gpu_util import csr, rel, to_dev
+from tests.gpu_util import csr, elementwise_rel, rel, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -142,7 +142,11 @@ def test_fsai_factor_matches_oracle(mat):
         assert info.iters <= 4
 
 
-def test_loss_gradient_wrt_g_matches_oracle():
+@pytest.mark.parametrize("scale_free", [False, True])
+def test_loss_gradient_wrt_g_matches_oracle(scale_free):
+    """sla_ggt_loss_grad (mode 0, and mode 1: the error of the best multiple
+    of G G^T b, its gradient taken at the minimising scale) against the
+    oracle's loss and autograd's gradient (through the scale in mode 1)."""
     import torch as T
     rp, c, v = I.diffusion2d_random(12, 6)
     n = len(rp) - 1
@@ -153,12 +157,20 @@ def test_loss_gradient_wrt_g_matches_oracle():
     gv = model.forward(gr).cpu().numpy()
     b = np.random.default_rng(1).standard_normal(n)
     xs, _ = oracle.pcg(rp, c, v, b, rtol=1e-13)
-    model.loss_grad(gr, to_dev(b), to_dev(xs))
+    Lg = float(model.loss_grad(gr, to_dev(b), to_dev(xs), scale_free))
     dG = gr.dG[:gr.nnz_g].cpu().numpy()
     g = T.tensor(gv, requires_grad=True)
-    L = OM.loss(gr.G.rowptr.cpu().numpy(), gr.G.col.cpu().numpy(), g, rp, c, v, b, xs)
+    L = OM.loss(gr.G.rowptr.cpu().numpy(), gr.G.col.cpu().numpy(), g, rp, c, v, b, xs, scale_free=scale_free)
     L.backward()
-    assert rel(dG, g.grad.numpy()) <= 1e-12
+    Lo = float(L.detach())
+    assert abs(Lg - Lo) <= 1e-12 * abs(Lo)
+    tol = 1e-10 if scale_free else 1e-12
+    assert rel(dG, g.grad.numpy()) <= tol
+    assert elementwise_rel(dG, g.grad.numpy()) <= tol
+    if scale_free:
+        # the loss and its gradient do not see a scale of G
+        gr.g_val[:gr.nnz_g].mul_(2.5)
+        assert abs(float(model.loss_grad(gr, to_dev(b), to_dev(xs), True)) - Lg) <= 1e-12 * Lg
 
 
 def test_training_beats_jacobi_on_unseen_system():

@@ -567,6 +567,50 @@ def test_mpnn_loss_zero_for_exact_factor_and_gradcheck():
     assert torch.autograd.gradcheck(f, ts, eps=1e-6, atol=1e-6, rtol=1e-5, fast_mode=True)
 
 
+def test_mpnn_scale_free_loss_is_the_minimum_over_scales():
+    """The scale-free training loss is min over k of the A-norm error of
+    x* - k G G^T b: pinned by the plain loss, which is a quadratic in k
+    (three evaluations with G scaled by sqrt(k) give its exact minimum), by
+    invariance under G -> a G, by a loss of 0 for an exact factor times any
+    scale, by 1 for G = 0, and by autograd's gradient (through k) against
+    central differences."""
+    import torch
+    from oracle import mpnn
+    rp, c, v = I.diffusion2d_random(5, 4, 1.2)
+    n = len(rp) - 1
+    A = dense(rp, c, v)
+    b = np.random.default_rng(3).standard_normal(n)
+    xs = np.linalg.solve(A, b)
+    P = mpnn.init_params(5, zero_head=False)
+    grp, gcol, gv = mpnn.forward({k: torch.tensor(t * 0.5) for k, t in P.items()}, rp, c, v)
+    gv = gv.detach()
+    L = lambda g, sf=False: float(mpnn.loss(grp, gcol, g, rp, c, v, b, xs, scale_free=sf))
+    # plain loss at scales k = 0, 1, 4 of G G^T: q(k) = a k^2 + b1 k + q0
+    q0, q1, q4 = L(gv * 0.0), L(gv), L(gv * 2.0)
+    a = (q4 - 4 * q1 + 3 * q0) / 12.0
+    b1 = q1 - q0 - a
+    kmin = -b1 / (2 * a)
+    lmin = q0 - b1 * b1 / (4 * a)
+    Lsf = L(gv, True)
+    assert a > 0 and abs(q0 - 1.0) <= 1e-14
+    assert abs(Lsf - lmin) <= 1e-12 and Lsf <= q1 + 1e-15
+    assert abs(L(gv * math.sqrt(kmin)) - lmin) <= 1e-12
+    for s_ in (0.37, 3.0, -1.5):
+        assert abs(L(gv * s_, True) - Lsf) <= 1e-12
+    assert L(gv * 0.0, True) == 1.0
+    # an exact factor (G G^T = A^-1) times any scale: loss 0
+    Gd = np.linalg.cholesky(np.linalg.inv(A))
+    rpf = np.array([0] + list(np.cumsum(np.arange(1, n + 1))), np.int32)
+    cf = np.concatenate([np.arange(i + 1) for i in range(n)]).astype(np.int32)
+    gvf = torch.tensor(np.concatenate([Gd[i, :i + 1] for i in range(n)]) * 1.7)
+    assert float(mpnn.loss(rpf, cf, gvf, rp, c, v, b, xs, scale_free=True)) < 1e-24
+    assert float(mpnn.loss(rpf, cf, gvf, rp, c, v, b, xs)) > 1.0
+    # gradient w.r.t. G's values through k, against central differences
+    g0 = gv.clone().requires_grad_(True)
+    assert torch.autograd.gradcheck(lambda g: mpnn.loss(grp, gcol, g, rp, c, v, b, xs, scale_free=True), (g0,),
+                                     eps=1e-6, atol=1e-7, rtol=1e-5)
+
+
 def _mpnn_path3_case():
     """A 3-node path graph and hand-chosen weights for which every step of the
     network can be followed on paper (the design: scaled entries, three node
