@@ -490,7 +490,10 @@ def extra_rows(dev, args, peak):
     its = np.atleast_1d(info.iters)
     fl = float((2 * int(rp[-1]) + 14 * N * N) * its.sum())
     tuned = sla.tuned_configs().get(("shared", N * N, int(rp[-1]), B))
-    out["batched_shared_1024x64x64"] = {"s": ms / 1e3, "iters_mean": float(its.mean()),
+    g2 = 2 * x  # dL/dx of L = sum x^2
+    adj = batched_adjoint_row(lambda: sla.adjoint_backward_batched(A, vt, x, g2, rtol=1e-8),
+                              (2 * int(rp[-1]) + 14 * N * N), 2 * B * int(rp[-1]))
+    out["batched_shared_1024x64x64"] = {"s": ms / 1e3, "iters_mean": float(its.mean()), "adjoint": adj,
                                         "iters_max": int(its.max()),
                                         "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
                                         "fp64_tflops": fl / (ms / 1e3) / 1e12,
@@ -515,7 +518,11 @@ def extra_rows(dev, args, peak):
     ms_std, _ = _time(lambda: sla.cg_batched_list(P, vt, bt, rtol=1e-8, config=0))
     ms_pipe, _ = _time(lambda: sla.cg_batched_list(P, vt, bt, rtol=1e-8, config=64))
     tuned = sla.tuned_configs().get(("list", P.n_max, P.total_rows, P.total_nnz, P.batch))
+    g2 = 2 * x  # dL/dx of L = sum x^2
+    adj = batched_adjoint_row(lambda: sla.adjoint_backward_batched_list(P, vt, x, g2, rtol=1e-8),
+                              [(2 * int(m[0][-1]) + 14 * (len(m[0]) - 1)) for m in mats], 2 * P.total_nnz)
     out["batched_list_512_fem"] = {"s": ms / 1e3, "total_rows": P.total_rows, "iters_mean": float(its.mean()),
+                                   "adjoint": adj,
                                    "tuned_config": tuned,
                                    "tuned_shape": sla.config_shape(tuned) if tuned is not None else None,
                                    "candidates": len(sla.LIST_CONFIGS),
@@ -556,7 +563,11 @@ def batched_bicgstab_rows(dev):
     ms, (x, info) = _time(lambda: sla.bicgstab_batched(A, vt, bt, rtol=1e-8))
     its = np.atleast_1d(info.iters)
     fl = float((2 * 2 * int(rp[-1]) + 2 * 15 * N * N) * its.sum())
-    out["bicgstab_batched_shared_1024x64x64"] = {
+    g2 = 2 * x  # dL/dx of L = sum x^2
+    adj = batched_adjoint_row(
+        lambda: sla.adjoint_backward_batched(A, vt, x, g2, method="bicgstab", rtol=1e-8),
+        (2 * 2 * int(rp[-1]) + 2 * 15 * N * N), 2 * B * int(rp[-1]))
+    out["bicgstab_batched_shared_1024x64x64"] = {"adjoint": adj,
         "s": ms / 1e3, "iters_mean": float(its.mean()), "iters_max": int(its.max()),
         "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
         "fp64_tflops": fl / (ms / 1e3) / 1e12, "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
@@ -575,6 +586,10 @@ def batched_bicgstab_rows(dev):
         fl += (2 * 2 * int(m[0][-1]) + 2 * 15 * (len(m[0]) - 1)) * int(its[s])
     # one CTA per system (1024 threads, vectors in the workspace) against the
     # default block teams (3 blocks from 32768 entries)
+    g2 = 2 * x  # dL/dx of L = sum x^2
+    adj = batched_adjoint_row(
+        lambda: sla.adjoint_backward_batched_list(P, vt, x, g2, method="bicgstab", rtol=1e-8),
+        [(2 * 2 * int(m[0][-1]) + 2 * 15 * (len(m[0]) - 1)) for m in mats], 2 * P.total_nnz)
     ms_cta, _ = _time(lambda: sla.bicgstab_batched_list(P, vt, bt, rtol=1e-8, config=3 | 16 | 32))
     ms_team, _ = _time(lambda: sla.bicgstab_batched_list(P, vt, bt, rtol=1e-8, config=0))
     tuned = sla.tuned_configs().get(("bicg_list", P.n_max, P.total_rows, P.total_nnz, P.batch))
@@ -583,8 +598,24 @@ def batched_bicgstab_rows(dev):
         "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
         "fp64_tflops": fl / (ms / 1e3) / 1e12, "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
         "tuned_config": tuned, "tuned_shape": sla.bicg_list_shape(tuned) if tuned is not None else None,
-        "candidates": len(sla.BICG_LIST_CONFIGS), "one_cta_s": ms_cta / 1e3, "teams_default_s": ms_team / 1e3}
+        "candidates": len(sla.BICG_LIST_CONFIGS), "one_cta_s": ms_cta / 1e3, "teams_default_s": ms_team / 1e3,
+        "adjoint": adj}
     return out
+
+
+def batched_adjoint_row(run, flops_per_iter, grad_flops):
+    """The batch's backward pass for L = sum x^2 (one call of
+    sla_adjoint_backward_batched_*: every system's adjoint solve in one
+    launch, then the gradient pass), timed with CUDA events.  flops_per_iter:
+    FP64 operations of one iteration, for every system alike (a number) or
+    per system (a list); grad_flops: those of the gradient pass."""
+    ms, (gb, gv, info) = _time(run)
+    its = np.atleast_1d(info.iters)
+    per = np.asarray(flops_per_iter, dtype=np.float64)
+    fl = float((per * its).sum()) + grad_flops
+    return {"s": ms / 1e3, "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+            "all_ok": bool((np.atleast_1d(info.status) == 0).all()),
+            "fp64_tflops": fl / (ms / 1e3) / 1e12, "fp64_frac": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
 
 
 def distributed_row(dev, N=64, P=8):
