@@ -40,7 +40,7 @@ FALLBACK_HBM_GBS = 6400.0
 # small case under the capture size rule) and scaled by rows to the bench's
 # N (traffic grows in proportion to the rows; profiles/pcg_iteration_diffusion3d_256.md);
 # valid only for these kernels.
-TRAFFIC_PER_ITER_176 = 923460608  # K1 561.1 MB + K2 271.1 MB + K3 91.3 MB, after K1's four-blocks-per-SM change
+TRAFFIC_PER_ITER_176 = 918527488  # K1 561.3 MB + K2 268.0 MB + K3 89.2 MB, the kernels as they are
 # FP64 peak: the driver measures none, so the run measures it itself
 # (sla_fp64_probe: independent FMA chains on every SM at full occupancy, best
 # of 5 after a warm-up, outside the timed region) and reports the derived
