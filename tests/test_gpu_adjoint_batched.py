@@ -4,6 +4,7 @@ system's lambda and -lambda_i x_j against the oracle's adjoint of that system
 alone; bit for bit what the separate batched solve, values gather and
 gradient pass give in the same launch shape; per-system statuses."""
 import numpy as np
+import scipy.sparse as sp
 import pytest
 import torch
 
@@ -137,3 +138,83 @@ def test_per_system_statuses(method):
     torch.cuda.synchronize()
     cs = np.atleast_1d(capped.status)
     assert cs[1] == 0 and all(sla.L.STATUS_NAMES[int(cs[s])] == "NOT_CONVERGED" for s in (0, 2, 3))
+
+
+def _adjoint_residuals_ok(rp, c, v, lam, g, method, tol):
+    """||A^T lambda - g|| <= tol ||g|| with the product taken on the CPU."""
+    A = sp.csr_matrix((v, c, rp))
+    At = A if method == "cg" else A.T.tocsr()
+    return np.linalg.norm(At @ lam - g) <= tol * np.linalg.norm(g)
+
+
+def _vs_oracle(rp, c, v, x, g, gb, gv, method):
+    """One system's adjoint against the oracle's at rtol 1e-12 (the smooth
+    dL/dx = 2x leaves some FEM systems short of 1e-13 in FP64)."""
+    ob, ov, io = oracle.adjoint_backward(rp, c, v, x, g, method=method, rtol=1e-12)
+    assert io["status"] == 0, io
+    for got, want in ((gb, ob), (gv, ov)):
+        assert rel(got, want) <= 1e-7
+        assert elementwise_rel(got, want) <= 1e-7
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("method", ["cg", "bicgstab"])
+def test_full_size_shared_1024_systems_64(method):
+    """The benchmark's shared-pattern batches (1024 systems on the 64 x 64
+    five-point pattern: diffusion for CG, upwind convection-diffusion for
+    BiCGStab, seeds 1000 + s) with L = sum x^2, adjoint rtol 1e-10: every
+    system's adjoint residual on the CPU, 16 sampled systems against the
+    oracle's adjoint element by element."""
+    B, N = 1024, 64
+    if method == "cg":
+        rp, c, vals = I.batched_shared_2d(N, B, seed0=1000, sigma=0.5)
+    else:
+        rp, c, vals = I.batched_convdiff_2d(N, B, seed0=1000)
+    A = csr(rp, c)
+    vt = to_dev(vals)
+    b = I.rhs_uniform(N * N, 7, batch=B)
+    solve = sla.cg_batched if method == "cg" else sla.bicgstab_batched
+    x, info = solve(A, vt, to_dev(b), rtol=1e-10)
+    gb, gv, ainfo = sla.adjoint_backward_batched(A, vt, x, 2 * x, method=method, rtol=1e-10)
+    torch.cuda.synchronize()
+    assert (np.atleast_1d(info.status) == 0).all() and (np.atleast_1d(ainfo.status) == 0).all()
+    xh, gbh, gvh = x.cpu().numpy(), gb.cpu().numpy(), gv.cpu().numpy()
+    for s in range(B):
+        assert _adjoint_residuals_ok(rp, c, vals[s], gbh[s], 2 * xh[s], method, 2e-10), s
+    idx = sorted(set(np.random.default_rng(12).choice(B, 14, replace=False).tolist()) | {0, B - 1})
+    for s in idx:
+        _vs_oracle(rp, c, vals[s], xh[s], 2 * xh[s], gbh[s], gvh[s], method)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("method", ["cg", "bicgstab"])
+def test_full_size_list_512(method):
+    """The benchmark's distinct-pattern batches (512 FEM Laplacians, seeds
+    2000 + s, for CG; 512 convection-diffusion rectangles, seeds 5000 + s,
+    for BiCGStab; n log-uniform in [1e3, 5e4], the large systems on block
+    teams) with L = sum x^2, adjoint rtol 1e-10: every adjoint residual on
+    the CPU, 16 systems (the four largest among them) against the oracle's
+    adjoint element by element."""
+    if method == "cg":
+        mats, seed_b = I.fem_list(512, seed0=2000), 3000
+    else:
+        mats, seed_b = I.convdiff_list(512, seed0=5000), 6000
+    P = sla.CSRList([(rp, c) for rp, c, _ in mats])
+    vt = to_dev(np.concatenate([v for _, _, v in mats]))
+    bt = to_dev(np.concatenate([I.rhs_uniform(len(rp) - 1, seed_b + s) for s, (rp, _, _) in enumerate(mats)]))
+    solve = sla.cg_batched_list if method == "cg" else sla.bicgstab_batched_list
+    x, info = solve(P, vt, bt, rtol=1e-10)
+    gb, gv, ainfo = sla.adjoint_backward_batched_list(P, vt, x, 2 * x, method=method, rtol=1e-10)
+    torch.cuda.synchronize()
+    assert (np.atleast_1d(info.status) == 0).all() and (np.atleast_1d(ainfo.status) == 0).all()
+    xh, gbh, gvh = x.cpu().numpy(), gb.cpu().numpy(), gv.cpu().numpy()
+    part = lambda a, off, s: a[off[s]:off[s + 1]]
+    for s, (rp, c, v) in enumerate(mats):
+        xs = part(xh, P.n_off_h, s)
+        assert _adjoint_residuals_ok(rp, c, v, part(gbh, P.n_off_h, s), 2 * xs, method, 2e-10), s
+    sizes = np.array([len(m[0]) for m in mats])
+    idx = set(np.argsort(sizes)[-4:].tolist()) | set(np.random.default_rng(13).choice(len(mats), 12, replace=False).tolist())
+    for s in sorted(idx):
+        rp, c, v = mats[s]
+        xs = part(xh, P.n_off_h, s)
+        _vs_oracle(rp, c, v, xs, 2 * xs, part(gbh, P.n_off_h, s), part(gvh, P.nnz_off_h, s), method)
