@@ -128,12 +128,13 @@ __device__ __forceinline__ void col_grid_sums(const double* part, int w, int nbl
     const int m = mj / w, j = mj % w;
     const double* src = part + (m * kMaxK + j) * kMaxBlocks;
     int b = g;
-    for (; b + 7 * G < nblocks; b += 8 * G) {
-      double v[8];
+    // 16 loads in flight per round (one L2 round trip each), added in order
+    for (; b + 15 * G < nblocks; b += 16 * G) {
+      double v[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = __ldcg(src + b + u * G);
+      for (int u = 0; u < 16; ++u) v[u] = __ldcg(src + b + u * G);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s += v[u];
+      for (int u = 0; u < 16; ++u) s += v[u];
     }
     for (; b < nblocks; b += G) s += __ldcg(src + b);
   }
@@ -484,12 +485,42 @@ __global__ void __launch_bounds__(kMT) multi_update_kernel(MultiPtrs P) {
 }
 
 // ---------------------------------------------------------------- K3
+// The end of a loop body (one thread): count it, stop every live column once
+// the hard cap on bodies is passed (each body advances some column's iters or
+// consumes a restart, so the cap only fires if the state machine is broken),
+// and set the loop's condition.
+__device__ void close_body(MultiState& st, const MultiDesc& d, int w, cudaGraphConditionalHandle cond,
+                           int use_cond) {
+  st.body += 1;
+  const int cap = d.max_iter + 2 * d.max_restarts + 8;
+  int live = 0;
+  for (int c = 0; c < w; ++c)
+    if (st.c[c].phase != kPhaseDone) live = 1;
+  if (live && st.body > cap) {
+    for (int c = 0; c < w; ++c)
+      if (st.c[c].phase != kPhaseDone) {
+        st.c[c].status = SLA_NOT_CONVERGED;
+        st.c[c].phase = kPhaseDone;
+      }
+    live = 0;
+  }
+  if (use_cond) cudaGraphSetConditional(cond, live ? 1u : 0u);
+}
+
+// P = Z + beta P for the running columns.  Only a column in its
+// true-residual pass (phase Check) has sums to make: without one, no block
+// writes partials and block 0 closes the body at the start (the p update
+// changes no phase, so the condition is already known); with one, the last
+// block adds the sums, takes the column's decision and closes the body.
 __global__ void __launch_bounds__(kMT)
 multi_pupdate_kernel(MultiPtrs P, cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ MSmem sm;
   const MultiDesc d = *P.d;
   const int w = d.w, n = d.n;
   load_phases(P.st, w, sm, kPhaseRun, kPhaseCheck);
+  bool checking = false;
+  for (int c = 0; c < w; ++c) checking |= sm.phase[c] == kPhaseCheck;
+  if (!checking && blockIdx.x == 0 && threadIdx.x == 0) close_body(*P.st, d, w, cond, use_cond);
   const int j = threadIdx.x % w;
   const int ph = sm.phase[j];
   const int i0 = (int)(((size_t)blockIdx.x * kMT + threadIdx.x) / w);
@@ -527,6 +558,7 @@ multi_pupdate_kernel(MultiPtrs P, cudaGraphConditionalHandle cond, int use_cond)
       v[1] = fma(ti, zi, v[1]);
     }
   }
+  if (!checking) return;
   col_block_sums<2>(v, w, P.part, sm.sh);
   if (!last_block_arrive(&P.st->cnt[3], &sm.last)) return;
   col_grid_sums<2>(P.part, w, gridDim.x, sm.tot, sm.scratch);
@@ -553,25 +585,7 @@ multi_pupdate_kernel(MultiPtrs P, cudaGraphConditionalHandle cond, int use_cond)
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    MultiState& st = *P.st;
-    // hard cap on loop bodies: each one advances some column's iters or
-    // consumes a restart, so this only fires if the state machine is broken
-    st.body += 1;
-    const int cap = d.max_iter + 2 * d.max_restarts + 8;
-    int live = 0;
-    for (int c = 0; c < w; ++c)
-      if (st.c[c].phase != kPhaseDone) live = 1;
-    if (live && st.body > cap) {
-      for (int c = 0; c < w; ++c)
-        if (st.c[c].phase != kPhaseDone) {
-          st.c[c].status = SLA_NOT_CONVERGED;
-          st.c[c].phase = kPhaseDone;
-        }
-      live = 0;
-    }
-    if (use_cond) cudaGraphSetConditional(cond, live ? 1u : 0u);
-  }
+  if (threadIdx.x == 0) close_body(*P.st, d, w, cond, use_cond);
 }
 
 // ---------------------------------------------------------------- final
