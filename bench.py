@@ -783,7 +783,8 @@ def inverse_rows(dev, peak, N=512, k=16):
             "step_s": ms_step / 1e3, "loss_theta0": float(L)}
 
 
-def learned_vs_jacobi(dev, systems=48, steps=800, lr=3e-3, n_lo=64, n_hi=128, evals=None, scale_free=False):
+def learned_vs_jacobi(dev, systems=48, steps=800, lr=3e-3, n_lo=64, n_hi=128, evals=None, scale_free=False,
+                      normalised=False):
     """Config 5: train the learned G G^T preconditioner (seeded, on systems the
     library's CG solves), then time PCG to rtol 1e-8 with it and with Jacobi on
     unseen systems; the FP64 true residual is checked by the solver."""
@@ -796,7 +797,7 @@ def learned_vs_jacobi(dev, systems=48, steps=800, lr=3e-3, n_lo=64, n_hi=128, ev
     zero = LP.LearnedPreconditioner(device=dev, seed=0)  # untrained: zero head
     t0 = time.perf_counter()
     hist = LP.train(model, systems=systems, steps=steps, lr=lr, n_lo=n_lo, n_hi=n_hi, log_every=max(1, steps // 8),
-                    scale_free=scale_free)
+                    scale_free=scale_free, normalised=normalised)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     # the scale-free loss (A-norm error of the best multiple of G G^T b) of
@@ -808,7 +809,8 @@ def learned_vs_jacobi(dev, systems=48, steps=800, lr=3e-3, n_lo=64, n_hi=128, ev
           "zero_head": LP.evaluate(zero, systems, n_lo, n_hi),
           "fsai": LP.evaluate(zero, systems, n_lo, n_hi, fsai=True)}
     out = {"train": {"systems": systems, "steps": steps, "grid": [n_lo, n_hi], "seconds": t_train,
-                     "loss": "scale-free" if scale_free else "plain",
+                     "loss": ("scale-free" if scale_free else "plain")
+                     + (", of the normalised factor" if normalised else ""),
                      "loss_first": hist[0], "loss_last": hist[-1], "scale_free_loss_normalised": ev}}
     evals = evals or [("2d_1024_sigma1", lambda: I.diffusion2d_random(1024, 900001, 1.0)),
                       ("3d_128_sigma1", lambda: I.diffusion3d_random(128, 900002, 1.0))]

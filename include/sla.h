@@ -436,6 +436,19 @@ int32_t sla_ggt_normalize(const sla_csr* A, const double* val, const sla_csr* G,
                           const sla_csr_t* GT, const double* g_val, double* g_out,
                           void* stream);
 
+/* Backward of sla_ggt_normalize for training through the normalisation:
+ * given dGn = dL/dGn on the pattern of G (Gn = the normalised factor of
+ * g_val, the values BEFORE normalisation), writes dG = dL/dg_val:
+ *   dG_aj = dGn_aj / sqrt(q_j) - (A G)_aj w_j / q_j^{3/2},
+ *   q_j = (G^T A G)_jj, w_j = sum_i dGn_ij G_ij  (A symmetric),
+ * and dG = dGn on a column whose form is not positive and finite (copied
+ * unchanged by the forward).  dG may be dGn; neither may overlap g_val
+ * (SLA_ERR_INVALID).  Same A, G, GT as sla_ggt_normalize.  One thread per
+ * column; asynchronous. */
+int32_t sla_ggt_normalize_bwd(const sla_csr* A, const double* val, const sla_csr* G,
+                              const sla_csr_t* GT, const double* g_val, const double* dGn,
+                              double* dG, void* stream);
+
 /* Adam on FP32 master weights (step t >= 1; clip > 0 clips each gradient
  * entry), writing the BF16 copy the kernels read. */
 int32_t sla_adam_step(int32_t np, float* p, const float* g, float* m, float* v,

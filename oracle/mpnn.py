@@ -156,6 +156,25 @@ def column_normalize(grp, gcol, g_val, rp, c, v):
     return out
 
 
+def column_normalize_t(grp, gcol, g_val, rp, c, v):
+    """The same normalisation with torch operations (differentiable in the
+    float64 tensor g_val), through dense matrices: Gn = G diag(q)^{-1/2},
+    q = diag(G^T A G), columns with q not positive and finite left as they
+    are; returns Gn's values in g_val's order.  For small systems (tests)."""
+    n = len(grp) - 1
+    rows = torch.tensor(np.repeat(np.arange(n), np.diff(grp)))
+    cols = torch.tensor(np.asarray(gcol, np.int64))
+    G = torch.zeros((n, n), dtype=torch.float64).index_put((rows, cols), g_val, accumulate=True)
+    Ad = torch.zeros((n, n), dtype=torch.float64)
+    ar = torch.tensor(np.repeat(np.arange(n), np.diff(rp)))
+    Ad = Ad.index_put((ar, torch.tensor(np.asarray(c, np.int64))), torch.tensor(np.asarray(v, np.float64)),
+                      accumulate=True)
+    q = torch.einsum("ij,ik,kj->j", G, Ad, G)
+    ok = (q > 0.0) & torch.isfinite(q)
+    scale = torch.where(ok, 1.0 / torch.sqrt(torch.where(ok, q, torch.ones_like(q))), torch.ones_like(q))
+    return g_val * scale[cols]
+
+
 def fsai_factor(rp, c, v):
     """The factored sparse approximate inverse on the pattern of tril(A)
     (Kolotilina and Yeremin), the classical non-learned G of M^{-1} = G G^T
@@ -202,7 +221,7 @@ def loss(grp, gcol, g_val, rp, c, v, b, xstar, scale_free=False):
     if scale_free:
         Ay = amul(y)
         yAy = y @ Ay
-        k = (xs @ Ay) / yAy if float(yAy) > 0.0 else torch.zeros((), dtype=torch.float64)
+        k = (xs @ Ay) / yAy if float(yAy.detach()) > 0.0 else torch.zeros((), dtype=torch.float64)
         y = k * y
     err = xs - y
     return (err @ amul(err)) / (xs @ bt)

@@ -1170,6 +1170,44 @@ __global__ void __launch_bounds__(256) ggt_normalize_kernel(int n, const int* __
     }
   }
 }
+// Backward of ggt_normalize_kernel: with q_j = (G^T A G)_jj and Gn_aj =
+// G_aj / sqrt(q_j), dq_j / dG_aj = 2 (A G)_aj (A symmetric), so for the
+// entries of column j
+//   dG_aj = dGn_aj / sqrt(q_j) - (A G)_aj w_j / q_j^{3/2},  w_j = sum_i dGn_ij G_ij;
+// a column left unchanged by the forward (q not positive and finite) passes
+// its gradient through.  One thread per column; the first pass forms q_j and
+// w_j, the second (A G)_aj again per entry.  dG may be dGn (each column's
+// entries are read before they are written, by the same thread).
+__global__ void __launch_bounds__(256) ggt_normalize_bwd_kernel(
+    int n, const int* __restrict__ rowptr, const int* __restrict__ col, const double* __restrict__ val,
+    const int* __restrict__ rpt, const int* __restrict__ rowt, const int* __restrict__ perm,
+    const double* __restrict__ g_val, const double* dGn, double* dG) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const int a = __ldg(rpt + j), e = __ldg(rpt + j + 1);
+    double q = 0.0, w = 0.0;
+    for (int ka = a; ka < e; ++ka) {
+      const int i = __ldg(rowt + ka);
+      double ag = 0.0;
+      for (int kb = a; kb < e; ++kb)
+        ag = fma(a_entry(rowptr, col, val, i, __ldg(rowt + kb)), g_val[__ldg(perm + kb)], ag);
+      const int p = __ldg(perm + ka);
+      q = fma(g_val[p], ag, q);
+      w = fma(dGn[p], g_val[p], w);
+    }
+    if (!(q > 0.0 && isfinite(q))) continue;  // unchanged by the forward: dG = dGn
+    const double inv = 1.0 / sqrt(q);
+    const double c3 = w * inv * inv * inv;
+    for (int ka = a; ka < e; ++ka) {
+      const int i = __ldg(rowt + ka);
+      double ag = 0.0;
+      for (int kb = a; kb < e; ++kb)
+        ag = fma(a_entry(rowptr, col, val, i, __ldg(rowt + kb)), g_val[__ldg(perm + kb)], ag);
+      const int p = __ldg(perm + ka);
+      dG[p] = fma(-ag, c3, dGn[p] * inv);
+    }
+  }
+}
+
 // The factored sparse approximate inverse (Kolotilina and Yeremin) on the
 // pattern of G = tril(A): one thread per column j (row j of the CSR of G^T,
 // whose entries list the rows P = {i >= j : A_ij != 0} in ascending order,
@@ -1269,6 +1307,28 @@ extern "C" int32_t sla_ggt_normalize(const sla_csr* A, const double* val, const 
   cudaStream_t s = (cudaStream_t)stream;
   ggt_normalize_kernel<<<grid_rows(n, 256), 256, 0, s>>>(n, A->rowptr, A->col, val, GT->rowptr_t, GT->col_t,
                                                           GT->perm_t, g_val, g_out);
+  MP_LAUNCH_CHECK();
+  return SLA_OK;
+}
+
+extern "C" int32_t sla_ggt_normalize_bwd(const sla_csr* A, const double* val, const sla_csr* G,
+                                         const sla_csr_t* GT, const double* g_val, const double* dGn, double* dG,
+                                         void* stream) {
+  if (A == nullptr || G == nullptr || GT == nullptr || A->n != G->n || A->n < 0 || G->nnz < 0)
+    return SLA_ERR_INVALID;
+  if (A->n == 0 || G->nnz == 0) return SLA_OK;
+  if (A->rowptr == nullptr || A->col == nullptr || val == nullptr || GT->rowptr_t == nullptr ||
+      GT->col_t == nullptr || GT->perm_t == nullptr || g_val == nullptr || dGn == nullptr || dG == nullptr)
+    return SLA_ERR_INVALID;
+  // dG may be dGn, but neither may overlap the forward's input values
+  if (ranges_overlap(dG, 8 * (size_t)G->nnz, g_val, 8 * (size_t)G->nnz)) return SLA_ERR_INVALID;
+  if (dG != dGn && ranges_overlap(dG, 8 * (size_t)G->nnz, dGn, 8 * (size_t)G->nnz)) return SLA_ERR_INVALID;
+  const int n = A->n;
+  // a column left unchanged passes dGn through: start from a copy
+  if (dG != dGn) SLA_CUDA_TRY(cudaMemcpyAsync(dG, dGn, 8 * (size_t)G->nnz, cudaMemcpyDeviceToDevice,
+                                              (cudaStream_t)stream));
+  ggt_normalize_bwd_kernel<<<grid_rows(n, 256), 256, 0, (cudaStream_t)stream>>>(
+      n, A->rowptr, A->col, val, GT->rowptr_t, GT->col_t, GT->perm_t, g_val, dGn, dG);
   MP_LAUNCH_CHECK();
   return SLA_OK;
 }

@@ -79,6 +79,7 @@ def _bind():
         "sla_ggt_loss_grad": ([CSR, P, CSR, P, CSRT, P, P, i32, P, P, P, sz, P], i32),
         "sla_ggt_loss_ws": ([i32], sz),
         "sla_ggt_normalize": ([CSR, P, CSR, CSRT, P, P, P], i32),
+        "sla_ggt_normalize_bwd": ([CSR, P, CSR, CSRT, P, P, P, P], i32),
         "sla_fsai_factor": ([CSR, P, CSR, CSRT, P, P, P], i32),
         "sla_adam_step": ([i32, P, P, P, P, f32, f32, f32, f32, i32, f32, P, P], i32),
         "sla_to_bf16": ([i32, P, P, P], i32),
@@ -140,6 +141,7 @@ class _Graph:
         self.dZ = f(n, WIDTH)
         self.dAgg = f(n, WIDTH)
         self.dG = torch.empty(max(m, 1), dtype=torch.float64, device=dev)
+        self.g_norm = torch.empty(max(m, 1), dtype=torch.float64, device=dev)  # normalised factor (training)
         self.loss = torch.empty(2, dtype=torch.float64, device=dev)
 
     def set_values(self, val: torch.Tensor):
@@ -261,14 +263,17 @@ class LearnedPreconditioner:
         return gr.g_val[:gr.nnz_g]
 
     # -------------------------------------------------------------- loss + backward
-    def loss_grad(self, gr: _Graph, b: torch.Tensor, xstar: torch.Tensor, scale_free: bool = False):
-        """Loss (device FP64 scalar) and dloss/dG (gr.dG).  scale_free: the
+    def loss_grad(self, gr: _Graph, b: torch.Tensor, xstar: torch.Tensor, scale_free: bool = False,
+                  g_val: torch.Tensor | None = None):
+        """Loss (device FP64 scalar) and dloss/dG (gr.dG) of the factor with
+        values g_val (default: the network's, gr.g_val).  scale_free: the
         A-norm error of the best multiple of G G^T b (sla_ggt_loss_grad
         mode 1), which PCG cannot tell from G G^T itself."""
         lib = _bind()
         ws = self._scratch("loss", lib.sla_ggt_loss_ws(gr.n))
+        gv = gr.g_val if g_val is None else g_val
         _chk("sla_ggt_loss_grad", lib.sla_ggt_loss_grad(
-            ctypes.byref(gr.A.c), gr.val.data_ptr(), ctypes.byref(gr.G.c), gr.g_val.data_ptr(),
+            ctypes.byref(gr.A.c), gr.val.data_ptr(), ctypes.byref(gr.G.c), gv.data_ptr(),
             ctypes.byref(gr.G._transpose_c), b.data_ptr(), xstar.data_ptr(), 1 if scale_free else 0,
             gr.loss.data_ptr(), gr.dG.data_ptr(), ws.data_ptr(), ws.numel(), sla._stream_ptr(self.dev)))
         return gr.loss[0]
@@ -325,6 +330,21 @@ class LearnedPreconditioner:
                                                     clip, self.pb.data_ptr(), sla._stream_ptr(self.dev)))
 
     # -------------------------------------------------------------- inference / solve
+    def loss_grad_normalised(self, gr: _Graph, b: torch.Tensor, xstar: torch.Tensor, scale_free: bool = False):
+        """The loss of the column-normalised factor (the one PCG uses) and
+        its gradient w.r.t. the network's values in gr.dG: normalise into
+        gr.g_norm, take the loss there, then sla_ggt_normalize_bwd."""
+        lib = _bind()
+        st = sla._stream_ptr(self.dev)
+        _chk("sla_ggt_normalize", lib.sla_ggt_normalize(
+            ctypes.byref(gr.A.c), gr.val.data_ptr(), ctypes.byref(gr.G.c), ctypes.byref(gr.G._transpose_c),
+            gr.g_val.data_ptr(), gr.g_norm.data_ptr(), st))
+        loss = self.loss_grad(gr, b, xstar, scale_free, g_val=gr.g_norm)
+        _chk("sla_ggt_normalize_bwd", lib.sla_ggt_normalize_bwd(
+            ctypes.byref(gr.A.c), gr.val.data_ptr(), ctypes.byref(gr.G.c), ctypes.byref(gr.G._transpose_c),
+            gr.g_val.data_ptr(), gr.dG.data_ptr(), gr.dG.data_ptr(), st))
+        return loss
+
     def normalize(self, gr: _Graph, g_val: torch.Tensor) -> torch.Tensor:
         """Columns of G divided by sqrt((G^T A G)_jj) (in place): the
         Kaporin-optimal column scaling, which the FSAI factor also has."""
@@ -433,12 +453,13 @@ def evaluate(model: LearnedPreconditioner, systems: int = 48, n_lo: int = 64, n_
 
 def train(model: LearnedPreconditioner, systems: int = 64, steps: int = 400, lr: float = 3e-3,
           n_lo: int = 64, n_hi: int = 128, seed0: int = 100000, log_every: int = 50, clip: float = 1.0,
-          verbose: bool = False, scale_free: bool = False):
+          verbose: bool = False, scale_free: bool = False, normalised: bool = False):
     """Trains on `systems` generated systems for `steps` steps; every step
     draws one system and a fresh b ~ N(0, I), solves it with the library's
     CG (rtol 1e-10) for x*, and takes one Adam step on the loss (the
-    scale-free loss with scale_free=True).  Returns the loss history (host
-    floats, every `log_every` steps averaged)."""
+    scale-free loss with scale_free=True; of the column-normalised factor,
+    through the normalisation's backward, with normalised=True).  Returns
+    the loss history (host floats, every `log_every` steps averaged)."""
     dev = model.dev
     pool = []
     for k in range(systems):
@@ -456,7 +477,10 @@ def train(model: LearnedPreconditioner, systems: int = 64, steps: int = 400, lr:
         b = torch.randn(A.n, dtype=torch.float64, device=dev, generator=gen)
         xs, info = sla.cg(A, vt, b, rtol=1e-10)
         model.forward(gr)
-        loss = model.loss_grad(gr, b, xs, scale_free)
+        if normalised:
+            loss = model.loss_grad_normalised(gr, b, xs, scale_free)
+        else:
+            loss = model.loss_grad(gr, b, xs, scale_free)
         model.backward(gr)
         model.adam(lr=lr, clip=clip)
         acc.append(loss)

@@ -1,5 +1,7 @@
 """Learned factored preconditioner: kernels against the FP64 oracle
 (oracle/mpnn.py), and what training gains over Jacobi-PCG."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -279,3 +281,42 @@ def test_dense_layer_tensor_core_shape_rules():
     assert float((Y.double() - ref).abs().max()) <= 1e-6 * float(ref.abs().max())
     assert lib.sla_mp_dense_fwd_ex(n, 3, X.data_ptr(), 0, None, 32, W.data_ptr(), None, None, 1, None,
                                    Y.data_ptr(), 7, None) == LP.L.SLA_ERR_INVALID
+
+
+@pytest.mark.parametrize("scale_free", [False, True])
+def test_training_through_the_normalisation_matches_oracle(scale_free):
+    """sla_ggt_normalize_bwd against autograd through the oracle's
+    differentiable normalisation, and the loss of the normalised factor with
+    its gradient w.r.t. the network's values (normalise, loss, backward of
+    the normalisation) against the oracle's autograd of the same chain."""
+    import torch as T
+    rp, c, v = I.diffusion2d_random(14, 8, 1.2)
+    n = len(rp) - 1
+    model = LP.LearnedPreconditioner(seed=4)
+    model.view("v").copy_(T.linspace(-0.2, 0.2, 32, device="cuda"))
+    model.view("vd").fill_(0.05)
+    model._sync_bf16()
+    gr = model.graph(csr(rp, c), to_dev(v))
+    gv = model.forward(gr).clone()
+    grp, gcol = gr.G.rowptr.cpu().numpy(), gr.G.col.cpu().numpy()
+    # the backward alone, on a random dL/dGn
+    dgn = np.random.default_rng(5).standard_normal(gr.nnz_g)
+    dG = T.empty_like(gv)
+    lib = LP._bind()
+    rc = lib.sla_ggt_normalize_bwd(ctypes.byref(gr.A.c), gr.val.data_ptr(), ctypes.byref(gr.G.c),
+                                   ctypes.byref(gr.G._transpose_c), gv.data_ptr(), to_dev(dgn).data_ptr(),
+                                   dG.data_ptr(), sla._stream_ptr(gv.device))
+    assert rc == 0
+    g = T.tensor(gv.cpu().numpy(), requires_grad=True)
+    (OM.column_normalize_t(grp, gcol, g, rp, c, v) * T.tensor(dgn)).sum().backward()
+    assert rel(dG.cpu().numpy(), g.grad.numpy()) <= 1e-12
+    # the whole chain
+    b = np.random.default_rng(6).standard_normal(n)
+    xs, _ = oracle.pcg(rp, c, v, b, rtol=1e-13)
+    L = float(model.loss_grad_normalised(gr, to_dev(b), to_dev(xs), scale_free))
+    got = gr.dG[:gr.nnz_g].cpu().numpy()
+    g2 = T.tensor(gv.cpu().numpy(), requires_grad=True)
+    Lo = OM.loss(grp, gcol, OM.column_normalize_t(grp, gcol, g2, rp, c, v), rp, c, v, b, xs, scale_free=scale_free)
+    Lo.backward()
+    assert abs(L - float(Lo.detach())) <= 1e-12 * abs(float(Lo.detach()))
+    assert rel(got, g2.grad.numpy()) <= 1e-10 and elementwise_rel(got, g2.grad.numpy()) <= 1e-10

@@ -611,6 +611,29 @@ def test_mpnn_scale_free_loss_is_the_minimum_over_scales():
                                      eps=1e-6, atol=1e-7, rtol=1e-5)
 
 
+def test_column_normalize_torch_form_matches_loops_and_gradcheck():
+    """The differentiable normalisation (for the gradient of training through
+    it) equals the loop form value for value, gives diag(G^T A G) = I, and
+    its autograd gradient matches central differences."""
+    import torch
+    from oracle import mpnn
+    rp, c, v = I.diffusion2d_random(5, 9, 1.3)
+    n = len(rp) - 1
+    P = mpnn.init_params(6, zero_head=False)
+    grp, gcol, gv = mpnn.forward({k: torch.tensor(t * 0.5) for k, t in P.items()}, rp, c, v)
+    gv = gv.detach()
+    ref = mpnn.column_normalize(grp, gcol, gv.numpy(), rp, c, v)
+    got = mpnn.column_normalize_t(grp, gcol, gv, rp, c, v).numpy()
+    assert np.allclose(got, ref, rtol=1e-14, atol=0)
+    Gn = dense(grp, gcol, got, n)
+    A = dense(rp, c, v)
+    assert np.allclose(np.diag(Gn.T @ A @ Gn), 1.0, rtol=1e-13)
+    g0 = gv.clone().requires_grad_(True)
+    w = torch.tensor(np.random.default_rng(2).standard_normal(len(gcol)))
+    assert torch.autograd.gradcheck(lambda g: (mpnn.column_normalize_t(grp, gcol, g, rp, c, v) * w).sum(), (g0,),
+                                     eps=1e-6, atol=1e-7, rtol=1e-5)
+
+
 def _mpnn_path3_case():
     """A 3-node path graph and hand-chosen weights for which every step of the
     network can be followed on paper (the design: scaled entries, three node
