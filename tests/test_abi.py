@@ -420,3 +420,26 @@ def test_eig_vector_adjoint_arguments_rejected_without_launch():
     for k, acc in ((0, 0), (9, 0), (6, 2)):
         assert lib.sla_eig_vector_grad_values(ctypes.byref(A), k, fake, fake, fake, acc,
                                               None) == L.SLA_ERR_INVALID
+
+
+def test_normalize_bwd_rejects_bad_arguments_without_launch():
+    """sla_ggt_normalize_bwd: mismatched sizes, null pointers and a dG that
+    overlaps the forward's values are rejected before any launch (fake
+    pointers: a launch would fault); dG == dGn is allowed."""
+    lib = L.lib()
+    lib.sla_ggt_normalize_bwd.restype = ctypes.c_int32
+    fake = ctypes.c_void_p(0x1000)
+    A = L.SlaCsr(10, 28, fake, fake)
+    G = L.SlaCsr(10, 19, fake, fake)
+    GT = L.SlaCsrT(fake, fake, fake)
+    g, d, o = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x20000), ctypes.c_void_p(0x30000)
+
+    def call(a=A, gg=G, gt=GT, gv=g, dgn=d, dg=o):
+        return lib.sla_ggt_normalize_bwd(ctypes.byref(a), fake, ctypes.byref(gg), None if gt is None else ctypes.byref(gt),
+                                         gv, dgn, dg, None)
+    assert call(a=L.SlaCsr(11, 28, fake, fake)) == L.SLA_ERR_INVALID          # n differs
+    assert call(gt=None) == L.SLA_ERR_INVALID
+    assert call(dgn=None) == L.SLA_ERR_INVALID
+    assert call(dg=ctypes.c_void_p(0x10000 + 8 * 18)) == L.SLA_ERR_INVALID     # dG overlaps g_val
+    assert call(dg=ctypes.c_void_p(0x20000 + 8)) == L.SLA_ERR_INVALID          # dG partly overlaps dGn
+    assert call(gg=L.SlaCsr(10, 0, fake, fake)) == L.SLA_OK                    # nothing to do
